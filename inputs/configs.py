@@ -1,0 +1,295 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+The paper's simulations use Planck LFI 70 GHz beams, rms maps and masks
+(Sect. 3) that are not available here.  These recipes stand in for them with
+closed-form spectra, Gaussian beams, a latitude cut plus point-source holes
+and a smooth scan-depth ("hits") pattern.  Everything is drawn from the
+Philox streams in :mod:`inputs.philox`, so any consumer regenerates identical
+inputs from the same seed.
+
+This module computes inputs only: power spectra, beams, masks, noise levels
+and white-noise draws.  It contains none of the sampler's arithmetic (no
+spherical harmonic transform, no solver).  The data map d = Y B a + n needs a
+transform, so callers assemble it with their own alm2map from ``signal_alm``
+and ``noise_map`` returned here.
+
+Layouts: alm arrays are complex128, m-major, index(l, m) = m(2L+1-m)/2 + l
+for 0 <= m <= l <= L; maps are float64 in HEALPix RING order.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import philox as px
+
+ARCMIN = math.pi / (180.0 * 60.0)
+DEG = math.pi / 180.0
+# North ecliptic pole in Galactic coordinates (l, b), degrees.
+NEP_GAL_DEG = (96.38, 29.81)
+
+
+# ----------------------------------------------------------------------------
+# index helpers
+# ----------------------------------------------------------------------------
+def nalm(lmax: int) -> int:
+    return (lmax + 1) * (lmax + 2) // 2
+
+
+def alm_index(l, m, lmax: int):
+    return m * (2 * lmax + 1 - m) // 2 + l
+
+
+def alm_lm(lmax: int):
+    """(l, m) integer arrays in storage order."""
+    ls, ms = [], []
+    for m in range(lmax + 1):
+        ls.append(np.arange(m, lmax + 1))
+        ms.append(np.full(lmax + 1 - m, m))
+    return np.concatenate(ls), np.concatenate(ms)
+
+
+# ----------------------------------------------------------------------------
+# spectra and beams
+# ----------------------------------------------------------------------------
+def cl_flat(lmax: int, amp: float = 1000.0) -> np.ndarray:
+    """C_l = 2 pi amp / (l (l+1)) uK^2 for l >= 2, C_0 = C_1 = 0."""
+    l = np.arange(lmax + 1, dtype=np.float64)
+    cl = np.zeros(lmax + 1)
+    cl[2:] = 2.0 * math.pi * amp / (l[2:] * (l[2:] + 1.0))
+    return cl
+
+
+def cl_damped(lmax: int, lcut: float = 1500.0) -> np.ndarray:
+    l = np.arange(lmax + 1, dtype=np.float64)
+    return cl_flat(lmax) * np.exp(-l * (l + 1.0) / lcut ** 2)
+
+
+def gauss_beam(lmax: int, fwhm_rad: float) -> np.ndarray:
+    """b_l = exp(-l(l+1) sigma_b^2 / 2), sigma_b = FWHM / sqrt(8 ln 2)."""
+    sig = fwhm_rad / math.sqrt(8.0 * math.log(2.0))
+    l = np.arange(lmax + 1, dtype=np.float64)
+    return np.exp(-0.5 * l * (l + 1.0) * sig * sig)
+
+
+# ----------------------------------------------------------------------------
+# HEALPix pixel centres (used here only to draw masks and noise levels)
+# ----------------------------------------------------------------------------
+def pixel_centres(nside: int):
+    """(z, phi) of every pixel centre in RING order (Gorski et al. 2005)."""
+    zs, phis = [], []
+    n = nside
+    for i in range(1, 4 * n):
+        if i < n:
+            npr, z, shift = 4 * i, 1.0 - i * i / (3.0 * n * n), 1.0
+        elif i <= 3 * n:
+            npr, z = 4 * n, 4.0 / 3.0 - 2.0 * i / (3.0 * n)
+            shift = 1.0 if (i - n) % 2 == 0 else 0.0
+        else:
+            ii = 4 * n - i
+            npr, z, shift = 4 * ii, -(1.0 - ii * ii / (3.0 * n * n)), 1.0
+        j = np.arange(npr, dtype=np.float64)
+        zs.append(np.full(npr, z))
+        phis.append((j + 0.5 * shift) * (2.0 * math.pi / npr))
+    return np.concatenate(zs), np.concatenate(phis)
+
+
+def _unit(z, phi):
+    s = np.sqrt(np.maximum(0.0, 1.0 - z * z))
+    return np.stack([s * np.cos(phi), s * np.sin(phi), z], axis=-1)
+
+
+def latitude_cut(z, bcut_deg: float) -> np.ndarray:
+    """True where the pixel is masked: |b| < bcut (b = Galactic latitude)."""
+    return np.abs(z) < math.sin(bcut_deg * DEG)
+
+
+def point_source_holes(z, phi, nholes: int, radius_deg: float, seed: int) -> np.ndarray:
+    """True inside any of ``nholes`` discs of the given radius whose centres are
+    uniform on the sphere (Philox stream 4); a pixel is inside if its centre is."""
+    if nholes == 0:
+        return np.zeros(z.shape, bool)
+    u = px.uniform(seed, px.STREAM_HOLES, 2 * nholes)
+    zc = 2.0 * u[0::2] - 1.0
+    pc = 2.0 * math.pi * u[1::2]
+    vc = _unit(zc, pc)
+    cosr = math.cos(radius_deg * DEG)
+    rad = radius_deg * DEG
+    masked = np.zeros(z.shape, bool)
+    negz = -z  # RING order has z non-increasing, so -z is sorted
+    for k in range(nholes):
+        th = math.acos(max(-1.0, min(1.0, zc[k])))
+        zhi = math.cos(max(0.0, th - rad))
+        zlo = math.cos(min(math.pi, th + rad))
+        i0 = int(np.searchsorted(negz, -zhi, side="left"))
+        i1 = int(np.searchsorted(negz, -zlo, side="right"))
+        vp = _unit(z[i0:i1], phi[i0:i1])
+        masked[i0:i1] |= (vp @ vc[k]) > cosr
+    return masked
+
+
+def hits_proxy(z, phi) -> np.ndarray:
+    """Scan-depth proxy hits = 1 + 4 sin^2(ecliptic latitude)."""
+    l0, b0 = (v * DEG for v in NEP_GAL_DEG)
+    nep = np.array([math.cos(b0) * math.cos(l0), math.cos(b0) * math.sin(l0), math.sin(b0)])
+    sinbeta = _unit(z, phi) @ nep
+    return 1.0 + 4.0 * sinbeta ** 2
+
+
+# ----------------------------------------------------------------------------
+# white noise
+# ----------------------------------------------------------------------------
+def white_alm(lmax: int, seed: int, stream: int, offset: int = 0) -> np.ndarray:
+    """Unit white noise in harmonic space: a_l0 ~ N(0,1) real; for m > 0 the
+    real and imaginary parts are N(0, 1/2) each."""
+    p = nalm(lmax)
+    g = px.normal(seed, stream, 2 * p, offset)
+    re, im = g[0::2], g[1::2]
+    _, ms = alm_lm(lmax)
+    scale = np.where(ms == 0, 1.0, math.sqrt(0.5))
+    out = (re + 1j * im) * scale
+    out[ms == 0] = re[ms == 0]
+    return out
+
+
+def white_map(npix: int, seed: int, stream: int, offset: int = 0) -> np.ndarray:
+    return px.normal(seed, stream, npix, offset)
+
+
+# ----------------------------------------------------------------------------
+# workloads
+# ----------------------------------------------------------------------------
+@dataclass
+class Problem:
+    """One constrained-realization problem (temperature, or T+E+B)."""
+    name: str
+    nside: int
+    lmax: int
+    ncomp: int                 # 1 = T, 3 = T,E,B
+    cl: np.ndarray             # (lmax+1,) for T; (4, lmax+1) = TT, EE, BB, TE for T+E+B
+    bl: np.ndarray             # (lmax+1,)
+    ninv: np.ndarray           # (npix,) T, or (2, npix) = (T, P) with Q and U sharing P
+    signal_alm: np.ndarray     # (ncomp, nalm) complex
+    noise_map: np.ndarray      # (ncomp_map, npix): T or T, Q, U
+    w1: np.ndarray             # (ncomp, nalm) complex
+    w2: np.ndarray             # (ncomp_map, npix)
+    tol: float
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def npix(self) -> int:
+        return 12 * self.nside * self.nside
+
+
+def _sqrt_cl_cholesky(cl4: np.ndarray):
+    """Lower Cholesky factor rows of the per-l (T, E) block for drawing
+    correlated signal alms; B is independent."""
+    tt, ee, bb, te = cl4
+    with np.errstate(divide="ignore", invalid="ignore"):
+        l11 = np.sqrt(tt)
+        l21 = np.where(tt > 0, te / np.where(tt > 0, l11, 1.0), 0.0)
+        l22 = np.sqrt(np.maximum(ee - l21 ** 2, 0.0))
+    return l11, l21, l22, np.sqrt(bb)
+
+
+def config(index: int, batch: int | None = None, lmax: int | None = None,
+           nside: int | None = None) -> Problem | list:
+    """Build one of the five workloads (0..4).
+
+    ``nside``/``lmax`` override the resolution (used for reduced-size parity
+    cases of the same recipe).  Config 2 returns a list of chains; config 4
+    returns ``batch`` problems (default 8) that share cl, beam and noise."""
+    if index == 0:
+        ns = nside or 32
+        L = lmax or 64
+        cl = cl_flat(L)
+        bl = gauss_beam(L, 2.0 * DEG)
+        npix = 12 * ns * ns
+        sigma = 10.0
+        ninv = np.full(npix, 1.0 / sigma ** 2)
+        a = np.sqrt(cl)[alm_lm(L)[0]] * white_alm(L, 0, px.STREAM_SIGNAL)
+        n = sigma * white_map(npix, 0, px.STREAM_NOISE)
+        w1 = white_alm(L, 1, px.STREAM_W1)
+        w2 = white_map(npix, 1, px.STREAM_W2)
+        return Problem("c0", ns, L, 1, cl, bl, ninv, a[None], n[None], w1[None], w2[None], 1e-8)
+    if index in (1, 3):
+        ns = nside or (256 if index == 1 else 512)
+        L = lmax or (512 if index == 1 else 1024)
+        seed = index
+        cl = cl_damped(L)
+        bl = gauss_beam(L, 30.0 * ARCMIN)
+        z, phi = pixel_centres(ns)
+        hits = hits_proxy(z, phi)
+        sig = 20.0 / np.sqrt(hits)
+        masked = latitude_cut(z, 20.0) | point_source_holes(z, phi, 50, 1.0, seed)
+        ninv = np.where(masked, 0.0, 1.0 / sig ** 2)
+        a = np.sqrt(cl)[alm_lm(L)[0]] * white_alm(L, seed, px.STREAM_SIGNAL)
+        n = sig * white_map(z.size, seed, px.STREAM_NOISE)
+        w1 = white_alm(L, seed + 100, px.STREAM_W1)
+        w2 = white_map(z.size, seed + 100, px.STREAM_W2)
+        return Problem(f"c{index}", ns, L, 1, cl, bl, ninv, a[None], n[None], w1[None],
+                       w2[None], 1e-6, {"fsky": float(1.0 - masked.mean())})
+    if index == 2:
+        nch = batch or 64
+        u = px.uniform(2, px.STREAM_CHAINS, 3 * nch)
+        chains = []
+        for c in range(nch):
+            ns = (64, 128, 256)[min(2, int(u[3 * c] * 3))]
+            L = 2 * ns if u[3 * c + 1] < 0.5 else 3 * ns - 1
+            if nside is not None:
+                ns = nside
+                L = lmax or 2 * ns
+            amp = 0.8 + 0.4 * u[3 * c + 2]
+            cl = amp * cl_flat(L)
+            bl = gauss_beam(L, (60.0 / ns) * DEG)
+            z, phi = pixel_centres(ns)
+            masked = latitude_cut(z, 15.0)
+            sigma = 15.0
+            ninv = np.where(masked, 0.0, 1.0 / sigma ** 2)
+            key = 1000 + c
+            a = np.sqrt(cl)[alm_lm(L)[0]] * white_alm(L, key, px.STREAM_SIGNAL)
+            n = sigma * white_map(z.size, key, px.STREAM_NOISE)
+            w1 = white_alm(L, key, px.STREAM_W1)
+            w2 = white_map(z.size, key, px.STREAM_W2)
+            chains.append(Problem(f"c2.{c}", ns, L, 1, cl, bl, ninv, a[None], n[None],
+                                  w1[None], w2[None], 1e-6, {"amp": amp}))
+        return chains
+    if index == 4:
+        ns = nside or 1024
+        L = lmax or 2048
+        nb = batch or 8
+        tt = cl_damped(L)
+        ee = 0.05 * tt
+        te = 0.3 * np.sqrt(tt * ee)
+        bb = 1e-3 * ee
+        cl4 = np.stack([tt, ee, bb, te])
+        bl = gauss_beam(L, 10.0 * ARCMIN)
+        z, phi = pixel_centres(ns)
+        hits = hits_proxy(z, phi)
+        masked = latitude_cut(z, 20.0) | point_source_holes(z, phi, 200, 1.0, 4)
+        sig_t = 30.0 / np.sqrt(hits)
+        sig_p = 42.0 / np.sqrt(hits)
+        ninv = np.stack([np.where(masked, 0.0, 1.0 / sig_t ** 2),
+                         np.where(masked, 0.0, 1.0 / sig_p ** 2)])
+        l11, l21, l22, lbb = _sqrt_cl_cholesky(cl4)
+        ls = alm_lm(L)[0]
+        p = nalm(L)
+        out = []
+        for b in range(nb):
+            key = 4000 + b
+            wt = white_alm(L, key, px.STREAM_SIGNAL, 0)
+            we = white_alm(L, key, px.STREAM_SIGNAL, 2 * p)
+            wb = white_alm(L, key, px.STREAM_SIGNAL, 4 * p)
+            a = np.stack([l11[ls] * wt, l21[ls] * wt + l22[ls] * we, lbb[ls] * wb])
+            npx = z.size
+            nmap = np.stack([sig_t * white_map(npx, key, px.STREAM_NOISE, 0),
+                             sig_p * white_map(npx, key, px.STREAM_NOISE, npx),
+                             sig_p * white_map(npx, key, px.STREAM_NOISE, 2 * npx)])
+            w1 = np.stack([white_alm(L, key, px.STREAM_W1, k * 2 * p) for k in range(3)])
+            w2 = np.stack([white_map(npx, key, px.STREAM_W2, k * npx) for k in range(3)])
+            out.append(Problem(f"c4.{b}", ns, L, 3, cl4, bl, ninv, a, nmap, w1, w2, 1e-6,
+                               {"fsky": float(1.0 - masked.mean())}))
+        return out
+    raise ValueError(f"unknown config {index}")

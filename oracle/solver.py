@@ -1,0 +1,225 @@
+"""Oracle constrained-realization solver (FP64, CPU).  Test infrastructure only.
+
+Eq. (mapmakingeq) of Sect. 2.2.1, with the beam applied in harmonic space
+and the synthesis Y written out:
+
+    A a = b,   A = S^-1 + B Y^T N^-1 Y B,
+    b = B Y^T (N^-1 d + N^-1/2 w2) + S^-1/2 w1.
+
+- S is diagonal in (l, m) with C_l (temperature) or the 3x3 (T, E, B) block
+  of Sect. 2.2.2 with EB = TB = 0.  Modes where S is singular (C_0 = C_1 = 0)
+  are held at zero: there A acts as the identity and b is zero.
+- B is the beam b_l; N^-1 is a diagonal pixel weight, 0 in the mask (App. A).
+- S^-1/2 is the inverse of the symmetric principal square root of S.
+- Solved by preconditioned conjugate gradients (Sect. 2.2.1 cites
+  Shewchuk 1994) with the diagonal preconditioner of Sect. 4,
+  M = S^-1 + b_l^2 D_lm, D_lm = sum_r g_lm(theta_r) sum_{p in r} N^-1_p.
+All inner products use the metric of :func:`oracle.sht.dot_q6`.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import sht
+
+
+class Problem:
+    """Operator data for one realization.
+
+    cl: (lmax+1,) for temperature or (4, lmax+1) = TT, EE, BB, TE.
+    ninv: (npix,) or (2, npix) = (N^-1 for T, N^-1 for Q and U).
+    """
+
+    def __init__(self, geom: sht.Geometry, lmax: int, cl, bl, ninv):
+        self.g = geom
+        self.lmax = lmax
+        cl = np.asarray(cl, np.float64)
+        self.ncomp = 1 if cl.ndim == 1 else 3
+        self.bl = np.asarray(bl, np.float64)
+        ninv = np.asarray(ninv, np.float64)
+        self.ninv = ninv.reshape(1, -1) if ninv.ndim == 1 else ninv
+        self.ls = sht.ls_of(lmax)
+        L1 = lmax + 1
+        # per-l inverse prior and inverse square root, as (ncomp, ncomp, L+1)
+        sinv = np.zeros((self.ncomp, self.ncomp, L1))
+        sinvh = np.zeros((self.ncomp, self.ncomp, L1))
+        active = np.zeros(L1, bool)
+        for l in range(L1):
+            if self.ncomp == 1:
+                S = np.array([[cl[l]]])
+            else:
+                tt, ee, bb, te = cl[:, l]
+                S = np.array([[tt, te, 0.0], [te, ee, 0.0], [0.0, 0.0, bb]])
+            w, V = np.linalg.eigh(S)
+            if np.all(w > 0):
+                active[l] = True
+                sinv[:, :, l] = (V / w) @ V.T
+                sinvh[:, :, l] = (V / np.sqrt(w)) @ V.T
+            else:
+                sinv[:, :, l] = np.eye(self.ncomp)
+        self.sinv, self.sinvh, self.active = sinv, sinvh, active
+        self.bmask = np.where(active, self.bl, 0.0)
+
+    # -- pieces -------------------------------------------------------------
+    def _per_l(self, mat, x):
+        """Apply an (ncomp, ncomp, L+1) per-l matrix to x of shape (ncomp, nalm)."""
+        M = mat[:, :, self.ls]
+        return np.einsum("ijp,jp->ip", M, x)
+
+    def Y(self, a):
+        if self.ncomp == 1:
+            return sht.alm2map(self.g, self.lmax, a[0])[None]
+        T = sht.alm2map(self.g, self.lmax, a[0])
+        Q, U = sht.alm2map_spin2(self.g, self.lmax, a[1], a[2])
+        return np.stack([T, Q, U])
+
+    def Yt(self, m):
+        if self.ncomp == 1:
+            return sht.alm2map_adjoint(self.g, self.lmax, m[0])[None]
+        T = sht.alm2map_adjoint(self.g, self.lmax, m[0])
+        E, B = sht.alm2map_spin2_adjoint(self.g, self.lmax, m[1], m[2])
+        return np.stack([T, E, B])
+
+    def ninv_maps(self):
+        if self.ncomp == 1:
+            return self.ninv[:1]
+        return np.stack([self.ninv[0], self.ninv[1], self.ninv[1]])
+
+    def beam(self, a):
+        return a * self.bmask[self.ls][None]
+
+    # -- operator -----------------------------------------------------------
+    def matvec(self, x):
+        x = np.asarray(x, np.complex128).reshape(self.ncomp, -1)
+        y = self.Y(self.beam(x)) * self.ninv_maps()
+        out = self.beam(self.Yt(y)) + self._per_l(self.sinv, x)
+        return _zero_im_m0(out, self.lmax)
+
+    def rhs(self, d, w1, w2):
+        d = np.asarray(d, np.float64).reshape(self.ncomp, -1)
+        w2 = np.asarray(w2, np.float64).reshape(self.ncomp, -1)
+        w1 = np.asarray(w1, np.complex128).reshape(self.ncomp, -1)
+        nv = self.ninv_maps()
+        pix = nv * d + np.sqrt(nv) * w2
+        b = self.beam(self.Yt(pix)) + self._per_l(self.sinvh, w1)
+        return _zero_im_m0(b, self.lmax)
+
+    def rhs_parts(self, d, w1, w2):
+        """(mean-field part, fluctuation part) of the right-hand side, Eqs.
+        (mean-field-map) and (fluc-map)."""
+        z = np.zeros_like(np.asarray(d, np.float64).reshape(self.ncomp, -1))
+        zw = np.zeros_like(np.asarray(w1, np.complex128).reshape(self.ncomp, -1))
+        return self.rhs(d, zw, z), self.rhs(z, w1, w2)
+
+    def precond_diag(self):
+        """(ncomp, ncomp, nalm) block of M = S^-1 + b^2 D (D diagonal per comp)."""
+        L = self.lmax
+        nv = self.ninv
+        wT = sht.ring_sums(self.g, nv[0])
+        D = [sht.diag_ringsum(self.g, L, wT, 0)]
+        if self.ncomp == 3:
+            wP = sht.ring_sums(self.g, nv[1])
+            dp = sht.diag_ringsum(self.g, L, wP, 2)
+            D += [dp, dp]
+        M = self.sinv[:, :, self.ls].copy()
+        b2 = self.bmask[self.ls] ** 2
+        for c in range(self.ncomp):
+            M[c, c] += b2 * D[c]
+        return M
+
+    def dot(self, a, c):
+        return sht.dot_q6(a, c, self.lmax)
+
+
+def _zero_im_m0(a, lmax):
+    a = np.array(a, np.complex128, copy=True)
+    m0 = sht.ms_of(lmax) == 0
+    a[..., m0] = a[..., m0].real
+    return a
+
+
+def apply_block_inverse(M, r):
+    """Solve M z = r per alm index for an (nc, nc, nalm) block diagonal M."""
+    nc = M.shape[0]
+    if nc == 1:
+        return r / M[0, 0][None]
+    Mt = np.moveaxis(M, 2, 0)                          # (nalm, nc, nc)
+    rt = np.moveaxis(r, 1, 0)[..., None]               # (nalm, nc, 1)
+    zr = np.linalg.solve(Mt, rt.real)[..., 0]
+    zi = np.linalg.solve(Mt, rt.imag)[..., 0]
+    return np.moveaxis(zr + 1j * zi, 0, 1)
+
+
+def pcg(prob: Problem, b, tol: float, maxiter: int = 1000, precond=True, x0=None):
+    """Plain preconditioned conjugate gradients in FP64.
+
+    Stops when ||b - A x|| / ||b|| <= tol (recursively updated residual,
+    checked once more with a fresh A x at exit).  Returns (x, iterations,
+    relative residual history)."""
+    b = np.asarray(b, np.complex128).reshape(prob.ncomp, -1)
+    M = prob.precond_diag() if precond else None
+    x = np.zeros_like(b) if x0 is None else np.array(x0, np.complex128).reshape(b.shape)
+    r = b - prob.matvec(x) if x0 is not None else b.copy()
+    z = apply_block_inverse(M, r) if precond else r.copy()
+    z = _zero_im_m0(z, prob.lmax)
+    p = z.copy()
+    bn = np.sqrt(prob.dot(b, b))
+    rz = prob.dot(r, z)
+    hist = [np.sqrt(prob.dot(r, r)) / bn]
+    it = 0
+    while hist[-1] > tol and it < maxiter:
+        q = prob.matvec(p)
+        alpha = rz / prob.dot(p, q)
+        x = x + alpha * p
+        r = r - alpha * q
+        z = apply_block_inverse(M, r) if precond else r.copy()
+        z = _zero_im_m0(z, prob.lmax)
+        rz_new = prob.dot(r, z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+        it += 1
+        hist.append(np.sqrt(prob.dot(r, r)) / bn)
+    return x, it, np.array(hist)
+
+
+def true_residual(prob: Problem, x, b) -> float:
+    b = np.asarray(b, np.complex128).reshape(prob.ncomp, -1)
+    r = b - prob.matvec(x)
+    return float(np.sqrt(prob.dot(r, r) / prob.dot(b, b)))
+
+
+# ----------------------------------------------------------------------------
+# Gaussian log-posterior (Eq. joint-posterior, a-dependent part)
+# ----------------------------------------------------------------------------
+def log_posterior(prob: Problem, a, d, cl_scale=None):
+    """L(a) = -1/2 (d - Y B a)^T N^-1 (d - Y B a) - 1/2 sum_{l, m=-l..l} |a_lm|^2 / C_l
+    for temperature (ncomp = 1), over active l.  ``cl_scale`` multiplies C_l
+    per l (the exponent of the binned log C_l parameters)."""
+    assert prob.ncomp == 1
+    a = np.asarray(a, np.complex128).reshape(1, -1)
+    res = np.asarray(d, np.float64).reshape(1, -1) - prob.Y(prob.beam(a))
+    chi2 = float(np.sum(res * res * prob.ninv[:1]))
+    ic = prob.sinv[0, 0].copy()
+    ic[~prob.active] = 0.0
+    if cl_scale is not None:
+        ic = ic / cl_scale
+    prior = prob.dot(a, a * ic[prob.ls][None])
+    return -0.5 * chi2 - 0.5 * prior
+
+
+def log_posterior_grad(prob: Problem, a, d, bins, cl_scale=None):
+    """Gradient of :func:`log_posterior` in the metric dot_q6 with respect to
+    a (B Y^T N^-1 (d - Y B a) - a / C_l) and with respect to the log C_l of
+    each bin (1/2 sum_{l in bin} sum_{m=-l..l} |a_lm|^2 / C_l)."""
+    a = np.asarray(a, np.complex128).reshape(1, -1)
+    res = np.asarray(d, np.float64).reshape(1, -1) - prob.Y(prob.beam(a))
+    ic = prob.sinv[0, 0].copy()
+    ic[~prob.active] = 0.0
+    if cl_scale is not None:
+        ic = ic / cl_scale
+    ga = prob.beam(prob.Yt(res * prob.ninv[:1])) - a * ic[prob.ls][None]
+    ga = _zero_im_m0(ga, prob.lmax)
+    w = np.where(sht.ms_of(prob.lmax) == 0, 1.0, 2.0)
+    per_lm = 0.5 * w * np.abs(a[0]) ** 2 * ic[prob.ls]
+    gl = np.array([per_lm[(prob.ls >= lo) & (prob.ls <= hi)].sum() for lo, hi in bins])
+    return ga, gl

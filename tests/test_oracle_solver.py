@@ -1,0 +1,252 @@
+"""Pins for the oracle solver (no GPU): dense brute force, the paper's
+full-sky closed form, the constant-latitude-mask block structure of App. A,
+linearity of Eqs. (mean-field-map)/(fluc-map), and finite differences of the
+log-posterior gradient."""
+import math
+
+import numpy as np
+import pytest
+
+from inputs import configs as C
+from oracle import sht, solver
+
+
+def _rand_alm(L, rng, ncomp=1):
+    P = (L + 1) * (L + 2) // 2
+    a = rng.normal(size=(ncomp, P)) + 1j * rng.normal(size=(ncomp, P))
+    ms = sht.ms_of(L)
+    a[:, ms == 0] = a[:, ms == 0].real
+    return a
+
+
+# ----------------------------------------------------------------- dense (P7)
+def _real_params(L):
+    ls, ms = sht.ls_of(L), sht.ms_of(L)
+    cols = []
+    for i, (l, m) in enumerate(zip(ls, ms)):
+        cols.append((i, l, m, "re"))
+        if m > 0:
+            cols.append((i, l, m, "im"))
+    return cols
+
+
+def _dense_Y(L, nside):
+    from scipy.special import sph_harm_y
+    z, phi = C.pixel_centres(nside)
+    th = np.arccos(z)
+    cols = _real_params(L)
+    Yd = np.zeros((z.size, len(cols)))
+    W = np.zeros(len(cols))
+    for k, (i, l, m, part) in enumerate(cols):
+        Y = sph_harm_y(l, m, th, phi)
+        if m == 0:
+            Yd[:, k], W[k] = Y.real, 1.0
+        elif part == "re":
+            Yd[:, k], W[k] = 2 * Y.real, 2.0
+        else:
+            Yd[:, k], W[k] = -2 * Y.imag, 2.0
+    return Yd, W, cols
+
+
+def _to_params(a, cols):
+    return np.array([a[i].real if p == "re" else a[i].imag for (i, l, m, p) in cols])
+
+
+def test_dense_bruteforce_masked():
+    nside, L = 4, 10
+    rng = np.random.default_rng(0)
+    g = sht.healpix(nside)
+    cl = C.cl_flat(L)
+    bl = C.gauss_beam(L, 20 * C.DEG)
+    ninv = rng.uniform(0.5, 2.0, g.npix) * (rng.uniform(size=g.npix) > 0.3)
+    prob = solver.Problem(g, L, cl, bl, ninv)
+    d = rng.normal(size=g.npix)
+    w1 = _rand_alm(L, rng)
+    w2 = rng.normal(size=g.npix)
+    b = prob.rhs(d, w1, w2)
+    x, it, hist = solver.pcg(prob, b, 1e-13, 500)
+    # dense system in real parameters (independent Y from scipy)
+    Yd, W, cols = _dense_Y(L, nside)
+    lcol = np.array([c[1] for c in cols])
+    act = lcol >= 2
+    bc = np.where(act, bl[lcol], 0.0)
+    sinv = np.where(act, 1.0 / np.where(act, cl[lcol], 1.0), 1.0)
+    A = np.diag(sinv) + (bc[:, None] / W[:, None]) * (Yd.T @ (ninv[:, None] * Yd)) * bc[None, :]
+    sh = np.where(act, 1.0 / np.sqrt(np.where(act, cl[lcol], 1.0)), 0.0)
+    rhs = bc / W * (Yd.T @ (ninv * d + np.sqrt(ninv) * w2)) + sh * _to_params(w1[0], cols)
+    assert np.allclose(_to_params(b[0], cols), rhs, rtol=1e-12, atol=1e-12 * np.abs(rhs).max())
+    xd = np.linalg.solve(A, rhs)
+    xo = _to_params(x[0], cols)
+    assert np.max(np.abs(xo - xd)) < 1e-10 * np.max(np.abs(xd))
+    # W A is symmetric positive definite
+    WA = W[:, None] * A
+    assert np.allclose(WA, WA.T, atol=1e-12 * np.abs(WA).max())
+    assert np.linalg.eigvalsh(0.5 * (WA + WA.T)).min() > 0
+
+
+def test_operator_symmetric_spin2():
+    nside, L = 4, 8
+    rng = np.random.default_rng(2)
+    g = sht.healpix(nside)
+    tt = C.cl_flat(L)
+    cl4 = np.stack([tt, 0.05 * tt, 1e-3 * 0.05 * tt, 0.3 * np.sqrt(0.05) * tt])
+    ninv = np.stack([rng.uniform(0.5, 2, g.npix), rng.uniform(0.2, 1, g.npix)])
+    prob = solver.Problem(g, L, cl4, C.gauss_beam(L, 0.2), ninv)
+    x, y = _rand_alm(L, rng, 3), _rand_alm(L, rng, 3)
+    ax, ay = prob.matvec(x), prob.matvec(y)
+    assert abs(prob.dot(x, ay) - prob.dot(ax, y)) < 1e-12 * abs(prob.dot(x, ay))
+    assert prob.dot(x, ax) > 0
+
+
+# ----------------------------------------------------------- closed form (P5)
+def test_fullsky_closed_form_gl():
+    """Uniform noise on an exact-quadrature grid: A = diag(1/C + b^2/N_l) with
+    N_l = 4 pi sigma^2 / N_pix, and the solution is Eqs. (hat_s_approx) +
+    (hat_f_approx) with r_lm = N_l (Y^T N^-1 d)_lm and
+    w1'_lm = sqrt(N_l) (Y^T N^-1/2 w2)_lm."""
+    L = 24
+    g = sht.gauss_legendre(L + 1, 2 * L + 2)
+    rng = np.random.default_rng(4)
+    sigma = 10.0
+    Nl = 4 * math.pi * sigma ** 2 / g.npix
+    ninv = g.pixel_weights() / Nl
+    cl = C.cl_flat(L)
+    bl = C.gauss_beam(L, 10 * C.DEG)
+    prob = solver.Problem(g, L, cl, bl, ninv)
+    d = rng.normal(size=g.npix) * 30
+    w1 = _rand_alm(L, rng)
+    w2 = rng.normal(size=g.npix)
+    b = prob.rhs(d, w1, w2)
+    x, it, _ = solver.pcg(prob, b, 1e-12, 50)
+    assert it <= 2      # the preconditioner is the exact inverse here
+    ls = sht.ls_of(L)
+    r = Nl * sht.alm2map_adjoint(g, L, ninv * d)
+    w1p = math.sqrt(Nl) * sht.alm2map_adjoint(g, L, np.sqrt(ninv) * w2)
+    C_, B_ = cl[ls], bl[ls]
+    den = Nl + B_ ** 2 * C_
+    ahat = r * B_ * C_ / den
+    fhat = w1[0] * Nl * np.sqrt(C_) / den + w1p * math.sqrt(Nl) * B_ * C_ / den
+    ref = np.where(ls >= 2, ahat + fhat, 0.0)
+    assert np.max(np.abs(x[0] - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
+def test_fullsky_closed_form_teb_gl():
+    """T+E+B generalisation: A = S^-1 + b^2 diag(1/N_T, 1/N_P, 1/N_P) per lm."""
+    L = 16
+    g = sht.gauss_legendre(L + 1, 2 * L + 2)
+    rng = np.random.default_rng(6)
+    NT, NP = 0.3, 0.7
+    ninv = np.stack([g.pixel_weights() / NT, g.pixel_weights() / NP])
+    tt = C.cl_flat(L)
+    cl4 = np.stack([tt, 0.05 * tt, 5e-5 * tt, 0.3 * np.sqrt(0.05) * tt])
+    bl = C.gauss_beam(L, 8 * C.DEG)
+    prob = solver.Problem(g, L, cl4, bl, ninv)
+    b = _rand_alm(L, rng, 3)
+    b[:, sht.ls_of(L) < 2] = 0
+    x, it, _ = solver.pcg(prob, b, 1e-12, 100)
+    ls = sht.ls_of(L)
+    ref = np.zeros_like(b)
+    for i in range(b.shape[1]):
+        l = ls[i]
+        if l < 2:
+            continue
+        tt_, ee, bb, te = cl4[:, l]
+        S = np.array([[tt_, te, 0], [te, ee, 0], [0, 0, bb]])
+        A = np.linalg.inv(S) + bl[l] ** 2 * np.diag([1 / NT, 1 / NP, 1 / NP])
+        ref[:, i] = np.linalg.solve(A, b[:, i].real) + 1j * np.linalg.solve(A, b[:, i].imag)
+    assert np.max(np.abs(x - ref)) < 1e-10 * np.max(np.abs(ref))
+
+
+# ------------------------------------------------ constant-latitude mask (P6)
+def test_constant_latitude_mask_block_structure():
+    """App. A: for a mask |b| < b0 and uniform noise the operator is
+    block-diagonal in m, and within a block entries with l + l' odd vanish.
+    The PCG solution equals the per-m dense block solves."""
+    L = 20
+    g = sht.gauss_legendre(L + 1, 2 * L + 2)
+    sigma = 5.0
+    lat_cut = np.abs(g.cth) < math.sin(25 * C.DEG)
+    ninv_ring = np.where(lat_cut, 0.0, 1.0 / sigma ** 2)
+    ninv = np.repeat(ninv_ring, g.nphi)
+    cl = C.cl_flat(L)
+    bl = C.gauss_beam(L, 10 * C.DEG)
+    prob = solver.Problem(g, L, cl, bl, ninv)
+    rng = np.random.default_rng(8)
+    b = _rand_alm(L, rng)
+    ls, ms = sht.ls_of(L), sht.ms_of(L)
+    b[:, ls < 2] = 0
+    x, it, _ = solver.pcg(prob, b, 1e-13, 500)
+    for m in range(L + 1):
+        lrange = np.arange(max(m, 2), L + 1)
+        lam = np.array([sht.lambda_lm(L, m, g.cth[r], g.sth[r])[lrange - m]
+                        for r in range(g.nring)])              # (nring, nl)
+        blk = (lam * (g.nphi * ninv_ring)[:, None]).T @ lam
+        blk = bl[lrange][:, None] * blk * bl[lrange][None, :] + np.diag(1.0 / cl[lrange])
+        odd = ((lrange[:, None] + lrange[None, :]) % 2) == 1
+        if odd.any():
+            assert np.max(np.abs(blk[odd])) < 1e-13 * np.max(np.abs(blk))
+        sel = (ms == m) & (ls >= 2)
+        rhs = b[0, sel]
+        ref = np.linalg.solve(blk, rhs.real) + 1j * np.linalg.solve(blk, rhs.imag)
+        assert np.max(np.abs(x[0, sel] - ref)) < 1e-10 * max(1e-30, np.max(np.abs(ref)))
+    # off-block coupling is absent: A applied to a single-m vector stays in m
+    v = np.zeros_like(b)
+    v[0, (ms == 3) & (ls >= 3)] = 1.0
+    Av = prob.matvec(v)
+    assert np.max(np.abs(Av[0, ms != 3])) < 1e-13 * np.max(np.abs(Av))
+
+
+# ----------------------------------------------------------- linearity (P9)
+def test_mean_field_plus_fluctuation():
+    p = C.config(0, nside=8, lmax=16)
+    g = sht.healpix(8)
+    prob = solver.Problem(g, 16, p.cl, p.bl, p.ninv)
+    d = sht.alm2map(g, 16, p.signal_alm[0] * p.bl[sht.ls_of(16)]) + p.noise_map[0]
+    bd, bw = prob.rhs_parts(d, p.w1, p.w2)
+    b = prob.rhs(d, p.w1, p.w2)
+    assert np.allclose(bd + bw, b, rtol=0, atol=1e-12 * np.abs(b).max())
+    xs = [solver.pcg(prob, v, 1e-13, 500)[0] for v in (bd, bw, b)]
+    assert np.max(np.abs(xs[0] + xs[1] - xs[2])) < 1e-10 * np.max(np.abs(xs[2]))
+
+
+def test_c0_pcg_converges():
+    p = C.config(0)
+    g = sht.healpix(p.nside)
+    L = p.lmax
+    prob = solver.Problem(g, L, p.cl, p.bl, p.ninv)
+    d = sht.alm2map(g, L, p.signal_alm[0] * p.bl[sht.ls_of(L)]) + p.noise_map[0]
+    b = prob.rhs(d, p.w1, p.w2)
+    x, it, hist = solver.pcg(prob, b, p.tol, 500)
+    assert hist[-1] <= p.tol
+    assert solver.true_residual(prob, x, b) <= 1.05 * p.tol
+    assert 1 <= it < 200
+
+
+# ----------------------------------------------------------- gradient (P8)
+def test_log_posterior_gradient_fd():
+    L, nside = 12, 8
+    g = sht.healpix(nside)
+    p = C.config(1, nside=nside, lmax=L)
+    prob = solver.Problem(g, L, p.cl, p.bl, p.ninv)
+    d = sht.alm2map(g, L, p.signal_alm[0] * p.bl[sht.ls_of(L)]) + p.noise_map[0]
+    rng = np.random.default_rng(9)
+    a = p.signal_alm + 0.3 * _rand_alm(L, rng) * np.sqrt(p.cl[sht.ls_of(L)])
+    a[:, sht.ls_of(L) < 2] = 0
+    bins = [(2, 5), (6, 9), (10, 12)]
+    ga, gl = solver.log_posterior_grad(prob, a, d, bins)
+    h = 1e-4
+    ls, ms = sht.ls_of(L), sht.ms_of(L)
+    for i in rng.choice(np.where(ls >= 2)[0], 8, replace=False):
+        for unit in (1.0, 1j) if ms[i] > 0 else (1.0,):
+            e = np.zeros_like(a)
+            e[0, i] = unit
+            fd = (solver.log_posterior(prob, a + h * e, d) - solver.log_posterior(prob, a - h * e, d)) / (2 * h)
+            an = prob.dot(e, ga)
+            assert abs(fd - an) < 1e-5 * max(1.0, abs(an))
+    for k, (lo, hi) in enumerate(bins):
+        def lp(eps):
+            sc = np.ones(L + 1)
+            sc[lo:hi + 1] = math.exp(eps)
+            return solver.log_posterior(prob, a, d, cl_scale=sc)
+        fd = (lp(h) - lp(-h)) / (2 * h)
+        assert abs(fd - gl[k]) < 1e-5 * max(1.0, abs(gl[k]))
