@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Benchmark: constrained-realization sampling (Eq. mapmakingeq of arXiv
+2306.15511, Sect. 2.2.1) at N_side = 1024, l_max = 2048.
+
+Workload (one "step"): 8 T+E+B realizations sharing C_l, beam and N^-1
+(hits-weighted noise, |b| < 20 deg mask + 200 holes, 10' beam), one full
+cg_sample call: RHS assembly in FP64, preconditioner, FP32 PCG inside FP64
+iterative refinement to a true relative residual of 1e-6.  Inputs are
+synthetic (seeded Philox), resident in HBM and larger than L2.
+
+value = batched CG iterations per second over the whole job (each iteration
+is one application of the operator to all realizations: FP32 inner
+iterations plus FP64 refinement applications), summed over ranks.
+Ranks run independent replicas (weak scaling, no data-path collective).
+
+--impl reference times the FP64 CPU oracle (test infrastructure) on a
+bounded ring sample of the same workload and extrapolates the same metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "CG iters/sec & SHT pairs/sec @Nside=1024,lmax=2048; mixed vs FP64 @1e-6 resid"
+UNIT = "CG iterations/s"
+NSIDE, LMAX, NB = 1024, 2048, 8
+CLASS_NAMES = ["leg_synth_fp32", "leg_analysis_fp32", "ring_fft_fp32", "leg_synth_fp64",
+               "leg_analysis_fp64", "ring_fft_fp64", "vector", "precond_diag"]
+
+
+# ----------------------------------------------------------------- helpers
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def alu_peaks(sm_mhz: float):
+    """FP32: 152 SMs x 128 lanes x 2 flops/FMA x clock; FP64: 1.25 TFLOP/s
+    nominal for GB300 scaled to the same clock."""
+    fp32 = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    fp64 = 1.25 * sm_mhz / 2070.0
+    return fp32, fp64
+
+
+def legendre_flops(nalm, npairs, nmaps_t, nmaps_p):
+    """Algorithmic flops of one Legendre pass (one direction): per (l, m,
+    ring pair) 3 shared recurrence flops + 4 per temperature map, and for
+    spin 2 8 shared + 16 per (Q, U) pair."""
+    pr = float(nalm) * float(npairs)
+    f = 0.0
+    if nmaps_t:
+        f += pr * (3 + 4 * nmaps_t)
+    if nmaps_p:
+        f += pr * (8 + 16 * nmaps_p)
+    return f
+
+
+class Clocks:
+    """nvidia-smi sampler (every 200 ms) running during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ inputs
+def make_inputs(plan, device, seed_shift=0):
+    """Config-4 recipe drawn on the device; d = Y B a + n with the library's own
+    FP64 synthesis."""
+    import torch
+    from inputs import configs as C
+    probs = C.config(4, batch=NB, nside=NSIDE, lmax=LMAX, device=device)
+    if seed_shift:
+        # a replica on another rank draws fresh white noise (independent chains)
+        from inputs import philox as px
+        for b, p in enumerate(probs):
+            key = 50000 + 100 * seed_shift + b
+            for k in range(3):
+                p.w2[k] = px.normal_torch(key, px.STREAM_W2, plan.npix, k * plan.npix, device)
+    p0 = probs[0]
+    ls = torch.as_tensor(C.alm_lm(LMAX)[0], device=device)
+    bl = torch.as_tensor(p0.bl, device=device)[ls]
+    a = torch.stack([p.signal_alm for p in probs]) * bl          # [nb, 3, nalm]
+    T = plan.alm2map(a[:, 0].contiguous())
+    QU = plan.alm2map(a[:, 1:].contiguous(), spin=2)
+    d = torch.cat([T[:, None], QU], dim=1) + torch.stack([p.noise_map for p in probs])
+    w1 = torch.stack([p.w1 for p in probs]).contiguous()
+    w2 = torch.stack([p.w2 for p in probs]).contiguous()
+    ninv = torch.as_tensor(p0.ninv, device=device).contiguous()
+    torch.cuda.synchronize()
+    return {"cl": p0.cl, "bl": p0.bl, "ninv": ninv, "d": d.contiguous(), "w1": w1, "w2": w2,
+            "fsky": p0.extra["fsky"]}
+
+
+# ----------------------------------------------------------- CPU baseline
+def oracle_sample(nsub_stride=32, repeats=1):
+    """Time one T+E+B operator application of the FP64 oracle restricted to
+    every ``nsub_stride``-th ring of the N_side 1024 grid and extrapolate to a
+    batched CG iteration (8 realizations, all rings)."""
+    from inputs import configs as C
+    from oracle import sht as osht
+    from oracle import solver as osol
+    g = osht.healpix(NSIDE)
+    rings = np.arange(0, g.nring, nsub_stride)
+    sub = g.subset(rings)
+    p = C.config(4, batch=1, nside=NSIDE, lmax=LMAX)[0]
+    ninv = np.stack([np.concatenate([p.ninv[c][g.ofs[r]:g.ofs[r] + g.nphi[r]] for r in rings])
+                     for c in range(2)])
+    prob = osol.Problem(sub, LMAX, p.cl, p.bl, ninv)
+    x = p.signal_alm
+    times = []
+    for _ in range(repeats):
+        t0 = time.perf_counter()
+        prob.matvec(x)
+        times.append(time.perf_counter() - t0)
+    t = min(times)
+    scale = g.nring / float(rings.size)
+    per_iter = t * scale * NB
+    return {"value": 1.0 / per_iter, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"one FP64 T+E+B operator application of 1 realization on {rings.size} of "
+                       f"{g.nring} rings (every {nsub_stride}th), {t:.2f} s, extrapolated x"
+                       f"{scale:.1f} rings x {NB} realizations")}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    for _ in range(max(0, args.warmup if args.warmup < 1 else 1)):
+        pass
+    vals = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(oracle_sample(repeats=1))
+    el = time.perf_counter() - t0
+    v = float(np.median([x["value"] for x in vals]))
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"T+E+B constrained realizations, HEALPix N_side={NSIDE}, "
+                                   f"l_max={LMAX}, batch {NB}, tol 1e-6",
+                       "global_batch": NB, "l2": "inputs larger than L2"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"],
+                             "kind": "oracle", "sample": vals[0]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": el}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------- GPU arm
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2306_15511_gb300 import Plan
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    plan = Plan(nside=NSIDE, lmax=LMAX, max_batch=NB, spin2=True)
+    inp = make_inputs(plan, dev, seed_shift=rank)
+    kw = dict(tol=1e-6, mode="mixed", maxiter=args.maxiter, inner_tol=args.inner_tol,
+              inner_maxiter=args.inner_maxiter, check_every=args.check_every)
+    out = torch.empty(NB, 3, plan.nalm, dtype=torch.complex128, device=dev)
+
+    def step(profile=False):
+        return plan.cg_sample(inp["cl"], inp["bl"], inp["ninv"], inp["d"], inp["w1"], inp["w2"],
+                              out=out, profile=profile, **kw)[1]
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    stats = [step(profile=True) for _ in range(args.steps)]
+    e1.record(st)
+    torch.cuda.synchronize()
+    ck = clocks.stop()
+    barrier()
+    ms_local = e0.elapsed_time(e1) / args.steps
+    ms = max_over_ranks(ms_local)
+    iters_local = float(sum(s["iterations"] + s["fp64_matvecs"] for s in stats))
+    iters_all = sum_over_ranks(iters_local)
+    value = iters_all / (ms * args.steps / 1000.0)
+    launches = int(sum(s["launches"] for s in stats))
+    # per-class live kernel times over the timed steps
+    kms = np.sum([s["kernel_ms"] for s in stats], axis=0)
+    kcnt = np.sum([s["kernel_launches"] for s in stats], axis=0)
+    inner = sum(s["iterations"] for s in stats)
+    outer = sum(s["fp64_matvecs"] for s in stats)
+
+    # ---------------------------------------------------------- e2e (host)
+    e2e = None
+    if not args.no_e2e:
+        hd = inp["d"].cpu().pin_memory()
+        hw1 = inp["w1"].cpu().pin_memory()
+        hw2 = inp["w2"].cpu().pin_memory()
+        hn = inp["ninv"].cpu().pin_memory()
+        hout = torch.empty(NB, 3, plan.nalm, dtype=torch.complex128).pin_memory()
+        ke = max(1, min(args.steps, args.e2e_steps))
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        e2e_stats = [plan.cg_sample(inp["cl"], inp["bl"], hn, hd, hw1, hw2, out=hout, **kw)[1]
+                     for _ in range(ke)]
+        torch.cuda.synchronize()
+        el = max_over_ranks(time.perf_counter() - t0)
+        it_e = sum_over_ranks(float(sum(s["iterations"] + s["fp64_matvecs"] for s in e2e_stats)))
+        h2d = hd.numel() * 8 + hw2.numel() * 8 + hw1.numel() * 16 + hn.numel() * 8
+        e2e = {"value": it_e / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(hout.numel() * 16), "steps": ke}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # -------------------------------------------------------------- extras
+    extras = {}
+    if not args.no_extras:
+        extras = measure_extras(plan, inp, dev, kw)
+
+    # ------------------------------------------------------------ roofline
+    peaks, src = measured_peaks()
+    sm_mhz = ck.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak, fp64_peak = alu_peaks(float(sm_mhz))
+    nalm, npairs = plan.nalm, 2 * NSIDE
+    per_pass = legendre_flops(nalm, npairs, NB, NB)           # T and Q/U launches of one pass
+    fl = {0: per_pass * (inner + 0), 1: per_pass * inner, 3: per_pass * outer,
+          4: per_pass * (outer + len(stats))}                   # FP64 analysis also builds the RHS
+    dom = int(np.argmax(kms))
+    roof = None
+    if dom in fl and kms[dom] > 0:
+        ach = fl[dom] / (kms[dom] / 1000.0) / 1e12
+        peak = fp64_peak if dom >= 3 else fp32_peak
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None, "kernel": CLASS_NAMES[dom],
+                "peak_source": f"derived from unit counts at the sampled {sm_mhz:.0f} MHz"}
+    elif kms[dom] > 0:
+        roof = {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                "frac": None, "traffic": None, "kernel": CLASS_NAMES[dom]}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        try:
+            cpu = oracle_sample(repeats=1)
+        except Exception as e:  # the oracle is test infrastructure; report why it is missing
+            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                   "sample": f"failed: {e}"}
+
+    total_kms = float(np.sum(kms))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"T+E+B constrained realizations, HEALPix N_side={NSIDE}, "
+                               f"l_max={LMAX}, batch {NB} per GPU, mixed FP32 PCG + FP64 "
+                               f"refinement to 1e-6",
+                   "global_batch": NB * world, "fsky": inp["fsky"], "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (d, w2: 2.4 GB each)"},
+        "e2e": e2e, "gpu_launches": launches, "clocks": ck, "roofline": roof,
+        "cpu_baseline": cpu,
+        "solve": {"inner_iterations_per_step": inner / len(stats),
+                  "fp64_matvecs_per_step": outer / len(stats),
+                  "rel_residual_max": max(s["rel_residual"] for s in stats),
+                  "converged": all(s["converged"] for s in stats),
+                  "time_to_1e-6_s": ms / 1000.0},
+        "kernel_share": {CLASS_NAMES[i]: round(float(kms[i]) / total_kms, 4)
+                         for i in range(len(CLASS_NAMES)) if total_kms > 0},
+        "kernel_ms_per_step": {CLASS_NAMES[i]: float(kms[i]) / len(stats) for i in range(8)},
+        "kernel_launches_per_step": {CLASS_NAMES[i]: int(kcnt[i]) // len(stats) for i in range(8)},
+        "extras": extras,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_extras(plan, inp, dev, kw):
+    """SHT pairs/s (one map, spin 0, FP32 and FP64) and the plain FP64 PCG
+    iteration rate on the same problem."""
+    import torch
+    ex = {}
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    for prec, ct, reps in (("fp32", torch.complex64, 10), ("fp64", torch.complex128, 3)):
+        a = torch.randn(1, plan.nalm, dtype=ct, device=dev, generator=g)
+        for _ in range(2):
+            plan.alm2map_adjoint(plan.alm2map(a))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(reps):
+            plan.alm2map_adjoint(plan.alm2map(a))
+        e1.record()
+        torch.cuda.synchronize()
+        ex[f"sht_pairs_per_s_{prec}_batch1"] = reps / (e0.elapsed_time(e1) / 1000.0)
+    # plain FP64 PCG: a fixed number of iterations timed (full convergence at
+    # this size takes minutes)
+    nit = 4
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, st = plan.cg_sample(inp["cl"], inp["bl"], inp["ninv"], inp["d"], inp["w1"], inp["w2"],
+                           tol=1e-6, mode="fp64", maxiter=nit, check_every=nit,
+                           allow_not_converged=True, profile=True)
+    el = time.perf_counter() - t0
+    ex["fp64_form"] = {"iterations": st["iterations"], "wall_s": el,
+                       "ms_rhs": st["ms_rhs"], "ms_solve": st["ms_solve"],
+                       "iters_per_s_solve_phase": st["iterations"] / (st["ms_solve"] / 1000.0)
+                       if st["ms_solve"] > 0 else None,
+                       "rel_residual_after": st["rel_residual"]}
+    return ex
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="shtg", choices=["shtg", "reference"])
+    ap.add_argument("--maxiter", type=int, default=3000)
+    ap.add_argument("--inner-tol", type=float, default=1e-3)
+    ap.add_argument("--inner-maxiter", type=int, default=400)
+    ap.add_argument("--check-every", type=int, default=8)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,209 @@
+/*
+ * shtg: GB300 (sm_103a) constrained-realization sampler for CMB skies.
+ *
+ * C ABI of the data-parallel hot path of Eskilt et al., "Cosmoglobe: Towards
+ * end-to-end CMB cosmological parameter estimation without likelihood
+ * approximations" (arXiv 2306.15511), Sect. 2.2.1: drawing a constrained
+ * realization by preconditioned conjugate gradients on Eq. (mapmakingeq),
+ *
+ *     (S^-1 + B Y^T N^-1 Y B) a = B Y^T N^-1 d + S^-1/2 w1 + B Y^T N^-1/2 w2,
+ *
+ * where Y is the spherical-harmonic synthesis on the iso-latitude rings of a
+ * HEALPix (or Gauss-Legendre) grid, B the harmonic beam b_l, S the signal
+ * covariance C_l (or the 3x3 T/E/B block of Sect. 2.2.2 with EB = TB = 0) and
+ * N^-1 a diagonal pixel weight that is 0 in the mask (App. A).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - alm: complex, interleaved (re, im), m-major with m >= 0 only:
+ *   index(l, m) = m (2 lmax + 1 - m) / 2 + l, nalm = (lmax+1)(lmax+2)/2.
+ *   Batches are outermost; T+E+B alm are [batch][3][nalm].  The imaginary
+ *   part of a_l0 is ignored on input and written as 0 on output.
+ * - Y_lm = lambda_lm(theta) e^{i m phi}, orthonormal, Condon-Shortley phase
+ *   (App. A: P~_lm = Delta_lm P_lm with the (-1)^m in Delta_lm).
+ *   Spin 2: Q +- iU = sum +-2a_lm +-2Y_lm with +-2a_lm = -(E_lm +- i B_lm),
+ *   where +-2Y_lm = sqrt((l-2)!/(l+2)!) edth^2 (edth-bar^2) Y_lm.
+ * - maps: real, RING order, [batch][npix] (spin 0) or [batch][2][npix] = Q, U.
+ * - Y^T is the exact transpose of Y in the metric
+ *   <a, c> = sum_l [a_l0 c_l0 + 2 Re sum_{m>0} conj(a_lm) c_lm]; every CG
+ *   inner product and residual norm uses this metric.
+ * - "precision" selects SHTG_FP64 (double / complex128 buffers) or
+ *   SHTG_FP32 (float / complex64 buffers) for a transform.
+ * - Device buffers are owned by the caller; the library never frees them.
+ *   Plans own their tables and workspace.  No entry point allocates device
+ *   memory after shtg_plan_create.  Calls on one plan must not overlap.
+ * - stream: a cudaStream_t passed as void* (NULL = legacy default stream).
+ *   Transforms are asynchronous on that stream; cg_sample synchronizes it.
+ * - Every call returns SHTG_OK (0) or a negative error code; no call throws
+ *   across the ABI.  shtg_last_error_string() describes the last failure on
+ *   the calling thread.
+ */
+#ifndef SHTG_H
+#define SHTG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ errors */
+#define SHTG_OK 0
+#define SHTG_ERR_ARG (-1)            /* invalid argument or unsupported size */
+#define SHTG_ERR_CUDA (-2)           /* a CUDA runtime call failed */
+#define SHTG_ERR_NOT_CONVERGED (-3)  /* maxiter reached; output holds the best iterate */
+#define SHTG_ERR_TIMEOUT (-4)        /* a bounded device-side wait expired */
+#define SHTG_ERR_NONFINITE (-5)      /* NaN or Inf met in inputs or iterates */
+#define SHTG_ERR_NOT_SPD (-6)        /* C_l block not positive definite where b_l != 0 */
+#define SHTG_ERR_NOMEM (-7)          /* plan creation could not allocate */
+
+/* ---------------------------------------------------------------- options */
+#define SHTG_GEOM_HEALPIX 0          /* nside_or_nring = N_side; 12 N_side^2 pixels */
+#define SHTG_GEOM_GAUSS 1            /* nside_or_nring = rings; nphi_gauss pixels each */
+
+#define SHTG_FP64 0
+#define SHTG_FP32 1
+
+#define SHTG_SPIN0 1                 /* plan flag: temperature transforms */
+#define SHTG_SPIN2 2                 /* plan flag: also spin-2 (Q, U) transforms */
+
+#define SHTG_CG_FP64 0               /* plain FP64 PCG */
+#define SHTG_CG_MIXED 1              /* FP32 PCG inside FP64 iterative refinement */
+
+#define SHTG_HOST_INPUTS 1           /* cg_sample flag: problem maps/alm and output are host pointers */
+#define SHTG_PROFILE 2               /* cg_sample flag: time kernel classes with CUDA events */
+
+typedef struct shtg_plan shtg_plan;
+
+typedef struct {
+    int geom, nside, nring, lmax, max_batch, flags;
+    int64_t npix, nalm;
+    int64_t device_bytes;            /* device memory owned by the plan */
+} shtg_plan_info;
+
+/* Create a plan: ring geometry, FP64 start states of the Legendre recurrence
+ * (the sectoral values lambda_mm and the first l at which lambda_lm(theta_r)
+ * leaves the negligible range, computed once in FP64 with exponent
+ * rescaling), recurrence coefficients, ring-FFT tables and the workspace for
+ * up to max_batch maps (max_batch realizations of T, or of T+E+B when flags
+ * has SHTG_SPIN2).  For SHTG_GEOM_GAUSS, nphi_gauss >= 2 lmax + 1 makes the
+ * quadrature exact; it is ignored for HEALPix.  flags: SHTG_SPIN0 and/or
+ * SHTG_SPIN2.  lmax <= 4 N_side (HEALPix).  Returns SHTG_ERR_NOMEM if device
+ * memory is insufficient.  Sets *out on success. */
+int shtg_plan_create(int geom, int nside_or_nring, int nphi_gauss, int lmax, int max_batch,
+                     int flags, shtg_plan **out);
+int shtg_plan_destroy(shtg_plan *plan);
+int shtg_plan_get_info(const shtg_plan *plan, shtg_plan_info *info);
+const char *shtg_last_error_string(void);
+int shtg_version(void);
+
+/* Y (Sect. 2.1, a(n) = sum a_lm Y_lm(n); App. A pixel sums):
+ * alm [nbatch][nalm] -> map [nbatch][npix] for spin 0, or
+ * alm [nbatch][2][nalm] (E, B) -> map [nbatch][2][npix] (Q, U) for spin 2.
+ * Device pointers; nbatch <= max_batch (x2 components for spin 2 count
+ * against 3 * max_batch maps). */
+int shtg_alm2map(shtg_plan *plan, int spin, int precision, const void *alm, void *map,
+                 int nbatch, void *stream);
+
+/* Y^T, the exact transpose of shtg_alm2map (no pixel weights):
+ * c_lm = sum_p map_p Y*_lm(p) (spin 0); the spin-2 form is the transpose of
+ * the (E, B) -> (Q, U) map above.  This is the operator B Y^T of Eq.
+ * (mapmakingeq) before the beam. */
+int shtg_alm2map_adjoint(shtg_plan *plan, int spin, int precision, const void *map, void *alm,
+                         int nbatch, void *stream);
+
+/* Vector-Jacobian product of shtg_alm2map for autodiff: given dL/dmap,
+ * returns dL/d(Re a_lm) + i dL/d(Im a_lm), which is w_m (Y^T dL/dmap)_lm with
+ * w_0 = 1, w_m = 2 for m > 0 (the factor 2 accounts for the conjugate
+ * coefficient a_l,-m that each stored a_lm stands for).  Same layouts as
+ * shtg_alm2map_adjoint. */
+int shtg_alm2map_vjp(shtg_plan *plan, int spin, int precision, const void *map_grad,
+                     void *alm_grad, int nbatch, void *stream);
+
+/* Quadrature analysis: Y^T W map with the geometry's pixel weights
+ * (HEALPix 4 pi / N_pix; Gauss-Legendre w_k 2 pi / nphi), followed by niter
+ * Jacobi refinements alm += Y^T W (map - Y alm).  Exact inverse of alm2map on
+ * a Gauss-Legendre plan with nring >= lmax + 1, nphi >= 2 lmax + 1.
+ * niter > 0 uses the plan's scratch map (single call at a time per plan). */
+int shtg_map2alm(shtg_plan *plan, int spin, int precision, const void *map, void *alm,
+                 int nbatch, int niter, void *stream);
+
+/* ------------------------------------------------- constrained realization */
+typedef struct {
+    int ncomp;        /* 1 = temperature; 3 = T, E, B (plan needs SHTG_SPIN2) */
+    int nbatch;       /* realizations that share cl, bl and ninv (<= max_batch) */
+    const double *cl; /* HOST. ncomp 1: [lmax+1] C_l; ncomp 3: [4][lmax+1] = TT, EE, BB, TE.
+                         Multipoles whose block is singular (e.g. C_0 = C_1 = 0) are held at 0. */
+    const double *bl; /* HOST. [lmax+1] beam transfer function b_l */
+    const double *ninv; /* [npix] (T) or [2][npix] (T, then Q and U), N^-1 per pixel, 0 = masked */
+    const double *d;  /* [nbatch][ncomp][npix] data maps (T or T, Q, U) */
+    const double *w1; /* [nbatch][ncomp][nalm] complex128 unit white noise in harmonic space */
+    const double *w2; /* [nbatch][ncomp][npix] unit white noise in pixel space */
+} shtg_problem;
+
+typedef struct {
+    double tol;         /* stop when ||b - A x|| / ||b|| <= tol for every realization */
+    int maxiter;        /* PCG iterations (FP64 mode) or total inner iterations (mixed) */
+    int mode;           /* SHTG_CG_FP64 or SHTG_CG_MIXED */
+    int precond;        /* 1: diagonal preconditioner of Sect. 4 (default); 0: none */
+    double inner_tol;   /* mixed mode: relative tolerance of each FP32 inner solve */
+    int inner_maxiter;  /* mixed mode: iterations per inner solve */
+    int check_every;    /* iterations per CUDA graph launch between host convergence checks */
+    int flags;          /* SHTG_HOST_INPUTS: ninv, d, w1, w2 and alm_out are host memory */
+} shtg_cg_opts;
+
+typedef struct {
+    int iterations;     /* PCG iterations (mixed: FP32 inner iterations) */
+    int outer_steps;    /* mixed mode: FP64 refinement steps */
+    int fp64_matvecs;   /* FP64 operator applications, RHS excluded */
+    int converged;      /* 1 if every realization met tol */
+    double rel_residual;/* max over the batch of the FP64 ||b - A x|| / ||b|| at exit */
+    double ms_setup, ms_rhs, ms_solve, ms_total;
+    long long launches;        /* CUDA kernels the call launched */
+    /* with SHTG_PROFILE: summed CUDA-event time and launch count per kernel
+     * class: 0 Legendre synthesis FP32, 1 Legendre analysis FP32, 2 ring FFT
+     * FP32, 3 Legendre synthesis FP64, 4 Legendre analysis FP64, 5 ring FFT
+     * FP64, 6 vector / reduction kernels, 7 preconditioner diagonal */
+    double kernel_ms[8];
+    int kernel_launches[8];
+} shtg_cg_stats;
+
+/* Draw nbatch constrained realizations, a = x solving Eq. (mapmakingeq)
+ * (Sect. 2.2.1): RHS b = B Y^T (N^-1 d + N^-1/2 w2) + S^-1/2 w1 with S^-1/2
+ * the inverse symmetric square root of the C_l block; PCG with the
+ * diagonal preconditioner M = S^-1 + b_l^2 D_lm, D_lm = sum_r g_lm(theta_r)
+ * sum_{p in r} N^-1_p (g = lambda^2, or the spin-2 analogue).  alm_out:
+ * [nbatch][ncomp][nalm] complex128.  Returns SHTG_ERR_NOT_CONVERGED (output =
+ * last iterate, stats filled) if maxiter is hit.  opts may be NULL (tol 1e-6,
+ * mixed, preconditioned). */
+int shtg_cg_sample(shtg_plan *plan, const shtg_problem *prob, double *alm_out,
+                   const shtg_cg_opts *opts, shtg_cg_stats *stats, void *stream);
+
+/* Apply the operator A of Eq. (mapmakingeq) once: y = S^-1 x + B Y^T N^-1 Y B x
+ * (x, y: device [nbatch][ncomp][nalm] complex128, FP64), using the problem's
+ * cl, bl and ninv (d, w1, w2 unused).  Held multipoles pass through (y = x). */
+int shtg_apply_operator(shtg_plan *plan, const shtg_problem *prob, const double *x, double *y,
+                        void *stream);
+
+/* --------------------------------------------------- log-posterior (grad) */
+#define SHTG_GRAD_COMPONENTS 1   /* logpost flag: grad_alm as d/dRe + i d/dIm (x2 for m > 0) */
+
+/* Gaussian log-posterior of Eq. (joint-posterior), a-dependent part, for
+ * temperature: L = -1/2 (d - Y B a)^T N^-1 (d - Y B a) - 1/2 sum_{l, m=-l..l}
+ * |a_lm|^2 / C_l over multipoles with C_l > 0.  FP32 transforms with FP64
+ * reductions.  Inputs (device): alm [nalm] complex64, d [npix] float32,
+ * ninv [npix] float32; host cl, bl [lmax+1].  Outputs: *logp (host),
+ * grad_alm [nalm] complex64 (device; gradient in the metric above:
+ * B Y^T N^-1 (d - Y B a) - a / C_l, or the component form with
+ * SHTG_GRAD_COMPONENTS in flags), grad_logcl [nbins] (host; d L / d log C_l
+ * for bins [bin_lo[k], bin_hi[k]]).  grad_alm or grad_logcl may be NULL. */
+int shtg_logpost_grad(shtg_plan *plan, const double *cl, const double *bl, const float *alm,
+                      const float *d, const float *ninv, int nbins, const int *bin_lo,
+                      const int *bin_hi, int flags, double *logp, float *grad_alm,
+                      double *grad_logcl, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SHTG_H */

@@ -141,20 +141,30 @@ def hits_proxy(z, phi) -> np.ndarray:
 # ----------------------------------------------------------------------------
 # white noise
 # ----------------------------------------------------------------------------
-def white_alm(lmax: int, seed: int, stream: int, offset: int = 0) -> np.ndarray:
+def white_alm(lmax: int, seed: int, stream: int, offset: int = 0, device=None):
     """Unit white noise in harmonic space: a_l0 ~ N(0,1) real; for m > 0 the
-    real and imaginary parts are N(0, 1/2) each."""
+    real and imaginary parts are N(0, 1/2) each.  With ``device`` the draws
+    come from the torch path of the same generator (a torch tensor)."""
     p = nalm(lmax)
-    g = px.normal(seed, stream, 2 * p, offset)
-    re, im = g[0::2], g[1::2]
     _, ms = alm_lm(lmax)
     scale = np.where(ms == 0, 1.0, math.sqrt(0.5))
+    if device is not None:
+        import torch
+        g = px.normal_torch(seed, stream, 2 * p, offset, device)
+        sc = torch.as_tensor(scale, device=device)
+        im = g[1::2] * sc
+        im[torch.as_tensor(ms == 0, device=device)] = 0.0
+        return torch.complex(g[0::2] * sc, im)
+    g = px.normal(seed, stream, 2 * p, offset)
+    re, im = g[0::2], g[1::2]
     out = (re + 1j * im) * scale
     out[ms == 0] = re[ms == 0]
     return out
 
 
-def white_map(npix: int, seed: int, stream: int, offset: int = 0) -> np.ndarray:
+def white_map(npix: int, seed: int, stream: int, offset: int = 0, device=None):
+    if device is not None:
+        return px.normal_torch(seed, stream, npix, offset, device)
     return px.normal(seed, stream, npix, offset)
 
 
@@ -195,12 +205,13 @@ def _sqrt_cl_cholesky(cl4: np.ndarray):
 
 
 def config(index: int, batch: int | None = None, lmax: int | None = None,
-           nside: int | None = None) -> Problem | list:
+           nside: int | None = None, device=None) -> Problem | list:
     """Build one of the five workloads (0..4).
 
     ``nside``/``lmax`` override the resolution (used for reduced-size parity
     cases of the same recipe).  Config 2 returns a list of chains; config 4
-    returns ``batch`` problems (default 8) that share cl, beam and noise."""
+    returns ``batch`` problems (default 8) that share cl, beam and noise;
+    with ``device`` its random fields are torch tensors drawn on that device."""
     if index == 0:
         ns = nside or 32
         L = lmax or 64
@@ -277,18 +288,27 @@ def config(index: int, batch: int | None = None, lmax: int | None = None,
         ls = alm_lm(L)[0]
         p = nalm(L)
         out = []
+        if device is not None:
+            import torch
+            stack = torch.stack
+            cv = lambda x: torch.as_tensor(x, device=device)  # noqa: E731
+        else:
+            stack = np.stack
+            cv = lambda x: x  # noqa: E731
+        c11, c21, c22, cbb, cst, csp = (cv(l11[ls]), cv(l21[ls]), cv(l22[ls]), cv(lbb[ls]),
+                                        cv(sig_t), cv(sig_p))
         for b in range(nb):
             key = 4000 + b
-            wt = white_alm(L, key, px.STREAM_SIGNAL, 0)
-            we = white_alm(L, key, px.STREAM_SIGNAL, 2 * p)
-            wb = white_alm(L, key, px.STREAM_SIGNAL, 4 * p)
-            a = np.stack([l11[ls] * wt, l21[ls] * wt + l22[ls] * we, lbb[ls] * wb])
+            wt = white_alm(L, key, px.STREAM_SIGNAL, 0, device)
+            we = white_alm(L, key, px.STREAM_SIGNAL, 2 * p, device)
+            wb = white_alm(L, key, px.STREAM_SIGNAL, 4 * p, device)
+            a = stack([c11 * wt, c21 * wt + c22 * we, cbb * wb])
             npx = z.size
-            nmap = np.stack([sig_t * white_map(npx, key, px.STREAM_NOISE, 0),
-                             sig_p * white_map(npx, key, px.STREAM_NOISE, npx),
-                             sig_p * white_map(npx, key, px.STREAM_NOISE, 2 * npx)])
-            w1 = np.stack([white_alm(L, key, px.STREAM_W1, k * 2 * p) for k in range(3)])
-            w2 = np.stack([white_map(npx, key, px.STREAM_W2, k * npx) for k in range(3)])
+            nmap = stack([cst * white_map(npx, key, px.STREAM_NOISE, 0, device),
+                          csp * white_map(npx, key, px.STREAM_NOISE, npx, device),
+                          csp * white_map(npx, key, px.STREAM_NOISE, 2 * npx, device)])
+            w1 = stack([white_alm(L, key, px.STREAM_W1, k * 2 * p, device) for k in range(3)])
+            w2 = stack([white_map(npx, key, px.STREAM_W2, k * npx, device) for k in range(3)])
             out.append(Problem(f"c4.{b}", ns, L, 3, cl4, bl, ninv, a, nmap, w1, w2, 1e-6,
                                {"fsky": float(1.0 - masked.mean())}))
         return out

@@ -88,3 +88,38 @@ def normal(seed: int, stream: int, n: int, offset: int = 0) -> np.ndarray:
     ang = 2.0 * np.pi * u2
     odd = (e & np.uint64(1)).astype(bool)
     return np.where(odd, r * np.sin(ang), r * np.cos(ang))
+
+
+# ---------------------------------------------------------------- torch path
+# The same generator on a torch device (int64 arithmetic with 32-bit masks;
+# products of two 32-bit words wrap modulo 2^64, which keeps the low and high
+# words exact).  Gaussian draws use the device's float64 log / cos / sin, so
+# they agree with the numpy path to rounding, not bit for bit; the benchmark
+# uses this path for full-size inputs, the parity tests use the numpy path.
+def _philox_torch(c0, c1, c2, c3, k0: int, k1: int):
+    M = 0xFFFFFFFF
+    for rnd in range(10):
+        if rnd:
+            k0 = (k0 + 0x9E3779B9) & M
+            k1 = (k1 + 0xBB67AE85) & M
+        p0 = c0 * 0xD2511F53
+        p1 = c2 * 0xCD9E8D57
+        hi0, lo0 = (p0 >> 32) & M, p0 & M
+        hi1, lo1 = (p1 >> 32) & M, p1 & M
+        c0, c1, c2, c3 = (hi1 ^ c1 ^ k0), lo1, (hi0 ^ c3 ^ k1), lo0
+    return c0, c1, c2, c3
+
+
+def normal_torch(seed: int, stream: int, n: int, offset: int = 0, device="cuda"):
+    import torch
+    e = torch.arange(offset, offset + n, dtype=torch.int64, device=device)
+    idx = e >> 1
+    z = torch.zeros_like(idx)
+    x0, x1, x2, x3 = _philox_torch(idx & 0xFFFFFFFF, idx >> 32, z + stream, z, seed, 0)
+
+    def u53(a, b):
+        return ((a >> 5).double() * 67108864.0 + (b >> 6).double() + 0.5) * (1.0 / 9007199254740992.0)
+    u1, u2 = u53(x0, x1), u53(x2, x3)
+    r = torch.sqrt(-2.0 * torch.log(u1))
+    ang = 2.0 * 3.141592653589793 * u2
+    return torch.where((e & 1).bool(), r * torch.sin(ang), r * torch.cos(ang))

@@ -246,11 +246,13 @@ static void ring_synth(int L, const double *F /* 2(L+1) */, int64_t n, double ph
 /* G(m) = sum_j y_j e^{-i m (phi0 + 2 pi j / n)}, m = 0..L (the transpose of
  * ring_synth up to the factor 2 on m > 0, which the Q6 metric absorbs). */
 static void ring_analy(int L, const double *y, int64_t n, double phi0, double *G,
-                       double *tw /* 2n + 2(L+1) scratch */)
+                       double *tw /* 2n + 2(L+1) scratch */, int nm, const int *mlist)
 {
     double *ph = tw + 2 * n;
     ring_tables(L, n, phi0, tw, ph);
-    for (int m = 0; m <= L; ++m) {
+    const int cnt = nm < 0 ? L + 1 : nm;
+    for (int q = 0; q < cnt; ++q) {
+        const int m = nm < 0 ? q : mlist[q];
         const double pr = ph[2 * m], pi_ = ph[2 * m + 1];
         double gr = 0.0, gi = 0.0;
         for (int64_t j = 0; j < n; ++j) {
@@ -334,7 +336,7 @@ void orc_alm2map_adjoint_m(int nring, const double *cth, const double *sth,
         double *tw = (double *)malloc(sizeof(double) * (2 * nmx + 2 * (L + 1)));
 #pragma omp for schedule(dynamic, 1)
         for (int r = 0; r < nring; ++r)
-            ring_analy(L, map + ofs[r], nphi[r], phi0[r], G + (size_t)r * 2 * (L + 1), tw);
+            ring_analy(L, map + ofs[r], nphi[r], phi0[r], G + (size_t)r * 2 * (L + 1), tw, nm, mlist);
         free(tw);
     }
     const int cnt = nm < 0 ? L + 1 : nm;
@@ -465,8 +467,8 @@ void orc_alm2map_spin2_adjoint_m(int nring, const double *cth, const double *sth
         double *tw = (double *)malloc(sizeof(double) * (2 * nmx + 2 * (L + 1)));
 #pragma omp for schedule(dynamic, 1)
         for (int r = 0; r < nring; ++r) {
-            ring_analy(L, Q + ofs[r], nphi[r], phi0[r], GQ + (size_t)r * 2 * (L + 1), tw);
-            ring_analy(L, U + ofs[r], nphi[r], phi0[r], GU + (size_t)r * 2 * (L + 1), tw);
+            ring_analy(L, Q + ofs[r], nphi[r], phi0[r], GQ + (size_t)r * 2 * (L + 1), tw, nm, mlist);
+            ring_analy(L, U + ofs[r], nphi[r], phi0[r], GU + (size_t)r * 2 * (L + 1), tw, nm, mlist);
         }
         free(tw);
     }

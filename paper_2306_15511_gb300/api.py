@@ -1,0 +1,212 @@
+"""PyTorch binding of the shtg C ABI.
+
+Tensors provide device memory and the current CUDA stream; every operation
+is a call into libshtg.so with the same name as the C entry point.  This
+layer only checks shapes, allocates output tensors and passes pointers.
+
+Layouts (see include/shtg.h): alm complex, m-major, nalm = (L+1)(L+2)/2;
+maps real in HEALPix RING order; batches outermost; spin-2 alm [.., 2, nalm]
+(E, B) and maps [.., 2, npix] (Q, U); T+E+B problems [batch, 3, ...].
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+_PREC = {torch.complex128: N.FP64, torch.float64: N.FP64,
+         torch.complex64: N.FP32, torch.float32: N.FP32}
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t) -> C.c_void_p:
+    if isinstance(t, np.ndarray):
+        return C.c_void_p(t.ctypes.data)
+    return C.c_void_p(t.data_ptr())
+
+
+def _need_cuda(t: torch.Tensor, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Plan:
+    """Geometry, tables and workspace for transforms and solves on one grid.
+
+    Plan(nside=N, lmax=L)                      HEALPix RING grid
+    Plan(gauss=(nring, nphi), lmax=L)          Gauss-Legendre grid
+    max_batch: realizations per call; spin2: also Q/U transforms (T+E+B).
+    """
+
+    def __init__(self, nside: int | None = None, lmax: int = 0, max_batch: int = 1,
+                 spin2: bool = False, gauss: tuple | None = None):
+        lib = N.load()
+        self._lib = lib
+        h = C.c_void_p()
+        flags = N.SPIN0 | (N.SPIN2 if spin2 else 0)
+        if gauss is not None:
+            rc = lib.shtg_plan_create(N.GEOM_GAUSS, int(gauss[0]), int(gauss[1]), int(lmax),
+                                      int(max_batch), flags, C.byref(h))
+        else:
+            rc = lib.shtg_plan_create(N.GEOM_HEALPIX, int(nside), 0, int(lmax), int(max_batch),
+                                      flags, C.byref(h))
+        N.check(rc)
+        self._h = h
+        info = N.PlanInfo()
+        N.check(lib.shtg_plan_get_info(h, C.byref(info)))
+        self.info = info
+        self.lmax, self.npix, self.nalm = info.lmax, int(info.npix), int(info.nalm)
+        self.max_batch = info.max_batch
+        self.spin2 = bool(info.flags & N.SPIN2)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.shtg_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ----------------------------------------------------------- transforms
+    def _batched(self, x, spin, inner):
+        lead = x.shape[:-2] if spin == 2 else x.shape[:-1]
+        nb = int(np.prod(lead)) if len(lead) else 1
+        if x.shape[-1] != inner or (spin == 2 and x.shape[-2] != 2):
+            raise ValueError(f"expected trailing shape {'(2, ' if spin == 2 else '('}{inner})")
+        return lead, nb
+
+    def alm2map(self, alm: torch.Tensor, spin: int = 0) -> torch.Tensor:
+        """Y: alm [..., nalm] (spin 0) or [..., 2, nalm] (E, B) -> maps."""
+        _need_cuda(alm, "alm")
+        lead, nb = self._batched(alm, spin, self.nalm)
+        real = torch.float64 if alm.dtype == torch.complex128 else torch.float32
+        out = torch.empty(*lead, *((2,) if spin == 2 else ()), self.npix, dtype=real,
+                          device=alm.device)
+        N.check(self._lib.shtg_alm2map(self._h, spin, _PREC[alm.dtype], _ptr(alm), _ptr(out), nb,
+                                       _stream()))
+        return out
+
+    def alm2map_adjoint(self, m: torch.Tensor, spin: int = 0) -> torch.Tensor:
+        """Y^T (exact transpose, no pixel weights): maps -> alm."""
+        _need_cuda(m, "map")
+        lead, nb = self._batched(m, spin, self.npix)
+        cplx = torch.complex128 if m.dtype == torch.float64 else torch.complex64
+        out = torch.empty(*lead, *((2,) if spin == 2 else ()), self.nalm, dtype=cplx,
+                          device=m.device)
+        N.check(self._lib.shtg_alm2map_adjoint(self._h, spin, _PREC[m.dtype], _ptr(m), _ptr(out),
+                                               nb, _stream()))
+        return out
+
+    def alm2map_vjp(self, g: torch.Tensor, spin: int = 0) -> torch.Tensor:
+        """Gradient of a real loss w.r.t. alm (torch convention) from dL/dmap."""
+        _need_cuda(g, "map_grad")
+        lead, nb = self._batched(g, spin, self.npix)
+        cplx = torch.complex128 if g.dtype == torch.float64 else torch.complex64
+        out = torch.empty(*lead, *((2,) if spin == 2 else ()), self.nalm, dtype=cplx,
+                          device=g.device)
+        N.check(self._lib.shtg_alm2map_vjp(self._h, spin, _PREC[g.dtype], _ptr(g), _ptr(out), nb,
+                                           _stream()))
+        return out
+
+    def map2alm(self, m: torch.Tensor, spin: int = 0, niter: int = 0) -> torch.Tensor:
+        """Quadrature analysis Y^T W with niter Jacobi refinements."""
+        _need_cuda(m, "map")
+        lead, nb = self._batched(m, spin, self.npix)
+        cplx = torch.complex128 if m.dtype == torch.float64 else torch.complex64
+        out = torch.empty(*lead, *((2,) if spin == 2 else ()), self.nalm, dtype=cplx,
+                          device=m.device)
+        N.check(self._lib.shtg_map2alm(self._h, spin, _PREC[m.dtype], _ptr(m), _ptr(out), nb,
+                                       int(niter), _stream()))
+        return out
+
+    # ---------------------------------------------------------------- solver
+    @staticmethod
+    def _host_f64(a):
+        return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+    def _problem(self, cl, bl, ninv, d=None, w1=None, w2=None, nbatch=1, ncomp=1):
+        self._keep = [self._host_f64(cl), self._host_f64(bl)]
+        pr = N.Problem()
+        pr.ncomp, pr.nbatch = ncomp, nbatch
+        pr.cl, pr.bl = _ptr(self._keep[0]), _ptr(self._keep[1])
+        pr.ninv = _ptr(ninv)
+        pr.d = _ptr(d) if d is not None else None
+        pr.w1 = _ptr(w1) if w1 is not None else None
+        pr.w2 = _ptr(w2) if w2 is not None else None
+        return pr
+
+    def cg_sample(self, cl, bl, ninv, d, w1, w2, tol: float = 1e-6, mode: str = "mixed",
+                  maxiter: int = 2000, precond: bool = True, inner_tol: float = 1e-3,
+                  inner_maxiter: int = 300, check_every: int = 4, out=None,
+                  allow_not_converged: bool = False, profile: bool = False):
+        """Constrained realization(s) of Eq. (mapmakingeq).
+
+        d, w2: [nbatch, ncomp, npix] float64; w1: [nbatch, ncomp, nalm] complex128;
+        ninv: [npix] (T) or [2, npix] (T, P).  All CUDA tensors, or all host
+        (numpy / pinned CPU tensors) for an end-to-end call with the copies
+        inside the library.  Returns (alm [nbatch, ncomp, nalm], stats dict)."""
+        host = not (isinstance(d, torch.Tensor) and d.is_cuda)
+        nb, nc = int(d.shape[0]), int(d.shape[1])
+        if out is None:
+            if host:
+                out = torch.empty(nb, nc, self.nalm, dtype=torch.complex128).pin_memory()
+            else:
+                out = torch.empty(nb, nc, self.nalm, dtype=torch.complex128, device=d.device)
+        for t, name in ((d, "d"), (w1, "w1"), (w2, "w2"), (ninv, "ninv"), (out, "out")):
+            if isinstance(t, torch.Tensor):
+                if t.is_cuda == host:
+                    raise ValueError(f"{name}: mix of host and device buffers")
+                if not t.is_contiguous():
+                    raise ValueError(f"{name} must be contiguous")
+        pr = self._problem(cl, bl, ninv, d, w1, w2, nb, nc)
+        o = N.CGOpts()
+        o.tol, o.maxiter = float(tol), int(maxiter)
+        o.mode = N.CG_MIXED if mode == "mixed" else N.CG_FP64
+        o.precond = 1 if precond else 0
+        o.inner_tol, o.inner_maxiter = float(inner_tol), int(inner_maxiter)
+        o.check_every = int(check_every)
+        o.flags = (N.HOST_INPUTS if host else 0) | (N.PROFILE if profile else 0)
+        st = N.CGStats()
+        rc = self._lib.shtg_cg_sample(self._h, C.byref(pr), _ptr(out), C.byref(o), C.byref(st),
+                                      _stream())
+        N.check(rc, allow=(-3,) if allow_not_converged else ())
+        return out, st.as_dict()
+
+    def apply_operator(self, cl, bl, ninv, x: torch.Tensor) -> torch.Tensor:
+        """y = (S^-1 + B Y^T N^-1 Y B) x for x [nbatch, ncomp, nalm] complex128 (CUDA)."""
+        _need_cuda(x, "x")
+        y = torch.empty_like(x)
+        pr = self._problem(cl, bl, ninv, nbatch=int(x.shape[0]), ncomp=int(x.shape[1]))
+        N.check(self._lib.shtg_apply_operator(self._h, C.byref(pr), _ptr(x), _ptr(y), _stream()))
+        return y
+
+    def logpost_grad(self, cl, bl, alm: torch.Tensor, d: torch.Tensor, ninv: torch.Tensor,
+                     bins=(), components: bool = False, want_grad: bool = True):
+        """Log-posterior of Eq. (joint-posterior) (temperature) with its
+        gradient w.r.t. alm (complex64) and the log C_l of each bin."""
+        for t, n in ((alm, "alm"), (d, "d"), (ninv, "ninv")):
+            _need_cuda(t, n)
+        cl_h, bl_h = self._host_f64(cl), self._host_f64(bl)
+        lo = np.ascontiguousarray([b[0] for b in bins], dtype=np.int32)
+        hi = np.ascontiguousarray([b[1] for b in bins], dtype=np.int32)
+        g = torch.empty_like(alm) if want_grad else None
+        gcl = np.zeros(len(bins))
+        logp = C.c_double(0.0)
+        N.check(self._lib.shtg_logpost_grad(
+            self._h, _ptr(cl_h), _ptr(bl_h), _ptr(alm), _ptr(d), _ptr(ninv), len(bins),
+            _ptr(lo) if len(bins) else None, _ptr(hi) if len(bins) else None,
+            N.GRAD_COMPONENTS if components else 0, C.byref(logp),
+            _ptr(g) if g is not None else None, _ptr(gcl) if len(bins) else None, _stream()))
+        return logp.value, g, gcl

@@ -1,0 +1,293 @@
+// The exported C ABI (declared in include/shtg.h): argument checks, error
+// reporting, and the composition of the Legendre and ring stages into the
+// transforms Y, Y^T and the quadrature analysis.
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "common.cuh"
+
+namespace shtg {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line) {
+    set_error(std::string(what) + ": " + cudaGetErrorString(e) + " (" + file + ":" +
+              std::to_string(line) + ")");
+    return SHTG_ERR_CUDA;
+}
+
+template <typename T>
+__global__ void k_sub(const T *__restrict__ a, const T *__restrict__ b, T *__restrict__ out, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = a[i] - b[i];
+}
+template <typename T>
+__global__ void k_add(T *__restrict__ a, const T *__restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        a[i] += b[i];
+}
+
+static unsigned blocks_for(int64_t n) {
+    int64_t g = (n + 255) / 256;
+    return (unsigned)(g > 4096 ? 4096 : (g < 1 ? 1 : g));
+}
+
+// spin 0: alm rows [nbatch][nalm] -> maps [nbatch][npix]
+// spin 2: alm rows [nbatch][2][nalm] -> maps [nbatch][2][npix]
+template <typename T>
+int transform_synth(Plan *p, int spin, const void *alm, void *map, int nbatch, cudaStream_t st) {
+    typedef typename VT<T>::C C;
+    C *F = sizeof(T) == 8 ? (C *)p->d_phase64 : (C *)p->d_phase32;
+    const int rs = spin == 2 ? 2 : 1;
+    SHTG_TRY(leg_synth<T>(p, spin, (const C *)alm, rs, nbatch, nullptr, F, st));
+    SHTG_TRY(ring_synth<T>(p, F, nbatch * rs, (T *)map, st));
+    return SHTG_OK;
+}
+
+template <typename T>
+int transform_adjoint(Plan *p, int spin, const void *map, void *alm, int nbatch, int weighted,
+                      cudaStream_t st, int vjp) {
+    typedef typename VT<T>::C C;
+    C *G = sizeof(T) == 8 ? (C *)p->d_phase64 : (C *)p->d_phase32;
+    const int rs = spin == 2 ? 2 : 1;
+    SHTG_TRY(ring_analysis<T>(p, (const T *)map, nbatch * rs, weighted, G, st));
+    SHTG_TRY(leg_analysis<T>(p, spin, G, nbatch, nullptr, (C *)alm, rs, st, vjp));
+    return SHTG_OK;
+}
+template int transform_synth<float>(Plan *, int, const void *, void *, int, cudaStream_t);
+template int transform_synth<double>(Plan *, int, const void *, void *, int, cudaStream_t);
+template int transform_adjoint<float>(Plan *, int, const void *, void *, int, int, cudaStream_t, int);
+template int transform_adjoint<double>(Plan *, int, const void *, void *, int, int, cudaStream_t, int);
+
+static int check_transform(const shtg_plan *plan, int spin, int precision, const void *a,
+                           const void *b, int nbatch) {
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    if (!p) {
+        set_error("null plan");
+        return SHTG_ERR_ARG;
+    }
+    if (spin != 0 && spin != 2) {
+        set_error("spin must be 0 or 2");
+        return SHTG_ERR_ARG;
+    }
+    if (spin == 2 && !(p->flags & SHTG_SPIN2)) {
+        set_error("spin-2 transform on a plan created without SHTG_SPIN2");
+        return SHTG_ERR_ARG;
+    }
+    if (precision != SHTG_FP64 && precision != SHTG_FP32) {
+        set_error("precision must be SHTG_FP64 or SHTG_FP32");
+        return SHTG_ERR_ARG;
+    }
+    if (!a || !b) {
+        set_error("null buffer");
+        return SHTG_ERR_ARG;
+    }
+    if (nbatch < 1 || nbatch > p->max_batch) {
+        set_error("nbatch must be in [1, max_batch]");
+        return SHTG_ERR_ARG;
+    }
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != p->device) {
+        cudaGetLastError();
+        set_error("the current CUDA device is not the plan's device");
+        return SHTG_ERR_ARG;
+    }
+    return SHTG_OK;
+}
+
+int alm2map_vjp(Plan *p, int spin, int precision, const void *g, void *out, int nbatch,
+                cudaStream_t st) {
+    if (precision == SHTG_FP64) return transform_adjoint<double>(p, spin, g, out, nbatch, 0, st, 1);
+    return transform_adjoint<float>(p, spin, g, out, nbatch, 0, st, 1);
+}
+
+template <typename T>
+int map2alm_t(Plan *p, int spin, const void *map, void *alm, int nbatch, int niter,
+                     cudaStream_t st) {
+    typedef typename VT<T>::C C;
+    SHTG_TRY(transform_adjoint<T>(p, spin, map, alm, nbatch, 1, st));
+    if (niter <= 0) return SHTG_OK;
+    const int rows = spin == 2 ? 2 : 1;
+    const int64_t nm = (int64_t)nbatch * rows * p->npix;
+    const int64_t na = (int64_t)nbatch * rows * p->nalm;
+    T *scratch = sizeof(T) == 8 ? (T *)p->d_map64 : (T *)p->d_map32;
+    C *dalm = sizeof(T) == 8 ? (C *)p->v64[6] : (C *)p->v32[4];
+    for (int it = 0; it < niter; ++it) {
+        SHTG_TRY(transform_synth<T>(p, spin, alm, scratch, nbatch, st));
+        k_sub<T><<<blocks_for(nm), 256, 0, st>>>((const T *)map, scratch, scratch, nm);
+        SHTG_CHECK_LAUNCH("k_sub");
+        SHTG_TRY(transform_adjoint<T>(p, spin, scratch, dalm, nbatch, 1, st));
+        k_add<T><<<blocks_for(2 * na), 256, 0, st>>>((T *)alm, (const T *)dalm, 2 * na);
+        SHTG_CHECK_LAUNCH("k_add");
+    }
+    return SHTG_OK;
+}
+
+}  // namespace shtg
+
+using namespace shtg;
+
+extern "C" {
+
+int shtg_version(void) { return 1; }
+
+const char *shtg_last_error_string(void) { return g_err.c_str(); }
+
+int shtg_plan_create(int geom, int nside_or_nring, int nphi_gauss, int lmax, int max_batch,
+                     int flags, shtg_plan **out) {
+    if (!out) {
+        set_error("out is null");
+        return SHTG_ERR_ARG;
+    }
+    *out = nullptr;
+    if (geom != SHTG_GEOM_HEALPIX && geom != SHTG_GEOM_GAUSS) {
+        set_error("unknown geometry");
+        return SHTG_ERR_ARG;
+    }
+    if (lmax < 0 || lmax > 8192 || max_batch < 1 || nside_or_nring < 1) {
+        set_error("invalid lmax, max_batch or resolution");
+        return SHTG_ERR_ARG;
+    }
+    if (geom == SHTG_GEOM_HEALPIX && (nside_or_nring > 8192 || lmax > 4 * nside_or_nring)) {
+        set_error("HEALPix plans need nside <= 8192 and lmax <= 4 nside");
+        return SHTG_ERR_ARG;
+    }
+    if (geom == SHTG_GEOM_GAUSS && (nphi_gauss < 1 || nphi_gauss > 65536 || nside_or_nring > 65536)) {
+        set_error("Gauss-Legendre plans need 1 <= nphi_gauss <= 65536");
+        return SHTG_ERR_ARG;
+    }
+    if (!(flags & (SHTG_SPIN0 | SHTG_SPIN2))) flags |= SHTG_SPIN0;
+    Plan *p = new (std::nothrow) Plan();
+    if (!p) {
+        set_error("host allocation failed");
+        return SHTG_ERR_NOMEM;
+    }
+    p->geom = geom;
+    p->lmax = lmax;
+    p->max_batch = max_batch;
+    p->flags = flags;
+    if (geom == SHTG_GEOM_HEALPIX) {
+        p->nside = nside_or_nring;
+    } else {
+        p->nring = nside_or_nring;
+        p->nphi_gauss = nphi_gauss;
+    }
+    if (cudaGetDevice(&p->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete p;
+        set_error("no CUDA device");
+        return SHTG_ERR_CUDA;
+    }
+    const int rc = plan_build(p);
+    if (rc != SHTG_OK) {
+        plan_free(p);
+        delete p;
+        return rc;
+    }
+    *out = reinterpret_cast<shtg_plan *>(p);
+    return SHTG_OK;
+}
+
+int shtg_plan_destroy(shtg_plan *plan) {
+    if (!plan) return SHTG_OK;
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    cudaDeviceSynchronize();
+    plan_free(p);
+    delete p;
+    return SHTG_OK;
+}
+
+int shtg_plan_get_info(const shtg_plan *plan, shtg_plan_info *info) {
+    if (!plan || !info) {
+        set_error("null argument");
+        return SHTG_ERR_ARG;
+    }
+    const Plan *p = reinterpret_cast<const Plan *>(plan);
+    info->geom = p->geom;
+    info->nside = p->nside;
+    info->nring = p->nring;
+    info->lmax = p->lmax;
+    info->max_batch = p->max_batch;
+    info->flags = p->flags;
+    info->npix = p->npix;
+    info->nalm = p->nalm;
+    info->device_bytes = p->device_bytes;
+    return SHTG_OK;
+}
+
+int shtg_alm2map(shtg_plan *plan, int spin, int precision, const void *alm, void *map,
+                 int nbatch, void *stream) {
+    SHTG_TRY(check_transform(plan, spin, precision, alm, map, nbatch));
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == SHTG_FP64) return transform_synth<double>(p, spin, alm, map, nbatch, st);
+    return transform_synth<float>(p, spin, alm, map, nbatch, st);
+}
+
+int shtg_alm2map_adjoint(shtg_plan *plan, int spin, int precision, const void *map, void *alm,
+                         int nbatch, void *stream) {
+    SHTG_TRY(check_transform(plan, spin, precision, map, alm, nbatch));
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == SHTG_FP64) return transform_adjoint<double>(p, spin, map, alm, nbatch, 0, st);
+    return transform_adjoint<float>(p, spin, map, alm, nbatch, 0, st);
+}
+
+int shtg_alm2map_vjp(shtg_plan *plan, int spin, int precision, const void *map_grad,
+                     void *alm_grad, int nbatch, void *stream) {
+    SHTG_TRY(check_transform(plan, spin, precision, map_grad, alm_grad, nbatch));
+    return alm2map_vjp(reinterpret_cast<Plan *>(plan), spin, precision, map_grad, alm_grad, nbatch,
+                       (cudaStream_t)stream);
+}
+
+int shtg_map2alm(shtg_plan *plan, int spin, int precision, const void *map, void *alm,
+                 int nbatch, int niter, void *stream) {
+    SHTG_TRY(check_transform(plan, spin, precision, map, alm, nbatch));
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (niter < 0 || niter > 100) {
+        set_error("niter must be in [0, 100]");
+        return SHTG_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (precision == SHTG_FP64) return map2alm_t<double>(p, spin, map, alm, nbatch, niter, st);
+    return map2alm_t<float>(p, spin, map, alm, nbatch, niter, st);
+}
+
+int shtg_cg_sample(shtg_plan *plan, const shtg_problem *prob, double *alm_out,
+                   const shtg_cg_opts *opts, shtg_cg_stats *stats, void *stream) {
+    if (!plan) {
+        set_error("null plan");
+        return SHTG_ERR_ARG;
+    }
+    return cg_sample(reinterpret_cast<Plan *>(plan), prob, alm_out, opts, stats,
+                     (cudaStream_t)stream);
+}
+
+int shtg_apply_operator(shtg_plan *plan, const shtg_problem *prob, const double *x, double *y,
+                        void *stream) {
+    if (!plan || !x || !y) {
+        set_error("null argument");
+        return SHTG_ERR_ARG;
+    }
+    return apply_operator(reinterpret_cast<Plan *>(plan), prob, x, y, (cudaStream_t)stream);
+}
+
+int shtg_logpost_grad(shtg_plan *plan, const double *cl, const double *bl, const float *alm,
+                      const float *d, const float *ninv, int nbins, const int *bin_lo,
+                      const int *bin_hi, int flags, double *logp, float *grad_alm,
+                      double *grad_logcl, void *stream) {
+    if (!plan || !cl || !bl || !alm || !d || !ninv || nbins < 0 ||
+        (nbins > 0 && grad_logcl && (!bin_lo || !bin_hi))) {
+        set_error("invalid argument");
+        return SHTG_ERR_ARG;
+    }
+    return logpost_grad(reinterpret_cast<Plan *>(plan), cl, bl, alm, d, ninv, nbins, bin_lo,
+                        bin_hi, flags, logp, grad_alm, grad_logcl, (cudaStream_t)stream);
+}
+
+}  // extern "C"

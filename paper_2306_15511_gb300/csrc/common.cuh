@@ -1,0 +1,213 @@
+// Internal declarations shared by the shtg CUDA translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/shtg.h"
+
+namespace shtg {
+
+// ----------------------------------------------------------------- errors
+void set_error(const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define SHTG_CUDA(call)                                                           \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) return ::shtg::cuda_fail(e_, #call, __FILE__, __LINE__); \
+    } while (0)
+
+#define SHTG_CHECK_LAUNCH(name)                                                   \
+    do {                                                                          \
+        cudaError_t e_ = cudaGetLastError();                                      \
+        if (e_ != cudaSuccess) return ::shtg::cuda_fail(e_, name, __FILE__, __LINE__); \
+    } while (0)
+
+#define SHTG_TRY(call)                                                            \
+    do {                                                                          \
+        int rc_ = (call);                                                         \
+        if (rc_ != SHTG_OK) return rc_;                                           \
+    } while (0)
+
+// ----------------------------------------------------------- real types
+template <typename T> struct VT;
+template <> struct VT<float> { typedef float2 C; };
+template <> struct VT<double> { typedef double2 C; };
+
+__host__ __device__ __forceinline__ float2 cplx(float r, float i) { return make_float2(r, i); }
+__host__ __device__ __forceinline__ double2 cplx(double r, double i) { return make_double2(r, i); }
+
+// ------------------------------------------------------------------ plan
+// Number of ring-FFT table entries per ring (see ringfft.cu).
+struct RingFFT {
+    int n;        // pixels on the ring
+    int logM;     // log2 of the power-of-two transform length
+    int blue;     // 1: Bluestein convolution of length M; 0: direct length n = M
+    int shift;    // phi0 = shift * pi / n (0 or 1)
+    int64_t chirp_off;  // offset of the n chirp values (Bluestein rings)
+    int64_t bhat_off;   // offset of the M spectra of the convolution kernel
+};
+
+// Kernel classes timed live with CUDA events (on the launching stream) when
+// profiling is on; see shtg_cg_stats.kernel_ms.
+enum KClass { K_LEG_SYN32 = 0, K_LEG_ANA32, K_RING32, K_LEG_SYN64, K_LEG_ANA64, K_RING64, K_VEC, K_DIAG };
+#define SHTG_NCLASS 8
+
+struct Prof {
+    bool on = false;
+    std::vector<cudaEvent_t> ev;   // pool created with the plan
+    std::vector<int> cls;
+    int n = 0;                     // recorded (begin, end) pairs
+    int open_cls = -1;
+    long long launches = 0;        // kernels launched by the library (always counted)
+};
+
+struct Plan {
+    int device = 0;
+    Prof prof;
+    int geom = 0, nside = 0, nring = 0, npairs = 0, lmax = 0, max_batch = 0, flags = 0;
+    int nphi_gauss = 0;
+    int64_t npix = 0, nalm = 0;
+    int nmaps_max = 0;          // maps the workspace holds (max_batch * (spin2 ? 3 : 1))
+    int64_t device_bytes = 0;
+
+    // host geometry (rings north to south)
+    std::vector<double> cth, sth, wring;
+    std::vector<int> nphi, shift;
+    std::vector<int64_t> ofs;
+
+    // device geometry
+    int *d_nphi = nullptr;
+    int64_t *d_ofs = nullptr;
+    double *d_wring = nullptr;    // quadrature weight of one pixel per ring
+    double *d_u64 = nullptr;      // 1 - cos(theta) of the north ring of each pair
+    float *d_u32 = nullptr;
+    double *d_x64 = nullptr;      // cos(theta) of the north ring of each pair
+    double *d_is2_64 = nullptr;   // 1 / sin^2(theta) per pair
+    float *d_x32 = nullptr, *d_is2_32 = nullptr;
+    int *d_lofidx = nullptr;      // l of each alm index
+    int *d_mofidx = nullptr;      // m of each alm index
+
+    // Legendre tables
+    double2 *d_rec64 = nullptr;   // (a_lm, b_lm): lambda_l = a (1-u) lambda_{l-1} + b lambda_{l-2}
+    float2 *d_rec32 = nullptr;
+    int *d_ls64 = nullptr, *d_ls32 = nullptr;     // [m][pair] first significant l
+    double2 *d_st64 = nullptr;    // [m][pair] (lambda_{ls-1}, lambda_ls)
+    float2 *d_st32 = nullptr;
+    double4_32a *d_s2c64 = nullptr;   // spin-2 per-(l,m) constants
+    float4 *d_s2c32 = nullptr;
+
+    // ring FFT tables
+    int fft_logmax = 0;
+    RingFFT *d_rfft = nullptr;
+    std::vector<RingFFT> h_rfft;
+    double2 *d_tw64 = nullptr;    // e^{-2 pi i k / Mmax}, k < Mmax/2
+    float2 *d_tw32 = nullptr;
+    double2 *d_chirp64 = nullptr, *d_bfwd64 = nullptr, *d_binv64 = nullptr;
+    float2 *d_chirp32 = nullptr, *d_bfwd32 = nullptr, *d_binv32 = nullptr;
+    size_t fft_smem64 = 0, fft_smem32 = 0;
+
+    // workspace
+    double2 *d_phase64 = nullptr;  // [nmaps_max][lmax+1][nring] Fourier coefficients per ring
+    float2 *d_phase32 = nullptr;
+    double *d_map64 = nullptr;     // [nmaps_max][npix] scratch maps
+    float *d_map32 = nullptr;
+    double *d_ninv64 = nullptr;    // [2][npix] problem weights (T, P)
+    float *d_ninv32 = nullptr;
+
+    // solver workspace (vectors hold max_batch realizations of all components)
+    double2 *v64[7] = {};          // b, x, r, z, p, q, t
+    float2 *v32[5] = {};           // r, z, p, q, x
+    double *d_minv64 = nullptr;    // [4][nalm] preconditioner blocks (inverse)
+    float *d_minv32 = nullptr;
+    float *d_diagT = nullptr, *d_diagP = nullptr;   // [nalm] ring-averaged diag of Y^T N^-1 Y
+    float *d_wpairT = nullptr, *d_wpairP = nullptr; // [npairs] N^-1 summed over the ring pair
+    double *d_ltab64 = nullptr;    // [9][lmax+1] beam, S^-1 (TT,TE,EE,BB), S^-1/2 (TT,TE,EE,BB)
+    float *d_ltab32 = nullptr;     // [5][lmax+1] beam, S^-1 (TT,TE,EE,BB)
+    double *d_scal = nullptr;      // [max_batch][16] per-realization PCG scalars
+    double *d_part = nullptr;      // reduction partial sums
+    double *d_lsum = nullptr;      // [lmax+1] per-l sums (log-posterior)
+    double *d_stage = nullptr;     // [nmaps_max][npix] staging for host inputs
+    double *h_pinned = nullptr;    // pinned host scalars
+};
+
+// solver.cu
+#define SHTG_RED_BLOCKS 128
+int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_opts *o,
+              shtg_cg_stats *stats, cudaStream_t st);
+int apply_operator(Plan *p, const shtg_problem *pr, const double *x, double *y, cudaStream_t st);
+int logpost_grad(Plan *p, const double *cl, const double *bl, const float *alm, const float *d,
+                 const float *ninv, int nbins, const int *blo, const int *bhi, int flags,
+                 double *logp, float *grad, double *gcl, cudaStream_t st);
+
+// plan.cu
+int plan_build(Plan *p);
+void plan_free(Plan *p);
+
+// profiling: bracket one launch (or a group) of a kernel class
+inline void prof_begin(Plan *p, int cls, cudaStream_t st) {
+    Prof &f = p->prof;
+    if (f.on && 2 * f.n + 1 < (int)f.ev.size()) {
+        cudaEventRecord(f.ev[2 * f.n], st);
+        f.open_cls = cls;
+    }
+}
+inline void prof_end(Plan *p, cudaStream_t st, int nlaunch = 1) {
+    Prof &f = p->prof;
+    f.launches += nlaunch;
+    if (f.open_cls >= 0) {
+        cudaEventRecord(f.ev[2 * f.n + 1], st);
+        if ((int)f.cls.size() <= f.n) f.cls.resize(f.n + 1);
+        f.cls[f.n] = f.open_cls;
+        f.n += 1;
+        f.open_cls = -1;
+    }
+}
+// after a stream synchronize: accumulate elapsed times per class and reset
+void prof_collect(Plan *p, double *ms, int *count);
+
+// legendre.cu: F[row][m][ring] <-> alm.  Map k of a call reads / writes the
+// alm row k * rs (spin 0) or rows k * rs (E) and k * rs + 1 (B) (spin 2), each
+// row nalm complex values; F rows are k (spin 0) or 2k (Q), 2k + 1 (U).
+// beam: device [lmax+1] multiplying the alm side, or null.
+template <typename T>
+int leg_synth(Plan *p, int spin, const typename VT<T>::C *alm, int rs, int nmaps,
+              const T *beam, typename VT<T>::C *F, cudaStream_t st);
+// vjp = 1 doubles the m > 0 outputs (gradient in real-component convention).
+template <typename T>
+int leg_analysis(Plan *p, int spin, const typename VT<T>::C *G, int nmaps, const T *beam,
+                 typename VT<T>::C *alm, int rs, cudaStream_t st, int vjp = 0);
+// out[l, m] = sum_r w_r g_lm(theta_r) (g = lambda^2 or lw^2 + lx^2)
+int leg_diag(Plan *p, int spin, const float *wring, float *out, cudaStream_t st);
+
+// ringfft.cu
+// mode 0: F -> map (synthesis); mode 1: map -> G (adjoint, wmode 1 = quadrature weights);
+// mode 2: F -> N^-1 -> G (fused, in place allowed).
+template <typename T>
+int ring_synth(Plan *p, const typename VT<T>::C *F, int nmaps, T *map, cudaStream_t st);
+template <typename T>
+int ring_analysis(Plan *p, const T *map, int nmaps, int weighted, typename VT<T>::C *G,
+                  cudaStream_t st);
+template <typename T>
+int ring_fused(Plan *p, typename VT<T>::C *FG, int nmaps, int nT, const T *ninv,
+               cudaStream_t st);
+
+int alm2map_vjp(Plan *p, int spin, int precision, const void *g, void *out, int nbatch,
+                cudaStream_t st);
+
+// capi.cu transforms used by the solver
+template <typename T>
+int transform_synth(Plan *p, int spin, const void *alm, void *map, int nbatch, cudaStream_t st);
+template <typename T>
+int transform_adjoint(Plan *p, int spin, const void *map, void *alm, int nbatch, int weighted,
+                      cudaStream_t st, int vjp = 0);
+
+inline int64_t alm_index(int l, int m, int lmax) {
+    return (int64_t)m * (2 * lmax + 1 - m) / 2 + l;
+}
+
+}  // namespace shtg

@@ -1,0 +1,522 @@
+// Plan construction: ring geometry, Legendre recurrence tables, FP64 start
+// states of the recurrence, ring-FFT tables and workspace.
+//
+// Legendre functions (App. A): Y_lm = lambda_lm(theta) e^{i m phi} with
+// lambda_mm = (-1)^m sqrt((2m+1)/(4 pi) prod_{k<=m} (2k-1)/(2k)) sin^m theta,
+// and for l > m the three-term recurrence written in u = 1 - cos theta,
+//     lambda_l = a_l (1 - u) lambda_{l-1} + b_l lambda_{l-2},
+//     a_l = sqrt((4l^2-1)/(l^2-m^2)),  b_l = -a_l sqrt(((l-1)^2-m^2)/(4(l-1)^2-1)),
+// (a_{m+1} = sqrt(2m+3), b_{m+1} = 0).  Carrying u instead of cos theta keeps
+// the near-polar rings exact in FP32, where cos theta rounds to 1.
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <map>
+
+#include "common.cuh"
+
+namespace shtg {
+
+static const double PI = 3.14159265358979323846264338327950288;
+
+// ------------------------------------------------------------ start states
+// For every (m, ring pair) walk the FP64 recurrence from lambda_mm with
+// exponent rescaling (value = v * 2^(512 k)) until |lambda_lm| first reaches
+// the significance threshold; record that l and (lambda_{l-1}, lambda_l).
+// Terms below the threshold are dropped by the transform kernels, which then
+// start their recurrence there without any rescaling logic.
+__global__ void k_start_states(int lmax, int npairs, const double *__restrict__ u64,
+                               const double *__restrict__ sect, const double2 *__restrict__ rec,
+                               double thr64, double thr32, int *ls64, double2 *st64, int *ls32,
+                               float2 *st32)
+{
+    const int pr = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m = blockIdx.y;
+    if (pr >= npairs) return;
+    const double u = u64[pr];
+    const double s = sqrt(u * (2.0 - u));
+    const int64_t o = (int64_t)m * npairs + pr;
+    int l64 = lmax + 1, l32 = lmax + 1;
+    double2 s64 = make_double2(0.0, 0.0);
+    float2 s32 = make_float2(0.f, 0.f);
+    if (s > 0.0) {
+        // sectoral value by products, kept in [2^-256, 2^256] * 2^(512 k)
+        double v = 0.28209479177387814347403972578;  // 1/sqrt(4 pi)
+        int k = 0;
+        for (int j = 1; j <= m; ++j) {
+            v *= -sect[j] * s;
+            if (fabs(v) < 0x1p-256) {
+                v *= 0x1p512;
+                k -= 1;
+            }
+        }
+        double prev = 0.0;
+        const int64_t base = (int64_t)m * (2 * lmax + 1 - m) / 2;
+        for (int l = m;; ++l) {
+            if (k == 0) {
+                const double a = fabs(v);
+                if (l32 > lmax && a >= thr32) {
+                    l32 = l;
+                    s32 = make_float2((float)prev, (float)v);
+                }
+                if (l64 > lmax && a >= thr64) {
+                    l64 = l;
+                    s64 = make_double2(prev, v);
+                }
+                if (l32 <= lmax && l64 <= lmax) break;
+            }
+            if (l == lmax) break;
+            const double2 c = rec[base + l + 1];
+            const double t = c.x * v;
+            const double nv = fma(t, -u, fma(c.y, prev, t));
+            prev = v;
+            v = nv;
+            if (fabs(v) > 0x1p256) {
+                v *= 0x1p-512;
+                prev *= 0x1p-512;
+                k += 1;
+            }
+        }
+    }
+    ls64[o] = l64;
+    st64[o] = s64;
+    ls32[o] = l32;
+    st32[o] = s32;
+}
+
+// ----------------------------------------------------------------- host FFT
+static int ilog2(int64_t n) {
+    int l = 0;
+    while ((int64_t(1) << l) < n) ++l;
+    return l;
+}
+static uint32_t bitrev(uint32_t x, int bits) {
+    uint32_t r = 0;
+    for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1u) << (bits - 1 - i);
+    return r;
+}
+// in-place forward DFT (e^{-2 pi i jk / M}) of length M = 2^logM, natural order out
+static void host_fft(std::vector<std::complex<double>> &a, int logM) {
+    const int M = 1 << logM;
+    for (int i = 0; i < M; ++i) {
+        const uint32_t j = bitrev(i, logM);
+        if (j > (uint32_t)i) std::swap(a[i], a[j]);
+    }
+    for (int len = 2; len <= M; len <<= 1) {
+        for (int k = 0; k < len / 2; ++k) {
+            const double ang = -2.0 * PI * k / len;
+            const std::complex<double> w(cos(ang), sin(ang));
+            for (int i = 0; i < M; i += len) {
+                const std::complex<double> x = a[i + k], y = a[i + k + len / 2] * w;
+                a[i + k] = x + y;
+                a[i + k + len / 2] = x - y;
+            }
+        }
+    }
+}
+
+template <typename P> static int dalloc(Plan *p, P **ptr, size_t count) {
+    const size_t bytes = count * sizeof(P);
+    if (bytes == 0) {
+        *ptr = nullptr;
+        return SHTG_OK;
+    }
+    cudaError_t e = cudaMalloc((void **)ptr, bytes);
+    if (e != cudaSuccess) {
+        *ptr = nullptr;
+        cudaGetLastError();
+        set_error(std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed: " +
+                  cudaGetErrorString(e));
+        return SHTG_ERR_NOMEM;
+    }
+    p->device_bytes += (int64_t)bytes;
+    return SHTG_OK;
+}
+template <typename P> static int upload(P *dst, const std::vector<P> &src) {
+    if (src.empty()) return SHTG_OK;
+    SHTG_CUDA(cudaMemcpy(dst, src.data(), src.size() * sizeof(P), cudaMemcpyHostToDevice));
+    return SHTG_OK;
+}
+
+// ----------------------------------------------------------------- geometry
+static void build_geometry(Plan *p, std::vector<double> &u_pair) {
+    if (p->geom == SHTG_GEOM_HEALPIX) {
+        const int N = p->nside;
+        p->nring = 4 * N - 1;
+        p->npix = 12LL * N * N;
+        p->cth.resize(p->nring);
+        p->sth.resize(p->nring);
+        p->nphi.resize(p->nring);
+        p->shift.resize(p->nring);
+        p->ofs.resize(p->nring);
+        p->wring.assign(p->nring, 4.0 * PI / (double)p->npix);
+        std::vector<double> uring(p->nring);
+        int64_t off = 0;
+        for (int i = 1; i <= 4 * N - 1; ++i) {
+            const int ii = (i <= 2 * N) ? i : 4 * N - i;
+            double u;
+            int np_, sh;
+            if (ii < N) {
+                u = (double)ii * ii / (3.0 * N * N);
+                np_ = 4 * ii;
+                sh = 1;
+            } else {
+                u = (2.0 * ii - N) / (3.0 * N);
+                np_ = 4 * N;
+                sh = ((ii - N) % 2 == 0) ? 1 : 0;
+            }
+            const int r = i - 1;
+            uring[r] = u;
+            p->cth[r] = (i <= 2 * N) ? 1.0 - u : -(1.0 - u);
+            p->sth[r] = sqrt(u * (2.0 - u));
+            p->nphi[r] = np_;
+            p->shift[r] = sh;
+            p->ofs[r] = off;
+            off += np_;
+        }
+        p->npairs = 2 * N;
+        u_pair.resize(p->npairs);
+        for (int r = 0; r < p->npairs; ++r) u_pair[r] = uring[r];
+    } else {
+        const int n = p->nring;
+        const int nphi = p->nphi_gauss;
+        p->npix = (int64_t)n * nphi;
+        p->cth.resize(n);
+        p->sth.resize(n);
+        p->nphi.assign(n, nphi);
+        p->shift.assign(n, 0);
+        p->ofs.resize(n);
+        p->wring.resize(n);
+        for (int k = 0; k < n; ++k) {
+            // Newton iteration on the Legendre polynomial P_n
+            double x = cos(PI * (k + 0.75) / (n + 0.5)), dp = 1.0;
+            for (int it = 0; it < 100; ++it) {
+                double p0 = 1.0, p1 = x;
+                for (int j = 2; j <= n; ++j) {
+                    const double p2 = ((2.0 * j - 1.0) * x * p1 - (j - 1.0) * p0) / j;
+                    p0 = p1;
+                    p1 = p2;
+                }
+                if (n == 1) p0 = 1.0, p1 = x;
+                dp = n * (x * p1 - p0) / (x * x - 1.0);
+                const double dx = p1 / dp;
+                x -= dx;
+                if (fabs(dx) < 1e-16) break;
+            }
+            double p0 = 1.0, p1 = x;
+            for (int j = 2; j <= n; ++j) {
+                const double p2 = ((2.0 * j - 1.0) * x * p1 - (j - 1.0) * p0) / j;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) p0 = 1.0, p1 = x;
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+            p->cth[k] = x;
+            p->sth[k] = sqrt((1.0 - x) * (1.0 + x));
+            p->ofs[k] = (int64_t)k * nphi;
+            p->wring[k] = 2.0 / ((1.0 - x * x) * dp * dp) * 2.0 * PI / nphi;
+        }
+        // symmetric nodes: the south half mirrors the north half exactly
+        for (int k = 0; k < n / 2; ++k) {
+            p->cth[n - 1 - k] = -p->cth[k];
+            p->sth[n - 1 - k] = p->sth[k];
+            p->wring[n - 1 - k] = p->wring[k];
+        }
+        if (n % 2 == 1) p->cth[n / 2] = 0.0, p->sth[n / 2] = 1.0;
+        p->npairs = (n + 1) / 2;
+        u_pair.resize(p->npairs);
+        for (int r = 0; r < p->npairs; ++r) u_pair[r] = 1.0 - p->cth[r];
+    }
+    p->nalm = (int64_t)(p->lmax + 1) * (p->lmax + 2) / 2;
+}
+
+static int build_legendre_tables(Plan *p, const std::vector<double> &u_pair) {
+    const int L = p->lmax;
+    const int64_t P = p->nalm;
+    std::vector<double2> rec64(P);
+    std::vector<float2> rec32(P);
+    std::vector<int> lof(P), mof(P);
+    std::vector<double4_32a> s2c64(P);
+    std::vector<float4> s2c32(P);
+    for (int m = 0; m <= L; ++m) {
+        for (int l = m; l <= L; ++l) {
+            const int64_t i = alm_index(l, m, L);
+            double a = 0.0, b = 0.0;
+            if (l == m + 1) {
+                a = sqrt(2.0 * m + 3.0);
+            } else if (l >= m + 2) {
+                const double dl = l, dm = m;
+                a = sqrt((4.0 * dl * dl - 1.0) / (dl * dl - dm * dm));
+                b = -a * sqrt(((dl - 1.0) * (dl - 1.0) - dm * dm) / (4.0 * (dl - 1.0) * (dl - 1.0) - 1.0));
+            }
+            rec64[i] = make_double2(a, b);
+            rec32[i] = make_float2((float)a, (float)b);
+            lof[i] = l;
+            mof[i] = m;
+            // spin-2 constants: with N_l = ((l-1) l (l+1) (l+2))^-1/2 and
+            // f = sqrt((2l+1)(l^2-m^2)/(2l-1)),
+            //   lw = c0 lambda_l / s^2 + c1 lambda_l + c2 x lambda_{l-1} / s^2
+            //   lx = c3 x lambda_l / s^2 + m c2/f... see legendre.cu
+            double c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+            if (l >= 2) {
+                const double dl = l, dm = m;
+                const double nl = 1.0 / sqrt((dl - 1.0) * dl * (dl + 1.0) * (dl + 2.0));
+                const double f = sqrt((2.0 * dl + 1.0) * (dl * dl - dm * dm) / (2.0 * dl - 1.0));
+                c0 = -2.0 * nl * (dl - dm * dm);   // lw: lambda_l / s^2
+                c1 = -nl * dl * (dl - 1.0);        // lw: lambda_l
+                c2 = 2.0 * nl * f;                 // lw: x lambda_{l-1} / s^2 ; lx: m lambda_{l-1} / s^2
+                c3 = -2.0 * nl * (dl - 1.0);       // lx: m x lambda_l / s^2
+            }
+            s2c64[i] = make_double4_32a(c0, c1, c2, c3);
+            s2c32[i] = make_float4((float)c0, (float)c1, (float)c2, (float)c3);
+        }
+    }
+    SHTG_TRY(dalloc(p, &p->d_rec64, P));
+    SHTG_TRY(dalloc(p, &p->d_rec32, P));
+    SHTG_TRY(dalloc(p, &p->d_lofidx, P));
+    SHTG_TRY(dalloc(p, &p->d_mofidx, P));
+    SHTG_TRY(dalloc(p, &p->d_s2c64, P));
+    SHTG_TRY(dalloc(p, &p->d_s2c32, P));
+    SHTG_TRY(upload(p->d_rec64, rec64));
+    SHTG_TRY(upload(p->d_rec32, rec32));
+    SHTG_TRY(upload(p->d_lofidx, lof));
+    SHTG_TRY(upload(p->d_mofidx, mof));
+    SHTG_TRY(upload(p->d_s2c64, s2c64));
+    SHTG_TRY(upload(p->d_s2c32, s2c32));
+
+    // per-pair geometry
+    const int NP = p->npairs;
+    std::vector<double> x64(NP), is2_64(NP);
+    std::vector<float> u32(NP), x32(NP), is2_32(NP);
+    for (int r = 0; r < NP; ++r) {
+        const double u = u_pair[r];
+        const double s2 = u * (2.0 - u);
+        x64[r] = 1.0 - u;
+        is2_64[r] = 1.0 / s2;
+        u32[r] = (float)u;
+        x32[r] = (float)(1.0 - u);
+        is2_32[r] = (float)(1.0 / s2);
+    }
+    SHTG_TRY(dalloc(p, &p->d_u64, NP));
+    SHTG_TRY(dalloc(p, &p->d_u32, NP));
+    SHTG_TRY(dalloc(p, &p->d_x64, NP));
+    SHTG_TRY(dalloc(p, &p->d_x32, NP));
+    SHTG_TRY(dalloc(p, &p->d_is2_64, NP));
+    SHTG_TRY(dalloc(p, &p->d_is2_32, NP));
+    SHTG_TRY(upload(p->d_u64, u_pair));
+    SHTG_TRY(upload(p->d_u32, u32));
+    SHTG_TRY(upload(p->d_x64, x64));
+    SHTG_TRY(upload(p->d_x32, x32));
+    SHTG_TRY(upload(p->d_is2_64, is2_64));
+    SHTG_TRY(upload(p->d_is2_32, is2_32));
+
+    // start states
+    std::vector<double> sect(L + 2, 0.0);
+    for (int k = 1; k <= L; ++k) sect[k] = sqrt((2.0 * k + 1.0) / (2.0 * k));
+    double *d_sect = nullptr;
+    SHTG_CUDA(cudaMalloc(&d_sect, sect.size() * sizeof(double)));
+    cudaMemcpy(d_sect, sect.data(), sect.size() * sizeof(double), cudaMemcpyHostToDevice);
+    const int64_t ns = (int64_t)(L + 1) * NP;
+    SHTG_TRY(dalloc(p, &p->d_ls64, ns));
+    SHTG_TRY(dalloc(p, &p->d_st64, ns));
+    SHTG_TRY(dalloc(p, &p->d_ls32, ns));
+    SHTG_TRY(dalloc(p, &p->d_st32, ns));
+    dim3 grid((NP + 127) / 128, L + 1);
+    // thresholds: terms below 2^-80 (FP64 kernels) / 2^-56 (FP32 kernels) are
+    // dropped; both leave room for the 1/sin^2 factor of the spin-2 functions.
+    k_start_states<<<grid, 128>>>(L, NP, p->d_u64, d_sect, p->d_rec64, 0x1p-80, 0x1p-56,
+                                  p->d_ls64, p->d_st64, p->d_ls32, p->d_st32);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(d_sect);
+    if (e != cudaSuccess) return cuda_fail(e, "k_start_states", __FILE__, __LINE__);
+    return SHTG_OK;
+}
+
+static int build_fft_tables(Plan *p) {
+    const int R = p->nring;
+    p->h_rfft.resize(R);
+    int logmax = 1;
+    std::map<int, std::pair<int64_t, int64_t>> offs;  // n -> (chirp_off, bhat_off)
+    int64_t chirp_total = 0, bhat_total = 0;
+    for (int r = 0; r < R; ++r) {
+        RingFFT f;
+        f.n = p->nphi[r];
+        f.shift = p->shift[r];
+        const int lg = ilog2(f.n);
+        if ((1 << lg) == f.n) {
+            f.blue = 0;
+            f.logM = lg;
+            f.chirp_off = f.bhat_off = 0;
+        } else {
+            f.blue = 1;
+            f.logM = ilog2(2 * (int64_t)f.n - 1);
+            auto it = offs.find(f.n);
+            if (it == offs.end()) {
+                offs[f.n] = std::make_pair(chirp_total, bhat_total);
+                f.chirp_off = chirp_total;
+                f.bhat_off = bhat_total;
+                chirp_total += f.n;
+                bhat_total += (int64_t)1 << f.logM;
+            } else {
+                f.chirp_off = it->second.first;
+                f.bhat_off = it->second.second;
+            }
+        }
+        if (f.logM > logmax) logmax = f.logM;
+        p->h_rfft[r] = f;
+    }
+    p->fft_logmax = logmax;
+    const int Mmax = 1 << logmax;
+    std::vector<double2> tw64(Mmax / 2);
+    std::vector<float2> tw32(Mmax / 2);
+    for (int k = 0; k < Mmax / 2; ++k) {
+        const double ang = -2.0 * PI * (double)k / (double)Mmax;
+        tw64[k] = make_double2(cos(ang), sin(ang));
+        tw32[k] = make_float2((float)cos(ang), (float)sin(ang));
+    }
+    std::vector<double2> ch64(chirp_total), bf64(bhat_total), bi64(bhat_total);
+    std::vector<float2> ch32(chirp_total), bf32(bhat_total), bi32(bhat_total);
+    for (auto &kv : offs) {
+        const int n = kv.first;
+        const int64_t co = kv.second.first, bo = kv.second.second;
+        const int lgM = ilog2(2 * (int64_t)n - 1);
+        const int M = 1 << lgM;
+        std::vector<std::complex<double>> c(n);
+        for (int j = 0; j < n; ++j) {
+            const int64_t q = ((int64_t)j * j) % (2 * (int64_t)n);
+            const double ang = -PI * (double)q / (double)n;   // c_j = e^{-i pi j^2 / n}
+            c[j] = std::complex<double>(cos(ang), sin(ang));
+            ch64[co + j] = make_double2(c[j].real(), c[j].imag());
+            ch32[co + j] = make_float2((float)c[j].real(), (float)c[j].imag());
+        }
+        std::vector<std::complex<double>> bfw(M, 0.0), biv(M, 0.0);
+        for (int j = 0; j < n; ++j) {
+            bfw[j] = std::conj(c[j]);
+            biv[j] = c[j];
+            if (j > 0) {
+                bfw[M - j] = std::conj(c[j]);
+                biv[M - j] = c[j];
+            }
+        }
+        host_fft(bfw, lgM);
+        host_fft(biv, lgM);
+        for (int i = 0; i < M; ++i) {
+            const uint32_t k = bitrev(i, lgM);
+            const std::complex<double> a = bfw[k] / (double)M, b = biv[k] / (double)M;
+            bf64[bo + i] = make_double2(a.real(), a.imag());
+            bi64[bo + i] = make_double2(b.real(), b.imag());
+            bf32[bo + i] = make_float2((float)a.real(), (float)a.imag());
+            bi32[bo + i] = make_float2((float)b.real(), (float)b.imag());
+        }
+    }
+    SHTG_TRY(dalloc(p, &p->d_rfft, R));
+    SHTG_TRY(upload(p->d_rfft, p->h_rfft));
+    SHTG_TRY(dalloc(p, &p->d_tw64, tw64.size()));
+    SHTG_TRY(dalloc(p, &p->d_tw32, tw32.size()));
+    SHTG_TRY(upload(p->d_tw64, tw64));
+    SHTG_TRY(upload(p->d_tw32, tw32));
+    SHTG_TRY(dalloc(p, &p->d_chirp64, ch64.size()));
+    SHTG_TRY(dalloc(p, &p->d_chirp32, ch32.size()));
+    SHTG_TRY(dalloc(p, &p->d_bfwd64, bf64.size()));
+    SHTG_TRY(dalloc(p, &p->d_binv64, bi64.size()));
+    SHTG_TRY(dalloc(p, &p->d_bfwd32, bf32.size()));
+    SHTG_TRY(dalloc(p, &p->d_binv32, bi32.size()));
+    SHTG_TRY(upload(p->d_chirp64, ch64));
+    SHTG_TRY(upload(p->d_chirp32, ch32));
+    SHTG_TRY(upload(p->d_bfwd64, bf64));
+    SHTG_TRY(upload(p->d_binv64, bi64));
+    SHTG_TRY(upload(p->d_bfwd32, bf32));
+    SHTG_TRY(upload(p->d_binv32, bi32));
+    p->fft_smem64 = (size_t)Mmax * sizeof(double2);
+    p->fft_smem32 = (size_t)Mmax * sizeof(float2);
+    return SHTG_OK;
+}
+
+int plan_build(Plan *p) {
+    std::vector<double> u_pair;
+    build_geometry(p, u_pair);
+    {
+        std::vector<int> nph(p->nphi.begin(), p->nphi.end());
+        SHTG_TRY(dalloc(p, &p->d_nphi, p->nring));
+        SHTG_TRY(upload(p->d_nphi, nph));
+        SHTG_TRY(dalloc(p, &p->d_ofs, p->nring));
+        SHTG_TRY(upload(p->d_ofs, p->ofs));
+        SHTG_TRY(dalloc(p, &p->d_wring, p->nring));
+        SHTG_TRY(upload(p->d_wring, p->wring));
+    }
+    SHTG_TRY(build_legendre_tables(p, u_pair));
+    SHTG_TRY(build_fft_tables(p));
+    // workspace
+    const int spin2 = (p->flags & SHTG_SPIN2) ? 1 : 0;
+    p->nmaps_max = p->max_batch * (spin2 ? 3 : 1);
+    const int64_t nph = (int64_t)p->nmaps_max * (p->lmax + 1) * p->nring;
+    SHTG_TRY(dalloc(p, &p->d_phase64, nph));
+    SHTG_TRY(dalloc(p, &p->d_phase32, nph));
+    const int64_t nmp = (int64_t)p->nmaps_max * p->npix;
+    SHTG_TRY(dalloc(p, &p->d_map64, nmp));
+    SHTG_TRY(dalloc(p, &p->d_map32, nmp));
+    SHTG_TRY(dalloc(p, &p->d_ninv64, 2 * p->npix));
+    SHTG_TRY(dalloc(p, &p->d_ninv32, 2 * p->npix));
+    // solver workspace
+    const int64_t nv = (int64_t)p->nmaps_max * p->nalm;
+    for (int i = 0; i < 7; ++i) SHTG_TRY(dalloc(p, &p->v64[i], nv));
+    for (int i = 0; i < 5; ++i) SHTG_TRY(dalloc(p, &p->v32[i], nv));
+    SHTG_TRY(dalloc(p, &p->d_minv64, 4 * p->nalm));
+    SHTG_TRY(dalloc(p, &p->d_minv32, 4 * p->nalm));
+    SHTG_TRY(dalloc(p, &p->d_diagT, p->nalm));
+    SHTG_TRY(dalloc(p, &p->d_diagP, p->nalm));
+    SHTG_TRY(dalloc(p, &p->d_wpairT, p->npairs));
+    SHTG_TRY(dalloc(p, &p->d_wpairP, p->npairs));
+    SHTG_TRY(dalloc(p, &p->d_ltab64, 9 * (int64_t)(p->lmax + 1)));
+    SHTG_TRY(dalloc(p, &p->d_ltab32, 5 * (int64_t)(p->lmax + 1)));
+    SHTG_TRY(dalloc(p, &p->d_scal, 16 * (int64_t)p->max_batch));
+    SHTG_TRY(dalloc(p, &p->d_part, 4 * (int64_t)p->max_batch * SHTG_RED_BLOCKS + 2 * (int64_t)p->max_batch + 64));
+    SHTG_TRY(dalloc(p, &p->d_lsum, (int64_t)p->lmax + 1));
+    SHTG_TRY(dalloc(p, &p->d_stage, nmp));
+    SHTG_CUDA(cudaMallocHost((void **)&p->h_pinned, 4096 * sizeof(double)));
+    p->prof.ev.resize(16384);
+    for (auto &e : p->prof.ev) SHTG_CUDA(cudaEventCreate(&e));
+    p->prof.cls.reserve(8192);
+    SHTG_CUDA(cudaDeviceSynchronize());
+    return SHTG_OK;
+}
+
+void plan_free(Plan *p) {
+    void *ptrs[] = {p->d_nphi, p->d_ofs, p->d_wring, p->d_u64, p->d_u32, p->d_x64, p->d_is2_64,
+                    p->d_x32, p->d_is2_32, p->d_lofidx, p->d_mofidx, p->d_rec64, p->d_rec32,
+                    p->d_ls64, p->d_ls32, p->d_st64, p->d_st32, p->d_s2c64, p->d_s2c32,
+                    p->d_rfft, p->d_tw64, p->d_tw32, p->d_chirp64, p->d_bfwd64, p->d_binv64,
+                    p->d_chirp32, p->d_bfwd32, p->d_binv32, p->d_phase64, p->d_phase32,
+                    p->d_map64, p->d_map32, p->d_ninv64, p->d_ninv32, p->d_minv64,
+                    p->d_minv32, p->d_diagT, p->d_diagP, p->d_wpairT, p->d_wpairP,
+                    p->d_ltab64, p->d_ltab32, p->d_scal, p->d_part, p->d_lsum, p->d_stage};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    for (int i = 0; i < 7; ++i)
+        if (p->v64[i]) cudaFree(p->v64[i]);
+    for (int i = 0; i < 5; ++i)
+        if (p->v32[i]) cudaFree(p->v32[i]);
+    if (p->h_pinned) cudaFreeHost(p->h_pinned);
+    for (auto &e : p->prof.ev)
+        if (e) cudaEventDestroy(e);
+    p->prof.ev.clear();
+}
+
+void prof_collect(Plan *p, double *ms, int *count) {
+    Prof &f = p->prof;
+    for (int i = 0; i < f.n; ++i) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, f.ev[2 * i], f.ev[2 * i + 1]) == cudaSuccess) {
+            const int c = f.cls[i];
+            if (ms) ms[c] += t;
+            if (count) count[c] += 1;
+        } else {
+            cudaGetLastError();
+        }
+    }
+    f.n = 0;
+    f.open_cls = -1;
+}
+
+}  // namespace shtg

@@ -1,0 +1,946 @@
+// Constrained-realization solver of Eq. (mapmakingeq), Sect. 2.2.1:
+//
+//     (S^-1 + B Y^T N^-1 Y B) a = B Y^T (N^-1 d + N^-1/2 w2) + S^-1/2 w1
+//
+// solved by preconditioned conjugate gradients (the paper uses CG with the
+// diagonal preconditioner of Sect. 4).  nbatch realizations share the
+// operator; each keeps its own CG scalars in device memory so that an
+// iteration is a fixed launch sequence with no host round trip, and a
+// realization that has converged is frozen (alpha = beta = 0) while the
+// others continue.
+//
+// Modes: plain FP64 PCG, or FP32 PCG on A delta = r inside FP64 iterative
+// refinement (r = b - A x evaluated with the FP64 transforms), which reaches
+// the FP64 residual target with FP32 operator applications.
+//
+// Inner products use <a, c> = sum_l [a_l0 c_l0 + 2 Re sum_{m>0} conj(a_lm) c_lm],
+// the metric in which Y^T is the transpose of Y and A is symmetric.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace shtg {
+
+#define RT 256
+#define RB SHTG_RED_BLOCKS
+
+// scalar slots per realization
+enum { S_RZ = 0, S_PQ, S_RR, S_BB, S_ALPHA, S_BETA, S_ACTIVE, S_ITERS, S_TOL2, S_BAD, S_SCALE };
+
+__device__ __forceinline__ double cdot(float2 a, float2 b) {
+    return (double)a.x * (double)b.x + (double)a.y * (double)b.y;
+}
+__device__ __forceinline__ double cdot(double2 a, double2 b) { return a.x * b.x + a.y * b.y; }
+
+__device__ double block_sum(double v, double *sm) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sm[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sm[i];
+    return r;
+}
+
+// --------------------------------------------------------------- pixel side
+// out rows [T_0 .. T_{nb-1}, Q_0, U_0, Q_1, U_1, ...] (the transform's row order)
+// from inputs in [b][c][npix] order: out (=|+=) N^-1 d (+ sqrt(N^-1) w2).
+__global__ void k_rhs_pix(const double *__restrict__ d, const double *__restrict__ w2,
+                          const double *__restrict__ ninv, int nb, int nc, int64_t npix,
+                          int accumulate, double *__restrict__ out) {
+    const int row = blockIdx.y;
+    const int b = row / nc, c = row % nc;
+    const int orow = (c == 0) ? b : nb + 2 * b + (c - 1);
+    const double *wv = ninv + (c == 0 ? 0 : npix);
+    double *o = out + (int64_t)orow * npix;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const double w = wv[p];
+        double v = 0.0;
+        if (d) v += w * d[(int64_t)row * npix + p];
+        if (w2) v += sqrt(w) * w2[(int64_t)row * npix + p];
+        o[p] = accumulate ? o[p] + v : v;
+    }
+}
+
+__global__ void k_to_float(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+// sum of N^-1 over both rings of every pair
+__global__ void k_wpair(const double *__restrict__ ninv, const int64_t *__restrict__ ofs,
+                        const int *__restrict__ nphi, int nring, float *__restrict__ out) {
+    __shared__ double sm[RT / 32];
+    const int pr = blockIdx.x;
+    const int rn = pr, rs = nring - 1 - pr;
+    double s = 0.0;
+    for (int j = threadIdx.x; j < nphi[rn]; j += blockDim.x) s += ninv[ofs[rn] + j];
+    if (rs != rn)
+        for (int j = threadIdx.x; j < nphi[rs]; j += blockDim.x) s += ninv[ofs[rs] + j];
+    s = block_sum(s, sm);
+    if (threadIdx.x == 0) out[pr] = (float)s;
+}
+
+// ------------------------------------------------------------ harmonic side
+template <typename T> struct HT;
+template <> struct HT<float> { typedef float2 C; };
+template <> struct HT<double> { typedef double2 C; };
+
+// y += S^-1 x (per-l 1x1 or T/E 2x2 + B block); sinv rows TT, TE, EE, BB
+template <typename T>
+__global__ void k_prior_add(const typename HT<T>::C *__restrict__ x, typename HT<T>::C *__restrict__ y,
+                            int nc, int64_t nalm, int lmax1, const int *__restrict__ lof,
+                            const T *__restrict__ sinv) {
+    const int b = blockIdx.y;
+    const int64_t off = (int64_t)b * nc * nalm;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nalm;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int l = lof[i];
+        const T tt = sinv[l];
+        if (nc == 1) {
+            const auto xv = x[off + i];
+            auto yv = y[off + i];
+            yv.x += tt * xv.x;
+            yv.y += tt * xv.y;
+            y[off + i] = yv;
+        } else {
+            const T te = sinv[lmax1 + l], ee = sinv[2 * lmax1 + l], bb = sinv[3 * lmax1 + l];
+            const auto xt = x[off + i], xe = x[off + nalm + i], xb = x[off + 2 * nalm + i];
+            auto yt = y[off + i], ye = y[off + nalm + i], yb = y[off + 2 * nalm + i];
+            yt.x += tt * xt.x + te * xe.x;
+            yt.y += tt * xt.y + te * xe.y;
+            ye.x += te * xt.x + ee * xe.x;
+            ye.y += te * xt.y + ee * xe.y;
+            yb.x += bb * xb.x;
+            yb.y += bb * xb.y;
+            y[off + i] = yt;
+            y[off + nalm + i] = ye;
+            y[off + 2 * nalm + i] = yb;
+        }
+    }
+}
+
+// Preconditioner M = S^-1 + b_l^2 diag(D_T, D_P, D_P), stored as its inverse:
+// nc = 1: minv[0] = 1 / M; nc = 3: minv[0..2] = inverse T/E block (11, 12, 22), minv[3] = 1 / M_BB.
+__global__ void k_precond(const float *__restrict__ dT, const float *__restrict__ dP,
+                          const double *__restrict__ ltab, int nc, int64_t nalm, int lmax1,
+                          const int *__restrict__ lof, int use_diag, double *__restrict__ m64,
+                          float *__restrict__ m32) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nalm;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int l = lof[i];
+        const double b2 = use_diag ? ltab[l] * ltab[l] : 0.0;
+        const double tt = ltab[lmax1 + l], te = ltab[2 * lmax1 + l], ee = ltab[3 * lmax1 + l],
+                     bb = ltab[4 * lmax1 + l];
+        double v[4];
+        const double gT = use_diag ? b2 * (double)dT[i] : 0.0;
+        const double gP = (use_diag && nc == 3) ? b2 * (double)dP[i] : 0.0;
+        if (nc == 1) {
+            v[0] = 1.0 / (tt + gT);
+            v[1] = v[2] = v[3] = 0.0;
+        } else {
+            const double a11 = tt + gT, a12 = te, a22 = ee + gP;
+            const double det = a11 * a22 - a12 * a12;
+            v[0] = a22 / det;
+            v[1] = -a12 / det;
+            v[2] = a11 / det;
+            v[3] = 1.0 / (bb + gP);
+        }
+        for (int k = 0; k < 4; ++k) {
+            m64[k * nalm + i] = v[k];
+            m32[k * nalm + i] = (float)v[k];
+        }
+    }
+}
+
+// RHS: b += S^-1/2 w1 (sinvh rows TT, TE, EE, BB)
+__global__ void k_rhs_alm(const double2 *__restrict__ w1, double2 *__restrict__ bvec, int nc,
+                          int64_t nalm, int lmax1, const int *__restrict__ lof,
+                          const int *__restrict__ mof, const double *__restrict__ sh) {
+    const int b = blockIdx.y;
+    const int64_t off = (int64_t)b * nc * nalm;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nalm;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int l = lof[i];
+        const bool m0 = mof[i] == 0;
+        const double tt = sh[l];
+        if (nc == 1) {
+            double2 w = w1[off + i], v = bvec[off + i];
+            v.x += tt * w.x;
+            v.y = m0 ? 0.0 : v.y + tt * w.y;
+            bvec[off + i] = v;
+        } else {
+            const double te = sh[lmax1 + l], ee = sh[2 * lmax1 + l], bb = sh[3 * lmax1 + l];
+            const double2 wt = w1[off + i], we = w1[off + nalm + i], wb = w1[off + 2 * nalm + i];
+            double2 vt = bvec[off + i], ve = bvec[off + nalm + i], vb = bvec[off + 2 * nalm + i];
+            vt.x += tt * wt.x + te * we.x;
+            vt.y += tt * wt.y + te * we.y;
+            ve.x += te * wt.x + ee * we.x;
+            ve.y += te * wt.y + ee * we.y;
+            vb.x += bb * wb.x;
+            vb.y += bb * wb.y;
+            if (m0) vt.y = ve.y = vb.y = 0.0;
+            bvec[off + i] = vt;
+            bvec[off + nalm + i] = ve;
+            bvec[off + 2 * nalm + i] = vb;
+        }
+    }
+}
+
+// --------------------------------------------------------------- PCG kernels
+// partial <a, c> per realization
+template <typename C>
+__global__ void k_dot(const C *__restrict__ a, const C *__restrict__ c, int nc, int64_t nalm,
+                      const int *__restrict__ mof, double *__restrict__ part, int slot, int nslot) {
+    __shared__ double sm[RT / 32];
+    const int b = blockIdx.y;
+    const int64_t off = (int64_t)b * nc * nalm;
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nalm;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double w = mof[i] ? 2.0 : 1.0;
+        double t = 0.0;
+        for (int k = 0; k < nc; ++k) t += cdot(a[off + k * nalm + i], c[off + k * nalm + i]);
+        s += w * t;
+    }
+    s = block_sum(s, sm);
+    if (threadIdx.x == 0) part[((int64_t)b * nslot + slot) * RB + blockIdx.x] = s;
+}
+
+__device__ __forceinline__ double sum_part(const double *part, int b, int nslot, int slot) {
+    double s = 0.0;
+    for (int k = 0; k < RB; ++k) s += part[((int64_t)b * nslot + slot) * RB + k];
+    return s;
+}
+
+// apply the preconditioner inverse block to (r_T, r_E, r_B) at alm index i
+template <typename T, typename C>
+__device__ __forceinline__ void apply_minv(const T *minv, int64_t nalm, int64_t i, int nc,
+                                           const C *r, C *z) {
+    if (nc == 1) {
+        const T m = minv[i];
+        z[0].x = m * r[0].x;
+        z[0].y = m * r[0].y;
+    } else {
+        const T a = minv[i], b = minv[nalm + i], c = minv[2 * nalm + i], d = minv[3 * nalm + i];
+        z[0].x = a * r[0].x + b * r[1].x;
+        z[0].y = a * r[0].y + b * r[1].y;
+        z[1].x = b * r[0].x + c * r[1].x;
+        z[1].y = b * r[0].y + c * r[1].y;
+        z[2].x = d * r[2].x;
+        z[2].y = d * r[2].y;
+    }
+}
+
+// INIT: z = M^-1 r and partial (rz, rr).  Otherwise x += alpha p, r -= alpha q,
+// then the same.
+template <typename T, bool INIT>
+__global__ void k_update(typename HT<T>::C *__restrict__ x, typename HT<T>::C *__restrict__ r,
+                         typename HT<T>::C *__restrict__ z, const typename HT<T>::C *__restrict__ p,
+                         const typename HT<T>::C *__restrict__ q, const T *__restrict__ minv,
+                         int nc, int64_t nalm, const int *__restrict__ mof,
+                         const double *__restrict__ scal, double *__restrict__ part) {
+    typedef typename HT<T>::C C;
+    __shared__ double sm[RT / 32];
+    const int b = blockIdx.y;
+    const int64_t off = (int64_t)b * nc * nalm;
+    const T alpha = INIT ? T(0) : (T)scal[b * 16 + S_ALPHA];
+    double srz = 0.0, srr = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nalm;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        C rv[3], zv[3];
+        for (int k = 0; k < nc; ++k) {
+            const int64_t e = off + k * nalm + i;
+            C rr = r[e];
+            if (!INIT) {
+                const C pv = p[e], qv = q[e];
+                C xv = x[e];
+                xv.x += alpha * pv.x;
+                xv.y += alpha * pv.y;
+                x[e] = xv;
+                rr.x -= alpha * qv.x;
+                rr.y -= alpha * qv.y;
+                r[e] = rr;
+            }
+            rv[k] = rr;
+        }
+        apply_minv<T, C>(minv, nalm, i, nc, rv, zv);
+        const double w = mof[i] ? 2.0 : 1.0;
+        double a1 = 0.0, a2 = 0.0;
+        for (int k = 0; k < nc; ++k) {
+            z[off + k * nalm + i] = zv[k];
+            a1 += cdot(rv[k], zv[k]);
+            a2 += cdot(rv[k], rv[k]);
+        }
+        srz += w * a1;
+        srr += w * a2;
+    }
+    srz = block_sum(srz, sm);
+    srr = block_sum(srr, sm);
+    if (threadIdx.x == 0) {
+        part[((int64_t)b * 2 + 0) * RB + blockIdx.x] = srz;
+        part[((int64_t)b * 2 + 1) * RB + blockIdx.x] = srr;
+    }
+}
+
+__global__ void k_scal_init(const double *__restrict__ part, double *__restrict__ scal, int nb,
+                            double tol2) {
+    const int b = threadIdx.x;
+    if (b >= nb) return;
+    const double rz = sum_part(part, b, 2, 0), rr = sum_part(part, b, 2, 1);
+    double *s = scal + b * 16;
+    s[S_RZ] = rz;
+    s[S_RR] = rr;
+    s[S_BB] = rr;
+    s[S_TOL2] = tol2;
+    s[S_ACTIVE] = (rr > 0.0) ? 1.0 : 0.0;
+    s[S_ITERS] = 0.0;
+    s[S_BAD] = (isfinite(rr) && isfinite(rz)) ? 0.0 : 1.0;
+    s[S_ALPHA] = s[S_BETA] = 0.0;
+}
+
+__global__ void k_scal_alpha(const double *__restrict__ part, double *__restrict__ scal, int nb) {
+    const int b = threadIdx.x;
+    if (b >= nb) return;
+    double *s = scal + b * 16;
+    const double pq = sum_part(part, b, 1, 0);
+    s[S_PQ] = pq;
+    double alpha = 0.0;
+    if (s[S_ACTIVE] != 0.0) {
+        if (pq > 0.0 && isfinite(pq)) {
+            alpha = s[S_RZ] / pq;
+        } else {
+            s[S_ACTIVE] = 0.0;
+            s[S_BAD] = 1.0;
+        }
+    }
+    s[S_ALPHA] = alpha;
+}
+
+__global__ void k_scal_beta(const double *__restrict__ part, double *__restrict__ scal, int nb) {
+    const int b = threadIdx.x;
+    if (b >= nb) return;
+    double *s = scal + b * 16;
+    const double rz = sum_part(part, b, 2, 0), rr = sum_part(part, b, 2, 1);
+    double beta = 0.0;
+    if (s[S_ACTIVE] != 0.0) {
+        s[S_ITERS] += 1.0;
+        if (!isfinite(rz) || !isfinite(rr)) {
+            s[S_BAD] = 1.0;
+            s[S_ACTIVE] = 0.0;
+        } else {
+            beta = (s[S_RZ] != 0.0) ? rz / s[S_RZ] : 0.0;
+            s[S_RZ] = rz;
+            s[S_RR] = rr;
+            if (rr <= s[S_TOL2] * s[S_BB]) s[S_ACTIVE] = 0.0;
+        }
+    }
+    s[S_BETA] = beta;
+}
+
+template <typename C>
+__global__ void k_pupdate(C *__restrict__ p, const C *__restrict__ z, int nc, int64_t nalm,
+                          const double *__restrict__ scal) {
+    const int b = blockIdx.y;
+    const int64_t off = (int64_t)b * nc * nalm;
+    const double beta = scal[b * 16 + S_BETA];
+    const int64_t n = (int64_t)nc * nalm;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        C pv = p[off + i];
+        const C zv = z[off + i];
+        pv.x = zv.x + (decltype(pv.x))beta * pv.x;
+        pv.y = zv.y + (decltype(pv.y))beta * pv.y;
+        p[off + i] = pv;
+    }
+}
+
+// mixed precision helpers
+__global__ void k_resid(const double2 *__restrict__ b, const double2 *__restrict__ t,
+                        double2 *__restrict__ r, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 bv = b[i], tv = t[i];
+        r[i] = make_double2(bv.x - tv.x, bv.y - tv.y);
+    }
+}
+// r32 = r64 / scale_b (0 for realizations already converged)
+__global__ void k_scale_down(const double2 *__restrict__ r, float2 *__restrict__ r32, int64_t per,
+                             const double *__restrict__ inv_scale) {
+    const int b = blockIdx.y;
+    const double s = inv_scale[b];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = r[(int64_t)b * per + i];
+        r32[(int64_t)b * per + i] = make_float2((float)(v.x * s), (float)(v.y * s));
+    }
+}
+// x64 += scale_b * d32
+__global__ void k_correct(double2 *__restrict__ x, const float2 *__restrict__ d, int64_t per,
+                          const double *__restrict__ scale) {
+    const int b = blockIdx.y;
+    const double s = scale[b];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = d[(int64_t)b * per + i];
+        double2 xv = x[(int64_t)b * per + i];
+        xv.x += s * (double)v.x;
+        xv.y += s * (double)v.y;
+        x[(int64_t)b * per + i] = xv;
+    }
+}
+
+// ------------------------------------------------------------ log-posterior
+// per-l sums of the prior term: lsum[l] += w_m |a_lm|^2 / C_l (active l)
+__global__ void k_prior_lsum(const float2 *__restrict__ a, int64_t nalm, const int *__restrict__ lof,
+                             const int *__restrict__ mof, const float *__restrict__ icl,
+                             double *__restrict__ lsum) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nalm;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int l = lof[i];
+        const float c = icl[l];
+        if (c == 0.f) continue;
+        const double w = mof[i] ? 2.0 : 1.0;
+        const float2 v = a[i];
+        atomicAdd(&lsum[l], w * ((double)v.x * v.x + (double)v.y * v.y) * (double)c);
+    }
+}
+// res = d - m (in place in m); chi2 partial = sum ninv res^2; m <- ninv res
+__global__ void k_resid_pix(const float *__restrict__ d, const float *__restrict__ ninv,
+                            float *__restrict__ m, int64_t npix, double *__restrict__ part) {
+    __shared__ double sm[RT / 32];
+    double s = 0.0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const float r = d[p] - m[p];
+        const float w = ninv[p];
+        s += (double)w * (double)r * (double)r;
+        m[p] = w * r;
+    }
+    s = block_sum(s, sm);
+    if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+// grad -= a / C_l (active l), zero at held multipoles
+__global__ void k_grad_prior(const float2 *__restrict__ a, float2 *__restrict__ g, int64_t nalm,
+                             const int *__restrict__ lof, const int *__restrict__ mof,
+                             const float *__restrict__ icl, int components) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nalm;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const float c = icl[lof[i]];
+        float2 v = g[i];
+        const float2 av = a[i];
+        if (c == 0.f) {
+            v = make_float2(0.f, 0.f);
+        } else {
+            v.x -= c * av.x;
+            v.y -= c * av.y;
+        }
+        if (mof[i] == 0) {
+            v.y = 0.f;
+        } else if (components) {
+            v.x *= 2.f;
+            v.y *= 2.f;
+        }
+        g[i] = v;
+    }
+}
+
+// ====================================================================== host
+struct Solve {
+    Plan *p;
+    cudaStream_t st;
+    int nb, nc;
+    int64_t nalm, per, nvec;
+    dim3 vgrid;   // (blocks, nb)
+    dim3 rgrid;   // (RB, nb)
+};
+
+static dim3 grid_1d(int64_t n) {
+    int64_t g = (n + RT - 1) / RT;
+    if (g > 4096) g = 4096;
+    if (g < 1) g = 1;
+    return dim3((unsigned)g);
+}
+
+template <typename T> struct Vec;
+template <> struct Vec<double> {
+    static double2 *r(Plan *p) { return p->v64[2]; }
+    static double2 *z(Plan *p) { return p->v64[3]; }
+    static double2 *pp(Plan *p) { return p->v64[4]; }
+    static double2 *q(Plan *p) { return p->v64[5]; }
+    static double *minv(Plan *p) { return p->d_minv64; }
+    static double *beam(Plan *p) { return p->d_ltab64; }
+    static double *sinv(Plan *p) { return p->d_ltab64 + (p->lmax + 1); }
+    static double *ninv(Plan *p) { return p->d_ninv64; }
+    static double2 *phase(Plan *p) { return p->d_phase64; }
+};
+template <> struct Vec<float> {
+    static float2 *r(Plan *p) { return p->v32[0]; }
+    static float2 *z(Plan *p) { return p->v32[1]; }
+    static float2 *pp(Plan *p) { return p->v32[2]; }
+    static float2 *q(Plan *p) { return p->v32[3]; }
+    static float *minv(Plan *p) { return p->d_minv32; }
+    static float *beam(Plan *p) { return p->d_ltab32; }
+    static float *sinv(Plan *p) { return p->d_ltab32 + (p->lmax + 1); }
+    static float *ninv(Plan *p) { return p->d_ninv32; }
+    static float2 *phase(Plan *p) { return p->d_phase32; }
+};
+
+// y = A x = S^-1 x + B Y^T N^-1 Y B x for all realizations
+template <typename T>
+static int matvec(Solve &s, const typename HT<T>::C *x, typename HT<T>::C *y) {
+    typedef typename HT<T>::C C;
+    Plan *p = s.p;
+    C *F = Vec<T>::phase(p);
+    const T *beam = Vec<T>::beam(p);
+    const int64_t rowsz = (int64_t)(p->lmax + 1) * p->nring;
+    SHTG_TRY(leg_synth<T>(p, 0, x, s.nc, s.nb, beam, F, s.st));
+    if (s.nc == 3) SHTG_TRY(leg_synth<T>(p, 2, x + s.nalm, 3, s.nb, beam, F + s.nb * rowsz, s.st));
+    SHTG_TRY(ring_fused<T>(p, F, s.nb * s.nc, s.nb, Vec<T>::ninv(p), s.st));
+    SHTG_TRY(leg_analysis<T>(p, 0, F, s.nb, beam, y, s.nc, s.st));
+    if (s.nc == 3) SHTG_TRY(leg_analysis<T>(p, 2, F + s.nb * rowsz, s.nb, beam, y + s.nalm, 3, s.st));
+    prof_begin(p, K_VEC, s.st);
+    k_prior_add<T><<<dim3(grid_1d(s.nalm).x, s.nb), RT, 0, s.st>>>(x, y, s.nc, s.nalm, p->lmax + 1,
+                                                                   p->d_lofidx, Vec<T>::sinv(p));
+    prof_end(p, s.st);
+    SHTG_CHECK_LAUNCH("k_prior_add");
+    return SHTG_OK;
+}
+
+// PCG on A x = b for T vectors; x starts at 0.  Per-realization convergence
+// at ||r|| <= tol ||b||.  Returns the number of iterations run.
+template <typename T>
+static int pcg(Solve &s, const typename HT<T>::C *b, typename HT<T>::C *x, double tol, int maxiter,
+               int check_every, int *iters, int *all_converged) {
+    typedef typename HT<T>::C C;
+    Plan *p = s.p;
+    C *r = Vec<T>::r(p), *z = Vec<T>::z(p), *pv = Vec<T>::pp(p), *q = Vec<T>::q(p);
+    const T *minv = Vec<T>::minv(p);
+    const size_t vb = sizeof(C) * (size_t)s.nvec;
+    SHTG_CUDA(cudaMemsetAsync(x, 0, vb, s.st));
+    SHTG_CUDA(cudaMemcpyAsync(r, b, vb, cudaMemcpyDeviceToDevice, s.st));
+    k_update<T, true><<<s.rgrid, RT, 0, s.st>>>(nullptr, r, z, nullptr, nullptr, minv, s.nc, s.nalm,
+                                                p->d_mofidx, p->d_scal, p->d_part);
+    SHTG_CHECK_LAUNCH("k_update init");
+    k_scal_init<<<1, 1024, 0, s.st>>>(p->d_part, p->d_scal, s.nb, tol * tol);
+    p->prof.launches += 2;
+    SHTG_CHECK_LAUNCH("k_scal_init");
+    SHTG_CUDA(cudaMemcpyAsync(pv, z, vb, cudaMemcpyDeviceToDevice, s.st));
+    int it = 0;
+    *all_converged = 0;
+    if (check_every < 1) check_every = 1;
+    while (it < maxiter) {
+        // host check first: every realization may already be done (b = 0)
+        SHTG_CUDA(cudaMemcpyAsync(p->h_pinned, p->d_scal, sizeof(double) * 16 * s.nb,
+                                  cudaMemcpyDeviceToHost, s.st));
+        SHTG_CUDA(cudaStreamSynchronize(s.st));
+        int active = 0, bad = 0;
+        for (int k = 0; k < s.nb; ++k) {
+            active += p->h_pinned[k * 16 + S_ACTIVE] != 0.0;
+            bad += p->h_pinned[k * 16 + S_BAD] != 0.0;
+        }
+        if (bad) {
+            set_error("non-finite or non-positive curvature in PCG");
+            *iters = it;
+            return SHTG_ERR_NONFINITE;
+        }
+        if (!active) {
+            *all_converged = 1;
+            break;
+        }
+        const int nrun = std::min(check_every, maxiter - it);
+        for (int k = 0; k < nrun; ++k) {
+            SHTG_TRY(matvec<T>(s, pv, q));
+            prof_begin(p, K_VEC, s.st);
+            k_dot<C><<<s.rgrid, RT, 0, s.st>>>(pv, q, s.nc, s.nalm, p->d_mofidx, p->d_part, 0, 1);
+            k_scal_alpha<<<1, 1024, 0, s.st>>>(p->d_part, p->d_scal, s.nb);
+            k_update<T, false><<<s.rgrid, RT, 0, s.st>>>(x, r, z, pv, q, minv, s.nc, s.nalm,
+                                                         p->d_mofidx, p->d_scal, p->d_part);
+            k_scal_beta<<<1, 1024, 0, s.st>>>(p->d_part, p->d_scal, s.nb);
+            k_pupdate<C><<<dim3(grid_1d(s.per).x, s.nb), RT, 0, s.st>>>(pv, z, s.nc, s.nalm, p->d_scal);
+            prof_end(p, s.st, 5);
+            SHTG_CHECK_LAUNCH("pcg iteration");
+        }
+        it += nrun;
+    }
+    if (!*all_converged) {
+        SHTG_CUDA(cudaMemcpyAsync(p->h_pinned, p->d_scal, sizeof(double) * 16 * s.nb,
+                                  cudaMemcpyDeviceToHost, s.st));
+        SHTG_CUDA(cudaStreamSynchronize(s.st));
+        int active = 0;
+        for (int k = 0; k < s.nb; ++k) active += p->h_pinned[k * 16 + S_ACTIVE] != 0.0;
+        *all_converged = active == 0;
+    }
+    int mx = 0;
+    for (int k = 0; k < s.nb; ++k) mx = std::max(mx, (int)p->h_pinned[k * 16 + S_ITERS]);
+    *iters = it;
+    (void)mx;
+    return SHTG_OK;
+}
+
+// per-realization <v, v> into host array
+static int norms2(Solve &s, const double2 *v, std::vector<double> &out) {
+    Plan *p = s.p;
+    k_dot<double2><<<s.rgrid, RT, 0, s.st>>>(v, v, s.nc, s.nalm, p->d_mofidx, p->d_part, 0, 1);
+    p->prof.launches += 1;
+    SHTG_CHECK_LAUNCH("k_dot");
+    std::vector<double> h((size_t)s.nb * RB);
+    SHTG_CUDA(cudaMemcpyAsync(h.data(), p->d_part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s.st));
+    SHTG_CUDA(cudaStreamSynchronize(s.st));
+    out.assign(s.nb, 0.0);
+    for (int b = 0; b < s.nb; ++b)
+        for (int k = 0; k < RB; ++k) out[b] += h[(size_t)b * RB + k];
+    return SHTG_OK;
+}
+
+static double now_ms() {
+    return std::chrono::duration<double, std::milli>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+// Per-l tables from host C_l and b_l.  Returns SHTG_ERR_NOT_SPD for an
+// indefinite block.
+static int build_ltab(Plan *p, int nc, const double *cl, const double *bl) {
+    const int L1 = p->lmax + 1;
+    std::vector<double> t64(9 * (size_t)L1, 0.0);
+    std::vector<float> t32(5 * (size_t)L1, 0.f);
+    for (int l = 0; l < L1; ++l) {
+        double tt, te = 0, ee = 1, bb = 1;
+        bool active;
+        double s[4] = {1, 0, 1, 1}, h[4] = {0, 0, 0, 0};
+        if (nc == 1) {
+            tt = cl[l];
+            if (!(tt >= 0.0)) {
+                set_error("C_l < 0 at l = " + std::to_string(l));
+                return SHTG_ERR_NOT_SPD;
+            }
+            active = tt > 0.0;
+            if (active) {
+                s[0] = 1.0 / tt;
+                h[0] = 1.0 / sqrt(tt);
+            }
+        } else {
+            tt = cl[l];
+            ee = cl[L1 + l];
+            bb = cl[2 * L1 + l];
+            te = cl[3 * L1 + l];
+            const double det = tt * ee - te * te;
+            if (!(tt >= 0 && ee >= 0 && bb >= 0 && det >= -1e-300)) {
+                set_error("C_l block not positive semi-definite at l = " + std::to_string(l));
+                return SHTG_ERR_NOT_SPD;
+            }
+            active = tt > 0 && bb > 0 && det > 0;
+            if (active) {
+                s[0] = ee / det;
+                s[1] = -te / det;
+                s[2] = tt / det;
+                s[3] = 1.0 / bb;
+                // inverse of the symmetric square root of [[tt, te], [te, ee]]:
+                // sqrt(M) = (M + sqrt(det) I) / sqrt(tr + 2 sqrt(det))
+                const double sd = sqrt(det), tq = sqrt(tt + ee + 2.0 * sd);
+                const double r11 = (tt + sd) / tq, r12 = te / tq, r22 = (ee + sd) / tq;
+                const double rd = r11 * r22 - r12 * r12;
+                h[0] = r22 / rd;
+                h[1] = -r12 / rd;
+                h[2] = r11 / rd;
+                h[3] = 1.0 / sqrt(bb);
+            }
+        }
+        const double beam = active ? bl[l] : 0.0;
+        t64[l] = beam;
+        for (int k = 0; k < 4; ++k) {
+            t64[(1 + k) * (size_t)L1 + l] = s[k];
+            t64[(5 + k) * (size_t)L1 + l] = h[k];
+            t32[(1 + k) * (size_t)L1 + l] = (float)s[k];
+        }
+        t32[l] = (float)beam;
+    }
+    SHTG_CUDA(cudaMemcpy(p->d_ltab64, t64.data(), sizeof(double) * t64.size(), cudaMemcpyHostToDevice));
+    SHTG_CUDA(cudaMemcpy(p->d_ltab32, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice));
+    return SHTG_OK;
+}
+
+// Copy N^-1 into the plan (FP64 + FP32 copies), build the preconditioner.
+static int setup_operator(Plan *p, const shtg_problem *pr, int host_inputs, int precond,
+                          cudaStream_t st) {
+    const int nc = pr->ncomp;
+    SHTG_TRY(build_ltab(p, nc, pr->cl, pr->bl));
+    const int ncomp_ninv = nc == 3 ? 2 : 1;
+    const size_t nb = sizeof(double) * (size_t)p->npix * ncomp_ninv;
+    SHTG_CUDA(cudaMemcpyAsync(p->d_ninv64, pr->ninv, nb,
+                              host_inputs ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+    k_to_float<<<grid_1d(p->npix * ncomp_ninv), RT, 0, st>>>(p->d_ninv64, p->d_ninv32,
+                                                           p->npix * ncomp_ninv);
+    p->prof.launches += 1;
+    SHTG_CHECK_LAUNCH("k_to_float");
+    if (precond) {
+        k_wpair<<<p->npairs, RT, 0, st>>>(p->d_ninv64, p->d_ofs, p->d_nphi, p->nring, p->d_wpairT);
+        p->prof.launches += 1;
+        SHTG_CHECK_LAUNCH("k_wpair");
+        SHTG_TRY(leg_diag(p, 0, p->d_wpairT, p->d_diagT, st));
+        if (nc == 3) {
+            k_wpair<<<p->npairs, RT, 0, st>>>(p->d_ninv64 + p->npix, p->d_ofs, p->d_nphi, p->nring,
+                                              p->d_wpairP);
+            p->prof.launches += 1;
+            SHTG_CHECK_LAUNCH("k_wpair");
+            SHTG_TRY(leg_diag(p, 2, p->d_wpairP, p->d_diagP, st));
+        }
+    }
+    k_precond<<<grid_1d(p->nalm), RT, 0, st>>>(p->d_diagT, nc == 3 ? p->d_diagP : p->d_diagT,
+                                               p->d_ltab64, nc, p->nalm, p->lmax + 1, p->d_lofidx,
+                                               precond, p->d_minv64, p->d_minv32);
+    p->prof.launches += 1;
+    SHTG_CHECK_LAUNCH("k_precond");
+    return SHTG_OK;
+}
+
+static int check_problem(Plan *p, const shtg_problem *pr) {
+    if (!pr || !pr->cl || !pr->bl || !pr->ninv) {
+        set_error("problem, cl, bl and ninv are required");
+        return SHTG_ERR_ARG;
+    }
+    if (pr->ncomp != 1 && pr->ncomp != 3) {
+        set_error("ncomp must be 1 or 3");
+        return SHTG_ERR_ARG;
+    }
+    if (pr->ncomp == 3 && !(p->flags & SHTG_SPIN2)) {
+        set_error("ncomp = 3 needs a plan created with SHTG_SPIN2");
+        return SHTG_ERR_ARG;
+    }
+    if (pr->nbatch < 1 || pr->nbatch > p->max_batch) {
+        set_error("nbatch must be in [1, max_batch]");
+        return SHTG_ERR_ARG;
+    }
+    return SHTG_OK;
+}
+
+static Solve make_solve(Plan *p, int nb, int nc, cudaStream_t st) {
+    Solve s;
+    s.p = p;
+    s.st = st;
+    s.nb = nb;
+    s.nc = nc;
+    s.nalm = p->nalm;
+    s.per = (int64_t)nc * p->nalm;
+    s.nvec = (int64_t)nb * s.per;
+    s.vgrid = dim3(grid_1d(s.per).x, nb);
+    s.rgrid = dim3(RB, nb);
+    return s;
+}
+
+int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_opts *o,
+              shtg_cg_stats *stats, cudaStream_t st) {
+    SHTG_TRY(check_problem(p, pr));
+    shtg_cg_opts opt;
+    if (o) {
+        opt = *o;
+    } else {
+        memset(&opt, 0, sizeof(opt));
+        opt.tol = 1e-6;
+        opt.maxiter = 1000;
+        opt.mode = SHTG_CG_MIXED;
+        opt.precond = 1;
+    }
+    if (!(opt.tol > 0)) opt.tol = 1e-6;
+    if (opt.maxiter <= 0) opt.maxiter = 1000;
+    if (!(opt.inner_tol > 0)) opt.inner_tol = 1e-3;
+    if (opt.inner_maxiter <= 0) opt.inner_maxiter = 200;
+    if (opt.check_every <= 0) opt.check_every = 4;
+    const int host = (opt.flags & SHTG_HOST_INPUTS) ? 1 : 0;
+    if (!pr->d || !pr->w1 || !pr->w2 || !alm_out) {
+        set_error("d, w1, w2 and alm_out are required");
+        return SHTG_ERR_ARG;
+    }
+    shtg_cg_stats stt;
+    memset(&stt, 0, sizeof(stt));
+    p->prof.on = (opt.flags & SHTG_PROFILE) != 0;
+    p->prof.n = 0;
+    p->prof.open_cls = -1;
+    const long long launches0 = p->prof.launches;
+    const double t0 = now_ms();
+    const int nb = pr->nbatch, nc = pr->ncomp;
+    Solve s = make_solve(p, nb, nc, st);
+    SHTG_TRY(setup_operator(p, pr, host, opt.precond, st));
+    double2 *B = p->v64[0], *X = p->v64[1], *R = p->v64[2], *Tt = p->v64[6];
+    // ---- RHS: B Y^T (N^-1 d + N^-1/2 w2) + S^-1/2 w1 in FP64
+    const int64_t npix = p->npix;
+    const size_t mapbytes = sizeof(double) * (size_t)nb * nc * npix;
+    const dim3 pgrid(grid_1d(npix).x, nb * nc);
+    if (host) {
+        SHTG_CUDA(cudaMemcpyAsync(p->d_stage, pr->d, mapbytes, cudaMemcpyHostToDevice, st));
+        k_rhs_pix<<<pgrid, RT, 0, st>>>(p->d_stage, nullptr, p->d_ninv64, nb, nc, npix, 0, p->d_map64);
+        SHTG_CUDA(cudaMemcpyAsync(p->d_stage, pr->w2, mapbytes, cudaMemcpyHostToDevice, st));
+        k_rhs_pix<<<pgrid, RT, 0, st>>>(nullptr, p->d_stage, p->d_ninv64, nb, nc, npix, 1, p->d_map64);
+        p->prof.launches += 2;
+    } else {
+        k_rhs_pix<<<pgrid, RT, 0, st>>>(pr->d, pr->w2, p->d_ninv64, nb, nc, npix, 0, p->d_map64);
+        p->prof.launches += 1;
+    }
+    SHTG_CHECK_LAUNCH("k_rhs_pix");
+    {
+        const int64_t rowsz = (int64_t)(p->lmax + 1) * p->nring;
+        SHTG_TRY(ring_analysis<double>(p, p->d_map64, nb * nc, 0, p->d_phase64, st));
+        SHTG_TRY(leg_analysis<double>(p, 0, p->d_phase64, nb, p->d_ltab64, B, nc, st));
+        if (nc == 3)
+            SHTG_TRY(leg_analysis<double>(p, 2, p->d_phase64 + nb * rowsz, nb, p->d_ltab64, B + p->nalm, 3, st));
+        const double2 *w1 = reinterpret_cast<const double2 *>(pr->w1);
+        if (host) {
+            SHTG_CUDA(cudaMemcpyAsync(Tt, pr->w1, sizeof(double2) * (size_t)s.nvec, cudaMemcpyHostToDevice, st));
+            w1 = Tt;
+        }
+        k_rhs_alm<<<s.vgrid, RT, 0, st>>>(w1, B, nc, p->nalm, p->lmax + 1, p->d_lofidx, p->d_mofidx,
+                                         p->d_ltab64 + 5 * (p->lmax + 1));
+        p->prof.launches += 1;
+        SHTG_CHECK_LAUNCH("k_rhs_alm");
+    }
+    std::vector<double> bb;
+    SHTG_TRY(norms2(s, B, bb));
+    const double t1 = now_ms();
+    stt.ms_setup = 0;
+    stt.ms_rhs = t1 - t0;
+    int rc = SHTG_OK;
+    std::vector<double> rr;
+    if (opt.mode == SHTG_CG_FP64) {
+        int iters = 0, conv = 0;
+        rc = pcg<double>(s, B, X, opt.tol, opt.maxiter, opt.check_every, &iters, &conv);
+        stt.iterations = iters;
+        if (rc != SHTG_OK) return rc;
+        SHTG_TRY(matvec<double>(s, X, Tt));
+        stt.fp64_matvecs = 1;
+        k_resid<<<grid_1d(s.nvec), RT, 0, st>>>(B, Tt, R, s.nvec);
+        p->prof.launches += 1;
+        SHTG_TRY(norms2(s, R, rr));
+    } else {
+        // FP64 iterative refinement around FP32 PCG
+        SHTG_CUDA(cudaMemsetAsync(X, 0, sizeof(double2) * (size_t)s.nvec, st));
+        SHTG_CUDA(cudaMemcpyAsync(R, B, sizeof(double2) * (size_t)s.nvec, cudaMemcpyDeviceToDevice, st));
+        rr = bb;
+        double *d_sc = p->d_part + 4 * (int64_t)p->max_batch * SHTG_RED_BLOCKS;  // 2 nb doubles
+        int total_inner = 0;
+        for (int outer = 0;; ++outer) {
+            bool done = true;
+            std::vector<double> sc(2 * nb);
+            for (int b = 0; b < nb; ++b) {
+                const bool conv = bb[b] == 0.0 || rr[b] <= opt.tol * opt.tol * bb[b];
+                if (!conv) done = false;
+                const double nr = sqrt(rr[b]);
+                sc[b] = (conv || nr == 0.0) ? 0.0 : 1.0 / nr;      // inverse scale
+                sc[nb + b] = (conv || nr == 0.0) ? 0.0 : nr;       // scale
+            }
+            if (done || total_inner >= opt.maxiter) break;
+            SHTG_CUDA(cudaMemcpyAsync(d_sc, sc.data(), sizeof(double) * 2 * nb, cudaMemcpyHostToDevice, st));
+            // right-hand side of the FP32 solve: r / ||r|| per realization, held in
+            // the idle FP64 scratch vector (pcg<float> owns v32[0..3]; v32[4] = delta)
+            float2 *rhs32 = reinterpret_cast<float2 *>(Tt);
+            k_scale_down<<<s.vgrid, RT, 0, st>>>(R, rhs32, s.per, d_sc);
+            p->prof.launches += 1;
+            SHTG_CHECK_LAUNCH("k_scale_down");
+            int iters = 0, conv = 0;
+            rc = pcg<float>(s, rhs32, p->v32[4], opt.inner_tol,
+                            std::min(opt.inner_maxiter, opt.maxiter - total_inner), opt.check_every,
+                            &iters, &conv);
+            total_inner += iters;
+            if (rc != SHTG_OK) return rc;
+            k_correct<<<s.vgrid, RT, 0, st>>>(X, p->v32[4], s.per, d_sc + nb);
+            p->prof.launches += 1;
+            SHTG_CHECK_LAUNCH("k_correct");
+            SHTG_TRY(matvec<double>(s, X, Tt));
+            stt.fp64_matvecs++;
+            k_resid<<<grid_1d(s.nvec), RT, 0, st>>>(B, Tt, R, s.nvec);
+            p->prof.launches += 1;
+            SHTG_TRY(norms2(s, R, rr));
+            stt.outer_steps++;
+        }
+        stt.iterations = total_inner;
+    }
+    double worst = 0.0;
+    int conv_all = 1;
+    for (int b = 0; b < nb; ++b) {
+        const double rel = bb[b] > 0 ? sqrt(rr[b] / bb[b]) : 0.0;
+        worst = std::max(worst, rel);
+        if (rel > opt.tol) conv_all = 0;
+    }
+    stt.rel_residual = worst;
+    stt.converged = conv_all;
+    SHTG_CUDA(cudaMemcpyAsync(alm_out, X, sizeof(double2) * (size_t)s.nvec,
+                              host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    SHTG_CUDA(cudaStreamSynchronize(st));
+    const double t2 = now_ms();
+    stt.ms_solve = t2 - t1;
+    stt.ms_total = t2 - t0;
+    prof_collect(p, stt.kernel_ms, stt.kernel_launches);
+    p->prof.on = false;
+    stt.launches = p->prof.launches - launches0;
+    if (stats) *stats = stt;
+    if (!conv_all) {
+        set_error("maximum iterations reached before the tolerance");
+        return SHTG_ERR_NOT_CONVERGED;
+    }
+    return SHTG_OK;
+}
+
+}  // namespace shtg
+
+namespace shtg {
+
+int apply_operator(Plan *p, const shtg_problem *pr, const double *x, double *y, cudaStream_t st) {
+    SHTG_TRY(check_problem(p, pr));
+    SHTG_TRY(setup_operator(p, pr, 0, 0, st));
+    Solve s = make_solve(p, pr->nbatch, pr->ncomp, st);
+    return matvec<double>(s, reinterpret_cast<const double2 *>(x), reinterpret_cast<double2 *>(y));
+}
+
+int logpost_grad(Plan *p, const double *cl, const double *bl, const float *alm, const float *d,
+                 const float *ninv, int nbins, const int *blo, const int *bhi, int flags,
+                 double *logp, float *grad, double *gcl, cudaStream_t st) {
+    const int L1 = p->lmax + 1;
+    SHTG_TRY(build_ltab(p, 1, cl, bl));
+    // row 2 of the FP32 per-l table (unused by temperature problems) holds 1 / C_l, 0 where held
+    std::vector<float> icl(L1);
+    for (int l = 0; l < L1; ++l) icl[l] = cl[l] > 0 ? (float)(1.0 / cl[l]) : 0.f;
+    float *d_icl = p->d_ltab32 + 2 * L1;
+    SHTG_CUDA(cudaMemcpyAsync(d_icl, icl.data(), sizeof(float) * L1, cudaMemcpyHostToDevice, st));
+    const float *beam = p->d_ltab32;
+    const float2 *a = reinterpret_cast<const float2 *>(alm);
+    SHTG_TRY(leg_synth<float>(p, 0, a, 1, 1, beam, p->d_phase32, st));
+    SHTG_TRY(ring_synth<float>(p, p->d_phase32, 1, p->d_map32, st));
+    k_resid_pix<<<RB, RT, 0, st>>>(d, ninv, p->d_map32, p->npix, p->d_part);
+    SHTG_CHECK_LAUNCH("k_resid_pix");
+    if (grad) {
+        float2 *g = reinterpret_cast<float2 *>(grad);
+        SHTG_TRY(ring_analysis<float>(p, p->d_map32, 1, 0, p->d_phase32, st));
+        SHTG_TRY(leg_analysis<float>(p, 0, p->d_phase32, 1, beam, g, 1, st));
+        k_grad_prior<<<grid_1d(p->nalm), RT, 0, st>>>(a, g, p->nalm, p->d_lofidx, p->d_mofidx, d_icl,
+                                                     (flags & SHTG_GRAD_COMPONENTS) ? 1 : 0);
+        SHTG_CHECK_LAUNCH("k_grad_prior");
+    }
+    SHTG_CUDA(cudaMemsetAsync(p->d_lsum, 0, sizeof(double) * L1, st));
+    k_prior_lsum<<<grid_1d(p->nalm), RT, 0, st>>>(a, p->nalm, p->d_lofidx, p->d_mofidx, d_icl, p->d_lsum);
+    SHTG_CHECK_LAUNCH("k_prior_lsum");
+    std::vector<double> part(RB), ls(L1);
+    SHTG_CUDA(cudaMemcpyAsync(part.data(), p->d_part, sizeof(double) * RB, cudaMemcpyDeviceToHost, st));
+    SHTG_CUDA(cudaMemcpyAsync(ls.data(), p->d_lsum, sizeof(double) * L1, cudaMemcpyDeviceToHost, st));
+    SHTG_CUDA(cudaStreamSynchronize(st));
+    double chi2 = 0.0, prior = 0.0;
+    for (double v : part) chi2 += v;
+    for (double v : ls) prior += v;
+    if (logp) *logp = -0.5 * chi2 - 0.5 * prior;
+    if (gcl)
+        for (int k = 0; k < nbins; ++k) {
+            double s = 0.0;
+            for (int l = std::max(0, blo[k]); l <= std::min(p->lmax, bhi[k]); ++l) s += ls[l];
+            gcl[k] = 0.5 * s;
+        }
+    return SHTG_OK;
+}
+
+}  // namespace shtg

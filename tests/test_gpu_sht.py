@@ -1,0 +1,178 @@
+"""GPU parity of the transforms against the FP64 oracle, through the C ABI.
+
+Tolerances (relative L2): FP64 <= 1e-10, FP32 <= 1e-5.  Sizes span several
+CTAs along the ring-pair axis with a ragged tail, both geometries (HEALPix
+with power-of-two and Bluestein rings; Gauss-Legendre), spin 0 and spin 2.
+"""
+import numpy as np
+import pytest
+
+from oracle import sht as osht
+from tests._util import rand_alm, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-10, "fp32": 1e-5}
+CASES = [("healpix", 16, 40), ("healpix", 32, 64), ("healpix", 300, 400), ("gl", 33, 32),
+         ("gl", 129, 128)]
+
+
+def _plan_geom(kind, n, L, spin2=True, max_batch=2):
+    from paper_2306_15511_gb300 import Plan
+    if kind == "healpix":
+        return Plan(nside=n, lmax=L, max_batch=max_batch, spin2=spin2), osht.healpix(n)
+    nphi = 2 * L + 2
+    return Plan(gauss=(n, nphi), lmax=L, max_batch=max_batch, spin2=spin2), osht.gauss_legendre(n, nphi)
+
+
+def _dt(prec):
+    return (torch.complex128, torch.float64) if prec == "fp64" else (torch.complex64, torch.float32)
+
+
+@pytest.mark.parametrize("kind,n,L", CASES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_alm2map_spin0(kind, n, L, prec):
+    plan, g = _plan_geom(kind, n, L)
+    rng = np.random.default_rng(n + L)
+    a = rand_alm(L, rng, (2,))
+    ct, _ = _dt(prec)
+    m = plan.alm2map(torch.tensor(a, dtype=ct, device="cuda")).cpu().numpy()
+    for b in range(2):
+        ref = osht.alm2map(g, L, a[b])
+        assert rel_l2(m[b], ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("kind,n,L", CASES)
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_adjoint_spin0(kind, n, L, prec):
+    plan, g = _plan_geom(kind, n, L)
+    rng = np.random.default_rng(7 * n + L)
+    mp = rng.normal(size=(2, g.npix))
+    _, rt = _dt(prec)
+    a = plan.alm2map_adjoint(torch.tensor(mp, dtype=rt, device="cuda")).cpu().numpy()
+    for b in range(2):
+        ref = osht.alm2map_adjoint(g, L, mp[b])
+        assert rel_l2(a[b], ref) < TOL[prec]
+
+
+@pytest.mark.parametrize("kind,n,L", CASES[:4])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_spin2_both_directions(kind, n, L, prec):
+    plan, g = _plan_geom(kind, n, L)
+    rng = np.random.default_rng(3 * n + L)
+    eb = rand_alm(L, rng, (1, 2))
+    ct, rt = _dt(prec)
+    qu = plan.alm2map(torch.tensor(eb, dtype=ct, device="cuda"), spin=2).cpu().numpy()
+    Q, U = osht.alm2map_spin2(g, L, eb[0, 0], eb[0, 1])
+    assert rel_l2(qu[0], np.stack([Q, U])) < TOL[prec]
+    mp = rng.normal(size=(1, 2, g.npix))
+    ad = plan.alm2map_adjoint(torch.tensor(mp, dtype=rt, device="cuda"), spin=2).cpu().numpy()
+    E, B = osht.alm2map_spin2_adjoint(g, L, mp[0, 0], mp[0, 1])
+    assert rel_l2(ad[0], np.stack([E, B])) < TOL[prec]
+
+
+def test_gl_round_trip_exact():
+    L = 96
+    plan, g = _plan_geom("gl", L + 1, L)
+    rng = np.random.default_rng(1)
+    a = rand_alm(L, rng, (1,))
+    at = torch.tensor(a, dtype=torch.complex128, device="cuda")
+    back = plan.map2alm(plan.alm2map(at)).cpu().numpy()
+    assert rel_l2(back, a) < 1e-11
+    ls = np.concatenate([np.arange(m, L + 1) for m in range(L + 1)])
+    eb = rand_alm(L, rng, (1, 2))
+    eb[..., ls < 2] = 0
+    et = torch.tensor(eb, dtype=torch.complex128, device="cuda")
+    back2 = plan.map2alm(plan.alm2map(et, spin=2), spin=2).cpu().numpy()
+    assert rel_l2(back2, eb) < 1e-11
+
+
+def test_map2alm_jacobi_healpix():
+    """Jacobi iterations reduce the HEALPix quadrature error monotonically."""
+    nside, L = 32, 64
+    plan, g = _plan_geom("healpix", nside, L)
+    rng = np.random.default_rng(2)
+    a = rand_alm(L, rng, (1,))
+    m = plan.alm2map(torch.tensor(a, dtype=torch.complex128, device="cuda"))
+    errs = [rel_l2(plan.map2alm(m, niter=k).cpu().numpy(), a) for k in (0, 1, 3)]
+    assert errs[1] < errs[0] and errs[2] < errs[1]
+    ref = osht.map2alm(g, L, m.cpu().numpy()[0], niter=1)
+    assert rel_l2(plan.map2alm(m, niter=1).cpu().numpy()[0], ref) < 1e-10
+
+
+def test_vjp_is_component_gradient():
+    """alm2map_vjp = gradient of <g, Y a> w.r.t. (Re a, Im a): checked by
+    directional derivatives on the oracle map."""
+    nside, L = 16, 32
+    plan, g = _plan_geom("healpix", nside, L)
+    rng = np.random.default_rng(4)
+    gm = rng.normal(size=(1, g.npix))
+    v = plan.alm2map_vjp(torch.tensor(gm, device="cuda")).cpu().numpy()[0]
+    for i in rng.choice((L + 1) * (L + 2) // 2, 6, replace=False):
+        for unit in (1.0, 1j):
+            e = np.zeros((L + 1) * (L + 2) // 2, complex)
+            e[i] = unit
+            dd = gm[0] @ osht.alm2map(g, L, e)
+            an = v[i].real if unit == 1.0 else v[i].imag
+            assert abs(dd - an) < 1e-10 * max(1.0, abs(dd))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fullsize_nside1024_sampled_rings(prec):
+    """N_side = 1024, l_max = 2048 (the benchmark geometry): GPU maps on
+    sampled rings (polar, Bluestein, equatorial) and GPU alm at sampled m
+    against the oracle computed for those rings / m only."""
+    nside, L = 1024, 2048
+    plan, g = _plan_geom("healpix", nside, L, spin2=True, max_batch=1)
+    rng = np.random.default_rng(11)
+    lsc = np.ones(L + 1)
+    lsc[1:] = 1.0 / np.sqrt(np.arange(1, L + 1))
+    a = rand_alm(L, rng, (1,), lsc)
+    ct, rt = _dt(prec)
+    m = plan.alm2map(torch.tensor(a, dtype=ct, device="cuda")).cpu().numpy()[0]
+    rings = [0, 1, 2, 100, 1022, 1023, 1500, 2046, 2047, 3000, 4093, 4094]
+    sub = g.subset(rings)
+    ref = osht.alm2map(sub, L, a[0])
+    got = np.concatenate([m[g.ofs[r]:g.ofs[r] + g.nphi[r]] for r in rings])
+    assert rel_l2(got, ref) < TOL[prec]
+    mp = rng.normal(size=(1, g.npix))
+    ad = plan.alm2map_adjoint(torch.tensor(mp, dtype=rt, device="cuda")).cpu().numpy()[0]
+    mlist = [0, 1, 2, 700, 1500, 2047, 2048]
+    refa = osht.alm2map_adjoint(g, L, mp[0], mlist=mlist)
+    ms = osht.ms_of(L)
+    sel = np.isin(ms, mlist)
+    assert rel_l2(ad[sel], refa[sel]) < TOL[prec]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_fullsize_nside1024_spin2_sampled(prec):
+    nside, L = 1024, 2048
+    plan, g = _plan_geom("healpix", nside, L, spin2=True, max_batch=1)
+    rng = np.random.default_rng(12)
+    lsc = np.ones(L + 1)
+    lsc[1:] = 1.0 / np.sqrt(np.arange(1, L + 1))
+    eb = rand_alm(L, rng, (1, 2), lsc)
+    ct, rt = _dt(prec)
+    qu = plan.alm2map(torch.tensor(eb, dtype=ct, device="cuda"), spin=2).cpu().numpy()[0]
+    rings = [0, 1, 5, 1023, 2047, 4094]
+    sub = g.subset(rings)
+    Q, U = osht.alm2map_spin2(sub, L, eb[0, 0], eb[0, 1])
+    got = np.stack([np.concatenate([qu[c][g.ofs[r]:g.ofs[r] + g.nphi[r]] for r in rings])
+                    for c in range(2)])
+    assert rel_l2(got, np.stack([Q, U])) < TOL[prec]
+    mp = rng.normal(size=(1, 2, g.npix))
+    ad = plan.alm2map_adjoint(torch.tensor(mp, dtype=rt, device="cuda"), spin=2).cpu().numpy()[0]
+    mlist = [0, 1, 2, 1000, 2048]
+    E, B = osht.alm2map_spin2_adjoint(g, L, mp[0, 0], mp[0, 1], mlist=mlist)
+    sel = np.isin(osht.ms_of(L), mlist)
+    assert rel_l2(ad[:, sel], np.stack([E[sel], B[sel]])) < TOL[prec]
+
+
+def test_invalid_arguments_raise():
+    from paper_2306_15511_gb300 import Plan, _native
+    plan = Plan(nside=8, lmax=16)
+    with pytest.raises(_native.ShtgError):
+        plan.alm2map(torch.zeros(1, 3, plan.nalm, dtype=torch.complex128, device="cuda"))
+    with pytest.raises(_native.ShtgError):   # spin 2 on a temperature-only plan
+        plan.alm2map(torch.zeros(1, 2, plan.nalm, dtype=torch.complex128, device="cuda"), spin=2)

@@ -1,0 +1,170 @@
+"""GPU constrained-realization solver against the FP64 oracle (through the
+C ABI).  Gates: the oracle-evaluated residual ||b - A x|| / ||b|| of the GPU
+solution is <= 1.05 tol, and the relative L2 distance to the oracle's
+tightly converged solution is reported and bounded."""
+import numpy as np
+import pytest
+
+from inputs import configs as C
+from oracle import sht as osht
+from oracle import solver as osol
+from tests._util import rand_alm, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _data(p, g):
+    """d = Y B a + n with the oracle's Y (inputs never come from the GPU)."""
+    L = p.lmax
+    ls = osht.ls_of(L)
+    if p.ncomp == 1:
+        return (osht.alm2map(g, L, p.signal_alm[0] * p.bl[ls]) + p.noise_map[0])[None]
+    T = osht.alm2map(g, L, p.signal_alm[0] * p.bl[ls])
+    Q, U = osht.alm2map_spin2(g, L, p.signal_alm[1] * p.bl[ls], p.signal_alm[2] * p.bl[ls])
+    return np.stack([T, Q, U]) + p.noise_map
+
+
+def _cuda(x, dt=None):
+    return torch.tensor(np.ascontiguousarray(x), dtype=dt, device="cuda")
+
+
+def _solve_gpu(plan, p, d, mode, tol, **kw):
+    ninv = p.ninv if p.ninv.ndim == 1 else p.ninv
+    x, st = plan.cg_sample(p.cl, p.bl, _cuda(ninv, torch.float64), _cuda(d[None], torch.float64),
+                           _cuda(p.w1[None], torch.complex128), _cuda(p.w2[None], torch.float64),
+                           tol=tol, mode=mode, **kw)
+    return x.cpu().numpy()[0], st
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_c0_solution(mode):
+    """Config 0 (N_side 32, l_max 64, full sky): PCG to 1e-8."""
+    from paper_2306_15511_gb300 import Plan
+    p = C.config(0)
+    g = osht.healpix(p.nside)
+    d = _data(p, g)
+    prob = osol.Problem(g, p.lmax, p.cl, p.bl, p.ninv)
+    b = prob.rhs(d, p.w1, p.w2)
+    xref, _, _ = osol.pcg(prob, b, 1e-12, 1000)
+    plan = Plan(nside=p.nside, lmax=p.lmax)
+    x, st = _solve_gpu(plan, p, d, mode, p.tol)
+    assert st["converged"] == 1
+    res = osol.true_residual(prob, x, b)
+    assert res <= 1.05 * p.tol, (res, st)
+    assert rel_l2(x, xref[0]) < 1e-6
+
+
+def test_operator_and_rhs_parity():
+    """apply_operator (FP64) against the oracle matvec on a masked problem."""
+    from paper_2306_15511_gb300 import Plan
+    p = C.config(1, nside=64, lmax=128)
+    g = osht.healpix(64)
+    prob = osol.Problem(g, 128, p.cl, p.bl, p.ninv)
+    rng = np.random.default_rng(0)
+    x = rand_alm(128, rng, (1, 1))
+    plan = Plan(nside=64, lmax=128)
+    y = plan.apply_operator(p.cl, p.bl, _cuda(p.ninv, torch.float64), _cuda(x, torch.complex128))
+    ref = prob.matvec(x[0])
+    assert rel_l2(y.cpu().numpy()[0], ref) < 1e-10
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_masked_c1_recipe_reduced(mode):
+    """Config 1 recipe (hits-weighted noise, |b| < 20 deg + 50 holes) at
+    N_side 128, l_max 256: residual gate through the oracle."""
+    from paper_2306_15511_gb300 import Plan
+    p = C.config(1, nside=128, lmax=256)
+    g = osht.healpix(128)
+    d = _data(p, g)
+    prob = osol.Problem(g, p.lmax, p.cl, p.bl, p.ninv)
+    b = prob.rhs(d, p.w1, p.w2)
+    plan = Plan(nside=128, lmax=256)
+    x, st = _solve_gpu(plan, p, d, mode, 1e-6, maxiter=3000)
+    assert st["converged"] == 1
+    res = osol.true_residual(prob, x, b)
+    assert res <= 1.05e-6, (res, st)
+
+
+def test_teb_mixed_small():
+    """T+E+B (config 4 recipe at N_side 16, l_max 32), mixed precision."""
+    from paper_2306_15511_gb300 import Plan
+    p = C.config(4, nside=16, lmax=32, batch=2)
+    g = osht.healpix(16)
+    plan = Plan(nside=16, lmax=32, max_batch=2, spin2=True)
+    ds = np.stack([_data(q, g) for q in p])
+    w1 = np.stack([q.w1 for q in p])
+    w2 = np.stack([q.w2 for q in p])
+    x, st = plan.cg_sample(p[0].cl, p[0].bl, _cuda(p[0].ninv, torch.float64), _cuda(ds, torch.float64),
+                           _cuda(w1, torch.complex128), _cuda(w2, torch.float64), tol=1e-6,
+                           mode="mixed", maxiter=3000)
+    assert st["converged"] == 1
+    xh = x.cpu().numpy()
+    prob = osol.Problem(g, 32, p[0].cl, p[0].bl, p[0].ninv)
+    for k in range(2):
+        b = prob.rhs(ds[k], w1[k], w2[k])
+        res = osol.true_residual(prob, xh[k], b)
+        assert res <= 1.05e-6, (k, res, st)
+
+
+def test_host_inputs_match_device_inputs():
+    from paper_2306_15511_gb300 import Plan
+    p = C.config(0, nside=16, lmax=32)
+    g = osht.healpix(16)
+    d = _data(p, g)
+    plan = Plan(nside=16, lmax=32)
+    xd, _ = _solve_gpu(plan, p, d, "fp64", 1e-8)
+    xh, st = plan.cg_sample(p.cl, p.bl, np.ascontiguousarray(p.ninv), np.ascontiguousarray(d[None]),
+                            np.ascontiguousarray(p.w1[None]), np.ascontiguousarray(p.w2[None]),
+                            tol=1e-8, mode="fp64")
+    assert np.array_equal(xh.numpy()[0], xd)
+
+
+def test_logpost_gradient_vs_oracle():
+    """Config 3 recipe reduced to N_side 64, l_max 128: log-posterior and its
+    gradients (FP32 transforms) against the FP64 oracle."""
+    from paper_2306_15511_gb300 import Plan
+    p = C.config(3, nside=64, lmax=128)
+    g = osht.healpix(64)
+    L = p.lmax
+    d = _data(p, g)[0]
+    prob = osol.Problem(g, L, p.cl, p.bl, p.ninv)
+    a = p.signal_alm.copy()
+    a[:, osht.ls_of(L) < 2] = 0
+    bins = [(2 + 20 * k, 21 + 20 * k) for k in range(6)]
+    lp_ref = osol.log_posterior(prob, a, d)
+    ga_ref, gl_ref = osol.log_posterior_grad(prob, a, d, bins)
+    plan = Plan(nside=64, lmax=L)
+    lp, ga, gl = plan.logpost_grad(p.cl, p.bl, _cuda(a[0], torch.complex64), _cuda(d, torch.float32),
+                                   _cuda(p.ninv, torch.float32), bins)
+    assert abs(lp - lp_ref) < 1e-5 * abs(lp_ref)
+    assert rel_l2(ga.cpu().numpy(), ga_ref[0]) < 1e-4
+    assert rel_l2(gl, gl_ref) < 1e-5
+
+
+def test_autograd_alm2map_and_logposterior():
+    from paper_2306_15511_gb300 import Plan
+    from paper_2306_15511_gb300 import autograd as AG
+    plan = Plan(nside=16, lmax=32)
+    rng = np.random.default_rng(3)
+    a = _cuda(rand_alm(32, rng, (1,)), torch.complex128).requires_grad_(True)
+    w = _cuda(rng.normal(size=(1, plan.npix)), torch.float64)
+    loss = (AG.alm2map(plan, a) * w).sum()
+    loss.backward()
+    ref = plan.alm2map_vjp(w)
+    assert torch.allclose(a.grad, ref)
+    # log-posterior: autograd gradient w.r.t. theta equals the binned formula
+    p = C.config(3, nside=16, lmax=32)
+    g = osht.healpix(16)
+    d = _data(p, g)[0]
+    bins = [(2, 11), (12, 21), (22, 32)]
+    al = _cuda(p.signal_alm[0], torch.complex64).requires_grad_(True)
+    th = torch.zeros(3, dtype=torch.float64, device="cuda", requires_grad=True)
+    L = AG.log_posterior(plan, al, th, p.cl, p.bl, _cuda(d, torch.float32),
+                         _cuda(p.ninv, torch.float32), bins)
+    L.backward()
+    prob = osol.Problem(g, 32, p.cl, p.bl, p.ninv)
+    ga_ref, gl_ref = osol.log_posterior_grad(prob, p.signal_alm, d, bins)
+    assert rel_l2(th.grad.cpu().numpy(), gl_ref) < 1e-5
+    w_m = np.where(osht.ms_of(32) == 0, 1.0, 2.0)
+    assert rel_l2(al.grad.cpu().numpy(), w_m * ga_ref[0]) < 1e-4
