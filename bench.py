@@ -238,8 +238,8 @@ def run_gpu(args):
 
     plan = Plan(nside=NSIDE, lmax=LMAX, max_batch=NB, spin2=True)
     inp = make_inputs(plan, dev, seed_shift=rank)
-    kw = dict(tol=1e-6, mode="mixed", maxiter=args.maxiter, inner_tol=args.inner_tol,
-              inner_maxiter=args.inner_maxiter, check_every=args.check_every)
+    kw = dict(tol=1e-6, mode="mixed", maxiter=args.maxiter, reliable_delta=args.reliable_delta,
+              check_every=args.check_every)
     out = torch.empty(NB, 3, plan.nalm, dtype=torch.complex128, device=dev)
 
     def step(profile=False):
@@ -404,8 +404,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="shtg", choices=["shtg", "reference"])
     ap.add_argument("--maxiter", type=int, default=3000)
-    ap.add_argument("--inner-tol", type=float, default=1e-3)
-    ap.add_argument("--inner-maxiter", type=int, default=400)
+    ap.add_argument("--reliable-delta", type=float, default=1e-2)
     ap.add_argument("--check-every", type=int, default=8)
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--no-e2e", action="store_true")

@@ -144,18 +144,19 @@ typedef struct {
 
 typedef struct {
     double tol;         /* stop when ||b - A x|| / ||b|| <= tol for every realization */
-    int maxiter;        /* PCG iterations (FP64 mode) or total inner iterations (mixed) */
+    int maxiter;        /* PCG iterations (FP64 mode) or FP32 iterations (mixed) */
     int mode;           /* SHTG_CG_FP64 or SHTG_CG_MIXED */
     int precond;        /* 1: diagonal preconditioner of Sect. 4 (default); 0: none */
-    double inner_tol;   /* mixed mode: relative tolerance of each FP32 inner solve */
-    int inner_maxiter;  /* mixed mode: iterations per inner solve */
+    double reliable_delta; /* mixed mode: an FP64 residual replacement happens when the FP32
+                              residual has dropped by this factor since the last one (default 1e-2) */
+    int reserved;       /* set to 0 */
     int check_every;    /* iterations per CUDA graph launch between host convergence checks */
     int flags;          /* SHTG_HOST_INPUTS: ninv, d, w1, w2 and alm_out are host memory */
 } shtg_cg_opts;
 
 typedef struct {
-    int iterations;     /* PCG iterations (mixed: FP32 inner iterations) */
-    int outer_steps;    /* mixed mode: FP64 refinement steps */
+    int iterations;     /* PCG iterations (mixed: FP32 iterations) */
+    int outer_steps;    /* mixed mode: FP64 residual replacements */
     int fp64_matvecs;   /* FP64 operator applications, RHS excluded */
     int converged;      /* 1 if every realization met tol */
     double rel_residual;/* max over the batch of the FP64 ||b - A x|| / ||b|| at exit */
@@ -173,7 +174,11 @@ typedef struct {
  * (Sect. 2.2.1): RHS b = B Y^T (N^-1 d + N^-1/2 w2) + S^-1/2 w1 with S^-1/2
  * the inverse symmetric square root of the C_l block; PCG with the
  * diagonal preconditioner M = S^-1 + b_l^2 D_lm, D_lm = sum_r g_lm(theta_r)
- * sum_{p in r} N^-1_p (g = lambda^2, or the spin-2 analogue).  alm_out:
+ * sum_{p in r} N^-1_p (g = lambda^2, or the spin-2 analogue).  Mixed mode
+ * runs the PCG on FP32 vectors and transforms and replaces its residual by
+ * the FP64 b - A x (FP64 transforms) each time it has dropped by
+ * reliable_delta, keeping the search direction; x accumulates in FP64 and
+ * convergence is judged on the FP64 residual.  alm_out:
  * [nbatch][ncomp][nalm] complex128.  Returns SHTG_ERR_NOT_CONVERGED (output =
  * last iterate, stats filled) if maxiter is hit.  opts may be NULL (tol 1e-6,
  * mixed, preconditioned). */

@@ -41,7 +41,7 @@ class Problem(C.Structure):
 
 class CGOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxiter", C.c_int), ("mode", C.c_int),
-                ("precond", C.c_int), ("inner_tol", C.c_double), ("inner_maxiter", C.c_int),
+                ("precond", C.c_int), ("reliable_delta", C.c_double), ("reserved", C.c_int),
                 ("check_every", C.c_int), ("flags", C.c_int)]
 
 

@@ -148,8 +148,8 @@ class Plan:
         return pr
 
     def cg_sample(self, cl, bl, ninv, d, w1, w2, tol: float = 1e-6, mode: str = "mixed",
-                  maxiter: int = 2000, precond: bool = True, inner_tol: float = 1e-3,
-                  inner_maxiter: int = 300, check_every: int = 4, out=None,
+                  maxiter: int = 4000, precond: bool = True, reliable_delta: float = 1e-2,
+                  check_every: int = 4, out=None,
                   allow_not_converged: bool = False, profile: bool = False):
         """Constrained realization(s) of Eq. (mapmakingeq).
 
@@ -175,7 +175,7 @@ class Plan:
         o.tol, o.maxiter = float(tol), int(maxiter)
         o.mode = N.CG_MIXED if mode == "mixed" else N.CG_FP64
         o.precond = 1 if precond else 0
-        o.inner_tol, o.inner_maxiter = float(inner_tol), int(inner_maxiter)
+        o.reliable_delta, o.reserved = float(reliable_delta), 0
         o.check_every = int(check_every)
         o.flags = (N.HOST_INPUTS if host else 0) | (N.PROFILE if profile else 0)
         st = N.CGStats()

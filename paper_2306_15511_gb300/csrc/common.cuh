@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -69,6 +70,7 @@ struct Prof {
 struct Plan {
     int device = 0;
     Prof prof;
+    std::map<long long, int> tuned;   // autotuned kernel variant per (precision, family, nmaps)
     int geom = 0, nside = 0, nring = 0, npairs = 0, lmax = 0, max_batch = 0, flags = 0;
     int nphi_gauss = 0;
     int64_t npix = 0, nalm = 0;
@@ -98,8 +100,11 @@ struct Plan {
     int *d_ls64 = nullptr, *d_ls32 = nullptr;     // [m][pair] first significant l
     double2 *d_st64 = nullptr;    // [m][pair] (lambda_{ls-1}, lambda_ls)
     float2 *d_st32 = nullptr;
-    double4_32a *d_s2c64 = nullptr;   // spin-2 per-(l,m) constants
+    double4_32a *d_s2c64 = nullptr;   // spin-2 recurrence (alpha, alpha+beta, alpha-beta, gamma)
     float4 *d_s2c32 = nullptr;
+    int2 *d_ls2_64 = nullptr, *d_ls2_32 = nullptr;  // [m][pair] start l of (y+, y-)
+    double4_32a *d_st2_64 = nullptr;  // [m][pair] (y+_{l-1}, y+_l, y-_{l-1}, y-_l) / 2
+    float4 *d_st2_32 = nullptr;
 
     // ring FFT tables
     int fft_logmax = 0;

@@ -1,557 +1,13 @@
-// Legendre stage of the spherical-harmonic transforms (the l-sum of Y and
-// its transpose), the compute-bound core of every operator application of
-// Eq. (mapmakingeq).
-//
-// Synthesis:  F_r(m) = sum_l a_lm lambda_lm(theta_r)            (spin 0)
-// Analysis:   c_lm   = sum_r lambda_lm(theta_r) G_r(m)           (transpose)
-// Rings come in north/south pairs theta, pi - theta; lambda_lm(pi - theta) =
-// (-1)^(l+m) lambda_lm(theta) (App. A), so one recurrence serves both rings:
-// even and odd l - m partial sums E, O give F_N = E + O, F_S = E - O.
-//
-// Spin 2 (Q, U from E, B): with lw = (2Y + -2Y)/2, lx = (2Y - -2Y)/2 (theta
-// parts, computed from lambda_l and lambda_{l-1}; lw has parity (-1)^(l+m),
-// lx the opposite one),
-//   F_Q = - sum_l (E lw + i B lx),   F_U = sum_l (i E lx - B lw),
-// and the analysis is the exact transpose
-//   E^ = sum_r (-lw G_Q - i lx G_U),  B^ = sum_r (i lx G_Q - lw G_U).
-//
-// Work decomposition: one CTA per (m, block of ring pairs, group of maps);
-// each thread owns NR ring pairs and keeps their recurrence in registers;
-// the per-l coefficients and alm of the CTA's m are staged in shared memory
-// and read as warp-wide broadcasts.  Each thread starts at the FP64-computed
-// start state of its rings (first l above the significance threshold), so
-// the loop carries no rescaling.  The analysis reduces over the warp's
-// rings with a butterfly transpose-reduce of 8 consecutive l at a time.
-#include "common.cuh"
+// Dispatch of the Legendre kernels: argument set-up, the diag kernel and an
+// autotuner that picks the (ring pairs per thread, maps per pass) shape of
+// each kernel family on first use.
+#include <map>
+
+#include "legendre_kernels.cuh"
 
 namespace shtg {
 
-#define LEG_THREADS 128
-#define LEG_CHUNK 128
-
-template <typename T> struct V4;
-template <> struct V4<float> { typedef float4 t; };
-template <> struct V4<double> { typedef double4_32a t; };
-
-template <typename T> struct LegArgs {
-    typedef typename VT<T>::C C;
-    typedef typename V4<T>::t C4;
-    int lmax, npairs, nring, nmaps;
-    int rs;             // alm row stride (in rows of nalm) between maps
-    int vjp;            // analysis: double the m > 0 outputs
-    int64_t nalm;
-    const C *alm;       // synthesis input / analysis output
-    C *F;               // [map][m][ring]
-    const T *beam;      // [lmax+1] or null
-    const C *rec;       // (a, b) per alm index
-    const C4 *s2c;      // spin-2 constants per alm index
-    const int *ls;      // [m][pair]
-    const C *st;        // [m][pair]
-    const T *u, *x, *is2;
-    const float *wpair; // diag kernel: ring weights summed over the pair
-    float *diag;        // diag kernel output
-};
-
-// one recurrence step: (l1, l2) = (lambda_{l-1}, lambda_{l-2}) -> (lambda_l, lambda_{l-1})
-template <typename T>
-__device__ __forceinline__ void rstep(T &l1, T &l2, const T a, const T b, const T u) {
-    const T t = a * l1;
-    const T n = fma(t, -u, fma(b, l2, t));
-    l2 = l1;
-    l1 = n;
-}
-
-template <typename T, int NR>
-struct PairState {
-    int pr[NR];
-    T u[NR], x[NR], is2[NR];
-    int ls[NR];
-    T st0[NR], st1[NR];
-    T l1[NR], l2[NR];
-};
-
-// Load the per-pair geometry and start states; returns the warp's l range.
-template <typename T, int NR>
-__device__ __forceinline__ void load_pairs(const LegArgs<T> &a, int m, PairState<T, NR> &S,
-                                           int &warp_lo, int &warp_hi, bool spin2) {
-    const int L = a.lmax;
-    int lo = L + 1, hi = -1;
-#pragma unroll
-    for (int j = 0; j < NR; ++j) {
-        const int pr = blockIdx.x * (LEG_THREADS * NR) + j * LEG_THREADS + threadIdx.x;
-        S.pr[j] = pr;
-        S.l1[j] = T(0);
-        S.l2[j] = T(0);
-        if (pr < a.npairs) {
-            S.u[j] = a.u[pr];
-            if (spin2) {
-                S.x[j] = a.x[pr];
-                S.is2[j] = a.is2[pr];
-            } else {
-                S.x[j] = T(0);
-                S.is2[j] = T(0);
-            }
-            const int64_t o = (int64_t)m * a.npairs + pr;
-            S.ls[j] = a.ls[o];
-            const typename VT<T>::C s = a.st[o];
-            S.st0[j] = s.x;
-            S.st1[j] = s.y;
-        } else {
-            S.u[j] = T(1);
-            S.x[j] = T(0);
-            S.is2[j] = T(1);
-            S.ls[j] = L + 1;
-            S.st0[j] = T(0);
-            S.st1[j] = T(0);
-        }
-        lo = min(lo, S.ls[j]);
-        if (S.ls[j] <= L) hi = max(hi, S.ls[j]);
-    }
-    warp_lo = __reduce_min_sync(0xffffffffu, lo);
-    warp_hi = __reduce_max_sync(0xffffffffu, hi);
-}
-
-template <typename T, int NR, bool INJ>
-__device__ __forceinline__ void step_all(PairState<T, NR> &S, const typename VT<T>::C cf, int l) {
-#pragma unroll
-    for (int j = 0; j < NR; ++j) {
-        rstep(S.l1[j], S.l2[j], cf.x, cf.y, S.u[j]);
-        if (INJ) {
-            if (l == S.ls[j]) {
-                S.l2[j] = S.st0[j];
-                S.l1[j] = S.st1[j];
-            }
-        }
-    }
-}
-
-// spin-2 theta functions from (lambda_l, lambda_{l-1}):
-//   lw = c0 lambda_l / s^2 + c1 lambda_l + c2 x lambda_{l-1} / s^2
-//   lx = m (c3 x lambda_l / s^2 + c2 lambda_{l-1} / s^2)
-template <typename T, typename C4>
-__device__ __forceinline__ void spin2_fn(const T lam, const T lamp, const T x, const T is2,
-                                         const C4 c, const T mm, T &lw, T &lx) {
-    const T A = lam * is2;
-    const T B = lamp * is2;
-    lw = fma(c.z, x * B, fma(c.x, A, c.y * lam));
-    lx = mm * fma(c.w, x * A, c.z * B);
-}
-
-// CTA-wide minimum of the warps' start l (all threads must call).
-__device__ __forceinline__ int cta_min(int v, int *s) {
-    const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) s[w] = v;
-    __syncthreads();
-    int r = s[0];
-#pragma unroll
-    for (int i = 1; i < LEG_THREADS / 32; ++i) r = min(r, s[i]);
-    __syncthreads();
-    return r;
-}
-
-// =========================================================== synthesis
-template <typename T, int NR, int NM, int SPIN>
-__global__ void __launch_bounds__(LEG_THREADS) k_leg_synth(const LegArgs<T> a) {
-    typedef typename VT<T>::C C;
-    typedef typename V4<T>::t C4;
-    constexpr int NA = (SPIN == 2) ? 2 * NM : NM;   // alm rows staged (E, B per map)
-    constexpr int NACC = (SPIN == 2) ? 8 : 2;        // reals per parity class per map
-    __shared__ C s_rec[LEG_CHUNK];
-    __shared__ C4 s_s2c[SPIN == 2 ? LEG_CHUNK : 1];
-    __shared__ C s_alm[NA][LEG_CHUNK];
-    __shared__ int s_red[LEG_THREADS / 32];
-
-    const int m = blockIdx.y;
-    const int L = a.lmax;
-    const int map0 = blockIdx.z * NM;
-    const int nm = min(NM, a.nmaps - map0);
-    const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2;
-    const T mm = T(m);
-
-    PairState<T, NR> S;
-    int warp_lo, warp_hi;
-    load_pairs<T, NR>(a, m, S, warp_lo, warp_hi, SPIN == 2);
-    const int lo = cta_min(warp_lo, s_red);
-
-    T accE[NR][NM][NACC], accO[NR][NM][NACC];
-#pragma unroll
-    for (int j = 0; j < NR; ++j)
-#pragma unroll
-        for (int k = 0; k < NM; ++k)
-#pragma unroll
-            for (int q = 0; q < NACC; ++q) accE[j][k][q] = accO[j][k][q] = T(0);
-
-    auto accumulate = [&](const int i, T(&acc)[NR][NM][NACC]) {
-        if (SPIN == 0) {
-#pragma unroll
-            for (int k = 0; k < NM; ++k) {
-                const C av = s_alm[k][i];
-#pragma unroll
-                for (int j = 0; j < NR; ++j) {
-                    acc[j][k][0] = fma(S.l1[j], av.x, acc[j][k][0]);
-                    acc[j][k][1] = fma(S.l1[j], av.y, acc[j][k][1]);
-                }
-            }
-        } else {
-            const C4 c = s_s2c[i];
-#pragma unroll
-            for (int j = 0; j < NR; ++j) {
-                T lw, lx;
-                spin2_fn(S.l1[j], S.l2[j], S.x[j], S.is2[j], c, mm, lw, lx);
-#pragma unroll
-                for (int k = 0; k < NM; ++k) {
-                    const C e = s_alm[2 * k][i];
-                    const C b = s_alm[2 * k + 1][i];
-                    // W parts: Q = -E lw, U = -B lw ; X parts: Q = -i B lx, U = i E lx
-                    acc[j][k][0] = fma(-e.x, lw, acc[j][k][0]);
-                    acc[j][k][1] = fma(-e.y, lw, acc[j][k][1]);
-                    acc[j][k][2] = fma(-b.x, lw, acc[j][k][2]);
-                    acc[j][k][3] = fma(-b.y, lw, acc[j][k][3]);
-                    acc[j][k][4] = fma(b.y, lx, acc[j][k][4]);
-                    acc[j][k][5] = fma(-b.x, lx, acc[j][k][5]);
-                    acc[j][k][6] = fma(-e.y, lx, acc[j][k][6]);
-                    acc[j][k][7] = fma(e.x, lx, acc[j][k][7]);
-                }
-            }
-        }
-    };
-
-    // rings with no significant l in this CTA still get their (zero) output
-    for (int c0 = lo; c0 <= L; c0 += LEG_CHUNK) {
-        const int c1 = min(c0 + LEG_CHUNK, L + 1);
-        __syncthreads();
-        for (int i = threadIdx.x; i < c1 - c0; i += LEG_THREADS) {
-            const int l = c0 + i;
-            const int64_t idx = base + l;
-            s_rec[i] = a.rec[idx];
-            if (SPIN == 2) s_s2c[i] = a.s2c[idx];
-            const T bm = a.beam ? a.beam[l] : T(1);
-#pragma unroll
-            for (int k = 0; k < NA; ++k) {
-                C v = cplx(T(0), T(0));
-                const int mk = (SPIN == 2) ? k / 2 : k;
-                if (mk < nm) {
-                    const int64_t row = (int64_t)(map0 + mk) * a.rs + ((SPIN == 2) ? (k & 1) : 0);
-                    v = a.alm[row * a.nalm + idx];
-                    if (m == 0) v.y = T(0);
-                    v.x *= bm;
-                    v.y *= bm;
-                }
-                s_alm[k][i] = v;
-            }
-        }
-        __syncthreads();
-        int l = max(c0, warp_lo);
-        const int la_end = min(c1 - 1, warp_hi);
-        for (; l <= la_end; ++l) {   // start states still being injected
-            step_all<T, NR, true>(S, s_rec[l - c0], l);
-            if ((l - m) & 1) accumulate(l - c0, accO);
-            else accumulate(l - c0, accE);
-        }
-        if (l < c1 && ((l - m) & 1)) {
-            step_all<T, NR, false>(S, s_rec[l - c0], l);
-            accumulate(l - c0, accO);
-            ++l;
-        }
-        for (; l + 1 < c1; l += 2) {
-            step_all<T, NR, false>(S, s_rec[l - c0], l);
-            accumulate(l - c0, accE);
-            step_all<T, NR, false>(S, s_rec[l + 1 - c0], l + 1);
-            accumulate(l + 1 - c0, accO);
-        }
-        if (l < c1) {
-            step_all<T, NR, false>(S, s_rec[l - c0], l);
-            accumulate(l - c0, accE);
-        }
-    }
-
-#pragma unroll
-    for (int j = 0; j < NR; ++j) {
-        const int pr = S.pr[j];
-        if (pr >= a.npairs) continue;
-        const int rn = pr, rs = a.nring - 1 - pr;
-#pragma unroll
-        for (int k = 0; k < NM; ++k) {
-            if (k >= nm) break;
-            if (SPIN == 0) {
-                C *out = a.F + ((int64_t)(map0 + k) * (L + 1) + m) * a.nring;
-                out[rn] = cplx(accE[j][k][0] + accO[j][k][0], accE[j][k][1] + accO[j][k][1]);
-                if (rs != rn)
-                    out[rs] = cplx(accE[j][k][0] - accO[j][k][0], accE[j][k][1] - accO[j][k][1]);
-            } else {
-                const T *E = accE[j][k], *O = accO[j][k];
-                // north: W + X over both classes; south: even W - X, odd X - W
-                C *oq = a.F + ((int64_t)(2 * (map0 + k)) * (L + 1) + m) * a.nring;
-                C *ou = a.F + ((int64_t)(2 * (map0 + k) + 1) * (L + 1) + m) * a.nring;
-                oq[rn] = cplx(E[0] + O[0] + E[4] + O[4], E[1] + O[1] + E[5] + O[5]);
-                ou[rn] = cplx(E[2] + O[2] + E[6] + O[6], E[3] + O[3] + E[7] + O[7]);
-                if (rs != rn) {
-                    oq[rs] = cplx(E[0] - O[0] - E[4] + O[4], E[1] - O[1] - E[5] + O[5]);
-                    ou[rs] = cplx(E[2] - O[2] - E[6] + O[6], E[3] - O[3] - E[7] + O[7]);
-                }
-            }
-        }
-    }
-}
-
-// =========================================================== analysis
-// butterfly transpose-reduce of 8 values over the warp: afterwards every lane
-// holds the warp sum of value index 4*b4 + 2*b3 + b2 (b = lane bits).
-template <typename T>
-__device__ __forceinline__ T treduce8(T (&v)[8], const int lane) {
-    const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1, b2 = (lane >> 2) & 1;
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const T send = b4 ? v[i] : v[i + 4];
-        const T keep = b4 ? v[i + 4] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const T send = b3 ? v[i] : v[i + 2];
-        const T keep = b3 ? v[i + 2] : v[i];
-        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-    {
-        const T send = b2 ? v[0] : v[1];
-        const T keep = b2 ? v[1] : v[0];
-        v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
-    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 2);
-    v[0] += __shfl_xor_sync(0xffffffffu, v[0], 1);
-    return v[0];
-}
-
-template <typename T, int NR, int NM, int SPIN>
-__global__ void __launch_bounds__(LEG_THREADS) k_leg_analysis(const LegArgs<T> a) {
-    typedef typename VT<T>::C C;
-    typedef typename V4<T>::t C4;
-    constexpr int NO = (SPIN == 2) ? 4 : 2;     // reals out per map per l (E, B or a)
-    __shared__ C s_rec[LEG_CHUNK];
-    __shared__ C4 s_s2c[SPIN == 2 ? LEG_CHUNK : 1];
-    __shared__ int s_red[LEG_THREADS / 32];
-    extern __shared__ unsigned char s_dyn[];
-    T *s_acc = reinterpret_cast<T *>(s_dyn);     // [(lmax+1-m)][NM][NO]
-
-    const int m = blockIdx.y;
-    const int L = a.lmax;
-    const int map0 = blockIdx.z * NM;
-    const int nm = min(NM, a.nmaps - map0);
-    const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2;
-    const int nl = L + 1 - m;
-    const int lane = threadIdx.x & 31;
-    const T mm = T(m);
-
-    for (int i = threadIdx.x; i < nl * NM * NO; i += LEG_THREADS) s_acc[i] = T(0);
-
-    PairState<T, NR> S;
-    int warp_lo, warp_hi;
-    load_pairs<T, NR>(a, m, S, warp_lo, warp_hi, SPIN == 2);
-
-    // per-pair even / odd combinations of the north and south ring data
-    T gE[NR][NM][2 * (NO / 2)], gO[NR][NM][2 * (NO / 2)];
-#pragma unroll
-    for (int j = 0; j < NR; ++j) {
-        const int pr = S.pr[j];
-        const bool ok = pr < a.npairs;
-        const int rn = pr, rs = a.nring - 1 - pr;
-#pragma unroll
-        for (int k = 0; k < NM; ++k) {
-#pragma unroll
-            for (int c = 0; c < NO / 2; ++c) {
-                C gn = cplx(T(0), T(0)), gs = cplx(T(0), T(0));
-                if (ok && k < nm) {
-                    const int row = (SPIN == 2) ? 2 * (map0 + k) + c : map0 + k;
-                    const C *g = a.F + ((int64_t)row * (L + 1) + m) * a.nring;
-                    gn = g[rn];
-                    if (rs != rn) gs = g[rs];
-                }
-                gE[j][k][2 * c] = gn.x + gs.x;
-                gE[j][k][2 * c + 1] = gn.y + gs.y;
-                gO[j][k][2 * c] = gn.x - gs.x;
-                gO[j][k][2 * c + 1] = gn.y - gs.y;
-            }
-        }
-    }
-    const int lo = cta_min(warp_lo, s_red) & ~7;
-    if (lo <= L) {
-        for (int c0 = lo; c0 <= L; c0 += LEG_CHUNK) {
-            const int c1 = min(c0 + LEG_CHUNK, L + 1);
-            __syncthreads();
-            for (int i = threadIdx.x; i < c1 - c0; i += LEG_THREADS) {
-                const int64_t idx = base + c0 + i;
-                if (c0 + i >= m) {
-                    s_rec[i] = a.rec[idx];
-                    if (SPIN == 2) s_s2c[i] = a.s2c[idx];
-                } else {
-                    s_rec[i] = cplx(T(0), T(0));
-                    if (SPIN == 2) s_s2c[i] = C4();
-                }
-            }
-            __syncthreads();
-            for (int g0 = c0; g0 < c1; g0 += 8) {
-                if (g0 + 7 < warp_lo) continue;      // warp-uniform
-                T part[NM][NO][8];
-#pragma unroll
-                for (int v = 0; v < 8; ++v) {
-                    const int l = g0 + v;
-                    const bool live = (l >= warp_lo) && (l < c1);
-                    if (live) {
-                        if (l <= warp_hi) step_all<T, NR, true>(S, s_rec[l - c0], l);
-                        else step_all<T, NR, false>(S, s_rec[l - c0], l);
-                    }
-                    const bool odd = (l - m) & 1;
-#pragma unroll
-                    for (int k = 0; k < NM; ++k)
-#pragma unroll
-                        for (int q = 0; q < NO; ++q) part[k][q][v] = T(0);
-                    if (live) {
-                        if (SPIN == 0) {
-#pragma unroll
-                            for (int j = 0; j < NR; ++j)
-#pragma unroll
-                                for (int k = 0; k < NM; ++k) {
-                                    const T gr = odd ? gO[j][k][0] : gE[j][k][0];
-                                    const T gi = odd ? gO[j][k][1] : gE[j][k][1];
-                                    part[k][0][v] = fma(S.l1[j], gr, part[k][0][v]);
-                                    part[k][1][v] = fma(S.l1[j], gi, part[k][1][v]);
-                                }
-                        } else {
-                            const C4 c = s_s2c[l - c0];
-#pragma unroll
-                            for (int j = 0; j < NR; ++j) {
-                                T lw, lx;
-                                spin2_fn(S.l1[j], S.l2[j], S.x[j], S.is2[j], c, mm, lw, lx);
-#pragma unroll
-                                for (int k = 0; k < NM; ++k) {
-                                    // even: W-terms use (Q_N + Q_S, U_N + U_S), X-terms the odd sums
-                                    const T *gw = odd ? gO[j][k] : gE[j][k];
-                                    const T *gx = odd ? gE[j][k] : gO[j][k];
-                                    // E^ += -lw GQ - i lx GU ; B^ += i lx GQ - lw GU
-                                    part[k][0][v] = fma(-lw, gw[0], fma(lx, gx[3], part[k][0][v]));
-                                    part[k][1][v] = fma(-lw, gw[1], fma(-lx, gx[2], part[k][1][v]));
-                                    part[k][2][v] = fma(-lw, gw[2], fma(-lx, gx[1], part[k][2][v]));
-                                    part[k][3][v] = fma(-lw, gw[3], fma(lx, gx[0], part[k][3][v]));
-                                }
-                            }
-                        }
-                    }
-                }
-                const int vsel = 4 * ((lane >> 4) & 1) + 2 * ((lane >> 3) & 1) + ((lane >> 2) & 1);
-                const int l = g0 + vsel;
-#pragma unroll
-                for (int k = 0; k < NM; ++k)
-#pragma unroll
-                    for (int q = 0; q < NO; ++q) {
-                        const T r = treduce8<T>(part[k][q], lane);
-                        if ((lane & 3) == 0 && l >= m && l <= L && k < nm)
-                            atomicAdd(&s_acc[((l - m) * NM + k) * NO + q], r);
-                    }
-            }
-        }
-    }
-    __syncthreads();
-    const bool single = gridDim.x == 1;
-    for (int i = threadIdx.x; i < nl * nm; i += LEG_THREADS) {
-        const int li = i / nm, k = i % nm;
-        const int l = m + li;
-        const T bm = (a.beam ? a.beam[l] : T(1)) * ((a.vjp && m > 0) ? T(2) : T(1));
-#pragma unroll
-        for (int c = 0; c < NO / 2; ++c) {
-            T re = s_acc[(li * NM + k) * NO + 2 * c] * bm;
-            T im = (m == 0) ? T(0) : s_acc[(li * NM + k) * NO + 2 * c + 1] * bm;
-            const int64_t row = (int64_t)(map0 + k) * a.rs + c;
-            C *dst = const_cast<C *>(a.alm) + row * a.nalm + base + l;
-            if (single) {
-                *dst = cplx(re, im);
-            } else {
-                atomicAdd(&dst->x, re);
-                atomicAdd(&dst->y, im);
-            }
-        }
-    }
-}
-
-// ====================================================== preconditioner
-// diag_lm = sum_pairs wpair_r g_lm(theta_r), g = lambda^2 (spin 0) or
-// lw^2 + lx^2 (spin 2); g has the same value on both rings of a pair.
-template <int NR, int SPIN>
-__global__ void __launch_bounds__(LEG_THREADS) k_leg_diag(const LegArgs<float> a) {
-    __shared__ float2 s_rec[LEG_CHUNK];
-    __shared__ float4 s_s2c[LEG_CHUNK];
-    __shared__ int s_red[LEG_THREADS / 32];
-    extern __shared__ unsigned char s_dyn[];
-    float *s_acc = reinterpret_cast<float *>(s_dyn);
-    const int m = blockIdx.y;
-    const int L = a.lmax;
-    const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2;
-    const int nl = L + 1 - m;
-    const int lane = threadIdx.x & 31;
-    for (int i = threadIdx.x; i < nl; i += LEG_THREADS) s_acc[i] = 0.f;
-    PairState<float, NR> S;
-    int warp_lo, warp_hi;
-    load_pairs<float, NR>(a, m, S, warp_lo, warp_hi, SPIN == 2);
-    float w[NR];
-#pragma unroll
-    for (int j = 0; j < NR; ++j) w[j] = S.pr[j] < a.npairs ? a.wpair[S.pr[j]] : 0.f;
-    const int lo = cta_min(warp_lo, s_red) & ~7;
-    if (lo <= L) {
-        for (int c0 = lo; c0 <= L; c0 += LEG_CHUNK) {
-            const int c1 = min(c0 + LEG_CHUNK, L + 1);
-            __syncthreads();
-            for (int i = threadIdx.x; i < c1 - c0; i += LEG_THREADS) {
-                const int64_t idx = base + c0 + i;
-                if (c0 + i >= m) {
-                    s_rec[i] = a.rec[idx];
-                    if (SPIN == 2) s_s2c[i] = a.s2c[idx];
-                } else {
-                    s_rec[i] = make_float2(0.f, 0.f);
-                    s_s2c[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
-            __syncthreads();
-            for (int g0 = c0; g0 < c1; g0 += 8) {
-                if (g0 + 7 < warp_lo) continue;
-                float part[8];
-#pragma unroll
-                for (int v = 0; v < 8; ++v) {
-                    const int l = g0 + v;
-                    part[v] = 0.f;
-                    if (l >= warp_lo && l < c1) {
-                        if (l <= warp_hi) step_all<float, NR, true>(S, s_rec[l - c0], l);
-                        else step_all<float, NR, false>(S, s_rec[l - c0], l);
-#pragma unroll
-                        for (int j = 0; j < NR; ++j) {
-                            float g;
-                            if (SPIN == 0) {
-                                g = S.l1[j] * S.l1[j];
-                            } else {
-                                float lw, lx;
-                                spin2_fn(S.l1[j], S.l2[j], S.x[j], S.is2[j], s_s2c[l - c0], (float)m, lw, lx);
-                                g = lw * lw + lx * lx;
-                            }
-                            part[v] = fmaf(w[j], g, part[v]);
-                        }
-                    }
-                }
-                const int vsel = 4 * ((lane >> 4) & 1) + 2 * ((lane >> 3) & 1) + ((lane >> 2) & 1);
-                const int l = g0 + vsel;
-                const float r = treduce8<float>(part, lane);
-                if ((lane & 3) == 0 && l >= m && l <= L) atomicAdd(&s_acc[l - m], r);
-            }
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nl; i += LEG_THREADS) {
-        float *dst = a.diag + base + m + i;
-        if (gridDim.x == 1) *dst = s_acc[i];
-        else atomicAdd(dst, s_acc[i]);
-    }
-}
-
-// ============================================================ launchers
-template <typename T> static LegArgs<T> make_args(Plan *p);
-template <> LegArgs<float> make_args<float>(Plan *p) {
+template <> LegArgs<float> leg_make_args<float>(Plan *p) {
     LegArgs<float> a{};
     a.lmax = p->lmax;
     a.npairs = p->npairs;
@@ -561,12 +17,12 @@ template <> LegArgs<float> make_args<float>(Plan *p) {
     a.s2c = p->d_s2c32;
     a.ls = p->d_ls32;
     a.st = p->d_st32;
+    a.ls2 = p->d_ls2_32;
+    a.st2 = p->d_st2_32;
     a.u = p->d_u32;
-    a.x = p->d_x32;
-    a.is2 = p->d_is2_32;
     return a;
 }
-template <> LegArgs<double> make_args<double>(Plan *p) {
+template <> LegArgs<double> leg_make_args<double>(Plan *p) {
     LegArgs<double> a{};
     a.lmax = p->lmax;
     a.npairs = p->npairs;
@@ -576,87 +32,95 @@ template <> LegArgs<double> make_args<double>(Plan *p) {
     a.s2c = p->d_s2c64;
     a.ls = p->d_ls64;
     a.st = p->d_st64;
+    a.ls2 = p->d_ls2_64;
+    a.st2 = p->d_st2_64;
     a.u = p->d_u64;
-    a.x = p->d_x64;
-    a.is2 = p->d_is2_64;
     return a;
 }
 
-// ring pairs per thread and maps per pass for each variant
-template <typename T, int SPIN> struct Cfg;
-template <> struct Cfg<float, 0> { enum { NR = 4, NM = 2, ANR = 4, ANM = 2 }; };
-template <> struct Cfg<float, 2> { enum { NR = 2, NM = 1, ANR = 2, ANM = 1 }; };
-template <> struct Cfg<double, 0> { enum { NR = 2, NM = 2, ANR = 2, ANM = 1 }; };
-template <> struct Cfg<double, 2> { enum { NR = 1, NM = 1, ANR = 1, ANM = 1 }; };
-
-template <typename T, int SPIN>
-static int launch_synth(Plan *p, const typename VT<T>::C *alm, int rs, int nmaps,
-                        const T *beam, typename VT<T>::C *F, cudaStream_t st) {
-    constexpr int NR = Cfg<T, SPIN>::NR, NM = Cfg<T, SPIN>::NM;
-    LegArgs<T> a = make_args<T>(p);
-    a.alm = alm;
-    a.rs = rs;
-    a.F = F;
-    a.beam = beam;
-    a.nmaps = nmaps;
-    dim3 grid((p->npairs + LEG_THREADS * NR - 1) / (LEG_THREADS * NR), p->lmax + 1,
-              (nmaps + NM - 1) / NM);
-    prof_begin(p, sizeof(T) == 8 ? K_LEG_SYN64 : K_LEG_SYN32, st);
-    k_leg_synth<T, NR, NM, SPIN><<<grid, LEG_THREADS, 0, st>>>(a);
-    prof_end(p, st);
-    SHTG_CHECK_LAUNCH("k_leg_synth");
-    return SHTG_OK;
-}
-
-template <typename T, int SPIN>
-static int launch_analysis(Plan *p, const typename VT<T>::C *G, int nmaps, const T *beam,
-                           typename VT<T>::C *alm, int rs, cudaStream_t st, int vjp) {
-    constexpr int NR = Cfg<T, SPIN>::ANR, NM = Cfg<T, SPIN>::ANM;
-    constexpr int NO = (SPIN == 2) ? 4 : 2;
-    LegArgs<T> a = make_args<T>(p);
-    a.alm = alm;
-    a.rs = rs;
-    a.vjp = vjp;
-    a.F = const_cast<typename VT<T>::C *>(G);
-    a.beam = beam;
-    a.nmaps = nmaps;
-    const int gx = (p->npairs + LEG_THREADS * NR - 1) / (LEG_THREADS * NR);
-    const int comps = (SPIN == 2) ? 2 : 1;
-    if (gx > 1) {
-        const size_t cs = sizeof(typename VT<T>::C) * (size_t)p->nalm;
-        SHTG_CUDA(cudaMemset2DAsync(alm, cs * rs, 0, cs * comps, nmaps, st));
+// ------------------------------------------------------------- autotuner
+// Key: (precision, family, nmaps).  On the first call with a key every
+// candidate runs twice on the caller's buffers (all compute the same
+// result); the second run of each is timed with CUDA events on the stream
+// and the fastest is kept.  SHTG_TUNE=0 in the environment keeps variant 0.
+static bool tuning_enabled() {
+    static int on = -1;
+    if (on < 0) {
+        const char *e = getenv("SHTG_TUNE");
+        on = (e && e[0] == '0') ? 0 : 1;
     }
-    const size_t smem = sizeof(T) * (size_t)(p->lmax + 1) * NM * NO;
-    auto kern = k_leg_analysis<T, NR, NM, SPIN>;
-    if (smem > 48 * 1024) SHTG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid(gx, p->lmax + 1, (nmaps + NM - 1) / NM);
-    prof_begin(p, sizeof(T) == 8 ? K_LEG_ANA64 : K_LEG_ANA32, st);
-    kern<<<grid, LEG_THREADS, smem, st>>>(a);
-    prof_end(p, st);
-    SHTG_CHECK_LAUNCH("k_leg_analysis");
-    return SHTG_OK;
+    return on == 1;
 }
 
-template <typename T>
-int leg_synth(Plan *p, int spin, const typename VT<T>::C *alm, int rs, int nmaps, const T *beam,
-              typename VT<T>::C *F, cudaStream_t st) {
-    if (spin == 2) return launch_synth<T, 2>(p, alm, rs, nmaps, beam, F, st);
-    return launch_synth<T, 0>(p, alm, rs, nmaps, beam, F, st);
+template <typename Run>
+static int tune(Plan *p, int key_prec, int family, int nmaps, int nvar, cudaStream_t st, Run run) {
+    const long long key = ((long long)key_prec * 16 + family) * 65536 + nmaps;
+    auto it = p->tuned.find(key);
+    if (it != p->tuned.end()) return run(it->second);
+    if (!tuning_enabled() || nvar <= 1 || p->prof.on) {
+        p->tuned[key] = 0;
+        return run(0);
+    }
+    cudaEvent_t e0, e1;
+    SHTG_CUDA(cudaEventCreate(&e0));
+    SHTG_CUDA(cudaEventCreate(&e1));
+    int best = 0;
+    float tbest = 1e30f;
+    for (int v = 0; v < nvar; ++v) {
+        int rc = run(v);
+        if (rc != SHTG_OK) continue;
+        cudaEventRecord(e0, st);
+        rc = run(v);
+        cudaEventRecord(e1, st);
+        if (rc != SHTG_OK) continue;
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < tbest) {
+            tbest = ms;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    p->tuned[key] = best;
+    return run(best);
 }
-template <typename T>
-int leg_analysis(Plan *p, int spin, const typename VT<T>::C *G, int nmaps, const T *beam,
-                 typename VT<T>::C *alm, int rs, cudaStream_t st, int vjp) {
-    if (spin == 2) return launch_analysis<T, 2>(p, G, nmaps, beam, alm, rs, st, vjp);
-    return launch_analysis<T, 0>(p, G, nmaps, beam, alm, rs, st, vjp);
+
+template <>
+int leg_synth<float>(Plan *p, int spin, const float2 *alm, int rs, int nmaps, const float *beam,
+                     float2 *F, cudaStream_t st) {
+    const Variants32 &V = variants32();
+    const int s = spin == 2 ? 1 : 0;
+    return tune(p, 1, s, nmaps, V.n[s], st, [&](int v) { return V.syn[s][v](p, alm, rs, nmaps, beam, F, st); });
 }
-template int leg_synth<float>(Plan *, int, const float2 *, int, int, const float *, float2 *, cudaStream_t);
-template int leg_synth<double>(Plan *, int, const double2 *, int, int, const double *, double2 *, cudaStream_t);
-template int leg_analysis<float>(Plan *, int, const float2 *, int, const float *, float2 *, int, cudaStream_t, int);
-template int leg_analysis<double>(Plan *, int, const double2 *, int, const double *, double2 *, int, cudaStream_t, int);
+template <>
+int leg_synth<double>(Plan *p, int spin, const double2 *alm, int rs, int nmaps, const double *beam,
+                      double2 *F, cudaStream_t st) {
+    const Variants64 &V = variants64();
+    const int s = spin == 2 ? 1 : 0;
+    return tune(p, 0, s, nmaps, V.n[s], st, [&](int v) { return V.syn[s][v](p, alm, rs, nmaps, beam, F, st); });
+}
+template <>
+int leg_analysis<float>(Plan *p, int spin, const float2 *G, int nmaps, const float *beam, float2 *alm,
+                        int rs, cudaStream_t st, int vjp) {
+    const Variants32 &V = variants32();
+    const int s = spin == 2 ? 1 : 0;
+    return tune(p, 1, 2 + s, nmaps, V.n[2 + s], st,
+                [&](int v) { return V.ana[s][v](p, G, nmaps, beam, alm, rs, st, vjp); });
+}
+template <>
+int leg_analysis<double>(Plan *p, int spin, const double2 *G, int nmaps, const double *beam,
+                         double2 *alm, int rs, cudaStream_t st, int vjp) {
+    const Variants64 &V = variants64();
+    const int s = spin == 2 ? 1 : 0;
+    return tune(p, 0, 2 + s, nmaps, V.n[2 + s], st,
+                [&](int v) { return V.ana[s][v](p, G, nmaps, beam, alm, rs, st, vjp); });
+}
 
 int leg_diag(Plan *p, int spin, const float *wpair, float *out, cudaStream_t st) {
     constexpr int NR = 4;
-    LegArgs<float> a = make_args<float>(p);
+    LegArgs<float> a = leg_make_args<float>(p);
     a.wpair = wpair;
     a.diag = out;
     const int gx = (p->npairs + LEG_THREADS * NR - 1) / (LEG_THREADS * NR);

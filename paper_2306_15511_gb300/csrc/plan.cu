@@ -84,6 +84,123 @@ __global__ void k_start_states(int lmax, int npairs, const double *__restrict__ 
     st32[o] = s32;
 }
 
+// Spin-2 start states.  The spin-2 kernels run two independent three-term
+// recurrences (the Wigner d^l_{m,-+2} recurrence, normalized by
+// sqrt((2l+1)/4pi)) for y+ = 2lambda_lm / 2 and y- = -2lambda_lm / 2, and form
+// lw = y+ + y-, lx = y+ - y- on the fly.  Kept apart, each recurrence carries
+// only its own rounding: near the poles the two differ by ~theta^4 and a
+// combined recurrence would let the large one pollute the small one.
+// Seeds at l0 = max(m, 2), free of cancellation (u = 1 - cos theta):
+//   m >= 2: 2lambda_mm = N_m m (m-1) lambda_mm tan^2(theta/2),
+//           -2lambda_mm = N_m m (m-1) lambda_mm cot^2(theta/2),
+//           N_m = ((m-1) m (m+1) (m+2))^-1/2, tan^2(theta/2) = u / (2 - u);
+//   m = 1:  +-2lambda_21 = -+sqrt(5/16pi) sin(theta) (1 -+ cos theta);
+//   m = 0:  +-2lambda_20 = sqrt(15/32pi) sin^2(theta)
+// (these follow from applying the spin-raising operator twice to Y_lm).
+// Each recurrence is walked in FP64 with exponent rescaling up to its first
+// significant l.
+struct Scaled {
+    double v;
+    int k;   // value = v * 2^(512 k)
+    __device__ void norm() {
+        if (v == 0.0) return;
+        while (fabs(v) < 0x1p-256) {
+            v *= 0x1p512;
+            k -= 1;
+        }
+        while (fabs(v) > 0x1p256) {
+            v *= 0x1p-512;
+            k += 1;
+        }
+    }
+};
+
+__global__ void k_start_spin2(int lmax, int npairs, const double *__restrict__ u64,
+                              const double *__restrict__ sect, const double4_32a *__restrict__ s2c,
+                              double thr64, double thr32, int2 *ls64, double4_32a *st64, int2 *ls32,
+                              float4 *st32) {
+    const int pr = blockIdx.x * blockDim.x + threadIdx.x;
+    const int m = blockIdx.y;
+    if (pr >= npairs) return;
+    const double u = u64[pr];
+    const double s = sqrt(u * (2.0 - u));
+    const int64_t o = (int64_t)m * npairs + pr;
+    int lp64 = lmax + 1, lp32 = lmax + 1, lm64 = lmax + 1, lm32 = lmax + 1;
+    double sd[4] = {0, 0, 0, 0};
+    float sf[4] = {0.f, 0.f, 0.f, 0.f};
+    const int l0 = m > 2 ? m : 2;
+    if (s > 0.0 && l0 <= lmax) {
+        Scaled y0[2];
+        if (m >= 2) {
+            double v = 0.28209479177387814347403972578;
+            int k = 0;
+            for (int j = 1; j <= m; ++j) {
+                v *= -sect[j] * s;
+                if (fabs(v) < 0x1p-256) {
+                    v *= 0x1p512;
+                    k -= 1;
+                }
+            }
+            const double dm = m;
+            const double nm = dm * (dm - 1.0) / sqrt((dm - 1.0) * dm * (dm + 1.0) * (dm + 2.0));
+            const double t2 = u / (2.0 - u);
+            y0[0].v = v * nm * t2;
+            y0[1].v = v * nm / t2;
+            y0[0].k = y0[1].k = k;
+        } else if (m == 1) {
+            const double c = sqrt(5.0 / (16.0 * 3.14159265358979323846)) * s;
+            y0[0].v = -c * u;
+            y0[1].v = c * (2.0 - u);
+            y0[0].k = y0[1].k = 0;
+        } else {
+            const double c = sqrt(15.0 / (32.0 * 3.14159265358979323846)) * s * s;
+            y0[0].v = c;
+            y0[1].v = c;
+            y0[0].k = y0[1].k = 0;
+        }
+        const int64_t base = (int64_t)m * (2 * lmax + 1 - m) / 2;
+        for (int sp = 0; sp < 2; ++sp) {   // sp 0: y+ (A = alpha + beta), 1: y- (alpha - beta)
+            Scaled y = y0[sp];
+            y.norm();
+            double prev = 0.0;
+            int got32 = 0, got64 = 0;
+            for (int l = l0;; ++l) {
+                if (y.k == 0) {
+                    const double a = fabs(y.v);
+                    if (!got32 && a >= thr32) {
+                        got32 = 1;
+                        (sp ? lm32 : lp32) = l;
+                        sf[2 * sp] = (float)(0.5 * prev);
+                        sf[2 * sp + 1] = (float)(0.5 * y.v);
+                    }
+                    if (!got64 && a >= thr64) {
+                        got64 = 1;
+                        (sp ? lm64 : lp64) = l;
+                        sd[2 * sp] = 0.5 * prev;
+                        sd[2 * sp + 1] = 0.5 * y.v;
+                    }
+                    if (got32 && got64) break;
+                }
+                if (l >= lmax) break;
+                const double4_32a c = s2c[base + l + 1];
+                const double t = fma(-c.x, u, sp ? c.z : c.y);
+                const double nv = fma(t, y.v, -c.w * prev);
+                prev = y.v;
+                y.v = nv;
+                if (fabs(y.v) > 0x1p256) {
+                    y.v *= 0x1p-512;
+                    prev *= 0x1p-512;
+                    y.k += 1;
+                }
+            }
+        }
+    }
+    ls64[o] = make_int2(lp64, lm64);
+    ls32[o] = make_int2(lp32, lm32);
+    st64[o] = make_double4_32a(sd[0], sd[1], sd[2], sd[3]);
+    st32[o] = make_float4(sf[0], sf[1], sf[2], sf[3]);
+}
+
 // ----------------------------------------------------------------- host FFT
 static int ilog2(int64_t n) {
     int l = 0;
@@ -253,22 +370,28 @@ static int build_legendre_tables(Plan *p, const std::vector<double> &u_pair) {
             rec32[i] = make_float2((float)a, (float)b);
             lof[i] = l;
             mof[i] = m;
-            // spin-2 constants: with N_l = ((l-1) l (l+1) (l+2))^-1/2 and
-            // f = sqrt((2l+1)(l^2-m^2)/(2l-1)),
-            //   lw = c0 lambda_l / s^2 + c1 lambda_l + c2 x lambda_{l-1} / s^2
-            //   lx = c3 x lambda_l / s^2 + m c2/f... see legendre.cu
-            double c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-            if (l >= 2) {
-                const double dl = l, dm = m;
-                const double nl = 1.0 / sqrt((dl - 1.0) * dl * (dl + 1.0) * (dl + 2.0));
-                const double f = sqrt((2.0 * dl + 1.0) * (dl * dl - dm * dm) / (2.0 * dl - 1.0));
-                c0 = -2.0 * nl * (dl - dm * dm);   // lw: lambda_l / s^2
-                c1 = -nl * dl * (dl - 1.0);        // lw: lambda_l
-                c2 = 2.0 * nl * f;                 // lw: x lambda_{l-1} / s^2 ; lx: m lambda_{l-1} / s^2
-                c3 = -2.0 * nl * (dl - 1.0);       // lx: m x lambda_l / s^2
+            // spin-2 recurrence (Wigner d^l_{m,-2}, normalized by sqrt((2l+1)/4pi)):
+            //   y_l = (alpha (1 - u) + beta) y_{l-1} - gamma y_{l-2}
+            // for y = 2lambda; -2lambda has -beta.  Coefficients of the step that
+            // produces l (from l-1, l-2), defined for l - 1 >= max(m, 2).  With
+            // k = l - 1, D = k sqrt((k+1)^2 - m^2) sqrt((k+1)^2 - 4),
+            // f = sqrt((2k+3)/(2k+1)): alpha = f (2k+1) k (k+1) / D,
+            // beta = 2 m f (2k+1) / D, gamma = f sqrt((2k+1)/(2k-1)) (k+1)
+            // sqrt(k^2 - m^2) sqrt(k^2 - 4) / D.
+            double al = 0, be = 0, ga = 0;
+            const int k = l - 1;
+            if (k >= 2 && k >= m) {
+                const double dk = k, dm = m;
+                const double D = dk * sqrt((dk + 1) * (dk + 1) - dm * dm) * sqrt((dk + 1) * (dk + 1) - 4.0);
+                const double f = sqrt((2 * dk + 3) / (2 * dk + 1));
+                al = f * (2 * dk + 1) * dk * (dk + 1) / D;
+                be = f * (2 * dk + 1) * 2.0 * dm / D;
+                ga = f * sqrt((2 * dk + 1) / (2 * dk - 1)) * (dk + 1) * sqrt(dk * dk - dm * dm) *
+                     sqrt(dk * dk - 4.0) / D;
             }
-            s2c64[i] = make_double4_32a(c0, c1, c2, c3);
-            s2c32[i] = make_float4((float)c0, (float)c1, (float)c2, (float)c3);
+            // stored as (alpha, alpha + beta, alpha - beta, gamma)
+            s2c64[i] = make_double4_32a(al, al + be, al - be, ga);
+            s2c32[i] = make_float4((float)al, (float)(al + be), (float)(al - be), (float)ga);
         }
     }
     SHTG_TRY(dalloc(p, &p->d_rec64, P));
@@ -326,6 +449,14 @@ static int build_legendre_tables(Plan *p, const std::vector<double> &u_pair) {
     // dropped; both leave room for the 1/sin^2 factor of the spin-2 functions.
     k_start_states<<<grid, 128>>>(L, NP, p->d_u64, d_sect, p->d_rec64, 0x1p-80, 0x1p-56,
                                   p->d_ls64, p->d_st64, p->d_ls32, p->d_st32);
+    if (p->flags & SHTG_SPIN2) {
+        SHTG_TRY(dalloc(p, &p->d_ls2_64, ns));
+        SHTG_TRY(dalloc(p, &p->d_st2_64, ns));
+        SHTG_TRY(dalloc(p, &p->d_ls2_32, ns));
+        SHTG_TRY(dalloc(p, &p->d_st2_32, ns));
+        k_start_spin2<<<grid, 128>>>(L, NP, p->d_u64, d_sect, p->d_s2c64, 0x1p-80, 0x1p-56,
+                                     p->d_ls2_64, p->d_st2_64, p->d_ls2_32, p->d_st2_32);
+    }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(d_sect);
@@ -471,7 +602,7 @@ int plan_build(Plan *p) {
     SHTG_TRY(dalloc(p, &p->d_ltab64, 9 * (int64_t)(p->lmax + 1)));
     SHTG_TRY(dalloc(p, &p->d_ltab32, 5 * (int64_t)(p->lmax + 1)));
     SHTG_TRY(dalloc(p, &p->d_scal, 16 * (int64_t)p->max_batch));
-    SHTG_TRY(dalloc(p, &p->d_part, 4 * (int64_t)p->max_batch * SHTG_RED_BLOCKS + 2 * (int64_t)p->max_batch + 64));
+    SHTG_TRY(dalloc(p, &p->d_part, 4 * (int64_t)p->max_batch * SHTG_RED_BLOCKS + 4 * (int64_t)p->max_batch + 64));
     SHTG_TRY(dalloc(p, &p->d_lsum, (int64_t)p->lmax + 1));
     SHTG_TRY(dalloc(p, &p->d_stage, nmp));
     SHTG_CUDA(cudaMallocHost((void **)&p->h_pinned, 4096 * sizeof(double)));
@@ -490,7 +621,8 @@ void plan_free(Plan *p) {
                     p->d_chirp32, p->d_bfwd32, p->d_binv32, p->d_phase64, p->d_phase32,
                     p->d_map64, p->d_map32, p->d_ninv64, p->d_ninv32, p->d_minv64,
                     p->d_minv32, p->d_diagT, p->d_diagP, p->d_wpairT, p->d_wpairP,
-                    p->d_ltab64, p->d_ltab32, p->d_scal, p->d_part, p->d_lsum, p->d_stage};
+                    p->d_ltab64, p->d_ltab32, p->d_scal, p->d_part, p->d_lsum, p->d_stage,
+                    p->d_ls2_64, p->d_st2_64, p->d_ls2_32, p->d_st2_32};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (int i = 0; i < 7; ++i)

@@ -15,7 +15,7 @@
 
 namespace shtg {
 
-#define RFFT_THREADS 256
+#define RFFT_THREADS 512
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -30,7 +30,7 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 }
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 
-// e^{i pi q / n} for integer q in [0, 2n)
+// e^{i pi q / n} for integer q in [0, n)
 __device__ __forceinline__ float2 phase_pi(int q, int n, float) {
     float s, c;
     sincospif((float)q / (float)n, &s, &c);
@@ -138,17 +138,39 @@ __global__ void __launch_bounds__(RFFT_THREADS) k_ring(const RingArgs<T> a) {
             // ---- fold F into the length-n spectrum of z = f_N + i f_S
             const C *Fn = a.FG + (int64_t)q * (L + 1) * a.nring + rn;
             const C *Fs = a.FG + (int64_t)q * (L + 1) * a.nring + rs;
+            // H(k) = e^{i pi s k / n} [ sum_t (-1)^{s t} F(k + t n)
+            //                         + sum_t (-1)^{s (t+1)} conj F(n - k + t n) ]
+            // (phi0 = s pi / n): one phase per bin, a sign per folded term.
             for (int k = threadIdx.x; k < n; k += blockDim.x) {
                 C hn = zero, hs = zero;
+                T sg = T(1);
                 for (int mm = k; mm <= L; mm += n) {
-                    const C ph = f.shift ? phase_pi((f.shift * mm) % (2 * n), n, T(0)) : C{T(1), T(0)};
-                    hn = cadd(hn, cmul(Fn[(int64_t)mm * a.nring], ph));
-                    if (!single) hs = cadd(hs, cmul(Fs[(int64_t)mm * a.nring], ph));
+                    const C vn = Fn[(int64_t)mm * a.nring];
+                    hn.x += sg * vn.x;
+                    hn.y += sg * vn.y;
+                    if (!single) {
+                        const C vs = Fs[(int64_t)mm * a.nring];
+                        hs.x += sg * vs.x;
+                        hs.y += sg * vs.y;
+                    }
+                    if (f.shift) sg = -sg;
                 }
+                sg = f.shift ? T(-1) : T(1);
                 for (int mm = (k == 0 ? n : n - k); mm <= L; mm += n) {
-                    const C ph = f.shift ? phase_pi((f.shift * mm) % (2 * n), n, T(0)) : C{T(1), T(0)};
-                    hn = cadd(hn, cconj(cmul(Fn[(int64_t)mm * a.nring], ph)));
-                    if (!single) hs = cadd(hs, cconj(cmul(Fs[(int64_t)mm * a.nring], ph)));
+                    const C vn = Fn[(int64_t)mm * a.nring];
+                    hn.x += sg * vn.x;
+                    hn.y -= sg * vn.y;
+                    if (!single) {
+                        const C vs = Fs[(int64_t)mm * a.nring];
+                        hs.x += sg * vs.x;
+                        hs.y -= sg * vs.y;
+                    }
+                    if (f.shift) sg = -sg;
+                }
+                if (f.shift) {
+                    const C ph = phase_pi(k, n, T(0));
+                    hn = cmul(hn, ph);
+                    hs = cmul(hs, ph);
                 }
                 const C z = {hn.x - hs.y, hn.y + hs.x};
                 buf[k] = f.blue ? cmul(z, cconj(chirp[k])) : z;
@@ -211,19 +233,32 @@ __global__ void __launch_bounds__(RFFT_THREADS) k_ring(const RingArgs<T> a) {
         // ---- unfold: G(m) = e^{-i m phi0} Y(m mod n), split north / south
         C *Gn = a.FG + (int64_t)q * (L + 1) * a.nring + rn;
         C *Gs = a.FG + (int64_t)q * (L + 1) * a.nring + rs;
-        for (int mm = threadIdx.x; mm <= L; mm += blockDim.x) {
-            const int k = mm % n;
+        // G(k + t n) = (-1)^{s t} e^{-i pi s k / n} Y(k), one phase per bin
+        const int nk = min(n, L + 1);
+        for (int k = threadIdx.x; k < nk; k += blockDim.x) {
             const int k2 = (n - k) % n;
             C w1 = buf[k], w2 = buf[k2];
             if (f.blue) {
                 w1 = cmul(w1, chirp[k]);
                 w2 = cmul(w2, chirp[k2]);
             }
-            const C yn = {T(0.5) * (w1.x + w2.x), T(0.5) * (w1.y - w2.y)};
-            const C ys = {T(0.5) * (w1.y + w2.y), T(-0.5) * (w1.x - w2.x)};
-            const C ph = f.shift ? cconj(phase_pi((f.shift * mm) % (2 * n), n, T(0))) : C{T(1), T(0)};
-            Gn[(int64_t)mm * a.nring] = cmul(yn, ph);
-            if (!single) Gs[(int64_t)mm * a.nring] = cmul(ys, ph);
+            C yn = {T(0.5) * (w1.x + w2.x), T(0.5) * (w1.y - w2.y)};
+            C ys = {T(0.5) * (w1.y + w2.y), T(-0.5) * (w1.x - w2.x)};
+            if (f.shift) {
+                const C ph = cconj(phase_pi(k, n, T(0)));
+                yn = cmul(yn, ph);
+                ys = cmul(ys, ph);
+            }
+            for (int mm = k; mm <= L; mm += n) {
+                Gn[(int64_t)mm * a.nring] = yn;
+                if (!single) Gs[(int64_t)mm * a.nring] = ys;
+                if (f.shift) {
+                    yn.x = -yn.x;
+                    yn.y = -yn.y;
+                    ys.x = -ys.x;
+                    ys.y = -ys.y;
+                }
+            }
         }
         __syncthreads();
     }

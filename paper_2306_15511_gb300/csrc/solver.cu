@@ -61,11 +61,15 @@ __global__ void k_rhs_pix(const double *__restrict__ d, const double *__restrict
     double *o = out + (int64_t)orow * npix;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix;
          p += (int64_t)gridDim.x * blockDim.x) {
+        // explicit roundings: host-staged inputs (two passes) and device inputs
+        // (one pass) give bit-identical sums
         const double w = wv[p];
-        double v = 0.0;
-        if (d) v += w * d[(int64_t)row * npix + p];
-        if (w2) v += sqrt(w) * w2[(int64_t)row * npix + p];
-        o[p] = accumulate ? o[p] + v : v;
+        const double t1 = d ? __dmul_rn(w, d[(int64_t)row * npix + p]) : 0.0;
+        const double t2 = w2 ? __dmul_rn(sqrt(w), w2[(int64_t)row * npix + p]) : 0.0;
+        double v = accumulate ? o[p] : 0.0;
+        if (d) v = __dadd_rn(v, t1);
+        if (w2) v = __dadd_rn(v, t2);
+        o[p] = v;
     }
 }
 
@@ -396,6 +400,35 @@ __global__ void k_correct(double2 *__restrict__ x, const float2 *__restrict__ d,
         xv.y += s * (double)v.y;
         x[(int64_t)b * per + i] = xv;
     }
+}
+
+// v *= f_b per realization (FP32 search direction after a residual replacement)
+__global__ void k_scale_vec(float2 *__restrict__ v, int64_t per, const double *__restrict__ f) {
+    const int b = blockIdx.y;
+    const float s = (float)f[b];
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float2 x = v[(int64_t)b * per + i];
+        x.x *= s;
+        x.y *= s;
+        v[(int64_t)b * per + i] = x;
+    }
+}
+
+// after a residual replacement: new rz, rr from the partials; tol2 per realization
+__global__ void k_scal_reliable(const double *__restrict__ part, double *__restrict__ scal, int nb,
+                                const double *__restrict__ tol2) {
+    const int b = threadIdx.x;
+    if (b >= nb) return;
+    double *s = scal + b * 16;
+    const double rz = sum_part(part, b, 2, 0), rr = sum_part(part, b, 2, 1);
+    s[S_RZ] = rz;
+    s[S_RR] = rr;
+    s[S_BB] = 1.0;                       // the FP32 residual is normalized to 1
+    s[S_TOL2] = tol2[b];
+    s[S_ACTIVE] = (tol2[b] >= 0.0 && rr > 0.0) ? 1.0 : 0.0;
+    s[S_BAD] = (isfinite(rr) && isfinite(rz)) ? s[S_BAD] : 1.0;
+    s[S_ALPHA] = s[S_BETA] = 0.0;
 }
 
 // ------------------------------------------------------------ log-posterior
@@ -737,6 +770,112 @@ static Solve make_solve(Plan *p, int nb, int nc, cudaStream_t st) {
     return s;
 }
 
+// FP32 PCG with reliable updates (residual replacement).  The iteration runs
+// on FP32 vectors normalized per realization; x accumulates in FP64.  When a
+// realization's FP32 residual has dropped by the factor delta (or reached the
+// target), the FP64 residual r = b - A x is recomputed with the FP64
+// transforms and replaces the FP32 one; the search direction is kept
+// (rescaled), so the Krylov progress survives the update.  Converged
+// realizations are frozen.  On return rr holds the final FP64 ||r||^2.
+static int mixed_solve(Solve &s, const shtg_cg_opts &opt, const std::vector<double> &bb,
+                       std::vector<double> &rr, shtg_cg_stats *stt) {
+    Plan *p = s.p;
+    cudaStream_t st = s.st;
+    const int nb = s.nb;
+    double2 *B = p->v64[0], *X = p->v64[1], *R = p->v64[2], *Tt = p->v64[6];
+    float2 *r32 = p->v32[0], *z32 = p->v32[1], *p32 = p->v32[2], *q32 = p->v32[3], *x32 = p->v32[4];
+    const float *minv = p->d_minv32;
+    // per-realization scalars on the device: [0,nb) 1/scale, [nb,2nb) FP32 target^2,
+    // [2nb,3nb) direction rescale, [3nb,4nb) scale
+    double *d_sc = p->d_part + 4 * (int64_t)p->max_batch * SHTG_RED_BLOCKS;
+    const size_t vb32 = sizeof(float2) * (size_t)s.nvec;
+    const double delta = opt.reliable_delta;
+    std::vector<double> scale(nb, 0.0), sc(4 * nb);
+    std::vector<char> done(nb, 0);
+    SHTG_CUDA(cudaMemsetAsync(X, 0, sizeof(double2) * (size_t)s.nvec, st));
+    SHTG_CUDA(cudaMemcpyAsync(R, B, sizeof(double2) * (size_t)s.nvec, cudaMemcpyDeviceToDevice, st));
+    rr = bb;
+    int it = 0, first = 1;
+    for (;;) {
+        // ---- residual replacement (the first pass starts the iteration)
+        int active = 0;
+        for (int b = 0; b < nb; ++b) {
+            done[b] = bb[b] == 0.0 || rr[b] <= opt.tol * opt.tol * bb[b];
+            const double nr = sqrt(rr[b]);
+            const double old = scale[b];
+            scale[b] = done[b] ? 0.0 : nr;
+            sc[b] = done[b] ? 0.0 : 1.0 / nr;
+            // FP32 target: ||r32|| <= max(delta, tol ||b|| / scale); -1 = frozen
+            const double t = done[b] ? -1.0 : std::max(delta, opt.tol * sqrt(bb[b]) / nr);
+            sc[nb + b] = t < 0 ? -1.0 : t * t;
+            sc[2 * nb + b] = (done[b] || old == 0.0) ? 0.0 : old / nr;
+            sc[3 * nb + b] = scale[b];
+            active += !done[b];
+        }
+        if (!active || it >= opt.maxiter) break;
+        SHTG_CUDA(cudaMemcpyAsync(d_sc, sc.data(), sizeof(double) * 4 * nb, cudaMemcpyHostToDevice, st));
+        k_scale_down<<<s.vgrid, RT, 0, st>>>(R, r32, s.per, d_sc);
+        if (first) SHTG_CUDA(cudaMemsetAsync(x32, 0, vb32, st));
+        else k_scale_vec<<<s.vgrid, RT, 0, st>>>(p32, s.per, d_sc + 2 * nb);
+        k_update<float, true><<<s.rgrid, RT, 0, st>>>(nullptr, r32, z32, nullptr, nullptr, minv, s.nc,
+                                                     s.nalm, p->d_mofidx, p->d_scal, p->d_part);
+        k_scal_reliable<<<1, 1024, 0, st>>>(p->d_part, p->d_scal, nb, d_sc + nb);
+        p->prof.launches += first ? 3 : 4;
+        SHTG_CHECK_LAUNCH("reliable update");
+        // the search direction is kept (rescaled to the new normalization); only
+        // the first pass starts it from z
+        if (first) SHTG_CUDA(cudaMemcpyAsync(p32, z32, vb32, cudaMemcpyDeviceToDevice, st));
+        first = 0;
+        // ---- FP32 iterations until some realization wants a replacement
+        for (;;) {
+            const int nrun = std::min(std::max(1, opt.check_every), opt.maxiter - it);
+            for (int k = 0; k < nrun; ++k) {
+                SHTG_TRY(matvec<float>(s, p32, q32));
+                prof_begin(p, K_VEC, st);
+                k_dot<float2><<<s.rgrid, RT, 0, st>>>(p32, q32, s.nc, s.nalm, p->d_mofidx, p->d_part, 0, 1);
+                k_scal_alpha<<<1, 1024, 0, st>>>(p->d_part, p->d_scal, nb);
+                k_update<float, false><<<s.rgrid, RT, 0, st>>>(x32, r32, z32, p32, q32, minv, s.nc,
+                                                               s.nalm, p->d_mofidx, p->d_scal, p->d_part);
+                k_scal_beta<<<1, 1024, 0, st>>>(p->d_part, p->d_scal, nb);
+                k_pupdate<float2><<<dim3(grid_1d(s.per).x, nb), RT, 0, st>>>(p32, z32, s.nc, s.nalm, p->d_scal);
+                prof_end(p, st, 5);
+                SHTG_CHECK_LAUNCH("pcg iteration");
+            }
+            it += nrun;
+            SHTG_CUDA(cudaMemcpyAsync(p->h_pinned, p->d_scal, sizeof(double) * 16 * nb,
+                                      cudaMemcpyDeviceToHost, st));
+            SHTG_CUDA(cudaStreamSynchronize(st));
+            int want = 0, still = 0;
+            for (int b = 0; b < nb; ++b) {
+                const double *h = p->h_pinned + b * 16;
+                if (h[S_BAD] != 0.0) {
+                    set_error("non-finite or non-positive curvature in the FP32 PCG");
+                    return SHTG_ERR_NONFINITE;
+                }
+                if (done[b]) continue;
+                const bool act = h[S_ACTIVE] != 0.0;
+                still += act;
+                if (!act || h[S_RR] <= delta * delta) want = 1;
+            }
+            if (want || !still || it >= opt.maxiter) break;
+        }
+        stt->iterations = it;
+        // ---- x += scale * x32 ; R = B - A X in FP64
+        k_correct<<<s.vgrid, RT, 0, st>>>(X, x32, s.per, d_sc + 3 * nb);
+        p->prof.launches += 1;
+        SHTG_CHECK_LAUNCH("k_correct");
+        SHTG_CUDA(cudaMemsetAsync(x32, 0, vb32, st));
+        SHTG_TRY(matvec<double>(s, X, Tt));
+        stt->fp64_matvecs++;
+        stt->outer_steps++;
+        k_resid<<<grid_1d(s.nvec), RT, 0, st>>>(B, Tt, R, s.nvec);
+        p->prof.launches += 1;
+        SHTG_TRY(norms2(s, R, rr));
+    }
+    stt->iterations = it;
+    return SHTG_OK;
+}
+
 int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_opts *o,
               shtg_cg_stats *stats, cudaStream_t st) {
     SHTG_TRY(check_problem(p, pr));
@@ -752,8 +891,7 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
     }
     if (!(opt.tol > 0)) opt.tol = 1e-6;
     if (opt.maxiter <= 0) opt.maxiter = 1000;
-    if (!(opt.inner_tol > 0)) opt.inner_tol = 1e-3;
-    if (opt.inner_maxiter <= 0) opt.inner_maxiter = 200;
+    if (!(opt.reliable_delta > 0 && opt.reliable_delta < 1)) opt.reliable_delta = 1e-2;
     if (opt.check_every <= 0) opt.check_every = 4;
     const int host = (opt.flags & SHTG_HOST_INPUTS) ? 1 : 0;
     if (!pr->d || !pr->w1 || !pr->w2 || !alm_out) {
@@ -820,47 +958,7 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
         p->prof.launches += 1;
         SHTG_TRY(norms2(s, R, rr));
     } else {
-        // FP64 iterative refinement around FP32 PCG
-        SHTG_CUDA(cudaMemsetAsync(X, 0, sizeof(double2) * (size_t)s.nvec, st));
-        SHTG_CUDA(cudaMemcpyAsync(R, B, sizeof(double2) * (size_t)s.nvec, cudaMemcpyDeviceToDevice, st));
-        rr = bb;
-        double *d_sc = p->d_part + 4 * (int64_t)p->max_batch * SHTG_RED_BLOCKS;  // 2 nb doubles
-        int total_inner = 0;
-        for (int outer = 0;; ++outer) {
-            bool done = true;
-            std::vector<double> sc(2 * nb);
-            for (int b = 0; b < nb; ++b) {
-                const bool conv = bb[b] == 0.0 || rr[b] <= opt.tol * opt.tol * bb[b];
-                if (!conv) done = false;
-                const double nr = sqrt(rr[b]);
-                sc[b] = (conv || nr == 0.0) ? 0.0 : 1.0 / nr;      // inverse scale
-                sc[nb + b] = (conv || nr == 0.0) ? 0.0 : nr;       // scale
-            }
-            if (done || total_inner >= opt.maxiter) break;
-            SHTG_CUDA(cudaMemcpyAsync(d_sc, sc.data(), sizeof(double) * 2 * nb, cudaMemcpyHostToDevice, st));
-            // right-hand side of the FP32 solve: r / ||r|| per realization, held in
-            // the idle FP64 scratch vector (pcg<float> owns v32[0..3]; v32[4] = delta)
-            float2 *rhs32 = reinterpret_cast<float2 *>(Tt);
-            k_scale_down<<<s.vgrid, RT, 0, st>>>(R, rhs32, s.per, d_sc);
-            p->prof.launches += 1;
-            SHTG_CHECK_LAUNCH("k_scale_down");
-            int iters = 0, conv = 0;
-            rc = pcg<float>(s, rhs32, p->v32[4], opt.inner_tol,
-                            std::min(opt.inner_maxiter, opt.maxiter - total_inner), opt.check_every,
-                            &iters, &conv);
-            total_inner += iters;
-            if (rc != SHTG_OK) return rc;
-            k_correct<<<s.vgrid, RT, 0, st>>>(X, p->v32[4], s.per, d_sc + nb);
-            p->prof.launches += 1;
-            SHTG_CHECK_LAUNCH("k_correct");
-            SHTG_TRY(matvec<double>(s, X, Tt));
-            stt.fp64_matvecs++;
-            k_resid<<<grid_1d(s.nvec), RT, 0, st>>>(B, Tt, R, s.nvec);
-            p->prof.launches += 1;
-            SHTG_TRY(norms2(s, R, rr));
-            stt.outer_steps++;
-        }
-        stt.iterations = total_inner;
+        SHTG_TRY(mixed_solve(s, opt, bb, rr, &stt));
     }
     double worst = 0.0;
     int conv_all = 1;

@@ -117,6 +117,7 @@ def test_host_inputs_match_device_inputs():
     xh, st = plan.cg_sample(p.cl, p.bl, np.ascontiguousarray(p.ninv), np.ascontiguousarray(d[None]),
                             np.ascontiguousarray(p.w1[None]), np.ascontiguousarray(p.w2[None]),
                             tol=1e-8, mode="fp64")
+    # host inputs are staged through the same kernels with explicit roundings
     assert np.array_equal(xh.numpy()[0], xd)
 
 
