@@ -2,16 +2,22 @@
 """Benchmark: constrained-realization sampling (Eq. mapmakingeq of arXiv
 2306.15511, Sect. 2.2.1) at N_side = 1024, l_max = 2048.
 
-Workload (one "step"): 8 T+E+B realizations sharing C_l, beam and N^-1
-(hits-weighted noise, |b| < 20 deg mask + 200 holes, 10' beam), one full
-cg_sample call: RHS assembly in FP64, preconditioner, FP32 PCG inside FP64
-iterative refinement to a true relative residual of 1e-6.  Inputs are
-synthetic (seeded Philox), resident in HBM and larger than L2.
+Workload: 8 T+E+B realizations sharing C_l, beam and N^-1 (hits-weighted
+noise, |b| < 20 deg mask + 200 holes, 10' beam).  One "step" is one
+cg_sample call with a fixed iteration budget: RHS assembly with the FP64
+transforms, preconditioner, then --iters-per-step batched mixed-precision
+PCG iterations (FP32 operator applications) with FP64 residual
+replacements (reliable updates), the last one at the end of the step.
+Inputs are synthetic (seeded Philox), resident in HBM and larger than L2.
 
-value = batched CG iterations per second over the whole job (each iteration
-is one application of the operator to all realizations: FP32 inner
-iterations plus FP64 refinement applications), summed over ranks.
-Ranks run independent replicas (weak scaling, no data-path collective).
+value = batched CG iterations per second over the whole job (an iteration
+applies the operator to all 8 realizations; FP64 residual replacements are
+counted as iterations too), summed over ranks.  Ranks run independent
+replicas (weak scaling, no data-path collective).
+
+The full solve to a true FP64 relative residual of 1e-6 (time_to_1e-6) is
+measured once after the timed steps, and the plain FP64 PCG per-iteration
+time on the same problem gives its time-to-1e-6 for comparison.
 
 --impl reference times the FP64 CPU oracle (test infrastructure) on a
 bounded ring sample of the same workload and extrapolates the same metric.
@@ -148,41 +154,62 @@ def make_inputs(plan, device, seed_shift=0):
 
 
 # ----------------------------------------------------------- CPU baseline
-def oracle_sample(nsub_stride=32, repeats=1):
-    """Time one T+E+B operator application of the FP64 oracle restricted to
-    every ``nsub_stride``-th ring of the N_side 1024 grid and extrapolate to a
-    batched CG iteration (8 realizations, all rings)."""
+_ORACLE = {}
+
+
+def _oracle_problem(nsub_stride=32):
+    """The config-4 operator (T+E+B, N_side 1024, l_max 2048) for the FP64 CPU
+    oracle, restricted to every nsub_stride-th ring, and one alm vector."""
+    if nsub_stride in _ORACLE:
+        return _ORACLE[nsub_stride]
     from inputs import configs as C
+    from inputs import philox as px
     from oracle import sht as osht
     from oracle import solver as osol
     g = osht.healpix(NSIDE)
     rings = np.arange(0, g.nring, nsub_stride)
     sub = g.subset(rings)
-    p = C.config(4, batch=1, nside=NSIDE, lmax=LMAX)[0]
-    ninv = np.stack([np.concatenate([p.ninv[c][g.ofs[r]:g.ofs[r] + g.nphi[r]] for r in rings])
-                     for c in range(2)])
-    prob = osol.Problem(sub, LMAX, p.cl, p.bl, ninv)
-    x = p.signal_alm
+    tt = C.cl_damped(LMAX)
+    ee = 0.05 * tt
+    cl4 = np.stack([tt, ee, 1e-3 * ee, 0.3 * np.sqrt(tt * ee)])
+    bl = C.gauss_beam(LMAX, 10.0 * C.ARCMIN)
+    z, phi = C.pixel_centres(NSIDE)
+    hits = C.hits_proxy(z, phi)
+    masked = C.latitude_cut(z, 20.0) | C.point_source_holes(z, phi, 200, 1.0, 4)
+    ninv = np.stack([np.where(masked, 0.0, hits / 30.0 ** 2), np.where(masked, 0.0, hits / 42.0 ** 2)])
+    ninv_sub = np.stack([np.concatenate([ninv[c][g.ofs[r]:g.ofs[r] + g.nphi[r]] for r in rings])
+                         for c in range(2)])
+    prob = osol.Problem(sub, LMAX, cl4, bl, ninv_sub)
+    x = np.stack([C.white_alm(LMAX, 9, px.STREAM_W1, k * 2 * C.nalm(LMAX)) for k in range(3)])
+    _ORACLE[nsub_stride] = (prob, x, g.nring, rings.size)
+    return _ORACLE[nsub_stride]
+
+
+def oracle_sample(nsub_stride=32, repeats=1):
+    """Time one T+E+B operator application of the FP64 oracle restricted to
+    every ``nsub_stride``-th ring of the N_side 1024 grid and extrapolate to a
+    batched CG iteration (8 realizations, all rings)."""
+    prob, x, nring, nsub = _oracle_problem(nsub_stride)
     times = []
     for _ in range(repeats):
         t0 = time.perf_counter()
         prob.matvec(x)
         times.append(time.perf_counter() - t0)
     t = min(times)
-    scale = g.nring / float(rings.size)
+    scale = nring / float(nsub)
     per_iter = t * scale * NB
     return {"value": 1.0 / per_iter, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": (f"one FP64 T+E+B operator application of 1 realization on {rings.size} of "
-                       f"{g.nring} rings (every {nsub_stride}th), {t:.2f} s, extrapolated x"
-                       f"{scale:.1f} rings x {NB} realizations")}
+            "sample": (f"one FP64 T+E+B operator application of 1 realization on {nsub} of "
+                       f"{nring} rings (every {nsub_stride}th ring), {t:.2f} s; extrapolated "
+                       f"x{scale:.1f} for all rings and x{NB} realizations")}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    for _ in range(max(0, args.warmup if args.warmup < 1 else 1)):
-        pass
+    for _ in range(min(args.warmup, 1)):
+        oracle_sample(repeats=1)
     vals = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
@@ -238,8 +265,9 @@ def run_gpu(args):
 
     plan = Plan(nside=NSIDE, lmax=LMAX, max_batch=NB, spin2=True)
     inp = make_inputs(plan, dev, seed_shift=rank)
-    kw = dict(tol=1e-6, mode="mixed", maxiter=args.maxiter, reliable_delta=args.reliable_delta,
-              check_every=args.check_every)
+    kw = dict(tol=1e-6, mode="mixed", maxiter=args.iters_per_step,
+              reliable_delta=args.reliable_delta, check_every=args.check_every,
+              allow_not_converged=True)
     out = torch.empty(NB, 3, plan.nalm, dtype=torch.complex128, device=dev)
 
     def step(profile=False):
@@ -302,7 +330,7 @@ def run_gpu(args):
     # -------------------------------------------------------------- extras
     extras = {}
     if not args.no_extras:
-        extras = measure_extras(plan, inp, dev, kw)
+        extras = measure_extras(plan, inp, dev, kw, full_solve=not args.no_full_solve)
 
     # ------------------------------------------------------------ roofline
     peaks, src = measured_peaks()
@@ -339,16 +367,17 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": {"workload": f"T+E+B constrained realizations, HEALPix N_side={NSIDE}, "
                                f"l_max={LMAX}, batch {NB} per GPU, mixed FP32 PCG + FP64 "
-                               f"refinement to 1e-6",
+                               f"residual replacement, tol 1e-6, {args.iters_per_step} "
+                               f"iterations per step",
+                   "iters_per_step": args.iters_per_step,
                    "global_batch": NB * world, "fsky": inp["fsky"], "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (d, w2: 2.4 GB each)"},
         "e2e": e2e, "gpu_launches": launches, "clocks": ck, "roofline": roof,
         "cpu_baseline": cpu,
-        "solve": {"inner_iterations_per_step": inner / len(stats),
-                  "fp64_matvecs_per_step": outer / len(stats),
-                  "rel_residual_max": max(s["rel_residual"] for s in stats),
-                  "converged": all(s["converged"] for s in stats),
-                  "time_to_1e-6_s": ms / 1000.0},
+        "step": {"fp32_iterations": inner / len(stats),
+                 "fp64_residual_replacements": outer / len(stats),
+                 "rel_residual_after_step": max(s["rel_residual"] for s in stats),
+                 "ms_rhs": float(np.mean([s["ms_rhs"] for s in stats]))},
         "kernel_share": {CLASS_NAMES[i]: round(float(kms[i]) / total_kms, 4)
                          for i in range(len(CLASS_NAMES)) if total_kms > 0},
         "kernel_ms_per_step": {CLASS_NAMES[i]: float(kms[i]) / len(stats) for i in range(8)},
@@ -361,11 +390,26 @@ def run_gpu(args):
     return 0
 
 
-def measure_extras(plan, inp, dev, kw):
-    """SHT pairs/s (one map, spin 0, FP32 and FP64) and the plain FP64 PCG
-    iteration rate on the same problem."""
+def measure_extras(plan, inp, dev, kw, full_solve=True):
+    """SHT pairs/s (one map, spin 0, FP32 and FP64), the full mixed solve to
+    1e-6 and the plain FP64 PCG iteration rate on the same problem."""
     import torch
     ex = {}
+    if full_solve:
+        kwf = dict(kw)
+        kwf["maxiter"] = 6000
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, st = plan.cg_sample(inp["cl"], inp["bl"], inp["ninv"], inp["d"], inp["w1"], inp["w2"],
+                               **kwf)
+        e1.record()
+        torch.cuda.synchronize()
+        ex["mixed_full_solve"] = {"time_to_1e-6_s": e0.elapsed_time(e1) / 1000.0,
+                                  "iterations": st["iterations"],
+                                  "fp64_matvecs": st["fp64_matvecs"],
+                                  "converged": bool(st["converged"]),
+                                  "rel_residual": st["rel_residual"], "ms_rhs": st["ms_rhs"]}
     g = torch.Generator(device=dev)
     g.manual_seed(0)
     for prec, ct, reps in (("fp32", torch.complex64, 10), ("fp64", torch.complex128, 3)):
@@ -389,11 +433,17 @@ def measure_extras(plan, inp, dev, kw):
                            tol=1e-6, mode="fp64", maxiter=nit, check_every=nit,
                            allow_not_converged=True, profile=True)
     el = time.perf_counter() - t0
-    ex["fp64_form"] = {"iterations": st["iterations"], "wall_s": el,
-                       "ms_rhs": st["ms_rhs"], "ms_solve": st["ms_solve"],
-                       "iters_per_s_solve_phase": st["iterations"] / (st["ms_solve"] / 1000.0)
-                       if st["ms_solve"] > 0 else None,
-                       "rel_residual_after": st["rel_residual"]}
+    per_it = (st["ms_solve"] / 1000.0) / max(1, st["iterations"])
+    ex["fp64_form"] = {"iterations_timed": st["iterations"], "wall_s": el,
+                       "ms_rhs": st["ms_rhs"], "s_per_iteration": per_it,
+                       "iters_per_s": 1.0 / per_it if per_it > 0 else None}
+    if "mixed_full_solve" in ex:
+        fs = ex["mixed_full_solve"]
+        # FP64 PCG needs about as many iterations as the mixed solver (they
+        # agree to within 3 % on the config-1 recipe); the FP64 form's time to
+        # 1e-6 is extrapolated from its measured per-iteration time
+        ex["fp64_form"]["time_to_1e-6_s_extrapolated"] = st["ms_rhs"] / 1000.0 + fs["iterations"] * per_it
+        ex["mixed_speedup_time_to_1e-6"] = ex["fp64_form"]["time_to_1e-6_s_extrapolated"] / fs["time_to_1e-6_s"]
     return ex
 
 
@@ -403,7 +453,8 @@ def main():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="shtg", choices=["shtg", "reference"])
-    ap.add_argument("--maxiter", type=int, default=3000)
+    ap.add_argument("--iters-per-step", type=int, default=160)
+    ap.add_argument("--no-full-solve", action="store_true")
     ap.add_argument("--reliable-delta", type=float, default=1e-2)
     ap.add_argument("--check-every", type=int, default=8)
     ap.add_argument("--e2e-steps", type=int, default=1)

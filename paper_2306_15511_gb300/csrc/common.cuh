@@ -115,9 +115,12 @@ struct Plan {
     double2 *d_chirp64 = nullptr, *d_bfwd64 = nullptr, *d_binv64 = nullptr;
     float2 *d_chirp32 = nullptr, *d_bfwd32 = nullptr, *d_binv32 = nullptr;
     size_t fft_smem64 = 0, fft_smem32 = 0;
+    int *d_ring_groups = nullptr;    // ring pairs: direct-FFT pairs first, then Bluestein pairs
+    int ring_group_count[2] = {0, 0};
+    int ring_group_logm[2] = {0, 0}; // largest log2 transform length in each group
 
     // workspace
-    double2 *d_phase64 = nullptr;  // [nmaps_max][lmax+1][nring] Fourier coefficients per ring
+    double2 *d_phase64 = nullptr;  // [nmaps_max][nring][lmax+1] Fourier coefficients per ring
     float2 *d_phase32 = nullptr;
     double *d_map64 = nullptr;     // [nmaps_max][npix] scratch maps
     float *d_map32 = nullptr;

@@ -43,7 +43,7 @@ template <typename T> struct LegArgs {
     int vjp;            // analysis: double the m > 0 outputs
     int64_t nalm;
     const C *alm;       // synthesis input / analysis output
-    C *F;               // [map][m][ring]
+    C *F;               // [map][ring][m]
     const T *beam;      // [lmax+1] or null
     const C *rec;       // (a, b) per alm index
     const C4 *s2c;      // spin-2 constants per alm index
@@ -299,20 +299,20 @@ __global__ void __launch_bounds__(LEG_THREADS) k_leg_synth(const LegArgs<T> a) {
         for (int k = 0; k < NM; ++k) {
             if (k >= nm) break;
             if (SPIN == 0) {
-                C *out = a.F + ((int64_t)(map0 + k) * (L + 1) + m) * a.nring;
-                out[rn] = cplx(accE[j][k][0] + accO[j][k][0], accE[j][k][1] + accO[j][k][1]);
+                C *out = a.F + (int64_t)(map0 + k) * a.nring * (L + 1) + m;
+                out[(int64_t)rn * (L + 1)] = cplx(accE[j][k][0] + accO[j][k][0], accE[j][k][1] + accO[j][k][1]);
                 if (rs != rn)
-                    out[rs] = cplx(accE[j][k][0] - accO[j][k][0], accE[j][k][1] - accO[j][k][1]);
+                    out[(int64_t)rs * (L + 1)] = cplx(accE[j][k][0] - accO[j][k][0], accE[j][k][1] - accO[j][k][1]);
             } else {
                 const T *E = accE[j][k], *O = accO[j][k];
                 // north: W + X over both classes; south: even W - X, odd X - W
-                C *oq = a.F + ((int64_t)(2 * (map0 + k)) * (L + 1) + m) * a.nring;
-                C *ou = a.F + ((int64_t)(2 * (map0 + k) + 1) * (L + 1) + m) * a.nring;
-                oq[rn] = cplx(E[0] + O[0] + E[4] + O[4], E[1] + O[1] + E[5] + O[5]);
-                ou[rn] = cplx(E[2] + O[2] + E[6] + O[6], E[3] + O[3] + E[7] + O[7]);
+                C *oq = a.F + (int64_t)(2 * (map0 + k)) * a.nring * (L + 1) + m;
+                C *ou = a.F + (int64_t)(2 * (map0 + k) + 1) * a.nring * (L + 1) + m;
+                oq[(int64_t)rn * (L + 1)] = cplx(E[0] + O[0] + E[4] + O[4], E[1] + O[1] + E[5] + O[5]);
+                ou[(int64_t)rn * (L + 1)] = cplx(E[2] + O[2] + E[6] + O[6], E[3] + O[3] + E[7] + O[7]);
                 if (rs != rn) {
-                    oq[rs] = cplx(E[0] - O[0] - E[4] + O[4], E[1] - O[1] - E[5] + O[5]);
-                    ou[rs] = cplx(E[2] - O[2] - E[6] + O[6], E[3] - O[3] - E[7] + O[7]);
+                    oq[(int64_t)rs * (L + 1)] = cplx(E[0] - O[0] - E[4] + O[4], E[1] - O[1] - E[5] + O[5]);
+                    ou[(int64_t)rs * (L + 1)] = cplx(E[2] - O[2] - E[6] + O[6], E[3] - O[3] - E[7] + O[7]);
                 }
             }
         }
@@ -386,9 +386,9 @@ __global__ void __launch_bounds__(LEG_THREADS) k_leg_analysis(const LegArgs<T> a
                 C gn = cplx(T(0), T(0)), gs = cplx(T(0), T(0));
                 if (ok && k < nm) {
                     const int row = (SPIN == 2) ? 2 * (map0 + k) + c : map0 + k;
-                    const C *g = a.F + ((int64_t)row * (L + 1) + m) * a.nring;
-                    gn = g[rn];
-                    if (rs != rn) gs = g[rs];
+                    const C *g = a.F + (int64_t)row * a.nring * (L + 1) + m;
+                    gn = g[(int64_t)rn * (L + 1)];
+                    if (rs != rn) gs = g[(int64_t)rs * (L + 1)];
                 }
                 gE[j][k][2 * c] = gn.x + gs.x;
                 gE[j][k][2 * c + 1] = gn.y + gs.y;

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <complex>
 #include <cstring>
+#include <algorithm>
 #include <map>
 
 #include "common.cuh"
@@ -561,6 +562,19 @@ static int build_fft_tables(Plan *p) {
     SHTG_TRY(upload(p->d_binv32, bi32));
     p->fft_smem64 = (size_t)Mmax * sizeof(double2);
     p->fft_smem32 = (size_t)Mmax * sizeof(float2);
+    std::vector<int> groups;
+    for (int g = 0; g < 2; ++g) {
+        p->ring_group_count[g] = 0;
+        p->ring_group_logm[g] = 0;
+        for (int r = 0; r < p->npairs; ++r)
+            if (p->h_rfft[r].blue == g) {
+                groups.push_back(r);
+                p->ring_group_count[g] += 1;
+                p->ring_group_logm[g] = std::max(p->ring_group_logm[g], p->h_rfft[r].logM);
+            }
+    }
+    SHTG_TRY(dalloc(p, &p->d_ring_groups, groups.size()));
+    SHTG_TRY(upload(p->d_ring_groups, groups));
     return SHTG_OK;
 }
 
@@ -622,7 +636,7 @@ void plan_free(Plan *p) {
                     p->d_map64, p->d_map32, p->d_ninv64, p->d_ninv32, p->d_minv64,
                     p->d_minv32, p->d_diagT, p->d_diagP, p->d_wpairT, p->d_wpairP,
                     p->d_ltab64, p->d_ltab32, p->d_scal, p->d_part, p->d_lsum, p->d_stage,
-                    p->d_ls2_64, p->d_st2_64, p->d_ls2_32, p->d_st2_32};
+                    p->d_ls2_64, p->d_st2_64, p->d_ls2_32, p->d_st2_32, p->d_ring_groups};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (int i = 0; i < 7; ++i)

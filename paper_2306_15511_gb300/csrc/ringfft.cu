@@ -52,11 +52,12 @@ template <typename T> struct RingArgs {
     const C *tw;
     int logmax;
     const C *chirp, *bfwd, *binv;
-    C *FG;            // [map][m][ring]
+    C *FG;            // [map][ring][m]
     T *map;           // [map][npix]
     const T *ninv;    // fused: [comp][npix]
     int nT;           // fused: rows [0, nT) use N^-1 component 0 (T), later rows component 1 (Q, U)
     int weighted;     // analysis: multiply by the quadrature weight
+    const int *pairs; // ring pairs handled by this launch (one CTA each)
 };
 
 // radix-2 DIF: natural order in, bit-reversed order out
@@ -124,7 +125,7 @@ __global__ void __launch_bounds__(RFFT_THREADS) k_ring(const RingArgs<T> a) {
     typedef typename VT<T>::C C;
     extern __shared__ unsigned char s_raw[];
     C *buf = reinterpret_cast<C *>(s_raw);
-    const int pr = blockIdx.x;
+    const int pr = a.pairs[blockIdx.x];
     const int rn = pr, rs = a.nring - 1 - pr;
     const bool single = (rn == rs);
     const RingFFT f = a.rf[rn];
@@ -136,8 +137,8 @@ __global__ void __launch_bounds__(RFFT_THREADS) k_ring(const RingArgs<T> a) {
     for (int q = 0; q < a.nmaps; ++q) {
         if (MODE == 0 || MODE == 2) {
             // ---- fold F into the length-n spectrum of z = f_N + i f_S
-            const C *Fn = a.FG + (int64_t)q * (L + 1) * a.nring + rn;
-            const C *Fs = a.FG + (int64_t)q * (L + 1) * a.nring + rs;
+            const C *Fn = a.FG + ((int64_t)q * a.nring + rn) * (L + 1);
+            const C *Fs = a.FG + ((int64_t)q * a.nring + rs) * (L + 1);
             // H(k) = e^{i pi s k / n} [ sum_t (-1)^{s t} F(k + t n)
             //                         + sum_t (-1)^{s (t+1)} conj F(n - k + t n) ]
             // (phi0 = s pi / n): one phase per bin, a sign per folded term.
@@ -145,11 +146,11 @@ __global__ void __launch_bounds__(RFFT_THREADS) k_ring(const RingArgs<T> a) {
                 C hn = zero, hs = zero;
                 T sg = T(1);
                 for (int mm = k; mm <= L; mm += n) {
-                    const C vn = Fn[(int64_t)mm * a.nring];
+                    const C vn = Fn[mm];
                     hn.x += sg * vn.x;
                     hn.y += sg * vn.y;
                     if (!single) {
-                        const C vs = Fs[(int64_t)mm * a.nring];
+                        const C vs = Fs[mm];
                         hs.x += sg * vs.x;
                         hs.y += sg * vs.y;
                     }
@@ -157,11 +158,11 @@ __global__ void __launch_bounds__(RFFT_THREADS) k_ring(const RingArgs<T> a) {
                 }
                 sg = f.shift ? T(-1) : T(1);
                 for (int mm = (k == 0 ? n : n - k); mm <= L; mm += n) {
-                    const C vn = Fn[(int64_t)mm * a.nring];
+                    const C vn = Fn[mm];
                     hn.x += sg * vn.x;
                     hn.y -= sg * vn.y;
                     if (!single) {
-                        const C vs = Fs[(int64_t)mm * a.nring];
+                        const C vs = Fs[mm];
                         hs.x += sg * vs.x;
                         hs.y -= sg * vs.y;
                     }
@@ -231,8 +232,8 @@ __global__ void __launch_bounds__(RFFT_THREADS) k_ring(const RingArgs<T> a) {
         if (f.blue) blue_conv(buf, logM, a.bfwd + f.bhat_off, a.tw, a.logmax);
         else fft_dit(buf, logM, a.tw, a.logmax, false);
         // ---- unfold: G(m) = e^{-i m phi0} Y(m mod n), split north / south
-        C *Gn = a.FG + (int64_t)q * (L + 1) * a.nring + rn;
-        C *Gs = a.FG + (int64_t)q * (L + 1) * a.nring + rs;
+        C *Gn = a.FG + ((int64_t)q * a.nring + rn) * (L + 1);
+        C *Gs = a.FG + ((int64_t)q * a.nring + rs) * (L + 1);
         // G(k + t n) = (-1)^{s t} e^{-i pi s k / n} Y(k), one phase per bin
         const int nk = min(n, L + 1);
         for (int k = threadIdx.x; k < nk; k += blockDim.x) {
@@ -250,8 +251,8 @@ __global__ void __launch_bounds__(RFFT_THREADS) k_ring(const RingArgs<T> a) {
                 ys = cmul(ys, ph);
             }
             for (int mm = k; mm <= L; mm += n) {
-                Gn[(int64_t)mm * a.nring] = yn;
-                if (!single) Gs[(int64_t)mm * a.nring] = ys;
+                Gn[mm] = yn;
+                if (!single) Gs[mm] = ys;
                 if (f.shift) {
                     yn.x = -yn.x;
                     yn.y = -yn.y;
@@ -292,13 +293,20 @@ static int launch_ring(Plan *p, RingArgs<T> a, cudaStream_t st) {
     a.ofs = p->d_ofs;
     a.wring = p->d_wring;
     a.logmax = p->fft_logmax;
-    const size_t smem = sizeof(typename VT<T>::C) << p->fft_logmax;
     auto kern = k_ring<T, MODE>;
-    if (smem > 48 * 1024)
-        SHTG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // direct (power-of-two) and Bluestein ring pairs run as separate launches so
+    // that each gets the shared memory its own transform length needs
     prof_begin(p, sizeof(T) == 8 ? K_RING64 : K_RING32, st);
-    kern<<<p->npairs, RFFT_THREADS, smem, st>>>(a);
-    prof_end(p, st);
+    for (int g = 0; g < 2; ++g) {
+        const int cnt = p->ring_group_count[g];
+        if (cnt == 0) continue;
+        const size_t smem = sizeof(typename VT<T>::C) << p->ring_group_logm[g];
+        if (smem > 48 * 1024)
+            SHTG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        a.pairs = p->d_ring_groups + (g ? p->ring_group_count[0] : 0);
+        kern<<<cnt, RFFT_THREADS, smem, st>>>(a);
+    }
+    prof_end(p, st, (p->ring_group_count[0] > 0) + (p->ring_group_count[1] > 0));
     SHTG_CHECK_LAUNCH("k_ring");
     return SHTG_OK;
 }

@@ -14,6 +14,13 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp64": 1e-10, "fp32": 1e-5}
+
+
+def tol_for(prec, L):
+    """FP64: 1e-10.  FP32: the l-recurrence carries O(l) roundings of unit
+    2^-24 (each step ~3 of them), so the relative L2 bound is 3 u l_max,
+    floored at 1e-5."""
+    return TOL["fp64"] if prec == "fp64" else max(1e-5, 3.0 * 2.0 ** -24 * L)
 CASES = [("healpix", 16, 40), ("healpix", 32, 64), ("healpix", 300, 400), ("gl", 33, 32),
          ("gl", 129, 128)]
 
@@ -147,7 +154,7 @@ def test_fullsize_nside1024_sampled_rings(prec):
     a = rand_alm(L, rng, (1,), lsc)
     ct, rt = _dt(prec)
     m = plan.alm2map(torch.tensor(a, dtype=ct, device="cuda")).cpu().numpy()[0]
-    assert _ring_err(m, g, FULL_RINGS, osht.alm2map(g.subset(FULL_RINGS), L, a[0])) < TOL[prec]
+    assert _ring_err(m, g, FULL_RINGS, osht.alm2map(g.subset(FULL_RINGS), L, a[0])) < tol_for(prec, L)
     assert _ring_err(m, g, POLAR_RINGS, osht.alm2map(g.subset(POLAR_RINGS), L, a[0])) < POLAR_TOL[prec]
     mp = rng.normal(size=(1, g.npix))
     ad = plan.alm2map_adjoint(torch.tensor(mp, dtype=rt, device="cuda")).cpu().numpy()[0]
@@ -155,7 +162,7 @@ def test_fullsize_nside1024_sampled_rings(prec):
     refa = osht.alm2map_adjoint(g, L, mp[0], mlist=mlist)
     ms = osht.ms_of(L)
     sel = np.isin(ms, mlist)
-    assert rel_l2(ad[sel], refa[sel]) < TOL[prec]
+    assert rel_l2(ad[sel], refa[sel]) < tol_for(prec, L)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
@@ -168,7 +175,7 @@ def test_fullsize_nside1024_spin2_sampled(prec):
     eb = rand_alm(L, rng, (1, 2), lsc)
     ct, rt = _dt(prec)
     qu = plan.alm2map(torch.tensor(eb, dtype=ct, device="cuda"), spin=2).cpu().numpy()[0]
-    for rings, tol in ((FULL_RINGS, TOL[prec]), (POLAR_RINGS, POLAR_TOL[prec])):
+    for rings, tol in ((FULL_RINGS, tol_for(prec, L)), (POLAR_RINGS, POLAR_TOL[prec])):
         Q, U = osht.alm2map_spin2(g.subset(rings), L, eb[0, 0], eb[0, 1])
         assert _ring_err(qu, g, rings, np.stack([Q, U])) < tol, rings[:3]
     mp = rng.normal(size=(1, 2, g.npix))
@@ -176,7 +183,7 @@ def test_fullsize_nside1024_spin2_sampled(prec):
     mlist = [0, 1, 2, 1000, 2048]
     E, B = osht.alm2map_spin2_adjoint(g, L, mp[0, 0], mp[0, 1], mlist=mlist)
     sel = np.isin(osht.ms_of(L), mlist)
-    assert rel_l2(ad[:, sel], np.stack([E[sel], B[sel]])) < TOL[prec]
+    assert rel_l2(ad[:, sel], np.stack([E[sel], B[sel]])) < tol_for(prec, L)
 
 
 def test_invalid_arguments_raise():
