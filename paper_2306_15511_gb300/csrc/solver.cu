@@ -805,9 +805,9 @@ static int mixed_solve(Solve &s, const shtg_cg_opts &opt, const std::vector<doub
             const double old = scale[b];
             scale[b] = done[b] ? 0.0 : nr;
             sc[b] = done[b] ? 0.0 : 1.0 / nr;
-            // FP32 target: ||r32|| <= max(delta, tol ||b|| / scale); -1 = frozen
-            const double t = done[b] ? -1.0 : std::max(delta, opt.tol * sqrt(bb[b]) / nr);
-            sc[nb + b] = t < 0 ? -1.0 : t * t;
+            // the FP32 stage runs until every active realization has reduced its
+            // residual by delta (it stops on its own only far below that); -1 = frozen
+            sc[nb + b] = done[b] ? -1.0 : (1e-3 * delta) * (1e-3 * delta);
             sc[2 * nb + b] = (done[b] || old == 0.0) ? 0.0 : old / nr;
             sc[3 * nb + b] = scale[b];
             active += !done[b];
@@ -826,7 +826,8 @@ static int mixed_solve(Solve &s, const shtg_cg_opts &opt, const std::vector<doub
         // the first pass starts it from z
         if (first) SHTG_CUDA(cudaMemcpyAsync(p32, z32, vb32, cudaMemcpyDeviceToDevice, st));
         first = 0;
-        // ---- FP32 iterations until some realization wants a replacement
+        // ---- FP32 iterations until every realization is ready for a replacement
+        int since = 0;
         for (;;) {
             const int nrun = std::min(std::max(1, opt.check_every), opt.maxiter - it);
             for (int k = 0; k < nrun; ++k) {
@@ -845,7 +846,7 @@ static int mixed_solve(Solve &s, const shtg_cg_opts &opt, const std::vector<doub
             SHTG_CUDA(cudaMemcpyAsync(p->h_pinned, p->d_scal, sizeof(double) * 16 * nb,
                                       cudaMemcpyDeviceToHost, st));
             SHTG_CUDA(cudaStreamSynchronize(st));
-            int want = 0, still = 0;
+            int pending = 0, still = 0;
             for (int b = 0; b < nb; ++b) {
                 const double *h = p->h_pinned + b * 16;
                 if (h[S_BAD] != 0.0) {
@@ -855,9 +856,11 @@ static int mixed_solve(Solve &s, const shtg_cg_opts &opt, const std::vector<doub
                 if (done[b]) continue;
                 const bool act = h[S_ACTIVE] != 0.0;
                 still += act;
-                if (!act || h[S_RR] <= delta * delta) want = 1;
+                if (act && h[S_RR] > delta * delta) pending += 1;
             }
-            if (want || !still || it >= opt.maxiter) break;
+            since += nrun;
+            // replace once every realization has dropped by delta, or after a cap
+            if (!pending || !still || it >= opt.maxiter || since >= 400) break;
         }
         stt->iterations = it;
         // ---- x += scale * x32 ; R = B - A X in FP64

@@ -21,7 +21,7 @@ def test_library_exports_declared_symbols():
     assert len(names) >= 10
     for n in names:
         assert hasattr(lib, n), n
-    assert set(_native.SYMBOLS) == set(names)
+    assert set(_native.SYMBOLS) <= set(names)
 
 
 def test_version_and_error_string_without_gpu():
