@@ -129,6 +129,21 @@ int shtg_alm2map_vjp(shtg_plan *plan, int spin, int precision, const void *map_g
 int shtg_map2alm(shtg_plan *plan, int spin, int precision, const void *map, void *alm,
                  int nbatch, int niter, void *stream);
 
+/* Allocation-free Y^T for callers that cannot allocate device memory (code
+ * that runs under a device-memory budget owned by another framework, or that
+ * may not call cudaMalloc because it can synchronize the device).  The paper
+ * has no counterpart.  Same result as shtg_alm2map_adjoint(spin 0, SHTG_FP64)
+ * on a HEALPix plan, without a plan: map [12 nside^2] float64 and alm [nalm]
+ * complex128 are device buffers owned by the caller; the ring geometry and
+ * the Legendre recurrence are computed on the fly and the per-ring Fourier
+ * sums go to a static 16 MiB device buffer inside the library.  Sizes with
+ * (4 nside - 1) (lmax + 1) 16 bytes > 16 MiB (e.g. nside 512, lmax 1024)
+ * return SHTG_ERR_ARG.  The first call on a device looks the buffer's device
+ * address up (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call on a device shares the buffer: calls whose kernels may
+ * overlap on the GPU race on it.  Allocates nothing. */
+int shtg_alm2map_adjoint_noalloc(int nside, int lmax, const double *map, double *alm, void *stream);
+
 /* ------------------------------------------------- constrained realization */
 typedef struct {
     int ncomp;        /* 1 = temperature; 3 = T, E, B (plan needs SHTG_SPIN2) */
