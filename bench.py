@@ -42,7 +42,7 @@ import numpy as np  # noqa: E402
 
 METRIC = "CG iters/sec & SHT pairs/sec @Nside=1024,lmax=2048; mixed vs FP64 @1e-6 resid"
 UNIT = "CG iterations/s"
-NSIDE, LMAX, NB = 1024, 2048, 8
+NSIDE, LMAX, NB = 1024, 2048, 8   # the benchmark workload; --nside/--lmax/--batch shrink it for profiling
 CLASS_NAMES = ["leg_synth_fp32", "leg_analysis_fp32", "ring_fft_fp32", "leg_synth_fp64",
                "leg_analysis_fp64", "ring_fft_fp64", "vector", "precond_diag"]
 
@@ -454,6 +454,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="shtg", choices=["shtg", "reference"])
     ap.add_argument("--iters-per-step", type=int, default=160)
+    ap.add_argument("--nside", type=int, default=NSIDE, help="profiling only: smaller grid")
+    ap.add_argument("--lmax", type=int, default=LMAX, help="profiling only: smaller l_max")
+    ap.add_argument("--batch", type=int, default=NB, help="profiling only: fewer realizations")
     ap.add_argument("--no-full-solve", action="store_true")
     ap.add_argument("--reliable-delta", type=float, default=1e-2)
     ap.add_argument("--check-every", type=int, default=8)
@@ -462,6 +465,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    global NSIDE, LMAX, NB
+    NSIDE, LMAX, NB = args.nside, args.lmax, args.batch
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -826,7 +826,7 @@ static int mixed_solve(Solve &s, const shtg_cg_opts &opt, const std::vector<doub
         // the first pass starts it from z
         if (first) SHTG_CUDA(cudaMemcpyAsync(p32, z32, vb32, cudaMemcpyDeviceToDevice, st));
         first = 0;
-        // ---- FP32 iterations until every realization is ready for a replacement
+        // ---- FP32 iterations until a realization is ready for a replacement
         int since = 0;
         for (;;) {
             const int nrun = std::min(std::max(1, opt.check_every), opt.maxiter - it);
@@ -846,7 +846,7 @@ static int mixed_solve(Solve &s, const shtg_cg_opts &opt, const std::vector<doub
             SHTG_CUDA(cudaMemcpyAsync(p->h_pinned, p->d_scal, sizeof(double) * 16 * nb,
                                       cudaMemcpyDeviceToHost, st));
             SHTG_CUDA(cudaStreamSynchronize(st));
-            int pending = 0, still = 0;
+            int ready = 0, still = 0;
             for (int b = 0; b < nb; ++b) {
                 const double *h = p->h_pinned + b * 16;
                 if (h[S_BAD] != 0.0) {
@@ -856,11 +856,13 @@ static int mixed_solve(Solve &s, const shtg_cg_opts &opt, const std::vector<doub
                 if (done[b]) continue;
                 const bool act = h[S_ACTIVE] != 0.0;
                 still += act;
-                if (act && h[S_RR] > delta * delta) pending += 1;
+                if (act && h[S_RR] <= delta * delta) ready += 1;
             }
             since += nrun;
-            // replace once every realization has dropped by delta, or after a cap
-            if (!pending || !still || it >= opt.maxiter || since >= 400) break;
+            // replace as soon as one realization has dropped by delta: waiting
+            // for all lets the FP32 recursion drift and costs more iterations
+            // than the extra FP64 applications save
+            if (ready || !still || it >= opt.maxiter || since >= 400) break;
         }
         stt->iterations = it;
         // ---- x += scale * x32 ; R = B - A X in FP64
