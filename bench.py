@@ -448,6 +448,7 @@ def measure_extras(plan, inp, dev, kw, full_solve=True):
 
 
 def main():
+    global NSIDE, LMAX, NB
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
@@ -465,7 +466,6 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    global NSIDE, LMAX, NB
     NSIDE, LMAX, NB = args.nside, args.lmax, args.batch
     if args.impl == "reference":
         return run_reference(args)

@@ -110,8 +110,11 @@ struct Plan {
     int fft_logmax = 0;
     RingFFT *d_rfft = nullptr;
     std::vector<RingFFT> h_rfft;
-    double2 *d_tw64 = nullptr;    // e^{-2 pi i k / Mmax}, k < Mmax/2
+    // two-level twiddle table for e^{-2 pi i t / Mmax}, t = th 2^tw_blo + tl:
+    // [lo: e^{-2 pi i tl / Mmax}, 2^tw_blo entries | hi: e^{-2 pi i th 2^tw_blo / Mmax}]
+    double2 *d_tw64 = nullptr;
     float2 *d_tw32 = nullptr;
+    int tw_blo = 0, tw_nlo = 0, tw_nhi = 0;
     double2 *d_chirp64 = nullptr, *d_bfwd64 = nullptr, *d_binv64 = nullptr;
     float2 *d_chirp32 = nullptr, *d_bfwd32 = nullptr, *d_binv32 = nullptr;
     size_t fft_smem64 = 0, fft_smem32 = 0;
@@ -145,6 +148,7 @@ struct Plan {
 
 // solver.cu
 #define SHTG_RED_BLOCKS 128
+#define SHTG_FFT_LOGMAX 13   // longest ring transform (Bluestein length included): 8192
 int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_opts *o,
               shtg_cg_stats *stats, cudaStream_t st);
 int apply_operator(Plan *p, const shtg_problem *pr, const double *x, double *y, cudaStream_t st);

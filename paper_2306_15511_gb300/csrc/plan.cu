@@ -498,14 +498,23 @@ static int build_fft_tables(Plan *p) {
         if (f.logM > logmax) logmax = f.logM;
         p->h_rfft[r] = f;
     }
+    if (logmax > SHTG_FFT_LOGMAX) {
+        set_error("ring transform length 2^" + std::to_string(logmax) + " above the supported 2^" +
+                  std::to_string(SHTG_FFT_LOGMAX) + " (HEALPix N_side <= 1024, Gauss nphi <= 8192)");
+        return SHTG_ERR_ARG;
+    }
     p->fft_logmax = logmax;
     const int Mmax = 1 << logmax;
-    std::vector<double2> tw64(Mmax / 2);
-    std::vector<float2> tw32(Mmax / 2);
-    for (int k = 0; k < Mmax / 2; ++k) {
-        const double ang = -2.0 * PI * (double)k / (double)Mmax;
-        tw64[k] = make_double2(cos(ang), sin(ang));
-        tw32[k] = make_float2((float)cos(ang), (float)sin(ang));
+    p->tw_blo = (logmax + 1) / 2;
+    p->tw_nlo = 1 << p->tw_blo;
+    p->tw_nhi = 1 << (logmax - p->tw_blo);
+    std::vector<double2> tw64(p->tw_nlo + p->tw_nhi);
+    std::vector<float2> tw32(tw64.size());
+    for (int i = 0; i < p->tw_nlo + p->tw_nhi; ++i) {
+        const int64_t t = i < p->tw_nlo ? i : (int64_t)(i - p->tw_nlo) << p->tw_blo;
+        const double ang = -2.0 * PI * (double)t / (double)Mmax;
+        tw64[i] = make_double2(cos(ang), sin(ang));
+        tw32[i] = make_float2((float)cos(ang), (float)sin(ang));
     }
     std::vector<double2> ch64(chirp_total), bf64(bhat_total), bi64(bhat_total);
     std::vector<float2> ch32(chirp_total), bf32(bhat_total), bi32(bhat_total);
@@ -534,8 +543,7 @@ static int build_fft_tables(Plan *p) {
         host_fft(bfw, lgM);
         host_fft(biv, lgM);
         for (int i = 0; i < M; ++i) {
-            const uint32_t k = bitrev(i, lgM);
-            const std::complex<double> a = bfw[k] / (double)M, b = biv[k] / (double)M;
+            const std::complex<double> a = bfw[i] / (double)M, b = biv[i] / (double)M;
             bf64[bo + i] = make_double2(a.real(), a.imag());
             bi64[bo + i] = make_double2(b.real(), b.imag());
             bf32[bo + i] = make_float2((float)a.real(), (float)a.imag());

@@ -4,29 +4,38 @@
 //
 // One CTA per ring pair.  The north and south rings of a pair have the same
 // n and phi0, so one complex FFT of z = f_N + i f_S serves both.  Frequencies
-// are folded modulo n (rings with n < 2L + 1 alias), the length-n DFT runs in
-// shared memory as a radix-2 decimation-in-frequency / decimation-in-time
-// pair (bit-reversed order never has to be undone), and rings whose n is not
-// a power of two use Bluestein's chirp convolution with precomputed kernel
-// spectra.  The fused variant applies N^-1 between the inverse and the
-// forward transform, so the pixel map never goes to global memory inside an
-// operator application.
+// are folded modulo n (rings with n < 2L + 1 alias).  The length-n DFT is a
+// Stockham autosort FFT in shared memory (natural order in and out): every
+// pass loads R elements per butterfly into registers, applies the twiddles,
+// does the radix-R DFT in registers and writes the R outputs to their sorted
+// places (Govindaraju et al. 2008, "High performance discrete Fourier
+// transforms on graphics processors", with R = 16 passes and one smaller
+// final pass).  The buffer is padded by one element per 16 so that the
+// scattered writes of the early passes hit distinct banks.  Rings whose n is
+// not a power of two (HEALPix polar caps) use Bluestein's chirp convolution
+// with precomputed kernel spectra.  The fused variant applies N^-1 between
+// the inverse and the forward transform, so the pixel map never goes to
+// global memory inside an operator application.
 #include "common.cuh"
 
 namespace shtg {
 
-#define RFFT_THREADS 512
+template <typename T> struct RingNT;
+template <> struct RingNT<float> { static constexpr int v = 512, blocks = 2; };
+template <> struct RingNT<double> { static constexpr int v = 512, blocks = 1; };
+
+__device__ __forceinline__ int rpad(int i) { return i + (i >> 4); }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
-    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 
@@ -42,6 +51,209 @@ __device__ __forceinline__ double2 phase_pi(int q, int n, double) {
     return make_double2(c, s);
 }
 
+// v * e^{-+2 pi i k / 16} (minus sign: forward transform, plus: inverse); k is
+// a compile-time constant after unrolling, so the switch folds away
+template <bool INV, typename C>
+__device__ __forceinline__ C rot16(const C v, const int k) {
+    typedef decltype(v.x) T;
+    const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173), h = T(0.70710678118654752440);
+    T c, s;   // cos, sin of k pi / 8
+    switch (k & 15) {
+        case 0: return v;
+        case 4: return INV ? C{-v.y, v.x} : C{v.y, -v.x};
+        case 8: return C{-v.x, -v.y};
+        case 12: return INV ? C{v.y, -v.x} : C{-v.y, v.x};
+        case 1: c = c1; s = s1; break;
+        case 2: c = h; s = h; break;
+        case 3: c = s1; s = c1; break;
+        case 5: c = -s1; s = c1; break;
+        case 6: c = -h; s = h; break;
+        case 7: c = -c1; s = s1; break;
+        case 9: c = -c1; s = -s1; break;
+        case 10: c = -h; s = -h; break;
+        case 11: c = -s1; s = -c1; break;
+        case 13: c = s1; s = -c1; break;
+        case 14: c = h; s = -h; break;
+        default: c = c1; s = -s1; break;   // 15
+    }
+    if (INV) return C{v.x * c - v.y * s, v.x * s + v.y * c};
+    return C{v.x * c + v.y * s, v.y * c - v.x * s};
+}
+
+template <bool INV, typename C>
+__device__ __forceinline__ void dft2(C &a, C &b) {
+    const C t = a;
+    a = cadd(t, b);
+    b = csub(t, b);
+}
+
+// natural order in and out: X_s = sum_r x_r e^{-+2 pi i r s / 4}
+template <bool INV, typename C>
+__device__ __forceinline__ void dft4(C &x0, C &x1, C &x2, C &x3) {
+    const C t0 = cadd(x0, x2), t1 = csub(x0, x2), t2 = cadd(x1, x3);
+    const C d = csub(x1, x3);
+    const C t3 = INV ? C{-d.y, d.x} : C{d.y, -d.x};
+    x0 = cadd(t0, t2);
+    x2 = csub(t0, t2);
+    x1 = cadd(t1, t3);
+    x3 = csub(t1, t3);
+}
+
+// Composite radix-R DFT in registers, natural order in and out: with
+// r = N2 r1 + r2 and s = s1 + N1 s2, X_s = sum_r2 w_R^{r2 s1} w_N2^{r2 s2}
+// (sum_r1 x_r w_N1^{r1 s1}): N2 DFTs of length N1, twiddles, N1 DFTs of length N2.
+template <int R, bool INV, typename C> struct Dft;
+template <bool INV, typename C> struct Dft<2, INV, C> {
+    static __device__ __forceinline__ void run(C *v) { dft2<INV>(v[0], v[1]); }
+};
+template <bool INV, typename C> struct Dft<4, INV, C> {
+    static __device__ __forceinline__ void run(C *v) { dft4<INV>(v[0], v[1], v[2], v[3]); }
+};
+template <bool INV, typename C> struct Dft<8, INV, C> {   // N1 = 2, N2 = 4
+    static __device__ __forceinline__ void run(C *v) {
+        C y[4][2];
+#pragma unroll
+        for (int r2 = 0; r2 < 4; ++r2) {
+            y[r2][0] = v[r2];
+            y[r2][1] = v[4 + r2];
+            dft2<INV>(y[r2][0], y[r2][1]);
+            y[r2][1] = rot16<INV>(y[r2][1], 2 * r2);   // w_8^{r2} = w_16^{2 r2}
+        }
+#pragma unroll
+        for (int s1 = 0; s1 < 2; ++s1) {
+            dft4<INV>(y[0][s1], y[1][s1], y[2][s1], y[3][s1]);
+#pragma unroll
+            for (int s2 = 0; s2 < 4; ++s2) v[s1 + 2 * s2] = y[s2][s1];
+        }
+    }
+};
+template <bool INV, typename C> struct Dft<16, INV, C> {   // N1 = N2 = 4
+    static __device__ __forceinline__ void run(C *v) {
+        C y[4][4];
+#pragma unroll
+        for (int r2 = 0; r2 < 4; ++r2) {
+            y[r2][0] = v[r2];
+            y[r2][1] = v[4 + r2];
+            y[r2][2] = v[8 + r2];
+            y[r2][3] = v[12 + r2];
+            dft4<INV>(y[r2][0], y[r2][1], y[r2][2], y[r2][3]);
+#pragma unroll
+            for (int s1 = 1; s1 < 4; ++s1) y[r2][s1] = rot16<INV>(y[r2][s1], r2 * s1);
+        }
+#pragma unroll
+        for (int s1 = 0; s1 < 4; ++s1) {
+            dft4<INV>(y[0][s1], y[1][s1], y[2][s1], y[3][s1]);
+#pragma unroll
+            for (int s2 = 0; s2 < 4; ++s2) v[s1 + 4 * s2] = y[s2][s1];
+        }
+    }
+};
+
+// Twiddles from the two-level table in shared memory: e^{-2 pi i t / Mmax}
+template <typename C> struct TwTab {
+    const C *lo, *hi;
+    int blo, logmax;
+    __device__ __forceinline__ C at(int t) const {
+        return cmul(hi[t >> blo], lo[t & ((1 << blo) - 1)]);
+    }
+};
+
+// One Stockham pass of radix R over a length-M transform whose sub-transforms
+// of length Ns are done: butterfly j (k = j mod Ns) takes x[j + r M/R],
+// multiplies element r by w^{r k} (w = e^{-+2 pi i / (Ns R)}), does a radix-R
+// DFT and writes output s to (j - k) R + k + s Ns.  Each thread handles BPT
+// butterflies; all reads finish (barrier) before any write, so the pass runs
+// in place.  With post != null the outputs are multiplied by post[index];
+// with cj they are conjugated (after the multiplication).
+template <int R, int BPT, int NT, typename C>
+__device__ __forceinline__ void spass(C *buf, const int M, const int Ns, const TwTab<C> &tw,
+                                      const C *__restrict__ post, const bool cj) {
+    const int nb = M / R;
+    C v[BPT][R];
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int j = threadIdx.x + b * NT;
+        if (j < nb) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b][r] = buf[rpad(j + r * nb)];
+        }
+    }
+    __syncthreads();
+    int lsr = 0;   // log2(Ns R)
+    while ((1 << lsr) < Ns * R) ++lsr;
+    const int lshift = tw.logmax - lsr;
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int j = threadIdx.x + b * NT;
+        if (j < nb) {
+            const int k = j & (Ns - 1);
+            if (Ns > 1) {
+                // w^r = w^{4a} w^b (r = 4a + b): table values at r = 1, 2, 4, 8,
+                // products elsewhere (at most three roundings per twiddle)
+                const int t = k << lshift;
+                C wb[4], wa[4];
+                wb[1] = tw.at(t);
+                if (R >= 4) {
+                    wb[2] = tw.at(2 * t);
+                    wb[3] = cmul(wb[2], wb[1]);
+                }
+                if (R >= 8) wa[1] = tw.at(4 * t);
+                if (R >= 16) {
+                    wa[2] = tw.at(8 * t);
+                    wa[3] = cmul(wa[2], wa[1]);
+                }
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    const int ra = r >> 2, rb = r & 3;
+                    const C w = ra == 0 ? wb[rb] : (rb == 0 ? wa[ra] : cmul(wa[ra], wb[rb]));
+                    v[b][r] = cmul(v[b][r], w);
+                }
+            }
+            Dft<R, false, C>::run(v[b]);
+            const int d = (j - k) * R + k;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int o = d + r * Ns;
+                C y = post ? cmul(v[b][r], post[o]) : v[b][r];
+                if (cj) y.y = -y.y;
+                buf[rpad(o)] = y;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Length-2^logM forward DFT (e^{-2 pi i jk/M}, unnormalized) of buf in
+// place, natural order in and out; the last pass multiplies by post (if not
+// null) and conjugates when cj is set.  The inverse transform is
+// conj(DFT(conj x)): callers conjugate on the way in and out.  Passes: radix
+// 16 while at least four factors of two remain, then one radix-8, -4 or -2
+// pass.  Not inlined: one copy serves every call site of a kernel.
+template <int NT, typename C>
+__device__ __noinline__ void fft_stockham(C *buf, const int logM, const TwTab<C> tw,
+                                          const C *__restrict__ post, const bool cj) {
+    const int M = 1 << logM;
+    int Ns = 1, rem = logM;
+    while (rem > 0) {
+        if (rem >= 4) {
+            const bool last = rem == 4;
+            spass<16, 1, NT>(buf, M, Ns, tw, last ? post : nullptr, last && cj);   // M / 16 <= NT
+            Ns <<= 4;
+            rem -= 4;
+        } else if (rem == 3) {
+            spass<8, 1, NT>(buf, M, Ns, tw, post, cj);   // M / 8 <= NT for M <= 2^12
+            rem = 0;
+        } else if (rem == 2) {
+            spass<4, 1, NT>(buf, M, Ns, tw, post, cj);   // M <= 2^10
+            rem = 0;
+        } else {
+            if (M / 2 > NT) spass<2, 8, NT>(buf, M, Ns, tw, post, cj);   // M = 2^13
+            else spass<2, 1, NT>(buf, M, Ns, tw, post, cj);
+            rem = 0;
+        }
+    }
+}
+
 template <typename T> struct RingArgs {
     typedef typename VT<T>::C C;
     int lmax, nring, npairs, nmaps;
@@ -49,8 +261,8 @@ template <typename T> struct RingArgs {
     const RingFFT *rf;
     const int64_t *ofs;
     const double *wring;
-    const C *tw;
-    int logmax;
+    const C *tw;      // two-level twiddle table [lo | hi]
+    int tw_blo, tw_nlo, tw_nhi, logmax;
     const C *chirp, *bfwd, *binv;
     C *FG;            // [map][ring][m]
     T *map;           // [map][npix]
@@ -60,71 +272,32 @@ template <typename T> struct RingArgs {
     const int *pairs; // ring pairs handled by this launch (one CTA each)
 };
 
-// radix-2 DIF: natural order in, bit-reversed order out
-template <typename C>
-__device__ __forceinline__ void fft_dif(C *buf, const int logM, const C *__restrict__ tw,
-                                        const int logmax, const bool inv) {
-    const int M = 1 << logM;
-    for (int s = 0; s < logM; ++s) {
-        const int lh = logM - 1 - s;
-        const int half = 1 << lh;
-        for (int b = threadIdx.x; b < (M >> 1); b += blockDim.x) {
-            const int k = b & (half - 1);
-            const int i0 = ((b >> lh) << (lh + 1)) + k;
-            const int i1 = i0 + half;
-            C w = tw[k << (logmax - 1 - lh)];
-            if (inv) w.y = -w.y;
-            const C x0 = buf[i0], x1 = buf[i1];
-            buf[i0] = cadd(x0, x1);
-            buf[i1] = cmul(csub(x0, x1), w);
-        }
-        __syncthreads();
-    }
-}
-
-// radix-2 DIT: bit-reversed order in, natural order out
-template <typename C>
-__device__ __forceinline__ void fft_dit(C *buf, const int logM, const C *__restrict__ tw,
-                                        const int logmax, const bool inv) {
-    const int M = 1 << logM;
-    for (int lh = 0; lh < logM; ++lh) {
-        const int half = 1 << lh;
-        for (int b = threadIdx.x; b < (M >> 1); b += blockDim.x) {
-            const int k = b & (half - 1);
-            const int i0 = ((b >> lh) << (lh + 1)) + k;
-            const int i1 = i0 + half;
-            C w = tw[k << (logmax - 1 - lh)];
-            if (inv) w.y = -w.y;
-            const C x0 = buf[i0];
-            const C x1 = cmul(buf[i1], w);
-            buf[i0] = cadd(x0, x1);
-            buf[i1] = csub(x0, x1);
-        }
-        __syncthreads();
-    }
-}
-
-__device__ __forceinline__ int brev(int i, int logM) {
-    return logM ? (int)(__brev((unsigned)i) >> (32 - logM)) : 0;
-}
-
-// Bluestein convolution core: buf holds a (natural, zero padded); on return buf
-// holds the circular convolution with the kernel whose scaled spectrum is bh
-// (bit-reversed order).
-template <typename C>
+// Bluestein convolution core: buf holds a (natural order, zero padded to M);
+// on return buf holds the CONJUGATE of its circular convolution with the
+// kernel whose scaled spectrum (natural order) is bh:
+// conv = IDFT(DFT(a) bh) = conj(DFT(conj(DFT(a) bh))).
+template <int NT, typename C>
 __device__ __forceinline__ void blue_conv(C *buf, const int logM, const C *__restrict__ bh,
-                                          const C *__restrict__ tw, const int logmax) {
-    fft_dif(buf, logM, tw, logmax, false);
-    for (int i = threadIdx.x; i < (1 << logM); i += blockDim.x) buf[i] = cmul(buf[i], bh[i]);
-    __syncthreads();
-    fft_dit(buf, logM, tw, logmax, true);
+                                          const TwTab<C> &tw) {
+    fft_stockham<NT>(buf, logM, tw, bh, true);
+    fft_stockham<NT>(buf, logM, tw, (const C *)nullptr, false);
 }
 
 template <typename T, int MODE>
-__global__ void __launch_bounds__(RFFT_THREADS) k_ring(const RingArgs<T> a) {
+__global__ void __launch_bounds__(RingNT<T>::v, RingNT<T>::blocks) k_ring(const RingArgs<T> a) {
     typedef typename VT<T>::C C;
-    extern __shared__ unsigned char s_raw[];
-    C *buf = reinterpret_cast<C *>(s_raw);
+    constexpr int NT = RingNT<T>::v;
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    C *s_tw = reinterpret_cast<C *>(s_raw);
+    C *buf = s_tw + a.tw_nlo + a.tw_nhi;
+    for (int i = threadIdx.x; i < a.tw_nlo + a.tw_nhi; i += NT) s_tw[i] = a.tw[i];
+    TwTab<C> tw;
+    tw.lo = s_tw;
+    tw.hi = s_tw + a.tw_nlo;
+    tw.blo = a.tw_blo;
+    tw.logmax = a.logmax;
+    // (the first FFT pass starts after a barrier that follows the fill below)
+
     const int pr = a.pairs[blockIdx.x];
     const int rn = pr, rs = a.nring - 1 - pr;
     const bool single = (rn == rs);
@@ -142,7 +315,7 @@ __global__ void __launch_bounds__(RFFT_THREADS) k_ring(const RingArgs<T> a) {
             // H(k) = e^{i pi s k / n} [ sum_t (-1)^{s t} F(k + t n)
             //                         + sum_t (-1)^{s (t+1)} conj F(n - k + t n) ]
             // (phi0 = s pi / n): one phase per bin, a sign per folded term.
-            for (int k = threadIdx.x; k < n; k += blockDim.x) {
+            for (int k = threadIdx.x; k < n; k += NT) {
                 C hn = zero, hs = zero;
                 T sg = T(1);
                 for (int mm = k; mm <= L; mm += n) {
@@ -174,74 +347,71 @@ __global__ void __launch_bounds__(RFFT_THREADS) k_ring(const RingArgs<T> a) {
                     hs = cmul(hs, ph);
                 }
                 const C z = {hn.x - hs.y, hn.y + hs.x};
-                buf[k] = f.blue ? cmul(z, cconj(chirp[k])) : z;
+                // inverse DFT = conj(DFT(conj .)): the direct path enters conjugated
+                buf[rpad(k)] = f.blue ? cmul(z, cconj(chirp[k])) : cconj(z);
             }
             if (f.blue)
-                for (int k = n + threadIdx.x; k < M; k += blockDim.x) buf[k] = zero;
+                for (int k = n + threadIdx.x; k < M; k += NT) buf[rpad(k)] = zero;
             __syncthreads();
-            // ---- inverse DFT (e^{+2 pi i jk/n})
-            if (f.blue) blue_conv(buf, logM, a.binv + f.bhat_off, a.tw, a.logmax);
-            else fft_dif(buf, logM, a.tw, a.logmax, true);   // z_j at buf[brev(j)]
+            // ---- inverse DFT (e^{+2 pi i jk/n}), natural order out; buf then
+            //      holds the conjugate of z (direct) or of z_j c_j (Bluestein)
+            if (f.blue) blue_conv<NT>(buf, logM, a.binv + f.bhat_off, tw);
+            else fft_stockham<NT>(buf, logM, tw, (const C *)nullptr, false);
             if (MODE == 0) {
                 T *mn = a.map + (int64_t)q * a.npix + a.ofs[rn];
                 T *ms = a.map + (int64_t)q * a.npix + a.ofs[rs];
-                for (int j = threadIdx.x; j < n; j += blockDim.x) {
-                    const C z = f.blue ? cmul(buf[j], cconj(chirp[j])) : buf[brev(j, logM)];
+                for (int j = threadIdx.x; j < n; j += NT) {
+                    C z = buf[rpad(j)];
+                    if (f.blue) z = cmul(z, chirp[j]);
+                    z.y = -z.y;
                     mn[j] = z.x;
                     if (!single) ms[j] = z.y;
                 }
                 __syncthreads();
                 continue;
             }
-            // ---- fused N^-1 weighting
+            // ---- fused N^-1 weighting (each thread rewrites the elements it read)
             const int comp = q < a.nT ? 0 : 1;
             const T *wn = a.ninv + (int64_t)comp * a.npix + a.ofs[rn];
             const T *ws = a.ninv + (int64_t)comp * a.npix + a.ofs[rs];
-            if (f.blue) {
-                for (int j = threadIdx.x; j < n; j += blockDim.x) {
-                    const C c = chirp[j];
-                    const C z = cmul(buf[j], cconj(c));
-                    const C y = {z.x * wn[j], single ? T(0) : z.y * ws[j]};
-                    buf[j] = cmul(y, c);
-                }
-                for (int k = n + threadIdx.x; k < M; k += blockDim.x) buf[k] = zero;
-            } else {
-                for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                    const int j = brev(i, logM);
-                    const C z = buf[i];
-                    buf[i] = C{z.x * wn[j], single ? T(0) : z.y * ws[j]};
-                }
+            for (int j = threadIdx.x; j < n; j += NT) {
+                C z = buf[rpad(j)];
+                if (f.blue) z = cmul(z, chirp[j]);
+                z.y = -z.y;
+                C y = {z.x * wn[j], single ? T(0) : z.y * ws[j]};
+                if (f.blue) y = cmul(y, chirp[j]);
+                buf[rpad(j)] = y;
             }
+            if (f.blue)
+                for (int k = n + threadIdx.x; k < M; k += NT) buf[rpad(k)] = zero;
             __syncthreads();
         } else {
             // ---- MODE 1: load z = w (m_N + i m_S)
             const T *mn = a.map + (int64_t)q * a.npix + a.ofs[rn];
             const T *ms = a.map + (int64_t)q * a.npix + a.ofs[rs];
             const T w = a.weighted ? T(a.wring[rn]) : T(1);
-            for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            for (int j = threadIdx.x; j < n; j += NT) {
                 const C z = {mn[j] * w, single ? T(0) : ms[j] * w};
-                if (f.blue) buf[j] = cmul(z, chirp[j]);
-                else buf[brev(j, logM)] = z;
+                buf[rpad(j)] = f.blue ? cmul(z, chirp[j]) : z;
             }
             if (f.blue)
-                for (int k = n + threadIdx.x; k < M; k += blockDim.x) buf[k] = zero;
+                for (int k = n + threadIdx.x; k < M; k += NT) buf[rpad(k)] = zero;
             __syncthreads();
         }
-        // ---- forward DFT (e^{-2 pi i jk/n}) of the bit-reversed (direct) or
-        //      chirped (Bluestein) buffer; result W in natural order
-        if (f.blue) blue_conv(buf, logM, a.bfwd + f.bhat_off, a.tw, a.logmax);
-        else fft_dit(buf, logM, a.tw, a.logmax, false);
+        // ---- forward DFT (e^{-2 pi i jk/n}); result W in natural order
+        if (f.blue) blue_conv<NT>(buf, logM, a.bfwd + f.bhat_off, tw);   // buf = conj(conv)
+        else fft_stockham<NT>(buf, logM, tw, (const C *)nullptr, false);
         // ---- unfold: G(m) = e^{-i m phi0} Y(m mod n), split north / south
         C *Gn = a.FG + ((int64_t)q * a.nring + rn) * (L + 1);
         C *Gs = a.FG + ((int64_t)q * a.nring + rs) * (L + 1);
         // G(k + t n) = (-1)^{s t} e^{-i pi s k / n} Y(k), one phase per bin
         const int nk = min(n, L + 1);
-        for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+        for (int k = threadIdx.x; k < nk; k += NT) {
             const int k2 = (n - k) % n;
-            C w1 = buf[k], w2 = buf[k2];
+            C w1 = buf[rpad(k)], w2 = buf[rpad(k2)];
             if (f.blue) {
-                w1 = cmul(w1, chirp[k]);
-                w2 = cmul(w2, chirp[k2]);
+                w1 = cmul(cconj(w1), chirp[k]);
+                w2 = cmul(cconj(w2), chirp[k2]);
             }
             C yn = {T(0.5) * (w1.x + w2.x), T(0.5) * (w1.y - w2.y)};
             C ys = {T(0.5) * (w1.y + w2.y), T(-0.5) * (w1.x - w2.x)};
@@ -285,6 +455,7 @@ template <> RingArgs<double> ring_args<double>(Plan *p) {
 
 template <typename T, int MODE>
 static int launch_ring(Plan *p, RingArgs<T> a, cudaStream_t st) {
+    typedef typename VT<T>::C C;
     a.lmax = p->lmax;
     a.nring = p->nring;
     a.npairs = p->npairs;
@@ -293,6 +464,9 @@ static int launch_ring(Plan *p, RingArgs<T> a, cudaStream_t st) {
     a.ofs = p->d_ofs;
     a.wring = p->d_wring;
     a.logmax = p->fft_logmax;
+    a.tw_blo = p->tw_blo;
+    a.tw_nlo = p->tw_nlo;
+    a.tw_nhi = p->tw_nhi;
     auto kern = k_ring<T, MODE>;
     // direct (power-of-two) and Bluestein ring pairs run as separate launches so
     // that each gets the shared memory its own transform length needs
@@ -300,11 +474,12 @@ static int launch_ring(Plan *p, RingArgs<T> a, cudaStream_t st) {
     for (int g = 0; g < 2; ++g) {
         const int cnt = p->ring_group_count[g];
         if (cnt == 0) continue;
-        const size_t smem = sizeof(typename VT<T>::C) << p->ring_group_logm[g];
+        const int M = 1 << p->ring_group_logm[g];
+        const size_t smem = sizeof(C) * ((size_t)p->tw_nlo + p->tw_nhi + M + M / 16);
         if (smem > 48 * 1024)
             SHTG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         a.pairs = p->d_ring_groups + (g ? p->ring_group_count[0] : 0);
-        kern<<<cnt, RFFT_THREADS, smem, st>>>(a);
+        kern<<<cnt, RingNT<T>::v, smem, st>>>(a);
     }
     prof_end(p, st, (p->ring_group_count[0] > 0) + (p->ring_group_count[1] > 0));
     SHTG_CHECK_LAUNCH("k_ring");
