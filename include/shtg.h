@@ -64,12 +64,18 @@ extern "C" {
 
 #define SHTG_FP64 0
 #define SHTG_FP32 1
+#define SHTG_TC32 2                  /* FP32 buffers; alm2map's Legendre sum on the tensor cores
+                                        (FP32 recurrence, bf16 hi/lo split products, FP32
+                                        accumulation: ~2^-16 relative per term); the adjoint
+                                        directions run the FP32 path */
 
 #define SHTG_SPIN0 1                 /* plan flag: temperature transforms */
 #define SHTG_SPIN2 2                 /* plan flag: also spin-2 (Q, U) transforms */
 
 #define SHTG_CG_FP64 0               /* plain FP64 PCG */
 #define SHTG_CG_MIXED 1              /* FP32 PCG inside FP64 iterative refinement */
+#define SHTG_CG_MIXED_TC 2           /* as SHTG_CG_MIXED with the FP32 operator's Legendre
+                                        synthesis on the tensor cores (SHTG_TC32) */
 
 #define SHTG_HOST_INPUTS 1           /* cg_sample flag: problem maps/alm and output are host pointers */
 #define SHTG_PROFILE 2               /* cg_sample flag: time kernel classes with CUDA events */
@@ -102,7 +108,9 @@ int shtg_version(void);
  * alm [nbatch][nalm] -> map [nbatch][npix] for spin 0, or
  * alm [nbatch][2][nalm] (E, B) -> map [nbatch][2][npix] (Q, U) for spin 2.
  * Device pointers; nbatch <= max_batch (x2 components for spin 2 count
- * against 3 * max_batch maps). */
+ * against 3 * max_batch maps).  With precision SHTG_TC32 the call also
+ * synchronizes the stream to check the tensor-core kernel's bounded waits
+ * (SHTG_ERR_TIMEOUT if one expired). */
 int shtg_alm2map(shtg_plan *plan, int spin, int precision, const void *alm, void *map,
                  int nbatch, void *stream);
 
@@ -160,7 +168,7 @@ typedef struct {
 typedef struct {
     double tol;         /* stop when ||b - A x|| / ||b|| <= tol for every realization */
     int maxiter;        /* PCG iterations (FP64 mode) or FP32 iterations (mixed) */
-    int mode;           /* SHTG_CG_FP64 or SHTG_CG_MIXED */
+    int mode;           /* SHTG_CG_FP64, SHTG_CG_MIXED or SHTG_CG_MIXED_TC */
     int precond;        /* 1: diagonal preconditioner of Sect. 4 (default); 0: none */
     double reliable_delta; /* mixed mode: an FP64 residual replacement happens when the FP32
                               residual has dropped by this factor since the last one (default 1e-2) */

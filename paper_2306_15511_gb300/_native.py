@@ -14,9 +14,9 @@ ERRORS = {-1: "SHTG_ERR_ARG", -2: "SHTG_ERR_CUDA", -3: "SHTG_ERR_NOT_CONVERGED",
           -4: "SHTG_ERR_TIMEOUT", -5: "SHTG_ERR_NONFINITE", -6: "SHTG_ERR_NOT_SPD",
           -7: "SHTG_ERR_NOMEM"}
 GEOM_HEALPIX, GEOM_GAUSS = 0, 1
-FP64, FP32 = 0, 1
+FP64, FP32, TC32 = 0, 1, 2
 SPIN0, SPIN2 = 1, 2
-CG_FP64, CG_MIXED = 0, 1
+CG_FP64, CG_MIXED, CG_MIXED_TC = 0, 1, 2
 HOST_INPUTS = 1
 PROFILE = 2
 GRAD_COMPONENTS = 1

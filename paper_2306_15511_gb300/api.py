@@ -87,15 +87,21 @@ class Plan:
             raise ValueError(f"expected trailing shape {'(2, ' if spin == 2 else '('}{inner})")
         return lead, nb
 
-    def alm2map(self, alm: torch.Tensor, spin: int = 0) -> torch.Tensor:
-        """Y: alm [..., nalm] (spin 0) or [..., 2, nalm] (E, B) -> maps."""
+    def alm2map(self, alm: torch.Tensor, spin: int = 0, tensor_cores: bool = False) -> torch.Tensor:
+        """Y: alm [..., nalm] (spin 0) or [..., 2, nalm] (E, B) -> maps.
+        tensor_cores (complex64 only): Legendre sum on the tensor cores
+        (bf16 hi/lo split products, FP32 accumulation)."""
         _need_cuda(alm, "alm")
         lead, nb = self._batched(alm, spin, self.nalm)
         real = torch.float64 if alm.dtype == torch.complex128 else torch.float32
         out = torch.empty(*lead, *((2,) if spin == 2 else ()), self.npix, dtype=real,
                           device=alm.device)
-        N.check(self._lib.shtg_alm2map(self._h, spin, _PREC[alm.dtype], _ptr(alm), _ptr(out), nb,
-                                       _stream()))
+        prec = _PREC[alm.dtype]
+        if tensor_cores:
+            if alm.dtype != torch.complex64:
+                raise ValueError("tensor_cores needs complex64 alm")
+            prec = N.TC32
+        N.check(self._lib.shtg_alm2map(self._h, spin, prec, _ptr(alm), _ptr(out), nb, _stream()))
         return out
 
     def alm2map_adjoint(self, m: torch.Tensor, spin: int = 0) -> torch.Tensor:
@@ -173,7 +179,10 @@ class Plan:
         pr = self._problem(cl, bl, ninv, d, w1, w2, nb, nc)
         o = N.CGOpts()
         o.tol, o.maxiter = float(tol), int(maxiter)
-        o.mode = N.CG_MIXED if mode == "mixed" else N.CG_FP64
+        modes = {"fp64": N.CG_FP64, "mixed": N.CG_MIXED, "mixed_tc": N.CG_MIXED_TC}
+        if mode not in modes:
+            raise ValueError(f"mode must be one of {sorted(modes)}")
+        o.mode = modes[mode]
         o.precond = 1 if precond else 0
         o.reliable_delta, o.reserved = float(reliable_delta), 0
         o.check_every = int(check_every)

@@ -79,8 +79,8 @@ static int check_transform(const shtg_plan *plan, int spin, int precision, const
         set_error("spin-2 transform on a plan created without SHTG_SPIN2");
         return SHTG_ERR_ARG;
     }
-    if (precision != SHTG_FP64 && precision != SHTG_FP32) {
-        set_error("precision must be SHTG_FP64 or SHTG_FP32");
+    if (precision != SHTG_FP64 && precision != SHTG_FP32 && precision != SHTG_TC32) {
+        set_error("precision must be SHTG_FP64, SHTG_FP32 or SHTG_TC32");
         return SHTG_ERR_ARG;
     }
     if (!a || !b) {
@@ -226,6 +226,13 @@ int shtg_alm2map(shtg_plan *plan, int spin, int precision, const void *alm, void
     Plan *p = reinterpret_cast<Plan *>(plan);
     cudaStream_t st = (cudaStream_t)stream;
     if (precision == SHTG_FP64) return transform_synth<double>(p, spin, alm, map, nbatch, st);
+    if (precision == SHTG_TC32) {
+        float2 *F = p->d_phase32;
+        const int rs = spin == 2 ? 2 : 1;
+        SHTG_TRY(leg_synth_tc(p, spin, (const float2 *)alm, rs, nbatch, nullptr, F, st));
+        SHTG_TRY(ring_synth<float>(p, F, nbatch * rs, (float *)map, st));
+        return check_device_flag(p, st);
+    }
     return transform_synth<float>(p, spin, alm, map, nbatch, st);
 }
 

@@ -141,6 +141,7 @@ struct Plan {
     float *d_ltab32 = nullptr;     // [5][lmax+1] beam, S^-1 (TT,TE,EE,BB)
     double *d_scal = nullptr;      // [max_batch][16] per-realization PCG scalars
     double *d_part = nullptr;      // reduction partial sums
+    int *d_flag = nullptr;         // [0]: set by a kernel whose bounded device wait expired
     double *d_lsum = nullptr;      // [lmax+1] per-l sums (log-posterior)
     double *d_stage = nullptr;     // [nmaps_max][npix] staging for host inputs
     double *h_pinned = nullptr;    // pinned host scalars
@@ -195,6 +196,11 @@ int leg_analysis(Plan *p, int spin, const typename VT<T>::C *G, int nmaps, const
                  typename VT<T>::C *alm, int rs, cudaStream_t st, int vjp = 0);
 // out[l, m] = sum_r w_r g_lm(theta_r) (g = lambda^2 or lw^2 + lx^2)
 int leg_diag(Plan *p, int spin, const float *wring, float *out, cudaStream_t st);
+// FP32 recurrence with the l-sum on the tensor cores (bf16 hi / lo split)
+int leg_synth_tc(Plan *p, int spin, const float2 *alm, int rs, int nmaps, const float *beam, float2 *F,
+                 cudaStream_t st);
+// SHTG_ERR_TIMEOUT if a kernel recorded an expired device wait (clears the flag)
+int check_device_flag(Plan *p, cudaStream_t st);
 
 // ringfft.cu
 // mode 0: F -> map (synthesis); mode 1: map -> G (adjoint, wmode 1 = quadrature weights);

@@ -54,6 +54,7 @@ template <typename T> struct LegArgs {
     const T *u;
     const float *wpair; // diag kernel: ring weights summed over the pair
     float *diag;        // diag kernel output
+    int *err;           // tensor-core kernels: set to 1 when a bounded wait expires
 };
 
 // one recurrence step: (l1, l2) = (lambda_{l-1}, lambda_{l-2}) -> (lambda_l, lambda_{l-1})

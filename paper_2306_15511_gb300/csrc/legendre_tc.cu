@@ -1,0 +1,433 @@
+// Legendre synthesis on the 5th-generation tensor cores (tcgen05).
+//
+// F_r(m) = sum_l lambda_lm(theta_r) a_lm is, for one m and a block of 128
+// ring pairs, the product of a [pair x l] matrix (the recurrence values,
+// generated on the fly) with an [l x column] matrix (the alm of all maps),
+// split by the parity of l - m into the even / odd sums E, O (App. A:
+// lambda_lm(pi - theta) = (-1)^(l+m) lambda_lm(theta)), F_N = E + O,
+// F_S = E - O.  Spin 2 uses the two Wigner recurrences y+, y- with
+// lw = y+ + y-, lx = y+ - y- as two A matrices and the (E, B) -> (Q, U)
+// sign pattern folded into the B matrices.
+//
+// Precision: every thread runs the FP32 recurrence of its ring pair exactly
+// as the FP32 CUDA-core kernels do (same FP64 start states), and each value
+// x is split into bf16 x_hi + x_lo (x_lo = bf16(x - x_hi)); the alm are split
+// the same way.  Three products hi*hi + lo*hi + hi*lo are accumulated in
+// FP32 in tensor memory, which keeps ~16 of the 24 mantissa bits of every
+// product (relative error ~2^-17 per term) at bf16 tensor-core rates.
+//
+// Pipeline per CTA (one m, 128 ring pairs, up to 8 maps): the l range is cut
+// into chunks of 32 (16 per parity class, one MMA K of 16 each).  All 128
+// threads generate the A tiles of chunk c (bf16 hi / lo, K-major core
+// matrices in shared memory) and the B tiles, then one thread issues the
+// tcgen05.mma of chunk c and commits them to an mbarrier; the threads go on
+// with chunk c + 1 in the other shared-memory stage while the tensor core
+// works.  The accumulators stay in tensor memory until the last chunk and
+// are read back with tcgen05.ld for the F_N / F_S epilogue.
+#include <cuda_bf16.h>
+
+#include "legendre_kernels.cuh"
+
+namespace shtg {
+namespace {
+
+constexpr int TC_M = 128;        // ring pairs per CTA = MMA M = threads
+constexpr int TC_NMT = 8;        // maps per CTA (grid.z covers more)
+constexpr int TC_ATILE = 4096;   // one A tile: 128 rows x 16 bf16 (K-major core matrices)
+constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;   // bounded mbarrier polling
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor, no swizzle: start address, LBO = byte
+// stride between core matrices adjacent in K, SBO = byte stride between
+// core matrices adjacent in M (or N); version 1 at bit 46.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16 with bf16 A and B (both K-major) and an
+// FP32 accumulator: D format bit 4, A / B format 1 (bf16) at bits 7 / 10,
+// N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+        smem_u32(bar)));
+}
+
+// Wait (bounded) for the completion of the mbarrier phase with the given
+// parity; false if the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < TC_WAIT_LIMIT && !done; ++it) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity));
+    }
+    return done != 0;
+}
+
+// 32 consecutive TMEM columns of this warp's 32 lanes: thread = lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// (a, b) -> bf16x2 hi and lo words, element a in the low half
+__device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t &lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - hf.x, b - hf.y);
+    hi = *reinterpret_cast<const uint32_t *>(&h);
+    lo = *reinterpret_cast<const uint32_t *>(&l);
+}
+
+// 8 values -> one 16-byte core-matrix row of hi and one of lo
+__device__ __forceinline__ void store_row8(unsigned char *hi_row, unsigned char *lo_row, const float (&x)[8]) {
+    uint4 h, l;
+    split2(x[0], x[1], h.x, l.x);
+    split2(x[2], x[3], h.y, l.y);
+    split2(x[4], x[5], h.z, l.z);
+    split2(x[6], x[7], h.w, l.w);
+    *reinterpret_cast<uint4 *>(hi_row) = h;
+    *reinterpret_cast<uint4 *>(lo_row) = l;
+}
+
+// Per-spin tile configuration.  NCOL: B rows of one product block (spin 0:
+// re, im of 8 maps; spin 2: Q re, Q im, U re, U im of 8 maps); a B tile holds
+// NCOL hi rows then NCOL lo rows, 16 K (l of one parity class) each.
+template <int SPIN> struct TcCfg;
+template <> struct TcCfg<0> {
+    static constexpr int NCOL = 16, NA = TC_NMT, NTA = 4, NTB = 2, TMEM = 64;
+};
+template <> struct TcCfg<2> {
+    static constexpr int NCOL = 32, NA = 2 * TC_NMT, NTA = 8, NTB = 4, TMEM = 128;
+};
+template <int SPIN> struct TcLayout {
+    static constexpr int BTILE = 2 * TcCfg<SPIN>::NCOL * 32;
+    static constexpr int STAGE = TcCfg<SPIN>::NTA * TC_ATILE + TcCfg<SPIN>::NTB * BTILE;
+    static constexpr int ALM = 2 * STAGE;                                   // staged alm [NA][128] float2
+    static constexpr int COEF = ALM + TcCfg<SPIN>::NA * LEG_CHUNK * 8;      // staged coefficients
+    static constexpr int BARS = COEF + LEG_CHUNK * (SPIN == 2 ? 16 : 8);    // 2 mbarriers
+    static constexpr int TMEMA = BARS + 16;                                 // TMEM base address
+    static constexpr int RED = TMEMA + 16;                                  // cta_min scratch
+    static constexpr int BYTES = RED + 16;
+};
+
+// Recurrence over one chunk of 32 l (l = q0 .. q0 + 31, staged coefficient
+// index i0 + (l - q0)); values of the even class (l - m even, K index
+// (l - q0) / 2) and the odd class go to their A tiles as bf16 hi / lo.
+// Row = this thread's ring pair; K group h = 0, 1 holds K 0..7, 8..15.
+template <int SPIN, bool INJ>
+__device__ __forceinline__ void gen_atiles(PairState<float, 1> &S, const float2 *s_rec, const float4 *s_s2c,
+                                           const int i0, const int q0, unsigned char *stg) {
+    const int rofs = threadIdx.x * 16;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        unsigned char *t = stg + h * 2048 + rofs;
+        if (SPIN == 0) {
+            float e[8], o[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int d = 16 * h + 2 * i;
+                stepx<float, 1, 0, INJ>(S, s_rec, s_s2c, i0 + d, q0 + d);
+                e[i] = S.a1[0];
+                stepx<float, 1, 0, INJ>(S, s_rec, s_s2c, i0 + d + 1, q0 + d + 1);
+                o[i] = S.a1[0];
+            }
+            store_row8(t, t + TC_ATILE, e);                   // E hi, E lo
+            store_row8(t + 2 * TC_ATILE, t + 3 * TC_ATILE, o); // O hi, O lo
+        } else {
+            float wE[8], wO[8], xE[8], xO[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int d = 16 * h + 2 * i;
+                stepx<float, 1, 2, INJ>(S, s_rec, s_s2c, i0 + d, q0 + d);
+                wE[i] = S.a1[0] + S.b1[0];
+                xE[i] = S.a1[0] - S.b1[0];
+                stepx<float, 1, 2, INJ>(S, s_rec, s_s2c, i0 + d + 1, q0 + d + 1);
+                wO[i] = S.a1[0] + S.b1[0];
+                xO[i] = S.a1[0] - S.b1[0];
+            }
+            // tiles: lwE hi, lo | lwO hi, lo | lxE hi, lo | lxO hi, lo
+            store_row8(t, t + TC_ATILE, wE);
+            store_row8(t + 2 * TC_ATILE, t + 3 * TC_ATILE, wO);
+            store_row8(t + 4 * TC_ATILE, t + 5 * TC_ATILE, xE);
+            store_row8(t + 6 * TC_ATILE, t + 7 * TC_ATILE, xO);
+        }
+    }
+}
+
+// B tiles of one chunk from the staged alm (already times the beam).  Tile
+// b: spin 0 -> class b (0 even, 1 odd); spin 2 -> b = 2 w + class with
+// W columns (-E re, -E im, -B re, -B im) and X columns (B im, -B re, -E im,
+// E re) per map, feeding (Q re, Q im, U re, U im).  Column c, K index k:
+// hi at row c, lo at row NCOL + c (K-major core matrices, LBO = 32 NCOL).
+template <int SPIN>
+__device__ __forceinline__ void gen_btiles(const float2 *s_alm, const int i0, unsigned char *bt) {
+    constexpr int NCOL = TcCfg<SPIN>::NCOL, NTB = TcCfg<SPIN>::NTB;
+    constexpr int BTILE = TcLayout<SPIN>::BTILE;
+    for (int it = threadIdx.x; it < NTB * NCOL * 8; it += TC_M) {
+        const int c = it % NCOL;
+        const int kp = (it / NCOL) % 8;
+        const int b = it / (NCOL * 8);
+        const int off = b & 1;
+        float v[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int idx = i0 + 2 * (2 * kp + q) + off;
+            if (SPIN == 0) {
+                const float2 av = s_alm[(c >> 1) * LEG_CHUNK + idx];
+                v[q] = (c & 1) ? av.y : av.x;
+            } else {
+                const int mk = c >> 2, comp = c & 3;
+                const float2 e = s_alm[(2 * mk) * LEG_CHUNK + idx];
+                const float2 bb = s_alm[(2 * mk + 1) * LEG_CHUNK + idx];
+                if (b < 2) v[q] = comp == 0 ? -e.x : comp == 1 ? -e.y : comp == 2 ? -bb.x : -bb.y;
+                else v[q] = comp == 0 ? bb.y : comp == 1 ? -bb.x : comp == 2 ? -e.y : e.x;
+            }
+        }
+        uint32_t hi, lo;
+        split2(v[0], v[1], hi, lo);
+        const int k0 = 2 * kp;
+        unsigned char *tile = bt + b * BTILE + (k0 >> 3) * (32 * NCOL) + (k0 & 7) * 2;
+        *reinterpret_cast<uint32_t *>(tile + c * 16) = hi;
+        *reinterpret_cast<uint32_t *>(tile + (NCOL + c) * 16) = lo;
+    }
+}
+
+template <int SPIN>
+__global__ void __launch_bounds__(TC_M) k_leg_synth_tc(const LegArgs<float> a) {
+    typedef TcCfg<SPIN> Cfg;
+    typedef TcLayout<SPIN> Lay;
+    constexpr int NCOL = Cfg::NCOL;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float2 *s_alm = reinterpret_cast<float2 *>(smem + Lay::ALM);
+    float2 *s_rec = reinterpret_cast<float2 *>(smem + Lay::COEF);
+    float4 *s_s2c = reinterpret_cast<float4 *>(smem + Lay::COEF);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + Lay::BARS);
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + Lay::TMEMA);
+    int *s_red = reinterpret_cast<int *>(smem + Lay::RED);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int m = blockIdx.y;
+    const int L = a.lmax;
+    const int map0 = blockIdx.z * TC_NMT;
+    const int nm = min(TC_NMT, a.nmaps - map0);
+    const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2;
+
+    PairState<float, 1> S;
+    int warp_lo, warp_hi;
+    load_pairs<float, 1, SPIN>(a, m, S, warp_lo, warp_hi);
+    const int lo = cta_min(warp_lo, s_red);
+    const int pr = S.pr[0];
+    const int rn = pr, rs = a.nring - 1 - pr;
+
+    if (lo > L) {   // no significant l for any pair of this CTA: zero output
+        if (pr < a.npairs) {
+            for (int k = 0; k < nm; ++k) {
+                for (int c = 0; c < (SPIN == 2 ? 2 : 1); ++c) {
+                    const int row = SPIN == 2 ? 2 * (map0 + k) + c : map0 + k;
+                    float2 *out = a.F + (int64_t)row * a.nring * (L + 1) + m;
+                    out[(int64_t)rn * (L + 1)] = make_float2(0.f, 0.f);
+                    if (rs != rn) out[(int64_t)rs * (L + 1)] = make_float2(0.f, 0.f);
+                }
+            }
+        }
+        return;
+    }
+
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
+                     "r"(Cfg::TMEM));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *s_tmem;
+
+    bool ok = true;
+    int chunk = 0;
+    const int l_begin = m + ((lo - m) & ~31);   // chunks start at l - m = 0 mod 32
+    for (int c0 = l_begin; c0 <= L; c0 += LEG_CHUNK) {
+        // ---- stage coefficients and beam-weighted alm of l = c0 .. c0 + 127
+        __syncthreads();
+        for (int i = tid; i < LEG_CHUNK; i += TC_M) {
+            const int l = c0 + i;
+            const bool in = l <= L;
+            const int64_t idx = base + l;
+            if (SPIN == 2) s_s2c[i] = in ? a.s2c[idx] : make_float4(0.f, 0.f, 0.f, 0.f);
+            else s_rec[i] = in ? a.rec[idx] : make_float2(0.f, 0.f);
+            const float bm = (in && a.beam) ? a.beam[l] : 1.f;
+#pragma unroll
+            for (int k = 0; k < Cfg::NA; ++k) {
+                float2 v = make_float2(0.f, 0.f);
+                const int mk = SPIN == 2 ? k / 2 : k;
+                if (in && mk < nm) {
+                    const int64_t row = (int64_t)(map0 + mk) * a.rs + (SPIN == 2 ? (k & 1) : 0);
+                    v = a.alm[row * a.nalm + idx];
+                    if (m == 0) v.y = 0.f;
+                    v.x *= bm;
+                    v.y *= bm;
+                }
+                s_alm[k * LEG_CHUNK + i] = v;
+            }
+        }
+        __syncthreads();
+        for (int q0 = c0; q0 < c0 + LEG_CHUNK && q0 <= L; q0 += 32, ++chunk) {
+            const int sidx = chunk & 1;
+            unsigned char *stg = smem + sidx * Lay::STAGE;
+            // the MMAs of chunk - 2 read this stage: wait for their commit
+            if (chunk >= 2) ok = mbar_wait(&bars[sidx], ((chunk >> 1) - 1) & 1) && ok;
+            const int i0 = q0 - c0;
+            if (q0 <= warp_hi) gen_atiles<SPIN, true>(S, s_rec, s_s2c, i0, q0, stg);
+            else gen_atiles<SPIN, false>(S, s_rec, s_s2c, i0, q0, stg);
+            gen_btiles<SPIN>(s_alm, i0, stg + Cfg::NTA * TC_ATILE);
+            asm volatile("fence.proxy.async.shared::cta;");
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t sa = smem_u32(stg);
+                const uint32_t sb = sa + Cfg::NTA * TC_ATILE;
+                const uint32_t full = idesc_bf16(TC_M, 2 * NCOL), half = idesc_bf16(TC_M, NCOL);
+                const uint32_t acc = chunk > 0;
+                auto A = [&](int t) { return sdesc(sa + t * TC_ATILE, 2048, 128); };
+                auto B = [&](int t) { return sdesc(sb + t * Lay::BTILE, 32 * NCOL, 128); };
+                if (SPIN == 0) {
+                    // D_E (columns 0 .. 2 NCOL) and D_O (2 NCOL .. 4 NCOL)
+                    mma_bf16(tmem, A(0), B(0), full, acc);
+                    mma_bf16(tmem, A(1), B(0), half, 1);
+                    mma_bf16(tmem + 2 * NCOL, A(2), B(1), full, acc);
+                    mma_bf16(tmem + 2 * NCOL, A(3), B(1), half, 1);
+                } else {
+                    // symmetric part: lw even with W even, lx odd with X odd;
+                    // antisymmetric part: lw odd with W odd, lx even with X even
+                    mma_bf16(tmem, A(0), B(0), full, acc);
+                    mma_bf16(tmem, A(1), B(0), half, 1);
+                    mma_bf16(tmem, A(6), B(3), full, 1);
+                    mma_bf16(tmem, A(7), B(3), half, 1);
+                    mma_bf16(tmem + 2 * NCOL, A(2), B(1), full, acc);
+                    mma_bf16(tmem + 2 * NCOL, A(3), B(1), half, 1);
+                    mma_bf16(tmem + 2 * NCOL, A(4), B(2), full, 1);
+                    mma_bf16(tmem + 2 * NCOL, A(5), B(2), half, 1);
+                }
+                mma_commit(&bars[sidx]);
+            }
+        }
+    }
+    // ---- the last commit covers every MMA issued before it
+    const int last = chunk - 1;
+    ok = mbar_wait(&bars[last & 1], (last >> 1) & 1) && ok;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!ok && tid == 0 && a.err) atomicExch(a.err, 1);
+
+    // ---- epilogue: this thread's TMEM lane is its ring pair
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    float d0[32], d1[32];
+    if (SPIN == 0) {
+        tmem_ld32(trow, d0);        // D_E: [0, 16) hi*hi + lo*hi, [16, 32) hi*lo
+        tmem_ld32(trow + 32, d1);   // D_O
+        if (ok && pr < a.npairs) {
+#pragma unroll
+            for (int k = 0; k < TC_NMT; ++k) {
+                if (k >= nm) break;
+                const float er = d0[2 * k] + d0[NCOL + 2 * k], ei = d0[2 * k + 1] + d0[NCOL + 2 * k + 1];
+                const float orr = d1[2 * k] + d1[NCOL + 2 * k], oi = d1[2 * k + 1] + d1[NCOL + 2 * k + 1];
+                float2 *out = a.F + (int64_t)(map0 + k) * a.nring * (L + 1) + m;
+                out[(int64_t)rn * (L + 1)] = make_float2(er + orr, ei + oi);
+                if (rs != rn) out[(int64_t)rs * (L + 1)] = make_float2(er - orr, ei - oi);
+            }
+        }
+    } else {
+        // symmetric part S (columns 0 .. 64), antisymmetric part X (64 .. 128)
+        float s2[32], x2[32];
+        tmem_ld32(trow, d0);         // S hi*hi + lo*hi
+        tmem_ld32(trow + 32, d1);    // S hi*lo
+#pragma unroll
+        for (int c = 0; c < 32; ++c) s2[c] = d0[c] + d1[c];
+        tmem_ld32(trow + 64, d0);
+        tmem_ld32(trow + 96, d1);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) x2[c] = d0[c] + d1[c];
+        if (ok && pr < a.npairs) {
+#pragma unroll
+            for (int k = 0; k < TC_NMT; ++k) {
+                if (k >= nm) break;
+                float2 *oq = a.F + (int64_t)(2 * (map0 + k)) * a.nring * (L + 1) + m;
+                float2 *ou = a.F + (int64_t)(2 * (map0 + k) + 1) * a.nring * (L + 1) + m;
+                const int c = 4 * k;
+                oq[(int64_t)rn * (L + 1)] = make_float2(s2[c] + x2[c], s2[c + 1] + x2[c + 1]);
+                ou[(int64_t)rn * (L + 1)] = make_float2(s2[c + 2] + x2[c + 2], s2[c + 3] + x2[c + 3]);
+                if (rs != rn) {
+                    oq[(int64_t)rs * (L + 1)] = make_float2(s2[c] - x2[c], s2[c + 1] - x2[c + 1]);
+                    ou[(int64_t)rs * (L + 1)] = make_float2(s2[c + 2] - x2[c + 2], s2[c + 3] - x2[c + 3]);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::TMEM));
+}
+
+template <int SPIN>
+int launch_synth_tc(Plan *p, const float2 *alm, int rs, int nmaps, const float *beam, float2 *F,
+                    cudaStream_t st) {
+    LegArgs<float> a = leg_make_args<float>(p);
+    a.alm = alm;
+    a.rs = rs;
+    a.F = F;
+    a.beam = beam;
+    a.nmaps = nmaps;
+    a.err = p->d_flag;
+    const int smem = TcLayout<SPIN>::BYTES;
+    SHTG_CUDA(cudaFuncSetAttribute(k_leg_synth_tc<SPIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    dim3 grid((p->npairs + TC_M - 1) / TC_M, p->lmax + 1, (nmaps + TC_NMT - 1) / TC_NMT);
+    prof_begin(p, K_LEG_SYN32, st);
+    k_leg_synth_tc<SPIN><<<grid, TC_M, smem, st>>>(a);
+    prof_end(p, st);
+    SHTG_CHECK_LAUNCH("k_leg_synth_tc");
+    return SHTG_OK;
+}
+
+}  // namespace
+
+int leg_synth_tc(Plan *p, int spin, const float2 *alm, int rs, int nmaps, const float *beam, float2 *F,
+                 cudaStream_t st) {
+    if (spin == 2) return launch_synth_tc<2>(p, alm, rs, nmaps, beam, F, st);
+    return launch_synth_tc<0>(p, alm, rs, nmaps, beam, F, st);
+}
+
+}  // namespace shtg

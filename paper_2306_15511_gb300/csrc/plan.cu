@@ -626,6 +626,8 @@ int plan_build(Plan *p) {
     SHTG_TRY(dalloc(p, &p->d_scal, 16 * (int64_t)p->max_batch));
     SHTG_TRY(dalloc(p, &p->d_part, 4 * (int64_t)p->max_batch * SHTG_RED_BLOCKS + 4 * (int64_t)p->max_batch + 64));
     SHTG_TRY(dalloc(p, &p->d_lsum, (int64_t)p->lmax + 1));
+    SHTG_TRY(dalloc(p, &p->d_flag, 16));
+    SHTG_CUDA(cudaMemset(p->d_flag, 0, 16 * sizeof(int)));
     SHTG_TRY(dalloc(p, &p->d_stage, nmp));
     SHTG_CUDA(cudaMallocHost((void **)&p->h_pinned, 4096 * sizeof(double)));
     p->prof.ev.resize(16384);
@@ -644,7 +646,7 @@ void plan_free(Plan *p) {
                     p->d_map64, p->d_map32, p->d_ninv64, p->d_ninv32, p->d_minv64,
                     p->d_minv32, p->d_diagT, p->d_diagP, p->d_wpairT, p->d_wpairP,
                     p->d_ltab64, p->d_ltab32, p->d_scal, p->d_part, p->d_lsum, p->d_stage,
-                    p->d_ls2_64, p->d_st2_64, p->d_ls2_32, p->d_st2_32, p->d_ring_groups};
+                    p->d_ls2_64, p->d_st2_64, p->d_ls2_32, p->d_st2_32, p->d_ring_groups, p->d_flag};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (int i = 0; i < 7; ++i)
@@ -671,6 +673,18 @@ void prof_collect(Plan *p, double *ms, int *count) {
     }
     f.n = 0;
     f.open_cls = -1;
+}
+
+int check_device_flag(Plan *p, cudaStream_t st) {
+    int h = 0;
+    SHTG_CUDA(cudaMemcpyAsync(&h, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SHTG_CUDA(cudaStreamSynchronize(st));
+    if (h) {
+        SHTG_CUDA(cudaMemsetAsync(p->d_flag, 0, sizeof(int), st));
+        set_error("a tensor-core kernel gave up waiting for its MMAs (bounded mbarrier wait expired)");
+        return SHTG_ERR_TIMEOUT;
+    }
+    return SHTG_OK;
 }
 
 }  // namespace shtg

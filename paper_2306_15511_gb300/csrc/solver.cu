@@ -491,6 +491,7 @@ struct Solve {
     Plan *p;
     cudaStream_t st;
     int nb, nc;
+    int tc = 0;   // FP32 operator: Legendre synthesis on the tensor cores
     int64_t nalm, per, nvec;
     dim3 vgrid;   // (blocks, nb)
     dim3 rgrid;   // (RB, nb)
@@ -527,6 +528,15 @@ template <> struct Vec<float> {
     static float2 *phase(Plan *p) { return p->d_phase32; }
 };
 
+// Legendre synthesis of the operator: FP64, FP32 or (s.tc) tensor-core FP32
+static int op_synth(Solve &s, int spin, const double2 *x, int rs, const double *beam, double2 *F) {
+    return leg_synth<double>(s.p, spin, x, rs, s.nb, beam, F, s.st);
+}
+static int op_synth(Solve &s, int spin, const float2 *x, int rs, const float *beam, float2 *F) {
+    if (s.tc) return leg_synth_tc(s.p, spin, x, rs, s.nb, beam, F, s.st);
+    return leg_synth<float>(s.p, spin, x, rs, s.nb, beam, F, s.st);
+}
+
 // y = A x = S^-1 x + B Y^T N^-1 Y B x for all realizations
 template <typename T>
 static int matvec(Solve &s, const typename HT<T>::C *x, typename HT<T>::C *y) {
@@ -535,8 +545,8 @@ static int matvec(Solve &s, const typename HT<T>::C *x, typename HT<T>::C *y) {
     C *F = Vec<T>::phase(p);
     const T *beam = Vec<T>::beam(p);
     const int64_t rowsz = (int64_t)(p->lmax + 1) * p->nring;
-    SHTG_TRY(leg_synth<T>(p, 0, x, s.nc, s.nb, beam, F, s.st));
-    if (s.nc == 3) SHTG_TRY(leg_synth<T>(p, 2, x + s.nalm, 3, s.nb, beam, F + s.nb * rowsz, s.st));
+    SHTG_TRY(op_synth(s, 0, x, s.nc, beam, F));
+    if (s.nc == 3) SHTG_TRY(op_synth(s, 2, x + s.nalm, 3, beam, F + s.nb * rowsz));
     SHTG_TRY(ring_fused<T>(p, F, s.nb * s.nc, s.nb, Vec<T>::ninv(p), s.st));
     SHTG_TRY(leg_analysis<T>(p, 0, F, s.nb, beam, y, s.nc, s.st));
     if (s.nc == 3) SHTG_TRY(leg_analysis<T>(p, 2, F + s.nb * rowsz, s.nb, beam, y + s.nalm, 3, s.st));
@@ -898,6 +908,10 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
     if (opt.maxiter <= 0) opt.maxiter = 1000;
     if (!(opt.reliable_delta > 0 && opt.reliable_delta < 1)) opt.reliable_delta = 1e-2;
     if (opt.check_every <= 0) opt.check_every = 4;
+    if (opt.mode != SHTG_CG_FP64 && opt.mode != SHTG_CG_MIXED && opt.mode != SHTG_CG_MIXED_TC) {
+        set_error("mode must be SHTG_CG_FP64, SHTG_CG_MIXED or SHTG_CG_MIXED_TC");
+        return SHTG_ERR_ARG;
+    }
     const int host = (opt.flags & SHTG_HOST_INPUTS) ? 1 : 0;
     if (!pr->d || !pr->w1 || !pr->w2 || !alm_out) {
         set_error("d, w1, w2 and alm_out are required");
@@ -912,6 +926,7 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
     const double t0 = now_ms();
     const int nb = pr->nbatch, nc = pr->ncomp;
     Solve s = make_solve(p, nb, nc, st);
+    s.tc = opt.mode == SHTG_CG_MIXED_TC;
     SHTG_TRY(setup_operator(p, pr, host, opt.precond, st));
     double2 *B = p->v64[0], *X = p->v64[1], *R = p->v64[2], *Tt = p->v64[6];
     // ---- RHS: B Y^T (N^-1 d + N^-1/2 w2) + S^-1/2 w1 in FP64
@@ -964,6 +979,7 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
         SHTG_TRY(norms2(s, R, rr));
     } else {
         SHTG_TRY(mixed_solve(s, opt, bb, rr, &stt));
+        if (s.tc) SHTG_TRY(check_device_flag(p, st));
     }
     double worst = 0.0;
     int conv_all = 1;
