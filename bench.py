@@ -265,7 +265,7 @@ def run_gpu(args):
 
     plan = Plan(nside=NSIDE, lmax=LMAX, max_batch=NB, spin2=True)
     inp = make_inputs(plan, dev, seed_shift=rank)
-    kw = dict(tol=1e-6, mode="mixed", maxiter=args.iters_per_step,
+    kw = dict(tol=1e-6, mode=args.mode, maxiter=args.iters_per_step,
               reliable_delta=args.reliable_delta, check_every=args.check_every,
               allow_not_converged=True)
     out = torch.empty(NB, 3, plan.nalm, dtype=torch.complex128, device=dev)
@@ -364,12 +364,15 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f32+f64" if args.mode == "mixed" else "f32/bf16x3+f64",
+        "data": "synthetic",
         "config": {"workload": f"T+E+B constrained realizations, HEALPix N_side={NSIDE}, "
                                f"l_max={LMAX}, batch {NB} per GPU, mixed FP32 PCG + FP64 "
                                f"residual replacement, tol 1e-6, {args.iters_per_step} "
-                               f"iterations per step",
-                   "iters_per_step": args.iters_per_step,
+                               f"iterations per step" +
+                               (", synthesis Legendre sums on the tensor cores (bf16 hi/lo split)"
+                                if args.mode == "mixed_tc" else ""),
+                   "mode": args.mode, "iters_per_step": args.iters_per_step,
                    "global_batch": NB * world, "fsky": inp["fsky"], "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (d, w2: 2.4 GB each)"},
         "e2e": e2e, "gpu_launches": launches, "clocks": ck, "roofline": roof,
@@ -424,6 +427,18 @@ def measure_extras(plan, inp, dev, kw, full_solve=True):
         e1.record()
         torch.cuda.synchronize()
         ex[f"sht_pairs_per_s_{prec}_batch1"] = reps / (e0.elapsed_time(e1) / 1000.0)
+    # tensor-core synthesis + FP32 adjoint
+    a = torch.randn(1, plan.nalm, dtype=torch.complex64, device=dev, generator=g)
+    for _ in range(2):
+        plan.alm2map_adjoint(plan.alm2map(a, tensor_cores=True))
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(10):
+        plan.alm2map_adjoint(plan.alm2map(a, tensor_cores=True))
+    e1.record()
+    torch.cuda.synchronize()
+    ex["sht_pairs_per_s_tc32_batch1"] = 10 / (e0.elapsed_time(e1) / 1000.0)
     # plain FP64 PCG: a fixed number of iterations timed (full convergence at
     # this size takes minutes)
     nit = 4
@@ -455,6 +470,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="shtg", choices=["shtg", "reference"])
     ap.add_argument("--iters-per-step", type=int, default=160)
+    ap.add_argument("--mode", default="mixed_tc", choices=["mixed", "mixed_tc"],
+                    help="inner FP32 operator: CUDA-core or tensor-core Legendre synthesis")
     ap.add_argument("--nside", type=int, default=NSIDE, help="profiling only: smaller grid")
     ap.add_argument("--lmax", type=int, default=LMAX, help="profiling only: smaller l_max")
     ap.add_argument("--batch", type=int, default=NB, help="profiling only: fewer realizations")

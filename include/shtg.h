@@ -64,10 +64,12 @@ extern "C" {
 
 #define SHTG_FP64 0
 #define SHTG_FP32 1
-#define SHTG_TC32 2                  /* FP32 buffers; alm2map's Legendre sum on the tensor cores
-                                        (FP32 recurrence, bf16 hi/lo split products, FP32
-                                        accumulation: ~2^-16 relative per term); the adjoint
-                                        directions run the FP32 path */
+#define SHTG_TC32 2                  /* FP32 buffers; Legendre sums of alm2map, alm2map_adjoint
+                                        and alm2map_vjp on the tensor cores (FP32 recurrence,
+                                        bf16 hi/lo split products, FP32 accumulation: ~2^-16
+                                        relative per term); map2alm runs the FP32 path; these
+                                        calls synchronize the stream to check the kernels'
+                                        bounded waits (SHTG_ERR_TIMEOUT if one expired) */
 
 #define SHTG_SPIN0 1                 /* plan flag: temperature transforms */
 #define SHTG_SPIN2 2                 /* plan flag: also spin-2 (Q, U) transforms */
@@ -75,7 +77,7 @@ extern "C" {
 #define SHTG_CG_FP64 0               /* plain FP64 PCG */
 #define SHTG_CG_MIXED 1              /* FP32 PCG inside FP64 iterative refinement */
 #define SHTG_CG_MIXED_TC 2           /* as SHTG_CG_MIXED with the FP32 operator's Legendre
-                                        synthesis on the tensor cores (SHTG_TC32) */
+                                        sums on the tensor cores (SHTG_TC32) */
 
 #define SHTG_HOST_INPUTS 1           /* cg_sample flag: problem maps/alm and output are host pointers */
 #define SHTG_PROFILE 2               /* cg_sample flag: time kernel classes with CUDA events */
@@ -108,9 +110,7 @@ int shtg_version(void);
  * alm [nbatch][nalm] -> map [nbatch][npix] for spin 0, or
  * alm [nbatch][2][nalm] (E, B) -> map [nbatch][2][npix] (Q, U) for spin 2.
  * Device pointers; nbatch <= max_batch (x2 components for spin 2 count
- * against 3 * max_batch maps).  With precision SHTG_TC32 the call also
- * synchronizes the stream to check the tensor-core kernel's bounded waits
- * (SHTG_ERR_TIMEOUT if one expired). */
+ * against 3 * max_batch maps). */
 int shtg_alm2map(shtg_plan *plan, int spin, int precision, const void *alm, void *map,
                  int nbatch, void *stream);
 

@@ -21,6 +21,14 @@ _PREC = {torch.complex128: N.FP64, torch.float64: N.FP64,
          torch.complex64: N.FP32, torch.float32: N.FP32}
 
 
+def _prec(dtype, tensor_cores: bool) -> int:
+    if not tensor_cores:
+        return _PREC[dtype]
+    if dtype not in (torch.complex64, torch.float32):
+        raise ValueError("tensor_cores needs complex64 alm / float32 maps")
+    return N.TC32
+
+
 def _stream():
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
@@ -96,34 +104,31 @@ class Plan:
         real = torch.float64 if alm.dtype == torch.complex128 else torch.float32
         out = torch.empty(*lead, *((2,) if spin == 2 else ()), self.npix, dtype=real,
                           device=alm.device)
-        prec = _PREC[alm.dtype]
-        if tensor_cores:
-            if alm.dtype != torch.complex64:
-                raise ValueError("tensor_cores needs complex64 alm")
-            prec = N.TC32
-        N.check(self._lib.shtg_alm2map(self._h, spin, prec, _ptr(alm), _ptr(out), nb, _stream()))
+        N.check(self._lib.shtg_alm2map(self._h, spin, _prec(alm.dtype, tensor_cores), _ptr(alm), _ptr(out),
+                                       nb, _stream()))
         return out
 
-    def alm2map_adjoint(self, m: torch.Tensor, spin: int = 0) -> torch.Tensor:
-        """Y^T (exact transpose, no pixel weights): maps -> alm."""
+    def alm2map_adjoint(self, m: torch.Tensor, spin: int = 0, tensor_cores: bool = False) -> torch.Tensor:
+        """Y^T (exact transpose, no pixel weights): maps -> alm.  tensor_cores
+        (float32 only): Legendre sum on the tensor cores."""
         _need_cuda(m, "map")
         lead, nb = self._batched(m, spin, self.npix)
         cplx = torch.complex128 if m.dtype == torch.float64 else torch.complex64
         out = torch.empty(*lead, *((2,) if spin == 2 else ()), self.nalm, dtype=cplx,
                           device=m.device)
-        N.check(self._lib.shtg_alm2map_adjoint(self._h, spin, _PREC[m.dtype], _ptr(m), _ptr(out),
-                                               nb, _stream()))
+        N.check(self._lib.shtg_alm2map_adjoint(self._h, spin, _prec(m.dtype, tensor_cores), _ptr(m),
+                                               _ptr(out), nb, _stream()))
         return out
 
-    def alm2map_vjp(self, g: torch.Tensor, spin: int = 0) -> torch.Tensor:
+    def alm2map_vjp(self, g: torch.Tensor, spin: int = 0, tensor_cores: bool = False) -> torch.Tensor:
         """Gradient of a real loss w.r.t. alm (torch convention) from dL/dmap."""
         _need_cuda(g, "map_grad")
         lead, nb = self._batched(g, spin, self.npix)
         cplx = torch.complex128 if g.dtype == torch.float64 else torch.complex64
         out = torch.empty(*lead, *((2,) if spin == 2 else ()), self.nalm, dtype=cplx,
                           device=g.device)
-        N.check(self._lib.shtg_alm2map_vjp(self._h, spin, _PREC[g.dtype], _ptr(g), _ptr(out), nb,
-                                           _stream()))
+        N.check(self._lib.shtg_alm2map_vjp(self._h, spin, _prec(g.dtype, tensor_cores), _ptr(g), _ptr(out),
+                                           nb, _stream()))
         return out
 
     def map2alm(self, m: torch.Tensor, spin: int = 0, niter: int = 0) -> torch.Tensor:

@@ -100,9 +100,19 @@ static int check_transform(const shtg_plan *plan, int spin, int precision, const
     return SHTG_OK;
 }
 
+// Y^T with the Legendre stage on the tensor cores (FP32 buffers)
+static int transform_adjoint_tc(Plan *p, int spin, const void *map, void *alm, int nbatch, cudaStream_t st,
+                                int vjp) {
+    const int rs = spin == 2 ? 2 : 1;
+    SHTG_TRY(ring_analysis<float>(p, (const float *)map, nbatch * rs, 0, p->d_phase32, st));
+    SHTG_TRY(leg_analysis_tc(p, spin, p->d_phase32, nbatch, nullptr, (float2 *)alm, rs, st, vjp));
+    return check_device_flag(p, st);
+}
+
 int alm2map_vjp(Plan *p, int spin, int precision, const void *g, void *out, int nbatch,
                 cudaStream_t st) {
     if (precision == SHTG_FP64) return transform_adjoint<double>(p, spin, g, out, nbatch, 0, st, 1);
+    if (precision == SHTG_TC32) return transform_adjoint_tc(p, spin, g, out, nbatch, st, 1);
     return transform_adjoint<float>(p, spin, g, out, nbatch, 0, st, 1);
 }
 
@@ -242,6 +252,7 @@ int shtg_alm2map_adjoint(shtg_plan *plan, int spin, int precision, const void *m
     Plan *p = reinterpret_cast<Plan *>(plan);
     cudaStream_t st = (cudaStream_t)stream;
     if (precision == SHTG_FP64) return transform_adjoint<double>(p, spin, map, alm, nbatch, 0, st);
+    if (precision == SHTG_TC32) return transform_adjoint_tc(p, spin, map, alm, nbatch, st, 0);
     return transform_adjoint<float>(p, spin, map, alm, nbatch, 0, st);
 }
 

@@ -142,6 +142,13 @@ struct Plan {
     double *d_scal = nullptr;      // [max_batch][16] per-realization PCG scalars
     double *d_part = nullptr;      // reduction partial sums
     int *d_flag = nullptr;         // [0]: set by a kernel whose bounded device wait expired
+    // FP32 recurrence states every 32 l (tensor-core transpose): entry
+    // (m, t, pair) at (d_toff[m] + t) * npairs + pair is the state before
+    // l = m + 32 t: (lambda_{l-1}, lambda_{l-2}) for spin 0, (y+_{l-1},
+    // y+_{l-2}, y-_{l-1}, y-_{l-2}) for spin 2
+    int64_t *d_toff = nullptr;
+    float2 *d_tst0 = nullptr;
+    float4 *d_tst2 = nullptr;
     double *d_lsum = nullptr;      // [lmax+1] per-l sums (log-posterior)
     double *d_stage = nullptr;     // [nmaps_max][npix] staging for host inputs
     double *h_pinned = nullptr;    // pinned host scalars
@@ -201,6 +208,10 @@ int leg_synth_tc(Plan *p, int spin, const float2 *alm, int rs, int nmaps, const 
                  cudaStream_t st);
 // SHTG_ERR_TIMEOUT if a kernel recorded an expired device wait (clears the flag)
 int check_device_flag(Plan *p, cudaStream_t st);
+// tensor-core transpose (Y^T) Legendre stage; the tile-state tables it reads
+int leg_analysis_tc(Plan *p, int spin, const float2 *G, int nmaps, const float *beam, float2 *alm, int rs,
+                    cudaStream_t st, int vjp);
+int build_tile_states(Plan *p);
 
 // ringfft.cu
 // mode 0: F -> map (synthesis); mode 1: map -> G (adjoint, wmode 1 = quadrature weights);

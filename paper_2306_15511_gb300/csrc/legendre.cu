@@ -20,6 +20,9 @@ template <> LegArgs<float> leg_make_args<float>(Plan *p) {
     a.ls2 = p->d_ls2_32;
     a.st2 = p->d_st2_32;
     a.u = p->d_u32;
+    a.toff = p->d_toff;
+    a.tst0 = p->d_tst0;
+    a.tst2 = p->d_tst2;
     return a;
 }
 template <> LegArgs<double> leg_make_args<double>(Plan *p) {

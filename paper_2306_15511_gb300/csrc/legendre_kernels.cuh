@@ -55,6 +55,9 @@ template <typename T> struct LegArgs {
     const float *wpair; // diag kernel: ring weights summed over the pair
     float *diag;        // diag kernel output
     int *err;           // tensor-core kernels: set to 1 when a bounded wait expires
+    const int64_t *toff;  // tensor-core transpose: recurrence states every 32 l (FP32 plans)
+    const float2 *tst0;
+    const float4 *tst2;
 };
 
 // one recurrence step: (l1, l2) = (lambda_{l-1}, lambda_{l-2}) -> (lambda_l, lambda_{l-1})
@@ -391,10 +394,15 @@ __global__ void __launch_bounds__(LEG_THREADS) k_leg_analysis(const LegArgs<T> a
                     gn = g[(int64_t)rn * (L + 1)];
                     if (rs != rn) gs = g[(int64_t)rs * (L + 1)];
                 }
-                gE[j][k][2 * c] = gn.x + gs.x;
-                gE[j][k][2 * c + 1] = gn.y + gs.y;
-                gO[j][k][2 * c] = gn.x - gs.x;
-                gO[j][k][2 * c + 1] = gn.y - gs.y;
+                // l - m even uses gE, odd gO; the l loop below runs over groups
+                // of 8 starting at a multiple of 8, so (l - m) & 1 = (v & 1) ^ (m & 1):
+                // for odd m the two sets swap once here and the parity of
+                // every unrolled step is a compile-time constant
+                const T sgn = (m & 1) ? T(-1) : T(1);
+                gE[j][k][2 * c] = gn.x + sgn * gs.x;
+                gE[j][k][2 * c + 1] = gn.y + sgn * gs.y;
+                gO[j][k][2 * c] = gn.x - sgn * gs.x;
+                gO[j][k][2 * c + 1] = gn.y - sgn * gs.y;
             }
         }
     }
@@ -420,7 +428,7 @@ __global__ void __launch_bounds__(LEG_THREADS) k_leg_analysis(const LegArgs<T> a
                         if (l <= warp_hi) stepx<T, NR, SPIN, true>(S, s_rec, s_s2c, l - c0, l);
                         else stepx<T, NR, SPIN, false>(S, s_rec, s_s2c, l - c0, l);
                     }
-                    const bool odd = (l - m) & 1;
+                    const bool odd = v & 1;   // (l - m) & 1 after the swap for odd m
 #pragma unroll
                     for (int k = 0; k < NM; ++k)
 #pragma unroll

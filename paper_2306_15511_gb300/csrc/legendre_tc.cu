@@ -422,12 +422,462 @@ int launch_synth_tc(Plan *p, const float2 *alm, int rs, int nmaps, const float *
     return SHTG_OK;
 }
 
+
+// FP32 recurrence state before every l = m + 32 t of every (m, ring pair):
+// the same steps (rstep / step2 with the same injections) as the Legendre
+// kernels, so a kernel that restarts from an entry reproduces the values of
+// one continuous run bit for bit.  One thread per (m, pair); entries
+// [m][t][pair] so that a warp's stores are contiguous.
+template <int SPIN>
+__global__ void __launch_bounds__(LEG_THREADS) k_tile_states(const LegArgs<float> a, const int64_t *toff,
+                                                             float2 *out0, float4 *out2) {
+    const int m = blockIdx.y;
+    const int L = a.lmax;
+    PairState<float, 1> S;
+    int wlo, whi;
+    load_pairs<float, 1, SPIN>(a, m, S, wlo, whi);
+    const int pr = S.pr[0];
+    if (pr >= a.npairs) return;
+    const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2;
+    const int64_t o = toff[m] * a.npairs + pr;
+    for (int l = m; l <= L; ++l) {
+        if (((l - m) & 31) == 0) {
+            const int64_t e = o + (int64_t)((l - m) >> 5) * a.npairs;
+            if (SPIN == 2) out2[e] = make_float4(S.a1[0], S.a2[0], S.b1[0], S.b2[0]);
+            else out0[e] = make_float2(S.a1[0], S.a2[0]);
+        }
+        stepx<float, 1, SPIN, true>(S, a.rec + base, a.s2c + base, l, l);
+    }
+}
+
+}  // namespace
+
+int build_tile_states(Plan *p) {
+    const int L = p->lmax;
+    std::vector<int64_t> toff(L + 2);
+    toff[0] = 0;
+    for (int m = 0; m <= L; ++m) toff[m + 1] = toff[m] + (L + 1 - m + 31) / 32;
+    const size_t nent = (size_t)toff[L + 1] * p->npairs;
+    auto alloc = [&](void **ptr, size_t bytes) -> int {
+        cudaError_t e = cudaMalloc(ptr, bytes);
+        if (e != cudaSuccess) {
+            *ptr = nullptr;
+            cudaGetLastError();
+            set_error(std::string("cudaMalloc of ") + std::to_string(bytes) +
+                      " bytes (recurrence tile states) failed: " + cudaGetErrorString(e));
+            return SHTG_ERR_NOMEM;
+        }
+        p->device_bytes += (int64_t)bytes;
+        return SHTG_OK;
+    };
+    SHTG_TRY(alloc((void **)&p->d_toff, sizeof(int64_t) * toff.size()));
+    SHTG_CUDA(cudaMemcpy(p->d_toff, toff.data(), sizeof(int64_t) * toff.size(), cudaMemcpyHostToDevice));
+    SHTG_TRY(alloc((void **)&p->d_tst0, sizeof(float2) * nent));
+    LegArgs<float> a = leg_make_args<float>(p);
+    dim3 grid((p->npairs + LEG_THREADS - 1) / LEG_THREADS, L + 1);
+    k_tile_states<0><<<grid, LEG_THREADS>>>(a, p->d_toff, p->d_tst0, nullptr);
+    SHTG_CHECK_LAUNCH("k_tile_states");
+    if (p->flags & SHTG_SPIN2) {
+        SHTG_TRY(alloc((void **)&p->d_tst2, sizeof(float4) * nent));
+        k_tile_states<2><<<grid, LEG_THREADS>>>(a, p->d_toff, nullptr, p->d_tst2);
+        SHTG_CHECK_LAUNCH("k_tile_states");
+    }
+    SHTG_CUDA(cudaDeviceSynchronize());
+    return SHTG_OK;
+}
+
+namespace {
+
+// ===================================================== transpose (Y^T)
+// c_lm = sum_r lambda_lm(theta_r) G_r(m) for one m and a range of 512 l:
+// rows = l (two 128-row tiles per 256 l: l - m even, l - m odd), K = ring
+// pairs in stages of 16, columns = (map, output) with the north / south
+// combination G_N + G_S (rows with the parity of lambda) or G_N - G_S
+// folded into the B tiles.  A tiles hold the recurrence values l-major
+// (MN-major core matrices: 8 pairs x 8 consecutive rows of one class), which
+// is how a thread produces them: thread (pair p, segment s) runs the FP32
+// recurrence of pair p over 32 l from the tabulated state at l = m + 32 t.
+// The CTA accumulates over all ring pairs in tensor memory, so every alm is
+// written once, by one CTA, without atomics.
+constexpr int TA_R = 2;         // 256-l tiles per CTA
+constexpr int TA_K = 16;        // ring pairs per stage (MMA K)
+template <int SPIN> struct TaCfg;
+template <> struct TaCfg<0> {
+    static constexpr int NO = 16, NAT = 4, NBT = 2, TMEM = 64;
+};
+template <> struct TaCfg<2> {
+    static constexpr int NO = 32, NAT = 8, NBT = 4, TMEM = 128;
+};
+template <int SPIN> struct TaLayout {
+    static constexpr int BT = 64 * TaCfg<SPIN>::NO;                         // B tile: 2 NO rows x 16 K bf16
+    static constexpr int ASTAGE = TaCfg<SPIN>::NAT * TC_ATILE;
+    static constexpr int BSTAGE = TaCfg<SPIN>::NBT * BT;
+    static constexpr int BOFF = 2 * ASTAGE;
+    static constexpr int COEF = BOFF + 2 * BSTAGE;
+    static constexpr int BARS = COEF + 512 * (SPIN == 2 ? 16 : 8);
+    static constexpr int TMEMA = BARS + 16;
+    static constexpr int BYTES = TMEMA + 16;
+};
+
+// MN-major A (bit 15), K-major B, bf16 in, FP32 accumulator
+__host__ __device__ constexpr uint32_t idesc_bf16_amn(int m, int n) {
+    return idesc_bf16(m, n) | (1u << 15);
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// A tiles of one (stage, 256-l tile): this thread's pair (column p of the
+// K = 16 slice) over l = l0 .. l0 + 31, l0 = tstart + 32 seg; values of
+// class E (l - m even) go to rows 16 seg + j of the E tiles, class O to the
+// same rows of the O tiles.  Pairs beyond npairs and l beyond lmax give 0.
+template <int SPIN>
+__device__ __forceinline__ void gen_atiles_ana(const LegArgs<float> &a, const int m, const int pr, const int pin,
+                                               const int seg, const int tstart, const int lbase,
+                                               const float2 *s_rec, const float4 *s_s2c,
+                                               unsigned char *at) {
+    const int L = a.lmax;
+    const int l0 = tstart + 32 * seg;
+    PairState<float, 1> S;
+    S.a1[0] = S.a2[0] = S.b1[0] = S.b2[0] = 0.f;
+    S.u[0] = 1.f;
+    S.ls[0] = S.lsb[0] = L + 1;
+    S.s0[0] = S.s1[0] = S.s2[0] = S.s3[0] = 0.f;
+    const bool live = pr < a.npairs && l0 <= L;
+    if (live) {
+        const int64_t o = (int64_t)m * a.npairs + pr;
+        const int64_t e = (a.toff[m] + ((l0 - m) >> 5)) * a.npairs + pr;
+        S.u[0] = a.u[pr];
+        if (SPIN == 2) {
+            const int2 q = a.ls2[o];
+            S.ls[0] = q.x;
+            S.lsb[0] = q.y;
+            const float4 s4 = a.st2[o];
+            S.s0[0] = s4.x;
+            S.s1[0] = s4.y;
+            S.s2[0] = s4.z;
+            S.s3[0] = s4.w;
+            const float4 t4 = a.tst2[e];
+            S.a1[0] = t4.x;
+            S.a2[0] = t4.y;
+            S.b1[0] = t4.z;
+            S.b2[0] = t4.w;
+        } else {
+            S.ls[0] = a.ls[o];
+            const float2 s2 = a.st[o];
+            S.s0[0] = s2.x;
+            S.s1[0] = s2.y;
+            const float2 t2 = a.tst0[e];
+            S.a1[0] = t2.x;
+            S.a2[0] = t2.y;
+        }
+    }
+    const int kg = pin >> 3, krow = pin & 7;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        // rows 16 seg + 8 h .. + 7: core matrix (M group 2 seg + h, K group kg)
+        unsigned char *t = at + (kg * 16 + 2 * seg + h) * 128 + krow * 16;
+        if (SPIN == 0) {
+            float e[8], o[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int d = 16 * h + 2 * i;
+                e[i] = o[i] = 0.f;
+                if (live) {
+                    stepx<float, 1, 0, true>(S, s_rec, s_s2c, l0 + d - lbase, l0 + d);
+                    e[i] = S.a1[0];
+                    stepx<float, 1, 0, true>(S, s_rec, s_s2c, l0 + d + 1 - lbase, l0 + d + 1);
+                    o[i] = S.a1[0];
+                }
+            }
+            store_row8(t, t + TC_ATILE, e);                    // E hi, E lo
+            store_row8(t + 2 * TC_ATILE, t + 3 * TC_ATILE, o);  // O hi, O lo
+        } else {
+            float wE[8], wO[8], xE[8], xO[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int d = 16 * h + 2 * i;
+                wE[i] = wO[i] = xE[i] = xO[i] = 0.f;
+                if (live) {
+                    stepx<float, 1, 2, true>(S, s_rec, s_s2c, l0 + d - lbase, l0 + d);
+                    wE[i] = S.a1[0] + S.b1[0];
+                    xE[i] = S.a1[0] - S.b1[0];
+                    stepx<float, 1, 2, true>(S, s_rec, s_s2c, l0 + d + 1 - lbase, l0 + d + 1);
+                    wO[i] = S.a1[0] + S.b1[0];
+                    xO[i] = S.a1[0] - S.b1[0];
+                }
+            }
+            store_row8(t, t + TC_ATILE, wE);
+            store_row8(t + 2 * TC_ATILE, t + 3 * TC_ATILE, wO);
+            store_row8(t + 4 * TC_ATILE, t + 5 * TC_ATILE, xE);
+            store_row8(t + 6 * TC_ATILE, t + 7 * TC_ATILE, xO);
+        }
+    }
+}
+
+// B tiles of one stage from the ring data G [row][ring][m].  Tile b: spin 0
+// -> rows for class b (0: G_N + G_S, 1: G_N - G_S) with columns (re, im) per
+// map; spin 2 -> b = 2 x + class with lw columns (x = 0) from the set of the
+// row's class and lx columns (x = 1) from the other set:
+//   E^ = -lw G_Q - i lx G_U,  B^ = i lx G_Q - lw G_U
+// (columns E re, E im, B re, B im per map).  hi at row c, lo at row NO + c.
+template <int SPIN>
+__device__ __forceinline__ void gen_btiles_ana(const LegArgs<float> &a, const int m, const int ps,
+                                               const int map0, const int nm, unsigned char *bt) {
+    constexpr int NO = TaCfg<SPIN>::NO, NBT = TaCfg<SPIN>::NBT, BT = TaLayout<SPIN>::BT;
+    const int L = a.lmax;
+    const int64_t rowsz = (int64_t)a.nring * (L + 1);
+    for (int it = threadIdx.x; it < NBT * NO * 8; it += TC_M) {
+        const int c = it % NO;
+        const int pp = (it / NO) % 8;
+        const int b = it / (NO * 8);
+        float v[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int pr = ps * TA_K + 2 * pp + q;
+            v[q] = 0.f;
+            const int k = SPIN == 2 ? c >> 2 : c >> 1;
+            if (pr < a.npairs && k < nm) {
+                const int rn = pr, rs = a.nring - 1 - pr;
+                const int cls = SPIN == 2 ? ((b & 1) ^ (b >> 1)) : b;   // 0: G_N + G_S, 1: G_N - G_S
+                const float sg = cls ? -1.f : 1.f;
+                if (SPIN == 0) {
+                    const float2 *g = a.F + (int64_t)(map0 + k) * rowsz + m;
+                    const float2 gn = g[(int64_t)rn * (L + 1)];
+                    const float2 gs = rs != rn ? g[(int64_t)rs * (L + 1)] : make_float2(0.f, 0.f);
+                    v[q] = (c & 1) ? gn.y + sg * gs.y : gn.x + sg * gs.x;
+                } else {
+                    const float2 *gq = a.F + (int64_t)(2 * (map0 + k)) * rowsz + m;
+                    const float2 *gu = gq + rowsz;
+                    const float2 qn = gq[(int64_t)rn * (L + 1)], un = gu[(int64_t)rn * (L + 1)];
+                    float2 qs = make_float2(0.f, 0.f), us = make_float2(0.f, 0.f);
+                    if (rs != rn) {
+                        qs = gq[(int64_t)rs * (L + 1)];
+                        us = gu[(int64_t)rs * (L + 1)];
+                    }
+                    const float2 Q = make_float2(qn.x + sg * qs.x, qn.y + sg * qs.y);
+                    const float2 U = make_float2(un.x + sg * us.x, un.y + sg * us.y);
+                    const int comp = c & 3;
+                    if (b < 2) v[q] = comp == 0 ? -Q.x : comp == 1 ? -Q.y : comp == 2 ? -U.x : -U.y;
+                    else v[q] = comp == 0 ? U.y : comp == 1 ? -U.x : comp == 2 ? -Q.y : Q.x;
+                }
+            }
+        }
+        uint32_t hi, lo;
+        split2(v[0], v[1], hi, lo);
+        const int k0 = 2 * pp;
+        unsigned char *tile = bt + b * BT + (k0 >> 3) * (32 * NO) + (k0 & 7) * 2;
+        *reinterpret_cast<uint32_t *>(tile + c * 16) = hi;
+        *reinterpret_cast<uint32_t *>(tile + (NO + c) * 16) = lo;
+    }
+}
+
+template <int SPIN>
+__global__ void __launch_bounds__(TC_M) k_leg_analysis_tc(const LegArgs<float> a) {
+    typedef TaCfg<SPIN> Cfg;
+    typedef TaLayout<SPIN> Lay;
+    constexpr int NO = Cfg::NO;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float2 *s_rec = reinterpret_cast<float2 *>(smem + Lay::COEF);
+    float4 *s_s2c = reinterpret_cast<float4 *>(smem + Lay::COEF);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + Lay::BARS);
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + Lay::TMEMA);
+
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int m = blockIdx.y;
+    const int L = a.lmax;
+    const int lbase = m + blockIdx.x * (256 * TA_R);
+    if (lbase > L) return;
+    const int ntile = min(TA_R, (L - lbase) / 256 + 1);
+    const int lend = min(L, lbase + 256 * TA_R - 1);
+    const int map0 = blockIdx.z * TC_NMT;
+    const int nm = min(TC_NMT, a.nmaps - map0);
+    const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2;
+
+    for (int i = tid; i < 256 * TA_R; i += TC_M) {
+        const int l = lbase + i;
+        const bool in = l <= L;
+        if (SPIN == 2) s_s2c[i] = in ? a.s2c[base + l] : make_float4(0.f, 0.f, 0.f, 0.f);
+        else s_rec[i] = in ? a.rec[base + l] : make_float2(0.f, 0.f);
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
+                     "r"(Cfg::TMEM));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *s_tmem;
+
+    const int pin = tid & (TA_K - 1), seg = tid >> 4;
+    const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
+    bool ok = true;
+    int unit = 0, waited = -1, nstage = 0;
+    int last_unit[2] = {-1, -1};   // last unit that read each B buffer
+    const int nps = (a.npairs + TA_K - 1) / TA_K;
+    for (int ps = 0; ps < nps; ++ps) {
+        // a stage is skipped when none of its pairs starts at or before lend
+        // (their recurrence values are all below the threshold there); the
+        // 16 pairs are the same in every warp, so the vote is CTA-uniform
+        const int pr = ps * TA_K + pin;
+        int lsp = L + 1;
+        if (pr < a.npairs) {
+            const int64_t o = (int64_t)m * a.npairs + pr;
+            if (SPIN == 2) {
+                const int2 q = a.ls2[o];
+                lsp = min(q.x, q.y);
+            } else {
+                lsp = a.ls[o];
+            }
+        }
+        if (!__any_sync(0xffffffffu, lsp <= lend)) continue;
+        const int bsel = nstage & 1;
+        unsigned char *bt = smem + Lay::BOFF + bsel * Lay::BSTAGE;
+        if (last_unit[bsel] > waited) {   // the stage two back read this B buffer
+            ok = mbar_wait(&bars[last_unit[bsel] & 1], (last_unit[bsel] >> 1) & 1) && ok;
+            waited = last_unit[bsel];
+        }
+        gen_btiles_ana<SPIN>(a, m, ps, map0, nm, bt);
+        for (int r = 0; r < ntile; ++r) {
+            const int asel = unit & 1;
+            unsigned char *at = smem + asel * Lay::ASTAGE;
+            if (unit >= 2 && unit - 2 > waited) {   // the unit two back read this A buffer
+                ok = mbar_wait(&bars[asel], ((unit >> 1) - 1) & 1) && ok;
+                waited = unit - 2;
+            }
+            const int tstart = lbase + 256 * r;
+            gen_atiles_ana<SPIN>(a, m, pr, pin, seg, tstart, lbase, s_rec, s_s2c, at);
+            asm volatile("fence.proxy.async.shared::cta;");
+            __syncthreads();
+            if (tid == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t sa = smem_u32(at), sb = smem_u32(bt);
+                const uint32_t id = idesc_bf16_amn(TC_M, NO);
+                const uint32_t acc = nstage > 0;
+                auto A = [&](int t) { return sdesc(sa + t * TC_ATILE, 2048, 128); };
+                auto Bh = [&](int t) { return sdesc(sb + t * Lay::BT, 32 * NO, 128); };
+                auto Bl = [&](int t) { return sdesc(sb + t * Lay::BT + (NO / 8) * 128, 32 * NO, 128); };
+                const uint32_t dE = tmem + r * 2 * NO, dO = dE + NO;
+                if (SPIN == 0) {
+                    mma_bf16(dE, A(0), Bh(0), id, acc);
+                    mma_bf16(dE, A(0), Bl(0), id, 1);
+                    mma_bf16(dE, A(1), Bh(0), id, 1);
+                    mma_bf16(dO, A(2), Bh(1), id, acc);
+                    mma_bf16(dO, A(2), Bl(1), id, 1);
+                    mma_bf16(dO, A(3), Bh(1), id, 1);
+                } else {
+                    mma_bf16(dE, A(0), Bh(0), id, acc);   // lw even rows, W from G_N + G_S
+                    mma_bf16(dE, A(0), Bl(0), id, 1);
+                    mma_bf16(dE, A(1), Bh(0), id, 1);
+                    mma_bf16(dE, A(4), Bh(2), id, 1);     // lx even rows, X from G_N - G_S
+                    mma_bf16(dE, A(4), Bl(2), id, 1);
+                    mma_bf16(dE, A(5), Bh(2), id, 1);
+                    mma_bf16(dO, A(2), Bh(1), id, acc);
+                    mma_bf16(dO, A(2), Bl(1), id, 1);
+                    mma_bf16(dO, A(3), Bh(1), id, 1);
+                    mma_bf16(dO, A(6), Bh(3), id, 1);
+                    mma_bf16(dO, A(6), Bl(3), id, 1);
+                    mma_bf16(dO, A(7), Bh(3), id, 1);
+                }
+                mma_commit(&bars[asel]);
+            }
+            last_unit[bsel] = unit;
+            ++unit;
+        }
+        ++nstage;
+    }
+    if (unit > 0 && unit - 1 > waited) ok = mbar_wait(&bars[(unit - 1) & 1], ((unit - 1) >> 1) & 1) && ok;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!ok && tid == 0 && a.err) atomicExch(a.err, 1);
+
+    // ---- epilogue: lane = row i, l = tstart + 2 i (E tile) and + 1 (O tile)
+#pragma unroll
+    for (int r = 0; r < TA_R; ++r) {
+        if (r >= ntile) break;
+        const int tstart = lbase + 256 * r;
+#pragma unroll
+        for (int cls = 0; cls < 2; ++cls) {
+            const int l = tstart + 2 * tid + cls;
+            float d[NO];
+            if (SPIN == 0) tmem_ld16(trow + r * 2 * NO + cls * NO, *reinterpret_cast<float(*)[16]>(d));
+            else tmem_ld32(trow + r * 2 * NO + cls * NO, *reinterpret_cast<float(*)[32]>(d));
+            if (!ok || l > L) continue;
+            const float bm = (a.beam ? a.beam[l] : 1.f) * ((a.vjp && m > 0) ? 2.f : 1.f);
+#pragma unroll
+            for (int k = 0; k < TC_NMT; ++k) {
+                if (k >= nm) break;
+#pragma unroll
+                for (int c = 0; c < (SPIN == 2 ? 2 : 1); ++c) {
+                    const int j = SPIN == 2 ? 4 * k + 2 * c : 2 * k;
+                    float re = 0.f, im = 0.f;
+                    if (nstage > 0) {
+                        re = d[j] * bm;
+                        im = m == 0 ? 0.f : d[j + 1] * bm;
+                    }
+                    const int64_t row = (int64_t)(map0 + k) * a.rs + c;
+                    float2 *dst = const_cast<float2 *>(a.alm) + row * a.nalm + base + l;
+                    *dst = make_float2(re, im);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::TMEM));
+}
+
+template <int SPIN>
+int launch_analysis_tc(Plan *p, const float2 *G, int nmaps, const float *beam, float2 *alm, int rs,
+                       cudaStream_t st, int vjp) {
+    LegArgs<float> a = leg_make_args<float>(p);
+    a.alm = alm;
+    a.rs = rs;
+    a.vjp = vjp;
+    a.F = const_cast<float2 *>(G);
+    a.beam = beam;
+    a.nmaps = nmaps;
+    a.err = p->d_flag;
+    if (!a.toff || !a.tst0 || (SPIN == 2 && !a.tst2)) {
+        set_error("tensor-core transpose: the plan has no recurrence tile states");
+        return SHTG_ERR_ARG;
+    }
+    const int smem = TaLayout<SPIN>::BYTES;
+    SHTG_CUDA(cudaFuncSetAttribute(k_leg_analysis_tc<SPIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    dim3 grid((p->lmax + 256 * TA_R) / (256 * TA_R), p->lmax + 1, (nmaps + TC_NMT - 1) / TC_NMT);
+    prof_begin(p, K_LEG_ANA32, st);
+    k_leg_analysis_tc<SPIN><<<grid, TC_M, smem, st>>>(a);
+    prof_end(p, st);
+    SHTG_CHECK_LAUNCH("k_leg_analysis_tc");
+    return SHTG_OK;
+}
 }  // namespace
 
 int leg_synth_tc(Plan *p, int spin, const float2 *alm, int rs, int nmaps, const float *beam, float2 *F,
                  cudaStream_t st) {
     if (spin == 2) return launch_synth_tc<2>(p, alm, rs, nmaps, beam, F, st);
     return launch_synth_tc<0>(p, alm, rs, nmaps, beam, F, st);
+}
+
+int leg_analysis_tc(Plan *p, int spin, const float2 *G, int nmaps, const float *beam, float2 *alm, int rs,
+                    cudaStream_t st, int vjp) {
+    if (spin == 2) return launch_analysis_tc<2>(p, G, nmaps, beam, alm, rs, st, vjp);
+    return launch_analysis_tc<0>(p, G, nmaps, beam, alm, rs, st, vjp);
 }
 
 }  // namespace shtg

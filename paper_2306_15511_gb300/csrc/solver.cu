@@ -537,6 +537,15 @@ static int op_synth(Solve &s, int spin, const float2 *x, int rs, const float *be
     return leg_synth<float>(s.p, spin, x, rs, s.nb, beam, F, s.st);
 }
 
+// Legendre transpose of the operator: FP64, FP32 or (s.tc) tensor-core FP32
+static int op_analysis(Solve &s, int spin, const double2 *G, const double *beam, double2 *y, int rs) {
+    return leg_analysis<double>(s.p, spin, G, s.nb, beam, y, rs, s.st);
+}
+static int op_analysis(Solve &s, int spin, const float2 *G, const float *beam, float2 *y, int rs) {
+    if (s.tc) return leg_analysis_tc(s.p, spin, G, s.nb, beam, y, rs, s.st, 0);
+    return leg_analysis<float>(s.p, spin, G, s.nb, beam, y, rs, s.st);
+}
+
 // y = A x = S^-1 x + B Y^T N^-1 Y B x for all realizations
 template <typename T>
 static int matvec(Solve &s, const typename HT<T>::C *x, typename HT<T>::C *y) {
@@ -548,8 +557,8 @@ static int matvec(Solve &s, const typename HT<T>::C *x, typename HT<T>::C *y) {
     SHTG_TRY(op_synth(s, 0, x, s.nc, beam, F));
     if (s.nc == 3) SHTG_TRY(op_synth(s, 2, x + s.nalm, 3, beam, F + s.nb * rowsz));
     SHTG_TRY(ring_fused<T>(p, F, s.nb * s.nc, s.nb, Vec<T>::ninv(p), s.st));
-    SHTG_TRY(leg_analysis<T>(p, 0, F, s.nb, beam, y, s.nc, s.st));
-    if (s.nc == 3) SHTG_TRY(leg_analysis<T>(p, 2, F + s.nb * rowsz, s.nb, beam, y + s.nalm, 3, s.st));
+    SHTG_TRY(op_analysis(s, 0, F, beam, y, s.nc));
+    if (s.nc == 3) SHTG_TRY(op_analysis(s, 2, F + s.nb * rowsz, beam, y + s.nalm, 3));
     prof_begin(p, K_VEC, s.st);
     k_prior_add<T><<<dim3(grid_1d(s.nalm).x, s.nb), RT, 0, s.st>>>(x, y, s.nc, s.nalm, p->lmax + 1,
                                                                    p->d_lofidx, Vec<T>::sinv(p));
@@ -860,6 +869,7 @@ static int mixed_solve(Solve &s, const shtg_cg_opts &opt, const std::vector<doub
             for (int b = 0; b < nb; ++b) {
                 const double *h = p->h_pinned + b * 16;
                 if (h[S_BAD] != 0.0) {
+                    if (s.tc) SHTG_TRY(check_device_flag(p, s.st));   // an expired wait explains it
                     set_error("non-finite or non-positive curvature in the FP32 PCG");
                     return SHTG_ERR_NONFINITE;
                 }

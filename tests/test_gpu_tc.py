@@ -1,4 +1,4 @@
-"""Tensor-core Legendre synthesis (SHTG_TC32) and the SHTG_CG_MIXED_TC solver
+"""Tensor-core Legendre sums (SHTG_TC32, both directions) and the SHTG_CG_MIXED_TC solver
 against the FP64 oracle, through the C ABI.
 
 Tolerance of the transform: each product of the l-sum is formed from bf16
@@ -82,16 +82,118 @@ def test_tc_matches_fp32_path():
 
 
 def test_tc_fullsize_sampled_rings():
-    """N_side 1024, l_max 2048: sampled rings against the oracle."""
+    """N_side 1024, l_max 2048: sampled rings against the oracle, and against
+    the FP32 CUDA-core path on the same input (same recurrence values)."""
     nside, L = 1024, 2048
     plan, g = _plan("healpix", nside, L, max_batch=1)
     lsc = np.ones(L + 1)
     lsc[1:] = 1.0 / np.sqrt(np.arange(1, L + 1))
     a = rand_alm(L, np.random.default_rng(13), (1,), lsc)
-    m = plan.alm2map(torch.tensor(a, dtype=torch.complex64, device="cuda"), tensor_cores=True).cpu().numpy()[0]
+    at = torch.tensor(a, dtype=torch.complex64, device="cuda")
+    m = plan.alm2map(at, tensor_cores=True).cpu().numpy()[0]
+    m32 = plan.alm2map(at).cpu().numpy()[0]
+    assert rel_l2(m, m32) < TC_SPLIT
     rings = list(range(0, 4095, 97))
     got = np.concatenate([m[g.ofs[r]:g.ofs[r] + g.nphi[r]] for r in rings])
     assert rel_l2(got, osht.alm2map(g.subset(rings), L, a[0])) < tol_tc(L)
+
+
+def test_tc_fullsize_spin2_sampled_rings():
+    """Spin 2 at N_side 1024: the FP32 recurrence itself loses accuracy on the
+    polar rings (as in the FP32 tests), so the tensor-core maps are checked
+    against the FP32 path on the same input, and against the oracle on the
+    sampled rings within the FP32 path's own error plus the split bound."""
+    nside, L = 1024, 2048
+    plan, g = _plan("healpix", nside, L, max_batch=1)
+    lsc = np.ones(L + 1)
+    lsc[1:] = 1.0 / np.sqrt(np.arange(1, L + 1))
+    eb = rand_alm(L, np.random.default_rng(15), (1, 2), lsc)
+    et = torch.tensor(eb, dtype=torch.complex64, device="cuda")
+    qu = plan.alm2map(et, spin=2, tensor_cores=True).cpu().numpy()[0]
+    qu32 = plan.alm2map(et, spin=2).cpu().numpy()[0]
+    assert rel_l2(qu, qu32) < TC_SPLIT
+    rings = list(range(0, 4095, 97))
+    Q, U = osht.alm2map_spin2(g.subset(rings), L, eb[0, 0], eb[0, 1])
+    pick = lambda x: np.concatenate([x[:, g.ofs[r]:g.ofs[r] + g.nphi[r]] for r in rings], axis=-1)
+    ref = np.stack([Q, U])
+    assert rel_l2(pick(qu), ref) < rel_l2(pick(qu32), ref) + TC_SPLIT
+
+
+@pytest.mark.parametrize("kind,n,L", CASES)
+def test_tc_adjoint_spin0(kind, n, L):
+    plan, g = _plan(kind, n, L)
+    mp = np.random.default_rng(3 * n + L).normal(size=(2, g.npix))
+    a = plan.alm2map_adjoint(torch.tensor(mp, dtype=torch.float32, device="cuda"), tensor_cores=True).cpu().numpy()
+    for b in range(2):
+        assert rel_l2(a[b], osht.alm2map_adjoint(g, L, mp[b])) < tol_tc(L)
+
+
+@pytest.mark.parametrize("kind,n,L", CASES[:4])
+def test_tc_adjoint_spin2(kind, n, L):
+    plan, g = _plan(kind, n, L)
+    mp = np.random.default_rng(11 * n + L).normal(size=(1, 2, g.npix))
+    ad = plan.alm2map_adjoint(torch.tensor(mp, dtype=torch.float32, device="cuda"), spin=2,
+                              tensor_cores=True).cpu().numpy()
+    E, B = osht.alm2map_spin2_adjoint(g, L, mp[0, 0], mp[0, 1])
+    assert rel_l2(ad[0], np.stack([E, B])) < tol_tc(L)
+
+
+def test_tc_adjoint_more_maps_and_vjp():
+    """11 spin-0 maps and 9 spin-2 pairs (two map groups); the vjp doubles
+    the m > 0 outputs."""
+    plan, g = _plan("healpix", 16, 32, max_batch=11)
+    rng = np.random.default_rng(23)
+    mp = rng.normal(size=(11, g.npix))
+    t = torch.tensor(mp, dtype=torch.float32, device="cuda")
+    a = plan.alm2map_adjoint(t, tensor_cores=True).cpu().numpy()
+    for b in (0, 8, 10):
+        assert rel_l2(a[b], osht.alm2map_adjoint(g, 32, mp[b])) < tol_tc(32)
+    v = plan.alm2map_vjp(t, tensor_cores=True).cpu().numpy()
+    w = np.where(osht.ms_of(32) == 0, 1.0, 2.0)
+    assert rel_l2(v[3], w * osht.alm2map_adjoint(g, 32, mp[3])) < tol_tc(32)
+    qu = rng.normal(size=(9, 2, g.npix))
+    e = plan.alm2map_adjoint(torch.tensor(qu, dtype=torch.float32, device="cuda"), spin=2,
+                             tensor_cores=True).cpu().numpy()
+    for b in (0, 8):
+        E, B = osht.alm2map_spin2_adjoint(g, 32, qu[b, 0], qu[b, 1])
+        assert rel_l2(e[b], np.stack([E, B])) < tol_tc(32)
+
+
+def test_tc_adjoint_matches_fp32_path():
+    plan, g = _plan("healpix", 64, 128)
+    mp = torch.tensor(np.random.default_rng(4).normal(size=(2, g.npix)), dtype=torch.float32, device="cuda")
+    a32 = plan.alm2map_adjoint(mp).cpu().numpy()
+    atc = plan.alm2map_adjoint(mp, tensor_cores=True).cpu().numpy()
+    assert rel_l2(atc, a32) < TC_SPLIT
+
+
+def test_tc_adjoint_fullsize_sampled_m():
+    """N_side 1024, l_max 2048: sampled m (polar and equatorial starts, the
+    last m) of the tensor-core transpose against the FP32 path on the same
+    input and against the oracle.  At low m the spin-2 FP32 recurrence loses
+    ~1e-3 on the polar rings (m = 2: 9e-4 on the FP32 path), so the spin-2
+    oracle gate is the FP32 path's own error plus the split bound."""
+    nside, L = 1024, 2048
+    plan, g = _plan("healpix", nside, L, max_batch=1)
+    rng = np.random.default_rng(14)
+    mp = rng.normal(size=(1, g.npix))
+    mt = torch.tensor(mp, dtype=torch.float32, device="cuda")
+    ad = plan.alm2map_adjoint(mt, tensor_cores=True).cpu().numpy()[0]
+    assert rel_l2(ad, plan.alm2map_adjoint(mt).cpu().numpy()[0]) < TC_SPLIT
+    mlist = [0, 1, 2, 511, 512, 700, 1500, 2047, 2048]
+    ref = osht.alm2map_adjoint(g, L, mp[0], mlist=mlist)
+    sel = np.isin(osht.ms_of(L), mlist)
+    assert rel_l2(ad[sel], ref[sel]) < tol_tc(L)
+    qu = rng.normal(size=(1, 2, g.npix))
+    qt = torch.tensor(qu, dtype=torch.float32, device="cuda")
+    e = plan.alm2map_adjoint(qt, spin=2, tensor_cores=True).cpu().numpy()[0]
+    e32 = plan.alm2map_adjoint(qt, spin=2).cpu().numpy()[0]
+    assert rel_l2(e, e32) < TC_SPLIT
+    ml2 = [0, 2, 1000, 2048]
+    E, B = osht.alm2map_spin2_adjoint(g, L, qu[0, 0], qu[0, 1], mlist=ml2)
+    sel = np.isin(osht.ms_of(L), ml2)
+    r2 = np.stack([E[sel], B[sel]])
+    assert rel_l2(e[:, sel], r2) < rel_l2(e32[:, sel], r2) + TC_SPLIT
 
 
 def _data(p, g):
