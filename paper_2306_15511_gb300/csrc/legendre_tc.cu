@@ -35,6 +35,7 @@ constexpr int TC_M = 128;        // ring pairs per CTA = MMA M = threads
 constexpr int TC_NMT = 8;        // maps per CTA (grid.z covers more)
 constexpr int TC_ATILE = 4096;   // one A tile: 128 rows x 16 bf16 (K-major core matrices)
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;   // bounded mbarrier polling
+constexpr int TC_ALMS = LEG_CHUNK + 1;          // staged alm row stride (odd: rows fall in distinct banks)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -133,7 +134,7 @@ template <int SPIN> struct TcLayout {
     static constexpr int BTILE = 2 * TcCfg<SPIN>::NCOL * 32;
     static constexpr int STAGE = TcCfg<SPIN>::NTA * TC_ATILE + TcCfg<SPIN>::NTB * BTILE;
     static constexpr int ALM = 2 * STAGE;                                   // staged alm [NA][128] float2
-    static constexpr int COEF = ALM + TcCfg<SPIN>::NA * LEG_CHUNK * 8;      // staged coefficients
+    static constexpr int COEF = ALM + ((TcCfg<SPIN>::NA * TC_ALMS * 8 + 15) & ~15);   // staged coefficients
     static constexpr int BARS = COEF + LEG_CHUNK * (SPIN == 2 ? 16 : 8);    // 2 mbarriers
     static constexpr int TMEMA = BARS + 16;                                 // TMEM base address
     static constexpr int RED = TMEMA + 16;                                  // cta_min scratch
@@ -193,30 +194,33 @@ template <int SPIN>
 __device__ __forceinline__ void gen_btiles(const float2 *s_alm, const int i0, unsigned char *bt) {
     constexpr int NCOL = TcCfg<SPIN>::NCOL, NTB = TcCfg<SPIN>::NTB;
     constexpr int BTILE = TcLayout<SPIN>::BTILE;
-    for (int it = threadIdx.x; it < NTB * NCOL * 8; it += TC_M) {
-        const int c = it % NCOL;
-        const int kp = (it / NCOL) % 8;
-        const int b = it / (NCOL * 8);
+    // item = (tile b, K group kg, column c, K pair kq): four consecutive lanes
+    // fill one 16-byte core-matrix row, a warp eight consecutive rows
+    for (int it = threadIdx.x; it < NTB * 8 * NCOL; it += TC_M) {
+        const int kq = it & 3;
+        const int c = (it >> 2) % NCOL;
+        const int kg = (it / (4 * NCOL)) & 1;
+        const int b = it / (8 * NCOL);
         const int off = b & 1;
+        const int k0 = 8 * kg + 2 * kq;
         float v[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            const int idx = i0 + 2 * (2 * kp + q) + off;
+            const int idx = i0 + 2 * (k0 + q) + off;
             if (SPIN == 0) {
-                const float2 av = s_alm[(c >> 1) * LEG_CHUNK + idx];
+                const float2 av = s_alm[(c >> 1) * TC_ALMS + idx];
                 v[q] = (c & 1) ? av.y : av.x;
             } else {
                 const int mk = c >> 2, comp = c & 3;
-                const float2 e = s_alm[(2 * mk) * LEG_CHUNK + idx];
-                const float2 bb = s_alm[(2 * mk + 1) * LEG_CHUNK + idx];
+                const float2 e = s_alm[(2 * mk) * TC_ALMS + idx];
+                const float2 bb = s_alm[(2 * mk + 1) * TC_ALMS + idx];
                 if (b < 2) v[q] = comp == 0 ? -e.x : comp == 1 ? -e.y : comp == 2 ? -bb.x : -bb.y;
                 else v[q] = comp == 0 ? bb.y : comp == 1 ? -bb.x : comp == 2 ? -e.y : e.x;
             }
         }
         uint32_t hi, lo;
         split2(v[0], v[1], hi, lo);
-        const int k0 = 2 * kp;
-        unsigned char *tile = bt + b * BTILE + (k0 >> 3) * (32 * NCOL) + (k0 & 7) * 2;
+        unsigned char *tile = bt + b * BTILE + kg * (32 * NCOL) + kq * 4;
         *reinterpret_cast<uint32_t *>(tile + c * 16) = hi;
         *reinterpret_cast<uint32_t *>(tile + (NCOL + c) * 16) = lo;
     }
@@ -302,7 +306,7 @@ __global__ void __launch_bounds__(TC_M) k_leg_synth_tc(const LegArgs<float> a) {
                     v.x *= bm;
                     v.y *= bm;
                 }
-                s_alm[k * LEG_CHUNK + i] = v;
+                s_alm[k * TC_ALMS + i] = v;
             }
         }
         __syncthreads();
@@ -513,7 +517,12 @@ template <int SPIN> struct TaLayout {
     static constexpr int ASTAGE = TaCfg<SPIN>::NAT * TC_ATILE;
     static constexpr int BSTAGE = TaCfg<SPIN>::NBT * BT;
     static constexpr int BOFF = 2 * ASTAGE;
-    static constexpr int COEF = BOFF + 2 * BSTAGE;
+    // ring data of one stage: [pair][row][north, south] float2, pair stride GS (odd)
+    static constexpr int NROW = SPIN == 2 ? 2 * TC_NMT : TC_NMT;
+    static constexpr int GS = 2 * NROW + 1;
+    static constexpr int GBUF = ((TA_K * GS * 8) + 15) & ~15;
+    static constexpr int GOFF = BOFF + 2 * BSTAGE;
+    static constexpr int COEF = GOFF + 2 * GBUF;
     static constexpr int BARS = COEF + 512 * (SPIN == 2 ? 16 : 8);
     static constexpr int TMEMA = BARS + 16;
     static constexpr int BYTES = TMEMA + 16;
@@ -537,51 +546,69 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// A tiles of one (stage, 256-l tile): this thread's pair (column p of the
-// K = 16 slice) over l = l0 .. l0 + 31, l0 = tstart + 32 seg; values of
-// class E (l - m even) go to rows 16 seg + j of the E tiles, class O to the
-// same rows of the O tiles.  Pairs beyond npairs and l beyond lmax give 0.
+// Start data of one ring pair for m (from the FP64 start states) and the
+// tabulated FP32 recurrence state before l0 = m + 32 t.
+struct PairStart {
+    int ls, lsb;
+    float s0, s1, s2, s3, u;
+};
 template <int SPIN>
-__device__ __forceinline__ void gen_atiles_ana(const LegArgs<float> &a, const int m, const int pr, const int pin,
-                                               const int seg, const int tstart, const int lbase,
-                                               const float2 *s_rec, const float4 *s_s2c,
-                                               unsigned char *at) {
-    const int L = a.lmax;
-    const int l0 = tstart + 32 * seg;
-    PairState<float, 1> S;
-    S.a1[0] = S.a2[0] = S.b1[0] = S.b2[0] = 0.f;
-    S.u[0] = 1.f;
-    S.ls[0] = S.lsb[0] = L + 1;
-    S.s0[0] = S.s1[0] = S.s2[0] = S.s3[0] = 0.f;
-    const bool live = pr < a.npairs && l0 <= L;
-    if (live) {
+__device__ __forceinline__ PairStart load_pair_start(const LegArgs<float> &a, int m, int pr) {
+    PairStart q;
+    q.ls = q.lsb = a.lmax + 1;
+    q.s0 = q.s1 = q.s2 = q.s3 = 0.f;
+    q.u = 1.f;
+    if (pr < a.npairs) {
         const int64_t o = (int64_t)m * a.npairs + pr;
-        const int64_t e = (a.toff[m] + ((l0 - m) >> 5)) * a.npairs + pr;
-        S.u[0] = a.u[pr];
+        q.u = a.u[pr];
         if (SPIN == 2) {
-            const int2 q = a.ls2[o];
-            S.ls[0] = q.x;
-            S.lsb[0] = q.y;
+            const int2 l2 = a.ls2[o];
             const float4 s4 = a.st2[o];
-            S.s0[0] = s4.x;
-            S.s1[0] = s4.y;
-            S.s2[0] = s4.z;
-            S.s3[0] = s4.w;
-            const float4 t4 = a.tst2[e];
-            S.a1[0] = t4.x;
-            S.a2[0] = t4.y;
-            S.b1[0] = t4.z;
-            S.b2[0] = t4.w;
+            q.ls = l2.x;
+            q.lsb = l2.y;
+            q.s0 = s4.x;
+            q.s1 = s4.y;
+            q.s2 = s4.z;
+            q.s3 = s4.w;
         } else {
-            S.ls[0] = a.ls[o];
             const float2 s2 = a.st[o];
-            S.s0[0] = s2.x;
-            S.s1[0] = s2.y;
-            const float2 t2 = a.tst0[e];
-            S.a1[0] = t2.x;
-            S.a2[0] = t2.y;
+            q.ls = a.ls[o];
+            q.s0 = s2.x;
+            q.s1 = s2.y;
         }
     }
+    return q;
+}
+template <int SPIN>
+__device__ __forceinline__ float4 load_tile_state(const LegArgs<float> &a, int m, int pr, int l0) {
+    if (pr >= a.npairs || l0 > a.lmax) return make_float4(0.f, 0.f, 0.f, 0.f);
+    const int64_t e = (a.toff[m] + ((l0 - m) >> 5)) * a.npairs + pr;
+    if (SPIN == 2) return a.tst2[e];
+    const float2 t = a.tst0[e];
+    return make_float4(t.x, t.y, 0.f, 0.f);
+}
+
+// A tiles of one (stage, 256-l tile): this thread's pair (column pin of the
+// K = 16 slice) over l = l0 .. l0 + 31, l0 = tstart + 32 seg, from state ts;
+// values of class E (l - m even) go to rows 16 seg + j of the E tiles, class
+// O to the same rows of the O tiles.  Pairs beyond npairs and l beyond lmax
+// give 0.
+template <int SPIN>
+__device__ __forceinline__ void gen_atiles_ana(const PairStart &q, const float4 ts, const bool live, const int pin,
+                                               const int seg, const int l0, const int lbase,
+                                               const float2 *s_rec, const float4 *s_s2c, unsigned char *at) {
+    PairState<float, 1> S;
+    S.u[0] = q.u;
+    S.ls[0] = q.ls;
+    S.lsb[0] = q.lsb;
+    S.s0[0] = q.s0;
+    S.s1[0] = q.s1;
+    S.s2[0] = q.s2;
+    S.s3[0] = q.s3;
+    S.a1[0] = ts.x;
+    S.a2[0] = ts.y;
+    S.b1[0] = ts.z;
+    S.b2[0] = ts.w;
     const int kg = pin >> 3, krow = pin & 7;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -625,58 +652,73 @@ __device__ __forceinline__ void gen_atiles_ana(const LegArgs<float> &a, const in
     }
 }
 
-// B tiles of one stage from the ring data G [row][ring][m].  Tile b: spin 0
-// -> rows for class b (0: G_N + G_S, 1: G_N - G_S) with columns (re, im) per
-// map; spin 2 -> b = 2 x + class with lw columns (x = 0) from the set of the
-// row's class and lx columns (x = 1) from the other set:
-//   E^ = -lw G_Q - i lx G_U,  B^ = i lx G_Q - lw G_U
-// (columns E re, E im, B re, B im per map).  hi at row c, lo at row NO + c.
+// Asynchronous copy (cp.async) of the ring data of stage ps into sg:
+// element (pair p, row q, ring z) at sg[p GS + 2 q + z]; rows are the maps of
+// this CTA (spin 2: Q, U of each); zeros for pairs beyond npairs, missing
+// maps and the south ring of the equator pair.
 template <int SPIN>
-__device__ __forceinline__ void gen_btiles_ana(const LegArgs<float> &a, const int m, const int ps,
-                                               const int map0, const int nm, unsigned char *bt) {
-    constexpr int NO = TaCfg<SPIN>::NO, NBT = TaCfg<SPIN>::NBT, BT = TaLayout<SPIN>::BT;
+__device__ __forceinline__ void stage_ring_data(const LegArgs<float> &a, const int m, const int ps, const int map0,
+                                                const int nm, float2 *sg) {
+    typedef TaLayout<SPIN> Lay;
     const int L = a.lmax;
     const int64_t rowsz = (int64_t)a.nring * (L + 1);
-    for (int it = threadIdx.x; it < NBT * NO * 8; it += TC_M) {
-        const int c = it % NO;
-        const int pp = (it / NO) % 8;
-        const int b = it / (NO * 8);
+    const int nrow = SPIN == 2 ? 2 * nm : nm;
+    for (int it = threadIdx.x; it < TA_K * Lay::NROW * 2; it += TC_M) {
+        const int z = it & 1;
+        const int q = (it >> 1) % Lay::NROW;
+        const int pp = it / (2 * Lay::NROW);
+        const int pr = ps * TA_K + pp;
+        float2 *dst = sg + pp * Lay::GS + 2 * q + z;
+        const int rn = pr, rs = a.nring - 1 - pr;
+        if (pr < a.npairs && q < nrow && !(z && rs == rn)) {
+            const int64_t grow = (SPIN == 2 ? 2 * map0 : map0) + q;
+            const float2 *src = a.F + grow * rowsz + (int64_t)(z ? rs : rn) * (L + 1) + m;
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+        } else {
+            *dst = make_float2(0.f, 0.f);
+        }
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// B tiles of one stage from the staged ring data.  Tile b: spin 0 -> rows
+// for class b (0: G_N + G_S, 1: G_N - G_S) with columns (re, im) per map;
+// spin 2 -> b = 2 x + class with lw columns (x = 0) from the set of the
+// row's class and lx columns (x = 1) from the other set:
+//   E^ = -lw G_Q - i lx G_U,  B^ = i lx G_Q - lw G_U
+// (columns E re, E im, B re, B im per map).  hi at row c, lo at row NO + c;
+// four consecutive lanes fill one 16-byte core-matrix row.
+template <int SPIN>
+__device__ __forceinline__ void gen_btiles_ana(const float2 *sg, unsigned char *bt) {
+    typedef TaLayout<SPIN> Lay;
+    constexpr int NO = TaCfg<SPIN>::NO, NBT = TaCfg<SPIN>::NBT, BT = Lay::BT;
+    for (int it = threadIdx.x; it < NBT * 8 * NO; it += TC_M) {
+        const int kq = it & 3;
+        const int c = (it >> 2) % NO;
+        const int kg = (it / (4 * NO)) & 1;
+        const int b = it / (8 * NO);
+        const int k0 = 8 * kg + 2 * kq;
+        const int cls = SPIN == 2 ? ((b & 1) ^ (b >> 1)) : b;   // 0: G_N + G_S, 1: G_N - G_S
+        const float sg_ = cls ? -1.f : 1.f;
         float v[2];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            const int pr = ps * TA_K + 2 * pp + q;
-            v[q] = 0.f;
-            const int k = SPIN == 2 ? c >> 2 : c >> 1;
-            if (pr < a.npairs && k < nm) {
-                const int rn = pr, rs = a.nring - 1 - pr;
-                const int cls = SPIN == 2 ? ((b & 1) ^ (b >> 1)) : b;   // 0: G_N + G_S, 1: G_N - G_S
-                const float sg = cls ? -1.f : 1.f;
-                if (SPIN == 0) {
-                    const float2 *g = a.F + (int64_t)(map0 + k) * rowsz + m;
-                    const float2 gn = g[(int64_t)rn * (L + 1)];
-                    const float2 gs = rs != rn ? g[(int64_t)rs * (L + 1)] : make_float2(0.f, 0.f);
-                    v[q] = (c & 1) ? gn.y + sg * gs.y : gn.x + sg * gs.x;
-                } else {
-                    const float2 *gq = a.F + (int64_t)(2 * (map0 + k)) * rowsz + m;
-                    const float2 *gu = gq + rowsz;
-                    const float2 qn = gq[(int64_t)rn * (L + 1)], un = gu[(int64_t)rn * (L + 1)];
-                    float2 qs = make_float2(0.f, 0.f), us = make_float2(0.f, 0.f);
-                    if (rs != rn) {
-                        qs = gq[(int64_t)rs * (L + 1)];
-                        us = gu[(int64_t)rs * (L + 1)];
-                    }
-                    const float2 Q = make_float2(qn.x + sg * qs.x, qn.y + sg * qs.y);
-                    const float2 U = make_float2(un.x + sg * us.x, un.y + sg * us.y);
-                    const int comp = c & 3;
-                    if (b < 2) v[q] = comp == 0 ? -Q.x : comp == 1 ? -Q.y : comp == 2 ? -U.x : -U.y;
-                    else v[q] = comp == 0 ? U.y : comp == 1 ? -U.x : comp == 2 ? -Q.y : Q.x;
-                }
+            const float2 *g = sg + (k0 + q) * Lay::GS;
+            if (SPIN == 0) {
+                const float2 gn = g[2 * (c >> 1)], gs = g[2 * (c >> 1) + 1];
+                v[q] = (c & 1) ? gn.y + sg_ * gs.y : gn.x + sg_ * gs.x;
+            } else {
+                const int k = c >> 2, comp = c & 3;
+                const float2 qn = g[4 * k], qs = g[4 * k + 1], un = g[4 * k + 2], us = g[4 * k + 3];
+                const float2 Q = make_float2(qn.x + sg_ * qs.x, qn.y + sg_ * qs.y);
+                const float2 U = make_float2(un.x + sg_ * us.x, un.y + sg_ * us.y);
+                if (b < 2) v[q] = comp == 0 ? -Q.x : comp == 1 ? -Q.y : comp == 2 ? -U.x : -U.y;
+                else v[q] = comp == 0 ? U.y : comp == 1 ? -U.x : comp == 2 ? -Q.y : Q.x;
             }
         }
         uint32_t hi, lo;
         split2(v[0], v[1], hi, lo);
-        const int k0 = 2 * pp;
-        unsigned char *tile = bt + b * BT + (k0 >> 3) * (32 * NO) + (k0 & 7) * 2;
+        unsigned char *tile = bt + b * BT + kg * (32 * NO) + kq * 4;
         *reinterpret_cast<uint32_t *>(tile + c * 16) = hi;
         *reinterpret_cast<uint32_t *>(tile + (NO + c) * 16) = lo;
     }
@@ -727,33 +769,66 @@ __global__ void __launch_bounds__(TC_M) k_leg_analysis_tc(const LegArgs<float> a
 
     const int pin = tid & (TA_K - 1), seg = tid >> 4;
     const uint32_t trow = tmem + ((uint32_t)(warp * 32) << 16);
-    bool ok = true;
-    int unit = 0, waited = -1, nstage = 0;
-    int last_unit[2] = {-1, -1};   // last unit that read each B buffer
-    const int nps = (a.npairs + TA_K - 1) / TA_K;
-    for (int ps = 0; ps < nps; ++ps) {
-        // a stage is skipped when none of its pairs starts at or before lend
-        // (their recurrence values are all below the threshold there); the
-        // 16 pairs are the same in every warp, so the vote is CTA-uniform
-        const int pr = ps * TA_K + pin;
-        int lsp = L + 1;
-        if (pr < a.npairs) {
+    float2 *sgb = reinterpret_cast<float2 *>(smem + Lay::GOFF);
+    int *s_first = reinterpret_cast<int *>(smem + Lay::TMEMA + 4);
+
+    // first stage with a pair whose recurrence starts at or before lend; the
+    // start l falls towards the equator, so every later stage is worked too
+    // (a stage without significant values contributes exact zeros)
+    if (tid == 0) *s_first = a.npairs;
+    __syncthreads();
+    {
+        int first = a.npairs;
+        for (int pr = tid; pr < a.npairs; pr += TC_M) {
             const int64_t o = (int64_t)m * a.npairs + pr;
+            int lsp;
             if (SPIN == 2) {
                 const int2 q = a.ls2[o];
                 lsp = min(q.x, q.y);
             } else {
                 lsp = a.ls[o];
             }
+            if (lsp <= lend) {
+                first = pr;
+                break;
+            }
         }
-        if (!__any_sync(0xffffffffu, lsp <= lend)) continue;
-        const int bsel = nstage & 1;
+        if (first < a.npairs) atomicMin(s_first, first);
+    }
+    __syncthreads();
+    const int s0 = *s_first / TA_K;
+    const int nps = (a.npairs + TA_K - 1) / TA_K;
+    const int nst = s0 < nps ? nps - s0 : 0;
+
+    bool ok = true;
+    int unit = 0, waited = -1;
+    int last_unit[2] = {-1, -1};   // last unit that read each B buffer
+    PairStart pst{}, pnext{};
+    float4 tcur = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (nst > 0) {
+        stage_ring_data<SPIN>(a, m, s0, map0, nm, sgb);
+        pst = load_pair_start<SPIN>(a, m, s0 * TA_K + pin);
+        tcur = load_tile_state<SPIN>(a, m, s0 * TA_K + pin, lbase + 32 * seg);
+    }
+    for (int si = 0; si < nst; ++si) {
+        const int ps = s0 + si;
+        const int pr = ps * TA_K + pin;
+        const bool more = si + 1 < nst;
+        if (more) {   // next stage's ring data and start states, in flight during this stage
+            stage_ring_data<SPIN>(a, m, ps + 1, map0, nm, sgb + ((si + 1) & 1) * (Lay::GBUF / 8));
+            pnext = load_pair_start<SPIN>(a, m, pr + TA_K);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();
+        const int bsel = si & 1;
         unsigned char *bt = smem + Lay::BOFF + bsel * Lay::BSTAGE;
         if (last_unit[bsel] > waited) {   // the stage two back read this B buffer
             ok = mbar_wait(&bars[last_unit[bsel] & 1], (last_unit[bsel] >> 1) & 1) && ok;
             waited = last_unit[bsel];
         }
-        gen_btiles_ana<SPIN>(a, m, ps, map0, nm, bt);
+        gen_btiles_ana<SPIN>(sgb + bsel * (Lay::GBUF / 8), bt);
         for (int r = 0; r < ntile; ++r) {
             const int asel = unit & 1;
             unsigned char *at = smem + asel * Lay::ASTAGE;
@@ -762,14 +837,20 @@ __global__ void __launch_bounds__(TC_M) k_leg_analysis_tc(const LegArgs<float> a
                 waited = unit - 2;
             }
             const int tstart = lbase + 256 * r;
-            gen_atiles_ana<SPIN>(a, m, pr, pin, seg, tstart, lbase, s_rec, s_s2c, at);
+            const int l0 = tstart + 32 * seg;
+            // state of the next unit: (this stage, next tile) or (next stage, first tile)
+            float4 tnext = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (r + 1 < ntile) tnext = load_tile_state<SPIN>(a, m, pr, l0 + 256);
+            else if (more) tnext = load_tile_state<SPIN>(a, m, pr + TA_K, lbase + 32 * seg);
+            gen_atiles_ana<SPIN>(pst, tcur, pr < a.npairs && l0 <= L, pin, seg, l0, lbase, s_rec, s_s2c, at);
+            tcur = tnext;
             asm volatile("fence.proxy.async.shared::cta;");
             __syncthreads();
             if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t sa = smem_u32(at), sb = smem_u32(bt);
                 const uint32_t id = idesc_bf16_amn(TC_M, NO);
-                const uint32_t acc = nstage > 0;
+                const uint32_t acc = si > 0;
                 auto A = [&](int t) { return sdesc(sa + t * TC_ATILE, 2048, 128); };
                 auto Bh = [&](int t) { return sdesc(sb + t * Lay::BT, 32 * NO, 128); };
                 auto Bl = [&](int t) { return sdesc(sb + t * Lay::BT + (NO / 8) * 128, 32 * NO, 128); };
@@ -800,7 +881,7 @@ __global__ void __launch_bounds__(TC_M) k_leg_analysis_tc(const LegArgs<float> a
             last_unit[bsel] = unit;
             ++unit;
         }
-        ++nstage;
+        pst = pnext;
     }
     if (unit > 0 && unit - 1 > waited) ok = mbar_wait(&bars[(unit - 1) & 1], ((unit - 1) >> 1) & 1) && ok;
     asm volatile("tcgen05.fence::after_thread_sync;");
@@ -826,7 +907,7 @@ __global__ void __launch_bounds__(TC_M) k_leg_analysis_tc(const LegArgs<float> a
                 for (int c = 0; c < (SPIN == 2 ? 2 : 1); ++c) {
                     const int j = SPIN == 2 ? 4 * k + 2 * c : 2 * k;
                     float re = 0.f, im = 0.f;
-                    if (nstage > 0) {
+                    if (nst > 0) {
                         re = d[j] * bm;
                         im = m == 0 ? 0.f : d[j + 1] * bm;
                     }
