@@ -20,9 +20,15 @@
 
 namespace shtg {
 
-template <typename T> struct RingNT;
-template <> struct RingNT<float> { static constexpr int v = 512, blocks = 2; };
-template <> struct RingNT<double> { static constexpr int v = 512, blocks = 1; };
+// Threads per CTA: 256 for transforms of length <= 4096 (every radix-16
+// pass then has one butterfly per thread), 512 above; resident CTAs per SM
+// for the register budget (128 registers: the inlined passes do not spill,
+// which measured faster than more resident CTAs with spills).
+template <typename T, int NT> struct RingBlocks;
+template <> struct RingBlocks<float, 256> { static constexpr int v = 2; };
+template <> struct RingBlocks<float, 512> { static constexpr int v = 1; };
+template <> struct RingBlocks<double, 256> { static constexpr int v = 2; };
+template <> struct RingBlocks<double, 512> { static constexpr int v = 1; };
 
 __device__ __forceinline__ int rpad(int i) { return i + (i >> 4); }
 
@@ -228,9 +234,9 @@ __device__ __forceinline__ void spass(C *buf, const int M, const int Ns, const T
 // null) and conjugates when cj is set.  The inverse transform is
 // conj(DFT(conj x)): callers conjugate on the way in and out.  Passes: radix
 // 16 while at least four factors of two remain, then one radix-8, -4 or -2
-// pass.  Not inlined: one copy serves every call site of a kernel.
+// pass.  Each kernel calls it from one place, so it is inlined once.
 template <int NT, typename C>
-__device__ __noinline__ void fft_stockham(C *buf, const int logM, const TwTab<C> tw,
+__device__ __forceinline__ void fft_stockham(C *buf, const int logM, const TwTab<C> tw,
                                           const C *__restrict__ post, const bool cj) {
     const int M = 1 << logM;
     int Ns = 1, rem = logM;
@@ -247,8 +253,8 @@ __device__ __noinline__ void fft_stockham(C *buf, const int logM, const TwTab<C>
             spass<4, 1, NT>(buf, M, Ns, tw, post, cj);   // M <= 2^10
             rem = 0;
         } else {
-            if (M / 2 > NT) spass<2, 8, NT>(buf, M, Ns, tw, post, cj);   // M = 2^13
-            else spass<2, 1, NT>(buf, M, Ns, tw, post, cj);
+            if (NT >= 512 && M / 2 > NT) spass<2, (NT >= 512 ? 8 : 1), NT>(buf, M, Ns, tw, post, cj);   // M = 2^13
+            else spass<2, 1, NT>(buf, M, Ns, tw, post, cj);   // M / 2 <= NT (256 threads: M <= 4096)
             rem = 0;
         }
     }
@@ -272,21 +278,24 @@ template <typename T> struct RingArgs {
     const int *pairs; // ring pairs handled by this launch (one CTA each)
 };
 
-// Bluestein convolution core: buf holds a (natural order, zero padded to M);
-// on return buf holds the CONJUGATE of its circular convolution with the
-// kernel whose scaled spectrum (natural order) is bh:
-// conv = IDFT(DFT(a) bh) = conj(DFT(conj(DFT(a) bh))).
+// One transform direction in place: a DFT for power-of-two rings (bh null),
+// a Bluestein convolution with kernel spectrum bh otherwise (buf then holds
+// its conjugate).  One FFT call site.
 template <int NT, typename C>
-__device__ __forceinline__ void blue_conv(C *buf, const int logM, const C *__restrict__ bh,
-                                          const TwTab<C> &tw) {
-    fft_stockham<NT>(buf, logM, tw, bh, true);
-    fft_stockham<NT>(buf, logM, tw, (const C *)nullptr, false);
+__device__ __forceinline__ void transform_dir(C *buf, const int logM, const TwTab<C> &tw, const C *__restrict__ bh) {
+    const int nf = bh ? 2 : 1;
+    for (int k = 0; k < nf; ++k) fft_stockham<NT>(buf, logM, tw, k == 0 ? bh : nullptr, bh != nullptr && k == 0);
 }
 
-template <typename T, int MODE>
-__global__ void __launch_bounds__(RingNT<T>::v, RingNT<T>::blocks) k_ring(const RingArgs<T> a) {
+// The transforms of one map: [fold or load] -> one (MODE 0, 1) or two
+// (MODE 2, with the N^-1 weighting between) transform directions -> [write
+// map or unfold].  A direction is one FFT (power-of-two rings) or, for
+// Bluestein rings, a convolution = DFT, times the kernel spectrum and
+// conjugated in the last pass, DFT again: buf then holds the conjugate of the
+// convolution.  The directions run in a loop, so the FFT is inlined once.
+template <typename T, int MODE, int NT>
+__global__ void __launch_bounds__(NT, RingBlocks<T, NT>::v) k_ring(const RingArgs<T> a) {
     typedef typename VT<T>::C C;
-    constexpr int NT = RingNT<T>::v;
     extern __shared__ __align__(16) unsigned char s_raw[];
     C *s_tw = reinterpret_cast<C *>(s_raw);
     C *buf = s_tw + a.tw_nlo + a.tw_nhi;
@@ -306,9 +315,38 @@ __global__ void __launch_bounds__(RingNT<T>::v, RingNT<T>::blocks) k_ring(const 
     const int L = a.lmax;
     const C *chirp = a.chirp + f.chirp_off;
     const C zero = {T(0), T(0)};
+    constexpr int NDIR = MODE == 2 ? 2 : 1;
 
     for (int q = 0; q < a.nmaps; ++q) {
-        if (MODE == 0 || MODE == 2) {
+        if (MODE != 1 && n >= 2 * L) {
+            // ---- fold without aliasing (n >= 2 l_max): F(m) alone fills bin m
+            // and conj F(m) bin n - m (phase e^{+-i pi s m / n}); with n = 2 l_max
+            // both land in bin n / 2 = l_max; bins strictly between l_max and
+            // n - l_max are zero.  One thread per m: independent loads.
+            const C *Fn = a.FG + ((int64_t)q * a.nring + rn) * (L + 1);
+            const C *Fs = a.FG + ((int64_t)q * a.nring + rs) * (L + 1);
+#pragma unroll 4
+            for (int mm = threadIdx.x; mm <= L; mm += NT) {
+                C hn = Fn[mm], hs = single ? zero : Fs[mm];
+                if (f.shift) {
+                    const C ph = phase_pi(mm, n, T(0));
+                    hn = cmul(hn, ph);
+                    hs = cmul(hs, ph);
+                }
+                C z1 = {hn.x - hs.y, hn.y + hs.x};      // bin mm
+                C z2 = {hn.x + hs.y, -hn.y + hs.x};     // bin n - mm: conj(hn) + i conj(hs)
+                if (mm == 0) z2 = zero;
+                const int k2 = n - mm;
+                if (2 * mm == n) {                      // bin n / 2 collects both
+                    z1.x += z2.x;
+                    z1.y += z2.y;
+                }
+                buf[rpad(mm)] = f.blue ? cmul(z1, cconj(chirp[mm])) : cconj(z1);
+                if (mm > 0 && 2 * mm != n)
+                    buf[rpad(k2)] = f.blue ? cmul(z2, cconj(chirp[k2])) : cconj(z2);
+            }
+            for (int k = L + 1 + threadIdx.x; k < n - L; k += NT) buf[rpad(k)] = zero;
+        } else if (MODE != 1) {
             // ---- fold F into the length-n spectrum of z = f_N + i f_S
             const C *Fn = a.FG + ((int64_t)q * a.nring + rn) * (L + 1);
             const C *Fs = a.FG + ((int64_t)q * a.nring + rs) * (L + 1);
@@ -350,84 +388,84 @@ __global__ void __launch_bounds__(RingNT<T>::v, RingNT<T>::blocks) k_ring(const 
                 // inverse DFT = conj(DFT(conj .)): the direct path enters conjugated
                 buf[rpad(k)] = f.blue ? cmul(z, cconj(chirp[k])) : cconj(z);
             }
-            if (f.blue)
-                for (int k = n + threadIdx.x; k < M; k += NT) buf[rpad(k)] = zero;
-            __syncthreads();
-            // ---- inverse DFT (e^{+2 pi i jk/n}), natural order out; buf then
-            //      holds the conjugate of z (direct) or of z_j c_j (Bluestein)
-            if (f.blue) blue_conv<NT>(buf, logM, a.binv + f.bhat_off, tw);
-            else fft_stockham<NT>(buf, logM, tw, (const C *)nullptr, false);
-            if (MODE == 0) {
-                T *mn = a.map + (int64_t)q * a.npix + a.ofs[rn];
-                T *ms = a.map + (int64_t)q * a.npix + a.ofs[rs];
-                for (int j = threadIdx.x; j < n; j += NT) {
-                    C z = buf[rpad(j)];
-                    if (f.blue) z = cmul(z, chirp[j]);
-                    z.y = -z.y;
-                    mn[j] = z.x;
-                    if (!single) ms[j] = z.y;
-                }
-                __syncthreads();
-                continue;
-            }
-            // ---- fused N^-1 weighting (each thread rewrites the elements it read)
-            const int comp = q < a.nT ? 0 : 1;
-            const T *wn = a.ninv + (int64_t)comp * a.npix + a.ofs[rn];
-            const T *ws = a.ninv + (int64_t)comp * a.npix + a.ofs[rs];
-            for (int j = threadIdx.x; j < n; j += NT) {
-                C z = buf[rpad(j)];
-                if (f.blue) z = cmul(z, chirp[j]);
-                z.y = -z.y;
-                C y = {z.x * wn[j], single ? T(0) : z.y * ws[j]};
-                if (f.blue) y = cmul(y, chirp[j]);
-                buf[rpad(j)] = y;
-            }
-            if (f.blue)
-                for (int k = n + threadIdx.x; k < M; k += NT) buf[rpad(k)] = zero;
-            __syncthreads();
         } else {
-            // ---- MODE 1: load z = w (m_N + i m_S)
+            // ---- load z = w (m_N + i m_S)
             const T *mn = a.map + (int64_t)q * a.npix + a.ofs[rn];
             const T *ms = a.map + (int64_t)q * a.npix + a.ofs[rs];
             const T w = a.weighted ? T(a.wring[rn]) : T(1);
+#pragma unroll 4
             for (int j = threadIdx.x; j < n; j += NT) {
                 const C z = {mn[j] * w, single ? T(0) : ms[j] * w};
                 buf[rpad(j)] = f.blue ? cmul(z, chirp[j]) : z;
             }
-            if (f.blue)
-                for (int k = n + threadIdx.x; k < M; k += NT) buf[rpad(k)] = zero;
-            __syncthreads();
         }
-        // ---- forward DFT (e^{-2 pi i jk/n}); result W in natural order
-        if (f.blue) blue_conv<NT>(buf, logM, a.bfwd + f.bhat_off, tw);   // buf = conj(conv)
-        else fft_stockham<NT>(buf, logM, tw, (const C *)nullptr, false);
-        // ---- unfold: G(m) = e^{-i m phi0} Y(m mod n), split north / south
-        C *Gn = a.FG + ((int64_t)q * a.nring + rn) * (L + 1);
-        C *Gs = a.FG + ((int64_t)q * a.nring + rs) * (L + 1);
-        // G(k + t n) = (-1)^{s t} e^{-i pi s k / n} Y(k), one phase per bin
-        const int nk = min(n, L + 1);
-        for (int k = threadIdx.x; k < nk; k += NT) {
-            const int k2 = (n - k) % n;
-            C w1 = buf[rpad(k)], w2 = buf[rpad(k2)];
-            if (f.blue) {
-                w1 = cmul(cconj(w1), chirp[k]);
-                w2 = cmul(cconj(w2), chirp[k2]);
+        if (f.blue)
+            for (int k = n + threadIdx.x; k < M; k += NT) buf[rpad(k)] = zero;
+        __syncthreads();
+        for (int dir = 0; dir < NDIR; ++dir) {
+            // inverse (e^{+2 pi i jk/n}) for MODE 0 and the first direction of
+            // MODE 2, forward (e^{-2 pi i jk/n}) otherwise
+            const bool fwd = MODE == 1 || dir == 1;
+            transform_dir<NT>(buf, logM, tw, f.blue ? (fwd ? a.bfwd : a.binv) + f.bhat_off : nullptr);
+            if (MODE == 2 && dir == 0) {
+                // ---- N^-1 weighting (each thread rewrites the elements it reads)
+                const int comp = q < a.nT ? 0 : 1;
+                const T *wn = a.ninv + (int64_t)comp * a.npix + a.ofs[rn];
+                const T *ws = a.ninv + (int64_t)comp * a.npix + a.ofs[rs];
+#pragma unroll 4
+                for (int j = threadIdx.x; j < n; j += NT) {
+                    C z = buf[rpad(j)];
+                    if (f.blue) z = cmul(z, chirp[j]);
+                    z.y = -z.y;
+                    C y = {z.x * wn[j], single ? T(0) : z.y * ws[j]};
+                    if (f.blue) y = cmul(y, chirp[j]);
+                    buf[rpad(j)] = y;
+                }
+                if (f.blue)
+                    for (int k = n + threadIdx.x; k < M; k += NT) buf[rpad(k)] = zero;
+                __syncthreads();
             }
-            C yn = {T(0.5) * (w1.x + w2.x), T(0.5) * (w1.y - w2.y)};
-            C ys = {T(0.5) * (w1.y + w2.y), T(-0.5) * (w1.x - w2.x)};
-            if (f.shift) {
-                const C ph = cconj(phase_pi(k, n, T(0)));
-                yn = cmul(yn, ph);
-                ys = cmul(ys, ph);
+        }
+        if (MODE == 0) {
+            // ---- ring pixels: z = conj(buf) (direct) or conj(buf c) (Bluestein)
+            T *mn = a.map + (int64_t)q * a.npix + a.ofs[rn];
+            T *ms = a.map + (int64_t)q * a.npix + a.ofs[rs];
+            for (int j = threadIdx.x; j < n; j += NT) {
+                C z = buf[rpad(j)];
+                if (f.blue) z = cmul(z, chirp[j]);
+                z.y = -z.y;
+                mn[j] = z.x;
+                if (!single) ms[j] = z.y;
             }
-            for (int mm = k; mm <= L; mm += n) {
-                Gn[mm] = yn;
-                if (!single) Gs[mm] = ys;
+        } else {
+            // ---- unfold: G(m) = e^{-i m phi0} Y(m mod n), split north / south
+            C *Gn = a.FG + ((int64_t)q * a.nring + rn) * (L + 1);
+            C *Gs = a.FG + ((int64_t)q * a.nring + rs) * (L + 1);
+            // G(k + t n) = (-1)^{s t} e^{-i pi s k / n} Y(k), one phase per bin
+            const int nk = min(n, L + 1);
+            for (int k = threadIdx.x; k < nk; k += NT) {
+                const int k2 = (n - k) % n;
+                C w1 = buf[rpad(k)], w2 = buf[rpad(k2)];
+                if (f.blue) {
+                    w1 = cmul(cconj(w1), chirp[k]);
+                    w2 = cmul(cconj(w2), chirp[k2]);
+                }
+                C yn = {T(0.5) * (w1.x + w2.x), T(0.5) * (w1.y - w2.y)};
+                C ys = {T(0.5) * (w1.y + w2.y), T(-0.5) * (w1.x - w2.x)};
                 if (f.shift) {
-                    yn.x = -yn.x;
-                    yn.y = -yn.y;
-                    ys.x = -ys.x;
-                    ys.y = -ys.y;
+                    const C ph = cconj(phase_pi(k, n, T(0)));
+                    yn = cmul(yn, ph);
+                    ys = cmul(ys, ph);
+                }
+                for (int mm = k; mm <= L; mm += n) {
+                    Gn[mm] = yn;
+                    if (!single) Gs[mm] = ys;
+                    if (f.shift) {
+                        yn.x = -yn.x;
+                        yn.y = -yn.y;
+                        ys.x = -ys.x;
+                        ys.y = -ys.y;
+                    }
                 }
             }
         }
@@ -467,19 +505,26 @@ static int launch_ring(Plan *p, RingArgs<T> a, cudaStream_t st) {
     a.tw_blo = p->tw_blo;
     a.tw_nlo = p->tw_nlo;
     a.tw_nhi = p->tw_nhi;
-    auto kern = k_ring<T, MODE>;
     // direct (power-of-two) and Bluestein ring pairs run as separate launches so
-    // that each gets the shared memory its own transform length needs
+    // that each gets the shared memory and thread count its transform length needs
     prof_begin(p, sizeof(T) == 8 ? K_RING64 : K_RING32, st);
     for (int g = 0; g < 2; ++g) {
         const int cnt = p->ring_group_count[g];
         if (cnt == 0) continue;
         const int M = 1 << p->ring_group_logm[g];
         const size_t smem = sizeof(C) * ((size_t)p->tw_nlo + p->tw_nhi + M + M / 16);
-        if (smem > 48 * 1024)
-            SHTG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         a.pairs = p->d_ring_groups + (g ? p->ring_group_count[0] : 0);
-        kern<<<cnt, RingNT<T>::v, smem, st>>>(a);
+        if (M <= 4096) {
+            auto kern = k_ring<T, MODE, 256>;
+            if (smem > 48 * 1024)
+                SHTG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            kern<<<cnt, 256, smem, st>>>(a);
+        } else {
+            auto kern = k_ring<T, MODE, 512>;
+            if (smem > 48 * 1024)
+                SHTG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            kern<<<cnt, 512, smem, st>>>(a);
+        }
     }
     prof_end(p, st, (p->ring_group_count[0] > 0) + (p->ring_group_count[1] > 0));
     SHTG_CHECK_LAUNCH("k_ring");
