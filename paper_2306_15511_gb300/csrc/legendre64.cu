@@ -9,15 +9,15 @@ namespace shtg {
 
 const Variants64 &variants64() {
     static const Variants64 V = {
-        {3, 2, 3, 2},
-        {{SV(0, 2, 2), SV(0, 2, 4), SV(0, 1, 4)},
-         {SV(2, 1, 2), SV(2, 1, 4)}},
-        {{AV(0, 2, 1), AV(0, 4, 1), AV(0, 2, 2)},
-         {AV(2, 1, 1), AV(2, 2, 1)}},
-        {{{2, 2}, {2, 4}, {1, 4}},
-         {{1, 2}, {1, 4}},
-         {{2, 1}, {4, 1}, {2, 2}},
-         {{1, 1}, {2, 1}}}};
+        {5, 4, 6, 4},
+        {{SV(0, 2, 2), SV(0, 2, 4), SV(0, 1, 4), SV(0, 4, 2), SV(0, 4, 4)},
+         {SV(2, 1, 2), SV(2, 1, 4), SV(2, 2, 2), SV(2, 2, 1)}},
+        {{AV(0, 2, 1), AV(0, 4, 1), AV(0, 2, 2), AV(0, 8, 1), AV(0, 6, 1), AV(0, 4, 2)},
+         {AV(2, 1, 1), AV(2, 2, 1), AV(2, 4, 1), AV(2, 3, 1)}},
+        {{{2, 2}, {2, 4}, {1, 4}, {4, 2}, {4, 4}},
+         {{1, 2}, {1, 4}, {2, 2}, {2, 1}},
+         {{2, 1}, {4, 1}, {2, 2}, {8, 1}, {6, 1}, {4, 2}},
+         {{1, 1}, {2, 1}, {4, 1}, {3, 1}}}};
     return V;
 }
 
