@@ -134,8 +134,9 @@ def make_inputs(plan, device, seed_shift=0):
     if seed_shift:
         # a replica on another rank draws fresh white noise (independent chains)
         from inputs import philox as px
+        from paper_2306_15511_gb300.replicas import w2_key
         for b, p in enumerate(probs):
-            key = 50000 + 100 * seed_shift + b
+            key = w2_key(seed_shift, b)
             for k in range(3):
                 p.w2[k] = px.normal_torch(key, px.STREAM_W2, plan.npix, k * plan.npix, device)
     p0 = probs[0]
@@ -234,34 +235,15 @@ def run_reference(args):
 # --------------------------------------------------------------- GPU arm
 def run_gpu(args):
     import torch
-    import torch.distributed as dist
     from paper_2306_15511_gb300 import Plan
+    from paper_2306_15511_gb300.replicas import Replicas
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=dev)
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
-    def sum_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+    rep = Replicas("nccl", dev)
+    rank, world = rep.rank, rep.world
+    barrier, max_over_ranks, sum_over_ranks = rep.barrier, rep.max, rep.sum
 
     plan = Plan(nside=NSIDE, lmax=LMAX, max_batch=NB, spin2=True)
     inp = make_inputs(plan, dev, seed_shift=rank)
@@ -323,8 +305,7 @@ def run_gpu(args):
                "d2h_bytes_per_step": int(hout.numel() * 16), "steps": ke}
 
     if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
+        rep.close()
         return 0
 
     # -------------------------------------------------------------- extras
@@ -388,8 +369,7 @@ def run_gpu(args):
         "extras": extras,
     }
     print(json.dumps(line), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+    rep.close()
     return 0
 
 
