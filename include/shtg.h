@@ -81,6 +81,10 @@ extern "C" {
 
 #define SHTG_HOST_INPUTS 1           /* cg_sample flag: problem maps/alm and output are host pointers */
 #define SHTG_PROFILE 2               /* cg_sample flag: time kernel classes with CUDA events */
+#define SHTG_NO_GRAPHS 4             /* cg_sample flag: launch every PCG iteration eagerly instead of
+                                        replaying one captured iteration as a CUDA graph (graphs are
+                                        also off with SHTG_PROFILE, or with SHTG_GRAPHS=0 in the
+                                        environment); results are identical either way */
 
 typedef struct shtg_plan shtg_plan;
 

@@ -19,6 +19,7 @@ SPIN0, SPIN2 = 1, 2
 CG_FP64, CG_MIXED, CG_MIXED_TC = 0, 1, 2
 HOST_INPUTS = 1
 PROFILE = 2
+NO_GRAPHS = 4
 GRAD_COMPONENTS = 1
 
 # every symbol include/shtg.h declares

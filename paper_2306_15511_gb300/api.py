@@ -161,8 +161,11 @@ class Plan:
     def cg_sample(self, cl, bl, ninv, d, w1, w2, tol: float = 1e-6, mode: str = "mixed",
                   maxiter: int = 4000, precond: bool = True, reliable_delta: float = 1e-2,
                   check_every: int = 4, out=None,
-                  allow_not_converged: bool = False, profile: bool = False):
+                  allow_not_converged: bool = False, profile: bool = False, graphs: bool = True):
         """Constrained realization(s) of Eq. (mapmakingeq).
+
+        graphs: replay one captured PCG iteration as a CUDA graph between the
+        convergence checks (same results as eager launches; off while profiling).
 
         d, w2: [nbatch, ncomp, npix] float64; w1: [nbatch, ncomp, nalm] complex128;
         ninv: [npix] (T) or [2, npix] (T, P).  All CUDA tensors, or all host
@@ -191,7 +194,7 @@ class Plan:
         o.precond = 1 if precond else 0
         o.reliable_delta, o.reserved = float(reliable_delta), 0
         o.check_every = int(check_every)
-        o.flags = (N.HOST_INPUTS if host else 0) | (N.PROFILE if profile else 0)
+        o.flags = (N.HOST_INPUTS if host else 0) | (N.PROFILE if profile else 0) | (0 if graphs else N.NO_GRAPHS)
         st = N.CGStats()
         rc = self._lib.shtg_cg_sample(self._h, C.byref(pr), _ptr(out), C.byref(o), C.byref(st),
                                       _stream())

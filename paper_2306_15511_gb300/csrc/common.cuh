@@ -142,6 +142,7 @@ struct Plan {
     double *d_scal = nullptr;      // [max_batch][16] per-realization PCG scalars
     double *d_part = nullptr;      // reduction partial sums
     int *d_flag = nullptr;         // [0]: set by a kernel whose bounded device wait expired
+    cudaStream_t cap_stream = nullptr;   // non-blocking stream on which solver iterations are captured
     // FP32 recurrence states every 32 l (tensor-core transpose): entry
     // (m, t, pair) at (d_toff[m] + t) * npairs + pair is the state before
     // l = m + 32 t: (lambda_{l-1}, lambda_{l-2}) for spin 0, (y+_{l-1},

@@ -627,6 +627,7 @@ int plan_build(Plan *p) {
     SHTG_TRY(dalloc(p, &p->d_scal, 16 * (int64_t)p->max_batch));
     SHTG_TRY(dalloc(p, &p->d_part, 4 * (int64_t)p->max_batch * SHTG_RED_BLOCKS + 4 * (int64_t)p->max_batch + 64));
     SHTG_TRY(dalloc(p, &p->d_lsum, (int64_t)p->lmax + 1));
+    SHTG_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
     SHTG_TRY(dalloc(p, &p->d_flag, 16));
     SHTG_CUDA(cudaMemset(p->d_flag, 0, 16 * sizeof(int)));
     SHTG_TRY(dalloc(p, &p->d_stage, nmp));
@@ -656,6 +657,7 @@ void plan_free(Plan *p) {
     for (int i = 0; i < 5; ++i)
         if (p->v32[i]) cudaFree(p->v32[i]);
     if (p->h_pinned) cudaFreeHost(p->h_pinned);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     for (auto &e : p->prof.ev)
         if (e) cudaEventDestroy(e);
     p->prof.ev.clear();

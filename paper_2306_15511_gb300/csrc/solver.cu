@@ -487,11 +487,29 @@ __global__ void k_grad_prior(const float2 *__restrict__ a, float2 *__restrict__ 
 }
 
 // ====================================================================== host
+// One PCG iteration (operator application + vector updates) captured as a
+// CUDA graph and replayed between the host's convergence checks: the
+// iteration's pointers and per-realization scalars live on the device, so
+// every iteration launches the same work.
+struct IterGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;   // library launches in one replay
+    void release() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        exec = nullptr;
+        graph = nullptr;
+    }
+    ~IterGraph() { release(); }
+};
+
 struct Solve {
     Plan *p;
     cudaStream_t st;
     int nb, nc;
-    int tc = 0;   // FP32 operator: Legendre synthesis on the tensor cores
+    int tc = 0;      // FP32 operator: Legendre sums on the tensor cores
+    int graphs = 1;  // replay captured iterations (off while profiling)
     int64_t nalm, per, nvec;
     dim3 vgrid;   // (blocks, nb)
     dim3 rgrid;   // (RB, nb)
@@ -567,6 +585,69 @@ static int matvec(Solve &s, const typename HT<T>::C *x, typename HT<T>::C *y) {
     return SHTG_OK;
 }
 
+// One PCG iteration on the device: q = A p, alpha, x/r/z update, beta, p.
+template <typename T>
+static int pcg_iteration(Solve &s, typename HT<T>::C *x, typename HT<T>::C *r, typename HT<T>::C *z,
+                         typename HT<T>::C *pv, typename HT<T>::C *q, const T *minv) {
+    typedef typename HT<T>::C C;
+    Plan *p = s.p;
+    SHTG_TRY(matvec<T>(s, pv, q));
+    prof_begin(p, K_VEC, s.st);
+    k_dot<C><<<s.rgrid, RT, 0, s.st>>>(pv, q, s.nc, s.nalm, p->d_mofidx, p->d_part, 0, 1);
+    k_scal_alpha<<<1, 1024, 0, s.st>>>(p->d_part, p->d_scal, s.nb);
+    k_update<T, false><<<s.rgrid, RT, 0, s.st>>>(x, r, z, pv, q, minv, s.nc, s.nalm, p->d_mofidx,
+                                                 p->d_scal, p->d_part);
+    k_scal_beta<<<1, 1024, 0, s.st>>>(p->d_part, p->d_scal, s.nb);
+    k_pupdate<C><<<dim3(grid_1d(s.per).x, s.nb), RT, 0, s.st>>>(pv, z, s.nc, s.nalm, p->d_scal);
+    prof_end(p, s.st, 5);
+    SHTG_CHECK_LAUNCH("pcg iteration");
+    return SHTG_OK;
+}
+
+// nrun iterations.  With graphs on (and profiling off) the first call runs
+// one iteration eagerly (any autotuning happens there), captures the next
+// one into g and replays it for the rest; later calls only replay.
+template <typename T>
+static int run_iterations(Solve &s, IterGraph &g, int nrun, typename HT<T>::C *x, typename HT<T>::C *r,
+                          typename HT<T>::C *z, typename HT<T>::C *pv, typename HT<T>::C *q,
+                          const T *minv) {
+    Plan *p = s.p;
+    if (!s.graphs || p->prof.on) {
+        for (int k = 0; k < nrun; ++k) SHTG_TRY(pcg_iteration<T>(s, x, r, z, pv, q, minv));
+        return SHTG_OK;
+    }
+    if (!g.exec && nrun > 0) {
+        SHTG_TRY(pcg_iteration<T>(s, x, r, z, pv, q, minv));
+        --nrun;
+        if (nrun == 0) return SHTG_OK;
+        // capture on the plan's own stream (the caller's may be the legacy
+        // default stream, which cannot be captured); capturing runs nothing,
+        // and the replays go to the caller's stream
+        const long long l0 = p->prof.launches;
+        const cudaStream_t caller = s.st;
+        s.st = p->cap_stream;
+        SHTG_CUDA(cudaStreamBeginCapture(s.st, cudaStreamCaptureModeRelaxed));
+        const int rc = pcg_iteration<T>(s, x, r, z, pv, q, minv);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(s.st, &graph);
+        s.st = caller;
+        g.launches = p->prof.launches - l0;
+        p->prof.launches = l0;
+        if (rc != SHTG_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+        g.graph = graph;
+        SHTG_CUDA(cudaGraphInstantiate(&g.exec, graph, 0));
+    }
+    for (int k = 0; k < nrun; ++k) {
+        SHTG_CUDA(cudaGraphLaunch(g.exec, s.st));
+        p->prof.launches += g.launches;
+    }
+    return SHTG_OK;
+}
+
 // PCG on A x = b for T vectors; x starts at 0.  Per-realization convergence
 // at ||r|| <= tol ||b||.  Returns the number of iterations run.
 template <typename T>
@@ -577,6 +658,7 @@ static int pcg(Solve &s, const typename HT<T>::C *b, typename HT<T>::C *x, doubl
     C *r = Vec<T>::r(p), *z = Vec<T>::z(p), *pv = Vec<T>::pp(p), *q = Vec<T>::q(p);
     const T *minv = Vec<T>::minv(p);
     const size_t vb = sizeof(C) * (size_t)s.nvec;
+    IterGraph graph;
     SHTG_CUDA(cudaMemsetAsync(x, 0, vb, s.st));
     SHTG_CUDA(cudaMemcpyAsync(r, b, vb, cudaMemcpyDeviceToDevice, s.st));
     k_update<T, true><<<s.rgrid, RT, 0, s.st>>>(nullptr, r, z, nullptr, nullptr, minv, s.nc, s.nalm,
@@ -609,18 +691,7 @@ static int pcg(Solve &s, const typename HT<T>::C *b, typename HT<T>::C *x, doubl
             break;
         }
         const int nrun = std::min(check_every, maxiter - it);
-        for (int k = 0; k < nrun; ++k) {
-            SHTG_TRY(matvec<T>(s, pv, q));
-            prof_begin(p, K_VEC, s.st);
-            k_dot<C><<<s.rgrid, RT, 0, s.st>>>(pv, q, s.nc, s.nalm, p->d_mofidx, p->d_part, 0, 1);
-            k_scal_alpha<<<1, 1024, 0, s.st>>>(p->d_part, p->d_scal, s.nb);
-            k_update<T, false><<<s.rgrid, RT, 0, s.st>>>(x, r, z, pv, q, minv, s.nc, s.nalm,
-                                                         p->d_mofidx, p->d_scal, p->d_part);
-            k_scal_beta<<<1, 1024, 0, s.st>>>(p->d_part, p->d_scal, s.nb);
-            k_pupdate<C><<<dim3(grid_1d(s.per).x, s.nb), RT, 0, s.st>>>(pv, z, s.nc, s.nalm, p->d_scal);
-            prof_end(p, s.st, 5);
-            SHTG_CHECK_LAUNCH("pcg iteration");
-        }
+        SHTG_TRY(run_iterations<T>(s, graph, nrun, x, r, z, pv, q, minv));
         it += nrun;
     }
     if (!*all_converged) {
@@ -814,6 +885,7 @@ static int mixed_solve(Solve &s, const shtg_cg_opts &opt, const std::vector<doub
     SHTG_CUDA(cudaMemsetAsync(X, 0, sizeof(double2) * (size_t)s.nvec, st));
     SHTG_CUDA(cudaMemcpyAsync(R, B, sizeof(double2) * (size_t)s.nvec, cudaMemcpyDeviceToDevice, st));
     rr = bb;
+    IterGraph graph;
     int it = 0, first = 1;
     for (;;) {
         // ---- residual replacement (the first pass starts the iteration)
@@ -849,18 +921,7 @@ static int mixed_solve(Solve &s, const shtg_cg_opts &opt, const std::vector<doub
         int since = 0;
         for (;;) {
             const int nrun = std::min(std::max(1, opt.check_every), opt.maxiter - it);
-            for (int k = 0; k < nrun; ++k) {
-                SHTG_TRY(matvec<float>(s, p32, q32));
-                prof_begin(p, K_VEC, st);
-                k_dot<float2><<<s.rgrid, RT, 0, st>>>(p32, q32, s.nc, s.nalm, p->d_mofidx, p->d_part, 0, 1);
-                k_scal_alpha<<<1, 1024, 0, st>>>(p->d_part, p->d_scal, nb);
-                k_update<float, false><<<s.rgrid, RT, 0, st>>>(x32, r32, z32, p32, q32, minv, s.nc,
-                                                               s.nalm, p->d_mofidx, p->d_scal, p->d_part);
-                k_scal_beta<<<1, 1024, 0, st>>>(p->d_part, p->d_scal, nb);
-                k_pupdate<float2><<<dim3(grid_1d(s.per).x, nb), RT, 0, st>>>(p32, z32, s.nc, s.nalm, p->d_scal);
-                prof_end(p, st, 5);
-                SHTG_CHECK_LAUNCH("pcg iteration");
-            }
+            SHTG_TRY(run_iterations<float>(s, graph, nrun, x32, r32, z32, p32, q32, minv));
             it += nrun;
             SHTG_CUDA(cudaMemcpyAsync(p->h_pinned, p->d_scal, sizeof(double) * 16 * nb,
                                       cudaMemcpyDeviceToHost, st));
@@ -937,6 +998,10 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
     const int nb = pr->nbatch, nc = pr->ncomp;
     Solve s = make_solve(p, nb, nc, st);
     s.tc = opt.mode == SHTG_CG_MIXED_TC;
+    {
+        const char *e = getenv("SHTG_GRAPHS");
+        s.graphs = !(opt.flags & SHTG_NO_GRAPHS) && !(e && e[0] == '0');
+    }
     SHTG_TRY(setup_operator(p, pr, host, opt.precond, st));
     double2 *B = p->v64[0], *X = p->v64[1], *R = p->v64[2], *Tt = p->v64[6];
     // ---- RHS: B Y^T (N^-1 d + N^-1/2 w2) + S^-1/2 w1 in FP64

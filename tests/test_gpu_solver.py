@@ -169,3 +169,23 @@ def test_autograd_alm2map_and_logposterior():
     assert rel_l2(th.grad.cpu().numpy(), gl_ref) < 1e-5
     w_m = np.where(osht.ms_of(32) == 0, 1.0, 2.0)
     assert rel_l2(al.grad.cpu().numpy(), w_m * ga_ref[0]) < 1e-4
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "mixed_tc"])
+def test_graph_replay_matches_eager(mode):
+    """The captured-and-replayed PCG iteration gives the same solution, bit for
+    bit, as eager launches (same kernels in the same order)."""
+    from paper_2306_15511_gb300 import Plan
+    p = C.config(4, nside=16, lmax=32, batch=2)
+    g = osht.healpix(16)
+    plan = Plan(nside=16, lmax=32, max_batch=2, spin2=True)
+    ds = np.stack([_data(q, g) for q in p])
+    args = (p[0].cl, p[0].bl, _cuda(p[0].ninv, torch.float64), _cuda(ds, torch.float64),
+            _cuda(np.stack([q.w1 for q in p]), torch.complex128),
+            _cuda(np.stack([q.w2 for q in p]), torch.float64))
+    plan.cg_sample(*args, tol=1e-6, mode=mode, maxiter=3000, check_every=8)   # autotuner trials
+    xg, sg = plan.cg_sample(*args, tol=1e-6, mode=mode, maxiter=3000, check_every=8, graphs=True)
+    xe, se = plan.cg_sample(*args, tol=1e-6, mode=mode, maxiter=3000, check_every=8, graphs=False)
+    assert sg["converged"] == 1 and sg["iterations"] == se["iterations"]
+    assert torch.equal(xg, xe)
+    assert sg["launches"] == se["launches"]
