@@ -439,7 +439,43 @@ def measure_extras(plan, inp, dev, kw, full_solve=True):
         # 1e-6 is extrapolated from its measured per-iteration time
         ex["fp64_form"]["time_to_1e-6_s_extrapolated"] = st["ms_rhs"] / 1000.0 + fs["iterations"] * per_it
         ex["mixed_speedup_time_to_1e-6"] = ex["fp64_form"]["time_to_1e-6_s_extrapolated"] / fs["time_to_1e-6_s"]
+    ex["c2_chains"] = measure_chains(dev)
     return ex
+
+
+def measure_chains(dev, nchains=64):
+    """Config-2 recipe: 64 independent chains with N_side in {64, 128, 256},
+    l_max in {2 N_side, 3 N_side - 1} and their own signal amplitudes, all
+    solved to 1e-6 in one chains call (one plan per geometry)."""
+    import torch
+    from inputs import configs as C
+    from paper_2306_15511_gb300 import Plan, chains_sample
+    groups = {}
+    for ch in C.config(2, batch=nchains):
+        groups.setdefault((ch.nside, ch.lmax), []).append(ch)
+    req = []
+    for (ns, L), chs in sorted(groups.items()):
+        plan = Plan(nside=ns, lmax=L, max_batch=len(chs))
+        ls = torch.as_tensor(C.alm_lm(L)[0], device=dev)
+        bl = torch.as_tensor(chs[0].bl, device=dev)
+        a = torch.stack([torch.as_tensor(ch.signal_alm[0], device=dev) for ch in chs]) * bl[ls]
+        n = torch.stack([torch.as_tensor(ch.noise_map[0], device=dev) for ch in chs])
+        d = (plan.alm2map(a.contiguous()) + n)[:, None].contiguous()
+        req.append({"plan": plan, "cl": C.cl_flat(L), "bl": chs[0].bl,
+                    "ninv": torch.as_tensor(chs[0].ninv, device=dev).contiguous(), "d": d,
+                    "w1": torch.stack([torch.as_tensor(ch.w1, device=dev) for ch in chs]).contiguous(),
+                    "w2": torch.stack([torch.as_tensor(ch.w2, device=dev) for ch in chs]).contiguous(),
+                    "cl_scale": [ch.extra["amp"] for ch in chs]})
+    chains_sample(req, tol=1e-6, mode="mixed_tc", maxiter=4000)   # autotuning and warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = chains_sample(req, tol=1e-6, mode="mixed_tc", maxiter=4000)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    return {"chains": nchains, "groups": len(req), "time_to_1e-6_s": el, "chains_per_s": nchains / el,
+            "geometries": [f"N_side {ns} l_max {L} x{len(chs)}" for (ns, L), chs in sorted(groups.items())],
+            "iterations": [st["iterations"] for _, st in res],
+            "converged": all(st["converged"] == 1 for _, st in res)}
 
 
 def main():

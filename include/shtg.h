@@ -167,6 +167,10 @@ typedef struct {
     const double *d;  /* [nbatch][ncomp][npix] data maps (T or T, Q, U) */
     const double *w1; /* [nbatch][ncomp][nalm] complex128 unit white noise in harmonic space */
     const double *w2; /* [nbatch][ncomp][npix] unit white noise in pixel space */
+    const double *cl_scale; /* HOST, optional. [nbatch]: realization b's C_l (the whole T/E/B
+                               block) is cl_scale[b] x cl; null = all 1.  Independent chains of
+                               one geometry with different signal amplitudes share one call.
+                               Entries must be positive. */
 } shtg_problem;
 
 typedef struct {
@@ -211,6 +215,21 @@ typedef struct {
  * mixed, preconditioned). */
 int shtg_cg_sample(shtg_plan *plan, const shtg_problem *prob, double *alm_out,
                    const shtg_cg_opts *opts, shtg_cg_stats *stats, void *stream);
+
+/* Many independent chains of uneven geometry in one call (the batching of
+ * Sect. 2.2 across Gibbs chains): group g's realizations share the geometry
+ * of plans[g] (its N_side, l_max), its beam and N^-1, and are problems[g]
+ * (nbatch realizations with their own amplitudes through cl_scale);
+ * alm_out[g] as in shtg_cg_sample.  Every group needs its own plan.  Groups
+ * run concurrently, each on its plan's own stream, after the work queued on
+ * `stream` and before anything queued on it later; realizations that have
+ * converged stop updating while the others go on.  stats: [ngroups] or
+ * NULL.  Returns the first error other than SHTG_ERR_NOT_CONVERGED, else
+ * SHTG_ERR_NOT_CONVERGED if a group did not converge, else SHTG_OK; the
+ * error string names the group. */
+int shtg_cg_sample_chains(int ngroups, shtg_plan *const *plans, const shtg_problem *problems,
+                          double *const *alm_out, const shtg_cg_opts *opts, shtg_cg_stats *stats,
+                          void *stream);
 
 /* Apply the operator A of Eq. (mapmakingeq) once: y = S^-1 x + B Y^T N^-1 Y B x
  * (x, y: device [nbatch][ncomp][nalm] complex128, FP64), using the problem's

@@ -26,7 +26,8 @@ GRAD_COMPONENTS = 1
 SYMBOLS = ("shtg_plan_create", "shtg_plan_destroy", "shtg_plan_get_info",
            "shtg_last_error_string", "shtg_version", "shtg_alm2map", "shtg_alm2map_adjoint",
            "shtg_alm2map_vjp",
-           "shtg_map2alm", "shtg_cg_sample", "shtg_apply_operator", "shtg_logpost_grad")
+           "shtg_map2alm", "shtg_cg_sample", "shtg_cg_sample_chains", "shtg_apply_operator",
+           "shtg_logpost_grad")
 
 
 class PlanInfo(C.Structure):
@@ -37,7 +38,8 @@ class PlanInfo(C.Structure):
 
 class Problem(C.Structure):
     _fields_ = [("ncomp", C.c_int), ("nbatch", C.c_int), ("cl", C.c_void_p), ("bl", C.c_void_p),
-                ("ninv", C.c_void_p), ("d", C.c_void_p), ("w1", C.c_void_p), ("w2", C.c_void_p)]
+                ("ninv", C.c_void_p), ("d", C.c_void_p), ("w1", C.c_void_p), ("w2", C.c_void_p),
+                ("cl_scale", C.c_void_p)]
 
 
 class CGOpts(C.Structure):

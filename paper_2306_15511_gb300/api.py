@@ -147,11 +147,18 @@ class Plan:
     def _host_f64(a):
         return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
 
-    def _problem(self, cl, bl, ninv, d=None, w1=None, w2=None, nbatch=1, ncomp=1):
+    def _problem(self, cl, bl, ninv, d=None, w1=None, w2=None, nbatch=1, ncomp=1, cl_scale=None):
         self._keep = [self._host_f64(cl), self._host_f64(bl)]
         pr = N.Problem()
         pr.ncomp, pr.nbatch = ncomp, nbatch
         pr.cl, pr.bl = _ptr(self._keep[0]), _ptr(self._keep[1])
+        pr.cl_scale = None
+        if cl_scale is not None:
+            sc = self._host_f64(cl_scale).reshape(-1)
+            if sc.size != nbatch:
+                raise ValueError("cl_scale needs one entry per realization")
+            self._keep.append(sc)
+            pr.cl_scale = _ptr(sc)
         pr.ninv = _ptr(ninv)
         pr.d = _ptr(d) if d is not None else None
         pr.w1 = _ptr(w1) if w1 is not None else None
@@ -161,8 +168,11 @@ class Plan:
     def cg_sample(self, cl, bl, ninv, d, w1, w2, tol: float = 1e-6, mode: str = "mixed",
                   maxiter: int = 4000, precond: bool = True, reliable_delta: float = 1e-2,
                   check_every: int = 4, out=None,
-                  allow_not_converged: bool = False, profile: bool = False, graphs: bool = True):
+                  allow_not_converged: bool = False, profile: bool = False, graphs: bool = True,
+                  cl_scale=None):
         """Constrained realization(s) of Eq. (mapmakingeq).
+
+        cl_scale: optional [nbatch] amplitudes; realization b uses cl_scale[b] x cl.
 
         graphs: replay one captured PCG iteration as a CUDA graph between the
         convergence checks (same results as eager launches; off while profiling).
@@ -184,7 +194,7 @@ class Plan:
                     raise ValueError(f"{name}: mix of host and device buffers")
                 if not t.is_contiguous():
                     raise ValueError(f"{name} must be contiguous")
-        pr = self._problem(cl, bl, ninv, d, w1, w2, nb, nc)
+        pr = self._problem(cl, bl, ninv, d, w1, w2, nb, nc, cl_scale)
         o = N.CGOpts()
         o.tol, o.maxiter = float(tol), int(maxiter)
         modes = {"fp64": N.CG_FP64, "mixed": N.CG_MIXED, "mixed_tc": N.CG_MIXED_TC}
@@ -201,11 +211,11 @@ class Plan:
         N.check(rc, allow=(-3,) if allow_not_converged else ())
         return out, st.as_dict()
 
-    def apply_operator(self, cl, bl, ninv, x: torch.Tensor) -> torch.Tensor:
+    def apply_operator(self, cl, bl, ninv, x: torch.Tensor, cl_scale=None) -> torch.Tensor:
         """y = (S^-1 + B Y^T N^-1 Y B) x for x [nbatch, ncomp, nalm] complex128 (CUDA)."""
         _need_cuda(x, "x")
         y = torch.empty_like(x)
-        pr = self._problem(cl, bl, ninv, nbatch=int(x.shape[0]), ncomp=int(x.shape[1]))
+        pr = self._problem(cl, bl, ninv, nbatch=int(x.shape[0]), ncomp=int(x.shape[1]), cl_scale=cl_scale)
         N.check(self._lib.shtg_apply_operator(self._h, C.byref(pr), _ptr(x), _ptr(y), _stream()))
         return y
 
@@ -227,3 +237,51 @@ class Plan:
             N.GRAD_COMPONENTS if components else 0, C.byref(logp),
             _ptr(g) if g is not None else None, _ptr(gcl) if len(bins) else None, _stream()))
         return logp.value, g, gcl
+
+
+def chains_sample(groups, tol: float = 1e-6, mode: str = "mixed_tc", maxiter: int = 4000,
+                  precond: bool = True, reliable_delta: float = 1e-2, check_every: int = 4,
+                  allow_not_converged: bool = False, graphs: bool = True):
+    """Constrained realizations of many chains of uneven geometry in one call.
+
+    groups: list of dicts, one per geometry, with keys plan, cl, bl, ninv, d,
+    w1, w2 (CUDA tensors shaped as for Plan.cg_sample) and optionally
+    cl_scale (one amplitude per realization of the group).  Every group needs
+    its own Plan.  Returns a list of (alm, stats) per group."""
+    if not groups:
+        raise ValueError("no groups")
+    lib = N.load()
+    n = len(groups)
+    plans = (C.c_void_p * n)()
+    probs = (N.Problem * n)()
+    outs = (C.c_void_p * n)()
+    stats = (N.CGStats * n)()
+    keep, results = [], []
+    for g, grp in enumerate(groups):
+        plan, d = grp["plan"], grp["d"]
+        for name in ("d", "w1", "w2", "ninv"):
+            _need_cuda(grp[name], name)
+        nb, nc = int(d.shape[0]), int(d.shape[1])
+        out = torch.empty(nb, nc, plan.nalm, dtype=torch.complex128, device=d.device)
+        pr = plan._problem(grp["cl"], grp["bl"], grp["ninv"], d, grp["w1"], grp["w2"], nb, nc,
+                           grp.get("cl_scale"))
+        keep.append(list(plan._keep))
+        plans[g] = plan._h
+        probs[g] = pr
+        outs[g] = out.data_ptr()
+        results.append(out)
+    o = N.CGOpts()
+    o.tol, o.maxiter = float(tol), int(maxiter)
+    modes = {"fp64": N.CG_FP64, "mixed": N.CG_MIXED, "mixed_tc": N.CG_MIXED_TC}
+    if mode not in modes:
+        raise ValueError(f"mode must be one of {sorted(modes)}")
+    o.mode = modes[mode]
+    o.precond = 1 if precond else 0
+    o.reliable_delta, o.reserved = float(reliable_delta), 0
+    o.check_every = int(check_every)
+    o.flags = 0 if graphs else N.NO_GRAPHS
+    rc = lib.shtg_cg_sample_chains(n, plans, probs, outs, C.byref(o), stats, _stream())
+    N.check(rc, allow=(-3,) if allow_not_converged else ())
+    del keep
+    return [(results[g], stats[g].as_dict()) for g in range(n)]
+

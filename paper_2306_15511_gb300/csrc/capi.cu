@@ -4,6 +4,8 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <thread>
+#include <vector>
 
 #include "common.cuh"
 
@@ -284,6 +286,66 @@ int shtg_cg_sample(shtg_plan *plan, const shtg_problem *prob, double *alm_out,
     }
     return cg_sample(reinterpret_cast<Plan *>(plan), prob, alm_out, opts, stats,
                      (cudaStream_t)stream);
+}
+
+int shtg_cg_sample_chains(int ngroups, shtg_plan *const *plans, const shtg_problem *probs,
+                          double *const *alm_out, const shtg_cg_opts *opts, shtg_cg_stats *stats,
+                          void *stream) {
+    if (ngroups < 1 || !plans || !probs || !alm_out) {
+        set_error("chains: need ngroups >= 1, plans, problems and outputs");
+        return SHTG_ERR_ARG;
+    }
+    for (int g = 0; g < ngroups; ++g) {
+        if (!plans[g]) {
+            set_error("chains: null plan");
+            return SHTG_ERR_ARG;
+        }
+        for (int h = 0; h < g; ++h)
+            if (plans[h] == plans[g]) {
+                set_error("chains: every group needs its own plan (a plan's workspace serves one solve)");
+                return SHTG_ERR_ARG;
+            }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (ngroups == 1)
+        return cg_sample(reinterpret_cast<Plan *>(plans[0]), &probs[0], alm_out[0], opts,
+                         stats ? &stats[0] : nullptr, st);
+    // fork: every group's work stream waits for the caller's stream
+    cudaEvent_t fork;
+    SHTG_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    SHTG_CUDA(cudaEventRecord(fork, st));
+    for (int g = 0; g < ngroups; ++g)
+        SHTG_CUDA(cudaStreamWaitEvent(reinterpret_cast<Plan *>(plans[g])->work_stream, fork, 0));
+    // one host thread per group: a solve waits on the host at its convergence checks
+    std::vector<int> rc(ngroups, SHTG_OK);
+    std::vector<std::string> msg(ngroups);
+    std::vector<std::thread> th;
+    for (int g = 0; g < ngroups; ++g) {
+        th.emplace_back([&, g]() {
+            Plan *p = reinterpret_cast<Plan *>(plans[g]);
+            if (cudaSetDevice(p->device) != cudaSuccess) {
+                rc[g] = SHTG_ERR_CUDA;
+                msg[g] = "cudaSetDevice failed";
+                return;
+            }
+            rc[g] = cg_sample(p, &probs[g], alm_out[g], opts, stats ? &stats[g] : nullptr, p->work_stream);
+            if (rc[g] != SHTG_OK) msg[g] = shtg_last_error_string();
+        });
+    }
+    for (auto &t : th) t.join();
+    // join: the caller's stream waits for every group
+    for (int g = 0; g < ngroups; ++g) {
+        SHTG_CUDA(cudaEventRecord(fork, reinterpret_cast<Plan *>(plans[g])->work_stream));
+        SHTG_CUDA(cudaStreamWaitEvent(st, fork, 0));
+    }
+    cudaEventDestroy(fork);
+    int worst = SHTG_OK;
+    for (int g = 0; g < ngroups; ++g)
+        if (rc[g] != SHTG_OK && (worst == SHTG_OK || worst == SHTG_ERR_NOT_CONVERGED)) {
+            worst = rc[g];
+            set_error("chain group " + std::to_string(g) + ": " + msg[g]);
+        }
+    return worst;
 }
 
 int shtg_apply_operator(shtg_plan *plan, const shtg_problem *prob, const double *x, double *y,

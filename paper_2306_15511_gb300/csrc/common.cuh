@@ -133,8 +133,11 @@ struct Plan {
     // solver workspace (vectors hold max_batch realizations of all components)
     double2 *v64[7] = {};          // b, x, r, z, p, q, t
     float2 *v32[5] = {};           // r, z, p, q, x
-    double *d_minv64 = nullptr;    // [4][nalm] preconditioner blocks (inverse)
+    double *d_minv64 = nullptr;    // [max_batch][4][nalm] inverse preconditioner blocks per realization
     float *d_minv32 = nullptr;
+    double *d_isc64 = nullptr;          // [max_batch] 1 / (C_l scale), 1 / sqrt(C_l scale)
+    double *d_rsc64 = nullptr;
+    float *d_isc32 = nullptr;
     float *d_diagT = nullptr, *d_diagP = nullptr;   // [nalm] ring-averaged diag of Y^T N^-1 Y
     float *d_wpairT = nullptr, *d_wpairP = nullptr; // [npairs] N^-1 summed over the ring pair
     double *d_ltab64 = nullptr;    // [9][lmax+1] beam, S^-1 (TT,TE,EE,BB), S^-1/2 (TT,TE,EE,BB)
@@ -143,6 +146,7 @@ struct Plan {
     double *d_part = nullptr;      // reduction partial sums
     int *d_flag = nullptr;         // [0]: set by a kernel whose bounded device wait expired
     cudaStream_t cap_stream = nullptr;   // non-blocking stream on which solver iterations are captured
+    cudaStream_t work_stream = nullptr;  // non-blocking stream of this plan's solve in a chains call
     // FP32 recurrence states every 32 l (tensor-core transpose): entry
     // (m, t, pair) at (d_toff[m] + t) * npairs + pair is the state before
     // l = m + 32 t: (lambda_{l-1}, lambda_{l-2}) for spin 0, (y+_{l-1},

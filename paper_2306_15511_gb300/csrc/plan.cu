@@ -616,8 +616,11 @@ int plan_build(Plan *p) {
     const int64_t nv = (int64_t)p->nmaps_max * p->nalm;
     for (int i = 0; i < 7; ++i) SHTG_TRY(dalloc(p, &p->v64[i], nv));
     for (int i = 0; i < 5; ++i) SHTG_TRY(dalloc(p, &p->v32[i], nv));
-    SHTG_TRY(dalloc(p, &p->d_minv64, 4 * p->nalm));
-    SHTG_TRY(dalloc(p, &p->d_minv32, 4 * p->nalm));
+    SHTG_TRY(dalloc(p, &p->d_minv64, 4 * (int64_t)p->max_batch * p->nalm));
+    SHTG_TRY(dalloc(p, &p->d_minv32, 4 * (int64_t)p->max_batch * p->nalm));
+    SHTG_TRY(dalloc(p, &p->d_isc64, p->max_batch));
+    SHTG_TRY(dalloc(p, &p->d_rsc64, p->max_batch));
+    SHTG_TRY(dalloc(p, &p->d_isc32, p->max_batch));
     SHTG_TRY(dalloc(p, &p->d_diagT, p->nalm));
     SHTG_TRY(dalloc(p, &p->d_diagP, p->nalm));
     SHTG_TRY(dalloc(p, &p->d_wpairT, p->npairs));
@@ -628,6 +631,7 @@ int plan_build(Plan *p) {
     SHTG_TRY(dalloc(p, &p->d_part, 4 * (int64_t)p->max_batch * SHTG_RED_BLOCKS + 4 * (int64_t)p->max_batch + 64));
     SHTG_TRY(dalloc(p, &p->d_lsum, (int64_t)p->lmax + 1));
     SHTG_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+    SHTG_CUDA(cudaStreamCreateWithFlags(&p->work_stream, cudaStreamNonBlocking));
     SHTG_TRY(dalloc(p, &p->d_flag, 16));
     SHTG_CUDA(cudaMemset(p->d_flag, 0, 16 * sizeof(int)));
     SHTG_TRY(dalloc(p, &p->d_stage, nmp));
@@ -649,7 +653,7 @@ void plan_free(Plan *p) {
                     p->d_minv32, p->d_diagT, p->d_diagP, p->d_wpairT, p->d_wpairP,
                     p->d_ltab64, p->d_ltab32, p->d_scal, p->d_part, p->d_lsum, p->d_stage,
                     p->d_ls2_64, p->d_st2_64, p->d_ls2_32, p->d_st2_32, p->d_ring_groups, p->d_flag,
-                    p->d_toff, p->d_tst0, p->d_tst2};
+                    p->d_toff, p->d_tst0, p->d_tst2, p->d_isc64, p->d_rsc64, p->d_isc32};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (int i = 0; i < 7; ++i)
@@ -658,6 +662,7 @@ void plan_free(Plan *p) {
         if (p->v32[i]) cudaFree(p->v32[i]);
     if (p->h_pinned) cudaFreeHost(p->h_pinned);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    if (p->work_stream) cudaStreamDestroy(p->work_stream);
     for (auto &e : p->prof.ev)
         if (e) cudaEventDestroy(e);
     p->prof.ev.clear();

@@ -102,13 +102,14 @@ template <> struct HT<double> { typedef double2 C; };
 template <typename T>
 __global__ void k_prior_add(const typename HT<T>::C *__restrict__ x, typename HT<T>::C *__restrict__ y,
                             int nc, int64_t nalm, int lmax1, const int *__restrict__ lof,
-                            const T *__restrict__ sinv) {
+                            const T *__restrict__ sinv, const T *__restrict__ isc) {
     const int b = blockIdx.y;
     const int64_t off = (int64_t)b * nc * nalm;
+    const T sc = isc[b];   // 1 / (C_l scale of realization b)
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nalm;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int l = lof[i];
-        const T tt = sinv[l];
+        const T tt = sinv[l] * sc;
         if (nc == 1) {
             const auto xv = x[off + i];
             auto yv = y[off + i];
@@ -116,7 +117,7 @@ __global__ void k_prior_add(const typename HT<T>::C *__restrict__ x, typename HT
             yv.y += tt * xv.y;
             y[off + i] = yv;
         } else {
-            const T te = sinv[lmax1 + l], ee = sinv[2 * lmax1 + l], bb = sinv[3 * lmax1 + l];
+            const T te = sinv[lmax1 + l] * sc, ee = sinv[2 * lmax1 + l] * sc, bb = sinv[3 * lmax1 + l] * sc;
             const auto xt = x[off + i], xe = x[off + nalm + i], xb = x[off + 2 * nalm + i];
             auto yt = y[off + i], ye = y[off + nalm + i], yb = y[off + 2 * nalm + i];
             yt.x += tt * xt.x + te * xe.x;
@@ -136,14 +137,19 @@ __global__ void k_prior_add(const typename HT<T>::C *__restrict__ x, typename HT
 // nc = 1: minv[0] = 1 / M; nc = 3: minv[0..2] = inverse T/E block (11, 12, 22), minv[3] = 1 / M_BB.
 __global__ void k_precond(const float *__restrict__ dT, const float *__restrict__ dP,
                           const double *__restrict__ ltab, int nc, int64_t nalm, int lmax1,
-                          const int *__restrict__ lof, int use_diag, double *__restrict__ m64,
-                          float *__restrict__ m32) {
+                          const int *__restrict__ lof, int use_diag, const double *__restrict__ isc,
+                          double *__restrict__ m64, float *__restrict__ m32) {
+    // realization b = blockIdx.y: S^-1 / (its C_l scale); one [4][nalm] block each
+    const int b = blockIdx.y;
+    const double sc = isc[b];
+    m64 += (int64_t)b * 4 * nalm;
+    m32 += (int64_t)b * 4 * nalm;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nalm;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int l = lof[i];
         const double b2 = use_diag ? ltab[l] * ltab[l] : 0.0;
-        const double tt = ltab[lmax1 + l], te = ltab[2 * lmax1 + l], ee = ltab[3 * lmax1 + l],
-                     bb = ltab[4 * lmax1 + l];
+        const double tt = ltab[lmax1 + l] * sc, te = ltab[2 * lmax1 + l] * sc, ee = ltab[3 * lmax1 + l] * sc,
+                     bb = ltab[4 * lmax1 + l] * sc;
         double v[4];
         const double gT = use_diag ? b2 * (double)dT[i] : 0.0;
         const double gP = (use_diag && nc == 3) ? b2 * (double)dP[i] : 0.0;
@@ -168,21 +174,23 @@ __global__ void k_precond(const float *__restrict__ dT, const float *__restrict_
 // RHS: b += S^-1/2 w1 (sinvh rows TT, TE, EE, BB)
 __global__ void k_rhs_alm(const double2 *__restrict__ w1, double2 *__restrict__ bvec, int nc,
                           int64_t nalm, int lmax1, const int *__restrict__ lof,
-                          const int *__restrict__ mof, const double *__restrict__ sh) {
+                          const int *__restrict__ mof, const double *__restrict__ sh,
+                          const double *__restrict__ rsc) {
     const int b = blockIdx.y;
     const int64_t off = (int64_t)b * nc * nalm;
+    const double sc = rsc[b];   // 1 / sqrt(C_l scale of realization b)
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nalm;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int l = lof[i];
         const bool m0 = mof[i] == 0;
-        const double tt = sh[l];
+        const double tt = sh[l] * sc;
         if (nc == 1) {
             double2 w = w1[off + i], v = bvec[off + i];
             v.x += tt * w.x;
             v.y = m0 ? 0.0 : v.y + tt * w.y;
             bvec[off + i] = v;
         } else {
-            const double te = sh[lmax1 + l], ee = sh[2 * lmax1 + l], bb = sh[3 * lmax1 + l];
+            const double te = sh[lmax1 + l] * sc, ee = sh[2 * lmax1 + l] * sc, bb = sh[3 * lmax1 + l] * sc;
             const double2 wt = w1[off + i], we = w1[off + nalm + i], wb = w1[off + 2 * nalm + i];
             double2 vt = bvec[off + i], ve = bvec[off + nalm + i], vb = bvec[off + 2 * nalm + i];
             vt.x += tt * wt.x + te * we.x;
@@ -276,7 +284,7 @@ __global__ void k_update(typename HT<T>::C *__restrict__ x, typename HT<T>::C *_
             }
             rv[k] = rr;
         }
-        apply_minv<T, C>(minv, nalm, i, nc, rv, zv);
+        apply_minv<T, C>(minv + (int64_t)b * 4 * nalm, nalm, i, nc, rv, zv);
         const double w = mof[i] ? 2.0 : 1.0;
         double a1 = 0.0, a2 = 0.0;
         for (int k = 0; k < nc; ++k) {
@@ -531,6 +539,7 @@ template <> struct Vec<double> {
     static double *minv(Plan *p) { return p->d_minv64; }
     static double *beam(Plan *p) { return p->d_ltab64; }
     static double *sinv(Plan *p) { return p->d_ltab64 + (p->lmax + 1); }
+    static double *isc(Plan *p) { return p->d_isc64; }
     static double *ninv(Plan *p) { return p->d_ninv64; }
     static double2 *phase(Plan *p) { return p->d_phase64; }
 };
@@ -542,6 +551,7 @@ template <> struct Vec<float> {
     static float *minv(Plan *p) { return p->d_minv32; }
     static float *beam(Plan *p) { return p->d_ltab32; }
     static float *sinv(Plan *p) { return p->d_ltab32 + (p->lmax + 1); }
+    static float *isc(Plan *p) { return p->d_isc32; }
     static float *ninv(Plan *p) { return p->d_ninv32; }
     static float2 *phase(Plan *p) { return p->d_phase32; }
 };
@@ -579,7 +589,7 @@ static int matvec(Solve &s, const typename HT<T>::C *x, typename HT<T>::C *y) {
     if (s.nc == 3) SHTG_TRY(op_analysis(s, 2, F + s.nb * rowsz, beam, y + s.nalm, 3));
     prof_begin(p, K_VEC, s.st);
     k_prior_add<T><<<dim3(grid_1d(s.nalm).x, s.nb), RT, 0, s.st>>>(x, y, s.nc, s.nalm, p->lmax + 1,
-                                                                   p->d_lofidx, Vec<T>::sinv(p));
+                                                                   p->d_lofidx, Vec<T>::sinv(p), Vec<T>::isc(p));
     prof_end(p, s.st);
     SHTG_CHECK_LAUNCH("k_prior_add");
     return SHTG_OK;
@@ -797,6 +807,21 @@ static int setup_operator(Plan *p, const shtg_problem *pr, int host_inputs, int 
                           cudaStream_t st) {
     const int nc = pr->ncomp;
     SHTG_TRY(build_ltab(p, nc, pr->cl, pr->bl));
+    {
+        // realization b's C_l is cl_scale[b] x cl: S^-1 scales by 1/s, S^-1/2 by 1/sqrt(s)
+        std::vector<double> i64(pr->nbatch), r64(pr->nbatch);
+        std::vector<float> i32(pr->nbatch);
+        for (int b = 0; b < pr->nbatch; ++b) {
+            const double sc = pr->cl_scale ? pr->cl_scale[b] : 1.0;
+            i64[b] = 1.0 / sc;
+            r64[b] = 1.0 / sqrt(sc);
+            i32[b] = (float)i64[b];
+        }
+        SHTG_CUDA(cudaMemcpyAsync(p->d_isc64, i64.data(), sizeof(double) * pr->nbatch, cudaMemcpyHostToDevice, st));
+        SHTG_CUDA(cudaMemcpyAsync(p->d_rsc64, r64.data(), sizeof(double) * pr->nbatch, cudaMemcpyHostToDevice, st));
+        SHTG_CUDA(cudaMemcpyAsync(p->d_isc32, i32.data(), sizeof(float) * pr->nbatch, cudaMemcpyHostToDevice, st));
+        SHTG_CUDA(cudaStreamSynchronize(st));   // the host vectors go out of scope
+    }
     const int ncomp_ninv = nc == 3 ? 2 : 1;
     const size_t nb = sizeof(double) * (size_t)p->npix * ncomp_ninv;
     SHTG_CUDA(cudaMemcpyAsync(p->d_ninv64, pr->ninv, nb,
@@ -818,9 +843,9 @@ static int setup_operator(Plan *p, const shtg_problem *pr, int host_inputs, int 
             SHTG_TRY(leg_diag(p, 2, p->d_wpairP, p->d_diagP, st));
         }
     }
-    k_precond<<<grid_1d(p->nalm), RT, 0, st>>>(p->d_diagT, nc == 3 ? p->d_diagP : p->d_diagT,
-                                               p->d_ltab64, nc, p->nalm, p->lmax + 1, p->d_lofidx,
-                                               precond, p->d_minv64, p->d_minv32);
+    k_precond<<<dim3(grid_1d(p->nalm).x, pr->nbatch), RT, 0, st>>>(
+        p->d_diagT, nc == 3 ? p->d_diagP : p->d_diagT, p->d_ltab64, nc, p->nalm, p->lmax + 1, p->d_lofidx,
+        precond, p->d_isc64, p->d_minv64, p->d_minv32);
     p->prof.launches += 1;
     SHTG_CHECK_LAUNCH("k_precond");
     return SHTG_OK;
@@ -843,6 +868,12 @@ static int check_problem(Plan *p, const shtg_problem *pr) {
         set_error("nbatch must be in [1, max_batch]");
         return SHTG_ERR_ARG;
     }
+    if (pr->cl_scale)
+        for (int b = 0; b < pr->nbatch; ++b)
+            if (!(pr->cl_scale[b] > 0.0) || !std::isfinite(pr->cl_scale[b])) {
+                set_error("cl_scale entries must be positive and finite");
+                return SHTG_ERR_ARG;
+            }
     return SHTG_OK;
 }
 
@@ -1031,7 +1062,7 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
             w1 = Tt;
         }
         k_rhs_alm<<<s.vgrid, RT, 0, st>>>(w1, B, nc, p->nalm, p->lmax + 1, p->d_lofidx, p->d_mofidx,
-                                         p->d_ltab64 + 5 * (p->lmax + 1));
+                                         p->d_ltab64 + 5 * (p->lmax + 1), p->d_rsc64);
         p->prof.launches += 1;
         SHTG_CHECK_LAUNCH("k_rhs_alm");
     }

@@ -38,3 +38,19 @@ def test_version_and_error_string_without_gpu():
 def test_oracle_builds():
     from oracle import _lib
     assert os.path.exists(_lib.build())
+
+
+def test_chains_rejects_bad_arguments_without_gpu():
+    """Argument checks of the chains entry point run before any CUDA call."""
+    from paper_2306_15511_gb300 import _native
+    lib = _native.load()
+    rc = lib.shtg_cg_sample_chains(0, None, None, None, None, None, None)
+    assert rc == -1
+    assert b"chains" in lib.shtg_last_error_string()
+    h = ctypes.c_void_p(1234)   # never dereferenced: the duplicate check comes first
+    plans = (ctypes.c_void_p * 2)(h, h)
+    probs = (_native.Problem * 2)()
+    outs = (ctypes.c_void_p * 2)()
+    rc = lib.shtg_cg_sample_chains(2, plans, probs, outs, None, None, None)
+    assert rc == -1
+    assert b"own plan" in lib.shtg_last_error_string()
