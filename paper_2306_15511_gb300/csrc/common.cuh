@@ -154,6 +154,10 @@ struct Plan {
     int64_t *d_toff = nullptr;
     float2 *d_tst0 = nullptr;
     float4 *d_tst2 = nullptr;
+    // the same in FP64 every 128 l (FP64 transpose), [m][t][pair] at (d_toff128[m] + t) * npairs + pair
+    int64_t *d_toff128 = nullptr;
+    double2 *d_tst64_0 = nullptr;
+    double4_32a *d_tst64_2 = nullptr;
     double *d_lsum = nullptr;      // [lmax+1] per-l sums (log-posterior)
     double *d_stage = nullptr;     // [nmaps_max][npix] staging for host inputs
     double *h_pinned = nullptr;    // pinned host scalars
@@ -217,6 +221,10 @@ int check_device_flag(Plan *p, cudaStream_t st);
 int leg_analysis_tc(Plan *p, int spin, const float2 *G, int nmaps, const float *beam, float2 *alm, int rs,
                     cudaStream_t st, int vjp);
 int build_tile_states(Plan *p);
+// FP64 Legendre transpose as a register-blocked contraction; its FP64 tile states
+int leg_analysis_g64(Plan *p, int spin, const double2 *G, int nmaps, const double *beam, double2 *alm, int rs,
+                     cudaStream_t st, int vjp);
+int build_tile_states64(Plan *p);
 
 // ringfft.cu
 // mode 0: F -> map (synthesis); mode 1: map -> G (adjoint, wmode 1 = quadrature weights);

@@ -38,6 +38,9 @@ template <> LegArgs<double> leg_make_args<double>(Plan *p) {
     a.ls2 = p->d_ls2_64;
     a.st2 = p->d_st2_64;
     a.u = p->d_u64;
+    a.toff128 = p->d_toff128;
+    a.tst64_0 = p->d_tst64_0;
+    a.tst64_2 = p->d_tst64_2;
     return a;
 }
 
@@ -115,10 +118,15 @@ int leg_analysis<float>(Plan *p, int spin, const float2 *G, int nmaps, const flo
 template <>
 int leg_analysis<double>(Plan *p, int spin, const double2 *G, int nmaps, const double *beam,
                          double2 *alm, int rs, cudaStream_t st, int vjp) {
+    // candidates: the register-blocked contraction (legendre_g64.cu, about
+    // half the FP64 instructions of the warp-reduction kernels when several
+    // maps share a recurrence; the default), then the warp-reduction shapes
     const Variants64 &V = variants64();
     const int s = spin == 2 ? 1 : 0;
-    return tune(p, 0, 2 + s, nmaps, V.n[2 + s], st,
-                [&](int v) { return V.ana[s][v](p, G, nmaps, beam, alm, rs, st, vjp); });
+    return tune(p, 0, 2 + s, nmaps, V.n[2 + s] + 1, st, [&](int v) {
+        if (v == 0) return leg_analysis_g64(p, spin, G, nmaps, beam, alm, rs, st, vjp);
+        return V.ana[s][v - 1](p, G, nmaps, beam, alm, rs, st, vjp);
+    });
 }
 
 int leg_diag(Plan *p, int spin, const float *wpair, float *out, cudaStream_t st) {

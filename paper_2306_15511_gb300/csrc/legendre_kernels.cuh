@@ -58,6 +58,9 @@ template <typename T> struct LegArgs {
     const int64_t *toff;  // tensor-core transpose: recurrence states every 32 l (FP32 plans)
     const float2 *tst0;
     const float4 *tst2;
+    const int64_t *toff128;   // FP64 transpose: FP64 recurrence states every 128 l (FP64 plans)
+    const double2 *tst64_0;
+    const double4_32a *tst64_2;
 };
 
 // one recurrence step: (l1, l2) = (lambda_{l-1}, lambda_{l-2}) -> (lambda_l, lambda_{l-1})

@@ -600,6 +600,7 @@ int plan_build(Plan *p) {
     }
     SHTG_TRY(build_legendre_tables(p, u_pair));
     SHTG_TRY(build_tile_states(p));
+    SHTG_TRY(build_tile_states64(p));
     SHTG_TRY(build_fft_tables(p));
     // workspace
     const int spin2 = (p->flags & SHTG_SPIN2) ? 1 : 0;
@@ -653,7 +654,8 @@ void plan_free(Plan *p) {
                     p->d_minv32, p->d_diagT, p->d_diagP, p->d_wpairT, p->d_wpairP,
                     p->d_ltab64, p->d_ltab32, p->d_scal, p->d_part, p->d_lsum, p->d_stage,
                     p->d_ls2_64, p->d_st2_64, p->d_ls2_32, p->d_st2_32, p->d_ring_groups, p->d_flag,
-                    p->d_toff, p->d_tst0, p->d_tst2, p->d_isc64, p->d_rsc64, p->d_isc32};
+                    p->d_toff, p->d_tst0, p->d_tst2, p->d_isc64, p->d_rsc64, p->d_isc32,
+                    p->d_toff128, p->d_tst64_0, p->d_tst64_2};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (int i = 0; i < 7; ++i)
