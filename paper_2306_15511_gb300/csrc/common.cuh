@@ -121,6 +121,7 @@ struct Plan {
     int *d_ring_groups = nullptr;    // ring pairs: direct-FFT pairs first, then Bluestein pairs
     int ring_group_count[2] = {0, 0};
     int ring_group_logm[2] = {0, 0}; // largest log2 transform length in each group
+    int ring_group_qs[2] = {0, 0};   // scratch for the south ring of aliased direct rings (n < 2 lmax)
 
     // workspace
     double2 *d_phase64 = nullptr;  // [nmaps_max][nring][lmax+1] Fourier coefficients per ring

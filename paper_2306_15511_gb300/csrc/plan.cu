@@ -574,11 +574,16 @@ static int build_fft_tables(Plan *p) {
     for (int g = 0; g < 2; ++g) {
         p->ring_group_count[g] = 0;
         p->ring_group_logm[g] = 0;
+        p->ring_group_qs[g] = 0;
         for (int r = 0; r < p->npairs; ++r)
             if (p->h_rfft[r].blue == g) {
                 groups.push_back(r);
                 p->ring_group_count[g] += 1;
                 p->ring_group_logm[g] = std::max(p->ring_group_logm[g], p->h_rfft[r].logM);
+                // Bluestein rings keep the south ring's folded spectrum in the
+                // upper half of their transform buffer (M >= 2n)
+                if (!g && p->h_rfft[r].n < 2 * p->lmax)
+                    p->ring_group_qs[g] = std::max(p->ring_group_qs[g], p->h_rfft[r].n);
             }
     }
     SHTG_TRY(dalloc(p, &p->d_ring_groups, groups.size()));

@@ -275,6 +275,7 @@ template <typename T> struct RingArgs {
     const T *ninv;    // fused: [comp][npix]
     int nT;           // fused: rows [0, nT) use N^-1 component 0 (T), later rows component 1 (Q, U)
     int weighted;     // analysis: multiply by the quadrature weight
+    int buf_len;      // shared transform buffer length (padded) of this launch
     const int *pairs; // ring pairs handled by this launch (one CTA each)
 };
 
@@ -299,6 +300,8 @@ __global__ void __launch_bounds__(NT, RingBlocks<T, NT>::v) k_ring(const RingArg
     extern __shared__ __align__(16) unsigned char s_raw[];
     C *s_tw = reinterpret_cast<C *>(s_raw);
     C *buf = s_tw + a.tw_nlo + a.tw_nhi;
+    C *scr_p = buf + a.buf_len;   // aliased fold: partial sums [north | south][NT]
+    C *scr_q = scr_p + 2 * NT;    // aliased direct rings: Q_S / Y_S [n]
     for (int i = threadIdx.x; i < a.tw_nlo + a.tw_nhi; i += NT) s_tw[i] = a.tw[i];
     TwTab<C> tw;
     tw.lo = s_tw;
@@ -347,47 +350,103 @@ __global__ void __launch_bounds__(NT, RingBlocks<T, NT>::v) k_ring(const RingArg
             }
             for (int k = L + 1 + threadIdx.x; k < n - L; k += NT) buf[rpad(k)] = zero;
         } else if (MODE != 1) {
-            // ---- fold F into the length-n spectrum of z = f_N + i f_S
+            // ---- aliased fold (n < 2 l_max) into the length-n spectrum of
+            // z = f_N + i f_S.  Per residue r: Q(r) = sum_t (-1)^{s t} F(r + t n)
+            // (phi0 = s pi / n); then H(k) = e^{i pi s k / n} [Q(k) + (-1)^s
+            // conj Q(n - k)] for k > 0 and H(0) = Q(0) + conj(Q(0) - F(0)).
+            // Rings with n < NT / 2 split each residue's sum over S = NT / n
+            // thread segments (coalesced reads, fixed summation order), so a
+            // small polar ring costs no more time than a long one.
             const C *Fn = a.FG + ((int64_t)q * a.nring + rn) * (L + 1);
             const C *Fs = a.FG + ((int64_t)q * a.nring + rs) * (L + 1);
-            // H(k) = e^{i pi s k / n} [ sum_t (-1)^{s t} F(k + t n)
-            //                         + sum_t (-1)^{s (t+1)} conj F(n - k + t n) ]
-            // (phi0 = s pi / n): one phase per bin, a sign per folded term.
-            for (int k = threadIdx.x; k < n; k += NT) {
-                C hn = zero, hs = zero;
-                T sg = T(1);
-                for (int mm = k; mm <= L; mm += n) {
-                    const C vn = Fn[mm];
-                    hn.x += sg * vn.x;
-                    hn.y += sg * vn.y;
-                    if (!single) {
-                        const C vs = Fs[mm];
-                        hs.x += sg * vs.x;
-                        hs.y += sg * vs.y;
+            // Q of the south ring: buf[n, 2n) for Bluestein rings (M >= 2n), else scratch
+            auto qsr = [&](int k) -> C & { return f.blue ? buf[rpad(n + k)] : scr_q[k]; };
+            const int S = n <= NT / 2 ? NT / n : 1;
+            if (S > 1) {
+                const int k = threadIdx.x % n, s = threadIdx.x / n;
+                if (s < S) {
+                    C pn = zero, ps = zero;
+                    T sg = (f.shift && (s & 1)) ? T(-1) : T(1);   // (-1)^{s t}, t = s + j S
+                    const bool flip = f.shift && (S & 1);
+                    for (int mm = k + s * n; mm <= L; mm += S * n) {
+                        const C vn = Fn[mm];
+                        pn.x += sg * vn.x;
+                        pn.y += sg * vn.y;
+                        if (!single) {
+                            const C vs = Fs[mm];
+                            ps.x += sg * vs.x;
+                            ps.y += sg * vs.y;
+                        }
+                        if (flip) sg = -sg;
                     }
-                    if (f.shift) sg = -sg;
+                    scr_p[s * n + k] = pn;
+                    scr_p[NT + s * n + k] = ps;
                 }
-                sg = f.shift ? T(-1) : T(1);
-                for (int mm = (k == 0 ? n : n - k); mm <= L; mm += n) {
-                    const C vn = Fn[mm];
-                    hn.x += sg * vn.x;
-                    hn.y -= sg * vn.y;
-                    if (!single) {
-                        const C vs = Fs[mm];
-                        hs.x += sg * vs.x;
-                        hs.y -= sg * vs.y;
+                __syncthreads();
+                for (int kk = threadIdx.x; kk < n; kk += NT) {
+                    C qn = zero, qq = zero;
+                    for (int s2 = 0; s2 < S; ++s2) {
+                        qn = cadd(qn, scr_p[s2 * n + kk]);
+                        qq = cadd(qq, scr_p[NT + s2 * n + kk]);
                     }
-                    if (f.shift) sg = -sg;
+                    buf[rpad(kk)] = qn;
+                    qsr(kk) = qq;
                 }
-                if (f.shift) {
-                    const C ph = phase_pi(k, n, T(0));
-                    hn = cmul(hn, ph);
-                    hs = cmul(hs, ph);
+            } else {
+                for (int k = threadIdx.x; k < n; k += NT) {
+                    C qn = zero, qq = zero;
+                    T sg = T(1);
+                    for (int mm = k; mm <= L; mm += n) {
+                        const C vn = Fn[mm];
+                        qn.x += sg * vn.x;
+                        qn.y += sg * vn.y;
+                        if (!single) {
+                            const C vs = Fs[mm];
+                            qq.x += sg * vs.x;
+                            qq.y += sg * vs.y;
+                        }
+                        if (f.shift) sg = -sg;
+                    }
+                    buf[rpad(k)] = qn;
+                    qsr(k) = qq;
                 }
-                const C z = {hn.x - hs.y, hn.y + hs.x};
-                // inverse DFT = conj(DFT(conj .)): the direct path enters conjugated
-                buf[rpad(k)] = f.blue ? cmul(z, cconj(chirp[k])) : cconj(z);
             }
+            __syncthreads();
+            // bins k and n - k from one thread, in place over Q_N
+            const T sig = f.shift ? T(-1) : T(1);
+            for (int j = threadIdx.x; 2 * j <= n; j += NT) {
+                const int k1 = j, k2 = j ? n - j : 0;
+                const C qn1 = buf[rpad(k1)], qn2 = buf[rpad(k2)];
+                const C qs1 = qsr(k1), qs2 = qsr(k2);
+                C hn1, hs1, hn2, hs2;
+                if (j == 0) {
+                    const C f0n = Fn[0], f0s = single ? zero : Fs[0];
+                    hn1 = {qn1.x + (qn1.x - f0n.x), qn1.y - (qn1.y - f0n.y)};
+                    hs1 = {qs1.x + (qs1.x - f0s.x), qs1.y - (qs1.y - f0s.y)};
+                } else {
+                    hn1 = {qn1.x + sig * qn2.x, qn1.y - sig * qn2.y};
+                    hs1 = {qs1.x + sig * qs2.x, qs1.y - sig * qs2.y};
+                }
+                hn2 = {qn2.x + sig * qn1.x, qn2.y - sig * qn1.y};
+                hs2 = {qs2.x + sig * qs1.x, qs2.y - sig * qs1.y};
+                if (f.shift) {
+                    // e^{i pi (n - k) / n} = -conj e^{i pi k / n}
+                    const C ph = phase_pi(k1, n, T(0));
+                    const C ph2 = {-ph.x, ph.y};
+                    hn1 = cmul(hn1, ph);
+                    hs1 = cmul(hs1, ph);
+                    hn2 = cmul(hn2, ph2);
+                    hs2 = cmul(hs2, ph2);
+                }
+                const C z1 = {hn1.x - hs1.y, hn1.y + hs1.x};
+                buf[rpad(k1)] = f.blue ? cmul(z1, cconj(chirp[k1])) : cconj(z1);
+                if (k2 != k1) {
+                    const C z2 = {hn2.x - hs2.y, hn2.y + hs2.x};
+                    buf[rpad(k2)] = f.blue ? cmul(z2, cconj(chirp[k2])) : cconj(z2);
+                }
+            }
+            // (Bluestein rings keep Q_S in buf[n, 2n): zero the tail only after)
+            if (f.blue) __syncthreads();
         } else {
             // ---- load z = w (m_N + i m_S)
             const T *mn = a.map + (int64_t)q * a.npix + a.ofs[rn];
@@ -442,29 +501,72 @@ __global__ void __launch_bounds__(NT, RingBlocks<T, NT>::v) k_ring(const RingArg
             C *Gn = a.FG + ((int64_t)q * a.nring + rn) * (L + 1);
             C *Gs = a.FG + ((int64_t)q * a.nring + rs) * (L + 1);
             // G(k + t n) = (-1)^{s t} e^{-i pi s k / n} Y(k), one phase per bin
-            const int nk = min(n, L + 1);
-            for (int k = threadIdx.x; k < nk; k += NT) {
-                const int k2 = (n - k) % n;
-                C w1 = buf[rpad(k)], w2 = buf[rpad(k2)];
-                if (f.blue) {
-                    w1 = cmul(cconj(w1), chirp[k]);
-                    w2 = cmul(cconj(w2), chirp[k2]);
+            if (n > L) {
+                for (int k = threadIdx.x; k <= L; k += NT) {
+                    const int k2 = k ? n - k : 0;
+                    C w1 = buf[rpad(k)], w2 = buf[rpad(k2)];
+                    if (f.blue) {
+                        w1 = cmul(cconj(w1), chirp[k]);
+                        w2 = cmul(cconj(w2), chirp[k2]);
+                    }
+                    C yn = {T(0.5) * (w1.x + w2.x), T(0.5) * (w1.y - w2.y)};
+                    C ys = {T(0.5) * (w1.y + w2.y), T(-0.5) * (w1.x - w2.x)};
+                    if (f.shift) {
+                        const C ph = cconj(phase_pi(k, n, T(0)));
+                        yn = cmul(yn, ph);
+                        ys = cmul(ys, ph);
+                    }
+                    Gn[k] = yn;
+                    if (!single) Gs[k] = ys;
                 }
-                C yn = {T(0.5) * (w1.x + w2.x), T(0.5) * (w1.y - w2.y)};
-                C ys = {T(0.5) * (w1.y + w2.y), T(-0.5) * (w1.x - w2.x)};
-                if (f.shift) {
-                    const C ph = cconj(phase_pi(k, n, T(0)));
-                    yn = cmul(yn, ph);
-                    ys = cmul(ys, ph);
+            } else {
+                // aliased rings: Y_N(k), Y_S(k) for bins k and n - k from one
+                // thread (Y_N in place over buf, Y_S beside it), then every m
+                // written once, coalesced
+                auto ysr = [&](int k) -> C & { return f.blue ? buf[rpad(n + k)] : scr_q[k]; };
+                for (int j = threadIdx.x; 2 * j <= n; j += NT) {
+                    const int k1 = j, k2 = j ? n - j : 0;
+                    C w1 = buf[rpad(k1)], w2 = buf[rpad(k2)];
+                    if (f.blue) {
+                        w1 = cmul(cconj(w1), chirp[k1]);
+                        w2 = cmul(cconj(w2), chirp[k2]);
+                    }
+                    C yn1 = {T(0.5) * (w1.x + w2.x), T(0.5) * (w1.y - w2.y)};
+                    C ys1 = {T(0.5) * (w1.y + w2.y), T(-0.5) * (w1.x - w2.x)};
+                    C yn2 = {yn1.x, -yn1.y};
+                    C ys2 = {ys1.x, -ys1.y};
+                    if (f.shift) {
+                        // e^{-i pi (n - k) / n} = -conj e^{-i pi k / n}
+                        const C ph = cconj(phase_pi(k1, n, T(0)));
+                        const C ph2 = {-ph.x, ph.y};
+                        yn1 = cmul(yn1, ph);
+                        ys1 = cmul(ys1, ph);
+                        yn2 = cmul(yn2, ph2);
+                        ys2 = cmul(ys2, ph2);
+                    }
+                    buf[rpad(k1)] = yn1;
+                    ysr(k1) = ys1;
+                    if (k2 != k1) {
+                        buf[rpad(k2)] = yn2;
+                        ysr(k2) = ys2;
+                    }
                 }
-                for (int mm = k; mm <= L; mm += n) {
+                __syncthreads();
+                int k = threadIdx.x % n, t = threadIdx.x / n;
+                const int dk = NT % n, dt = NT / n;
+                for (int mm = threadIdx.x; mm <= L; mm += NT) {
+                    C yn = buf[rpad(k)], ys = ysr(k);
+                    if (f.shift && (t & 1)) {
+                        yn = {-yn.x, -yn.y};
+                        ys = {-ys.x, -ys.y};
+                    }
                     Gn[mm] = yn;
                     if (!single) Gs[mm] = ys;
-                    if (f.shift) {
-                        yn.x = -yn.x;
-                        yn.y = -yn.y;
-                        ys.x = -ys.x;
-                        ys.y = -ys.y;
+                    k += dk;
+                    t += dt;
+                    if (k >= n) {
+                        k -= n;
+                        t += 1;
                     }
                 }
             }
@@ -512,9 +614,12 @@ static int launch_ring(Plan *p, RingArgs<T> a, cudaStream_t st) {
         const int cnt = p->ring_group_count[g];
         if (cnt == 0) continue;
         const int M = 1 << p->ring_group_logm[g];
-        const size_t smem = sizeof(C) * ((size_t)p->tw_nlo + p->tw_nhi + M + M / 16);
+        const int nt = M <= 4096 ? 256 : 512;
+        a.buf_len = M + M / 16;
+        const size_t smem = sizeof(C) * ((size_t)p->tw_nlo + p->tw_nhi + a.buf_len + 2 * nt +
+                                         p->ring_group_qs[g]);
         a.pairs = p->d_ring_groups + (g ? p->ring_group_count[0] : 0);
-        if (M <= 4096) {
+        if (nt == 256) {
             auto kern = k_ring<T, MODE, 256>;
             if (smem > 48 * 1024)
                 SHTG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
