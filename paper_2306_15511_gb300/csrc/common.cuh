@@ -51,6 +51,7 @@ struct RingFFT {
     int shift;    // phi0 = shift * pi / n (0 or 1)
     int64_t chirp_off;  // offset of the n chirp values (Bluestein rings)
     int64_t bhat_off;   // offset of the M spectra of the convolution kernel
+    int64_t ph_off;     // shifted rings: offset of e^{i pi k / n}, k = 0 .. min(lmax, n - 1)
 };
 
 // Kernel classes timed live with CUDA events (on the launching stream) when
@@ -117,11 +118,14 @@ struct Plan {
     int tw_blo = 0, tw_nlo = 0, tw_nhi = 0;
     double2 *d_chirp64 = nullptr, *d_bfwd64 = nullptr, *d_binv64 = nullptr;
     float2 *d_chirp32 = nullptr, *d_bfwd32 = nullptr, *d_binv32 = nullptr;
+    double2 *d_rph64 = nullptr;   // ring phase tables (RingFFT::ph_off)
+    float2 *d_rph32 = nullptr;
     size_t fft_smem64 = 0, fft_smem32 = 0;
-    int *d_ring_groups = nullptr;    // ring pairs: direct-FFT pairs first, then Bluestein pairs
+    int *d_ring_groups = nullptr;    // ring pairs: alias-free direct pairs first, then the rest
     int ring_group_count[2] = {0, 0};
     int ring_group_logm[2] = {0, 0}; // largest log2 transform length in each group
-    int ring_group_qs[2] = {0, 0};   // scratch for the south ring of aliased direct rings (n < 2 lmax)
+    int ring_group_qs[2] = {0, 0};   // separate scratch for the south ring of aliased direct rings
+    int ring_group_alias[2] = {0, 0}; // group holds rings with n < 2 lmax
 
     // workspace
     double2 *d_phase64 = nullptr;  // [nmaps_max][nring][lmax+1] Fourier coefficients per ring

@@ -44,55 +44,6 @@ template <> LegArgs<double> leg_make_args<double>(Plan *p) {
     return a;
 }
 
-// ------------------------------------------------------------- autotuner
-// Key: (precision, family, nmaps).  On the first call with a key every
-// candidate runs twice on the caller's buffers (all compute the same
-// result); the second run of each is timed with CUDA events on the stream
-// and the fastest is kept.  SHTG_TUNE=0 in the environment keeps variant 0.
-static bool tuning_enabled() {
-    static int on = -1;
-    if (on < 0) {
-        const char *e = getenv("SHTG_TUNE");
-        on = (e && e[0] == '0') ? 0 : 1;
-    }
-    return on == 1;
-}
-
-template <typename Run>
-static int tune(Plan *p, int key_prec, int family, int nmaps, int nvar, cudaStream_t st, Run run) {
-    const long long key = ((long long)key_prec * 16 + family) * 65536 + nmaps;
-    auto it = p->tuned.find(key);
-    if (it != p->tuned.end()) return run(it->second);
-    if (!tuning_enabled() || nvar <= 1 || p->prof.on) {
-        p->tuned[key] = 0;
-        return run(0);
-    }
-    cudaEvent_t e0, e1;
-    SHTG_CUDA(cudaEventCreate(&e0));
-    SHTG_CUDA(cudaEventCreate(&e1));
-    int best = 0;
-    float tbest = 1e30f;
-    for (int v = 0; v < nvar; ++v) {
-        int rc = run(v);
-        if (rc != SHTG_OK) continue;
-        cudaEventRecord(e0, st);
-        rc = run(v);
-        cudaEventRecord(e1, st);
-        if (rc != SHTG_OK) continue;
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < tbest) {
-            tbest = ms;
-            best = v;
-        }
-    }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
-    p->tuned[key] = best;
-    return run(best);
-}
-
 template <>
 int leg_synth<float>(Plan *p, int spin, const float2 *alm, int rs, int nmaps, const float *beam,
                      float2 *F, cudaStream_t st) {

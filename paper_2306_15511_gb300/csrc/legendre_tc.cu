@@ -20,10 +20,12 @@
 // into chunks of 32 (16 per parity class, one MMA K of 16 each).  All 128
 // threads generate the A tiles of chunk c (bf16 hi / lo, K-major core
 // matrices in shared memory) and the B tiles, then one thread issues the
-// tcgen05.mma of chunk c and commits them to an mbarrier; the threads go on
-// with chunk c + 1 in the other shared-memory stage while the tensor core
-// works.  The accumulators stay in tensor memory until the last chunk and
-// are read back with tcgen05.ld for the F_N / F_S epilogue.
+// tcgen05.mma of chunk c and commits them to an mbarrier.  With two stages
+// the threads go on with chunk c + 1 in the other stage while the tensor
+// core works; with one stage (half the shared memory, twice the resident
+// CTAs) they wait for the commit and the other CTAs on the SM fill the gap.
+// The accumulators stay in tensor memory until the last chunk and are read
+// back with tcgen05.ld for the F_N / F_S epilogue.
 #include <cuda_bf16.h>
 
 #include "legendre_kernels.cuh"
@@ -35,7 +37,6 @@ constexpr int TC_M = 128;        // ring pairs per CTA = MMA M = threads
 constexpr int TC_NMT = 8;        // maps per CTA (grid.z covers more)
 constexpr int TC_ATILE = 4096;   // one A tile: 128 rows x 16 bf16 (K-major core matrices)
 constexpr uint32_t TC_WAIT_LIMIT = 1u << 22;   // bounded mbarrier polling
-constexpr int TC_ALMS = LEG_CHUNK + 1;          // staged alm row stride (odd: rows fall in distinct banks)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -130,12 +131,19 @@ template <> struct TcCfg<0> {
 template <> struct TcCfg<2> {
     static constexpr int NCOL = 32, NA = 2 * TC_NMT, NTA = 8, NTB = 4, TMEM = 128;
 };
-template <int SPIN> struct TcLayout {
+// Shared memory of the synthesis CTA: NSTG operand stages (A and B tiles of
+// one 32-l chunk each), the alm and recurrence coefficients of SCH l, two
+// mbarriers, the TMEM address and scratch.  One stage halves the footprint
+// (spin 2: 50 KB instead of 99 KB with SCH = 64), so four CTAs instead of two
+// share an SM; the MMA of a chunk then has to finish before the CTA writes
+// the next chunk's tiles, and the other CTAs fill that gap.
+template <int SPIN, int NSTG, int SCH> struct TcLayout {
+    static constexpr int ALMS = SCH + 1;   // staged alm row stride (odd: rows fall in distinct banks)
     static constexpr int BTILE = 2 * TcCfg<SPIN>::NCOL * 32;
     static constexpr int STAGE = TcCfg<SPIN>::NTA * TC_ATILE + TcCfg<SPIN>::NTB * BTILE;
-    static constexpr int ALM = 2 * STAGE;                                   // staged alm [NA][128] float2
-    static constexpr int COEF = ALM + ((TcCfg<SPIN>::NA * TC_ALMS * 8 + 15) & ~15);   // staged coefficients
-    static constexpr int BARS = COEF + LEG_CHUNK * (SPIN == 2 ? 16 : 8);    // 2 mbarriers
+    static constexpr int ALM = NSTG * STAGE;                                // staged alm [NA][ALMS] float2
+    static constexpr int COEF = ALM + ((TcCfg<SPIN>::NA * ALMS * 8 + 15) & ~15);   // staged coefficients
+    static constexpr int BARS = COEF + SCH * (SPIN == 2 ? 16 : 8);          // 2 mbarriers
     static constexpr int TMEMA = BARS + 16;                                 // TMEM base address
     static constexpr int RED = TMEMA + 16;                                  // cta_min scratch
     static constexpr int BYTES = RED + 16;
@@ -190,10 +198,10 @@ __device__ __forceinline__ void gen_atiles(PairState<float, 1> &S, const float2 
 // W columns (-E re, -E im, -B re, -B im) and X columns (B im, -B re, -E im,
 // E re) per map, feeding (Q re, Q im, U re, U im).  Column c, K index k:
 // hi at row c, lo at row NCOL + c (K-major core matrices, LBO = 32 NCOL).
-template <int SPIN>
+template <int SPIN, int ALMS>
 __device__ __forceinline__ void gen_btiles(const float2 *s_alm, const int i0, unsigned char *bt) {
     constexpr int NCOL = TcCfg<SPIN>::NCOL, NTB = TcCfg<SPIN>::NTB;
-    constexpr int BTILE = TcLayout<SPIN>::BTILE;
+    constexpr int BTILE = 2 * NCOL * 32;
     // item = (tile b, K group kg, column c, K pair kq): four consecutive lanes
     // fill one 16-byte core-matrix row, a warp eight consecutive rows
     for (int it = threadIdx.x; it < NTB * 8 * NCOL; it += TC_M) {
@@ -208,12 +216,12 @@ __device__ __forceinline__ void gen_btiles(const float2 *s_alm, const int i0, un
         for (int q = 0; q < 2; ++q) {
             const int idx = i0 + 2 * (k0 + q) + off;
             if (SPIN == 0) {
-                const float2 av = s_alm[(c >> 1) * TC_ALMS + idx];
+                const float2 av = s_alm[(c >> 1) * ALMS + idx];
                 v[q] = (c & 1) ? av.y : av.x;
             } else {
                 const int mk = c >> 2, comp = c & 3;
-                const float2 e = s_alm[(2 * mk) * TC_ALMS + idx];
-                const float2 bb = s_alm[(2 * mk + 1) * TC_ALMS + idx];
+                const float2 e = s_alm[(2 * mk) * ALMS + idx];
+                const float2 bb = s_alm[(2 * mk + 1) * ALMS + idx];
                 if (b < 2) v[q] = comp == 0 ? -e.x : comp == 1 ? -e.y : comp == 2 ? -bb.x : -bb.y;
                 else v[q] = comp == 0 ? bb.y : comp == 1 ? -bb.x : comp == 2 ? -e.y : e.x;
             }
@@ -226,10 +234,10 @@ __device__ __forceinline__ void gen_btiles(const float2 *s_alm, const int i0, un
     }
 }
 
-template <int SPIN>
+template <int SPIN, int NSTG, int SCH>
 __global__ void __launch_bounds__(TC_M) k_leg_synth_tc(const LegArgs<float> a) {
     typedef TcCfg<SPIN> Cfg;
-    typedef TcLayout<SPIN> Lay;
+    typedef TcLayout<SPIN, NSTG, SCH> Lay;
     constexpr int NCOL = Cfg::NCOL;
     extern __shared__ __align__(1024) unsigned char smem[];
     float2 *s_alm = reinterpret_cast<float2 *>(smem + Lay::ALM);
@@ -285,10 +293,10 @@ __global__ void __launch_bounds__(TC_M) k_leg_synth_tc(const LegArgs<float> a) {
     bool ok = true;
     int chunk = 0;
     const int l_begin = m + ((lo - m) & ~31);   // chunks start at l - m = 0 mod 32
-    for (int c0 = l_begin; c0 <= L; c0 += LEG_CHUNK) {
-        // ---- stage coefficients and beam-weighted alm of l = c0 .. c0 + 127
+    for (int c0 = l_begin; c0 <= L; c0 += SCH) {
+        // ---- stage coefficients and beam-weighted alm of l = c0 .. c0 + SCH - 1
         __syncthreads();
-        for (int i = tid; i < LEG_CHUNK; i += TC_M) {
+        for (int i = tid; i < SCH; i += TC_M) {
             const int l = c0 + i;
             const bool in = l <= L;
             const int64_t idx = base + l;
@@ -306,19 +314,20 @@ __global__ void __launch_bounds__(TC_M) k_leg_synth_tc(const LegArgs<float> a) {
                     v.x *= bm;
                     v.y *= bm;
                 }
-                s_alm[k * TC_ALMS + i] = v;
+                s_alm[k * Lay::ALMS + i] = v;
             }
         }
         __syncthreads();
-        for (int q0 = c0; q0 < c0 + LEG_CHUNK && q0 <= L; q0 += 32, ++chunk) {
-            const int sidx = chunk & 1;
+        for (int q0 = c0; q0 < c0 + SCH && q0 <= L; q0 += 32, ++chunk) {
+            const int sidx = chunk % NSTG;
             unsigned char *stg = smem + sidx * Lay::STAGE;
-            // the MMAs of chunk - 2 read this stage: wait for their commit
-            if (chunk >= 2) ok = mbar_wait(&bars[sidx], ((chunk >> 1) - 1) & 1) && ok;
+            // the MMAs of chunk - NSTG read this stage: wait for their commit
+            // (the k-th commit on a barrier completes its phase k)
+            if (chunk >= NSTG) ok = mbar_wait(&bars[sidx], ((chunk - NSTG) / NSTG) & 1) && ok;
             const int i0 = q0 - c0;
             if (q0 <= warp_hi) gen_atiles<SPIN, true>(S, s_rec, s_s2c, i0, q0, stg);
             else gen_atiles<SPIN, false>(S, s_rec, s_s2c, i0, q0, stg);
-            gen_btiles<SPIN>(s_alm, i0, stg + Cfg::NTA * TC_ATILE);
+            gen_btiles<SPIN, Lay::ALMS>(s_alm, i0, stg + Cfg::NTA * TC_ATILE);
             asm volatile("fence.proxy.async.shared::cta;");
             __syncthreads();
             if (tid == 0) {
@@ -353,7 +362,7 @@ __global__ void __launch_bounds__(TC_M) k_leg_synth_tc(const LegArgs<float> a) {
     }
     // ---- the last commit covers every MMA issued before it
     const int last = chunk - 1;
-    ok = mbar_wait(&bars[last & 1], (last >> 1) & 1) && ok;
+    ok = mbar_wait(&bars[last % NSTG], (last / NSTG) & 1) && ok;
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (!ok && tid == 0 && a.err) atomicExch(a.err, 1);
 
@@ -406,7 +415,7 @@ __global__ void __launch_bounds__(TC_M) k_leg_synth_tc(const LegArgs<float> a) {
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::TMEM));
 }
 
-template <int SPIN>
+template <int SPIN, int NSTG, int SCH>
 int launch_synth_tc(Plan *p, const float2 *alm, int rs, int nmaps, const float *beam, float2 *F,
                     cudaStream_t st) {
     LegArgs<float> a = leg_make_args<float>(p);
@@ -416,16 +425,16 @@ int launch_synth_tc(Plan *p, const float2 *alm, int rs, int nmaps, const float *
     a.beam = beam;
     a.nmaps = nmaps;
     a.err = p->d_flag;
-    const int smem = TcLayout<SPIN>::BYTES;
-    SHTG_CUDA(cudaFuncSetAttribute(k_leg_synth_tc<SPIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const int smem = TcLayout<SPIN, NSTG, SCH>::BYTES;
+    auto kern = k_leg_synth_tc<SPIN, NSTG, SCH>;
+    SHTG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     dim3 grid((p->npairs + TC_M - 1) / TC_M, p->lmax + 1, (nmaps + TC_NMT - 1) / TC_NMT);
     prof_begin(p, K_LEG_SYN32, st);
-    k_leg_synth_tc<SPIN><<<grid, TC_M, smem, st>>>(a);
+    kern<<<grid, TC_M, smem, st>>>(a);
     prof_end(p, st);
     SHTG_CHECK_LAUNCH("k_leg_synth_tc");
     return SHTG_OK;
 }
-
 
 // FP32 recurrence state before every l = m + 32 t of every (m, ring pair):
 // the same steps (rstep / step2 with the same injections) as the Legendre
@@ -503,7 +512,6 @@ namespace {
 // recurrence of pair p over 32 l from the tabulated state at l = m + 32 t.
 // The CTA accumulates over all ring pairs in tensor memory, so every alm is
 // written once, by one CTA, without atomics.
-constexpr int TA_R = 2;         // 256-l tiles per CTA
 constexpr int TA_K = 16;        // ring pairs per stage (MMA K)
 template <int SPIN> struct TaCfg;
 template <> struct TaCfg<0> {
@@ -512,18 +520,24 @@ template <> struct TaCfg<0> {
 template <> struct TaCfg<2> {
     static constexpr int NO = 32, NAT = 8, NBT = 4, TMEM = 128;
 };
-template <int SPIN> struct TaLayout {
+// Shared memory of the transpose CTA (TR 256-l tiles): NAS A buffers (the
+// tiles of one (stage, 256-l tile) unit), NBS B buffers (one per stage of 16
+// pairs), the double-buffered ring data, the coefficients of 256 TR l, two
+// mbarriers and the TMEM address.  Fewer buffers and TR = 1 shrink the CTA
+// (spin 2: 52 KB instead of 99 KB) so that four CTAs share an SM.
+template <int SPIN, int NAS, int NBS, int TR> struct TaLayout {
     static constexpr int BT = 64 * TaCfg<SPIN>::NO;                         // B tile: 2 NO rows x 16 K bf16
     static constexpr int ASTAGE = TaCfg<SPIN>::NAT * TC_ATILE;
     static constexpr int BSTAGE = TaCfg<SPIN>::NBT * BT;
-    static constexpr int BOFF = 2 * ASTAGE;
+    static constexpr int BOFF = NAS * ASTAGE;
     // ring data of one stage: [pair][row][north, south] float2, pair stride GS (odd)
     static constexpr int NROW = SPIN == 2 ? 2 * TC_NMT : TC_NMT;
     static constexpr int GS = 2 * NROW + 1;
     static constexpr int GBUF = ((TA_K * GS * 8) + 15) & ~15;
-    static constexpr int GOFF = BOFF + 2 * BSTAGE;
+    static constexpr int GOFF = BOFF + NBS * BSTAGE;
     static constexpr int COEF = GOFF + 2 * GBUF;
-    static constexpr int BARS = COEF + 512 * (SPIN == 2 ? 16 : 8);
+    static constexpr int BARS = COEF + 256 * TR * (SPIN == 2 ? 16 : 8);
+    static constexpr int TMEM = TR * TaCfg<SPIN>::TMEM / 2;   // 2 NO columns per 256-l tile
     static constexpr int TMEMA = BARS + 16;
     static constexpr int BYTES = TMEMA + 16;
 };
@@ -659,7 +673,7 @@ __device__ __forceinline__ void gen_atiles_ana(const PairStart &q, const float4 
 template <int SPIN>
 __device__ __forceinline__ void stage_ring_data(const LegArgs<float> &a, const int m, const int ps, const int map0,
                                                 const int nm, float2 *sg) {
-    typedef TaLayout<SPIN> Lay;
+    typedef TaLayout<SPIN, 1, 1, 1> Lay;   // (ring-data geometry only)
     const int L = a.lmax;
     const int64_t rowsz = (int64_t)a.nring * (L + 1);
     const int nrow = SPIN == 2 ? 2 * nm : nm;
@@ -690,7 +704,7 @@ __device__ __forceinline__ void stage_ring_data(const LegArgs<float> &a, const i
 // four consecutive lanes fill one 16-byte core-matrix row.
 template <int SPIN>
 __device__ __forceinline__ void gen_btiles_ana(const float2 *sg, unsigned char *bt) {
-    typedef TaLayout<SPIN> Lay;
+    typedef TaLayout<SPIN, 1, 1, 1> Lay;   // (tile geometry only)
     constexpr int NO = TaCfg<SPIN>::NO, NBT = TaCfg<SPIN>::NBT, BT = Lay::BT;
     for (int it = threadIdx.x; it < NBT * 8 * NO; it += TC_M) {
         const int kq = it & 3;
@@ -724,10 +738,10 @@ __device__ __forceinline__ void gen_btiles_ana(const float2 *sg, unsigned char *
     }
 }
 
-template <int SPIN>
+template <int SPIN, int NAS, int NBS, int TR>
 __global__ void __launch_bounds__(TC_M) k_leg_analysis_tc(const LegArgs<float> a) {
     typedef TaCfg<SPIN> Cfg;
-    typedef TaLayout<SPIN> Lay;
+    typedef TaLayout<SPIN, NAS, NBS, TR> Lay;
     constexpr int NO = Cfg::NO;
     extern __shared__ __align__(1024) unsigned char smem[];
     float2 *s_rec = reinterpret_cast<float2 *>(smem + Lay::COEF);
@@ -738,15 +752,15 @@ __global__ void __launch_bounds__(TC_M) k_leg_analysis_tc(const LegArgs<float> a
     const int tid = threadIdx.x, warp = tid >> 5;
     const int m = blockIdx.y;
     const int L = a.lmax;
-    const int lbase = m + blockIdx.x * (256 * TA_R);
+    const int lbase = m + blockIdx.x * (256 * TR);
     if (lbase > L) return;
-    const int ntile = min(TA_R, (L - lbase) / 256 + 1);
-    const int lend = min(L, lbase + 256 * TA_R - 1);
+    const int ntile = min(TR, (L - lbase) / 256 + 1);
+    const int lend = min(L, lbase + 256 * TR - 1);
     const int map0 = blockIdx.z * TC_NMT;
     const int nm = min(TC_NMT, a.nmaps - map0);
     const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2;
 
-    for (int i = tid; i < 256 * TA_R; i += TC_M) {
+    for (int i = tid; i < 256 * TR; i += TC_M) {
         const int l = lbase + i;
         const bool in = l <= L;
         if (SPIN == 2) s_s2c[i] = in ? a.s2c[base + l] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -759,7 +773,7 @@ __global__ void __launch_bounds__(TC_M) k_leg_analysis_tc(const LegArgs<float> a
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(s_tmem)),
-                     "r"(Cfg::TMEM));
+                     "r"(Lay::TMEM));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -802,7 +816,9 @@ __global__ void __launch_bounds__(TC_M) k_leg_analysis_tc(const LegArgs<float> a
 
     bool ok = true;
     int unit = 0, waited = -1;
-    int last_unit[2] = {-1, -1};   // last unit that read each B buffer
+    int last_unit[NBS];            // last unit that read each B buffer
+#pragma unroll
+    for (int i = 0; i < NBS; ++i) last_unit[i] = -1;
     PairStart pst{}, pnext{};
     float4 tcur = make_float4(0.f, 0.f, 0.f, 0.f);
     if (nst > 0) {
@@ -822,19 +838,22 @@ __global__ void __launch_bounds__(TC_M) k_leg_analysis_tc(const LegArgs<float> a
             asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncthreads();
-        const int bsel = si & 1;
+        // unit u commits to barrier u % NAS, completing its phase u / NAS; the
+        // commits complete in order, so waiting for u covers every unit before it
+        const int bsel = si % NBS;
         unsigned char *bt = smem + Lay::BOFF + bsel * Lay::BSTAGE;
-        if (last_unit[bsel] > waited) {   // the stage two back read this B buffer
-            ok = mbar_wait(&bars[last_unit[bsel] & 1], (last_unit[bsel] >> 1) & 1) && ok;
-            waited = last_unit[bsel];
+        if (last_unit[bsel] > waited) {   // the stage NBS back read this B buffer
+            const int u = last_unit[bsel];
+            ok = mbar_wait(&bars[u % NAS], (u / NAS) & 1) && ok;
+            waited = u;
         }
-        gen_btiles_ana<SPIN>(sgb + bsel * (Lay::GBUF / 8), bt);
+        gen_btiles_ana<SPIN>(sgb + (si & 1) * (Lay::GBUF / 8), bt);   // ring data: double-buffered per stage
         for (int r = 0; r < ntile; ++r) {
-            const int asel = unit & 1;
+            const int asel = unit % NAS;
             unsigned char *at = smem + asel * Lay::ASTAGE;
-            if (unit >= 2 && unit - 2 > waited) {   // the unit two back read this A buffer
-                ok = mbar_wait(&bars[asel], ((unit >> 1) - 1) & 1) && ok;
-                waited = unit - 2;
+            if (unit >= NAS && unit - NAS > waited) {   // the unit NAS back read this A buffer
+                ok = mbar_wait(&bars[asel], ((unit - NAS) / NAS) & 1) && ok;
+                waited = unit - NAS;
             }
             const int tstart = lbase + 256 * r;
             const int l0 = tstart + 32 * seg;
@@ -883,13 +902,13 @@ __global__ void __launch_bounds__(TC_M) k_leg_analysis_tc(const LegArgs<float> a
         }
         pst = pnext;
     }
-    if (unit > 0 && unit - 1 > waited) ok = mbar_wait(&bars[(unit - 1) & 1], ((unit - 1) >> 1) & 1) && ok;
+    if (unit > 0 && unit - 1 > waited) ok = mbar_wait(&bars[(unit - 1) % NAS], ((unit - 1) / NAS) & 1) && ok;
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (!ok && tid == 0 && a.err) atomicExch(a.err, 1);
 
     // ---- epilogue: lane = row i, l = tstart + 2 i (E tile) and + 1 (O tile)
 #pragma unroll
-    for (int r = 0; r < TA_R; ++r) {
+    for (int r = 0; r < TR; ++r) {
         if (r >= ntile) break;
         const int tstart = lbase + 256 * r;
 #pragma unroll
@@ -920,10 +939,10 @@ __global__ void __launch_bounds__(TC_M) k_leg_analysis_tc(const LegArgs<float> a
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::TMEM));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Lay::TMEM));
 }
 
-template <int SPIN>
+template <int SPIN, int NAS, int NBS, int TR>
 int launch_analysis_tc(Plan *p, const float2 *G, int nmaps, const float *beam, float2 *alm, int rs,
                        cudaStream_t st, int vjp) {
     LegArgs<float> a = leg_make_args<float>(p);
@@ -938,27 +957,51 @@ int launch_analysis_tc(Plan *p, const float2 *G, int nmaps, const float *beam, f
         set_error("tensor-core transpose: the plan has no recurrence tile states");
         return SHTG_ERR_ARG;
     }
-    const int smem = TaLayout<SPIN>::BYTES;
-    SHTG_CUDA(cudaFuncSetAttribute(k_leg_analysis_tc<SPIN>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    dim3 grid((p->lmax + 256 * TA_R) / (256 * TA_R), p->lmax + 1, (nmaps + TC_NMT - 1) / TC_NMT);
+    const int smem = TaLayout<SPIN, NAS, NBS, TR>::BYTES;
+    auto kern = k_leg_analysis_tc<SPIN, NAS, NBS, TR>;
+    SHTG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    dim3 grid((p->lmax + 256 * TR) / (256 * TR), p->lmax + 1, (nmaps + TC_NMT - 1) / TC_NMT);
     prof_begin(p, K_LEG_ANA32, st);
-    k_leg_analysis_tc<SPIN><<<grid, TC_M, smem, st>>>(a);
+    kern<<<grid, TC_M, smem, st>>>(a);
     prof_end(p, st);
     SHTG_CHECK_LAUNCH("k_leg_analysis_tc");
     return SHTG_OK;
 }
 }  // namespace
 
+// Shapes tried by the autotuner (key kind 2): synthesis (stages, staged l)
+// = (1, 64) [four CTAs per SM at spin 2], (2, 128), (1, 128); transpose
+// (A buffers, B buffers, 256-l tiles) = (1, 1, 1) [four CTAs per SM],
+// (2, 2, 2), (1, 2, 1), (2, 2, 1).  Every shape sums the same products in the
+// same order, so the choice does not change a bit of the result.
 int leg_synth_tc(Plan *p, int spin, const float2 *alm, int rs, int nmaps, const float *beam, float2 *F,
                  cudaStream_t st) {
-    if (spin == 2) return launch_synth_tc<2>(p, alm, rs, nmaps, beam, F, st);
-    return launch_synth_tc<0>(p, alm, rs, nmaps, beam, F, st);
+    return tune(p, 2, spin == 2 ? 1 : 0, nmaps, 3, st, [&](int v) {
+        if (spin == 2) {
+            if (v == 1) return launch_synth_tc<2, 2, 128>(p, alm, rs, nmaps, beam, F, st);
+            if (v == 2) return launch_synth_tc<2, 1, 128>(p, alm, rs, nmaps, beam, F, st);
+            return launch_synth_tc<2, 1, 64>(p, alm, rs, nmaps, beam, F, st);
+        }
+        if (v == 1) return launch_synth_tc<0, 2, 128>(p, alm, rs, nmaps, beam, F, st);
+        if (v == 2) return launch_synth_tc<0, 1, 128>(p, alm, rs, nmaps, beam, F, st);
+        return launch_synth_tc<0, 1, 64>(p, alm, rs, nmaps, beam, F, st);
+    });
 }
 
 int leg_analysis_tc(Plan *p, int spin, const float2 *G, int nmaps, const float *beam, float2 *alm, int rs,
                     cudaStream_t st, int vjp) {
-    if (spin == 2) return launch_analysis_tc<2>(p, G, nmaps, beam, alm, rs, st, vjp);
-    return launch_analysis_tc<0>(p, G, nmaps, beam, alm, rs, st, vjp);
+    return tune(p, 2, spin == 2 ? 3 : 2, nmaps, 4, st, [&](int v) {
+        if (spin == 2) {
+            if (v == 1) return launch_analysis_tc<2, 2, 2, 2>(p, G, nmaps, beam, alm, rs, st, vjp);
+            if (v == 2) return launch_analysis_tc<2, 1, 2, 1>(p, G, nmaps, beam, alm, rs, st, vjp);
+            if (v == 3) return launch_analysis_tc<2, 2, 2, 1>(p, G, nmaps, beam, alm, rs, st, vjp);
+            return launch_analysis_tc<2, 1, 1, 1>(p, G, nmaps, beam, alm, rs, st, vjp);
+        }
+        if (v == 1) return launch_analysis_tc<0, 2, 2, 2>(p, G, nmaps, beam, alm, rs, st, vjp);
+        if (v == 2) return launch_analysis_tc<0, 1, 2, 1>(p, G, nmaps, beam, alm, rs, st, vjp);
+        if (v == 3) return launch_analysis_tc<0, 2, 2, 1>(p, G, nmaps, beam, alm, rs, st, vjp);
+        return launch_analysis_tc<0, 1, 1, 1>(p, G, nmaps, beam, alm, rs, st, vjp);
+    });
 }
 
 }  // namespace shtg

@@ -550,6 +550,37 @@ static int build_fft_tables(Plan *p) {
             bi32[bo + i] = make_float2((float)b.real(), (float)b.imag());
         }
     }
+    // e^{i pi k / n} (phi0 = pi / n) for k <= min(lmax, n - 1), one table per
+    // distinct n of the shifted rings
+    std::map<int, int64_t> phoffs;
+    std::vector<double2> ph64;
+    std::vector<float2> ph32;
+    for (int r = 0; r < R; ++r) {
+        RingFFT &f = p->h_rfft[r];
+        f.ph_off = 0;
+        if (!f.shift) continue;
+        auto it = phoffs.find(f.n);
+        if (it != phoffs.end()) {
+            f.ph_off = it->second;
+            continue;
+        }
+        f.ph_off = (int64_t)ph64.size();
+        phoffs[f.n] = f.ph_off;
+        const int kmax = std::min(p->lmax, f.n - 1);
+        for (int k = 0; k <= kmax; ++k) {
+            const double ang = PI * (double)k / (double)f.n;
+            ph64.push_back(make_double2(cos(ang), sin(ang)));
+            ph32.push_back(make_float2((float)cos(ang), (float)sin(ang)));
+        }
+    }
+    if (ph64.empty()) {
+        ph64.push_back(make_double2(1.0, 0.0));
+        ph32.push_back(make_float2(1.0f, 0.0f));
+    }
+    SHTG_TRY(dalloc(p, &p->d_rph64, ph64.size()));
+    SHTG_TRY(dalloc(p, &p->d_rph32, ph32.size()));
+    SHTG_TRY(upload(p->d_rph64, ph64));
+    SHTG_TRY(upload(p->d_rph32, ph32));
     SHTG_TRY(dalloc(p, &p->d_rfft, R));
     SHTG_TRY(upload(p->d_rfft, p->h_rfft));
     SHTG_TRY(dalloc(p, &p->d_tw64, tw64.size()));
@@ -570,21 +601,32 @@ static int build_fft_tables(Plan *p) {
     SHTG_TRY(upload(p->d_binv32, bi32));
     p->fft_smem64 = (size_t)Mmax * sizeof(double2);
     p->fft_smem32 = (size_t)Mmax * sizeof(float2);
+    // launch groups: 0 = direct rings without aliasing (n a power of two and
+    // n >= 2 lmax: the equatorial belt), 1 = the rest (Bluestein rings and
+    // small power-of-two rings); each launch gets the thread count and shared
+    // memory of its longest transform
     std::vector<int> groups;
     for (int g = 0; g < 2; ++g) {
         p->ring_group_count[g] = 0;
         p->ring_group_logm[g] = 0;
         p->ring_group_qs[g] = 0;
-        for (int r = 0; r < p->npairs; ++r)
-            if (p->h_rfft[r].blue == g) {
-                groups.push_back(r);
-                p->ring_group_count[g] += 1;
-                p->ring_group_logm[g] = std::max(p->ring_group_logm[g], p->h_rfft[r].logM);
-                // Bluestein rings keep the south ring's folded spectrum in the
-                // upper half of their transform buffer (M >= 2n)
-                if (!g && p->h_rfft[r].n < 2 * p->lmax)
-                    p->ring_group_qs[g] = std::max(p->ring_group_qs[g], p->h_rfft[r].n);
+        p->ring_group_alias[g] = 0;
+        int nq = 0;
+        for (int r = 0; r < p->npairs; ++r) {
+            const RingFFT &f = p->h_rfft[r];
+            const int gr = (!f.blue && f.n >= 2 * p->lmax) ? 0 : 1;
+            if (gr != g) continue;
+            groups.push_back(r);
+            p->ring_group_count[g] += 1;
+            p->ring_group_logm[g] = std::max(p->ring_group_logm[g], f.logM);
+            if (f.n < 2 * p->lmax) {
+                p->ring_group_alias[g] = 1;
+                if (!f.blue) nq = std::max(nq, f.n);
             }
+        }
+        // the south ring's folded spectrum of an aliased ring goes to buf[n, 2n)
+        // when the launch's buffer has room (always for Bluestein rings: M >= 2n)
+        if (2 * (int64_t)nq > ((int64_t)1 << p->ring_group_logm[g])) p->ring_group_qs[g] = nq;
     }
     SHTG_TRY(dalloc(p, &p->d_ring_groups, groups.size()));
     SHTG_TRY(upload(p->d_ring_groups, groups));
@@ -660,7 +702,7 @@ void plan_free(Plan *p) {
                     p->d_ltab64, p->d_ltab32, p->d_scal, p->d_part, p->d_lsum, p->d_stage,
                     p->d_ls2_64, p->d_st2_64, p->d_ls2_32, p->d_st2_32, p->d_ring_groups, p->d_flag,
                     p->d_toff, p->d_tst0, p->d_tst2, p->d_isc64, p->d_rsc64, p->d_isc32,
-                    p->d_toff128, p->d_tst64_0, p->d_tst64_2};
+                    p->d_toff128, p->d_tst64_0, p->d_tst64_2, p->d_rph64, p->d_rph32};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (int i = 0; i < 7; ++i)

@@ -45,18 +45,6 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
 }
 __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -a.y); }
 
-// e^{i pi q / n} for integer q in [0, n)
-__device__ __forceinline__ float2 phase_pi(int q, int n, float) {
-    float s, c;
-    sincospif((float)q / (float)n, &s, &c);
-    return make_float2(c, s);
-}
-__device__ __forceinline__ double2 phase_pi(int q, int n, double) {
-    double s, c;
-    sincospi((double)q / (double)n, &s, &c);
-    return make_double2(c, s);
-}
-
 // v * e^{-+2 pi i k / 16} (minus sign: forward transform, plus: inverse); k is
 // a compile-time constant after unrolling, so the switch folds away
 template <bool INV, typename C>
@@ -270,12 +258,14 @@ template <typename T> struct RingArgs {
     const C *tw;      // two-level twiddle table [lo | hi]
     int tw_blo, tw_nlo, tw_nhi, logmax;
     const C *chirp, *bfwd, *binv;
+    const C *rph;     // ring phase tables e^{i pi k / n}
     C *FG;            // [map][ring][m]
     T *map;           // [map][npix]
     const T *ninv;    // fused: [comp][npix]
     int nT;           // fused: rows [0, nT) use N^-1 component 0 (T), later rows component 1 (Q, U)
     int weighted;     // analysis: multiply by the quadrature weight
     int buf_len;      // shared transform buffer length (padded) of this launch
+    int qs_len;       // separate south-ring scratch of aliased direct rings (0: in buf)
     const int *pairs; // ring pairs handled by this launch (one CTA each)
 };
 
@@ -301,7 +291,7 @@ __global__ void __launch_bounds__(NT, RingBlocks<T, NT>::v) k_ring(const RingArg
     C *s_tw = reinterpret_cast<C *>(s_raw);
     C *buf = s_tw + a.tw_nlo + a.tw_nhi;
     C *scr_p = buf + a.buf_len;   // aliased fold: partial sums [north | south][NT]
-    C *scr_q = scr_p + 2 * NT;    // aliased direct rings: Q_S / Y_S [n]
+    C *scr_q = scr_p + 2 * NT;    // aliased direct rings without room in buf: Q_S / Y_S [n]
     for (int i = threadIdx.x; i < a.tw_nlo + a.tw_nhi; i += NT) s_tw[i] = a.tw[i];
     TwTab<C> tw;
     tw.lo = s_tw;
@@ -317,6 +307,7 @@ __global__ void __launch_bounds__(NT, RingBlocks<T, NT>::v) k_ring(const RingArg
     const int n = f.n, logM = f.logM, M = 1 << logM;
     const int L = a.lmax;
     const C *chirp = a.chirp + f.chirp_off;
+    const C *ph = a.rph + f.ph_off;   // e^{i pi k / n} (shifted rings)
     const C zero = {T(0), T(0)};
     constexpr int NDIR = MODE == 2 ? 2 : 1;
 
@@ -332,9 +323,9 @@ __global__ void __launch_bounds__(NT, RingBlocks<T, NT>::v) k_ring(const RingArg
             for (int mm = threadIdx.x; mm <= L; mm += NT) {
                 C hn = Fn[mm], hs = single ? zero : Fs[mm];
                 if (f.shift) {
-                    const C ph = phase_pi(mm, n, T(0));
-                    hn = cmul(hn, ph);
-                    hs = cmul(hs, ph);
+                    const C phk = ph[mm];
+                    hn = cmul(hn, phk);
+                    hs = cmul(hs, phk);
                 }
                 C z1 = {hn.x - hs.y, hn.y + hs.x};      // bin mm
                 C z2 = {hn.x + hs.y, -hn.y + hs.x};     // bin n - mm: conj(hn) + i conj(hs)
@@ -359,8 +350,9 @@ __global__ void __launch_bounds__(NT, RingBlocks<T, NT>::v) k_ring(const RingArg
             // small polar ring costs no more time than a long one.
             const C *Fn = a.FG + ((int64_t)q * a.nring + rn) * (L + 1);
             const C *Fs = a.FG + ((int64_t)q * a.nring + rs) * (L + 1);
-            // Q of the south ring: buf[n, 2n) for Bluestein rings (M >= 2n), else scratch
-            auto qsr = [&](int k) -> C & { return f.blue ? buf[rpad(n + k)] : scr_q[k]; };
+            // Q of the south ring: buf[n, 2n) when the launch's buffer has room
+            // (Bluestein rings: M >= 2n), else scratch
+            auto qsr = [&](int k) -> C & { return (f.blue || !a.qs_len) ? buf[rpad(n + k)] : scr_q[k]; };
             const int S = n <= NT / 2 ? NT / n : 1;
             if (S > 1) {
                 const int k = threadIdx.x % n, s = threadIdx.x / n;
@@ -431,10 +423,10 @@ __global__ void __launch_bounds__(NT, RingBlocks<T, NT>::v) k_ring(const RingArg
                 hs2 = {qs2.x + sig * qs1.x, qs2.y - sig * qs1.y};
                 if (f.shift) {
                     // e^{i pi (n - k) / n} = -conj e^{i pi k / n}
-                    const C ph = phase_pi(k1, n, T(0));
-                    const C ph2 = {-ph.x, ph.y};
-                    hn1 = cmul(hn1, ph);
-                    hs1 = cmul(hs1, ph);
+                    const C ph1 = ph[k1];
+                    const C ph2 = {-ph1.x, ph1.y};
+                    hn1 = cmul(hn1, ph1);
+                    hs1 = cmul(hs1, ph1);
                     hn2 = cmul(hn2, ph2);
                     hs2 = cmul(hs2, ph2);
                 }
@@ -512,9 +504,9 @@ __global__ void __launch_bounds__(NT, RingBlocks<T, NT>::v) k_ring(const RingArg
                     C yn = {T(0.5) * (w1.x + w2.x), T(0.5) * (w1.y - w2.y)};
                     C ys = {T(0.5) * (w1.y + w2.y), T(-0.5) * (w1.x - w2.x)};
                     if (f.shift) {
-                        const C ph = cconj(phase_pi(k, n, T(0)));
-                        yn = cmul(yn, ph);
-                        ys = cmul(ys, ph);
+                        const C phk = cconj(ph[k]);
+                        yn = cmul(yn, phk);
+                        ys = cmul(ys, phk);
                     }
                     Gn[k] = yn;
                     if (!single) Gs[k] = ys;
@@ -523,7 +515,7 @@ __global__ void __launch_bounds__(NT, RingBlocks<T, NT>::v) k_ring(const RingArg
                 // aliased rings: Y_N(k), Y_S(k) for bins k and n - k from one
                 // thread (Y_N in place over buf, Y_S beside it), then every m
                 // written once, coalesced
-                auto ysr = [&](int k) -> C & { return f.blue ? buf[rpad(n + k)] : scr_q[k]; };
+                auto ysr = [&](int k) -> C & { return (f.blue || !a.qs_len) ? buf[rpad(n + k)] : scr_q[k]; };
                 for (int j = threadIdx.x; 2 * j <= n; j += NT) {
                     const int k1 = j, k2 = j ? n - j : 0;
                     C w1 = buf[rpad(k1)], w2 = buf[rpad(k2)];
@@ -537,10 +529,10 @@ __global__ void __launch_bounds__(NT, RingBlocks<T, NT>::v) k_ring(const RingArg
                     C ys2 = {ys1.x, -ys1.y};
                     if (f.shift) {
                         // e^{-i pi (n - k) / n} = -conj e^{-i pi k / n}
-                        const C ph = cconj(phase_pi(k1, n, T(0)));
-                        const C ph2 = {-ph.x, ph.y};
-                        yn1 = cmul(yn1, ph);
-                        ys1 = cmul(ys1, ph);
+                        const C ph1 = cconj(ph[k1]);
+                        const C ph2 = {-ph1.x, ph1.y};
+                        yn1 = cmul(yn1, ph1);
+                        ys1 = cmul(ys1, ph1);
                         yn2 = cmul(yn2, ph2);
                         ys2 = cmul(ys2, ph2);
                     }
@@ -580,6 +572,7 @@ template <> RingArgs<float> ring_args<float>(Plan *p) {
     RingArgs<float> a{};
     a.tw = p->d_tw32;
     a.chirp = p->d_chirp32;
+    a.rph = p->d_rph32;
     a.bfwd = p->d_bfwd32;
     a.binv = p->d_binv32;
     return a;
@@ -588,6 +581,7 @@ template <> RingArgs<double> ring_args<double>(Plan *p) {
     RingArgs<double> a{};
     a.tw = p->d_tw64;
     a.chirp = p->d_chirp64;
+    a.rph = p->d_rph64;
     a.bfwd = p->d_bfwd64;
     a.binv = p->d_binv64;
     return a;
@@ -607,8 +601,8 @@ static int launch_ring(Plan *p, RingArgs<T> a, cudaStream_t st) {
     a.tw_blo = p->tw_blo;
     a.tw_nlo = p->tw_nlo;
     a.tw_nhi = p->tw_nhi;
-    // direct (power-of-two) and Bluestein ring pairs run as separate launches so
-    // that each gets the shared memory and thread count its transform length needs
+    // alias-free direct ring pairs and the rest run as separate launches so that
+    // each gets the shared memory and thread count its transform length needs
     prof_begin(p, sizeof(T) == 8 ? K_RING64 : K_RING32, st);
     for (int g = 0; g < 2; ++g) {
         const int cnt = p->ring_group_count[g];
@@ -616,8 +610,9 @@ static int launch_ring(Plan *p, RingArgs<T> a, cudaStream_t st) {
         const int M = 1 << p->ring_group_logm[g];
         const int nt = M <= 4096 ? 256 : 512;
         a.buf_len = M + M / 16;
-        const size_t smem = sizeof(C) * ((size_t)p->tw_nlo + p->tw_nhi + a.buf_len + 2 * nt +
-                                         p->ring_group_qs[g]);
+        a.qs_len = p->ring_group_qs[g];
+        const size_t smem = sizeof(C) * ((size_t)p->tw_nlo + p->tw_nhi + a.buf_len +
+                                         (p->ring_group_alias[g] ? 2 * nt + a.qs_len : 0));
         a.pairs = p->d_ring_groups + (g ? p->ring_group_count[0] : 0);
         if (nt == 256) {
             auto kern = k_ring<T, MODE, 256>;
