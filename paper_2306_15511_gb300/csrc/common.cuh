@@ -54,6 +54,19 @@ struct RingFFT {
     int64_t ph_off;     // shifted rings: offset of e^{i pi k / n}, k = 0 .. min(lmax, n - 1)
 };
 
+// Ring FFT launches (ringfft.cu): threads per CTA for a launch whose
+// longest buffer is 2^logm, and the butterflies per thread of the first
+// radix-R pass (R = 2, 4, 8; log2 M not a multiple of four) that the kernel
+// of that thread count is compiled for.  Launch buckets hold rings with
+// M = 2^logm (and M = 2^(logm - 1) for aliased direct rings); the bucket of
+// lengths <= 1024 runs 64 threads.
+__host__ __device__ constexpr int ring_threads(int logm) {
+    return logm >= 13 ? 512 : logm == 12 ? 256 : logm == 11 ? 128 : 64;
+}
+__host__ __device__ constexpr int ring_first_bpt(int R, int nt) {
+    return nt >= 512 ? (R == 2 ? 8 : 1) : nt == 256 ? 1 : nt == 128 ? (R == 2 ? 1 : 2) : (R == 8 ? 1 : 4);
+}
+
 // Kernel classes timed live with CUDA events (on the launching stream) when
 // profiling is on; see shtg_cg_stats.kernel_ms.
 enum KClass { K_LEG_SYN32 = 0, K_LEG_ANA32, K_RING32, K_LEG_SYN64, K_LEG_ANA64, K_RING64, K_VEC, K_DIAG };
@@ -121,11 +134,13 @@ struct Plan {
     double2 *d_rph64 = nullptr;   // ring phase tables (RingFFT::ph_off)
     float2 *d_rph32 = nullptr;
     size_t fft_smem64 = 0, fft_smem32 = 0;
-    int *d_ring_groups = nullptr;    // ring pairs: alias-free direct pairs first, then the rest
-    int ring_group_count[2] = {0, 0};
-    int ring_group_logm[2] = {0, 0}; // largest log2 transform length in each group
-    int ring_group_qs[2] = {0, 0};   // separate scratch for the south ring of aliased direct rings
-    int ring_group_alias[2] = {0, 0}; // group holds rings with n < 2 lmax
+    int *d_ring_groups = nullptr;    // ring pairs, ordered by launch bucket
+    struct RingLaunch {
+        int off, count;   // slice of d_ring_groups
+        int logm;         // log2 of the bucket's buffer length (every member's M, and 2n if aliased)
+        int alias;        // bucket holds rings with n < 2 lmax
+    };
+    std::vector<RingLaunch> ring_launch;
 
     // workspace
     double2 *d_phase64 = nullptr;  // [nmaps_max][nring][lmax+1] Fourier coefficients per ring

@@ -325,7 +325,10 @@ __global__ void __launch_bounds__(TC_M) k_leg_synth_tc(const LegArgs<float> a) {
             // (the k-th commit on a barrier completes its phase k)
             if (chunk >= NSTG) ok = mbar_wait(&bars[sidx], ((chunk - NSTG) / NSTG) & 1) && ok;
             const int i0 = q0 - c0;
-            if (q0 <= warp_hi) gen_atiles<SPIN, true>(S, s_rec, s_s2c, i0, q0, stg);
+            // injection steps only where some pair of the warp starts in this chunk
+            const bool starts = (S.ls[0] >= q0 && S.ls[0] < q0 + 32) ||
+                                (SPIN == 2 && S.lsb[0] >= q0 && S.lsb[0] < q0 + 32);
+            if (q0 <= warp_hi && __any_sync(0xffffffffu, starts)) gen_atiles<SPIN, true>(S, s_rec, s_s2c, i0, q0, stg);
             else gen_atiles<SPIN, false>(S, s_rec, s_s2c, i0, q0, stg);
             gen_btiles<SPIN, Lay::ALMS>(s_alm, i0, stg + Cfg::NTA * TC_ATILE);
             asm volatile("fence.proxy.async.shared::cta;");
@@ -606,8 +609,9 @@ __device__ __forceinline__ float4 load_tile_state(const LegArgs<float> &a, int m
 // K = 16 slice) over l = l0 .. l0 + 31, l0 = tstart + 32 seg, from state ts;
 // values of class E (l - m even) go to rows 16 seg + j of the E tiles, class
 // O to the same rows of the O tiles.  Pairs beyond npairs and l beyond lmax
-// give 0.
-template <int SPIN>
+// give 0.  INJ: some pair of the warp starts its recurrence inside the
+// segment (the tabulated state already holds every earlier start).
+template <int SPIN, bool INJ>
 __device__ __forceinline__ void gen_atiles_ana(const PairStart &q, const float4 ts, const bool live, const int pin,
                                                const int seg, const int l0, const int lbase,
                                                const float2 *s_rec, const float4 *s_s2c, unsigned char *at) {
@@ -635,9 +639,9 @@ __device__ __forceinline__ void gen_atiles_ana(const PairStart &q, const float4 
                 const int d = 16 * h + 2 * i;
                 e[i] = o[i] = 0.f;
                 if (live) {
-                    stepx<float, 1, 0, true>(S, s_rec, s_s2c, l0 + d - lbase, l0 + d);
+                    stepx<float, 1, 0, INJ>(S, s_rec, s_s2c, l0 + d - lbase, l0 + d);
                     e[i] = S.a1[0];
-                    stepx<float, 1, 0, true>(S, s_rec, s_s2c, l0 + d + 1 - lbase, l0 + d + 1);
+                    stepx<float, 1, 0, INJ>(S, s_rec, s_s2c, l0 + d + 1 - lbase, l0 + d + 1);
                     o[i] = S.a1[0];
                 }
             }
@@ -650,10 +654,10 @@ __device__ __forceinline__ void gen_atiles_ana(const PairStart &q, const float4 
                 const int d = 16 * h + 2 * i;
                 wE[i] = wO[i] = xE[i] = xO[i] = 0.f;
                 if (live) {
-                    stepx<float, 1, 2, true>(S, s_rec, s_s2c, l0 + d - lbase, l0 + d);
+                    stepx<float, 1, 2, INJ>(S, s_rec, s_s2c, l0 + d - lbase, l0 + d);
                     wE[i] = S.a1[0] + S.b1[0];
                     xE[i] = S.a1[0] - S.b1[0];
-                    stepx<float, 1, 2, true>(S, s_rec, s_s2c, l0 + d + 1 - lbase, l0 + d + 1);
+                    stepx<float, 1, 2, INJ>(S, s_rec, s_s2c, l0 + d + 1 - lbase, l0 + d + 1);
                     wO[i] = S.a1[0] + S.b1[0];
                     xO[i] = S.a1[0] - S.b1[0];
                 }
@@ -697,44 +701,75 @@ __device__ __forceinline__ void stage_ring_data(const LegArgs<float> &a, const i
 
 // B tiles of one stage from the staged ring data.  Tile b: spin 0 -> rows
 // for class b (0: G_N + G_S, 1: G_N - G_S) with columns (re, im) per map;
-// spin 2 -> b = 2 x + class with lw columns (x = 0) from the set of the
-// row's class and lx columns (x = 1) from the other set:
+// spin 2 -> b = 2 x + class' with lw columns (x = 0, class' = b) and lx
+// columns (x = 1, class' = the other one):
 //   E^ = -lw G_Q - i lx G_U,  B^ = i lx G_Q - lw G_U
-// (columns E re, E im, B re, B im per map).  hi at row c, lo at row NO + c;
-// four consecutive lanes fill one 16-byte core-matrix row.
+// (columns E re, E im, B re, B im per map).  hi at row c, lo at row NO + c.
+// One thread per (K group kg, K pair kq, column c) writes that column's word
+// (two consecutive ring pairs) in every tile: a warp covers 8 consecutive
+// columns x 4 K pairs, i.e. 32 distinct banks per store, and reads only the
+// two scalars per ring pair that its column needs.
 template <int SPIN>
 __device__ __forceinline__ void gen_btiles_ana(const float2 *sg, unsigned char *bt) {
     typedef TaLayout<SPIN, 1, 1, 1> Lay;   // (tile geometry only)
-    constexpr int NO = TaCfg<SPIN>::NO, NBT = TaCfg<SPIN>::NBT, BT = Lay::BT;
-    for (int it = threadIdx.x; it < NBT * 8 * NO; it += TC_M) {
+    constexpr int NO = TaCfg<SPIN>::NO, BT = Lay::BT;
+    const float *sgf = reinterpret_cast<const float *>(sg);
+    for (int it = threadIdx.x; it < 8 * NO; it += TC_M) {
         const int kq = it & 3;
         const int c = (it >> 2) % NO;
-        const int kg = (it / (4 * NO)) & 1;
-        const int b = it / (8 * NO);
+        const int kg = it / (4 * NO);
         const int k0 = 8 * kg + 2 * kq;
-        const int cls = SPIN == 2 ? ((b & 1) ^ (b >> 1)) : b;   // 0: G_N + G_S, 1: G_N - G_S
-        const float sg_ = cls ? -1.f : 1.f;
-        float v[2];
+        unsigned char *tile = bt + kg * (32 * NO) + kq * 4;
+        if (SPIN == 0) {
+            // column c: component c & 1 of map c >> 1
+            float vp[2], vm[2];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const float2 *g = sg + (k0 + q) * Lay::GS;
-            if (SPIN == 0) {
-                const float2 gn = g[2 * (c >> 1)], gs = g[2 * (c >> 1) + 1];
-                v[q] = (c & 1) ? gn.y + sg_ * gs.y : gn.x + sg_ * gs.x;
-            } else {
-                const int k = c >> 2, comp = c & 3;
-                const float2 qn = g[4 * k], qs = g[4 * k + 1], un = g[4 * k + 2], us = g[4 * k + 3];
-                const float2 Q = make_float2(qn.x + sg_ * qs.x, qn.y + sg_ * qs.y);
-                const float2 U = make_float2(un.x + sg_ * us.x, un.y + sg_ * us.y);
-                if (b < 2) v[q] = comp == 0 ? -Q.x : comp == 1 ? -Q.y : comp == 2 ? -U.x : -U.y;
-                else v[q] = comp == 0 ? U.y : comp == 1 ? -U.x : comp == 2 ? -Q.y : Q.x;
+            for (int q = 0; q < 2; ++q) {
+                const float *g = sgf + 2 * ((k0 + q) * Lay::GS + 2 * (c >> 1)) + (c & 1);
+                const float gn = g[0], gs = g[2];
+                vp[q] = gn + gs;
+                vm[q] = gn + (-1.f) * gs;
             }
+            uint32_t hi, lo;
+            split2(vp[0], vp[1], hi, lo);
+            *reinterpret_cast<uint32_t *>(tile + c * 16) = hi;
+            *reinterpret_cast<uint32_t *>(tile + (NO + c) * 16) = lo;
+            split2(vm[0], vm[1], hi, lo);
+            *reinterpret_cast<uint32_t *>(tile + BT + c * 16) = hi;
+            *reinterpret_cast<uint32_t *>(tile + BT + (NO + c) * 16) = lo;
+        } else {
+            // column c = 4 k + comp of map k; the lw tiles take w = (-Q re,
+            // -Q im, -U re, -U im)[comp], the lx tiles x = (U im, -U re,
+            // -Q im, Q re)[comp], each as N + S or N - S
+            const int k = c >> 2, comp = c & 3;
+            const int wf = comp < 2 ? 0 : 1, wc = comp & 1;            // field (Q 0, U 1), re / im
+            const int xf = comp < 2 ? 1 : 0, xc = (comp & 1) ^ 1;
+            const float xs = (comp == 1 || comp == 2) ? -1.f : 1.f;
+            float wp[2], wm[2], xp[2], xm[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const float *g = sgf + 2 * ((k0 + q) * Lay::GS + 4 * k);
+                const float wn = g[4 * wf + wc], wsv = g[4 * wf + 2 + wc];
+                const float xn = g[4 * xf + xc], xsv = g[4 * xf + 2 + xc];
+                wp[q] = -(wn + wsv);
+                wm[q] = -(wn + (-1.f) * wsv);
+                xp[q] = xs * (xn + xsv);
+                xm[q] = xs * (xn + (-1.f) * xsv);
+            }
+            uint32_t hi, lo;
+            split2(wp[0], wp[1], hi, lo);   // b = 0: lw, class 0
+            *reinterpret_cast<uint32_t *>(tile + c * 16) = hi;
+            *reinterpret_cast<uint32_t *>(tile + (NO + c) * 16) = lo;
+            split2(wm[0], wm[1], hi, lo);   // b = 1: lw, class 1
+            *reinterpret_cast<uint32_t *>(tile + BT + c * 16) = hi;
+            *reinterpret_cast<uint32_t *>(tile + BT + (NO + c) * 16) = lo;
+            split2(xm[0], xm[1], hi, lo);   // b = 2: lx, class 1
+            *reinterpret_cast<uint32_t *>(tile + 2 * BT + c * 16) = hi;
+            *reinterpret_cast<uint32_t *>(tile + 2 * BT + (NO + c) * 16) = lo;
+            split2(xp[0], xp[1], hi, lo);   // b = 3: lx, class 0
+            *reinterpret_cast<uint32_t *>(tile + 3 * BT + c * 16) = hi;
+            *reinterpret_cast<uint32_t *>(tile + 3 * BT + (NO + c) * 16) = lo;
         }
-        uint32_t hi, lo;
-        split2(v[0], v[1], hi, lo);
-        unsigned char *tile = bt + b * BT + kg * (32 * NO) + kq * 4;
-        *reinterpret_cast<uint32_t *>(tile + c * 16) = hi;
-        *reinterpret_cast<uint32_t *>(tile + (NO + c) * 16) = lo;
     }
 }
 
@@ -861,7 +896,12 @@ __global__ void __launch_bounds__(TC_M) k_leg_analysis_tc(const LegArgs<float> a
             float4 tnext = make_float4(0.f, 0.f, 0.f, 0.f);
             if (r + 1 < ntile) tnext = load_tile_state<SPIN>(a, m, pr, l0 + 256);
             else if (more) tnext = load_tile_state<SPIN>(a, m, pr + TA_K, lbase + 32 * seg);
-            gen_atiles_ana<SPIN>(pst, tcur, pr < a.npairs && l0 <= L, pin, seg, l0, lbase, s_rec, s_s2c, at);
+            const bool live = pr < a.npairs && l0 <= L;
+            const bool starts = (pst.ls >= l0 && pst.ls < l0 + 32) || (SPIN == 2 && pst.lsb >= l0 && pst.lsb < l0 + 32);
+            if (__any_sync(0xffffffffu, live && starts))
+                gen_atiles_ana<SPIN, true>(pst, tcur, live, pin, seg, l0, lbase, s_rec, s_s2c, at);
+            else
+                gen_atiles_ana<SPIN, false>(pst, tcur, live, pin, seg, l0, lbase, s_rec, s_s2c, at);
             tcur = tnext;
             asm volatile("fence.proxy.async.shared::cta;");
             __syncthreads();

@@ -12,6 +12,7 @@
 #include <complex>
 #include <cstring>
 #include <algorithm>
+#include <functional>
 #include <map>
 
 #include "common.cuh"
@@ -601,32 +602,48 @@ static int build_fft_tables(Plan *p) {
     SHTG_TRY(upload(p->d_binv32, bi32));
     p->fft_smem64 = (size_t)Mmax * sizeof(double2);
     p->fft_smem32 = (size_t)Mmax * sizeof(float2);
-    // launch groups: 0 = direct rings without aliasing (n a power of two and
-    // n >= 2 lmax: the equatorial belt), 1 = the rest (Bluestein rings and
-    // small power-of-two rings); each launch gets the thread count and shared
-    // memory of its longest transform
+    // Launch buckets by transform length, each launch with M / 16 threads
+    // (one radix-16 butterfly per thread): Bluestein rings by their M, direct
+    // rings without aliasing (n >= 2 lmax) by n, aliased direct rings by 2n so
+    // that the south ring's folded spectrum fits in buf[n, 2n); buckets of
+    // length 1024 and below share one launch.
     std::vector<int> groups;
-    for (int g = 0; g < 2; ++g) {
-        p->ring_group_count[g] = 0;
-        p->ring_group_logm[g] = 0;
-        p->ring_group_qs[g] = 0;
-        p->ring_group_alias[g] = 0;
-        int nq = 0;
+    {
+        std::map<int, std::vector<int>, std::greater<int>> bucket;   // key -> ring pairs
+        std::map<int, int> keymax;
         for (int r = 0; r < p->npairs; ++r) {
             const RingFFT &f = p->h_rfft[r];
-            const int gr = (!f.blue && f.n >= 2 * p->lmax) ? 0 : 1;
-            if (gr != g) continue;
-            groups.push_back(r);
-            p->ring_group_count[g] += 1;
-            p->ring_group_logm[g] = std::max(p->ring_group_logm[g], f.logM);
-            if (f.n < 2 * p->lmax) {
-                p->ring_group_alias[g] = 1;
-                if (!f.blue) nq = std::max(nq, f.n);
-            }
+            const bool aliased = f.n < 2 * p->lmax;
+            const int slot = (f.blue || !aliased) ? f.logM : f.logM + 1;
+            const int key = std::max(slot, 10);
+            bucket[key].push_back(r);
+            keymax[key] = std::max(keymax.count(key) ? keymax[key] : 0, slot);
         }
-        // the south ring's folded spectrum of an aliased ring goes to buf[n, 2n)
-        // when the launch's buffer has room (always for Bluestein rings: M >= 2n)
-        if (2 * (int64_t)nq > ((int64_t)1 << p->ring_group_logm[g])) p->ring_group_qs[g] = nq;
+        p->ring_launch.clear();
+        for (auto &kv : bucket) {
+            Plan::RingLaunch g;
+            g.off = (int)groups.size();
+            g.count = (int)kv.second.size();
+            g.logm = keymax[kv.first];
+            g.alias = 0;
+            const int nt = ring_threads(g.logm);
+            for (int r : kv.second) {
+                const RingFFT &f = p->h_rfft[r];
+                groups.push_back(r);
+                if (f.n < 2 * p->lmax) g.alias = 1;
+                // the kernel's passes cover this ring: M / 16 butterflies per
+                // radix-16 pass, M / R in the first pass
+                const int M = 1 << f.logM, R = 1 << (f.logM & 3);
+                const bool ok = M <= 16 * nt && (R == 1 || M / R <= nt * ring_first_bpt(R, nt)) &&
+                                (f.n >= 2 * p->lmax || 2 * (int64_t)f.n <= ((int64_t)1 << g.logm));
+                if (!ok) {
+                    set_error("ring " + std::to_string(r) + ": transform length " + std::to_string(M) +
+                              " does not fit its launch bucket 2^" + std::to_string(g.logm));
+                    return SHTG_ERR_ARG;
+                }
+            }
+            p->ring_launch.push_back(g);
+        }
     }
     SHTG_TRY(dalloc(p, &p->d_ring_groups, groups.size()));
     SHTG_TRY(upload(p->d_ring_groups, groups));

@@ -20,15 +20,11 @@
 
 namespace shtg {
 
-// Threads per CTA: 256 for transforms of length <= 4096 (every radix-16
-// pass then has one butterfly per thread), 512 above; resident CTAs per SM
-// for the register budget (128 registers: the inlined passes do not spill,
-// which measured faster than more resident CTAs with spills).
-template <typename T, int NT> struct RingBlocks;
-template <> struct RingBlocks<float, 256> { static constexpr int v = 2; };
-template <> struct RingBlocks<float, 512> { static constexpr int v = 1; };
-template <> struct RingBlocks<double, 256> { static constexpr int v = 2; };
-template <> struct RingBlocks<double, 512> { static constexpr int v = 1; };
+// Threads per CTA: M / 16 for the launch's longest transform M (every
+// radix-16 pass then has one butterfly per thread), at least 64; resident
+// CTAs per SM for a budget of 128 registers a thread (the inlined passes do
+// not spill, which measured faster than more resident CTAs with spills).
+template <int NT> struct RingBlocks { static constexpr int v = 512 / NT; };
 
 __device__ __forceinline__ int rpad(int i) { return i + (i >> 4); }
 
@@ -159,7 +155,7 @@ template <typename C> struct TwTab {
 // butterflies; all reads finish (barrier) before any write, so the pass runs
 // in place.  With post != null the outputs are multiplied by post[index];
 // with cj they are conjugated (after the multiplication).
-template <int R, int BPT, int NT, typename C>
+template <int R, int BPT, int NT, bool TW, typename C>
 __device__ __forceinline__ void spass(C *buf, const int M, const int Ns, const TwTab<C> &tw,
                                       const C *__restrict__ post, const bool cj) {
     const int nb = M / R;
@@ -181,7 +177,7 @@ __device__ __forceinline__ void spass(C *buf, const int M, const int Ns, const T
         const int j = threadIdx.x + b * NT;
         if (j < nb) {
             const int k = j & (Ns - 1);
-            if (Ns > 1) {
+            if (TW && Ns > 1) {
                 // w^r = w^{4a} w^b (r = 4a + b): table values at r = 1, 2, 4, 8,
                 // products elsewhere (at most three roundings per twiddle)
                 const int t = k << lshift;
@@ -226,25 +222,27 @@ __device__ __forceinline__ void spass(C *buf, const int M, const int Ns, const T
 template <int NT, typename C>
 __device__ __forceinline__ void fft_stockham(C *buf, const int logM, const TwTab<C> tw,
                                           const C *__restrict__ post, const bool cj) {
+    // M <= 16 NT.  A radix-2, -4 or -8 pass (when log2 M is not a multiple of
+    // four) goes first, where it needs no twiddles (Ns = 1), with
+    // ring_first_bpt butterflies per thread (the plan checks that this covers
+    // M / R for every ring of the launch); the radix-16 passes follow with at
+    // most one butterfly per thread, the last of them applying post / cj.
     const int M = 1 << logM;
     int Ns = 1, rem = logM;
+    const int r0 = logM & 3;
+    if (r0 != 0) {
+        const bool last = rem == r0;
+        if (r0 == 3) spass<8, ring_first_bpt(8, NT), NT, false>(buf, M, 1, tw, last ? post : nullptr, last && cj);
+        else if (r0 == 2) spass<4, ring_first_bpt(4, NT), NT, false>(buf, M, 1, tw, last ? post : nullptr, last && cj);
+        else spass<2, ring_first_bpt(2, NT), NT, false>(buf, M, 1, tw, last ? post : nullptr, last && cj);
+        Ns = 1 << r0;
+        rem -= r0;
+    }
     while (rem > 0) {
-        if (rem >= 4) {
-            const bool last = rem == 4;
-            spass<16, 1, NT>(buf, M, Ns, tw, last ? post : nullptr, last && cj);   // M / 16 <= NT
-            Ns <<= 4;
-            rem -= 4;
-        } else if (rem == 3) {
-            spass<8, 1, NT>(buf, M, Ns, tw, post, cj);   // M / 8 <= NT for M <= 2^12
-            rem = 0;
-        } else if (rem == 2) {
-            spass<4, 1, NT>(buf, M, Ns, tw, post, cj);   // M <= 2^10
-            rem = 0;
-        } else {
-            if (NT >= 512 && M / 2 > NT) spass<2, (NT >= 512 ? 8 : 1), NT>(buf, M, Ns, tw, post, cj);   // M = 2^13
-            else spass<2, 1, NT>(buf, M, Ns, tw, post, cj);   // M / 2 <= NT (256 threads: M <= 4096)
-            rem = 0;
-        }
+        const bool last = rem == 4;
+        spass<16, 1, NT, true>(buf, M, Ns, tw, last ? post : nullptr, last && cj);
+        Ns <<= 4;
+        rem -= 4;
     }
 }
 
@@ -265,7 +263,6 @@ template <typename T> struct RingArgs {
     int nT;           // fused: rows [0, nT) use N^-1 component 0 (T), later rows component 1 (Q, U)
     int weighted;     // analysis: multiply by the quadrature weight
     int buf_len;      // shared transform buffer length (padded) of this launch
-    int qs_len;       // separate south-ring scratch of aliased direct rings (0: in buf)
     const int *pairs; // ring pairs handled by this launch (one CTA each)
 };
 
@@ -285,13 +282,12 @@ __device__ __forceinline__ void transform_dir(C *buf, const int logM, const TwTa
 // conjugated in the last pass, DFT again: buf then holds the conjugate of the
 // convolution.  The directions run in a loop, so the FFT is inlined once.
 template <typename T, int MODE, int NT>
-__global__ void __launch_bounds__(NT, RingBlocks<T, NT>::v) k_ring(const RingArgs<T> a) {
+__global__ void __launch_bounds__(NT, RingBlocks<NT>::v) k_ring(const RingArgs<T> a) {
     typedef typename VT<T>::C C;
     extern __shared__ __align__(16) unsigned char s_raw[];
     C *s_tw = reinterpret_cast<C *>(s_raw);
     C *buf = s_tw + a.tw_nlo + a.tw_nhi;
     C *scr_p = buf + a.buf_len;   // aliased fold: partial sums [north | south][NT]
-    C *scr_q = scr_p + 2 * NT;    // aliased direct rings without room in buf: Q_S / Y_S [n]
     for (int i = threadIdx.x; i < a.tw_nlo + a.tw_nhi; i += NT) s_tw[i] = a.tw[i];
     TwTab<C> tw;
     tw.lo = s_tw;
@@ -350,9 +346,9 @@ __global__ void __launch_bounds__(NT, RingBlocks<T, NT>::v) k_ring(const RingArg
             // small polar ring costs no more time than a long one.
             const C *Fn = a.FG + ((int64_t)q * a.nring + rn) * (L + 1);
             const C *Fs = a.FG + ((int64_t)q * a.nring + rs) * (L + 1);
-            // Q of the south ring: buf[n, 2n) when the launch's buffer has room
-            // (Bluestein rings: M >= 2n), else scratch
-            auto qsr = [&](int k) -> C & { return (f.blue || !a.qs_len) ? buf[rpad(n + k)] : scr_q[k]; };
+            // Q of the south ring in buf[n, 2n) (the launch's buffer holds 2n
+            // for every aliased ring; Bluestein rings: M >= 2n)
+            auto qsr = [&](int k) -> C & { return buf[rpad(n + k)]; };
             const int S = n <= NT / 2 ? NT / n : 1;
             if (S > 1) {
                 const int k = threadIdx.x % n, s = threadIdx.x / n;
@@ -515,7 +511,7 @@ __global__ void __launch_bounds__(NT, RingBlocks<T, NT>::v) k_ring(const RingArg
                 // aliased rings: Y_N(k), Y_S(k) for bins k and n - k from one
                 // thread (Y_N in place over buf, Y_S beside it), then every m
                 // written once, coalesced
-                auto ysr = [&](int k) -> C & { return (f.blue || !a.qs_len) ? buf[rpad(n + k)] : scr_q[k]; };
+                auto ysr = [&](int k) -> C & { return buf[rpad(n + k)]; };
                 for (int j = threadIdx.x; 2 * j <= n; j += NT) {
                     const int k1 = j, k2 = j ? n - j : 0;
                     C w1 = buf[rpad(k1)], w2 = buf[rpad(k2)];
@@ -587,6 +583,14 @@ template <> RingArgs<double> ring_args<double>(Plan *p) {
     return a;
 }
 
+template <typename T, int MODE, int NT>
+static int launch_ring_nt(const RingArgs<T> &a, int ctas, size_t smem, cudaStream_t st) {
+    auto kern = k_ring<T, MODE, NT>;
+    if (smem > 48 * 1024) SHTG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<ctas, NT, smem, st>>>(a);
+    return SHTG_OK;
+}
+
 template <typename T, int MODE>
 static int launch_ring(Plan *p, RingArgs<T> a, cudaStream_t st) {
     typedef typename VT<T>::C C;
@@ -601,32 +605,28 @@ static int launch_ring(Plan *p, RingArgs<T> a, cudaStream_t st) {
     a.tw_blo = p->tw_blo;
     a.tw_nlo = p->tw_nlo;
     a.tw_nhi = p->tw_nhi;
-    // alias-free direct ring pairs and the rest run as separate launches so that
-    // each gets the shared memory and thread count its transform length needs
+    // one launch per length bucket, each with the thread count and shared
+    // memory of its longest transform
     prof_begin(p, sizeof(T) == 8 ? K_RING64 : K_RING32, st);
-    for (int g = 0; g < 2; ++g) {
-        const int cnt = p->ring_group_count[g];
-        if (cnt == 0) continue;
-        const int M = 1 << p->ring_group_logm[g];
-        const int nt = M <= 4096 ? 256 : 512;
+    int nl = 0;
+    for (const Plan::RingLaunch &g : p->ring_launch) {
+        if (g.count == 0) continue;
+        const int M = 1 << g.logm;
+        const int nt = ring_threads(g.logm);
         a.buf_len = M + M / 16;
-        a.qs_len = p->ring_group_qs[g];
-        const size_t smem = sizeof(C) * ((size_t)p->tw_nlo + p->tw_nhi + a.buf_len +
-                                         (p->ring_group_alias[g] ? 2 * nt + a.qs_len : 0));
-        a.pairs = p->d_ring_groups + (g ? p->ring_group_count[0] : 0);
-        if (nt == 256) {
-            auto kern = k_ring<T, MODE, 256>;
-            if (smem > 48 * 1024)
-                SHTG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            kern<<<cnt, 256, smem, st>>>(a);
-        } else {
-            auto kern = k_ring<T, MODE, 512>;
-            if (smem > 48 * 1024)
-                SHTG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            kern<<<cnt, 512, smem, st>>>(a);
+        const size_t smem = sizeof(C) * ((size_t)p->tw_nlo + p->tw_nhi + a.buf_len + (g.alias ? 2 * nt : 0));
+        a.pairs = p->d_ring_groups + g.off;
+        int rc = SHTG_OK;
+        switch (nt) {
+            case 64: rc = launch_ring_nt<T, MODE, 64>(a, g.count, smem, st); break;
+            case 128: rc = launch_ring_nt<T, MODE, 128>(a, g.count, smem, st); break;
+            case 256: rc = launch_ring_nt<T, MODE, 256>(a, g.count, smem, st); break;
+            default: rc = launch_ring_nt<T, MODE, 512>(a, g.count, smem, st); break;
         }
+        if (rc != SHTG_OK) return rc;
+        ++nl;
     }
-    prof_end(p, st, (p->ring_group_count[0] > 0) + (p->ring_group_count[1] > 0));
+    prof_end(p, st, nl);
     SHTG_CHECK_LAUNCH("k_ring");
     return SHTG_OK;
 }

@@ -30,10 +30,26 @@ namespace shtg {
 // scalar slots per realization
 enum { S_RZ = 0, S_PQ, S_RR, S_BB, S_ALPHA, S_BETA, S_ACTIVE, S_ITERS, S_TOL2, S_BAD, S_SCALE };
 
-__device__ __forceinline__ double cdot(float2 a, float2 b) {
-    return (double)a.x * (double)b.x + (double)a.y * (double)b.y;
-}
 __device__ __forceinline__ double cdot(double2 a, double2 b) { return a.x * b.x + a.y * b.y; }
+
+// Per-element partial dot products.  FP32 vectors sum the component
+// products of one alm index (at most three complex terms) in FP32: one
+// rounding of ~2^-24 relative per element that does not grow with the
+// vector length; the caller adds the element's sum into an FP64
+// accumulator.  This keeps the reductions of the FP32 iteration to two FP64
+// operations per element (GB300's FP64 pipe is narrow).  FP64 vectors stay
+// in FP64 throughout.
+template <typename C> struct DotAcc;
+template <> struct DotAcc<float2> {
+    typedef float t;
+    static __device__ __forceinline__ float add(float acc, float2 a, float2 b) {
+        return fmaf(a.x, b.x, fmaf(a.y, b.y, acc));
+    }
+};
+template <> struct DotAcc<double2> {
+    typedef double t;
+    static __device__ __forceinline__ double add(double acc, double2 a, double2 b) { return acc + cdot(a, b); }
+};
 
 __device__ double block_sum(double v, double *sm) {
 #pragma unroll
@@ -219,9 +235,9 @@ __global__ void k_dot(const C *__restrict__ a, const C *__restrict__ c, int nc, 
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nalm;
          i += (int64_t)gridDim.x * blockDim.x) {
         const double w = mof[i] ? 2.0 : 1.0;
-        double t = 0.0;
-        for (int k = 0; k < nc; ++k) t += cdot(a[off + k * nalm + i], c[off + k * nalm + i]);
-        s += w * t;
+        typename DotAcc<C>::t t = 0;
+        for (int k = 0; k < nc; ++k) t = DotAcc<C>::add(t, a[off + k * nalm + i], c[off + k * nalm + i]);
+        s += w * (double)t;
     }
     s = block_sum(s, sm);
     if (threadIdx.x == 0) part[((int64_t)b * nslot + slot) * RB + blockIdx.x] = s;
@@ -286,14 +302,14 @@ __global__ void k_update(typename HT<T>::C *__restrict__ x, typename HT<T>::C *_
         }
         apply_minv<T, C>(minv + (int64_t)b * 4 * nalm, nalm, i, nc, rv, zv);
         const double w = mof[i] ? 2.0 : 1.0;
-        double a1 = 0.0, a2 = 0.0;
+        typename DotAcc<C>::t a1 = 0, a2 = 0;
         for (int k = 0; k < nc; ++k) {
             z[off + k * nalm + i] = zv[k];
-            a1 += cdot(rv[k], zv[k]);
-            a2 += cdot(rv[k], rv[k]);
+            a1 = DotAcc<C>::add(a1, rv[k], zv[k]);
+            a2 = DotAcc<C>::add(a2, rv[k], rv[k]);
         }
-        srz += w * a1;
-        srr += w * a2;
+        srz += w * (double)a1;
+        srr += w * (double)a2;
     }
     srz = block_sum(srz, sm);
     srr = block_sum(srr, sm);
