@@ -64,6 +64,9 @@ extern "C" {
 
 #define SHTG_FP64 0
 #define SHTG_FP32 1
+#define SHTG_DF64 3                  /* FP64 buffers; Legendre sums of alm2map, alm2map_adjoint and
+                                        alm2map_vjp in double-FP32 arithmetic (SHTG_ARITH_DF64);
+                                        map2alm runs the FP64 path */
 #define SHTG_TC32 2                  /* FP32 buffers; Legendre sums of alm2map, alm2map_adjoint
                                         and alm2map_vjp on the tensor cores (FP32 recurrence,
                                         bf16 hi/lo split products, FP32 accumulation: ~2^-16
@@ -78,6 +81,12 @@ extern "C" {
 #define SHTG_CG_MIXED 1              /* FP32 PCG inside FP64 iterative refinement */
 #define SHTG_CG_MIXED_TC 2           /* as SHTG_CG_MIXED with the FP32 operator's Legendre
                                         sums on the tensor cores (SHTG_TC32) */
+
+#define SHTG_ARITH_DEFAULT 0         /* shtg_cg_opts.fp64_arith */
+#define SHTG_ARITH_FP64 1            /* native FP64 multiply-adds */
+#define SHTG_ARITH_DF64 2            /* double-FP32 (hi + lo float pairs, ~2^-47 relative per
+                                        operation) on the FP32 pipe, FP64 storage; same results
+                                        as SHTG_ARITH_FP64 to ~1e-13 relative */
 
 #define SHTG_HOST_INPUTS 1           /* cg_sample flag: problem maps/alm and output are host pointers */
 #define SHTG_PROFILE 2               /* cg_sample flag: time kernel classes with CUDA events */
@@ -180,7 +189,10 @@ typedef struct {
     int precond;        /* 1: diagonal preconditioner of Sect. 4 (default); 0: none */
     double reliable_delta; /* mixed mode: an FP64 residual replacement happens when the FP32
                               residual has dropped by this factor since the last one (default 1e-2) */
-    int reserved;       /* set to 0 */
+    int fp64_arith;     /* arithmetic of the FP64-accurate steps (RHS, residual replacements,
+                           the whole FP64 PCG): SHTG_ARITH_DEFAULT (0: double-FP32 in the mixed
+                           modes, native FP64 in SHTG_CG_FP64), SHTG_ARITH_FP64 or
+                           SHTG_ARITH_DF64 */
     int check_every;    /* iterations per CUDA graph launch between host convergence checks */
     int flags;          /* SHTG_HOST_INPUTS: ninv, d, w1, w2 and alm_out are host memory */
 } shtg_cg_opts;

@@ -14,7 +14,8 @@ ERRORS = {-1: "SHTG_ERR_ARG", -2: "SHTG_ERR_CUDA", -3: "SHTG_ERR_NOT_CONVERGED",
           -4: "SHTG_ERR_TIMEOUT", -5: "SHTG_ERR_NONFINITE", -6: "SHTG_ERR_NOT_SPD",
           -7: "SHTG_ERR_NOMEM"}
 GEOM_HEALPIX, GEOM_GAUSS = 0, 1
-FP64, FP32, TC32 = 0, 1, 2
+FP64, FP32, TC32, DF64 = 0, 1, 2, 3
+ARITH_DEFAULT, ARITH_FP64, ARITH_DF64 = 0, 1, 2
 SPIN0, SPIN2 = 1, 2
 CG_FP64, CG_MIXED, CG_MIXED_TC = 0, 1, 2
 HOST_INPUTS = 1
@@ -44,7 +45,7 @@ class Problem(C.Structure):
 
 class CGOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxiter", C.c_int), ("mode", C.c_int),
-                ("precond", C.c_int), ("reliable_delta", C.c_double), ("reserved", C.c_int),
+                ("precond", C.c_int), ("reliable_delta", C.c_double), ("fp64_arith", C.c_int),
                 ("check_every", C.c_int), ("flags", C.c_int)]
 
 

@@ -21,12 +21,25 @@ _PREC = {torch.complex128: N.FP64, torch.float64: N.FP64,
          torch.complex64: N.FP32, torch.float32: N.FP32}
 
 
-def _prec(dtype, tensor_cores: bool) -> int:
+def _prec(dtype, tensor_cores: bool, double_float: bool = False) -> int:
+    if double_float:
+        if tensor_cores or dtype not in (torch.complex128, torch.float64):
+            raise ValueError("double_float needs complex128 alm / float64 maps (and no tensor_cores)")
+        return N.DF64
     if not tensor_cores:
         return _PREC[dtype]
     if dtype not in (torch.complex64, torch.float32):
         raise ValueError("tensor_cores needs complex64 alm / float32 maps")
     return N.TC32
+
+
+_ARITH = {"default": N.ARITH_DEFAULT, "fp64": N.ARITH_FP64, "df64": N.ARITH_DF64}
+
+
+def _arith(fp64_arith: str) -> int:
+    if fp64_arith not in _ARITH:
+        raise ValueError(f"fp64_arith must be one of {sorted(_ARITH)}")
+    return _ARITH[fp64_arith]
 
 
 def _stream():
@@ -95,39 +108,45 @@ class Plan:
             raise ValueError(f"expected trailing shape {'(2, ' if spin == 2 else '('}{inner})")
         return lead, nb
 
-    def alm2map(self, alm: torch.Tensor, spin: int = 0, tensor_cores: bool = False) -> torch.Tensor:
+    def alm2map(self, alm: torch.Tensor, spin: int = 0, tensor_cores: bool = False,
+                double_float: bool = False) -> torch.Tensor:
         """Y: alm [..., nalm] (spin 0) or [..., 2, nalm] (E, B) -> maps.
         tensor_cores (complex64 only): Legendre sum on the tensor cores
-        (bf16 hi/lo split products, FP32 accumulation)."""
+        (bf16 hi/lo split products, FP32 accumulation).  double_float
+        (complex128 only): FP64-accurate Legendre sum in double-FP32
+        arithmetic on the FP32 pipe."""
         _need_cuda(alm, "alm")
         lead, nb = self._batched(alm, spin, self.nalm)
         real = torch.float64 if alm.dtype == torch.complex128 else torch.float32
         out = torch.empty(*lead, *((2,) if spin == 2 else ()), self.npix, dtype=real,
                           device=alm.device)
-        N.check(self._lib.shtg_alm2map(self._h, spin, _prec(alm.dtype, tensor_cores), _ptr(alm), _ptr(out),
+        N.check(self._lib.shtg_alm2map(self._h, spin, _prec(alm.dtype, tensor_cores, double_float), _ptr(alm), _ptr(out),
                                        nb, _stream()))
         return out
 
-    def alm2map_adjoint(self, m: torch.Tensor, spin: int = 0, tensor_cores: bool = False) -> torch.Tensor:
+    def alm2map_adjoint(self, m: torch.Tensor, spin: int = 0, tensor_cores: bool = False,
+                        double_float: bool = False) -> torch.Tensor:
         """Y^T (exact transpose, no pixel weights): maps -> alm.  tensor_cores
-        (float32 only): Legendre sum on the tensor cores."""
+        (float32 only): Legendre sum on the tensor cores; double_float
+        (float64 only): in double-FP32 arithmetic."""
         _need_cuda(m, "map")
         lead, nb = self._batched(m, spin, self.npix)
         cplx = torch.complex128 if m.dtype == torch.float64 else torch.complex64
         out = torch.empty(*lead, *((2,) if spin == 2 else ()), self.nalm, dtype=cplx,
                           device=m.device)
-        N.check(self._lib.shtg_alm2map_adjoint(self._h, spin, _prec(m.dtype, tensor_cores), _ptr(m),
+        N.check(self._lib.shtg_alm2map_adjoint(self._h, spin, _prec(m.dtype, tensor_cores, double_float), _ptr(m),
                                                _ptr(out), nb, _stream()))
         return out
 
-    def alm2map_vjp(self, g: torch.Tensor, spin: int = 0, tensor_cores: bool = False) -> torch.Tensor:
+    def alm2map_vjp(self, g: torch.Tensor, spin: int = 0, tensor_cores: bool = False,
+                    double_float: bool = False) -> torch.Tensor:
         """Gradient of a real loss w.r.t. alm (torch convention) from dL/dmap."""
         _need_cuda(g, "map_grad")
         lead, nb = self._batched(g, spin, self.npix)
         cplx = torch.complex128 if g.dtype == torch.float64 else torch.complex64
         out = torch.empty(*lead, *((2,) if spin == 2 else ()), self.nalm, dtype=cplx,
                           device=g.device)
-        N.check(self._lib.shtg_alm2map_vjp(self._h, spin, _prec(g.dtype, tensor_cores), _ptr(g), _ptr(out),
+        N.check(self._lib.shtg_alm2map_vjp(self._h, spin, _prec(g.dtype, tensor_cores, double_float), _ptr(g), _ptr(out),
                                            nb, _stream()))
         return out
 
@@ -169,10 +188,14 @@ class Plan:
                   maxiter: int = 4000, precond: bool = True, reliable_delta: float = 1e-2,
                   check_every: int = 4, out=None,
                   allow_not_converged: bool = False, profile: bool = False, graphs: bool = True,
-                  cl_scale=None):
+                  cl_scale=None, fp64_arith: str = "default"):
         """Constrained realization(s) of Eq. (mapmakingeq).
 
         cl_scale: optional [nbatch] amplitudes; realization b uses cl_scale[b] x cl.
+
+        fp64_arith: arithmetic of the FP64-accurate steps (RHS, residual
+        replacements; the whole solve in mode "fp64"): "default" (double-FP32
+        in the mixed modes, native FP64 in mode "fp64"), "fp64" or "df64".
 
         graphs: replay one captured PCG iteration as a CUDA graph between the
         convergence checks (same results as eager launches; off while profiling).
@@ -202,7 +225,7 @@ class Plan:
             raise ValueError(f"mode must be one of {sorted(modes)}")
         o.mode = modes[mode]
         o.precond = 1 if precond else 0
-        o.reliable_delta, o.reserved = float(reliable_delta), 0
+        o.reliable_delta, o.fp64_arith = float(reliable_delta), _arith(fp64_arith)
         o.check_every = int(check_every)
         o.flags = (N.HOST_INPUTS if host else 0) | (N.PROFILE if profile else 0) | (0 if graphs else N.NO_GRAPHS)
         st = N.CGStats()
@@ -241,7 +264,7 @@ class Plan:
 
 def chains_sample(groups, tol: float = 1e-6, mode: str = "mixed_tc", maxiter: int = 4000,
                   precond: bool = True, reliable_delta: float = 1e-2, check_every: int = 4,
-                  allow_not_converged: bool = False, graphs: bool = True):
+                  allow_not_converged: bool = False, graphs: bool = True, fp64_arith: str = "default"):
     """Constrained realizations of many chains of uneven geometry in one call.
 
     groups: list of dicts, one per geometry, with keys plan, cl, bl, ninv, d,
@@ -277,7 +300,7 @@ def chains_sample(groups, tol: float = 1e-6, mode: str = "mixed_tc", maxiter: in
         raise ValueError(f"mode must be one of {sorted(modes)}")
     o.mode = modes[mode]
     o.precond = 1 if precond else 0
-    o.reliable_delta, o.reserved = float(reliable_delta), 0
+    o.reliable_delta, o.fp64_arith = float(reliable_delta), _arith(fp64_arith)
     o.check_every = int(check_every)
     o.flags = 0 if graphs else N.NO_GRAPHS
     rc = lib.shtg_cg_sample_chains(n, plans, probs, outs, C.byref(o), stats, _stream())

@@ -61,6 +61,21 @@ int transform_adjoint(Plan *p, int spin, const void *map, void *alm, int nbatch,
     SHTG_TRY(leg_analysis<T>(p, spin, G, nbatch, nullptr, (C *)alm, rs, st, vjp));
     return SHTG_OK;
 }
+// Y and Y^T on FP64 buffers with the Legendre sums in double-FP32 arithmetic
+static int transform_synth_df(Plan *p, int spin, const void *alm, void *map, int nbatch, cudaStream_t st) {
+    const int rs = spin == 2 ? 2 : 1;
+    SHTG_TRY(leg_synth_df(p, spin, (const double2 *)alm, rs, nbatch, nullptr, p->d_phase64, st));
+    SHTG_TRY(ring_synth<double>(p, p->d_phase64, nbatch * rs, (double *)map, st));
+    return SHTG_OK;
+}
+static int transform_adjoint_df(Plan *p, int spin, const void *map, void *alm, int nbatch, cudaStream_t st,
+                                int vjp) {
+    const int rs = spin == 2 ? 2 : 1;
+    SHTG_TRY(ring_analysis<double>(p, (const double *)map, nbatch * rs, 0, p->d_phase64, st));
+    SHTG_TRY(leg_analysis_df(p, spin, p->d_phase64, nbatch, nullptr, (double2 *)alm, rs, st, vjp));
+    return SHTG_OK;
+}
+
 template int transform_synth<float>(Plan *, int, const void *, void *, int, cudaStream_t);
 template int transform_synth<double>(Plan *, int, const void *, void *, int, cudaStream_t);
 template int transform_adjoint<float>(Plan *, int, const void *, void *, int, int, cudaStream_t, int);
@@ -81,8 +96,8 @@ static int check_transform(const shtg_plan *plan, int spin, int precision, const
         set_error("spin-2 transform on a plan created without SHTG_SPIN2");
         return SHTG_ERR_ARG;
     }
-    if (precision != SHTG_FP64 && precision != SHTG_FP32 && precision != SHTG_TC32) {
-        set_error("precision must be SHTG_FP64, SHTG_FP32 or SHTG_TC32");
+    if (precision != SHTG_FP64 && precision != SHTG_FP32 && precision != SHTG_TC32 && precision != SHTG_DF64) {
+        set_error("precision must be SHTG_FP64, SHTG_FP32, SHTG_TC32 or SHTG_DF64");
         return SHTG_ERR_ARG;
     }
     if (!a || !b) {
@@ -114,6 +129,7 @@ static int transform_adjoint_tc(Plan *p, int spin, const void *map, void *alm, i
 int alm2map_vjp(Plan *p, int spin, int precision, const void *g, void *out, int nbatch,
                 cudaStream_t st) {
     if (precision == SHTG_FP64) return transform_adjoint<double>(p, spin, g, out, nbatch, 0, st, 1);
+    if (precision == SHTG_DF64) return transform_adjoint_df(p, spin, g, out, nbatch, st, 1);
     if (precision == SHTG_TC32) return transform_adjoint_tc(p, spin, g, out, nbatch, st, 1);
     return transform_adjoint<float>(p, spin, g, out, nbatch, 0, st, 1);
 }
@@ -238,6 +254,7 @@ int shtg_alm2map(shtg_plan *plan, int spin, int precision, const void *alm, void
     Plan *p = reinterpret_cast<Plan *>(plan);
     cudaStream_t st = (cudaStream_t)stream;
     if (precision == SHTG_FP64) return transform_synth<double>(p, spin, alm, map, nbatch, st);
+    if (precision == SHTG_DF64) return transform_synth_df(p, spin, alm, map, nbatch, st);
     if (precision == SHTG_TC32) {
         float2 *F = p->d_phase32;
         const int rs = spin == 2 ? 2 : 1;
@@ -254,6 +271,7 @@ int shtg_alm2map_adjoint(shtg_plan *plan, int spin, int precision, const void *m
     Plan *p = reinterpret_cast<Plan *>(plan);
     cudaStream_t st = (cudaStream_t)stream;
     if (precision == SHTG_FP64) return transform_adjoint<double>(p, spin, map, alm, nbatch, 0, st);
+    if (precision == SHTG_DF64) return transform_adjoint_df(p, spin, map, alm, nbatch, st, 0);
     if (precision == SHTG_TC32) return transform_adjoint_tc(p, spin, map, alm, nbatch, st, 0);
     return transform_adjoint<float>(p, spin, map, alm, nbatch, 0, st);
 }
@@ -274,7 +292,7 @@ int shtg_map2alm(shtg_plan *plan, int spin, int precision, const void *map, void
         return SHTG_ERR_ARG;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    if (precision == SHTG_FP64) return map2alm_t<double>(p, spin, map, alm, nbatch, niter, st);
+    if (precision == SHTG_FP64 || precision == SHTG_DF64) return map2alm_t<double>(p, spin, map, alm, nbatch, niter, st);
     return map2alm_t<float>(p, spin, map, alm, nbatch, niter, st);
 }
 

@@ -245,6 +245,12 @@ int build_tile_states(Plan *p);
 int leg_analysis_g64(Plan *p, int spin, const double2 *G, int nmaps, const double *beam, double2 *alm, int rs,
                      cudaStream_t st, int vjp);
 int build_tile_states64(Plan *p);
+// FP64-accurate Legendre sums in double-FP32 arithmetic on FP64 buffers
+// (legendre_df.cu); the transpose reads the FP64 tile states above
+int leg_synth_df(Plan *p, int spin, const double2 *alm, int rs, int nmaps, const double *beam, double2 *F,
+                 cudaStream_t st);
+int leg_analysis_df(Plan *p, int spin, const double2 *G, int nmaps, const double *beam, double2 *alm, int rs,
+                    cudaStream_t st, int vjp);
 
 // ringfft.cu
 // mode 0: F -> map (synthesis); mode 1: map -> G (adjoint, wmode 1 = quadrature weights);

@@ -1012,8 +1012,9 @@ int launch_analysis_tc(Plan *p, const float2 *G, int nmaps, const float *beam, f
 // Shapes tried by the autotuner (key kind 2): synthesis (stages, staged l)
 // = (1, 64) [four CTAs per SM at spin 2], (2, 128), (1, 128); transpose
 // (A buffers, B buffers, 256-l tiles) = (1, 1, 1) [four CTAs per SM],
-// (2, 2, 2), (1, 2, 1), (2, 2, 1).  Every shape sums the same products in the
-// same order, so the choice does not change a bit of the result.
+// (2, 2, 2), (1, 2, 1), (2, 2, 1), (1, 2, 2), (1, 1, 2) [three CTAs per SM].
+// Every shape sums the same products in the same order, so the choice does
+// not change a bit of the result.
 int leg_synth_tc(Plan *p, int spin, const float2 *alm, int rs, int nmaps, const float *beam, float2 *F,
                  cudaStream_t st) {
     return tune(p, 2, spin == 2 ? 1 : 0, nmaps, 3, st, [&](int v) {
@@ -1028,19 +1029,24 @@ int leg_synth_tc(Plan *p, int spin, const float2 *alm, int rs, int nmaps, const 
     });
 }
 
+template <int SPIN>
+static int analysis_tc_shape(int v, Plan *p, const float2 *G, int nmaps, const float *beam, float2 *alm, int rs,
+                             cudaStream_t st, int vjp) {
+    switch (v) {
+        case 1: return launch_analysis_tc<SPIN, 2, 2, 2>(p, G, nmaps, beam, alm, rs, st, vjp);
+        case 2: return launch_analysis_tc<SPIN, 1, 2, 1>(p, G, nmaps, beam, alm, rs, st, vjp);
+        case 3: return launch_analysis_tc<SPIN, 2, 2, 1>(p, G, nmaps, beam, alm, rs, st, vjp);
+        case 4: return launch_analysis_tc<SPIN, 1, 2, 2>(p, G, nmaps, beam, alm, rs, st, vjp);
+        case 5: return launch_analysis_tc<SPIN, 1, 1, 2>(p, G, nmaps, beam, alm, rs, st, vjp);
+        default: return launch_analysis_tc<SPIN, 1, 1, 1>(p, G, nmaps, beam, alm, rs, st, vjp);
+    }
+}
+
 int leg_analysis_tc(Plan *p, int spin, const float2 *G, int nmaps, const float *beam, float2 *alm, int rs,
                     cudaStream_t st, int vjp) {
-    return tune(p, 2, spin == 2 ? 3 : 2, nmaps, 4, st, [&](int v) {
-        if (spin == 2) {
-            if (v == 1) return launch_analysis_tc<2, 2, 2, 2>(p, G, nmaps, beam, alm, rs, st, vjp);
-            if (v == 2) return launch_analysis_tc<2, 1, 2, 1>(p, G, nmaps, beam, alm, rs, st, vjp);
-            if (v == 3) return launch_analysis_tc<2, 2, 2, 1>(p, G, nmaps, beam, alm, rs, st, vjp);
-            return launch_analysis_tc<2, 1, 1, 1>(p, G, nmaps, beam, alm, rs, st, vjp);
-        }
-        if (v == 1) return launch_analysis_tc<0, 2, 2, 2>(p, G, nmaps, beam, alm, rs, st, vjp);
-        if (v == 2) return launch_analysis_tc<0, 1, 2, 1>(p, G, nmaps, beam, alm, rs, st, vjp);
-        if (v == 3) return launch_analysis_tc<0, 2, 2, 1>(p, G, nmaps, beam, alm, rs, st, vjp);
-        return launch_analysis_tc<0, 1, 1, 1>(p, G, nmaps, beam, alm, rs, st, vjp);
+    return tune(p, 2, spin == 2 ? 3 : 2, nmaps, 6, st, [&](int v) {
+        if (spin == 2) return analysis_tc_shape<2>(v, p, G, nmaps, beam, alm, rs, st, vjp);
+        return analysis_tc_shape<0>(v, p, G, nmaps, beam, alm, rs, st, vjp);
     });
 }
 

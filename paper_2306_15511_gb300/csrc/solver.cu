@@ -533,6 +533,7 @@ struct Solve {
     cudaStream_t st;
     int nb, nc;
     int tc = 0;      // FP32 operator: Legendre sums on the tensor cores
+    int df = 0;      // FP64 operator: Legendre sums in double-FP32 arithmetic
     int graphs = 1;  // replay captured iterations (off while profiling)
     int64_t nalm, per, nvec;
     dim3 vgrid;   // (blocks, nb)
@@ -572,8 +573,10 @@ template <> struct Vec<float> {
     static float2 *phase(Plan *p) { return p->d_phase32; }
 };
 
-// Legendre synthesis of the operator: FP64, FP32 or (s.tc) tensor-core FP32
+// Legendre synthesis of the operator: FP64 (s.df: double-FP32), FP32 or
+// (s.tc) tensor-core FP32
 static int op_synth(Solve &s, int spin, const double2 *x, int rs, const double *beam, double2 *F) {
+    if (s.df) return leg_synth_df(s.p, spin, x, rs, s.nb, beam, F, s.st);
     return leg_synth<double>(s.p, spin, x, rs, s.nb, beam, F, s.st);
 }
 static int op_synth(Solve &s, int spin, const float2 *x, int rs, const float *beam, float2 *F) {
@@ -581,8 +584,10 @@ static int op_synth(Solve &s, int spin, const float2 *x, int rs, const float *be
     return leg_synth<float>(s.p, spin, x, rs, s.nb, beam, F, s.st);
 }
 
-// Legendre transpose of the operator: FP64, FP32 or (s.tc) tensor-core FP32
+// Legendre transpose of the operator: FP64 (s.df: double-FP32), FP32 or
+// (s.tc) tensor-core FP32
 static int op_analysis(Solve &s, int spin, const double2 *G, const double *beam, double2 *y, int rs) {
+    if (s.df) return leg_analysis_df(s.p, spin, G, s.nb, beam, y, rs, s.st, 0);
     return leg_analysis<double>(s.p, spin, G, s.nb, beam, y, rs, s.st);
 }
 static int op_analysis(Solve &s, int spin, const float2 *G, const float *beam, float2 *y, int rs) {
@@ -1030,6 +1035,11 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
         set_error("mode must be SHTG_CG_FP64, SHTG_CG_MIXED or SHTG_CG_MIXED_TC");
         return SHTG_ERR_ARG;
     }
+    if (opt.fp64_arith != SHTG_ARITH_DEFAULT && opt.fp64_arith != SHTG_ARITH_FP64 &&
+        opt.fp64_arith != SHTG_ARITH_DF64) {
+        set_error("fp64_arith must be SHTG_ARITH_DEFAULT, SHTG_ARITH_FP64 or SHTG_ARITH_DF64");
+        return SHTG_ERR_ARG;
+    }
     const int host = (opt.flags & SHTG_HOST_INPUTS) ? 1 : 0;
     if (!pr->d || !pr->w1 || !pr->w2 || !alm_out) {
         set_error("d, w1, w2 and alm_out are required");
@@ -1045,6 +1055,7 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
     const int nb = pr->nbatch, nc = pr->ncomp;
     Solve s = make_solve(p, nb, nc, st);
     s.tc = opt.mode == SHTG_CG_MIXED_TC;
+    s.df = opt.fp64_arith == SHTG_ARITH_DF64 || (opt.fp64_arith == SHTG_ARITH_DEFAULT && opt.mode != SHTG_CG_FP64);
     {
         const char *e = getenv("SHTG_GRAPHS");
         s.graphs = !(opt.flags & SHTG_NO_GRAPHS) && !(e && e[0] == '0');
@@ -1069,9 +1080,8 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
     {
         const int64_t rowsz = (int64_t)(p->lmax + 1) * p->nring;
         SHTG_TRY(ring_analysis<double>(p, p->d_map64, nb * nc, 0, p->d_phase64, st));
-        SHTG_TRY(leg_analysis<double>(p, 0, p->d_phase64, nb, p->d_ltab64, B, nc, st));
-        if (nc == 3)
-            SHTG_TRY(leg_analysis<double>(p, 2, p->d_phase64 + nb * rowsz, nb, p->d_ltab64, B + p->nalm, 3, st));
+        SHTG_TRY(op_analysis(s, 0, p->d_phase64, p->d_ltab64, B, nc));
+        if (nc == 3) SHTG_TRY(op_analysis(s, 2, p->d_phase64 + nb * rowsz, p->d_ltab64, B + p->nalm, 3));
         const double2 *w1 = reinterpret_cast<const double2 *>(pr->w1);
         if (host) {
             SHTG_CUDA(cudaMemcpyAsync(Tt, pr->w1, sizeof(double2) * (size_t)s.nvec, cudaMemcpyHostToDevice, st));

@@ -54,3 +54,24 @@ def test_chains_rejects_bad_arguments_without_gpu():
     rc = lib.shtg_cg_sample_chains(2, plans, probs, outs, None, None, None)
     assert rc == -1
     assert b"own plan" in lib.shtg_last_error_string()
+
+
+def test_binding_constants_match_header():
+    """Every #define the binding mirrors has the header's value, and the
+    option struct keeps the header's field order."""
+    from paper_2306_15511_gb300 import _native as N
+    src = open(os.path.join(ROOT, "include", "shtg.h")).read()
+    defs = {k: int(v) for k, v in re.findall(r"#define\s+(SHTG_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", src)}
+    pairs = {"FP64": "SHTG_FP64", "FP32": "SHTG_FP32", "TC32": "SHTG_TC32", "DF64": "SHTG_DF64",
+             "ARITH_DEFAULT": "SHTG_ARITH_DEFAULT", "ARITH_FP64": "SHTG_ARITH_FP64",
+             "ARITH_DF64": "SHTG_ARITH_DF64", "CG_FP64": "SHTG_CG_FP64", "CG_MIXED": "SHTG_CG_MIXED",
+             "CG_MIXED_TC": "SHTG_CG_MIXED_TC", "HOST_INPUTS": "SHTG_HOST_INPUTS",
+             "PROFILE": "SHTG_PROFILE", "NO_GRAPHS": "SHTG_NO_GRAPHS", "SPIN0": "SHTG_SPIN0",
+             "SPIN2": "SHTG_SPIN2"}
+    for py, c in pairs.items():
+        assert getattr(N, py) == defs[c], (py, c)
+    end = src.index("} shtg_cg_opts;")
+    body = src[src.rindex("typedef struct {", 0, end):end]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    fields = re.findall(r"\b(?:int|double)\s+(\w+)\s*;", body)
+    assert fields == [f for f, _ in N.CGOpts._fields_]
