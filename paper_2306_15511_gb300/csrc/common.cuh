@@ -67,6 +67,9 @@ __host__ __device__ constexpr int ring_first_bpt(int R, int nt) {
     return nt >= 512 ? (R == 2 ? 8 : 1) : nt == 256 ? 1 : nt == 128 ? (R == 2 ? 1 : 2) : (R == 8 ? 1 : 4);
 }
 
+// l stride of the FP64 recurrence tile states
+#define SHTG_TS64 32
+
 // Kernel classes timed live with CUDA events (on the launching stream) when
 // profiling is on; see shtg_cg_stats.kernel_ms.
 enum KClass { K_LEG_SYN32 = 0, K_LEG_ANA32, K_RING32, K_LEG_SYN64, K_LEG_ANA64, K_RING64, K_VEC, K_DIAG };
@@ -167,6 +170,11 @@ struct Plan {
     int *d_flag = nullptr;         // [0]: set by a kernel whose bounded device wait expired
     cudaStream_t cap_stream = nullptr;   // non-blocking stream on which solver iterations are captured
     cudaStream_t work_stream = nullptr;  // non-blocking stream of this plan's solve in a chains call
+    // ring-stage launch buckets after the first run on side streams, forked
+    // from and joined back into the caller's stream with events
+    static constexpr int RING_SIDE = 4;
+    cudaStream_t ring_side[RING_SIDE] = {};
+    cudaEvent_t ring_fork = nullptr, ring_join[RING_SIDE] = {};
     // FP32 recurrence states every 32 l (tensor-core transpose): entry
     // (m, t, pair) at (d_toff[m] + t) * npairs + pair is the state before
     // l = m + 32 t: (lambda_{l-1}, lambda_{l-2}) for spin 0, (y+_{l-1},
@@ -174,8 +182,9 @@ struct Plan {
     int64_t *d_toff = nullptr;
     float2 *d_tst0 = nullptr;
     float4 *d_tst2 = nullptr;
-    // the same in FP64 every 128 l (FP64 transpose), [m][t][pair] at (d_toff128[m] + t) * npairs + pair
-    int64_t *d_toff128 = nullptr;
+    // the same in FP64 every SHTG_TS64 l (FP64 and double-FP32 transposes),
+    // [m][t][pair] at (d_toff64[m] + t) * npairs + pair
+    int64_t *d_toff64 = nullptr;
     double2 *d_tst64_0 = nullptr;
     double4_32a *d_tst64_2 = nullptr;
     double *d_lsum = nullptr;      // [lmax+1] per-l sums (log-posterior)

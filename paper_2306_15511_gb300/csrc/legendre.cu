@@ -38,7 +38,7 @@ template <> LegArgs<double> leg_make_args<double>(Plan *p) {
     a.ls2 = p->d_ls2_64;
     a.st2 = p->d_st2_64;
     a.u = p->d_u64;
-    a.toff128 = p->d_toff128;
+    a.toff64 = p->d_toff64;
     a.tst64_0 = p->d_tst64_0;
     a.tst64_2 = p->d_tst64_2;
     return a;

@@ -16,8 +16,8 @@
 // Synthesis: one thread per ring pair (NR of them) and NM maps, as the
 // CUDA-core kernels, the recurrence in registers.  Transpose: the
 // register-blocked contraction of the FP64 transpose (legendre_g64.cu) with
-// stages of 32 ring pairs, whose recurrences restart every 128 l from the
-// plan's FP64 tile states.
+// stages of 32 ring pairs, whose recurrences all four warps generate in
+// 32-l segments from the plan's FP64 tile states (every SHTG_TS64 l).
 #include "df.cuh"
 #include "legendre_kernels.cuh"
 
@@ -308,8 +308,8 @@ __global__ void __launch_bounds__(LEG_THREADS) k_leg_synth_df(const LegArgs<doub
 }
 
 // =========================================================== transpose
-constexpr int D_LR = 128;   // l per CTA (rows); the FP64 tile states are every 128 l
-constexpr int D_KP = 32;    // ring pairs per stage (one generator warp)
+constexpr int D_LR = 128;   // l per CTA (rows): four 32-l segments, one per warp
+constexpr int D_KP = 32;    // ring pairs per stage (a warp's lanes)
 constexpr int D_NT = 128;   // threads
 constexpr int D_NMT = 8;    // maps per CTA (grid.z covers more)
 constexpr int D_LS = D_KP + 1;   // row stride of the value tile (odd: rows in distinct banks)
@@ -386,15 +386,18 @@ __global__ void __launch_bounds__(D_NT) k_leg_analysis_df(const LegArgs<double> 
 
     for (int s = s0; s < nps; ++s) {
         __syncthreads();   // the previous stage's tiles are consumed
-        if (tid < D_KP) {
-            // ---- recurrence of pair s * 32 + tid over the 128 rows, from the
-            // FP64 state tabulated at l = lbase
-            const int pr = s * D_KP + tid;
+        {
+            // ---- recurrences of the stage's 32 ring pairs: warp w runs rows
+            // 32 w .. 32 w + 31 of pair s * 32 + lane from the FP64 state
+            // tabulated at l0 = lbase + 32 w
+            const int pp = tid & 31, seg = tid >> 5;
+            const int pr = s * D_KP + pp;
+            const int l0 = lbase + 32 * seg;
             DfPair<1> S;
             df_pair_load<1, SPIN>(a, m, pr, S, 0);
-            const bool live = pr < a.npairs;
+            const bool live = pr < a.npairs && l0 <= L;
             if (live) {
-                const int64_t e = (a.toff128[m] + (lbase - m) / D_LR) * a.npairs + pr;
+                const int64_t e = (a.toff64[m] + (l0 - m) / SHTG_TS64) * a.npairs + pr;
                 if (SPIN == 2) {
                     const double4_32a t4 = a.tst64_2[e];
                     S.a1[0] = df_from(t4.x);
@@ -407,10 +410,10 @@ __global__ void __launch_bounds__(D_NT) k_leg_analysis_df(const LegArgs<double> 
                     S.a2[0] = df_from(t2.y);
                 }
             }
-            // injection steps only if some pair of the warp starts in this range
-            const bool inj = __any_sync(0xffffffffu, live && ((S.ls[0] >= lbase && S.ls[0] <= lend) ||
-                                                              (SPIN == 2 && S.lsb[0] >= lbase && S.lsb[0] <= lend)));
-            for (int i = 0; i < D_LR; ++i) {
+            // injection steps only if some pair of the warp starts in this segment
+            const bool inj = __any_sync(0xffffffffu, live && ((S.ls[0] >= l0 && S.ls[0] < l0 + 32) ||
+                                                              (SPIN == 2 && S.lsb[0] >= l0 && S.lsb[0] < l0 + 32)));
+            for (int i = 32 * seg; i < 32 * seg + 32; ++i) {
                 df v0 = df_zero(), v1 = df_zero();
                 if (live) {
                     if (inj) df_stepx<1, SPIN, true>(S, s_rec, s_s2c, i, lbase + i);
@@ -422,8 +425,8 @@ __global__ void __launch_bounds__(D_NT) k_leg_analysis_df(const LegArgs<double> 
                         v0 = S.a1[0];
                     }
                 }
-                lam[i * D_LS + tid] = v0;
-                if (SPIN == 2) lam[D_LR * D_LS + i * D_LS + tid] = v1;
+                lam[i * D_LS + pp] = v0;
+                if (SPIN == 2) lam[D_LR * D_LS + i * D_LS + pp] = v1;
             }
         }
         // ---- ring data of the stage: per (pair, map) the even / odd sets
@@ -534,7 +537,7 @@ int launch_analysis_df(Plan *p, const double2 *G, int nmaps, const double *beam,
     a.F = const_cast<double2 *>(G);
     a.beam = beam;
     a.nmaps = nmaps;
-    if (!a.toff128 || !a.tst64_0 || (SPIN == 2 && !a.tst64_2)) {
+    if (!a.toff64 || !a.tst64_0 || (SPIN == 2 && !a.tst64_2)) {
         set_error("double-FP32 transpose: the plan has no FP64 recurrence tile states");
         return SHTG_ERR_ARG;
     }

@@ -11,8 +11,8 @@
 // ring pairs needs no cross-thread reduction: per (l, ring pair, map) the
 // FP64 pipe sees the 2 (spin 0) or 8 (spin 2) multiply-adds of the
 // contraction and nothing else.  The recurrence restarts every 128 l from
-// FP64 states tabulated at plan creation by the same steps, so its values
-// equal those of one continuous run.
+// FP64 states tabulated (every SHTG_TS64 l) at plan creation by the same
+// steps, so its values equal those of one continuous run.
 #include <string>
 #include <vector>
 
@@ -28,8 +28,9 @@ constexpr int G_NMT = 8;    // maps per CTA (grid.z covers more)
 constexpr int G_LS = G_KP + 1;   // row stride of the value tile (odd: rows in distinct banks)
 constexpr int G_GS = 9;          // map stride of the ring-data sets
 
-// FP64 recurrence state before every l = m + 128 t of every (m, ring pair),
-// [m][t][pair]: the steps of the Legendre kernels, one thread per (m, pair).
+// FP64 recurrence state before every l = m + SHTG_TS64 t of every (m, ring
+// pair), [m][t][pair]: the steps of the Legendre kernels, one thread per
+// (m, pair).
 template <int SPIN>
 __global__ void __launch_bounds__(LEG_THREADS) k_tile_states64(const LegArgs<double> a, const int64_t *toff,
                                                                double2 *out0, double4_32a *out2) {
@@ -43,8 +44,8 @@ __global__ void __launch_bounds__(LEG_THREADS) k_tile_states64(const LegArgs<dou
     const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2;
     const int64_t o = toff[m] * a.npairs + pr;
     for (int l = m; l <= L; ++l) {
-        if (((l - m) & (G_LR - 1)) == 0) {
-            const int64_t e = o + (int64_t)((l - m) / G_LR) * a.npairs;
+        if (((l - m) & (SHTG_TS64 - 1)) == 0) {
+            const int64_t e = o + (int64_t)((l - m) / SHTG_TS64) * a.npairs;
             if (SPIN == 2) out2[e] = make_double4_32a(S.a1[0], S.a2[0], S.b1[0], S.b2[0]);
             else out0[e] = make_double2(S.a1[0], S.a2[0]);
         }
@@ -137,7 +138,7 @@ __global__ void __launch_bounds__(G_NT) k_leg_analysis_g64(const LegArgs<double>
             const bool live = pr < a.npairs;
             if (live) {
                 const int64_t o = (int64_t)m * a.npairs + pr;
-                const int64_t e = (a.toff128[m] + (lbase - m) / G_LR) * a.npairs + pr;
+                const int64_t e = (a.toff64[m] + (lbase - m) / SHTG_TS64) * a.npairs + pr;
                 S.u[0] = a.u[pr];
                 if (SPIN == 2) {
                     const int2 q = a.ls2[o];
@@ -260,7 +261,7 @@ int launch_g64(Plan *p, const double2 *G, int nmaps, const double *beam, double2
     a.F = const_cast<double2 *>(G);
     a.beam = beam;
     a.nmaps = nmaps;
-    if (!a.toff128 || !a.tst64_0 || (SPIN == 2 && !a.tst64_2)) {
+    if (!a.toff64 || !a.tst64_0 || (SPIN == 2 && !a.tst64_2)) {
         set_error("FP64 transpose: the plan has no FP64 recurrence tile states");
         return SHTG_ERR_ARG;
     }
@@ -281,7 +282,7 @@ int build_tile_states64(Plan *p) {
     const int L = p->lmax;
     std::vector<int64_t> toff(L + 2);
     toff[0] = 0;
-    for (int m = 0; m <= L; ++m) toff[m + 1] = toff[m] + (L + 1 - m + G_LR - 1) / G_LR;
+    for (int m = 0; m <= L; ++m) toff[m + 1] = toff[m] + (L + 1 - m + SHTG_TS64 - 1) / SHTG_TS64;
     const size_t nent = (size_t)toff[L + 1] * p->npairs;
     auto alloc = [&](void **ptr, size_t bytes) -> int {
         cudaError_t e = cudaMalloc(ptr, bytes);
@@ -295,16 +296,16 @@ int build_tile_states64(Plan *p) {
         p->device_bytes += (int64_t)bytes;
         return SHTG_OK;
     };
-    SHTG_TRY(alloc((void **)&p->d_toff128, sizeof(int64_t) * toff.size()));
-    SHTG_CUDA(cudaMemcpy(p->d_toff128, toff.data(), sizeof(int64_t) * toff.size(), cudaMemcpyHostToDevice));
+    SHTG_TRY(alloc((void **)&p->d_toff64, sizeof(int64_t) * toff.size()));
+    SHTG_CUDA(cudaMemcpy(p->d_toff64, toff.data(), sizeof(int64_t) * toff.size(), cudaMemcpyHostToDevice));
     SHTG_TRY(alloc((void **)&p->d_tst64_0, sizeof(double2) * nent));
     LegArgs<double> a = leg_make_args<double>(p);
     dim3 grid((p->npairs + LEG_THREADS - 1) / LEG_THREADS, L + 1);
-    k_tile_states64<0><<<grid, LEG_THREADS>>>(a, p->d_toff128, p->d_tst64_0, nullptr);
+    k_tile_states64<0><<<grid, LEG_THREADS>>>(a, p->d_toff64, p->d_tst64_0, nullptr);
     SHTG_CHECK_LAUNCH("k_tile_states64");
     if (p->flags & SHTG_SPIN2) {
         SHTG_TRY(alloc((void **)&p->d_tst64_2, sizeof(double4_32a) * nent));
-        k_tile_states64<2><<<grid, LEG_THREADS>>>(a, p->d_toff128, nullptr, p->d_tst64_2);
+        k_tile_states64<2><<<grid, LEG_THREADS>>>(a, p->d_toff64, nullptr, p->d_tst64_2);
         SHTG_CHECK_LAUNCH("k_tile_states64");
     }
     SHTG_CUDA(cudaDeviceSynchronize());

@@ -121,7 +121,7 @@ template <typename T> struct LegArgs {
     const int64_t *toff;  // tensor-core transpose: recurrence states every 32 l (FP32 plans)
     const float2 *tst0;
     const float4 *tst2;
-    const int64_t *toff128;   // FP64 transpose: FP64 recurrence states every 128 l (FP64 plans)
+    const int64_t *toff64;    // FP64 recurrence states every SHTG_TS64 l (FP64 and double-FP32 transposes)
     const double2 *tst64_0;
     const double4_32a *tst64_2;
 };

@@ -697,6 +697,11 @@ int plan_build(Plan *p) {
     SHTG_TRY(dalloc(p, &p->d_lsum, (int64_t)p->lmax + 1));
     SHTG_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
     SHTG_CUDA(cudaStreamCreateWithFlags(&p->work_stream, cudaStreamNonBlocking));
+    SHTG_CUDA(cudaEventCreateWithFlags(&p->ring_fork, cudaEventDisableTiming));
+    for (int i = 0; i < Plan::RING_SIDE; ++i) {
+        SHTG_CUDA(cudaStreamCreateWithFlags(&p->ring_side[i], cudaStreamNonBlocking));
+        SHTG_CUDA(cudaEventCreateWithFlags(&p->ring_join[i], cudaEventDisableTiming));
+    }
     SHTG_TRY(dalloc(p, &p->d_flag, 16));
     SHTG_CUDA(cudaMemset(p->d_flag, 0, 16 * sizeof(int)));
     SHTG_TRY(dalloc(p, &p->d_stage, nmp));
@@ -719,7 +724,7 @@ void plan_free(Plan *p) {
                     p->d_ltab64, p->d_ltab32, p->d_scal, p->d_part, p->d_lsum, p->d_stage,
                     p->d_ls2_64, p->d_st2_64, p->d_ls2_32, p->d_st2_32, p->d_ring_groups, p->d_flag,
                     p->d_toff, p->d_tst0, p->d_tst2, p->d_isc64, p->d_rsc64, p->d_isc32,
-                    p->d_toff128, p->d_tst64_0, p->d_tst64_2, p->d_rph64, p->d_rph32};
+                    p->d_toff64, p->d_tst64_0, p->d_tst64_2, p->d_rph64, p->d_rph32};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (int i = 0; i < 7; ++i)
@@ -729,6 +734,11 @@ void plan_free(Plan *p) {
     if (p->h_pinned) cudaFreeHost(p->h_pinned);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     if (p->work_stream) cudaStreamDestroy(p->work_stream);
+    for (int i = 0; i < Plan::RING_SIDE; ++i) {
+        if (p->ring_side[i]) cudaStreamDestroy(p->ring_side[i]);
+        if (p->ring_join[i]) cudaEventDestroy(p->ring_join[i]);
+    }
+    if (p->ring_fork) cudaEventDestroy(p->ring_fork);
     for (auto &e : p->prof.ev)
         if (e) cudaEventDestroy(e);
     p->prof.ev.clear();

@@ -606,11 +606,23 @@ static int launch_ring(Plan *p, RingArgs<T> a, cudaStream_t st) {
     a.tw_nlo = p->tw_nlo;
     a.tw_nhi = p->tw_nhi;
     // one launch per length bucket, each with the thread count and shared
-    // memory of its longest transform
+    // memory of its longest transform.  The buckets touch disjoint ring
+    // pairs, so all but the first run on the plan's side streams, forked from
+    // and joined back into st with events (parallel branches when st is
+    // being captured into a graph): the short single-wave launches of the
+    // small polar rings then overlap with the long ones.
     prof_begin(p, sizeof(T) == 8 ? K_RING64 : K_RING32, st);
-    int nl = 0;
-    for (const Plan::RingLaunch &g : p->ring_launch) {
+    int nl = 0, nside = 0;
+    const int nb = (int)p->ring_launch.size();
+    if (nb > 1) SHTG_CUDA(cudaEventRecord(p->ring_fork, st));
+    for (int gi = 0; gi < nb; ++gi) {
+        const Plan::RingLaunch &g = p->ring_launch[gi];
         if (g.count == 0) continue;
+        cudaStream_t ls = st;
+        if (gi > 0 && nside < Plan::RING_SIDE) {
+            ls = p->ring_side[nside];
+            SHTG_CUDA(cudaStreamWaitEvent(ls, p->ring_fork, 0));
+        }
         const int M = 1 << g.logm;
         const int nt = ring_threads(g.logm);
         a.buf_len = M + M / 16;
@@ -618,12 +630,17 @@ static int launch_ring(Plan *p, RingArgs<T> a, cudaStream_t st) {
         a.pairs = p->d_ring_groups + g.off;
         int rc = SHTG_OK;
         switch (nt) {
-            case 64: rc = launch_ring_nt<T, MODE, 64>(a, g.count, smem, st); break;
-            case 128: rc = launch_ring_nt<T, MODE, 128>(a, g.count, smem, st); break;
-            case 256: rc = launch_ring_nt<T, MODE, 256>(a, g.count, smem, st); break;
-            default: rc = launch_ring_nt<T, MODE, 512>(a, g.count, smem, st); break;
+            case 64: rc = launch_ring_nt<T, MODE, 64>(a, g.count, smem, ls); break;
+            case 128: rc = launch_ring_nt<T, MODE, 128>(a, g.count, smem, ls); break;
+            case 256: rc = launch_ring_nt<T, MODE, 256>(a, g.count, smem, ls); break;
+            default: rc = launch_ring_nt<T, MODE, 512>(a, g.count, smem, ls); break;
         }
         if (rc != SHTG_OK) return rc;
+        if (ls != st) {
+            SHTG_CUDA(cudaEventRecord(p->ring_join[nside], ls));
+            SHTG_CUDA(cudaStreamWaitEvent(st, p->ring_join[nside], 0));
+            ++nside;
+        }
         ++nl;
     }
     prof_end(p, st, nl);
