@@ -202,35 +202,39 @@ template <int SPIN, int ALMS>
 __device__ __forceinline__ void gen_btiles(const float2 *s_alm, const int i0, unsigned char *bt) {
     constexpr int NCOL = TcCfg<SPIN>::NCOL, NTB = TcCfg<SPIN>::NTB;
     constexpr int BTILE = 2 * NCOL * 32;
-    // item = (tile b, K group kg, column c, K pair kq): four consecutive lanes
-    // fill one 16-byte core-matrix row, a warp eight consecutive rows
-    for (int it = threadIdx.x; it < NTB * 8 * NCOL; it += TC_M) {
-        const int kq = it & 3;
-        const int c = (it >> 2) % NCOL;
-        const int kg = (it / (4 * NCOL)) & 1;
-        const int b = it / (8 * NCOL);
+    // item = (tile b, K group kg, column c): one 16-byte core-matrix row of
+    // hi and one of lo (the 8 K values, l = i0 + off + 16 kg + 2 j, of column
+    // c), consecutive threads on consecutive rows.  Column c of tile b reads
+    // one component of one staged alm row: spin 0 (re, im) of map c / 2;
+    // spin 2 W tiles (b < 2) -(E re, E im, B re, B im), X tiles (B im, -B re,
+    // -E im, E re) of map c / 4, component c % 4.
+    for (int it = threadIdx.x; it < NTB * 2 * NCOL; it += TC_M) {
+        const int c = it % NCOL, kg = (it / NCOL) & 1, b = it / (2 * NCOL);
         const int off = b & 1;
-        const int k0 = 8 * kg + 2 * kq;
-        float v[2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int idx = i0 + 2 * (k0 + q) + off;
-            if (SPIN == 0) {
-                const float2 av = s_alm[(c >> 1) * ALMS + idx];
-                v[q] = (c & 1) ? av.y : av.x;
+        int row, ri;
+        float sg;
+        if (SPIN == 0) {
+            row = c >> 1;
+            ri = c & 1;
+            sg = 1.f;
+        } else {
+            const int mk = c >> 2, comp = c & 3;
+            if (b < 2) {
+                row = 2 * mk + (comp >= 2 ? 1 : 0);
+                ri = comp & 1;
+                sg = -1.f;
             } else {
-                const int mk = c >> 2, comp = c & 3;
-                const float2 e = s_alm[(2 * mk) * ALMS + idx];
-                const float2 bb = s_alm[(2 * mk + 1) * ALMS + idx];
-                if (b < 2) v[q] = comp == 0 ? -e.x : comp == 1 ? -e.y : comp == 2 ? -bb.x : -bb.y;
-                else v[q] = comp == 0 ? bb.y : comp == 1 ? -bb.x : comp == 2 ? -e.y : e.x;
+                row = 2 * mk + (comp < 2 ? 1 : 0);
+                ri = (comp & 1) ^ 1;
+                sg = (comp == 1 || comp == 2) ? -1.f : 1.f;
             }
         }
-        uint32_t hi, lo;
-        split2(v[0], v[1], hi, lo);
-        unsigned char *tile = bt + b * BTILE + kg * (32 * NCOL) + kq * 4;
-        *reinterpret_cast<uint32_t *>(tile + c * 16) = hi;
-        *reinterpret_cast<uint32_t *>(tile + (NCOL + c) * 16) = lo;
+        const float *src = reinterpret_cast<const float *>(s_alm + row * ALMS + i0 + off + 16 * kg) + ri;
+        float x[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) x[j] = sg * src[4 * j];
+        unsigned char *r = bt + b * BTILE + kg * (32 * NCOL) + c * 16;
+        store_row8(r, r + NCOL * 16, x);
     }
 }
 

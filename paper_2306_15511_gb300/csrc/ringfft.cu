@@ -22,9 +22,12 @@ namespace shtg {
 
 // Threads per CTA: M / 16 for the launch's longest transform M (every
 // radix-16 pass then has one butterfly per thread), at least 64; resident
-// CTAs per SM for a budget of 128 registers a thread (the inlined passes do
-// not spill, which measured faster than more resident CTAs with spills).
-template <int NT> struct RingBlocks { static constexpr int v = 512 / NT; };
+// CTAs per SM for a budget of 128 registers a thread in FP32 (the inlined
+// passes do not spill), 255 in FP64 up to 256 threads (the FP64 passes
+// spill at 128).
+template <typename T, int NT> struct RingBlocks {
+    static constexpr int v = sizeof(T) == 8 ? (NT >= 256 ? 1 : 256 / NT) : 512 / NT;
+};
 
 __device__ __forceinline__ int rpad(int i) { return i + (i >> 4); }
 
@@ -282,7 +285,7 @@ __device__ __forceinline__ void transform_dir(C *buf, const int logM, const TwTa
 // conjugated in the last pass, DFT again: buf then holds the conjugate of the
 // convolution.  The directions run in a loop, so the FFT is inlined once.
 template <typename T, int MODE, int NT>
-__global__ void __launch_bounds__(NT, RingBlocks<NT>::v) k_ring(const RingArgs<T> a) {
+__global__ void __launch_bounds__(NT, RingBlocks<T, NT>::v) k_ring(const RingArgs<T> a) {
     typedef typename VT<T>::C C;
     extern __shared__ __align__(16) unsigned char s_raw[];
     C *s_tw = reinterpret_cast<C *>(s_raw);
