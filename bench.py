@@ -65,6 +65,13 @@ def alu_peaks(sm_mhz: float):
     return fp32, fp64
 
 
+def contraction_flops(nalm, npairs, nmaps_t, nmaps_p):
+    """Algorithmic flops of the Legendre contraction alone (what the tensor
+    cores do in the tensor-core kernels): per (l, m, ring pair) 4 per
+    temperature map and 16 per (Q, U) pair."""
+    return float(nalm) * float(npairs) * (4 * nmaps_t + 16 * nmaps_p)
+
+
 def legendre_flops(nalm, npairs, nmaps_t, nmaps_p):
     """Algorithmic flops of one Legendre pass (one direction): per (l, m,
     ring pair) 3 shared recurrence flops + 4 per temperature map, and for
@@ -249,7 +256,7 @@ def run_gpu(args):
     inp = make_inputs(plan, dev, seed_shift=rank)
     kw = dict(tol=1e-6, mode=args.mode, maxiter=args.iters_per_step,
               reliable_delta=args.reliable_delta, check_every=args.check_every,
-              allow_not_converged=True)
+              allow_not_converged=True, fp64_arith=args.fp64_arith)
     out = torch.empty(NB, 3, plan.nalm, dtype=torch.complex128, device=dev)
 
     def step(profile=False):
@@ -314,24 +321,69 @@ def run_gpu(args):
         extras = measure_extras(plan, inp, dev, kw, full_solve=not args.no_full_solve)
 
     # ------------------------------------------------------------ roofline
+    # One entry per kernel class with the resource that bounds it and the
+    # class's algorithmic work over its live CUDA-event time in the timed
+    # steps; "roofline" is the class with the largest share.
+    #  - tensor-core Legendre kernels (mode mixed_tc): the contraction's
+    #    flops against the measured sustained bf16 tensor rate (three bf16
+    #    products per FP32-accurate multiply-add are issued on top);
+    #  - CUDA-core FP32 Legendre kernels (mode mixed): all flops against the
+    #    FP32 lanes at the sampled clock;
+    #  - FP64-accurate Legendre kernels: in double-FP32 (the mixed modes'
+    #    default) against the FP32 lanes / 6 (a double-FP32 flop costs about
+    #    six FP32 operations), in native FP64 against the nominal FP64 rate;
+    #  - ring stages: HBM, the bytes of the Fourier coefficients read and
+    #    written plus the N^-1 map (FP32 fused launches; FP64: three fused and
+    #    the RHS's map -> coefficients launch per step).
     peaks, src = measured_peaks()
     sm_mhz = ck.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     fp32_peak, fp64_peak = alu_peaks(float(sm_mhz))
+    bf16_sus = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
     nalm, npairs = plan.nalm, 2 * NSIDE
+    nring, npix = 4 * NSIDE - 1, 12 * NSIDE * NSIDE
     per_pass = legendre_flops(nalm, npairs, NB, NB)           # T and Q/U launches of one pass
-    fl = {0: per_pass * (inner + 0), 1: per_pass * inner, 3: per_pass * outer,
-          4: per_pass * (outer + len(stats))}                   # FP64 analysis also builds the RHS
-    dom = int(np.argmax(kms))
-    roof = None
-    if dom in fl and kms[dom] > 0:
-        ach = fl[dom] / (kms[dom] / 1000.0) / 1e12
-        peak = fp64_peak if dom >= 3 else fp32_peak
-        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None, "kernel": CLASS_NAMES[dom],
-                "peak_source": f"derived from unit counts at the sampled {sm_mhz:.0f} MHz"}
-    elif kms[dom] > 0:
-        roof = {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
-                "frac": None, "traffic": None, "kernel": CLASS_NAMES[dom]}
+    per_pass_c = contraction_flops(nalm, npairs, NB, NB)
+    df = args.fp64_arith == "df64" or (args.fp64_arith == "default" and args.mode != "fp64")
+    coef32 = 2.0 * 3 * NB * nring * (LMAX + 1) * 8           # read + write, T, Q, U of NB maps
+    ring_bytes = {2: (coef32 + 2 * npix * 4) * inner,
+                  5: (2 * coef32 + 2 * npix * 8) * outer + (3 * NB * npix * 8 + coef32) * len(stats)}
+    fl = {0: inner, 1: inner, 3: outer, 4: outer + len(stats)}   # passes (FP64 analysis also builds the RHS)
+    roofs = {}
+    for c in range(len(CLASS_NAMES)):
+        if kms[c] <= 0:
+            continue
+        t = kms[c] / 1000.0
+        if c in (0, 1):
+            if args.mode == "mixed_tc":
+                ach = per_pass_c * fl[c] / t / 1e12
+                r = {"bound": "tensor", "achieved": ach, "peak": bf16_sus, "unit": "TFLOP/s",
+                     "peak_source": f"{src} bf16 (sustained)"}
+            else:
+                ach = per_pass * fl[c] / t / 1e12
+                r = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "peak_source": f"FP32 lanes x 2 flops at the sampled {sm_mhz:.0f} MHz"}
+        elif c in (3, 4):
+            ach = per_pass * fl[c] / t / 1e12
+            if df:
+                r = {"bound": "alu", "achieved": ach, "peak": fp32_peak / 6.0, "unit": "TFLOP/s",
+                     "peak_source": f"FP32 lanes x 2 flops at the sampled {sm_mhz:.0f} MHz / 6 "
+                                    "(double-FP32 arithmetic)"}
+            else:
+                r = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "peak_source": "nominal GB300 FP64 rate at the sampled clock"}
+        elif c in ring_bytes:
+            ach = ring_bytes[c] / t / 1e9
+            r = {"bound": "hbm", "achieved": ach, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                 "peak_source": f"{src} copy bandwidth"}
+        else:
+            continue
+        r["frac"] = r["achieved"] / r["peak"] if r["peak"] else None
+        r["traffic"] = None
+        r["kernel"] = CLASS_NAMES[c]
+        roofs[CLASS_NAMES[c]] = r
+    dom = CLASS_NAMES[int(np.argmax(kms))]
+    roof = roofs.get(dom) or {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                              "frac": None, "traffic": None, "kernel": dom}
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -345,18 +397,21 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32+f64" if args.mode == "mixed" else "f32/bf16x3+f64",
+        "vs_baseline": None,
+        "dtype": ("f32" if args.mode == "mixed" else "f32/bf16x3" if args.mode == "mixed_tc" else "f64") +
+                 ("+df64" if df else "+f64") + (" (f64 ring FFTs)" if args.mode != "fp64" else ""),
         "data": "synthetic",
         "config": {"workload": f"T+E+B constrained realizations, HEALPix N_side={NSIDE}, "
-                               f"l_max={LMAX}, batch {NB} per GPU, mixed FP32 PCG + FP64 "
-                               f"residual replacement, tol 1e-6, {args.iters_per_step} "
+                               f"l_max={LMAX}, batch {NB} per GPU, mixed FP32 PCG + FP64-accurate "
+                               f"residual replacement" + (" (double-FP32 Legendre sums)" if df else "") +
+                               f", tol 1e-6, {args.iters_per_step} "
                                f"iterations per step" +
                                (", synthesis Legendre sums on the tensor cores (bf16 hi/lo split)"
                                 if args.mode == "mixed_tc" else ""),
-                   "mode": args.mode, "iters_per_step": args.iters_per_step,
+                   "mode": args.mode, "fp64_arith": args.fp64_arith, "iters_per_step": args.iters_per_step,
                    "global_batch": NB * world, "fsky": inp["fsky"], "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (d, w2: 2.4 GB each)"},
-        "e2e": e2e, "gpu_launches": launches, "clocks": ck, "roofline": roof,
+        "e2e": e2e, "gpu_launches": launches, "clocks": ck, "roofline": roof, "rooflines": roofs,
         "cpu_baseline": cpu,
         "step": {"fp32_iterations": inner / len(stats),
                  "fp64_residual_replacements": outer / len(stats),
@@ -374,8 +429,9 @@ def run_gpu(args):
 
 
 def measure_extras(plan, inp, dev, kw, full_solve=True):
-    """SHT pairs/s (one map, spin 0, FP32 and FP64), the full mixed solve to
-    1e-6 and the plain FP64 PCG iteration rate on the same problem."""
+    """SHT pairs/s (one map, spin 0: FP32, FP64, double-FP32), the full mixed
+    solve to 1e-6 and the plain FP64-accurate PCG iteration rate on the same
+    problem (native FP64 arithmetic, and double-FP32)."""
     import torch
     ex = {}
     if full_solve:
@@ -395,15 +451,16 @@ def measure_extras(plan, inp, dev, kw, full_solve=True):
                                   "rel_residual": st["rel_residual"], "ms_rhs": st["ms_rhs"]}
     g = torch.Generator(device=dev)
     g.manual_seed(0)
-    for prec, ct, reps in (("fp32", torch.complex64, 10), ("fp64", torch.complex128, 3)):
+    for prec, ct, reps, dfl in (("fp32", torch.complex64, 10, False), ("fp64", torch.complex128, 3, False),
+                                ("df64", torch.complex128, 3, True)):
         a = torch.randn(1, plan.nalm, dtype=ct, device=dev, generator=g)
         for _ in range(2):
-            plan.alm2map_adjoint(plan.alm2map(a))
+            plan.alm2map_adjoint(plan.alm2map(a, double_float=dfl), double_float=dfl)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record()
         for _ in range(reps):
-            plan.alm2map_adjoint(plan.alm2map(a))
+            plan.alm2map_adjoint(plan.alm2map(a, double_float=dfl), double_float=dfl)
         e1.record()
         torch.cuda.synchronize()
         ex[f"sht_pairs_per_s_{prec}_batch1"] = reps / (e0.elapsed_time(e1) / 1000.0)
@@ -432,6 +489,13 @@ def measure_extras(plan, inp, dev, kw, full_solve=True):
     ex["fp64_form"] = {"iterations_timed": st["iterations"], "wall_s": el,
                        "ms_rhs": st["ms_rhs"], "s_per_iteration": per_it,
                        "iters_per_s": 1.0 / per_it if per_it > 0 else None}
+    # the same plain PCG with its Legendre sums in double-FP32 arithmetic
+    _, st2 = plan.cg_sample(inp["cl"], inp["bl"], inp["ninv"], inp["d"], inp["w1"], inp["w2"],
+                            tol=1e-6, mode="fp64", maxiter=nit, check_every=nit,
+                            allow_not_converged=True, profile=True, fp64_arith="df64")
+    per_it2 = (st2["ms_solve"] / 1000.0) / max(1, st2["iterations"])
+    ex["fp64_form_df64"] = {"iterations_timed": st2["iterations"], "s_per_iteration": per_it2,
+                            "iters_per_s": 1.0 / per_it2 if per_it2 > 0 else None}
     if "mixed_full_solve" in ex:
         fs = ex["mixed_full_solve"]
         # FP64 PCG needs about as many iterations as the mixed solver (they
@@ -488,6 +552,8 @@ def main():
     ap.add_argument("--iters-per-step", type=int, default=160)
     ap.add_argument("--mode", default="mixed_tc", choices=["mixed", "mixed_tc"],
                     help="inner FP32 operator: CUDA-core or tensor-core Legendre synthesis")
+    ap.add_argument("--fp64-arith", default="default", choices=["default", "fp64", "df64"],
+                    help="arithmetic of the FP64-accurate steps (default: double-FP32 in the mixed modes)")
     ap.add_argument("--nside", type=int, default=NSIDE, help="profiling only: smaller grid")
     ap.add_argument("--lmax", type=int, default=LMAX, help="profiling only: smaller l_max")
     ap.add_argument("--batch", type=int, default=NB, help="profiling only: fewer realizations")

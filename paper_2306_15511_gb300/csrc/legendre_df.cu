@@ -555,19 +555,20 @@ int launch_analysis_df(Plan *p, const double2 *G, int nmaps, const double *beam,
 }  // namespace
 
 // Autotuned (key kind 3): synthesis (ring pairs per thread, maps per pass)
-// spin 0: (1, 4), (1, 8), (2, 4); spin 2: (1, 2), (1, 4), (2, 1).  The
+// spin 0: (1, 8), (1, 4), (2, 4); spin 2: (1, 4), (1, 2), (2, 1) (the first
+// of each was the fastest at N_side 1024, l_max 2048, 8 maps).  The
 // transpose has one shape.
 int leg_synth_df(Plan *p, int spin, const double2 *alm, int rs, int nmaps, const double *beam, double2 *F,
                  cudaStream_t st) {
     return tune(p, 3, spin == 2 ? 1 : 0, nmaps, 3, st, [&](int v) {
         if (spin == 2) {
-            if (v == 1) return launch_synth_df<1, 4, 2>(p, alm, rs, nmaps, beam, F, st);
+            if (v == 1) return launch_synth_df<1, 2, 2>(p, alm, rs, nmaps, beam, F, st);
             if (v == 2) return launch_synth_df<2, 1, 2>(p, alm, rs, nmaps, beam, F, st);
-            return launch_synth_df<1, 2, 2>(p, alm, rs, nmaps, beam, F, st);
+            return launch_synth_df<1, 4, 2>(p, alm, rs, nmaps, beam, F, st);
         }
-        if (v == 1) return launch_synth_df<1, 8, 0>(p, alm, rs, nmaps, beam, F, st);
+        if (v == 1) return launch_synth_df<1, 4, 0>(p, alm, rs, nmaps, beam, F, st);
         if (v == 2) return launch_synth_df<2, 4, 0>(p, alm, rs, nmaps, beam, F, st);
-        return launch_synth_df<1, 4, 0>(p, alm, rs, nmaps, beam, F, st);
+        return launch_synth_df<1, 8, 0>(p, alm, rs, nmaps, beam, F, st);
     });
 }
 

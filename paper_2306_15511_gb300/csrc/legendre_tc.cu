@@ -1015,8 +1015,9 @@ int launch_analysis_tc(Plan *p, const float2 *G, int nmaps, const float *beam, f
 
 // Shapes tried by the autotuner (key kind 2): synthesis (stages, staged l)
 // = (1, 64) [four CTAs per SM at spin 2], (2, 128), (1, 128); transpose
-// (A buffers, B buffers, 256-l tiles) = (1, 1, 1) [four CTAs per SM],
-// (2, 2, 2), (1, 2, 1), (2, 2, 1), (1, 2, 2), (1, 1, 2) [three CTAs per SM].
+// (A buffers, B buffers, 256-l tiles) = (1, 1, 2) [three CTAs per SM; the
+// fastest at N_side 1024, l_max 2048, 8 maps], (1, 2, 2), (2, 2, 2),
+// (1, 1, 1) [four CTAs per SM], (1, 2, 1), (2, 2, 1).
 // Every shape sums the same products in the same order, so the choice does
 // not change a bit of the result.
 int leg_synth_tc(Plan *p, int spin, const float2 *alm, int rs, int nmaps, const float *beam, float2 *F,
@@ -1037,12 +1038,12 @@ template <int SPIN>
 static int analysis_tc_shape(int v, Plan *p, const float2 *G, int nmaps, const float *beam, float2 *alm, int rs,
                              cudaStream_t st, int vjp) {
     switch (v) {
-        case 1: return launch_analysis_tc<SPIN, 2, 2, 2>(p, G, nmaps, beam, alm, rs, st, vjp);
-        case 2: return launch_analysis_tc<SPIN, 1, 2, 1>(p, G, nmaps, beam, alm, rs, st, vjp);
-        case 3: return launch_analysis_tc<SPIN, 2, 2, 1>(p, G, nmaps, beam, alm, rs, st, vjp);
-        case 4: return launch_analysis_tc<SPIN, 1, 2, 2>(p, G, nmaps, beam, alm, rs, st, vjp);
-        case 5: return launch_analysis_tc<SPIN, 1, 1, 2>(p, G, nmaps, beam, alm, rs, st, vjp);
-        default: return launch_analysis_tc<SPIN, 1, 1, 1>(p, G, nmaps, beam, alm, rs, st, vjp);
+        case 1: return launch_analysis_tc<SPIN, 1, 2, 2>(p, G, nmaps, beam, alm, rs, st, vjp);
+        case 2: return launch_analysis_tc<SPIN, 2, 2, 2>(p, G, nmaps, beam, alm, rs, st, vjp);
+        case 3: return launch_analysis_tc<SPIN, 1, 1, 1>(p, G, nmaps, beam, alm, rs, st, vjp);
+        case 4: return launch_analysis_tc<SPIN, 1, 2, 1>(p, G, nmaps, beam, alm, rs, st, vjp);
+        case 5: return launch_analysis_tc<SPIN, 2, 2, 1>(p, G, nmaps, beam, alm, rs, st, vjp);
+        default: return launch_analysis_tc<SPIN, 1, 1, 2>(p, G, nmaps, beam, alm, rs, st, vjp);
     }
 }
 
