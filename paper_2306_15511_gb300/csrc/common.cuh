@@ -142,6 +142,7 @@ struct Plan {
         int off, count;   // slice of d_ring_groups
         int logm;         // log2 of the bucket's buffer length (every member's M, and 2n if aliased)
         int alias;        // bucket holds rings with n < 2 lmax
+        int chirp;        // longest Bluestein ring of the bucket (its chirp is staged in shared memory)
     };
     std::vector<RingLaunch> ring_launch;
 

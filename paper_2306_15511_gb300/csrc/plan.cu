@@ -626,11 +626,13 @@ static int build_fft_tables(Plan *p) {
             g.count = (int)kv.second.size();
             g.logm = keymax[kv.first];
             g.alias = 0;
+            g.chirp = 0;
             const int nt = ring_threads(g.logm);
             for (int r : kv.second) {
                 const RingFFT &f = p->h_rfft[r];
                 groups.push_back(r);
                 if (f.n < 2 * p->lmax) g.alias = 1;
+                if (f.blue) g.chirp = std::max(g.chirp, f.n);
                 // the kernel's passes cover this ring: M / 16 butterflies per
                 // radix-16 pass, M / R in the first pass
                 const int M = 1 << f.logM, R = 1 << (f.logM & 3);

@@ -266,6 +266,7 @@ template <typename T> struct RingArgs {
     int nT;           // fused: rows [0, nT) use N^-1 component 0 (T), later rows component 1 (Q, U)
     int weighted;     // analysis: multiply by the quadrature weight
     int buf_len;      // shared transform buffer length (padded) of this launch
+    int chirp_len;    // shared chirp buffer length (longest Bluestein ring of the launch)
     const int *pairs; // ring pairs handled by this launch (one CTA each)
 };
 
@@ -290,7 +291,8 @@ __global__ void __launch_bounds__(NT, RingBlocks<T, NT>::v) k_ring(const RingArg
     extern __shared__ __align__(16) unsigned char s_raw[];
     C *s_tw = reinterpret_cast<C *>(s_raw);
     C *buf = s_tw + a.tw_nlo + a.tw_nhi;
-    C *scr_p = buf + a.buf_len;   // aliased fold: partial sums [north | south][NT]
+    C *s_chirp = buf + a.buf_len;          // this ring's chirp (Bluestein rings)
+    C *scr_p = s_chirp + a.chirp_len;      // aliased fold: partial sums [north | south][NT]
     for (int i = threadIdx.x; i < a.tw_nlo + a.tw_nhi; i += NT) s_tw[i] = a.tw[i];
     TwTab<C> tw;
     tw.lo = s_tw;
@@ -305,7 +307,13 @@ __global__ void __launch_bounds__(NT, RingBlocks<T, NT>::v) k_ring(const RingArg
     const RingFFT f = a.rf[rn];
     const int n = f.n, logM = f.logM, M = 1 << logM;
     const int L = a.lmax;
+    // the chirp is read up to five times per element and map: stage it once
     const C *chirp = a.chirp + f.chirp_off;
+    if (f.blue) {
+        for (int i = threadIdx.x; i < n; i += NT) s_chirp[i] = chirp[i];
+        chirp = s_chirp;
+    }
+    __syncthreads();
     const C *ph = a.rph + f.ph_off;   // e^{i pi k / n} (shifted rings)
     const C zero = {T(0), T(0)};
     constexpr int NDIR = MODE == 2 ? 2 : 1;
@@ -629,7 +637,9 @@ static int launch_ring(Plan *p, RingArgs<T> a, cudaStream_t st) {
         const int M = 1 << g.logm;
         const int nt = ring_threads(g.logm);
         a.buf_len = M + M / 16;
-        const size_t smem = sizeof(C) * ((size_t)p->tw_nlo + p->tw_nhi + a.buf_len + (g.alias ? 2 * nt : 0));
+        a.chirp_len = g.chirp;
+        const size_t smem =
+            sizeof(C) * ((size_t)p->tw_nlo + p->tw_nhi + a.buf_len + a.chirp_len + (g.alias ? 2 * nt : 0));
         a.pairs = p->d_ring_groups + g.off;
         int rc = SHTG_OK;
         switch (nt) {
