@@ -529,9 +529,12 @@ template <> struct TaCfg<2> {
 };
 // Shared memory of the transpose CTA (TR 256-l tiles): NAS A buffers (the
 // tiles of one (stage, 256-l tile) unit), NBS B buffers (one per stage of 16
-// pairs), the double-buffered ring data, the coefficients of 256 TR l, two
-// mbarriers and the TMEM address.  Fewer buffers and TR = 1 shrink the CTA
-// (spin 2: 52 KB instead of 99 KB) so that four CTAs share an SM.
+// pairs), the ring data of one stage, the coefficients of 256 TR l, two
+// mbarriers and the TMEM address.  The ring data are consumed when the
+// stage's B tiles are built, so the next stage's copy is issued right after
+// (it overlaps with the stage's A generation) and one buffer suffices.
+// Fewer buffers shrink the CTA (spin 2 with one A and one B buffer: 53 KB
+// with two 256-l tiles, 49 KB with one) so that four CTAs share an SM.
 template <int SPIN, int NAS, int NBS, int TR> struct TaLayout {
     static constexpr int BT = 64 * TaCfg<SPIN>::NO;                         // B tile: 2 NO rows x 16 K bf16
     static constexpr int ASTAGE = TaCfg<SPIN>::NAT * TC_ATILE;
@@ -542,7 +545,7 @@ template <int SPIN, int NAS, int NBS, int TR> struct TaLayout {
     static constexpr int GS = 2 * NROW + 1;
     static constexpr int GBUF = ((TA_K * GS * 8) + 15) & ~15;
     static constexpr int GOFF = BOFF + NBS * BSTAGE;
-    static constexpr int COEF = GOFF + 2 * GBUF;
+    static constexpr int COEF = GOFF + GBUF;
     static constexpr int BARS = COEF + 256 * TR * (SPIN == 2 ? 16 : 8);
     static constexpr int TMEM = TR * TaCfg<SPIN>::TMEM / 2;   // 2 NO columns per 256-l tile
     static constexpr int TMEMA = BARS + 16;
@@ -869,13 +872,8 @@ __global__ void __launch_bounds__(TC_M) k_leg_analysis_tc(const LegArgs<float> a
         const int ps = s0 + si;
         const int pr = ps * TA_K + pin;
         const bool more = si + 1 < nst;
-        if (more) {   // next stage's ring data and start states, in flight during this stage
-            stage_ring_data<SPIN>(a, m, ps + 1, map0, nm, sgb + ((si + 1) & 1) * (Lay::GBUF / 8));
-            pnext = load_pair_start<SPIN>(a, m, pr + TA_K);
-            asm volatile("cp.async.wait_group 1;" ::: "memory");
-        } else {
-            asm volatile("cp.async.wait_group 0;" ::: "memory");
-        }
+        if (more) pnext = load_pair_start<SPIN>(a, m, pr + TA_K);   // in flight during this stage
+        asm volatile("cp.async.wait_group 0;" ::: "memory");          // this stage's ring data
         __syncthreads();
         // unit u commits to barrier u % NAS, completing its phase u / NAS; the
         // commits complete in order, so waiting for u covers every unit before it
@@ -886,7 +884,7 @@ __global__ void __launch_bounds__(TC_M) k_leg_analysis_tc(const LegArgs<float> a
             ok = mbar_wait(&bars[u % NAS], (u / NAS) & 1) && ok;
             waited = u;
         }
-        gen_btiles_ana<SPIN>(sgb + (si & 1) * (Lay::GBUF / 8), bt);   // ring data: double-buffered per stage
+        gen_btiles_ana<SPIN>(sgb, bt);
         for (int r = 0; r < ntile; ++r) {
             const int asel = unit % NAS;
             unsigned char *at = smem + asel * Lay::ASTAGE;
@@ -909,6 +907,9 @@ __global__ void __launch_bounds__(TC_M) k_leg_analysis_tc(const LegArgs<float> a
             tcur = tnext;
             asm volatile("fence.proxy.async.shared::cta;");
             __syncthreads();
+            // every thread has built this stage's B tiles: the ring-data buffer
+            // takes the next stage's copy, in flight during the stage's units
+            if (r == 0 && more) stage_ring_data<SPIN>(a, m, ps + 1, map0, nm, sgb);
             if (tid == 0) {
                 asm volatile("tcgen05.fence::after_thread_sync;");
                 const uint32_t sa = smem_u32(at), sb = smem_u32(bt);
