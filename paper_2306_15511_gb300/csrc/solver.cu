@@ -114,28 +114,38 @@ template <typename T> struct HT;
 template <> struct HT<float> { typedef float2 C; };
 template <> struct HT<double> { typedef double2 C; };
 
-// y += S^-1 x (per-l 1x1 or T/E 2x2 + B block); sinv rows TT, TE, EE, BB
-template <typename T>
+// y += S^-1 x (per-l 1x1 or T/E 2x2 + B block); sinv rows TT, TE, EE, BB.
+// DOT: also the partial <x, y> of the result per realization (the PCG's
+// <p, A p>, the operator's last kernel doing the dot's reads), launched on
+// the reduction grid (RB blocks per realization) with the per-element sums
+// of k_dot, so alpha is the same bit for bit.
+template <typename T, bool DOT>
 __global__ void k_prior_add(const typename HT<T>::C *__restrict__ x, typename HT<T>::C *__restrict__ y,
                             int nc, int64_t nalm, int lmax1, const int *__restrict__ lof,
-                            const T *__restrict__ sinv, const T *__restrict__ isc) {
+                            const T *__restrict__ sinv, const T *__restrict__ isc,
+                            const int *__restrict__ mof, double *__restrict__ part) {
+    typedef typename HT<T>::C C;
+    __shared__ double sm[DOT ? RT / 32 : 1];
     const int b = blockIdx.y;
     const int64_t off = (int64_t)b * nc * nalm;
     const T sc = isc[b];   // 1 / (C_l scale of realization b)
+    double s = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nalm;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int l = lof[i];
         const T tt = sinv[l] * sc;
+        typename DotAcc<C>::t t = 0;
         if (nc == 1) {
-            const auto xv = x[off + i];
-            auto yv = y[off + i];
+            const C xv = x[off + i];
+            C yv = y[off + i];
             yv.x += tt * xv.x;
             yv.y += tt * xv.y;
             y[off + i] = yv;
+            if (DOT) t = DotAcc<C>::add(t, xv, yv);
         } else {
             const T te = sinv[lmax1 + l] * sc, ee = sinv[2 * lmax1 + l] * sc, bb = sinv[3 * lmax1 + l] * sc;
-            const auto xt = x[off + i], xe = x[off + nalm + i], xb = x[off + 2 * nalm + i];
-            auto yt = y[off + i], ye = y[off + nalm + i], yb = y[off + 2 * nalm + i];
+            const C xt = x[off + i], xe = x[off + nalm + i], xb = x[off + 2 * nalm + i];
+            C yt = y[off + i], ye = y[off + nalm + i], yb = y[off + 2 * nalm + i];
             yt.x += tt * xt.x + te * xe.x;
             yt.y += tt * xt.y + te * xe.y;
             ye.x += te * xt.x + ee * xe.x;
@@ -145,7 +155,17 @@ __global__ void k_prior_add(const typename HT<T>::C *__restrict__ x, typename HT
             y[off + i] = yt;
             y[off + nalm + i] = ye;
             y[off + 2 * nalm + i] = yb;
+            if (DOT) {
+                t = DotAcc<C>::add(t, xt, yt);
+                t = DotAcc<C>::add(t, xe, ye);
+                t = DotAcc<C>::add(t, xb, yb);
+            }
         }
+        if (DOT) s += (mof[i] ? 2.0 : 1.0) * (double)t;
+    }
+    if (DOT) {
+        s = block_sum(s, sm);
+        if (threadIdx.x == 0) part[(int64_t)b * RB + blockIdx.x] = s;
     }
 }
 
@@ -597,7 +617,7 @@ static int op_analysis(Solve &s, int spin, const float2 *G, const float *beam, f
 
 // y = A x = S^-1 x + B Y^T N^-1 Y B x for all realizations
 template <typename T>
-static int matvec(Solve &s, const typename HT<T>::C *x, typename HT<T>::C *y) {
+static int matvec(Solve &s, const typename HT<T>::C *x, typename HT<T>::C *y, bool dot = false) {
     typedef typename HT<T>::C C;
     Plan *p = s.p;
     C *F = Vec<T>::phase(p);
@@ -609,8 +629,12 @@ static int matvec(Solve &s, const typename HT<T>::C *x, typename HT<T>::C *y) {
     SHTG_TRY(op_analysis(s, 0, F, beam, y, s.nc));
     if (s.nc == 3) SHTG_TRY(op_analysis(s, 2, F + s.nb * rowsz, beam, y + s.nalm, 3));
     prof_begin(p, K_VEC, s.st);
-    k_prior_add<T><<<dim3(grid_1d(s.nalm).x, s.nb), RT, 0, s.st>>>(x, y, s.nc, s.nalm, p->lmax + 1,
-                                                                   p->d_lofidx, Vec<T>::sinv(p), Vec<T>::isc(p));
+    if (dot)   // y's final values and <x, y> partials (slot 0) in one pass
+        k_prior_add<T, true><<<s.rgrid, RT, 0, s.st>>>(x, y, s.nc, s.nalm, p->lmax + 1, p->d_lofidx,
+                                                       Vec<T>::sinv(p), Vec<T>::isc(p), p->d_mofidx, p->d_part);
+    else
+        k_prior_add<T, false><<<dim3(grid_1d(s.nalm).x, s.nb), RT, 0, s.st>>>(
+            x, y, s.nc, s.nalm, p->lmax + 1, p->d_lofidx, Vec<T>::sinv(p), Vec<T>::isc(p), nullptr, nullptr);
     prof_end(p, s.st);
     SHTG_CHECK_LAUNCH("k_prior_add");
     return SHTG_OK;
@@ -622,15 +646,14 @@ static int pcg_iteration(Solve &s, typename HT<T>::C *x, typename HT<T>::C *r, t
                          typename HT<T>::C *pv, typename HT<T>::C *q, const T *minv) {
     typedef typename HT<T>::C C;
     Plan *p = s.p;
-    SHTG_TRY(matvec<T>(s, pv, q));
+    SHTG_TRY(matvec<T>(s, pv, q, true));   // q = A p and the partials of <p, q>
     prof_begin(p, K_VEC, s.st);
-    k_dot<C><<<s.rgrid, RT, 0, s.st>>>(pv, q, s.nc, s.nalm, p->d_mofidx, p->d_part, 0, 1);
     k_scal_alpha<<<1, 1024, 0, s.st>>>(p->d_part, p->d_scal, s.nb);
     k_update<T, false><<<s.rgrid, RT, 0, s.st>>>(x, r, z, pv, q, minv, s.nc, s.nalm, p->d_mofidx,
                                                  p->d_scal, p->d_part);
     k_scal_beta<<<1, 1024, 0, s.st>>>(p->d_part, p->d_scal, s.nb);
     k_pupdate<C><<<dim3(grid_1d(s.per).x, s.nb), RT, 0, s.st>>>(pv, z, s.nc, s.nalm, p->d_scal);
-    prof_end(p, s.st, 5);
+    prof_end(p, s.st, 4);
     SHTG_CHECK_LAUNCH("pcg iteration");
     return SHTG_OK;
 }
