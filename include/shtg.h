@@ -27,8 +27,10 @@
  * - Y^T is the exact transpose of Y in the metric
  *   <a, c> = sum_l [a_l0 c_l0 + 2 Re sum_{m>0} conj(a_lm) c_lm]; every CG
  *   inner product and residual norm uses this metric.
- * - "precision" selects SHTG_FP64 (double / complex128 buffers) or
- *   SHTG_FP32 (float / complex64 buffers) for a transform.
+ * - "precision" selects SHTG_FP64 or SHTG_DF64 (double / complex128 buffers;
+ *   native FP64 or double-FP32 arithmetic in the Legendre sums) or SHTG_FP32
+ *   or SHTG_TC32 (float / complex64 buffers; CUDA cores or tensor cores in
+ *   the Legendre sums) for a transform.
  * - Device buffers are owned by the caller; the library never frees them.
  *   Plans own their tables and workspace.  No entry point allocates device
  *   memory after shtg_plan_create.  Calls on one plan must not overlap.
@@ -78,15 +80,17 @@ extern "C" {
 #define SHTG_SPIN2 2                 /* plan flag: also spin-2 (Q, U) transforms */
 
 #define SHTG_CG_FP64 0               /* plain FP64 PCG */
-#define SHTG_CG_MIXED 1              /* FP32 PCG inside FP64 iterative refinement */
+#define SHTG_CG_MIXED 1              /* FP32 PCG inside FP64-accurate iterative refinement
+                                        (residual replacement; arithmetic: fp64_arith) */
 #define SHTG_CG_MIXED_TC 2           /* as SHTG_CG_MIXED with the FP32 operator's Legendre
                                         sums on the tensor cores (SHTG_TC32) */
 
 #define SHTG_ARITH_DEFAULT 0         /* shtg_cg_opts.fp64_arith */
 #define SHTG_ARITH_FP64 1            /* native FP64 multiply-adds */
-#define SHTG_ARITH_DF64 2            /* double-FP32 (hi + lo float pairs, ~2^-47 relative per
-                                        operation) on the FP32 pipe, FP64 storage; same results
-                                        as SHTG_ARITH_FP64 to ~1e-13 relative */
+#define SHTG_ARITH_DF64 2            /* Legendre sums in double-FP32 (hi + lo float pairs, ~2^-47
+                                        relative per operation) on the FP32 pipe, FP64 storage and
+                                        FP64 ring FFTs; the transforms agree with SHTG_ARITH_FP64
+                                        to 1e-12 relative (tested) */
 
 #define SHTG_HOST_INPUTS 1           /* cg_sample flag: problem maps/alm and output are host pointers */
 #define SHTG_PROFILE 2               /* cg_sample flag: time kernel classes with CUDA events */
