@@ -48,7 +48,7 @@ __device__ __forceinline__ dfc4 dfc4_from(double4_32a v) {
 
 template <int NR> struct DfPair {
     int pr[NR];
-    df u[NR], w[NR];   // u = 1 - cos theta, w = cos theta
+    df u[NR];   // u = 1 - cos theta
     int ls[NR], lsb[NR];
     df s0[NR], s1[NR], s2[NR], s3[NR];
     df a1[NR], a2[NR], b1[NR], b2[NR];
@@ -59,7 +59,6 @@ __device__ __forceinline__ void df_pair_reset(DfPair<NR> &S, int j, int L) {
     S.a1[j] = S.a2[j] = S.b1[j] = S.b2[j] = df_zero();
     S.s0[j] = S.s1[j] = S.s2[j] = S.s3[j] = df_zero();
     S.u[j] = df_make(1.f, 0.f);
-    S.w[j] = df_zero();
     S.ls[j] = S.lsb[j] = L + 1;
 }
 
@@ -71,7 +70,6 @@ __device__ __forceinline__ void df_pair_load(const LegArgs<double> &a, int m, in
     if (pr >= a.npairs) return;
     const double u = a.u[pr];
     S.u[j] = df_from(u);
-    S.w[j] = df_from(1.0 - u);
     const int64_t o = (int64_t)m * a.npairs + pr;
     if (SPIN == 2) {
         const int2 q = a.ls2[o];
@@ -90,12 +88,17 @@ __device__ __forceinline__ void df_pair_load(const LegArgs<double> &a, int m, in
     }
 }
 
-// spin 0: lambda_l = a cos(theta) lambda_{l-1} + b lambda_{l-2}
+// spin 0: lambda_l = a (1 - u) lambda_{l-1} + b lambda_{l-2}, formed as
+// t + b lambda_{l-2} - t u with t = a lambda_{l-1} (as the FP64 kernels do):
+// near the poles u ~ 1e-6 keeps its full relative precision, which a
+// rounded cos(theta) = 1 - u would not (2^-48 absolute on cos(theta) is
+// 1e-8 relative on u at the first HEALPix ring of N_side 1024)
 template <int NR, bool INJ>
 __device__ __forceinline__ void df_step0(DfPair<NR> &S, const dfc2 cf, int l) {
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
-        const df n = df_add(df_mul(df_mul(cf.a, S.w[j]), S.a1[j]), df_mul(cf.b, S.a2[j]));
+        const df t = df_mul(cf.a, S.a1[j]);
+        const df n = df_sub(df_add(t, df_mul(cf.b, S.a2[j])), df_mul(t, S.u[j]));
         S.a2[j] = S.a1[j];
         S.a1[j] = n;
         if (INJ && l == S.ls[j]) {

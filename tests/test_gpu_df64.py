@@ -140,3 +140,35 @@ def test_fp64_arith_rejects_unknown():
     with pytest.raises(ValueError):
         plan.cg_sample(np.ones(33), np.ones(33), torch.ones(plan.npix, dtype=torch.float64, device="cuda"),
                        z, w1, z, fp64_arith="quad")
+
+
+def test_df64_fullsize_sampled():
+    """N_side 1024, l_max 2048 (the benchmark geometry): double-FP32 maps on
+    sampled rings (polar, Bluestein, equatorial) and alm at sampled m within
+    1e-10 of the oracle computed for those rings / m only, spin 0 and 2."""
+    from tests.test_gpu_sht import FULL_RINGS, POLAR_RINGS, _ring_err
+    nside, L = 1024, 2048
+    plan, g = _plan_geom("healpix", nside, L, max_batch=1)
+    rng = np.random.default_rng(31)
+    lsc = np.ones(L + 1)
+    lsc[1:] = 1.0 / np.sqrt(np.arange(1, L + 1))
+    a = rand_alm(L, rng, (1,), lsc)
+    m = plan.alm2map(_c(a, torch.complex128), double_float=True).cpu().numpy()[0]
+    for rings in (FULL_RINGS, POLAR_RINGS):
+        assert _ring_err(m, g, rings, osht.alm2map(g.subset(rings), L, a[0])) < TOL, rings[:3]
+    mp = rng.normal(size=(1, g.npix))
+    ad = plan.alm2map_adjoint(_c(mp, torch.float64), double_float=True).cpu().numpy()[0]
+    mlist = [0, 1, 2, 700, 1500, 2047, 2048]
+    sel = np.isin(osht.ms_of(L), mlist)
+    assert rel_l2(ad[sel], osht.alm2map_adjoint(g, L, mp[0], mlist=mlist)[sel]) < TOL
+    eb = rand_alm(L, rng, (1, 2), lsc)
+    qu = plan.alm2map(_c(eb, torch.complex128), spin=2, double_float=True).cpu().numpy()[0]
+    for rings in (FULL_RINGS, POLAR_RINGS):
+        Q, U = osht.alm2map_spin2(g.subset(rings), L, eb[0, 0], eb[0, 1])
+        assert _ring_err(qu, g, rings, np.stack([Q, U])) < TOL, rings[:3]
+    mp2 = rng.normal(size=(1, 2, g.npix))
+    ad2 = plan.alm2map_adjoint(_c(mp2, torch.float64), spin=2, double_float=True).cpu().numpy()[0]
+    ml2 = [0, 1, 2, 1000, 2048]
+    E, B = osht.alm2map_spin2_adjoint(g, L, mp2[0, 0], mp2[0, 1], mlist=ml2)
+    sel2 = np.isin(osht.ms_of(L), ml2)
+    assert rel_l2(ad2[:, sel2], np.stack([E[sel2], B[sel2]])) < TOL
