@@ -162,7 +162,7 @@ using namespace shtg;
 
 extern "C" {
 
-int shtg_version(void) { return 1; }
+int shtg_version(void) { return 2; }
 
 const char *shtg_last_error_string(void) { return g_err.c_str(); }
 
