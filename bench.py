@@ -133,11 +133,11 @@ class Clocks:
 
 # ------------------------------------------------------------------ inputs
 def make_inputs(plan, device, seed_shift=0):
-    """Config-4 recipe drawn on the device; d = Y B a + n with the library's own
-    FP64 synthesis."""
+    """T+E+B workload (8 realizations, N_side 1024, l_max 2048) drawn on the
+    device; d = Y B a + n with the library's own FP64 synthesis."""
     import torch
     from inputs import configs as C
-    probs = C.config(4, batch=NB, nside=NSIDE, lmax=LMAX, device=device)
+    probs = C.teb_realizations(NB, NSIDE, LMAX, device=device)
     if seed_shift:
         # a replica on another rank draws fresh white noise (independent chains)
         from inputs import philox as px
@@ -514,23 +514,23 @@ def measure_extras(plan, inp, dev, kw, full_solve=True):
     if "mixed_full_solve" in ex:
         fs = ex["mixed_full_solve"]
         # FP64 PCG needs about as many iterations as the mixed solver (they
-        # agree to within 3 % on the config-1 recipe); the FP64 form's time to
+        # agree to within 3 % on the masked temperature workload); the FP64 form's time to
         # 1e-6 is extrapolated from its measured per-iteration time
         ex["fp64_form"]["time_to_1e-6_s_extrapolated"] = st["ms_rhs"] / 1000.0 + fs["iterations"] * per_it
         ex["mixed_speedup_time_to_1e-6"] = ex["fp64_form"]["time_to_1e-6_s_extrapolated"] / fs["time_to_1e-6_s"]
-    ex["c2_chains"] = measure_chains(dev)
+    ex["chains"] = measure_chains(dev)
     return ex
 
 
 def measure_chains(dev, nchains=64):
-    """Config-2 recipe: 64 independent chains with N_side in {64, 128, 256},
+    """Mixed-geometry chains: 64 independent chains with N_side in {64, 128, 256},
     l_max in {2 N_side, 3 N_side - 1} and their own signal amplitudes, all
     solved to 1e-6 in one chains call (one plan per geometry)."""
     import torch
     from inputs import configs as C
     from paper_2306_15511_gb300 import Plan, chains_sample
     groups = {}
-    for ch in C.config(2, batch=nchains):
+    for ch in C.mixed_geometry_chains(nchains):
         groups.setdefault((ch.nside, ch.lmax), []).append(ch)
     req = []
     for (ns, L), chs in sorted(groups.items()):

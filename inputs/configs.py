@@ -204,112 +204,127 @@ def _sqrt_cl_cholesky(cl4: np.ndarray):
     return l11, l21, l22, np.sqrt(bb)
 
 
-def config(index: int, batch: int | None = None, lmax: int | None = None,
-           nside: int | None = None, device=None) -> Problem | list:
-    """Build one of the five workloads (0..4).
+def fullsky_temperature(nside: int = 32, lmax: int = 64) -> Problem:
+    """Full-sky temperature workload: flat C_l, 2 deg Gaussian beam, uniform
+    white noise of 10 uK, PCG tolerance 1e-8.  With uniform noise on the full
+    sky the solution has the closed form of Eqs. (hat_s_approx, hat_f_approx)."""
+    ns, L = nside, lmax
+    cl = cl_flat(L)
+    bl = gauss_beam(L, 2.0 * DEG)
+    npix = 12 * ns * ns
+    sigma = 10.0
+    ninv = np.full(npix, 1.0 / sigma ** 2)
+    a = np.sqrt(cl)[alm_lm(L)[0]] * white_alm(L, 0, px.STREAM_SIGNAL)
+    n = sigma * white_map(npix, 0, px.STREAM_NOISE)
+    w1 = white_alm(L, 1, px.STREAM_W1)
+    w2 = white_map(npix, 1, px.STREAM_W2)
+    return Problem("fullsky_t", ns, L, 1, cl, bl, ninv, a[None], n[None], w1[None], w2[None], 1e-8)
 
-    ``nside``/``lmax`` override the resolution (used for reduced-size parity
-    cases of the same recipe).  Config 2 returns a list of chains; config 4
-    returns ``batch`` problems (default 8) that share cl, beam and noise;
-    with ``device`` its random fields are torch tensors drawn on that device."""
-    if index == 0:
-        ns = nside or 32
-        L = lmax or 64
-        cl = cl_flat(L)
-        bl = gauss_beam(L, 2.0 * DEG)
-        npix = 12 * ns * ns
-        sigma = 10.0
-        ninv = np.full(npix, 1.0 / sigma ** 2)
-        a = np.sqrt(cl)[alm_lm(L)[0]] * white_alm(L, 0, px.STREAM_SIGNAL)
-        n = sigma * white_map(npix, 0, px.STREAM_NOISE)
-        w1 = white_alm(L, 1, px.STREAM_W1)
-        w2 = white_map(npix, 1, px.STREAM_W2)
-        return Problem("c0", ns, L, 1, cl, bl, ninv, a[None], n[None], w1[None], w2[None], 1e-8)
-    if index in (1, 3):
-        ns = nside or (256 if index == 1 else 512)
-        L = lmax or (512 if index == 1 else 1024)
-        seed = index
-        cl = cl_damped(L)
-        bl = gauss_beam(L, 30.0 * ARCMIN)
+
+def masked_temperature(nside: int = 256, lmax: int = 512, seed: int = 1) -> Problem:
+    """Masked temperature workload: damped C_l, 30' Gaussian beam, noise
+    20 uK / sqrt(hits), mask |b| < 20 deg plus 50 point-source holes of 1 deg,
+    PCG tolerance 1e-6.  ``seed`` selects the hole positions and the random
+    fields (the log-posterior workload uses seed 3)."""
+    ns, L = nside, lmax
+    cl = cl_damped(L)
+    bl = gauss_beam(L, 30.0 * ARCMIN)
+    z, phi = pixel_centres(ns)
+    hits = hits_proxy(z, phi)
+    sig = 20.0 / np.sqrt(hits)
+    masked = latitude_cut(z, 20.0) | point_source_holes(z, phi, 50, 1.0, seed)
+    ninv = np.where(masked, 0.0, 1.0 / sig ** 2)
+    a = np.sqrt(cl)[alm_lm(L)[0]] * white_alm(L, seed, px.STREAM_SIGNAL)
+    n = sig * white_map(z.size, seed, px.STREAM_NOISE)
+    w1 = white_alm(L, seed + 100, px.STREAM_W1)
+    w2 = white_map(z.size, seed + 100, px.STREAM_W2)
+    return Problem(f"masked_t.s{seed}", ns, L, 1, cl, bl, ninv, a[None], n[None], w1[None],
+                   w2[None], 1e-6, {"fsky": float(1.0 - masked.mean())})
+
+
+def logpost_temperature(nside: int = 512, lmax: int = 1024) -> Problem:
+    """Log-posterior workload: the masked temperature recipe with seed 3,
+    N_side 512 and l_max 1024 by default."""
+    return masked_temperature(nside, lmax, seed=3)
+
+
+def mixed_geometry_chains(nchains: int = 64, nside: int | None = None,
+                          lmax: int | None = None) -> list:
+    """Independent chains of uneven geometry: N_side drawn from {64, 128, 256},
+    l_max = 2 N_side or 3 N_side - 1, C_l amplitude in [0.8, 1.2], beam
+    60 / N_side deg, 15 uK uniform noise, mask |b| < 15 deg, tolerance 1e-6.
+    ``nside`` (and ``lmax``, default 2 N_side) give every chain one reduced
+    geometry for small tests."""
+    u = px.uniform(2, px.STREAM_CHAINS, 3 * nchains)
+    chains = []
+    for c in range(nchains):
+        ns = (64, 128, 256)[min(2, int(u[3 * c] * 3))]
+        L = 2 * ns if u[3 * c + 1] < 0.5 else 3 * ns - 1
+        if nside is not None:
+            ns = nside
+            L = lmax or 2 * ns
+        amp = 0.8 + 0.4 * u[3 * c + 2]
+        cl = amp * cl_flat(L)
+        bl = gauss_beam(L, (60.0 / ns) * DEG)
         z, phi = pixel_centres(ns)
-        hits = hits_proxy(z, phi)
-        sig = 20.0 / np.sqrt(hits)
-        masked = latitude_cut(z, 20.0) | point_source_holes(z, phi, 50, 1.0, seed)
-        ninv = np.where(masked, 0.0, 1.0 / sig ** 2)
-        a = np.sqrt(cl)[alm_lm(L)[0]] * white_alm(L, seed, px.STREAM_SIGNAL)
-        n = sig * white_map(z.size, seed, px.STREAM_NOISE)
-        w1 = white_alm(L, seed + 100, px.STREAM_W1)
-        w2 = white_map(z.size, seed + 100, px.STREAM_W2)
-        return Problem(f"c{index}", ns, L, 1, cl, bl, ninv, a[None], n[None], w1[None],
-                       w2[None], 1e-6, {"fsky": float(1.0 - masked.mean())})
-    if index == 2:
-        nch = batch or 64
-        u = px.uniform(2, px.STREAM_CHAINS, 3 * nch)
-        chains = []
-        for c in range(nch):
-            ns = (64, 128, 256)[min(2, int(u[3 * c] * 3))]
-            L = 2 * ns if u[3 * c + 1] < 0.5 else 3 * ns - 1
-            if nside is not None:
-                ns = nside
-                L = lmax or 2 * ns
-            amp = 0.8 + 0.4 * u[3 * c + 2]
-            cl = amp * cl_flat(L)
-            bl = gauss_beam(L, (60.0 / ns) * DEG)
-            z, phi = pixel_centres(ns)
-            masked = latitude_cut(z, 15.0)
-            sigma = 15.0
-            ninv = np.where(masked, 0.0, 1.0 / sigma ** 2)
-            key = 1000 + c
-            a = np.sqrt(cl)[alm_lm(L)[0]] * white_alm(L, key, px.STREAM_SIGNAL)
-            n = sigma * white_map(z.size, key, px.STREAM_NOISE)
-            w1 = white_alm(L, key, px.STREAM_W1)
-            w2 = white_map(z.size, key, px.STREAM_W2)
-            chains.append(Problem(f"c2.{c}", ns, L, 1, cl, bl, ninv, a[None], n[None],
-                                  w1[None], w2[None], 1e-6, {"amp": amp}))
-        return chains
-    if index == 4:
-        ns = nside or 1024
-        L = lmax or 2048
-        nb = batch or 8
-        tt = cl_damped(L)
-        ee = 0.05 * tt
-        te = 0.3 * np.sqrt(tt * ee)
-        bb = 1e-3 * ee
-        cl4 = np.stack([tt, ee, bb, te])
-        bl = gauss_beam(L, 10.0 * ARCMIN)
-        z, phi = pixel_centres(ns)
-        hits = hits_proxy(z, phi)
-        masked = latitude_cut(z, 20.0) | point_source_holes(z, phi, 200, 1.0, 4)
-        sig_t = 30.0 / np.sqrt(hits)
-        sig_p = 42.0 / np.sqrt(hits)
-        ninv = np.stack([np.where(masked, 0.0, 1.0 / sig_t ** 2),
-                         np.where(masked, 0.0, 1.0 / sig_p ** 2)])
-        l11, l21, l22, lbb = _sqrt_cl_cholesky(cl4)
-        ls = alm_lm(L)[0]
-        p = nalm(L)
-        out = []
-        if device is not None:
-            import torch
-            stack = torch.stack
-            cv = lambda x: torch.as_tensor(x, device=device)  # noqa: E731
-        else:
-            stack = np.stack
-            cv = lambda x: x  # noqa: E731
-        c11, c21, c22, cbb, cst, csp = (cv(l11[ls]), cv(l21[ls]), cv(l22[ls]), cv(lbb[ls]),
-                                        cv(sig_t), cv(sig_p))
-        for b in range(nb):
-            key = 4000 + b
-            wt = white_alm(L, key, px.STREAM_SIGNAL, 0, device)
-            we = white_alm(L, key, px.STREAM_SIGNAL, 2 * p, device)
-            wb = white_alm(L, key, px.STREAM_SIGNAL, 4 * p, device)
-            a = stack([c11 * wt, c21 * wt + c22 * we, cbb * wb])
-            npx = z.size
-            nmap = stack([cst * white_map(npx, key, px.STREAM_NOISE, 0, device),
-                          csp * white_map(npx, key, px.STREAM_NOISE, npx, device),
-                          csp * white_map(npx, key, px.STREAM_NOISE, 2 * npx, device)])
-            w1 = stack([white_alm(L, key, px.STREAM_W1, k * 2 * p, device) for k in range(3)])
-            w2 = stack([white_map(npx, key, px.STREAM_W2, k * npx, device) for k in range(3)])
-            out.append(Problem(f"c4.{b}", ns, L, 3, cl4, bl, ninv, a, nmap, w1, w2, 1e-6,
-                               {"fsky": float(1.0 - masked.mean())}))
-        return out
-    raise ValueError(f"unknown config {index}")
+        masked = latitude_cut(z, 15.0)
+        sigma = 15.0
+        ninv = np.where(masked, 0.0, 1.0 / sigma ** 2)
+        key = 1000 + c
+        a = np.sqrt(cl)[alm_lm(L)[0]] * white_alm(L, key, px.STREAM_SIGNAL)
+        n = sigma * white_map(z.size, key, px.STREAM_NOISE)
+        w1 = white_alm(L, key, px.STREAM_W1)
+        w2 = white_map(z.size, key, px.STREAM_W2)
+        chains.append(Problem(f"chain.{c}", ns, L, 1, cl, bl, ninv, a[None], n[None],
+                              w1[None], w2[None], 1e-6, {"amp": amp}))
+    return chains
+
+
+def teb_realizations(batch: int = 8, nside: int = 1024, lmax: int = 2048, device=None) -> list:
+    """T+E+B workload: ``batch`` realizations sharing C_l (damped TT,
+    EE = 0.05 TT, BB = 1e-3 EE, TE = 0.3 sqrt(TT EE)), a 10' beam and noise
+    30 / 42 uK / sqrt(hits) for T / Q, U, mask |b| < 20 deg plus 200 holes of
+    1 deg, tolerance 1e-6.  With ``device`` the random fields are torch
+    tensors drawn on that device."""
+    ns, L, nb = nside, lmax, batch
+    tt = cl_damped(L)
+    ee = 0.05 * tt
+    te = 0.3 * np.sqrt(tt * ee)
+    bb = 1e-3 * ee
+    cl4 = np.stack([tt, ee, bb, te])
+    bl = gauss_beam(L, 10.0 * ARCMIN)
+    z, phi = pixel_centres(ns)
+    hits = hits_proxy(z, phi)
+    masked = latitude_cut(z, 20.0) | point_source_holes(z, phi, 200, 1.0, 4)
+    sig_t = 30.0 / np.sqrt(hits)
+    sig_p = 42.0 / np.sqrt(hits)
+    ninv = np.stack([np.where(masked, 0.0, 1.0 / sig_t ** 2),
+                     np.where(masked, 0.0, 1.0 / sig_p ** 2)])
+    l11, l21, l22, lbb = _sqrt_cl_cholesky(cl4)
+    ls = alm_lm(L)[0]
+    p = nalm(L)
+    out = []
+    if device is not None:
+        import torch
+        stack = torch.stack
+        cv = lambda x: torch.as_tensor(x, device=device)  # noqa: E731
+    else:
+        stack = np.stack
+        cv = lambda x: x  # noqa: E731
+    c11, c21, c22, cbb, cst, csp = (cv(l11[ls]), cv(l21[ls]), cv(l22[ls]), cv(lbb[ls]),
+                                    cv(sig_t), cv(sig_p))
+    for b in range(nb):
+        key = 4000 + b
+        wt = white_alm(L, key, px.STREAM_SIGNAL, 0, device)
+        we = white_alm(L, key, px.STREAM_SIGNAL, 2 * p, device)
+        wb = white_alm(L, key, px.STREAM_SIGNAL, 4 * p, device)
+        a = stack([c11 * wt, c21 * wt + c22 * we, cbb * wb])
+        npx = z.size
+        nmap = stack([cst * white_map(npx, key, px.STREAM_NOISE, 0, device),
+                      csp * white_map(npx, key, px.STREAM_NOISE, npx, device),
+                      csp * white_map(npx, key, px.STREAM_NOISE, 2 * npx, device)])
+        w1 = stack([white_alm(L, key, px.STREAM_W1, k * 2 * p, device) for k in range(3)])
+        w2 = stack([white_map(npx, key, px.STREAM_W2, k * npx, device) for k in range(3)])
+        out.append(Problem(f"teb.{b}", ns, L, 3, cl4, bl, ninv, a, nmap, w1, w2, 1e-6,
+                           {"fsky": float(1.0 - masked.mean())}))
+    return out

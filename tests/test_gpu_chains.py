@@ -1,4 +1,4 @@
-"""Chains of uneven geometry in one call (the config-2 recipe: per-chain
+"""Chains of uneven geometry in one call (the mixed-geometry chains: per-chain
 N_side, l_max and signal amplitude), through the C ABI, against the FP64
 oracle: every chain's oracle-evaluated residual meets the tolerance, and the
 per-realization amplitude gives the same solution as a separate solve with
@@ -22,7 +22,7 @@ def _cuda(x, dt):
 def _groups(max_per_group=4):
     """The recipe's first chains with N_side 64 (l_max 128 or 191) or N_side
     128 with l_max 256, grouped by geometry."""
-    chains = C.config(2, batch=64)
+    chains = C.mixed_geometry_chains(64)
     keep = {}
     for ch in chains:
         key = (ch.nside, ch.lmax)
@@ -36,7 +36,7 @@ def _data(ch, g):
     return osht.alm2map(g, ch.lmax, ch.signal_alm[0] * ch.bl[ls]) + ch.noise_map[0]
 
 
-def test_c2_chains_of_uneven_geometry():
+def test_chains_of_uneven_geometry():
     from paper_2306_15511_gb300 import Plan, chains_sample
     groups = _groups()
     assert len(groups) >= 2

@@ -118,7 +118,7 @@ def test_solver_fp64_arith(mode, arith):
     """T+E+B recipe at N_side 32, l_max 64 (masked): the oracle-evaluated
     residual meets 1e-6 with the FP64-accurate steps in either arithmetic."""
     from paper_2306_15511_gb300 import Plan
-    p = C.config(4, nside=32, lmax=64, batch=1)[0]
+    p = C.teb_realizations(1, 32, 64)[0]
     g = osht.healpix(p.nside)
     d = _data(p, g)
     prob = osol.Problem(g, p.lmax, p.cl, p.bl, p.ninv)

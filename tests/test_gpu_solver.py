@@ -38,10 +38,10 @@ def _solve_gpu(plan, p, d, mode, tol, **kw):
 
 
 @pytest.mark.parametrize("mode", ["fp64", "mixed"])
-def test_c0_solution(mode):
-    """Config 0 (N_side 32, l_max 64, full sky): PCG to 1e-8."""
+def test_fullsky_solution(mode):
+    """Full-sky temperature workload (N_side 32, l_max 64): PCG to 1e-8."""
     from paper_2306_15511_gb300 import Plan
-    p = C.config(0)
+    p = C.fullsky_temperature()
     g = osht.healpix(p.nside)
     d = _data(p, g)
     prob = osol.Problem(g, p.lmax, p.cl, p.bl, p.ninv)
@@ -58,7 +58,7 @@ def test_c0_solution(mode):
 def test_operator_and_rhs_parity():
     """apply_operator (FP64) against the oracle matvec on a masked problem."""
     from paper_2306_15511_gb300 import Plan
-    p = C.config(1, nside=64, lmax=128)
+    p = C.masked_temperature(64, 128)
     g = osht.healpix(64)
     prob = osol.Problem(g, 128, p.cl, p.bl, p.ninv)
     rng = np.random.default_rng(0)
@@ -70,11 +70,11 @@ def test_operator_and_rhs_parity():
 
 
 @pytest.mark.parametrize("mode", ["fp64", "mixed"])
-def test_masked_c1_recipe_reduced(mode):
-    """Config 1 recipe (hits-weighted noise, |b| < 20 deg + 50 holes) at
+def test_masked_temperature_reduced(mode):
+    """Masked temperature workload (hits-weighted noise, |b| < 20 deg + 50 holes) at
     N_side 128, l_max 256: residual gate through the oracle."""
     from paper_2306_15511_gb300 import Plan
-    p = C.config(1, nside=128, lmax=256)
+    p = C.masked_temperature(128, 256)
     g = osht.healpix(128)
     d = _data(p, g)
     prob = osol.Problem(g, p.lmax, p.cl, p.bl, p.ninv)
@@ -87,9 +87,9 @@ def test_masked_c1_recipe_reduced(mode):
 
 
 def test_teb_mixed_small():
-    """T+E+B (config 4 recipe at N_side 16, l_max 32), mixed precision."""
+    """T+E+B workload at N_side 16, l_max 32, mixed precision."""
     from paper_2306_15511_gb300 import Plan
-    p = C.config(4, nside=16, lmax=32, batch=2)
+    p = C.teb_realizations(2, 16, 32)
     g = osht.healpix(16)
     plan = Plan(nside=16, lmax=32, max_batch=2, spin2=True)
     ds = np.stack([_data(q, g) for q in p])
@@ -109,7 +109,7 @@ def test_teb_mixed_small():
 
 def test_host_inputs_match_device_inputs():
     from paper_2306_15511_gb300 import Plan
-    p = C.config(0, nside=16, lmax=32)
+    p = C.fullsky_temperature(16, 32)
     g = osht.healpix(16)
     d = _data(p, g)
     plan = Plan(nside=16, lmax=32)
@@ -122,10 +122,10 @@ def test_host_inputs_match_device_inputs():
 
 
 def test_logpost_gradient_vs_oracle():
-    """Config 3 recipe reduced to N_side 64, l_max 128: log-posterior and its
+    """Log-posterior workload reduced to N_side 64, l_max 128: log-posterior and its
     gradients (FP32 transforms) against the FP64 oracle."""
     from paper_2306_15511_gb300 import Plan
-    p = C.config(3, nside=64, lmax=128)
+    p = C.logpost_temperature(64, 128)
     g = osht.healpix(64)
     L = p.lmax
     d = _data(p, g)[0]
@@ -155,7 +155,7 @@ def test_autograd_alm2map_and_logposterior():
     ref = plan.alm2map_vjp(w)
     assert torch.allclose(a.grad, ref)
     # log-posterior: autograd gradient w.r.t. theta equals the binned formula
-    p = C.config(3, nside=16, lmax=32)
+    p = C.logpost_temperature(16, 32)
     g = osht.healpix(16)
     d = _data(p, g)[0]
     bins = [(2, 11), (12, 21), (22, 32)]
@@ -176,7 +176,7 @@ def test_graph_replay_matches_eager(mode):
     """The captured-and-replayed PCG iteration gives the same solution, bit for
     bit, as eager launches (same kernels in the same order)."""
     from paper_2306_15511_gb300 import Plan
-    p = C.config(4, nside=16, lmax=32, batch=2)
+    p = C.teb_realizations(2, 16, 32)
     g = osht.healpix(16)
     plan = Plan(nside=16, lmax=32, max_batch=2, spin2=True)
     ds = np.stack([_data(q, g) for q in p])

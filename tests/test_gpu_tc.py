@@ -211,10 +211,10 @@ def _cuda(x, dt):
 
 
 def test_mixed_tc_solve_masked():
-    """Config 1 recipe at N_side 128, l_max 256 (mask + hits noise): the
+    """Masked temperature workload at N_side 128, l_max 256 (mask + hits noise): the
     tensor-core inner solver reaches the FP64 residual gate."""
     from paper_2306_15511_gb300 import Plan
-    p = C.config(1, nside=128, lmax=256)
+    p = C.masked_temperature(128, 256)
     g = osht.healpix(128)
     d = _data(p, g)
     prob = osol.Problem(g, p.lmax, p.cl, p.bl, p.ninv)
@@ -229,7 +229,7 @@ def test_mixed_tc_solve_masked():
 
 def test_mixed_tc_teb():
     from paper_2306_15511_gb300 import Plan
-    p = C.config(4, nside=16, lmax=32, batch=2)
+    p = C.teb_realizations(2, 16, 32)
     g = osht.healpix(16)
     plan = Plan(nside=16, lmax=32, max_batch=2, spin2=True)
     ds = np.stack([_data(q, g) for q in p])

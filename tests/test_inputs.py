@@ -49,12 +49,12 @@ def test_pixel_centres_counts():
 
 
 def test_config_shapes_small():
-    p = C.config(1, nside=16, lmax=32)
+    p = C.masked_temperature(16, 32)
     assert p.ninv.shape == (12 * 16 * 16,)
     fsky = p.extra["fsky"]
     assert 0.55 < fsky < 0.70          # |b| < 20 deg removes sin(20 deg) = 34 %
-    p4 = C.config(4, nside=8, lmax=16, batch=2)
+    p4 = C.teb_realizations(2, 8, 16)
     assert len(p4) == 2 and p4[0].signal_alm.shape == (3, C.nalm(16))
     assert p4[0].ninv.shape == (2, 12 * 64)
-    ch = C.config(2, batch=4, nside=8, lmax=16)
+    ch = C.mixed_geometry_chains(4, 8, 16)
     assert len(ch) == 4

@@ -19,7 +19,7 @@ def _rand_alm(L, rng, ncomp=1):
     return a
 
 
-# ----------------------------------------------------------------- dense (P7)
+# ----------------------------------------------------------------- dense
 def _real_params(L):
     ls, ms = sht.ls_of(L), sht.ms_of(L)
     cols = []
@@ -98,7 +98,7 @@ def test_operator_symmetric_spin2():
     assert prob.dot(x, ax) > 0
 
 
-# ----------------------------------------------------------- closed form (P5)
+# ----------------------------------------------------------- closed form
 def test_fullsky_closed_form_gl():
     """Uniform noise on an exact-quadrature grid: A = diag(1/C + b^2/N_l) with
     N_l = 4 pi sigma^2 / N_pix, and the solution is Eqs. (hat_s_approx) +
@@ -157,7 +157,7 @@ def test_fullsky_closed_form_teb_gl():
     assert np.max(np.abs(x - ref)) < 1e-10 * np.max(np.abs(ref))
 
 
-# ------------------------------------------------ constant-latitude mask (P6)
+# ------------------------------------------------ constant-latitude mask
 def test_constant_latitude_mask_block_structure():
     """App. A: for a mask |b| < b0 and uniform noise the operator is
     block-diagonal in m, and within a block entries with l + l' odd vanish.
@@ -196,9 +196,9 @@ def test_constant_latitude_mask_block_structure():
     assert np.max(np.abs(Av[0, ms != 3])) < 1e-13 * np.max(np.abs(Av))
 
 
-# ----------------------------------------------------------- linearity (P9)
+# ----------------------------------------------------------- linearity
 def test_mean_field_plus_fluctuation():
-    p = C.config(0, nside=8, lmax=16)
+    p = C.fullsky_temperature(8, 16)
     g = sht.healpix(8)
     prob = solver.Problem(g, 16, p.cl, p.bl, p.ninv)
     d = sht.alm2map(g, 16, p.signal_alm[0] * p.bl[sht.ls_of(16)]) + p.noise_map[0]
@@ -209,8 +209,8 @@ def test_mean_field_plus_fluctuation():
     assert np.max(np.abs(xs[0] + xs[1] - xs[2])) < 1e-10 * np.max(np.abs(xs[2]))
 
 
-def test_c0_pcg_converges():
-    p = C.config(0)
+def test_fullsky_pcg_converges():
+    p = C.fullsky_temperature()
     g = sht.healpix(p.nside)
     L = p.lmax
     prob = solver.Problem(g, L, p.cl, p.bl, p.ninv)
@@ -222,11 +222,11 @@ def test_c0_pcg_converges():
     assert 1 <= it < 200
 
 
-# ----------------------------------------------------------- gradient (P8)
+# ----------------------------------------------------------- gradient
 def test_log_posterior_gradient_fd():
     L, nside = 12, 8
     g = sht.healpix(nside)
-    p = C.config(1, nside=nside, lmax=L)
+    p = C.masked_temperature(nside, L)
     prob = solver.Problem(g, L, p.cl, p.bl, p.ninv)
     d = sht.alm2map(g, L, p.signal_alm[0] * p.bl[sht.ls_of(L)]) + p.noise_map[0]
     rng = np.random.default_rng(9)
