@@ -1,0 +1,108 @@
+"""Host-side parts of bench.py (no GPU): the CPU-baseline extrapolation, the
+reference arm's JSON line and the flop counts behind the rooflines."""
+import argparse
+import json
+import time
+
+import pytest
+
+import bench
+
+
+class _FakeProblem:
+    """Stands in for the oracle's operator: one application costs
+    a + b x (rings in the subset) seconds."""
+
+    def __init__(self, nsub, a, b):
+        self.cost = a + b * nsub
+
+    def matvec(self, x):
+        time.sleep(self.cost)
+
+
+def test_oracle_fit_separates_ring_independent_work(monkeypatch):
+    a, b, nring = 0.05, 4e-4, 4095
+
+    def fake_problem(stride):
+        nsub = len(range(0, nring, stride))
+        return _FakeProblem(nsub, a, b), None, nring, nsub
+
+    monkeypatch.setattr(bench, "_oracle_problem", fake_problem)
+    r = bench.oracle_sample(strides=(32, 8))
+    expect = 1.0 / ((a + b * nring) * bench.NB)
+    # sleep() overshoots by up to a few ms per sample
+    assert r["value"] == pytest.approx(expect, rel=0.15)
+    assert r["kind"] == "oracle" and r["unit"] == bench.UNIT and r["cores"] >= 1
+    assert "fitted a + b x rings" in r["sample"]
+    # scaling the whole denser sample by the ring ratio would count a about 8 times
+    naive = 1.0 / ((a + b * 512) * (nring / 512) * bench.NB)
+    assert r["value"] > 1.15 * naive
+
+
+def test_oracle_fit_falls_back_on_noisy_samples(monkeypatch):
+    # the sparser subset measured slower than the denser one: no negative slope
+    costs = {128: 0.03, 512: 0.02}
+
+    class P:
+        def __init__(self, n):
+            self.n = n
+
+        def matvec(self, x):
+            time.sleep(costs[self.n])
+
+    def fake_problem(stride):
+        nsub = 128 if stride == 32 else 512
+        return P(nsub), None, 4095, nsub
+
+    monkeypatch.setattr(bench, "_oracle_problem", fake_problem)
+    r = bench.oracle_sample(strides=(32, 8))
+    assert r["value"] > 0.0
+    assert r["value"] == pytest.approx(1.0 / (0.02 * 4095 / 512 * bench.NB), rel=0.3)
+
+
+def _fake_sample(**kw):
+    return {"value": 2.5e-3, "unit": bench.UNIT, "cores": 16, "kind": "oracle", "sample": "fake"}
+
+
+def test_reference_line_contract(monkeypatch, capsys):
+    monkeypatch.setattr(bench, "oracle_sample", _fake_sample)
+    monkeypatch.delenv("RANK", raising=False)
+    args = argparse.Namespace(steps=2, warmup=3, gpus=1)
+    assert bench.run_reference(args) == 0
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference"
+    assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
+    assert d["value"] == pytest.approx(2.5e-3)
+    assert d["ms_per_step"] == pytest.approx(1000.0 / 2.5e-3)
+    assert d["higher_is_better"] is True and d["vs_baseline"] is None
+    assert d["steps"] == 2 and d["warmup"] == 3
+    assert "workload" in d["config"]
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] == 16
+    e = d["e2e"]
+    assert e["value"] == d["value"] and e["unit"] == d["unit"]
+    assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_reference_other_ranks_print_nothing(monkeypatch, capsys):
+    monkeypatch.setattr(bench, "oracle_sample", _fake_sample)
+    monkeypatch.setenv("RANK", "1")
+    assert bench.run_reference(argparse.Namespace(steps=2, warmup=3, gpus=2)) == 0
+    assert capsys.readouterr().out.strip() == ""
+
+
+def test_flop_counts_and_alu_peaks():
+    # per (l, m, ring pair): 4 flops per temperature map, 16 per (Q, U) pair
+    assert bench.contraction_flops(10, 3, 2, 1) == 10 * 3 * (4 * 2 + 16 * 1)
+    # plus the recurrence: 3 shared (spin 0) and 8 shared (spin 2)
+    assert bench.legendre_flops(10, 3, 2, 1) == 10 * 3 * ((3 + 4 * 2) + (8 + 16 * 1))
+    assert bench.legendre_flops(10, 3, 2, 0) == 10 * 3 * (3 + 4 * 2)
+    fp32, fp64 = bench.alu_peaks(2070.0)
+    assert fp32 == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
+    assert fp64 == pytest.approx(1.25)
