@@ -114,8 +114,11 @@ typedef struct {
  * up to max_batch maps (max_batch realizations of T, or of T+E+B when flags
  * has SHTG_SPIN2).  For SHTG_GEOM_GAUSS, nphi_gauss >= 2 lmax + 1 makes the
  * quadrature exact; it is ignored for HEALPix.  flags: SHTG_SPIN0 and/or
- * SHTG_SPIN2.  lmax <= 4 N_side (HEALPix).  Returns SHTG_ERR_NOMEM if device
- * memory is insufficient.  Sets *out on success. */
+ * SHTG_SPIN2.  Limits (SHTG_ERR_ARG outside them): 0 <= lmax <= 8192,
+ * 1 <= max_batch <= 4096; HEALPix 1 <= N_side <= 8192 and lmax <= 4 N_side;
+ * Gauss-Legendre 1 <= rings <= 65536 and 1 <= nphi_gauss <= 65536; every
+ * ring's FFT length within the ring stage's supported range.  Returns
+ * SHTG_ERR_NOMEM if device memory is insufficient.  Sets *out on success. */
 int shtg_plan_create(int geom, int nside_or_nring, int nphi_gauss, int lmax, int max_batch,
                      int flags, shtg_plan **out);
 int shtg_plan_destroy(shtg_plan *plan);
@@ -163,9 +166,10 @@ int shtg_map2alm(shtg_plan *plan, int spin, int precision, const void *map, void
  * on a HEALPix plan, without a plan: map [12 nside^2] float64 and alm [nalm]
  * complex128 are device buffers owned by the caller; the ring geometry and
  * the Legendre recurrence are computed on the fly and the per-ring Fourier
- * sums go to a static 16 MiB device buffer inside the library.  Sizes with
+ * sums go to a static 16 MiB device buffer inside the library.  Needs
+ * 1 <= nside <= 8192, 0 <= lmax <= 4 nside and non-null buffers; sizes with
  * (4 nside - 1) (lmax + 1) 16 bytes > 16 MiB (e.g. nside 512, lmax 1024)
- * return SHTG_ERR_ARG.  The first call on a device looks the buffer's device
+ * return SHTG_ERR_ARG like any other invalid argument.  The first call on a device looks the buffer's device
  * address up (cudaGetSymbolAddress); make that first call before any stream
  * capture.  Every call on a device shares the buffer: calls whose kernels may
  * overlap on the GPU race on it.  Allocates nothing. */

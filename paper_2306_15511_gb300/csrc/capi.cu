@@ -177,8 +177,8 @@ int shtg_plan_create(int geom, int nside_or_nring, int nphi_gauss, int lmax, int
         set_error("unknown geometry");
         return SHTG_ERR_ARG;
     }
-    if (lmax < 0 || lmax > 8192 || max_batch < 1 || nside_or_nring < 1) {
-        set_error("invalid lmax, max_batch or resolution");
+    if (lmax < 0 || lmax > 8192 || max_batch < 1 || max_batch > 4096 || nside_or_nring < 1) {
+        set_error("need 0 <= lmax <= 8192, 1 <= max_batch <= 4096 and a positive resolution");
         return SHTG_ERR_ARG;
     }
     if (geom == SHTG_GEOM_HEALPIX && (nside_or_nring > 8192 || lmax > 4 * nside_or_nring)) {

@@ -157,8 +157,8 @@ using namespace shtg;
 
 extern "C" int shtg_alm2map_adjoint_noalloc(int nside, int lmax, const double *map, double *alm,
                                             void *stream) {
-    if (nside < 1 || lmax < 0 || lmax > 4 * nside || !map || !alm) {
-        set_error("noalloc adjoint: need nside >= 1, 0 <= lmax <= 4 nside and non-null buffers");
+    if (nside < 1 || nside > 8192 || lmax < 0 || lmax > 4 * nside || !map || !alm) {
+        set_error("noalloc adjoint: need 1 <= nside <= 8192, 0 <= lmax <= 4 nside and non-null buffers");
         return SHTG_ERR_ARG;
     }
     const long long nring = 4LL * nside - 1;

@@ -75,3 +75,60 @@ def test_binding_constants_match_header():
     body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
     fields = re.findall(r"\b(?:int|double)\s+(\w+)\s*;", body)
     assert fields == [f for f, _ in N.CGOpts._fields_]
+
+
+def test_plan_create_limits_without_gpu():
+    """Every documented limit of shtg_plan_create is checked before any CUDA
+    call, so invalid plans fail with SHTG_ERR_ARG even without a GPU."""
+    from paper_2306_15511_gb300 import _native as N
+    lib = N.load()
+    H, G = 0, 1   # SHTG_GEOM_HEALPIX, SHTG_GEOM_GAUSS
+    bad = [
+        (H, 8, 0, -1, 1),        # lmax < 0
+        (H, 8, 0, 8193, 1),      # lmax > 8192
+        (H, 8, 0, 16, 0),        # max_batch < 1
+        (H, 8, 0, 16, 4097),     # max_batch > 4096
+        (H, 0, 0, 0, 1),         # N_side < 1
+        (H, 8193, 0, 16, 1),     # N_side > 8192
+        (H, 8, 0, 33, 1),        # lmax > 4 N_side
+        (G, 16, 0, 8, 1),        # nphi_gauss < 1
+        (G, 16, 65537, 8, 1),    # nphi_gauss > 65536
+        (G, 65537, 32, 8, 1),    # rings > 65536
+        (5, 8, 0, 16, 1),        # unknown geometry
+    ]
+    for geom, n, nphi, lmax, mb in bad:
+        h = ctypes.c_void_p(7)
+        rc = lib.shtg_plan_create(geom, n, nphi, lmax, mb, N.SPIN0, ctypes.byref(h))
+        assert rc == -1, (geom, n, nphi, lmax, mb, rc)
+        assert h.value is None, "a failed create must clear *out"
+        assert lib.shtg_last_error_string()
+    assert lib.shtg_plan_create(H, 8, 0, 16, 1, N.SPIN0, None) == -1
+
+
+def test_transform_and_solver_calls_reject_null_plans_without_gpu():
+    from paper_2306_15511_gb300 import _native as N
+    lib = N.load()
+    buf = ctypes.c_void_p(16)   # never dereferenced: the plan check comes first
+    for f in (lib.shtg_alm2map, lib.shtg_alm2map_adjoint, lib.shtg_alm2map_vjp):
+        assert f(None, 0, N.FP64, buf, buf, 1, None) == -1
+    assert lib.shtg_map2alm(None, 0, N.FP64, buf, buf, 1, 0, None) == -1
+    pr, o, st = N.Problem(), N.CGOpts(), N.CGStats()
+    assert lib.shtg_cg_sample(None, ctypes.byref(pr), buf, ctypes.byref(o), ctypes.byref(st),
+                              None) == -1
+    assert lib.shtg_apply_operator(None, ctypes.byref(pr), buf, buf, None) == -1
+    info = N.PlanInfo()
+    assert lib.shtg_plan_get_info(None, ctypes.byref(info)) == -1
+    assert lib.shtg_plan_destroy(None) == N.SHTG_OK
+
+
+def test_noalloc_rejects_invalid_sizes_without_gpu():
+    from paper_2306_15511_gb300 import _native as N
+    lib = N.load()
+    f = lib.shtg_alm2map_adjoint_noalloc
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    buf = ctypes.c_void_p(16)
+    for nside, lmax, a, b in [(0, 0, buf, buf), (8193, 16, buf, buf), (8, -1, buf, buf),
+                              (8, 33, buf, buf), (8, 16, None, buf), (8, 16, buf, None),
+                              (512, 1024, buf, buf)]:     # scratch above 16 MiB
+        assert f(nside, lmax, a, b, None) == -1, (nside, lmax)
+        assert b"noalloc" in lib.shtg_last_error_string()
