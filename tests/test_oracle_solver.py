@@ -1,7 +1,8 @@
 """Pins for the oracle solver (no GPU): dense brute force, the paper's
 full-sky closed form, the constant-latitude-mask block structure of App. A,
-linearity of Eqs. (mean-field-map)/(fluc-map), and finite differences of the
-log-posterior gradient."""
+linearity of Eqs. (mean-field-map)/(fluc-map), finite differences of the
+log-posterior gradient, and the diagonal preconditioner against the
+operator's own diagonal."""
 import math
 
 import numpy as np
@@ -250,3 +251,61 @@ def test_log_posterior_gradient_fd():
             return solver.log_posterior(prob, a, d, cl_scale=sc)
         fd = (lp(h) - lp(-h)) / (2 * h)
         assert abs(fd - gl[k]) < 1e-5 * max(1.0, abs(gl[k]))
+
+
+# ---------------------------------------------------- preconditioner diagonal
+@pytest.mark.parametrize("ncomp", [1, 3])
+def test_precond_diag_is_the_operator_diagonal(ncomp):
+    """M = S^-1 + b_l^2 D_lm (Sect. 4's diagonal preconditioner) against the
+    diagonal of A read off the operator itself, for an arbitrary N^-1 (holes,
+    no ring symmetry).  |Y_lm(p)|^2 does not depend on phi, so D_lm is the
+    mean of the real-part and imaginary-part diagonal entries of
+    Y^T N^-1 Y (their e^{2 i m phi} terms cancel); for m = 0 only the real
+    part exists.  The T-E entries of M are the prior's; the noise couples no
+    T and E (different maps)."""
+    L, nside = 8, 4
+    g = sht.healpix(nside)
+    rng = np.random.default_rng(3)
+    npix = g.npix
+    ninv = rng.uniform(0.5, 2.0, size=(2, npix)) * (rng.uniform(size=(2, npix)) > 0.2)
+    ls = np.arange(L + 1)
+    tt = np.where(ls >= 2, 1.0 / np.maximum(ls * (ls + 1.0), 1.0), 0.0)
+    if ncomp == 1:
+        cl, nv = tt, ninv[0]
+    else:
+        ee = 0.3 * tt
+        cl, nv = np.stack([tt, ee, 0.1 * ee, 0.4 * np.sqrt(tt * ee)]), ninv
+    bl = np.exp(-0.01 * ls * (ls + 1))
+    prob = solver.Problem(g, L, cl, bl, nv)
+    M = prob.precond_diag()
+    P = (L + 1) * (L + 2) // 2
+    ms = sht.ms_of(L)
+    for c in range(ncomp):
+        for j in range(P):
+            e = np.zeros((ncomp, P), complex)
+            e[c, j] = 1.0
+            Are = prob.matvec(e)
+            d = Are[c, j].real
+            if ms[j] > 0:
+                e[c, j] = 1j
+                d = 0.5 * (d + prob.matvec(e)[c, j].imag)
+            assert d == pytest.approx(M[c, c, j], rel=1e-12, abs=1e-12), (c, j)
+            if ncomp == 3 and c == 1:
+                assert Are[0, j].real == pytest.approx(M[0, 1, j], rel=1e-12, abs=1e-14), j
+
+
+def test_apply_block_inverse_solves_each_block():
+    """z = M^-1 r per alm index: multiplying back gives r, for 1x1 and for
+    3x3 symmetric blocks with complex right-hand sides."""
+    rng = np.random.default_rng(4)
+    n = 37
+    r1 = rng.normal(size=(1, n)) + 1j * rng.normal(size=(1, n))
+    M1 = rng.uniform(0.5, 2.0, size=(1, 1, n))
+    z1 = solver.apply_block_inverse(M1, r1)
+    assert np.allclose(M1[0, 0] * z1[0], r1[0], rtol=1e-14, atol=0)
+    A = rng.normal(size=(n, 3, 3))
+    M3 = np.moveaxis(A @ np.swapaxes(A, 1, 2) + 3 * np.eye(3), 0, 2)    # SPD blocks
+    r3 = rng.normal(size=(3, n)) + 1j * rng.normal(size=(3, n))
+    z3 = solver.apply_block_inverse(M3, r3)
+    back = np.einsum("ijn,jn->in", M3, z3)
+    assert np.allclose(back, r3, rtol=0, atol=1e-12 * np.abs(r3).max())
