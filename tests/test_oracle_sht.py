@@ -102,6 +102,19 @@ def test_adjoint_mlist_subset():
     assert np.array_equal(full[sel], sub[sel])
 
 
+def test_spin2_adjoint_mlist_subset():
+    """The spin-2 adjoint restricted to a list of m equals the full spin-2
+    adjoint (itself pinned by the adjoint identity) at those m."""
+    g, L = sht.healpix(8), 16
+    rng = np.random.default_rng(2)
+    Q, U = rng.normal(size=g.npix), rng.normal(size=g.npix)
+    E, B = sht.alm2map_spin2_adjoint(g, L, Q, U)
+    Es, Bs = sht.alm2map_spin2_adjoint(g, L, Q, U, mlist=[0, 2, 9, 16])
+    sel = np.isin(sht.ms_of(L), [0, 2, 9, 16])
+    assert np.array_equal(E[sel], Es[sel]) and np.array_equal(B[sel], Bs[sel])
+    assert np.abs(E[sel]).max() > 0 and np.abs(B[sel]).max() > 0
+
+
 def test_spin2_pure_modes_closed_form():
     """E_22 = 1, B = 0 against the closed forms 2Y_22 = k (1 - cos t)^2 e^{2ip}
     and -2Y_22 = k (1 + cos t)^2 e^{2ip}, k = sqrt(5 / 64 pi), with
