@@ -117,7 +117,9 @@ typedef struct {
  * SHTG_SPIN2.  Limits (SHTG_ERR_ARG outside them): 0 <= lmax <= 8192,
  * 1 <= max_batch <= 4096; HEALPix 1 <= N_side <= 8192 and lmax <= 4 N_side;
  * Gauss-Legendre 1 <= rings <= 65536 and 1 <= nphi_gauss <= 65536; every
- * ring's FFT length within the ring stage's supported range.  Returns
+ * ring's FFT length within the ring stage's range of 2^13 points, Bluestein
+ * lengths included (HEALPix N_side <= 1024; Gauss-Legendre nphi a power of
+ * two <= 8192, or any nphi <= 4096).  Returns
  * SHTG_ERR_NOMEM if device memory is insufficient.  Sets *out on success. */
 int shtg_plan_create(int geom, int nside_or_nring, int nphi_gauss, int lmax, int max_batch,
                      int flags, shtg_plan **out);

@@ -501,7 +501,8 @@ static int build_fft_tables(Plan *p) {
     }
     if (logmax > SHTG_FFT_LOGMAX) {
         set_error("ring transform length 2^" + std::to_string(logmax) + " above the supported 2^" +
-                  std::to_string(SHTG_FFT_LOGMAX) + " (HEALPix N_side <= 1024, Gauss nphi <= 8192)");
+                  std::to_string(SHTG_FFT_LOGMAX) + " (HEALPix N_side <= 1024; Gauss-Legendre nphi a "
+                  "power of two <= 8192, or any nphi <= 4096)");
         return SHTG_ERR_ARG;
     }
     p->fft_logmax = logmax;
