@@ -106,3 +106,45 @@ def test_flop_counts_and_alu_peaks():
     fp32, fp64 = bench.alu_peaks(2070.0)
     assert fp32 == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
     assert fp64 == pytest.approx(1.25)
+
+
+def test_clock_sampler_parses_nvidia_smi_rows(tmp_path):
+    """The clocks record of the JSON line: median SM clock under load, the
+    maximum, and every throttle reason seen Active in any sample."""
+    rows = [
+        "0, 2070, 2070, 812.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 2055, 2070, 1310.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2070, 2070, 1290.2, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+    ]
+    path = tmp_path / "clocks.csv"
+    path.write_text("\n".join(rows) + "\n")
+
+    class _Done:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    ck = bench.Clocks(0)
+    ck.proc, ck.path = _Done(), str(path)
+    r = ck.stop()
+    assert r["sm_mhz"] == 2070.0 and r["sm_max_mhz"] == 2070.0
+    assert r["reasons"] == ["sw_power_cap"] and r["samples"] == 3
+    assert not path.exists()
+
+
+def test_clock_sampler_without_nvidia_smi():
+    ck = bench.Clocks(0)
+    r = ck.stop()       # never started
+    assert r["sm_mhz"] is None and r["reasons"]
+
+
+def test_measured_peaks_fallback(monkeypatch, tmp_path):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    peaks, src = bench.measured_peaks()
+    assert src == "fallback" and peaks["hbm_gbs"] == 6800.0 and peaks["bf16_tflops"] == 1900.0
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6682.5, "bf16_tflops": 1900.3}')
+    peaks, src = bench.measured_peaks()
+    assert src == "measured" and peaks["hbm_gbs"] == 6682.5
