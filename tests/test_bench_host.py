@@ -1,5 +1,6 @@
 """Host-side parts of bench.py (no GPU): the CPU-baseline extrapolation, the
-reference arm's JSON line and the flop counts behind the rooflines."""
+reference arm's JSON line, the flop counts behind the rooflines, the clock
+sampler's parsing and the peak-file fallback."""
 import argparse
 import json
 import time
