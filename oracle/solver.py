@@ -223,3 +223,62 @@ def log_posterior_grad(prob: Problem, a, d, bins, cl_scale=None):
     per_lm = 0.5 * w * np.abs(a[0]) ** 2 * ic[prob.ls]
     gl = np.array([per_lm[(prob.ls >= lo) & (prob.ls <= hi)].sum() for lo, hi in bins])
     return ga, gl
+
+
+# ----------------------------------------------------------------------------
+# Joint (C_l, a) move of Sect. 2.2.2 (Jewell et al. 2009, Racine et al. 2016)
+# ----------------------------------------------------------------------------
+def _cl_blocks(cl, lmax):
+    """(L+1, n, n) per-l signal covariance: C_l (n = 1) or the T/E/B block
+    with TE and EB = TB = 0 (n = 3) from (TT, EE, BB, TE)."""
+    cl = np.asarray(cl, np.float64)
+    if cl.ndim == 1:
+        return cl[: lmax + 1, None, None].copy()
+    tt, ee, bb, te = cl[:, : lmax + 1]
+    C = np.zeros((lmax + 1, 3, 3))
+    C[:, 0, 0], C[:, 1, 1], C[:, 2, 2] = tt, ee, bb
+    C[:, 0, 1] = C[:, 1, 0] = te
+    return C
+
+
+def fluctuation_rescale(cl_old, cl_new, f, lmax):
+    """f^scaled = (C^new_l)^{1/2} (C^old_l)^{-1/2} f_lm, the deterministic
+    rescaling of the fluctuation term in the joint move.  Square roots are
+    the symmetric principal ones (the reading used for S^-1/2 throughout);
+    multipoles where either block is not positive definite (C_0 = C_1 = 0)
+    are held at zero, as in the solver.  f: (n, nalm) with n = 1 or 3."""
+    f = np.asarray(f, np.complex128)
+    n = f.shape[0]
+    Co, Cn = _cl_blocks(cl_old, lmax), _cl_blocks(cl_new, lmax)
+    ls = sht.ls_of(lmax)
+    M = np.zeros((lmax + 1, n, n))
+    for l in range(lmax + 1):
+        wo, Vo = np.linalg.eigh(Co[l])
+        wn, Vn = np.linalg.eigh(Cn[l])
+        if np.all(wo > 0) and np.all(wn > 0):
+            M[l] = ((Vn * np.sqrt(wn)) @ Vn.T) @ ((Vo / np.sqrt(wo)) @ Vo.T)
+    return np.einsum("pij,jp->ip", M[ls], f)
+
+
+def joint_log_target(prob: Problem, d, a_hat, f_hat):
+    """log pi(theta) of the joint move's acceptance rule:
+    -1/2 (d - Y B a^)^T N^-1 (d - Y B a^) - 1/2 a^T S^-1 a^
+    - 1/2 f^T B Y^T N^-1 Y B f^, with a^ the mean field and f^ the
+    fluctuation term (the scaled one for a proposal).  Products in the
+    alm metric of dot_q6; S^-1 acts on the active multipoles only."""
+    nc = prob.ncomp
+    a_hat = np.asarray(a_hat, np.complex128).reshape(nc, -1)
+    f_hat = np.asarray(f_hat, np.complex128).reshape(nc, -1)
+    nv = prob.ninv_maps()
+    res = np.asarray(d, np.float64).reshape(nc, -1) - prob.Y(prob.beam(a_hat))
+    chi2 = float(np.sum(res * res * nv))
+    sinv = prob.sinv * prob.active[None, None, :]
+    prior = prob.dot(a_hat, prob._per_l(sinv, a_hat))
+    yf = prob.Y(prob.beam(f_hat))
+    fl = float(np.sum(yf * yf * nv))
+    return -0.5 * chi2 - 0.5 * prior - 0.5 * fl
+
+
+def joint_acceptance(log_pi_new, log_pi_old, log_prior_new=0.0, log_prior_old=0.0):
+    """A = min[1, pi(theta') P(theta') / (pi(theta) P(theta))] (Eq. acceptance-rate)."""
+    return float(min(1.0, np.exp((log_pi_new + log_prior_new) - (log_pi_old + log_prior_old))))

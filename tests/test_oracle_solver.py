@@ -336,3 +336,97 @@ def test_log_posterior_value_direct():
             prior += abs(am) ** 2 / cl[l]
     expect = -0.5 * chi2 - 0.5 * prior
     assert solver.log_posterior(prob, a, d) == pytest.approx(expect, rel=1e-12)
+
+
+# ------------------------------------------------------------- joint move
+def _cl4(L, rng):
+    ls = np.arange(L + 1)
+    tt = np.where(ls >= 2, rng.uniform(0.5, 2.0, L + 1) / np.maximum(ls * (ls + 1.0), 1.0), 0.0)
+    ee = tt * rng.uniform(0.02, 0.1, L + 1)
+    bb = ee * rng.uniform(1e-3, 1e-1, L + 1)
+    te = rng.uniform(-0.8, 0.8, L + 1) * np.sqrt(tt * ee)
+    return np.stack([tt, ee, bb, te])
+
+
+def test_fluctuation_rescale_maps_old_covariance_to_new():
+    """M = (C')^{1/2} C^{-1/2} per l must carry the old covariance to the new
+    one, M C M^T = C' (any consistent square root does; a transposed factor
+    or swapped order fails for non-commuting T/E blocks), act as
+    sqrt(C'/C) for temperature, as the identity for C' = C, and hold the
+    singular l < 2 at zero."""
+    L = 6
+    rng = np.random.default_rng(11)
+    co, cn = _cl4(L, rng), _cl4(L, rng)
+    P = (L + 1) * (L + 2) // 2
+    ls, ms = sht.ls_of(L), sht.ms_of(L)
+    for l in range(2, L + 1):
+        j = np.where((ls == l) & (ms == 1))[0][0]
+        M = np.zeros((3, 3))
+        for c in range(3):
+            e = np.zeros((3, P), complex)
+            e[c, j] = 1.0
+            M[:, c] = solver.fluctuation_rescale(co, cn, e, L)[:, j].real
+        Co = np.array([[co[0, l], co[3, l], 0], [co[3, l], co[1, l], 0], [0, 0, co[2, l]]])
+        Cn = np.array([[cn[0, l], cn[3, l], 0], [cn[3, l], cn[1, l], 0], [0, 0, cn[2, l]]])
+        assert np.allclose(M @ Co @ M.T, Cn, rtol=1e-12, atol=1e-14 * np.abs(Cn).max())
+    f = _rand_alm(L, rng, 3)
+    assert np.allclose(solver.fluctuation_rescale(co, co, f, L)[:, ls >= 2], f[:, ls >= 2], rtol=1e-12)
+    assert np.all(solver.fluctuation_rescale(co, cn, f, L)[:, ls < 2] == 0)
+    ft = _rand_alm(L, rng, 1)
+    st = solver.fluctuation_rescale(co[0], cn[0], ft, L)
+    ratio = np.where(ls >= 2, np.sqrt(cn[0, ls] / np.where(ls >= 2, co[0, ls], 1.0)), 0.0)
+    assert np.allclose(st[0], ratio * ft[0], rtol=1e-13, atol=0)
+
+
+def test_joint_log_target_direct():
+    """log pi(theta) of the acceptance rule term by term with an independent
+    synthesis (scipy Y_lm on the pixel centres) and an explicit prior sum;
+    with f = 0 it is the log-posterior."""
+    nside, L = 4, 8
+    rng = np.random.default_rng(12)
+    g = sht.healpix(nside)
+    cl = C.cl_flat(L) * (1.0 + 0.05 * np.arange(L + 1))
+    bl = C.gauss_beam(L, 15 * C.DEG)
+    ninv = rng.uniform(0.5, 2.0, g.npix) * (rng.uniform(size=g.npix) > 0.25)
+    prob = solver.Problem(g, L, cl, bl, ninv)
+    a, f = _rand_alm(L, rng), _rand_alm(L, rng)
+    a[:, sht.ls_of(L) < 2] = 0
+    d = rng.normal(size=g.npix)
+    Yd, W, cols = _dense_Y(L, nside)
+    ls = np.array([c[1] for c in cols])
+    bc = np.where(ls >= 2, bl[ls], 0.0)
+    chi2 = np.sum((d - Yd @ (bc * _to_params(a[0], cols))) ** 2 * ninv)
+    fl = np.sum((Yd @ (bc * _to_params(f[0], cols))) ** 2 * ninv)
+    prior = 0.0
+    for l in range(2, L + 1):
+        for m in range(-l, l + 1):
+            prior += abs(a[0, abs(m) * (2 * L + 1 - abs(m)) // 2 + l]) ** 2 / cl[l]
+    expect = -0.5 * (chi2 + prior + fl)
+    assert solver.joint_log_target(prob, d, a, f) == pytest.approx(expect, rel=1e-12)
+    assert solver.joint_log_target(prob, d, a, 0 * f) == pytest.approx(
+        solver.log_posterior(prob, a, d), rel=1e-13)
+
+
+def test_joint_log_target_fluctuation_term_is_the_noise_part_of_A():
+    """T+E+B: the fluctuation term is -1/2 <f, (A - S^-1) f>, the noise part
+    of the solver's operator (Q and U weighted by the polarization N^-1)."""
+    nside, L = 4, 8
+    rng = np.random.default_rng(13)
+    g = sht.healpix(nside)
+    ninv = np.stack([rng.uniform(0.5, 2.0, g.npix), rng.uniform(0.2, 1.0, g.npix)])
+    prob = solver.Problem(g, L, _cl4(L, rng), C.gauss_beam(L, 0.2), ninv)
+    f = _rand_alm(L, rng, 3)
+    f[:, sht.ls_of(L) < 2] = 0
+    zero = np.zeros((3, g.npix))
+    lp = solver.joint_log_target(prob, prob.Y(prob.beam(0 * f)), 0 * f, f)
+    sinv_f = prob._per_l(prob.sinv * prob.active[None, None, :], f)
+    noise = prob.dot(f, prob.matvec(f)) - prob.dot(f, sinv_f)
+    assert lp == pytest.approx(-0.5 * noise, rel=1e-11)
+    assert solver.joint_log_target(prob, zero, 0 * f, 0 * f) == 0.0
+
+
+def test_joint_acceptance_rule():
+    assert solver.joint_acceptance(-10.0, -12.0) == 1.0
+    assert solver.joint_acceptance(-12.0, -10.0) == pytest.approx(math.exp(-2.0))
+    assert solver.joint_acceptance(-12.0, -10.0, 1.5, -0.5) == 1.0
+    assert solver.joint_acceptance(-12.0, -10.0, 0.5, 0.0) == pytest.approx(math.exp(-1.5))
