@@ -15,6 +15,10 @@ and the synthesis Y written out:
   Shewchuk 1994) with the diagonal preconditioner of Sect. 4,
   M = S^-1 + b_l^2 D_lm, D_lm = sum_r g_lm(theta_r) sum_{p in r} N^-1_p.
 All inner products use the metric of :func:`oracle.sht.dot_q6`.
+
+Also here: the Gaussian log-posterior of Eq. (joint-posterior) with its
+gradients, and the pieces of the joint (C_l, a) move of Sect. 2.2.2 (the
+fluctuation rescaling, log pi(theta) and the acceptance rule).
 """
 from __future__ import annotations
 
