@@ -16,6 +16,10 @@
 #pragma once
 #include <cuda_runtime.h>
 
+// host and device: the kernels use these on the GPU, and a CPU test checks
+// the error-free transformations and error bounds exactly on the host
+#define SHTG_DF_FN __host__ __device__ __forceinline__
+
 namespace shtg {
 
 struct __align__(8) df {
@@ -25,26 +29,26 @@ struct __align__(16) dfc {   // complex
     df re, im;
 };
 
-__device__ __forceinline__ df df_make(float h, float l) {
+SHTG_DF_FN df df_make(float h, float l) {
     df r;
     r.hi = h;
     r.lo = l;
     return r;
 }
-__device__ __forceinline__ df df_zero() { return df_make(0.f, 0.f); }
+SHTG_DF_FN df df_zero() { return df_make(0.f, 0.f); }
 
-__device__ __forceinline__ float two_sum(float a, float b, float &e) {
+SHTG_DF_FN float two_sum(float a, float b, float &e) {
     const float s = a + b;
     const float bb = s - a;
     e = (a - (s - bb)) + (b - bb);
     return s;
 }
-__device__ __forceinline__ float fast_two_sum(float a, float b, float &e) {
+SHTG_DF_FN float fast_two_sum(float a, float b, float &e) {
     const float s = a + b;
     e = b - (s - a);
     return s;
 }
-__device__ __forceinline__ float two_prod(float a, float b, float &e) {
+SHTG_DF_FN float two_prod(float a, float b, float &e) {
     const float p = a * b;
     e = fmaf(a, b, -p);
     return p;
@@ -52,16 +56,21 @@ __device__ __forceinline__ float two_prod(float a, float b, float &e) {
 
 // nearest df of a double (three FP64-pipe operations: used only when data
 // are staged, never per multiply-add)
-__device__ __forceinline__ df df_from(double x) {
+SHTG_DF_FN df df_from(double x) {
+#ifdef __CUDA_ARCH__
     const float h = __double2float_rn(x);
     return df_make(h, __double2float_rn(x - (double)h));
+#else
+    const float h = (float)x;   // round to nearest, the host default
+    return df_make(h, (float)(x - (double)h));
+#endif
 }
-__device__ __forceinline__ double df_to(df a) { return (double)a.hi + (double)a.lo; }
+SHTG_DF_FN double df_to(df a) { return (double)a.hi + (double)a.lo; }
 
-__device__ __forceinline__ df df_neg(df a) { return df_make(-a.hi, -a.lo); }
+SHTG_DF_FN df df_neg(df a) { return df_make(-a.hi, -a.lo); }
 
 // a + b: error below 2^-47 (|a| + |b|)
-__device__ __forceinline__ df df_add(df a, df b) {
+SHTG_DF_FN df df_add(df a, df b) {
     float e;
     const float s = two_sum(a.hi, b.hi, e);
     e += a.lo + b.lo;
@@ -69,10 +78,10 @@ __device__ __forceinline__ df df_add(df a, df b) {
     const float h = fast_two_sum(s, e, l);
     return df_make(h, l);
 }
-__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+SHTG_DF_FN df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
 
 // a * b: error below 2^-46 |a b|
-__device__ __forceinline__ df df_mul(df a, df b) {
+SHTG_DF_FN df df_mul(df a, df b) {
     float e;
     const float p = two_prod(a.hi, b.hi, e);
     e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
@@ -88,9 +97,9 @@ __device__ __forceinline__ df df_mul(df a, df b) {
 struct dfacc {
     float hi, lo;
 };
-__device__ __forceinline__ void df_acc_zero(dfacc &s) { s.hi = s.lo = 0.f; }
+SHTG_DF_FN void df_acc_zero(dfacc &s) { s.hi = s.lo = 0.f; }
 // s += a * b
-__device__ __forceinline__ void df_fma(dfacc &s, df a, df b) {
+SHTG_DF_FN void df_fma(dfacc &s, df a, df b) {
     float e;
     const float p = two_prod(a.hi, b.hi, e);
     e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
@@ -99,11 +108,11 @@ __device__ __forceinline__ void df_fma(dfacc &s, df a, df b) {
     s.lo += e2 + e;
 }
 // (two_sum: after cancellation hi may be smaller than lo)
-__device__ __forceinline__ void df_acc_norm(dfacc &s) {
+SHTG_DF_FN void df_acc_norm(dfacc &s) {
     float l;
     s.hi = two_sum(s.hi, s.lo, l);
     s.lo = l;
 }
-__device__ __forceinline__ double df_acc_to(const dfacc &s) { return (double)s.hi + (double)s.lo; }
+SHTG_DF_FN double df_acc_to(const dfacc &s) { return (double)s.hi + (double)s.lo; }
 
 }  // namespace shtg
