@@ -9,8 +9,9 @@
 // pass loads R elements per butterfly into registers, applies the twiddles,
 // does the radix-R DFT in registers and writes the R outputs to their sorted
 // places (Govindaraju et al. 2008, "High performance discrete Fourier
-// transforms on graphics processors", with R = 16 passes and one smaller
-// final pass).  The buffer is padded by one element per 16 so that the
+// transforms on graphics processors", with one radix-2, -4 or -8 pass first,
+// where it needs no twiddles, and radix-16 passes after it).  The buffer is
+// padded by one element per 16 so that the
 // scattered writes of the early passes hit distinct banks.  Rings whose n is
 // not a power of two (HEALPix polar caps) use Bluestein's chirp convolution
 // with precomputed kernel spectra.  The fused variant applies N^-1 between
@@ -219,9 +220,9 @@ __device__ __forceinline__ void spass(C *buf, const int M, const int Ns, const T
 // Length-2^logM forward DFT (e^{-2 pi i jk/M}, unnormalized) of buf in
 // place, natural order in and out; the last pass multiplies by post (if not
 // null) and conjugates when cj is set.  The inverse transform is
-// conj(DFT(conj x)): callers conjugate on the way in and out.  Passes: radix
-// 16 while at least four factors of two remain, then one radix-8, -4 or -2
-// pass.  Each kernel calls it from one place, so it is inlined once.
+// conj(DFT(conj x)): callers conjugate on the way in and out.  Passes: one
+// radix-8, -4 or -2 pass when log2 M is not a multiple of four, then radix
+// 16.  Each kernel calls it from one place, so it is inlined once.
 template <int NT, typename C>
 __device__ __forceinline__ void fft_stockham(C *buf, const int logM, const TwTab<C> tw,
                                           const C *__restrict__ post, const bool cj) {
