@@ -4,34 +4,43 @@
 
 Workload: 8 T+E+B realizations sharing C_l, beam and N^-1 (hits-weighted
 noise, |b| < 20 deg mask + 200 holes, 10' beam).  One "step" is one
-cg_sample call with a fixed iteration budget: RHS assembly with the FP64
-transforms, preconditioner, then --iters-per-step batched mixed-precision
-PCG iterations (FP32 operator applications) with FP64 residual
+cg_sample call with a fixed iteration budget: RHS assembly (FP64-accurate
+transforms), preconditioner, then --iters-per-step batched mixed-precision
+PCG iterations (FP32 operator applications) with FP64-accurate residual
 replacements (reliable updates), the last one at the end of the step.
 Inputs are synthetic (seeded Philox), resident in HBM and larger than L2.
+The timed steps run the library's default path (the PCG iteration replayed
+as a CUDA graph); one more step, run with per-kernel-class CUDA events
+after the timed region, gives the kernel shares and the rooflines.
 
-value = batched CG iterations per second over the whole job (an iteration
-applies the operator to all 8 realizations; FP64 residual replacements are
-counted as iterations too), summed over ranks.  Ranks run independent
-replicas (weak scaling, no data-path collective).
+value = batched FP32 PCG iterations per second over the whole job (an
+iteration applies the FP32 operator to all 8 realizations; the
+FP64-accurate residual replacements are not counted), summed over ranks.
+Ranks run independent replicas (weak scaling, no data-path collective);
+`--gpus N` spawns N local ranks itself unless it runs under torchrun.
 
-The full solve to a true FP64 relative residual of 1e-6 (time_to_1e-6) is
-measured once after the timed steps, and the plain FP64 PCG per-iteration
-time on the same problem gives its time-to-1e-6 for comparison.
+Extras: the full solve to a true FP64-accurate relative residual of 1e-6;
+the same steps with native FP64 residual replacements; the plain FP64 PCG
+per-iteration time; both forms solved to 1e-6 on the masked temperature
+workload (N_side 256, l_max 512), whose iteration ratio turns the FP64 form's
+per-iteration time at the benchmark size into its time to 1e-6 (a stated
+model, checked by that measured pair); SHT pairs/s; the mixed-geometry
+chains; measured FMA peaks for the arithmetic rooflines.
 
---impl reference times the FP64 CPU oracle (test infrastructure) on a
-bounded ring sample of the same workload and extrapolates the same metric.
+--impl reference times the FP64 CPU oracle (test infrastructure) on bounded
+ring samples of the same workload, and once on the full grid to check the
+extrapolation.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
 import subprocess
 import sys
 import tempfile
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -45,6 +54,16 @@ UNIT = "CG iterations/s"
 NSIDE, LMAX, NB = 1024, 2048, 8   # the benchmark workload; --nside/--lmax/--batch shrink it for profiling
 CLASS_NAMES = ["leg_synth_fp32", "leg_analysis_fp32", "ring_fft_fp32", "leg_synth_fp64",
                "leg_analysis_fp64", "ring_fft_fp64", "vector", "precond_diag"]
+# CUDA sources of each kernel class (a traffic figure measured by ncu is
+# reported only while these files are unchanged since the capture)
+CLASS_SOURCES = {
+    "leg_synth_fp32": ["legendre_tc.cu", "legendre_kernels.cuh", "legendre32.cu"],
+    "leg_analysis_fp32": ["legendre_tc.cu", "legendre_kernels.cuh", "legendre32.cu"],
+    "ring_fft_fp32": ["ringfft.cu"],
+    "leg_synth_fp64": ["legendre_df.cu", "df.cuh", "legendre_kernels.cuh", "legendre64.cu"],
+    "leg_analysis_fp64": ["legendre_df.cu", "df.cuh", "legendre_g64.cu", "legendre64.cu"],
+    "ring_fft_fp64": ["ringfft.cu"],
+}
 
 
 # ----------------------------------------------------------------- helpers
@@ -57,12 +76,26 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def alu_peaks(sm_mhz: float):
-    """FP32: 152 SMs x 128 lanes x 2 flops/FMA x clock; FP64: 1.25 TFLOP/s
-    nominal for GB300 scaled to the same clock."""
-    fp32 = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
-    fp64 = 1.25 * sm_mhz / 2070.0
-    return fp32, fp64
+def sources_hash(names) -> str:
+    h = hashlib.sha256()
+    for n in sorted(names):
+        with open(os.path.join(ROOT, "paper_2306_15511_gb300", "csrc", n), "rb") as f:
+            h.update(n.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record(cls: str, launch_units: float):
+    """DRAM bytes per launch of a kernel class from the committed ncu record
+    (profiles/traffic.json: bytes per unit of work, the sources' hash at the
+    capture), scaled to this launch's units; None once the sources changed."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path) or cls not in CLASS_SOURCES:
+        return None
+    with open(path) as f:
+        rec = json.load(f).get(cls)
+    if not rec or rec.get("sources_sha") != sources_hash(CLASS_SOURCES[cls]):
+        return None
+    return rec["dram_bytes_per_unit"] * launch_units
 
 
 def contraction_flops(nalm, npairs, nmaps_t, nmaps_p):
@@ -83,6 +116,31 @@ def legendre_flops(nalm, npairs, nmaps_t, nmaps_p):
     if nmaps_p:
         f += pr * (8 + 16 * nmaps_p)
     return f
+
+
+def ring_fft_flops(nside: int) -> float:
+    """Algorithmic flops of one direction of the ring transforms of one map
+    on a HEALPix grid: one complex DFT of length n per north / south ring pair
+    (the pair's two real rings packed into one complex sequence), counted as
+    5 n log2 n whatever algorithm computes it (Bluestein's overhead for
+    non-power-of-two rings is not counted).  Polar pairs i = 1 .. N-1 have
+    n = 4 i; the N + 1 equatorial pairs (the equator ring alone) n = 4 N."""
+    f = 0.0
+    for i in range(1, nside):
+        n = 4 * i
+        f += 5.0 * n * np.log2(n)
+    n = 4 * nside
+    f += (nside + 1) * 5.0 * n * np.log2(n)
+    return f
+
+
+def fma_peaks():
+    """Measured FMA throughput (TFLOP/s) of this GPU, FP32 and FP64, and its SM count."""
+    from paper_2306_15511_gb300.api import fma_peak
+    sms, fp32 = fma_peak("fp32")
+    _, fp64 = fma_peak("fp64")
+    return {"sm_count": sms, "fp32_tflops": fp32, "fp64_tflops": fp64,
+            "how": "8 independent FMA chains per thread, every SM filled, CUDA events, 2 flops per FMA"}
 
 
 class Clocks:
@@ -131,21 +189,32 @@ class Clocks:
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
 
 
+def rank_summary(rep, ms_local: float, iters_local: float, steps: int):
+    """Whole-job timing over replicas: the slowest rank's time per step and
+    the sum of all ranks' iterations; value = iterations / time."""
+    ms = rep.max(ms_local)
+    total = rep.sum(iters_local)
+    return ms, total, total / (ms * steps / 1000.0)
+
+
 # ------------------------------------------------------------------ inputs
-def make_inputs(plan, device, seed_shift=0):
+def make_inputs(plan, device, rank=0):
     """T+E+B workload (8 realizations, N_side 1024, l_max 2048) drawn on the
-    device; d = Y B a + n with the library's own FP64 synthesis."""
+    device; d = Y B a + n with the library's own FP64 synthesis.  Ranks > 0
+    draw fresh white noise w1 and w2 (independent chains)."""
     import torch
     from inputs import configs as C
+    from inputs import philox as px
+    from paper_2306_15511_gb300.replicas import w1_key, w2_key
     probs = C.teb_realizations(NB, NSIDE, LMAX, device=device)
-    if seed_shift:
-        # a replica on another rank draws fresh white noise (independent chains)
-        from inputs import philox as px
-        from paper_2306_15511_gb300.replicas import w2_key
+    if rank:
+        nalm = C.nalm(LMAX)
         for b, p in enumerate(probs):
-            key = w2_key(seed_shift, b)
-            for k in range(3):
-                p.w2[k] = px.normal_torch(key, px.STREAM_W2, plan.npix, k * plan.npix, device)
+            k1, k2 = w1_key(rank, b), w2_key(rank, b)
+            p.w1 = torch.stack([C.white_alm(LMAX, k1, px.STREAM_W1, k * 2 * nalm, device)
+                                for k in range(3)])
+            p.w2 = torch.stack([px.normal_torch(k2, px.STREAM_W2, plan.npix, k * plan.npix, device)
+                                for k in range(3)])
     p0 = probs[0]
     ls = torch.as_tensor(C.alm_lm(LMAX)[0], device=device)
     bl = torch.as_tensor(p0.bl, device=device)[ls]
@@ -201,6 +270,12 @@ def _oracle_problem(nsub_stride=32):
     return _ORACLE[nsub_stride]
 
 
+def oracle_threads(n: int = 0) -> int:
+    """Set (n > 0) and return the oracle's worker threads."""
+    from oracle import _lib
+    return int(_lib.lib().orc_set_threads(int(n)))
+
+
 def oracle_sample(strides=(32, 16)):
     """Time one T+E+B operator application of the FP64 oracle on every
     s-th ring of the N_side 1024 grid for each stride s, fit
@@ -220,17 +295,67 @@ def oracle_sample(strides=(32, 16)):
         a, b = 0.0, t2 / n2
     per_real = a + b * nring
     desc = ", ".join(f"{t:.2f} s on {n} rings" for n, t in sorted(pts))
-    return {"value": 1.0 / (per_real * NB), "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+    return {"value": 1.0 / (per_real * NB), "unit": UNIT, "cores": oracle_threads(), "kind": "oracle",
+            "per_realization_s": per_real,
             "sample": (f"one FP64 T+E+B operator application of 1 realization on ring subsets of "
                        f"the {nring}-ring grid (every {'th / '.join(str(s_) for s_ in strides)}th "
                        f"ring): {desc}; fitted a + b x rings (a = {a:.2f} s, b = {1e3 * b:.2f} ms) "
                        f"and extrapolated to {nring} rings, then x{NB} realizations")}
 
 
+def oracle_full_grid():
+    """One T+E+B operator application of the FP64 oracle on the whole grid
+    (1 realization), timed: the check of the ring-sample extrapolation."""
+    from oracle import solver as osol
+    g, cl4, bl, ninv, x = _oracle_full()
+    prob = osol.Problem(g, LMAX, cl4, bl, ninv)
+    t0 = time.perf_counter()
+    prob.matvec(x)
+    return time.perf_counter() - t0
+
+
+def oracle_extras():
+    """The oracle's other figures (FP64, host cores): SHT pairs/s on the
+    masked temperature grid (N_side 256, l_max 512), CG iterations/s on the
+    full-sky workload (solved to its 1e-8) and on the masked one (5
+    iterations), and the benchmark operator on one core."""
+    from inputs import configs as C
+    from oracle import sht as osht
+    from oracle import solver as osol
+    out = {"cores": oracle_threads()}
+    p = C.masked_temperature(256, 512)
+    g = osht.healpix(256)
+    t0 = time.perf_counter()
+    osht.alm2map_adjoint(g, 512, osht.alm2map(g, 512, p.signal_alm[0]))
+    out["sht_pairs_per_s_nside256_lmax512"] = 1.0 / (time.perf_counter() - t0)
+    prob = osol.Problem(g, 512, p.cl, p.bl, p.ninv)
+    b = prob.rhs(p.noise_map, p.w1, p.w2)
+    t0 = time.perf_counter()
+    _, it, _ = osol.pcg(prob, b, 1e-6, maxiter=5)
+    out["cg_iters_per_s_nside256_lmax512"] = it / (time.perf_counter() - t0)
+    q = C.fullsky_temperature()
+    g0 = osht.healpix(q.nside)
+    prob0 = osol.Problem(g0, q.lmax, q.cl, q.bl, q.ninv)
+    b0 = prob0.rhs(q.noise_map, q.w1, q.w2)
+    t0 = time.perf_counter()
+    _, it0, hist = osol.pcg(prob0, b0, q.tol, maxiter=1000)
+    el = time.perf_counter() - t0
+    out["fullsky_nside32_lmax64"] = {"iterations_to_1e-8": it0, "s": el, "cg_iters_per_s": it0 / el}
+    nthr = oracle_threads()
+    try:
+        oracle_threads(1)
+        s1 = oracle_sample(strides=(128, 64))
+        out["single_core"] = {"value": s1["value"], "unit": UNIT, "sample": s1["sample"]}
+    finally:
+        oracle_threads(nthr)
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    full_s = oracle_full_grid()
     for _ in range(min(args.warmup, 1)):
         oracle_sample()
     vals = []
@@ -239,71 +364,89 @@ def run_reference(args):
         vals.append(oracle_sample())
     el = time.perf_counter() - t0
     v = float(np.median([x["value"] for x in vals]))
+    pred = float(np.median([x["per_realization_s"] for x in vals]))
+    extras = oracle_extras() if not getattr(args, "no_extras", False) else {}
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "impl": "reference",
+            "warmup": args.warmup, "ms_per_step": 1000.0 * el / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
             "config": {"workload": f"T+E+B constrained realizations, HEALPix N_side={NSIDE}, "
                                    f"l_max={LMAX}, batch {NB}, tol 1e-6",
                        "global_batch": NB, "l2": "inputs larger than L2"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": vals[0]["cores"],
                              "kind": "oracle", "sample": vals[0]["sample"]},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-            "wall_s": el}
+            "fit_check": {"full_grid_operator_s": full_s, "fit_predicted_s": pred,
+                          "rel_err": (pred - full_s) / full_s,
+                          "full_grid_value": 1.0 / (full_s * NB)},
+            "extras": extras, "wall_s": el}
     print(json.dumps(line), flush=True)
     return 0
 
 
 # --------------------------------------------------------------- GPU arm
-def run_gpu(args):
+def _event_time(fn, reps=1):
+    import torch
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        r = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1000.0 / reps, r
+
+
+def _apply_sizes(args):
+    global NSIDE, LMAX, NB
+    NSIDE, LMAX, NB = args.nside, args.lmax, args.batch
+
+
+def gpu_rank(args):
+    """One rank of the GPU arm (rank 0 prints the JSON line)."""
     import torch
     from paper_2306_15511_gb300 import Plan
     from paper_2306_15511_gb300.replicas import Replicas
 
+    _apply_sizes(args)
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     rep = Replicas("nccl", dev)
     rank, world = rep.rank, rep.world
-    barrier, max_over_ranks, sum_over_ranks = rep.barrier, rep.max, rep.sum
 
     plan = Plan(nside=NSIDE, lmax=LMAX, max_batch=NB, spin2=True)
-    inp = make_inputs(plan, dev, seed_shift=rank)
+    inp = make_inputs(plan, dev, rank=rank)
     kw = dict(tol=1e-6, mode=args.mode, maxiter=args.iters_per_step,
               reliable_delta=args.reliable_delta, check_every=args.check_every,
               allow_not_converged=True, fp64_arith=args.fp64_arith)
     out = torch.empty(NB, 3, plan.nalm, dtype=torch.complex128, device=dev)
 
-    def step(profile=False):
+    def step(profile=False, **over):
+        k = dict(kw)
+        k.update(over)
         return plan.cg_sample(inp["cl"], inp["bl"], inp["ninv"], inp["d"], inp["w1"], inp["w2"],
-                              out=out, profile=profile, **kw)[1]
+                              out=out, profile=profile, **k)[1]
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    barrier()
+    rep.barrier()
     clocks = Clocks(local)
     clocks.start()
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(st)
-    stats = [step(profile=True) for _ in range(args.steps)]
+    stats = [step() for _ in range(args.steps)]
     e1.record(st)
     torch.cuda.synchronize()
     ck = clocks.stop()
-    barrier()
+    rep.barrier()
     ms_local = e0.elapsed_time(e1) / args.steps
-    ms = max_over_ranks(ms_local)
-    iters_local = float(sum(s["iterations"] + s["fp64_matvecs"] for s in stats))
-    iters_all = sum_over_ranks(iters_local)
-    value = iters_all / (ms * args.steps / 1000.0)
+    iters_local = float(sum(s["iterations"] for s in stats))
+    ms, iters_all, value = rank_summary(rep, ms_local, iters_local, args.steps)
     launches = int(sum(s["launches"] for s in stats))
-    # per-class live kernel times over the timed steps
-    kms = np.sum([s["kernel_ms"] for s in stats], axis=0)
-    kcnt = np.sum([s["kernel_launches"] for s in stats], axis=0)
-    inner = sum(s["iterations"] for s in stats)
-    outer = sum(s["fp64_matvecs"] for s in stats)
 
     # ---------------------------------------------------------- e2e (host)
     e2e = None
@@ -315,13 +458,13 @@ def run_gpu(args):
         hout = torch.empty(NB, 3, plan.nalm, dtype=torch.complex128).pin_memory()
         ke = max(1, min(args.steps, args.e2e_steps))
         torch.cuda.synchronize()
-        barrier()
+        rep.barrier()
         t0 = time.perf_counter()
         e2e_stats = [plan.cg_sample(inp["cl"], inp["bl"], hn, hd, hw1, hw2, out=hout, **kw)[1]
                      for _ in range(ke)]
         torch.cuda.synchronize()
-        el = max_over_ranks(time.perf_counter() - t0)
-        it_e = sum_over_ranks(float(sum(s["iterations"] + s["fp64_matvecs"] for s in e2e_stats)))
+        el = rep.max(time.perf_counter() - t0)
+        it_e = rep.sum(float(sum(s["iterations"] for s in e2e_stats)))
         h2d = hd.numel() * 8 + hw2.numel() * 8 + hw1.numel() * 16 + hn.numel() * 8
         e2e = {"value": it_e / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(hout.numel() * 16), "steps": ke}
@@ -330,29 +473,37 @@ def run_gpu(args):
         rep.close()
         return 0
 
-    # -------------------------------------------------------------- extras
+    # ------------------------------------------ profiled step (kernel shares)
+    sp = step(profile=True)
+    kms = np.asarray(sp["kernel_ms"], dtype=np.float64)
+    kcnt = np.asarray(sp["kernel_launches"], dtype=np.int64)
+    inner, outer = sp["iterations"], sp["fp64_matvecs"]
+    peaks_alu = fma_peaks()
+
     extras = {}
     if not args.no_extras:
-        extras = measure_extras(plan, inp, dev, kw, full_solve=not args.no_full_solve)
+        extras = measure_extras(plan, inp, dev, kw, step, full_solve=not args.no_full_solve)
 
     # ------------------------------------------------------------ roofline
     # One entry per kernel class with the resource that bounds it and the
-    # class's algorithmic work over its live CUDA-event time in the timed
-    # steps; "roofline" is the class with the largest share.
+    # class's algorithmic work over its CUDA-event time in the profiled step
+    # (per-launch averages: the work of one launch over its mean duration);
+    # "roofline" is the class with the largest share.
     #  - tensor-core Legendre kernels (mode mixed_tc): the contraction's
     #    flops against the measured sustained bf16 tensor rate (three bf16
     #    products per FP32-accurate multiply-add are issued on top);
     #  - CUDA-core FP32 Legendre kernels (mode mixed): all flops against the
-    #    FP32 lanes at the sampled clock;
+    #    measured FP32 FMA rate;
     #  - FP64-accurate Legendre kernels: in double-FP32 (the mixed modes'
-    #    default) against the FP32 lanes / 6 (a double-FP32 flop costs about
-    #    six FP32 operations), in native FP64 against the nominal FP64 rate;
-    #  - ring stages: HBM, the bytes of the Fourier coefficients read and
-    #    written plus the N^-1 map (FP32 fused launches; FP64: three fused and
-    #    the RHS's map -> coefficients launch per step).
+    #    default) against the measured FP32 FMA rate / 6 (a double-FP32 flop
+    #    costs about six FP32 operations), in native FP64 against the
+    #    measured FP64 FMA rate;
+    #  - FP32 ring stage: HBM, the bytes of the Fourier coefficients read and
+    #    written plus the N^-1 map;
+    #  - FP64 ring stage: the measured FP64 FMA rate, with 5 n log2 n flops
+    #    per ring-pair transform and direction.
     peaks, src = measured_peaks()
-    sm_mhz = ck.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-    fp32_peak, fp64_peak = alu_peaks(float(sm_mhz))
+    fp32_peak, fp64_peak = peaks_alu["fp32_tflops"], peaks_alu["fp64_tflops"]
     bf16_sus = peaks.get("bf16_tflops_sustained") or peaks.get("bf16_tflops")
     nalm, npairs = plan.nalm, 2 * NSIDE
     nring, npix = 4 * NSIDE - 1, 12 * NSIDE * NSIDE
@@ -360,42 +511,52 @@ def run_gpu(args):
     per_pass_c = contraction_flops(nalm, npairs, NB, NB)
     df = args.fp64_arith == "df64" or (args.fp64_arith == "default" and args.mode != "fp64")
     coef32 = 2.0 * 3 * NB * nring * (LMAX + 1) * 8           # read + write, T, Q, U of NB maps
-    ring_bytes = {2: (coef32 + 2 * npix * 4) * inner,
-                  5: (2 * coef32 + 2 * npix * 8) * outer + (3 * NB * npix * 8 + coef32) * len(stats)}
-    fl = {0: inner, 1: inner, 3: outer, 4: outer + len(stats)}   # passes (FP64 analysis also builds the RHS)
+    fft1 = ring_fft_flops(NSIDE) * 3 * NB                     # one direction, all maps
+    # work of the whole profiled step per class, and the units of one launch
+    work = {0: per_pass_c * inner if args.mode == "mixed_tc" else per_pass * inner,
+            1: per_pass_c * inner if args.mode == "mixed_tc" else per_pass * inner,
+            2: (coef32 + 2 * npix * 4) * inner,
+            3: per_pass * outer, 4: per_pass * (outer + 1),
+            5: fft1 * (2 * outer + 1)}
+    coef_units = 3 * NB * nring * (LMAX + 1)                 # Fourier coefficients of one pass
     roofs = {}
     for c in range(len(CLASS_NAMES)):
-        if kms[c] <= 0:
+        if kms[c] <= 0 or c not in work:
             continue
         t = kms[c] / 1000.0
+        name = CLASS_NAMES[c]
         if c in (0, 1):
             if args.mode == "mixed_tc":
-                ach = per_pass_c * fl[c] / t / 1e12
-                r = {"bound": "tensor", "achieved": ach, "peak": bf16_sus, "unit": "TFLOP/s",
+                r = {"bound": "tensor", "achieved": work[c] / t / 1e12, "peak": bf16_sus, "unit": "TFLOP/s",
                      "peak_source": f"{src} bf16 (sustained)"}
             else:
-                ach = per_pass * fl[c] / t / 1e12
-                r = {"bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "peak_source": f"FP32 lanes x 2 flops at the sampled {sm_mhz:.0f} MHz"}
+                r = {"bound": "alu", "achieved": work[c] / t / 1e12, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "peak_source": "measured FP32 FMA rate (probe)"}
         elif c in (3, 4):
-            ach = per_pass * fl[c] / t / 1e12
             if df:
-                r = {"bound": "alu", "achieved": ach, "peak": fp32_peak / 6.0, "unit": "TFLOP/s",
-                     "peak_source": f"FP32 lanes x 2 flops at the sampled {sm_mhz:.0f} MHz / 6 "
-                                    "(double-FP32 arithmetic)"}
+                r = {"bound": "alu", "achieved": work[c] / t / 1e12, "peak": fp32_peak / 6.0,
+                     "unit": "TFLOP/s", "peak_source": "measured FP32 FMA rate (probe) / 6 (double-FP32)"}
             else:
-                r = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "peak_source": "nominal GB300 FP64 rate at the sampled clock"}
-        elif c in ring_bytes:
-            ach = ring_bytes[c] / t / 1e9
-            r = {"bound": "hbm", "achieved": ach, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
+                r = {"bound": "alu", "achieved": work[c] / t / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "peak_source": "measured FP64 FMA rate (probe)"}
+        elif c == 2:
+            r = {"bound": "hbm", "achieved": work[c] / t / 1e9, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                  "peak_source": f"{src} copy bandwidth"}
         else:
-            continue
+            r = {"bound": "alu", "achieved": work[c] / t / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                 "peak_source": "measured FP64 FMA rate (probe); 5 n log2 n flops per ring-pair DFT"}
         r["frac"] = r["achieved"] / r["peak"] if r["peak"] else None
-        r["traffic"] = None
-        r["kernel"] = CLASS_NAMES[c]
-        roofs[CLASS_NAMES[c]] = r
+        r["ms_per_launch"] = float(kms[c]) / max(1, int(kcnt[c]))
+        r["launches"] = int(kcnt[c])
+        # DRAM traffic of one pass (all launches of one operator direction) from
+        # the committed ncu record, scaled by the Fourier coefficients per pass
+        tr = traffic_record(name, coef_units) if c in (0, 1, 2) else None
+        r["traffic"] = tr
+        r["traffic_per"] = "pass" if tr is not None else None
+        if c == 2:
+            r["algorithmic_bytes_per_pass"] = coef32 + 2 * npix * 4
+        r["kernel"] = name
+        roofs[name] = r
     dom = CLASS_NAMES[int(np.argmax(kms))]
     roof = roofs.get(dom) or {"bound": "hbm", "achieved": None, "peak": peaks.get("hbm_gbs"), "unit": "GB/s",
                               "frac": None, "traffic": None, "kernel": dom}
@@ -404,6 +565,7 @@ def run_gpu(args):
     if not args.no_cpu_baseline:
         try:
             cpu = oracle_sample(strides=(16, 4))
+            cpu.pop("per_realization_s", None)
         except Exception as e:  # the oracle is test infrastructure; report why it is missing
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                    "sample": f"failed: {e}"}
@@ -419,23 +581,28 @@ def run_gpu(args):
         "config": {"workload": f"T+E+B constrained realizations, HEALPix N_side={NSIDE}, "
                                f"l_max={LMAX}, batch {NB} per GPU, mixed FP32 PCG + FP64-accurate "
                                f"residual replacement" + (" (double-FP32 Legendre sums)" if df else "") +
-                               f", tol 1e-6, {args.iters_per_step} "
+                               f", tol 1e-6, {args.iters_per_step} FP32 "
                                f"iterations per step" +
-                               (", synthesis Legendre sums on the tensor cores (bf16 hi/lo split)"
+                               (", Legendre sums on the tensor cores (bf16 hi/lo split)"
                                 if args.mode == "mixed_tc" else ""),
                    "mode": args.mode, "fp64_arith": args.fp64_arith, "iters_per_step": args.iters_per_step,
                    "global_batch": NB * world, "fsky": inp["fsky"], "parallelism": f"replicas x{world}",
+                   "timed_path": "default (PCG iteration replayed as a CUDA graph)",
+                   "value_counts": "FP32 PCG iterations (FP64-accurate residual replacements not counted)",
                    "l2": "inputs larger than L2 (d, w2: 2.4 GB each)"},
         "e2e": e2e, "gpu_launches": launches, "clocks": ck, "roofline": roof, "rooflines": roofs,
+        "alu_peaks": peaks_alu,
         "cpu_baseline": cpu,
-        "step": {"fp32_iterations": inner / len(stats),
-                 "fp64_residual_replacements": outer / len(stats),
+        "step": {"fp32_iterations": iters_local / len(stats),
+                 "fp64_residual_replacements": float(np.mean([s["fp64_matvecs"] for s in stats])),
                  "rel_residual_after_step": max(s["rel_residual"] for s in stats),
                  "ms_rhs": float(np.mean([s["ms_rhs"] for s in stats]))},
+        "profiled_step": {"note": "one step with per-class CUDA events (eager launches), after the timed steps",
+                          "ms_total": sp["ms_total"], "iterations": inner, "fp64_matvecs": outer},
         "kernel_share": {CLASS_NAMES[i]: round(float(kms[i]) / total_kms, 4)
                          for i in range(len(CLASS_NAMES)) if total_kms > 0},
-        "kernel_ms_per_step": {CLASS_NAMES[i]: float(kms[i]) / len(stats) for i in range(8)},
-        "kernel_launches_per_step": {CLASS_NAMES[i]: int(kcnt[i]) // len(stats) for i in range(8)},
+        "kernel_ms_per_step": {CLASS_NAMES[i]: float(kms[i]) for i in range(8)},
+        "kernel_launches_per_step": {CLASS_NAMES[i]: int(kcnt[i]) for i in range(8)},
         "extras": extras,
     }
     print(json.dumps(line), flush=True)
@@ -443,83 +610,114 @@ def run_gpu(args):
     return 0
 
 
-def measure_extras(plan, inp, dev, kw, full_solve=True):
-    """SHT pairs/s (one map, spin 0: FP32, FP64, double-FP32), the full mixed
-    solve to 1e-6 and the plain FP64-accurate PCG iteration rate on the same
-    problem (native FP64 arithmetic, and double-FP32)."""
+def run_gpu(args):
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        from paper_2306_15511_gb300.replicas import launch_local
+        launch_local(args.gpus, gpu_rank, (args,))
+        return 0
+    return gpu_rank(args)
+
+
+def _sht_rate(plan, dev, spin, nb, prec, reps):
+    import torch
+    g = torch.Generator(device=dev)
+    g.manual_seed(0)
+    ct = torch.complex64 if prec in ("fp32", "tc32") else torch.complex128
+    shape = (nb, 2, plan.nalm) if spin == 2 else (nb, plan.nalm)
+    a = torch.randn(*shape, dtype=ct, device=dev, generator=g)
+    kw = {"tensor_cores": prec == "tc32", "double_float": prec == "df64"}
+
+    def pair():
+        return plan.alm2map_adjoint(plan.alm2map(a, spin=spin, **kw), spin=spin, **kw)
+
+    pair()
+    t, _ = _event_time(pair, reps)
+    return nb / t
+
+
+def measure_extras(plan, inp, dev, kw, step, full_solve=True):
     import torch
     ex = {}
     if full_solve:
         kwf = dict(kw)
         kwf["maxiter"] = 6000
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        _, st = plan.cg_sample(inp["cl"], inp["bl"], inp["ninv"], inp["d"], inp["w1"], inp["w2"],
-                               **kwf)
-        e1.record()
-        torch.cuda.synchronize()
-        ex["mixed_full_solve"] = {"time_to_1e-6_s": e0.elapsed_time(e1) / 1000.0,
-                                  "iterations": st["iterations"],
+        t, (_, st) = _event_time(lambda: plan.cg_sample(inp["cl"], inp["bl"], inp["ninv"], inp["d"],
+                                                        inp["w1"], inp["w2"], **kwf))
+        ex["mixed_full_solve"] = {"time_to_1e-6_s": t, "iterations": st["iterations"],
                                   "fp64_matvecs": st["fp64_matvecs"],
                                   "converged": bool(st["converged"]),
                                   "rel_residual": st["rel_residual"], "ms_rhs": st["ms_rhs"]}
-    g = torch.Generator(device=dev)
-    g.manual_seed(0)
-    for prec, ct, reps, dfl in (("fp32", torch.complex64, 10, False), ("fp64", torch.complex128, 3, False),
-                                ("df64", torch.complex128, 3, True)):
-        a = torch.randn(1, plan.nalm, dtype=ct, device=dev, generator=g)
-        for _ in range(2):
-            plan.alm2map_adjoint(plan.alm2map(a, double_float=dfl), double_float=dfl)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record()
-        for _ in range(reps):
-            plan.alm2map_adjoint(plan.alm2map(a, double_float=dfl), double_float=dfl)
-        e1.record()
-        torch.cuda.synchronize()
-        ex[f"sht_pairs_per_s_{prec}_batch1"] = reps / (e0.elapsed_time(e1) / 1000.0)
-    # tensor-core synthesis + FP32 adjoint
-    a = torch.randn(1, plan.nalm, dtype=torch.complex64, device=dev, generator=g)
-    for _ in range(2):
-        plan.alm2map_adjoint(plan.alm2map(a, tensor_cores=True))
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record()
-    for _ in range(10):
-        plan.alm2map_adjoint(plan.alm2map(a, tensor_cores=True))
-    e1.record()
-    torch.cuda.synchronize()
-    ex["sht_pairs_per_s_tc32_batch1"] = 10 / (e0.elapsed_time(e1) / 1000.0)
-    # plain FP64 PCG: a fixed number of iterations timed (full convergence at
-    # this size takes minutes)
-    nit = 4
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    _, st = plan.cg_sample(inp["cl"], inp["bl"], inp["ninv"], inp["d"], inp["w1"], inp["w2"],
-                           tol=1e-6, mode="fp64", maxiter=nit, check_every=nit,
-                           allow_not_converged=True, profile=True)
-    el = time.perf_counter() - t0
-    per_it = (st["ms_solve"] / 1000.0) / max(1, st["iterations"])
-    ex["fp64_form"] = {"iterations_timed": st["iterations"], "wall_s": el,
-                       "ms_rhs": st["ms_rhs"], "s_per_iteration": per_it,
-                       "iters_per_s": 1.0 / per_it if per_it > 0 else None}
-    # the same plain PCG with its Legendre sums in double-FP32 arithmetic
-    _, st2 = plan.cg_sample(inp["cl"], inp["bl"], inp["ninv"], inp["d"], inp["w1"], inp["w2"],
-                            tol=1e-6, mode="fp64", maxiter=nit, check_every=nit,
-                            allow_not_converged=True, profile=True, fp64_arith="df64")
-    per_it2 = (st2["ms_solve"] / 1000.0) / max(1, st2["iterations"])
-    ex["fp64_form_df64"] = {"iterations_timed": st2["iterations"], "s_per_iteration": per_it2,
-                            "iters_per_s": 1.0 / per_it2 if per_it2 > 0 else None}
+    # the headline steps with native FP64 residual replacements and RHS
+    t, sts = _event_time(lambda: [step(fp64_arith="fp64") for _ in range(2)])
+    ex["steps_fp64_arith_fp64"] = {"value": sum(s["iterations"] for s in sts) / (2 * t), "unit": UNIT,
+                                   "ms_per_step": 1000.0 * t,
+                                   "fp64_matvecs_per_step": sts[0]["fp64_matvecs"]}
+    # plain FP64 PCG: per-iteration time from two budgets (4 and 8 iterations),
+    # so the RHS, the preconditioner and the final residual drop out
+    for arith in ("fp64", "df64"):
+        plan.cg_sample(inp["cl"], inp["bl"], inp["ninv"], inp["d"], inp["w1"], inp["w2"], tol=1e-6,
+                       mode="fp64", maxiter=1, allow_not_converged=True, fp64_arith=arith)   # tuning
+        runs = {}
+        for nit in (4, 8):
+            t, (_, st) = _event_time(lambda: plan.cg_sample(
+                inp["cl"], inp["bl"], inp["ninv"], inp["d"], inp["w1"], inp["w2"], tol=1e-6,
+                mode="fp64", maxiter=nit, check_every=4, allow_not_converged=True, fp64_arith=arith))
+            runs[nit] = (t, st)
+        per_it = (runs[8][0] - runs[4][0]) / (runs[8][1]["iterations"] - runs[4][1]["iterations"])
+        ex[f"fp64_form_{arith}"] = {"s_per_iteration": per_it, "iters_per_s": 1.0 / per_it,
+                                    "fixed_s": runs[4][0] - 4 * per_it,
+                                    "how": "two calls with 4 and 8 PCG iterations, difference / 4"}
+    ex["masked_nside256"] = measure_masked_pair(dev)
     if "mixed_full_solve" in ex:
         fs = ex["mixed_full_solve"]
-        # FP64 PCG needs about as many iterations as the mixed solver (they
-        # agree to within 3 % on the masked temperature workload); the FP64 form's time to
-        # 1e-6 is extrapolated from its measured per-iteration time
-        ex["fp64_form"]["time_to_1e-6_s_extrapolated"] = st["ms_rhs"] / 1000.0 + fs["iterations"] * per_it
-        ex["mixed_speedup_time_to_1e-6"] = ex["fp64_form"]["time_to_1e-6_s_extrapolated"] / fs["time_to_1e-6_s"]
+        ratio = ex["masked_nside256"]["iteration_ratio_fp64_over_mixed"]
+        f64 = ex["fp64_form_fp64"]
+        it_model = fs["iterations"] * ratio
+        ex["fp64_form_time_to_1e-6_model"] = {
+            "s": f64["fixed_s"] + it_model * f64["s_per_iteration"],
+            "iterations_model": it_model,
+            "model": ("measured fixed cost + measured s/iteration x (the mixed solve's FP32 iterations at "
+                      "this size x the FP64 / mixed iteration ratio measured to 1e-6 on the masked "
+                      "N_side 256 workload)")}
+        ex["mixed_speedup_time_to_1e-6"] = ex["fp64_form_time_to_1e-6_model"]["s"] / fs["time_to_1e-6_s"]
+    sht = {}
+    for spin in (0, 2):
+        for nb in (1, NB):
+            for prec, reps in (("fp32", 3), ("tc32", 3), ("fp64", 1), ("df64", 1)):
+                sht[f"spin{spin}_batch{nb}_{prec}"] = _sht_rate(plan, dev, spin, nb, prec, reps)
+    ex["sht_pairs_per_s"] = sht
+    ex["sht_pairs_per_s_note"] = ("one alm2map + one alm2map_adjoint per map (spin 2: per (E, B) -> "
+                                  "(Q, U) map pair), N_side 1024, l_max 2048, CUDA events")
     ex["chains"] = measure_chains(dev)
+    torch.cuda.synchronize()
     return ex
+
+
+def measure_masked_pair(dev):
+    """Both forms solved to 1e-6 on the masked temperature workload
+    (N_side 256, l_max 512): iterations and time to 1e-6 of the plain FP64
+    PCG (native FP64) and of the mixed solver (tensor cores)."""
+    import torch
+    from inputs import configs as C
+    from paper_2306_15511_gb300 import Plan
+    p = C.masked_temperature(256, 512)
+    plan = Plan(nside=256, lmax=512)
+    ls = torch.as_tensor(C.alm_lm(512)[0], device=dev)
+    a = torch.as_tensor(p.signal_alm[0], device=dev) * torch.as_tensor(p.bl, device=dev)[ls]
+    d = (plan.alm2map(a[None].contiguous()) + torch.as_tensor(p.noise_map, device=dev))[:, None].contiguous()
+    args = (p.cl, p.bl, torch.as_tensor(p.ninv, device=dev), d,
+            torch.as_tensor(p.w1[None], device=dev).contiguous(), torch.as_tensor(p.w2[None], device=dev).contiguous())
+    out = {}
+    for mode in ("mixed_tc", "fp64"):
+        plan.cg_sample(*args, tol=1e-6, mode=mode, maxiter=2)   # autotuning outside the timing
+        t, (_, st) = _event_time(lambda: plan.cg_sample(*args, tol=1e-6, mode=mode, maxiter=8000,
+                                                        check_every=8))
+        out[mode] = {"time_to_1e-6_s": t, "iterations": st["iterations"], "fp64_matvecs": st["fp64_matvecs"],
+                     "converged": bool(st["converged"]), "rel_residual": st["rel_residual"]}
+    out["iteration_ratio_fp64_over_mixed"] = out["fp64"]["iterations"] / max(1, out["mixed_tc"]["iterations"])
+    out["speedup_time_to_1e-6"] = out["fp64"]["time_to_1e-6_s"] / out["mixed_tc"]["time_to_1e-6_s"]
+    plan.close()
+    return out
 
 
 def measure_chains(dev, nchains=64):
@@ -558,7 +756,6 @@ def measure_chains(dev, nchains=64):
 
 
 def main():
-    global NSIDE, LMAX, NB
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=2)
@@ -566,7 +763,7 @@ def main():
     ap.add_argument("--impl", default="shtg", choices=["shtg", "reference"])
     ap.add_argument("--iters-per-step", type=int, default=160)
     ap.add_argument("--mode", default="mixed_tc", choices=["mixed", "mixed_tc"],
-                    help="inner FP32 operator: CUDA-core or tensor-core Legendre synthesis")
+                    help="inner FP32 operator: CUDA-core or tensor-core Legendre sums")
     ap.add_argument("--fp64-arith", default="default", choices=["default", "fp64", "df64"],
                     help="arithmetic of the FP64-accurate steps (default: double-FP32 in the mixed modes)")
     ap.add_argument("--nside", type=int, default=NSIDE, help="profiling only: smaller grid")
@@ -580,7 +777,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
-    NSIDE, LMAX, NB = args.nside, args.lmax, args.batch
+    _apply_sizes(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

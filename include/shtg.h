@@ -171,11 +171,29 @@ int shtg_map2alm(shtg_plan *plan, int spin, int precision, const void *map, void
  * sums go to a static 16 MiB device buffer inside the library.  Needs
  * 1 <= nside <= 8192, 0 <= lmax <= 4 nside and non-null buffers; sizes with
  * (4 nside - 1) (lmax + 1) 16 bytes > 16 MiB (e.g. nside 512, lmax 1024)
- * return SHTG_ERR_ARG like any other invalid argument.  The first call on a device looks the buffer's device
- * address up (cudaGetSymbolAddress); make that first call before any stream
- * capture.  Every call on a device shares the buffer: calls whose kernels may
- * overlap on the GPU race on it.  Allocates nothing. */
+ * return SHTG_ERR_ARG like any other invalid argument.  The first call on a
+ * device does the set-up: it looks the buffer's device address up
+ * (cudaGetSymbolAddress) and caches it for that device.  With lazy module
+ * loading (the CUDA default) that lookup also loads this part of the library
+ * onto the device, which reserves the 16 MiB buffer and may synchronize the
+ * device; so make the first call during set-up, outside any stream capture
+ * and outside any region whose memory budget or timing must not be touched.
+ * The cached address does not survive cudaDeviceReset: do not call this entry
+ * point on a device after resetting it.  Every call on a device shares the
+ * buffer: calls whose kernels may overlap on the GPU race on it.  Each c_lm is
+ * accumulated from the ring pairs with FP64 atomic additions, whose order
+ * varies from run to run, so two identical calls may differ by rounding
+ * (results are not bitwise reproducible; the plan-based transpose is).
+ * Allocates nothing after that set-up. */
 int shtg_alm2map_adjoint_noalloc(int nside, int lmax, const double *map, double *alm, void *stream);
+
+/* Measurement helper (the paper has no counterpart): the fused multiply-add
+ * throughput of the current device at its current clocks, for the roofline
+ * of the Legendre kernels.  precision: SHTG_FP32 or SHTG_FP64.  Each thread
+ * of a grid that fills every SM runs 8 independent FMA chains; 2 flops per
+ * FMA.  Writes the SM count and the measured TFLOP/s; synchronizes the
+ * stream; allocates and frees a small output buffer (stream-ordered). */
+int shtg_probe_fma_peak(int precision, int *sm_count, double *tflops, void *stream);
 
 /* ------------------------------------------------- constrained realization */
 typedef struct {

@@ -42,6 +42,8 @@ def lib():
             L = C.CDLL(LIB)
             ci = C.c_int
             L.orc_abi_version.restype = ci
+            L.orc_set_threads.argtypes = [ci]
+            L.orc_set_threads.restype = ci
             L.orc_healpix_geom.argtypes = [ci, _D, _D, _I64, _D, _I64]
             L.orc_gl_geom.argtypes = [ci, _D, _D, _D]
             L.orc_lambda.argtypes = [ci, ci, C.c_double, C.c_double, _D]

@@ -22,13 +22,22 @@
  * OpenMP only distributes independent rings or independent m values.
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
 
 #define ORC_PI 3.14159265358979323846264338327950288
 
-int orc_abi_version(void) { return 3; }
+int orc_abi_version(void) { return 4; }
+
+/* Worker threads of the OpenMP loops below (n > 0 sets them; every call
+ * returns the count in force).  Used only to time the oracle on one core. */
+int orc_set_threads(int n)
+{
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+}
 
 /* ------------------------------------------------------------------------- */
 /* geometry                                                                  */

@@ -28,7 +28,7 @@ SYMBOLS = ("shtg_plan_create", "shtg_plan_destroy", "shtg_plan_get_info",
            "shtg_last_error_string", "shtg_version", "shtg_alm2map", "shtg_alm2map_adjoint",
            "shtg_alm2map_vjp",
            "shtg_map2alm", "shtg_cg_sample", "shtg_cg_sample_chains", "shtg_apply_operator",
-           "shtg_logpost_grad")
+           "shtg_logpost_grad", "shtg_probe_fma_peak")
 
 
 class PlanInfo(C.Structure):
@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True):
         L.shtg_apply_operator.argtypes = [vp, C.POINTER(Problem), vp, vp, vp]
         L.shtg_logpost_grad.argtypes = [vp, vp, vp, vp, vp, vp, ci, vp, vp, ci, C.POINTER(cd),
                                         vp, vp, vp]
+        L.shtg_probe_fma_peak.argtypes = [ci, C.POINTER(ci), C.POINTER(cd), vp]
         for s in SYMBOLS:
             if s != "shtg_last_error_string":
                 getattr(L, s).restype = ci

@@ -262,6 +262,16 @@ class Plan:
         return logp.value, g, gcl
 
 
+def fma_peak(precision: str = "fp32"):
+    """Measured FMA throughput of the current GPU: (SM count, TFLOP/s) for
+    precision "fp32" or "fp64" (2 flops per FMA)."""
+    lib = N.load()
+    sms, tf = C.c_int(0), C.c_double(0.0)
+    N.check(lib.shtg_probe_fma_peak(N.FP32 if precision == "fp32" else N.FP64, C.byref(sms),
+                                    C.byref(tf), _stream()))
+    return sms.value, tf.value
+
+
 def chains_sample(groups, tol: float = 1e-6, mode: str = "mixed_tc", maxiter: int = 4000,
                   precond: bool = True, reliable_delta: float = 1e-2, check_every: int = 4,
                   allow_not_converged: bool = False, graphs: bool = True, fp64_arith: str = "default"):

@@ -11,6 +11,14 @@
 // contents; each call overwrites every element it reads, and the output is
 // zeroed before it is accumulated.  Calls whose kernels overlap on the GPU
 // (different streams, or different host threads) race on the buffer.
+//
+// The buffer's device address is looked up once per device, on the first
+// call; under lazy module loading that lookup also loads this module onto the
+// device and so reserves the 16 MiB.  A cudaDeviceReset invalidates the cached
+// address, so the entry point is not for use on a device after a reset.  The
+// transpose accumulates each c_lm from all ring pairs with FP64 atomic
+// additions; their order is not fixed, so repeated calls agree only to
+// rounding.
 #include <mutex>
 
 #include "common.cuh"

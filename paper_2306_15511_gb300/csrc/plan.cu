@@ -10,6 +10,7 @@
 // the near-polar rings exact in FP32, where cos theta rounds to 1.
 #include <cmath>
 #include <complex>
+#include <cstdlib>
 #include <cstring>
 #include <algorithm>
 #include <functional>
@@ -767,6 +768,13 @@ int check_device_flag(Plan *p, cudaStream_t st) {
     int h = 0;
     SHTG_CUDA(cudaMemcpyAsync(&h, p->d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     SHTG_CUDA(cudaStreamSynchronize(st));
+    // Host-side fault injection for tests of the error path: with
+    // SHTG_FAKE_WAIT_EXPIRY=1 in the environment the flag reads as set, as if
+    // a kernel's bounded wait had expired (no device wait is forced to expire).
+    {
+        const char *e = getenv("SHTG_FAKE_WAIT_EXPIRY");
+        if (e && e[0] == '1') h = 1;
+    }
     if (h) {
         SHTG_CUDA(cudaMemsetAsync(p->d_flag, 0, sizeof(int), st));
         set_error("a tensor-core kernel gave up waiting for its MMAs (bounded mbarrier wait expired)");

@@ -1117,6 +1117,12 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
     }
     std::vector<double> bb;
     SHTG_TRY(norms2(s, B, bb));
+    for (int b = 0; b < nb; ++b)
+        if (!std::isfinite(bb[b])) {
+            set_error("non-finite right-hand side in realization " + std::to_string(b) +
+                      ": d, w1, w2 or N^-1 holds NaN or Inf");
+            return SHTG_ERR_NONFINITE;
+        }
     const double t1 = now_ms();
     stt.ms_setup = 0;
     stt.ms_rhs = t1 - t0;

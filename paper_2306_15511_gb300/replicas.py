@@ -14,10 +14,19 @@ from __future__ import annotations
 
 import os
 
-# Philox keys of the white noise w2 for realization b of rank r: ranks > 0
-# draw fresh keys so that replicas are independent chains; rank 0 keeps the
-# recipe's own keys.
+# Philox keys of the white noise (w1 in harmonic space, w2 in pixel space)
+# for realization b of rank r: ranks > 0 draw fresh keys for both, so that
+# replicas are independent chains; rank 0 keeps the recipe's own keys.
+_W1_KEY_BASE = 40000
 _W2_KEY_BASE = 50000
+
+
+def w1_key(rank: int, b: int) -> int | None:
+    """Philox key for realization b's harmonic white noise on a rank (None:
+    the recipe's default key)."""
+    if rank == 0:
+        return None
+    return _W1_KEY_BASE + 100 * rank + b
 
 
 def w2_key(rank: int, b: int) -> int | None:
@@ -26,6 +35,31 @@ def w2_key(rank: int, b: int) -> int | None:
     if rank == 0:
         return None
     return _W2_KEY_BASE + 100 * rank + b
+
+
+def free_port() -> int:
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_entry(rank, world, port, fn, args):
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank),
+                      MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    rc = fn(*args)
+    if rc:
+        raise SystemExit(rc)
+
+
+def launch_local(nprocs: int, fn, args=()) -> None:
+    """Run fn(*args) in nprocs spawned processes, one per local GPU, with the
+    torchrun environment (RANK, WORLD_SIZE, LOCAL_RANK, MASTER_ADDR =
+    127.0.0.1, MASTER_PORT) set in each; returns when all have exited and
+    raises if one failed.  fn must be importable (a module-level function)."""
+    import torch.multiprocessing as mp
+    mp.start_processes(_rank_entry, args=(nprocs, free_port(), fn, tuple(args)), nprocs=nprocs,
+                       join=True, start_method="spawn")
 
 
 class Replicas:

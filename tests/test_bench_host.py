@@ -62,11 +62,15 @@ def test_oracle_fit_falls_back_on_noisy_samples(monkeypatch):
 
 
 def _fake_sample(**kw):
-    return {"value": 2.5e-3, "unit": bench.UNIT, "cores": 16, "kind": "oracle", "sample": "fake"}
+    time.sleep(0.01)
+    return {"value": 2.5e-3, "unit": bench.UNIT, "cores": 16, "kind": "oracle", "sample": "fake",
+            "per_realization_s": 1.0 / (2.5e-3 * bench.NB)}
 
 
 def test_reference_line_contract(monkeypatch, capsys):
     monkeypatch.setattr(bench, "oracle_sample", _fake_sample)
+    monkeypatch.setattr(bench, "oracle_full_grid", lambda: 55.0)
+    monkeypatch.setattr(bench, "oracle_extras", lambda: {"cores": 16})
     monkeypatch.delenv("RANK", raising=False)
     args = argparse.Namespace(steps=2, warmup=3, gpus=1)
     assert bench.run_reference(args) == 0
@@ -80,7 +84,8 @@ def test_reference_line_contract(monkeypatch, capsys):
     assert d["impl"] == "reference"
     assert d["metric"] == bench.METRIC and d["unit"] == bench.UNIT
     assert d["value"] == pytest.approx(2.5e-3)
-    assert d["ms_per_step"] == pytest.approx(1000.0 / 2.5e-3)
+    # ms_per_step is the wall time of one bounded sample step, not 1 / value
+    assert 5.0 <= d["ms_per_step"] < 1000.0
     assert d["higher_is_better"] is True and d["vs_baseline"] is None
     assert d["steps"] == 2 and d["warmup"] == 3
     assert "workload" in d["config"]
@@ -89,6 +94,10 @@ def test_reference_line_contract(monkeypatch, capsys):
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+    fc = d["fit_check"]
+    assert fc["full_grid_operator_s"] == 55.0
+    assert fc["fit_predicted_s"] == pytest.approx(50.0)
+    assert fc["rel_err"] == pytest.approx(-5.0 / 55.0)
 
 
 def test_reference_other_ranks_print_nothing(monkeypatch, capsys):
@@ -98,15 +107,40 @@ def test_reference_other_ranks_print_nothing(monkeypatch, capsys):
     assert capsys.readouterr().out.strip() == ""
 
 
-def test_flop_counts_and_alu_peaks():
+def test_flop_counts():
     # per (l, m, ring pair): 4 flops per temperature map, 16 per (Q, U) pair
     assert bench.contraction_flops(10, 3, 2, 1) == 10 * 3 * (4 * 2 + 16 * 1)
     # plus the recurrence: 3 shared (spin 0) and 8 shared (spin 2)
     assert bench.legendre_flops(10, 3, 2, 1) == 10 * 3 * ((3 + 4 * 2) + (8 + 16 * 1))
     assert bench.legendre_flops(10, 3, 2, 0) == 10 * 3 * (3 + 4 * 2)
-    fp32, fp64 = bench.alu_peaks(2070.0)
-    assert fp32 == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
-    assert fp64 == pytest.approx(1.25)
+
+
+def test_ring_fft_flops_counts_one_dft_per_ring_pair():
+    import math
+    # N_side 1: no polar pairs, two equatorial pairs of n = 4 (one is the equator alone)
+    assert bench.ring_fft_flops(1) == 2 * 5 * 4 * 2
+    # N_side 2: polar pair n = 4, three equatorial pairs of n = 8
+    assert bench.ring_fft_flops(2) == 5 * 4 * 2 + 3 * 5 * 8 * 3
+    # the pairs cover every ring: 2 sum(n) - n_equator = 12 N^2 pixels
+    n = 64
+    pix = 2 * sum(4 * i for i in range(1, n)) + (n + 1) * 2 * 4 * n - 4 * n
+    assert pix == 12 * n * n
+    assert bench.ring_fft_flops(n) > 5 * 4 * n * math.log2(4 * n) * (n + 1)
+
+
+def test_traffic_record_needs_unchanged_sources(monkeypatch, tmp_path):
+    (tmp_path / "profiles").mkdir()
+    csrc = tmp_path / "paper_2306_15511_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (csrc / "ringfft.cu").write_text("kernel v1")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    sha = bench.sources_hash(["ringfft.cu"])
+    (tmp_path / "profiles" / "traffic.json").write_text(
+        json.dumps({"ring_fft_fp32": {"dram_bytes_per_unit": 20.0, "sources_sha": sha}}))
+    assert bench.traffic_record("ring_fft_fp32", 1000) == 20000.0
+    assert bench.traffic_record("leg_synth_fp32", 1000) is None
+    (csrc / "ringfft.cu").write_text("kernel v2")
+    assert bench.traffic_record("ring_fft_fp32", 1000) is None
 
 
 def test_clock_sampler_parses_nvidia_smi_rows(tmp_path):

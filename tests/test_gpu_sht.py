@@ -127,16 +127,26 @@ def test_vjp_is_component_gradient():
 
 # Sampled-ring checks at full size: every 97th ring (a pixel-weighted sample
 # of the whole map, so its relative L2 estimates the full-map error) and,
-# separately, the polar rings.  FP32 near the poles: the three-term recurrence
-# at theta -> 0 has a near-double root, and rounding grows like
-# eps / theta there, so the first rings carry ~1e-4..1e-3 relative error in
-# FP32; FP64 meets 1e-10 everywhere.
+# separately, the polar rings, where FP64 meets 1e-10 as everywhere else.
 FULL_RINGS = list(range(0, 4095, 97))
 POLAR_RINGS = [0, 1, 2, 3, 4094, 4093]
-# FP32 on the polar rings: rounding grows ~ u l / theta there (theta_0 =
-# sqrt(2/3)/N_side for the first HEALPix ring), a bound of ~0.15 at
-# N_side 1024, l_max 2048; measured: ~5e-3 (spin 0) and ~1.2e-2 (spin 2).
-POLAR_TOL = {"fp64": 1e-10, "fp32": 2.0 ** -24 * 2048 / (0.8165 / 1024)}
+
+
+def polar_tol(prec, spin, L):
+    """FP32 on the first polar rings.  For theta -> 0 the two roots of the
+    three-term l-recurrence merge (e^{+-i theta}), so a rounding of relative
+    size u = 2^-24 made at step k grows like sin((l - k) theta) / sin(theta)
+    ~ (l - k) while l theta < 1 (l_max theta_0 ~ 1.6 on the first ring of
+    N_side 1024).  Independent roundings at every step then add up to a
+    relative error of about u sqrt(sum_k (l - k)^2) ~ u l_max^{3/2} / sqrt(3)
+    per rounding per step: c u l_max^{3/2} with c ~ 1 for the spin-0
+    recurrence (three roundings a step) and c ~ 2 for the two coupled spin-2
+    recurrences (measured at l_max 2048: 5e-3 and 1.2e-2 against
+    u l_max^{3/2} = 5.5e-3).  The gate is twice that, so a threefold
+    regression fails."""
+    if prec == "fp64":
+        return 1e-10
+    return (2.0 if spin == 0 else 4.0) * 2.0 ** -24 * L ** 1.5
 
 
 def _ring_err(m, g, rings, ref):
@@ -158,7 +168,9 @@ def test_fullsize_nside1024_sampled_rings(prec):
     ct, rt = _dt(prec)
     m = plan.alm2map(torch.tensor(a, dtype=ct, device="cuda")).cpu().numpy()[0]
     assert _ring_err(m, g, FULL_RINGS, osht.alm2map(g.subset(FULL_RINGS), L, a[0])) < tol_for(prec, L)
-    assert _ring_err(m, g, POLAR_RINGS, osht.alm2map(g.subset(POLAR_RINGS), L, a[0])) < POLAR_TOL[prec]
+    ep = _ring_err(m, g, POLAR_RINGS, osht.alm2map(g.subset(POLAR_RINGS), L, a[0]))
+    print(f"{prec} spin 0 polar rings: relative error {ep:.3e} (gate {polar_tol(prec, 0, L):.3e})")
+    assert ep < polar_tol(prec, 0, L)
     mp = rng.normal(size=(1, g.npix))
     ad = plan.alm2map_adjoint(torch.tensor(mp, dtype=rt, device="cuda")).cpu().numpy()[0]
     mlist = [0, 1, 2, 700, 1500, 2047, 2048]
@@ -178,9 +190,11 @@ def test_fullsize_nside1024_spin2_sampled(prec):
     eb = rand_alm(L, rng, (1, 2), lsc)
     ct, rt = _dt(prec)
     qu = plan.alm2map(torch.tensor(eb, dtype=ct, device="cuda"), spin=2).cpu().numpy()[0]
-    for rings, tol in ((FULL_RINGS, tol_for(prec, L)), (POLAR_RINGS, POLAR_TOL[prec])):
+    for rings, tol in ((FULL_RINGS, tol_for(prec, L)), (POLAR_RINGS, polar_tol(prec, 2, L))):
         Q, U = osht.alm2map_spin2(g.subset(rings), L, eb[0, 0], eb[0, 1])
-        assert _ring_err(qu, g, rings, np.stack([Q, U])) < tol, rings[:3]
+        e = _ring_err(qu, g, rings, np.stack([Q, U]))
+        print(f"{prec} spin 2 rings {rings[:3]}...: relative error {e:.3e} (gate {tol:.3e})")
+        assert e < tol, rings[:3]
     mp = rng.normal(size=(1, 2, g.npix))
     ad = plan.alm2map_adjoint(torch.tensor(mp, dtype=rt, device="cuda"), spin=2).cpu().numpy()[0]
     mlist = [0, 1, 2, 1000, 2048]

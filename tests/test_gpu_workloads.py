@@ -1,0 +1,128 @@
+"""The masked temperature, log-posterior and chains workloads at their stated
+sizes, through the C ABI, against the FP64 oracle.
+
+- Masked temperature (N_side 256, l_max 512, hits-weighted noise, |b| < 20 deg
+  plus 50 holes): plain FP64 PCG and both mixed forms to 1e-6; the
+  oracle-evaluated residual of each GPU solution is <= 1.05e-6 and its
+  relative L2 distance to the oracle's solution converged to 1e-11 (stored
+  by tests/golden/make_masked_solution.py, which calls only the oracle) is
+  <= 1e-5.
+- Log-posterior (N_side 512, l_max 1024, 50 bins of width 20): value and
+  gradients (FP32 transforms) against the oracle's.
+- Chains: the N_side 256 geometries of the mixed-geometry recipe (l_max 512
+  and 767) in one chains call; every chain's oracle-evaluated residual.
+"""
+import os
+
+import numpy as np
+import pytest
+
+from inputs import configs as C
+from oracle import sht as osht
+from oracle import solver as osol
+from tests._util import rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "masked_t_n256_l512_x.npy")
+
+
+def _cuda(x, dt):
+    return torch.tensor(np.ascontiguousarray(x), dtype=dt, device="cuda")
+
+
+def _data_t(p, g):
+    ls = osht.ls_of(p.lmax)
+    return osht.alm2map(g, p.lmax, p.signal_alm[0] * p.bl[ls]) + p.noise_map[0]
+
+
+@pytest.fixture(scope="module")
+def masked():
+    p = C.masked_temperature(256, 512)
+    g = osht.healpix(256)
+    d = _data_t(p, g)
+    prob = osol.Problem(g, 512, p.cl, p.bl, p.ninv)
+    b = prob.rhs(d[None], p.w1, p.w2)
+    return p, g, d, prob, b, np.load(GOLDEN)
+
+
+@pytest.fixture(scope="module")
+def masked_plan():
+    from paper_2306_15511_gb300 import Plan
+    return Plan(nside=256, lmax=512)
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed", "mixed_tc"])
+def test_masked_full_size(mode, masked, masked_plan):
+    p, g, d, prob, b, xref = masked
+    x, st = masked_plan.cg_sample(p.cl, p.bl, _cuda(p.ninv, torch.float64), _cuda(d[None, None], torch.float64),
+                                  _cuda(p.w1[None], torch.complex128), _cuda(p.w2[None], torch.float64),
+                                  tol=1e-6, mode=mode, maxiter=8000, check_every=8)
+    assert st["converged"] == 1, st
+    xh = x.cpu().numpy()[0]
+    res = osol.true_residual(prob, xh, b)
+    err = rel_l2(xh[0], xref)
+    print(f"masked N_side 256 / l_max 512 {mode}: {st['iterations']} iterations, "
+          f"{st['fp64_matvecs']} FP64 operator applications, oracle residual {res:.3e}, "
+          f"error vs oracle solution {err:.3e}")
+    assert res <= 1.05e-6, (res, st)
+    assert err <= 1e-5, err
+
+
+def test_logposterior_full_size():
+    """Log-posterior workload at N_side 512, l_max 1024 with the 50 bins of 20
+    multipoles (l = 2 .. 1001): value and gradients against the oracle."""
+    from paper_2306_15511_gb300 import Plan
+    p = C.logpost_temperature()
+    g = osht.healpix(512)
+    L = p.lmax
+    d = _data_t(p, g)
+    prob = osol.Problem(g, L, p.cl, p.bl, p.ninv)
+    a = p.signal_alm.copy()
+    a[:, osht.ls_of(L) < 2] = 0
+    bins = [(2 + 20 * k, 21 + 20 * k) for k in range(50)]
+    lp_ref = osol.log_posterior(prob, a, d)
+    ga_ref, gl_ref = osol.log_posterior_grad(prob, a, d, bins)
+    plan = Plan(nside=512, lmax=L)
+    lp, ga, gl = plan.logpost_grad(p.cl, p.bl, _cuda(a[0], torch.complex64), _cuda(d, torch.float32),
+                                   _cuda(p.ninv, torch.float32), bins)
+    e_lp = abs(lp - lp_ref) / abs(lp_ref)
+    e_ga = rel_l2(ga.cpu().numpy(), ga_ref[0])
+    e_gl = rel_l2(gl, gl_ref)
+    print(f"log-posterior N_side 512 / l_max 1024: value {e_lp:.2e}, grad alm {e_ga:.2e}, "
+          f"grad log C_l bins {e_gl:.2e}")
+    assert e_lp < 1e-5
+    assert e_ga < 1e-4
+    assert e_gl < 1e-5
+
+
+def test_chains_nside256_groups():
+    """The recipe's N_side 256 chains (l_max 512 and 767), two per geometry,
+    in one chains call with the tensor-core inner solver."""
+    from paper_2306_15511_gb300 import Plan, chains_sample
+    keep = {}
+    for ch in C.mixed_geometry_chains(64):
+        if ch.nside == 256 and len(keep.setdefault((ch.nside, ch.lmax), [])) < 2:
+            keep[(ch.nside, ch.lmax)].append(ch)
+    assert sorted(keep) == [(256, 512), (256, 767)]
+    req, refs = [], []
+    for (ns, L), chs in sorted(keep.items()):
+        g = osht.healpix(ns)
+        d = np.stack([_data_t(ch, g)[None] for ch in chs])
+        plan = Plan(nside=ns, lmax=L, max_batch=len(chs))
+        req.append({"plan": plan, "cl": C.cl_flat(L), "bl": chs[0].bl,
+                    "ninv": _cuda(chs[0].ninv, torch.float64), "d": _cuda(d, torch.float64),
+                    "w1": _cuda(np.stack([ch.w1 for ch in chs]), torch.complex128),
+                    "w2": _cuda(np.stack([ch.w2 for ch in chs]), torch.float64),
+                    "cl_scale": [ch.extra["amp"] for ch in chs]})
+        refs.append((g, chs, d))
+    res = chains_sample(req, tol=1e-6, mode="mixed_tc", maxiter=6000)
+    for (x, st), (g, chs, d) in zip(res, refs):
+        assert st["converged"] == 1, st
+        xh = x.cpu().numpy()
+        for k, ch in enumerate(chs):
+            prob = osol.Problem(g, ch.lmax, ch.cl, ch.bl, ch.ninv)
+            r = osol.true_residual(prob, xh[k], prob.rhs(d[k], ch.w1, ch.w2))
+            print(f"chain {ch.name} N_side {ch.nside} l_max {ch.lmax}: oracle residual {r:.3e}")
+            assert r <= 1.05e-6, (ch.name, r, st)
