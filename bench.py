@@ -709,7 +709,7 @@ def measure_masked_pair(dev):
             torch.as_tensor(p.w1[None], device=dev).contiguous(), torch.as_tensor(p.w2[None], device=dev).contiguous())
     out = {}
     for mode in ("mixed_tc", "fp64"):
-        plan.cg_sample(*args, tol=1e-6, mode=mode, maxiter=2)   # autotuning outside the timing
+        plan.cg_sample(*args, tol=1e-6, mode=mode, maxiter=2, allow_not_converged=True)   # autotuning
         t, (_, st) = _event_time(lambda: plan.cg_sample(*args, tol=1e-6, mode=mode, maxiter=8000,
                                                         check_every=8))
         out[mode] = {"time_to_1e-6_s": t, "iterations": st["iterations"], "fp64_matvecs": st["fp64_matvecs"],

@@ -94,6 +94,12 @@ extern "C" {
 
 #define SHTG_HOST_INPUTS 1           /* cg_sample flag: problem maps/alm and output are host pointers */
 #define SHTG_PROFILE 2               /* cg_sample flag: time kernel classes with CUDA events */
+#define SHTG_SPLIT_RHS 8             /* cg_sample flag: solve the mean field of Eq. (mean-field-map),
+                                        A a^ = B Y^T N^-1 d, and the fluctuation of Eq. (fluc-map),
+                                        A f^ = S^-1/2 w1 + B Y^T N^-1/2 w2, as 2 nbatch systems of one
+                                        batch; alm_out is then [2][nbatch][ncomp][nalm] (the nbatch
+                                        mean fields, then the nbatch fluctuations; a = a^ + f^) and the
+                                        plan needs max_batch >= 2 nbatch */
 #define SHTG_NO_GRAPHS 4             /* cg_sample flag: launch every PCG iteration eagerly instead of
                                         replaying one captured iteration as a CUDA graph (graphs are
                                         also off with SHTG_PROFILE, or with SHTG_GRAPHS=0 in the
@@ -279,6 +285,37 @@ int shtg_cg_sample_chains(int ngroups, shtg_plan *const *plans, const shtg_probl
 int shtg_apply_operator(shtg_plan *plan, const shtg_problem *prob, const double *x, double *y,
                         void *stream);
 
+/* ------------------------------------------- joint (C_l, a) move (Sect. 2.2.2) */
+/* The deterministic rescaling of the fluctuation term,
+ * f^scaled_lm = (C'_l)^{1/2} (C_l)^{-1/2} f^_lm, per l with the T/E/B block
+ * of Sect. 2.2.2 (EB = TB = 0) and the symmetric principal square roots;
+ * multipoles where either block is singular are set to 0.  cl_old, cl_new:
+ * HOST, as shtg_problem.cl ([lmax+1] for ncomp 1, [4][lmax+1] = TT, EE, BB,
+ * TE for ncomp 3).  f, f_out: device [nbatch][ncomp][nalm] complex128 (may be
+ * the same buffer).  Synchronizes the stream. */
+int shtg_fluctuation_rescale(shtg_plan *plan, int ncomp, const double *cl_old, const double *cl_new,
+                             const double *f, double *f_out, int nbatch, void *stream);
+
+/* log pi(theta) of the joint move's acceptance rule (Eq. acceptance-rate),
+ * per realization b of prob (cl, bl, ninv, d, nbatch, ncomp, cl_scale used):
+ * log pi = -1/2 (d - Y B a^)^T N^-1 (d - Y B a^) - 1/2 a^T S^-1 a^
+ *          - 1/2 f^T B Y^T N^-1 Y B f^
+ * with a^ the mean field and f^ the (scaled, for a proposal) fluctuation;
+ * alm products in the metric above, S^-1 over the multipoles with a
+ * non-singular block.  The prior term, printed with a and a^, is read as
+ * a^T S^-1 a^.  a_hat, f_hat: device [nbatch][ncomp][nalm] complex128; d as in
+ * shtg_problem (device).  precision SHTG_FP64 or SHTG_DF64 selects the
+ * arithmetic of the synthesis (both FP64-accurate); sums in FP64.
+ * log_pi: HOST [nbatch].  Synchronizes the stream. */
+int shtg_joint_log_target(shtg_plan *plan, const shtg_problem *prob, int precision, const double *a_hat,
+                          const double *f_hat, double *log_pi, void *stream);
+
+/* Acceptance probability of the joint move (Eq. acceptance-rate):
+ * A = min[1, pi(theta') P(theta') / (pi(theta) P(theta))] from the logs of
+ * pi and of the prior P.  Host arithmetic only (no device work). */
+int shtg_joint_acceptance(double log_pi_new, double log_pi_old, double log_prior_new, double log_prior_old,
+                          double *accept);
+
 /* --------------------------------------------------- log-posterior (grad) */
 #define SHTG_GRAD_COMPONENTS 1   /* logpost flag: grad_alm as d/dRe + i d/dIm (x2 for m > 0) */
 
@@ -295,6 +332,15 @@ int shtg_logpost_grad(shtg_plan *plan, const double *cl, const double *bl, const
                       const float *d, const float *ninv, int nbins, const int *bin_lo,
                       const int *bin_hi, int flags, double *logp, float *grad_alm,
                       double *grad_logcl, void *stream);
+
+/* The same with the binned log C_l parameters of the joint posterior: C_l is
+ * replaced by C_l exp(theta[k]) on the multipoles [bin_lo[k], bin_hi[k]]
+ * (theta HOST [nbins], or NULL for theta = 0) before the evaluation, and
+ * grad_theta[k] = d L / d theta_k.  Other arguments as shtg_logpost_grad. */
+int shtg_logpost_grad_binned(shtg_plan *plan, const double *cl, const double *bl, const float *alm,
+                             const float *d, const float *ninv, int nbins, const int *bin_lo,
+                             const int *bin_hi, const double *theta, int flags, double *logp,
+                             float *grad_alm, double *grad_theta, void *stream);
 
 #ifdef __cplusplus
 }

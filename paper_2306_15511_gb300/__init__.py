@@ -6,6 +6,6 @@ hand-written in CUDA for sm_103a (libshtg.so, C ABI in include/shtg.h).
 
 The CUDA library is loaded on first use; there is no CPU fallback.
 """
-from .api import Plan, chains_sample  # noqa: F401
+from .api import Plan, chains_sample, joint_acceptance  # noqa: F401
 
-__all__ = ["Plan", "chains_sample"]
+__all__ = ["Plan", "chains_sample", "joint_acceptance"]

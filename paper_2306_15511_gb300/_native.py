@@ -21,6 +21,7 @@ CG_FP64, CG_MIXED, CG_MIXED_TC = 0, 1, 2
 HOST_INPUTS = 1
 PROFILE = 2
 NO_GRAPHS = 4
+SPLIT_RHS = 8
 GRAD_COMPONENTS = 1
 
 # every symbol include/shtg.h declares
@@ -28,7 +29,8 @@ SYMBOLS = ("shtg_plan_create", "shtg_plan_destroy", "shtg_plan_get_info",
            "shtg_last_error_string", "shtg_version", "shtg_alm2map", "shtg_alm2map_adjoint",
            "shtg_alm2map_vjp",
            "shtg_map2alm", "shtg_cg_sample", "shtg_cg_sample_chains", "shtg_apply_operator",
-           "shtg_logpost_grad", "shtg_probe_fma_peak")
+           "shtg_logpost_grad", "shtg_probe_fma_peak", "shtg_fluctuation_rescale",
+           "shtg_joint_log_target", "shtg_joint_acceptance", "shtg_logpost_grad_binned")
 
 
 class PlanInfo(C.Structure):
@@ -103,6 +105,11 @@ def load(build_if_missing: bool = True):
         L.shtg_logpost_grad.argtypes = [vp, vp, vp, vp, vp, vp, ci, vp, vp, ci, C.POINTER(cd),
                                         vp, vp, vp]
         L.shtg_probe_fma_peak.argtypes = [ci, C.POINTER(ci), C.POINTER(cd), vp]
+        L.shtg_fluctuation_rescale.argtypes = [vp, ci, vp, vp, vp, vp, ci, vp]
+        L.shtg_joint_log_target.argtypes = [vp, C.POINTER(Problem), ci, vp, vp, vp, vp]
+        L.shtg_joint_acceptance.argtypes = [cd, cd, cd, cd, C.POINTER(cd)]
+        L.shtg_logpost_grad_binned.argtypes = [vp, vp, vp, vp, vp, vp, ci, vp, vp, vp, ci, C.POINTER(cd),
+                                               vp, vp, vp]
         for s in SYMBOLS:
             if s != "shtg_last_error_string":
                 getattr(L, s).restype = ci

@@ -188,10 +188,15 @@ class Plan:
                   maxiter: int = 4000, precond: bool = True, reliable_delta: float = 1e-2,
                   check_every: int = 4, out=None,
                   allow_not_converged: bool = False, profile: bool = False, graphs: bool = True,
-                  cl_scale=None, fp64_arith: str = "default"):
+                  cl_scale=None, fp64_arith: str = "default", split: bool = False):
         """Constrained realization(s) of Eq. (mapmakingeq).
 
         cl_scale: optional [nbatch] amplitudes; realization b uses cl_scale[b] x cl.
+
+        split: solve the mean field (Eq. mean-field-map) and the fluctuation
+        (Eq. fluc-map) as separate systems of one batch; the result is then
+        [2, nbatch, ncomp, nalm] (mean fields, fluctuations) and the plan
+        needs max_batch >= 2 nbatch.
 
         fp64_arith: arithmetic of the FP64-accurate steps (RHS, residual
         replacements; the whole solve in mode "fp64"): "default" (double-FP32
@@ -206,11 +211,14 @@ class Plan:
         inside the library.  Returns (alm [nbatch, ncomp, nalm], stats dict)."""
         host = not (isinstance(d, torch.Tensor) and d.is_cuda)
         nb, nc = int(d.shape[0]), int(d.shape[1])
+        nsys = 2 * nb if split else nb
         if out is None:
             if host:
-                out = torch.empty(nb, nc, self.nalm, dtype=torch.complex128).pin_memory()
+                out = torch.empty(nsys, nc, self.nalm, dtype=torch.complex128).pin_memory()
             else:
-                out = torch.empty(nb, nc, self.nalm, dtype=torch.complex128, device=d.device)
+                out = torch.empty(nsys, nc, self.nalm, dtype=torch.complex128, device=d.device)
+        if out.numel() != nsys * nc * self.nalm:
+            raise ValueError("out must hold [2 nbatch if split else nbatch, ncomp, nalm] complex128")
         for t, name in ((d, "d"), (w1, "w1"), (w2, "w2"), (ninv, "ninv"), (out, "out")):
             if isinstance(t, torch.Tensor):
                 if t.is_cuda == host:
@@ -227,12 +235,45 @@ class Plan:
         o.precond = 1 if precond else 0
         o.reliable_delta, o.fp64_arith = float(reliable_delta), _arith(fp64_arith)
         o.check_every = int(check_every)
-        o.flags = (N.HOST_INPUTS if host else 0) | (N.PROFILE if profile else 0) | (0 if graphs else N.NO_GRAPHS)
+        o.flags = ((N.HOST_INPUTS if host else 0) | (N.PROFILE if profile else 0) |
+                   (0 if graphs else N.NO_GRAPHS) | (N.SPLIT_RHS if split else 0))
         st = N.CGStats()
         rc = self._lib.shtg_cg_sample(self._h, C.byref(pr), _ptr(out), C.byref(o), C.byref(st),
                                       _stream())
         N.check(rc, allow=(-3,) if allow_not_converged else ())
+        if split:
+            out = out.view(2, nb, nc, self.nalm)
         return out, st.as_dict()
+
+    # ----------------------------------------------------------- joint move
+    def fluctuation_rescale(self, cl_old, cl_new, f: torch.Tensor, out=None) -> torch.Tensor:
+        """f^scaled = (C'_l)^{1/2} (C_l)^{-1/2} f (Sect. 2.2.2) for f
+        [nbatch, ncomp, nalm] complex128 (CUDA); cl as for cg_sample."""
+        _need_cuda(f, "f")
+        nb, nc = int(f.shape[0]), int(f.shape[1])
+        if f.dtype != torch.complex128 or f.shape[-1] != self.nalm:
+            raise ValueError("f must be [nbatch, ncomp, nalm] complex128")
+        out = torch.empty_like(f) if out is None else out
+        co, cn = self._host_f64(cl_old), self._host_f64(cl_new)
+        N.check(self._lib.shtg_fluctuation_rescale(self._h, nc, _ptr(co), _ptr(cn), _ptr(f), _ptr(out), nb,
+                                                   _stream()))
+        return out
+
+    def joint_log_target(self, cl, bl, ninv, d, a_hat: torch.Tensor, f_hat: torch.Tensor,
+                         precision: str = "df64", cl_scale=None) -> np.ndarray:
+        """log pi(theta) of Eq. (acceptance-rate) per realization: the data
+        term of the mean field a_hat, its prior term and the noise term of the
+        fluctuation f_hat (all CUDA, [nbatch, ncomp, nalm] complex128; d
+        [nbatch, ncomp, npix] float64).  precision: "fp64" or "df64" transforms."""
+        for t, n in ((a_hat, "a_hat"), (f_hat, "f_hat"), (d, "d"), (ninv, "ninv")):
+            _need_cuda(t, n)
+        nb, nc = int(d.shape[0]), int(d.shape[1])
+        pr = self._problem(cl, bl, ninv, d, None, None, nb, nc, cl_scale)
+        lp = np.zeros(nb)
+        prec = {"fp64": N.FP64, "df64": N.DF64}[precision]
+        N.check(self._lib.shtg_joint_log_target(self._h, C.byref(pr), prec, _ptr(a_hat), _ptr(f_hat),
+                                                _ptr(lp), _stream()))
+        return lp
 
     def apply_operator(self, cl, bl, ninv, x: torch.Tensor, cl_scale=None) -> torch.Tensor:
         """y = (S^-1 + B Y^T N^-1 Y B) x for x [nbatch, ncomp, nalm] complex128 (CUDA)."""
@@ -243,23 +284,40 @@ class Plan:
         return y
 
     def logpost_grad(self, cl, bl, alm: torch.Tensor, d: torch.Tensor, ninv: torch.Tensor,
-                     bins=(), components: bool = False, want_grad: bool = True):
+                     bins=(), components: bool = False, want_grad: bool = True, theta=None):
         """Log-posterior of Eq. (joint-posterior) (temperature) with its
-        gradient w.r.t. alm (complex64) and the log C_l of each bin."""
+        gradient w.r.t. alm (complex64) and the log C_l of each bin.  theta:
+        optional per-bin log offsets (C_l -> C_l exp(theta_k) on bin k, applied
+        by the library)."""
         for t, n in ((alm, "alm"), (d, "d"), (ninv, "ninv")):
             _need_cuda(t, n)
         cl_h, bl_h = self._host_f64(cl), self._host_f64(bl)
         lo = np.ascontiguousarray([b[0] for b in bins], dtype=np.int32)
         hi = np.ascontiguousarray([b[1] for b in bins], dtype=np.int32)
+        th = None
+        if theta is not None:
+            th = self._host_f64(theta).reshape(-1)
+            if th.size != len(bins):
+                raise ValueError("theta needs one entry per bin")
         g = torch.empty_like(alm) if want_grad else None
         gcl = np.zeros(len(bins))
         logp = C.c_double(0.0)
-        N.check(self._lib.shtg_logpost_grad(
+        N.check(self._lib.shtg_logpost_grad_binned(
             self._h, _ptr(cl_h), _ptr(bl_h), _ptr(alm), _ptr(d), _ptr(ninv), len(bins),
             _ptr(lo) if len(bins) else None, _ptr(hi) if len(bins) else None,
+            _ptr(th) if th is not None else None,
             N.GRAD_COMPONENTS if components else 0, C.byref(logp),
             _ptr(g) if g is not None else None, _ptr(gcl) if len(bins) else None, _stream()))
         return logp.value, g, gcl
+
+
+def joint_acceptance(log_pi_new: float, log_pi_old: float, log_prior_new: float = 0.0,
+                     log_prior_old: float = 0.0) -> float:
+    """Acceptance probability of the joint move, Eq. (acceptance-rate)."""
+    a = C.c_double(0.0)
+    N.check(N.load().shtg_joint_acceptance(float(log_pi_new), float(log_pi_old), float(log_prior_new),
+                                           float(log_prior_old), C.byref(a)))
+    return a.value
 
 
 def fma_peak(precision: str = "fp32"):

@@ -32,13 +32,9 @@ class GaussianLogPosterior(torch.autograd.Function):
 
     @staticmethod
     def forward(ctx, plan, alm, theta, cl, bl, d, ninv, bins):
-        import numpy as np
-        scale = np.ones(len(cl))
-        th = theta.detach().cpu().numpy()
-        for k, (lo, hi) in enumerate(bins):
-            scale[lo:hi + 1] = np.exp(th[k])
-        logp, g, gcl = plan.logpost_grad(np.asarray(cl) * scale, bl, alm.contiguous(), d, ninv,
-                                         bins, components=True)
+        # the library applies C_l exp(theta_k) per bin and returns dL/dtheta
+        logp, g, gcl = plan.logpost_grad(cl, bl, alm.contiguous(), d, ninv, bins, components=True,
+                                         theta=theta.detach().cpu().double().numpy())
         ctx.save_for_backward(g)
         ctx.gcl = torch.as_tensor(gcl, dtype=theta.dtype, device=theta.device)
         return torch.tensor(logp, dtype=torch.float64, device=alm.device)

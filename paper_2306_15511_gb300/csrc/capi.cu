@@ -1,6 +1,8 @@
 // The exported C ABI (declared in include/shtg.h): argument checks, error
 // reporting, and the composition of the Legendre and ring stages into the
 // transforms Y, Y^T and the quadrature analysis.
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <string>
@@ -386,6 +388,66 @@ int shtg_logpost_grad(shtg_plan *plan, const double *cl, const double *bl, const
     }
     return logpost_grad(reinterpret_cast<Plan *>(plan), cl, bl, alm, d, ninv, nbins, bin_lo,
                         bin_hi, flags, logp, grad_alm, grad_logcl, (cudaStream_t)stream);
+}
+
+int shtg_logpost_grad_binned(shtg_plan *plan, const double *cl, const double *bl, const float *alm,
+                             const float *d, const float *ninv, int nbins, const int *bin_lo,
+                             const int *bin_hi, const double *theta, int flags, double *logp,
+                             float *grad_alm, double *grad_theta, void *stream) {
+    if (!plan || !cl || !bl || !alm || !d || !ninv || nbins < 0 || (nbins > 0 && (!bin_lo || !bin_hi))) {
+        set_error("logpost_grad_binned: null argument or negative nbins");
+        return SHTG_ERR_ARG;
+    }
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    // C_l exp(theta_k) on the multipoles of bin k (Eq. joint-posterior with
+    // binned log C_l parameters)
+    std::vector<double> c(cl, cl + p->lmax + 1);
+    if (theta)
+        for (int k = 0; k < nbins; ++k) {
+            const double f = std::exp(theta[k]);
+            for (int l = std::max(0, bin_lo[k]); l <= std::min(p->lmax, bin_hi[k]); ++l) c[l] *= f;
+        }
+    return logpost_grad(p, c.data(), bl, alm, d, ninv, nbins, bin_lo, bin_hi, flags, logp, grad_alm,
+                        grad_theta, (cudaStream_t)stream);
+}
+
+int shtg_fluctuation_rescale(shtg_plan *plan, int ncomp, const double *cl_old, const double *cl_new,
+                             const double *f, double *f_out, int nbatch, void *stream) {
+    if (!plan) {
+        set_error("null plan");
+        return SHTG_ERR_ARG;
+    }
+    Plan *p = reinterpret_cast<Plan *>(plan);
+    if (nbatch > p->max_batch) {
+        set_error("fluctuation_rescale: nbatch above max_batch");
+        return SHTG_ERR_ARG;
+    }
+    return fluctuation_rescale(p, ncomp, cl_old, cl_new, f, f_out, nbatch, (cudaStream_t)stream);
+}
+
+int shtg_joint_log_target(shtg_plan *plan, const shtg_problem *prob, int precision, const double *a_hat,
+                          const double *f_hat, double *log_pi, void *stream) {
+    if (!plan) {
+        set_error("null plan");
+        return SHTG_ERR_ARG;
+    }
+    return joint_log_target(reinterpret_cast<Plan *>(plan), prob, precision, a_hat, f_hat, log_pi,
+                            (cudaStream_t)stream);
+}
+
+int shtg_joint_acceptance(double log_pi_new, double log_pi_old, double log_prior_new, double log_prior_old,
+                          double *accept) {
+    if (!accept) {
+        set_error("joint_acceptance: null output");
+        return SHTG_ERR_ARG;
+    }
+    const double x = (log_pi_new + log_prior_new) - (log_pi_old + log_prior_old);
+    if (std::isnan(x)) {
+        set_error("joint_acceptance: NaN log ratio");
+        return SHTG_ERR_NONFINITE;
+    }
+    *accept = x >= 0.0 ? 1.0 : std::exp(x);
+    return SHTG_OK;
 }
 
 }  // extern "C"

@@ -67,6 +67,8 @@ __host__ __device__ constexpr int ring_first_bpt(int R, int nt) {
     return nt >= 512 ? (R == 2 ? 8 : 1) : nt == 256 ? 1 : nt == 128 ? (R == 2 ? 1 : 2) : (R == 8 ? 1 : 4);
 }
 
+#define SHTG_FFT_LOGMAX 13   // longest ring transform (Bluestein length included): 8192
+
 // l stride of the FP64 recurrence tile states
 #define SHTG_TS64 32
 
@@ -134,6 +136,11 @@ struct Plan {
     int tw_blo = 0, tw_nlo = 0, tw_nhi = 0;
     double2 *d_chirp64 = nullptr, *d_bfwd64 = nullptr, *d_binv64 = nullptr;
     float2 *d_chirp32 = nullptr, *d_bfwd32 = nullptr, *d_binv32 = nullptr;
+    // fixed-length launches (ringfft.cu): per-pass twiddles of the radix-16
+    // passes for M = 2^logm, at twf_off[logm] (logm = 10 .. 13)
+    double2 *d_twf64 = nullptr;
+    float2 *d_twf32 = nullptr;
+    int64_t twf_off[SHTG_FFT_LOGMAX + 1] = {};
     double2 *d_rph64 = nullptr;   // ring phase tables (RingFFT::ph_off)
     float2 *d_rph32 = nullptr;
     size_t fft_smem64 = 0, fft_smem32 = 0;
@@ -143,6 +150,7 @@ struct Plan {
         int logm;         // log2 of the bucket's buffer length (every member's M, and 2n if aliased)
         int alias;        // bucket holds rings with n < 2 lmax
         int chirp;        // longest Bluestein ring of the bucket (its chirp is staged in shared memory)
+        int fix;          // launches of 128 threads and more: log2 of every member's M (fixed-length passes); 0 = any
     };
     std::vector<RingLaunch> ring_launch;
 
@@ -189,16 +197,20 @@ struct Plan {
     double2 *d_tst64_0 = nullptr;
     double4_32a *d_tst64_2 = nullptr;
     double *d_lsum = nullptr;      // [lmax+1] per-l sums (log-posterior)
+    double *d_jtab = nullptr;      // [13][lmax+1] joint move: old and new spectra [2][4], rescaling rows [5]
     double *d_stage = nullptr;     // [nmaps_max][npix] staging for host inputs
     double *h_pinned = nullptr;    // pinned host scalars
 };
 
 // solver.cu
 #define SHTG_RED_BLOCKS 128
-#define SHTG_FFT_LOGMAX 13   // longest ring transform (Bluestein length included): 8192
 int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_opts *o,
               shtg_cg_stats *stats, cudaStream_t st);
 int apply_operator(Plan *p, const shtg_problem *pr, const double *x, double *y, cudaStream_t st);
+int fluctuation_rescale(Plan *p, int nc, const double *cl_old, const double *cl_new, const double *f,
+                        double *g, int nbatch, cudaStream_t st);
+int joint_log_target(Plan *p, const shtg_problem *pr, int precision, const double *a_hat,
+                     const double *f_hat, double *logpi, cudaStream_t st);
 int logpost_grad(Plan *p, const double *cl, const double *bl, const float *alm, const float *d,
                  const float *ninv, int nbins, const int *blo, const int *bhi, int flags,
                  double *logp, float *grad, double *gcl, cudaStream_t st);

@@ -519,6 +519,25 @@ static int build_fft_tables(Plan *p) {
         tw64[i] = make_double2(cos(ang), sin(ang));
         tw32[i] = make_float2((float)cos(ang), (float)sin(ang));
     }
+    // per-pass twiddles of the fixed-length FFT passes (ringfft.cu) for
+    // M = 2^10 .. 2^13: radix-16 pass p with NS = 2^(logm mod 4) 16^p > 1 holds
+    // e^{-2 pi i r k / (16 NS)} for r = 1 at k and r = 4 at NS + k, k < NS
+    std::vector<double2> twf64;
+    std::vector<float2> twf32;
+    for (int lg = 10; lg <= SHTG_FFT_LOGMAX; ++lg) {
+        p->twf_off[lg] = (int64_t)twf64.size();
+        for (int ps = 0; ps < (lg >> 2); ++ps) {
+            const int ns = (1 << (lg & 3)) << (4 * ps);
+            if (ns == 1) continue;
+            for (int r : {1, 4})
+                for (int k = 0; k < ns; ++k) {
+                    const int64_t t = ((int64_t)r * k) % (16 * (int64_t)ns);
+                    const double ang = -2.0 * PI * (double)t / (16.0 * ns);
+                    twf64.push_back(make_double2(cos(ang), sin(ang)));
+                    twf32.push_back(make_float2((float)cos(ang), (float)sin(ang)));
+                }
+        }
+    }
     std::vector<double2> ch64(chirp_total), bf64(bhat_total), bi64(bhat_total);
     std::vector<float2> ch32(chirp_total), bf32(bhat_total), bi32(bhat_total);
     for (auto &kv : offs) {
@@ -586,6 +605,10 @@ static int build_fft_tables(Plan *p) {
     SHTG_TRY(upload(p->d_rph32, ph32));
     SHTG_TRY(dalloc(p, &p->d_rfft, R));
     SHTG_TRY(upload(p->d_rfft, p->h_rfft));
+    SHTG_TRY(dalloc(p, &p->d_twf64, twf64.size()));
+    SHTG_TRY(dalloc(p, &p->d_twf32, twf32.size()));
+    SHTG_TRY(upload(p->d_twf64, twf64));
+    SHTG_TRY(upload(p->d_twf32, twf32));
     SHTG_TRY(dalloc(p, &p->d_tw64, tw64.size()));
     SHTG_TRY(dalloc(p, &p->d_tw32, tw32.size()));
     SHTG_TRY(upload(p->d_tw64, tw64));
@@ -608,17 +631,20 @@ static int build_fft_tables(Plan *p) {
     // (one radix-16 butterfly per thread): Bluestein rings by their M, direct
     // rings without aliasing (n >= 2 lmax) by n, aliased direct rings by 2n so
     // that the south ring's folded spectrum fits in buf[n, 2n); buckets of
-    // length 1024 and below share one launch.
+    // length 1024 and below share one launch.  Buckets above 1024 are split
+    // by the members' own M (the aliased direct rings of a bucket have half
+    // its length), so each of their launches runs one fixed transform length.
     std::vector<int> groups;
     {
-        std::map<int, std::vector<int>, std::greater<int>> bucket;   // key -> ring pairs
+        // (key, fix) -> ring pairs; key = launch length, fix = members' log2 M (0: mixed)
+        std::map<std::pair<int, int>, std::vector<int>, std::greater<std::pair<int, int>>> bucket;
         std::map<int, int> keymax;
         for (int r = 0; r < p->npairs; ++r) {
             const RingFFT &f = p->h_rfft[r];
             const bool aliased = f.n < 2 * p->lmax;
             const int slot = (f.blue || !aliased) ? f.logM : f.logM + 1;
             const int key = std::max(slot, 10);
-            bucket[key].push_back(r);
+            bucket[std::make_pair(key, key > 10 ? f.logM : 0)].push_back(r);
             keymax[key] = std::max(keymax.count(key) ? keymax[key] : 0, slot);
         }
         p->ring_launch.clear();
@@ -626,10 +652,11 @@ static int build_fft_tables(Plan *p) {
             Plan::RingLaunch g;
             g.off = (int)groups.size();
             g.count = (int)kv.second.size();
-            g.logm = keymax[kv.first];
+            g.logm = keymax[kv.first.first];
+            g.fix = kv.first.second;
             g.alias = 0;
             g.chirp = 0;
-            const int nt = ring_threads(g.logm);
+            const int nt = g.fix ? (1 << g.fix) / 16 : ring_threads(g.logm);
             for (int r : kv.second) {
                 const RingFFT &f = p->h_rfft[r];
                 groups.push_back(r);
@@ -638,7 +665,11 @@ static int build_fft_tables(Plan *p) {
                 // the kernel's passes cover this ring: M / 16 butterflies per
                 // radix-16 pass, M / R in the first pass
                 const int M = 1 << f.logM, R = 1 << (f.logM & 3);
-                const bool ok = M <= 16 * nt && (R == 1 || M / R <= nt * ring_first_bpt(R, nt)) &&
+                // launches of buckets above 1024 run the fixed-length passes
+                // of their members' one length, 2^logm or 2^(logm - 1)
+                const bool fix_ok = g.fix == 0 ? g.logm <= 10
+                                               : (g.fix == f.logM && (f.logM == g.logm || f.logM == g.logm - 1));
+                const bool ok = fix_ok && M <= 16 * nt && (R == 1 || M / R <= nt * ring_first_bpt(R, nt)) &&
                                 (f.n >= 2 * p->lmax || 2 * (int64_t)f.n <= ((int64_t)1 << g.logm));
                 if (!ok) {
                     set_error("ring " + std::to_string(r) + ": transform length " + std::to_string(M) +
@@ -695,6 +726,7 @@ int plan_build(Plan *p) {
     SHTG_TRY(dalloc(p, &p->d_wpairT, p->npairs));
     SHTG_TRY(dalloc(p, &p->d_wpairP, p->npairs));
     SHTG_TRY(dalloc(p, &p->d_ltab64, 9 * (int64_t)(p->lmax + 1)));
+    SHTG_TRY(dalloc(p, &p->d_jtab, 13 * (int64_t)(p->lmax + 1)));
     SHTG_TRY(dalloc(p, &p->d_ltab32, 5 * (int64_t)(p->lmax + 1)));
     SHTG_TRY(dalloc(p, &p->d_scal, 16 * (int64_t)p->max_batch));
     SHTG_TRY(dalloc(p, &p->d_part, 4 * (int64_t)p->max_batch * SHTG_RED_BLOCKS + 4 * (int64_t)p->max_batch + 64));
@@ -728,7 +760,8 @@ void plan_free(Plan *p) {
                     p->d_ltab64, p->d_ltab32, p->d_scal, p->d_part, p->d_lsum, p->d_stage,
                     p->d_ls2_64, p->d_st2_64, p->d_ls2_32, p->d_st2_32, p->d_ring_groups, p->d_flag,
                     p->d_toff, p->d_tst0, p->d_tst2, p->d_isc64, p->d_rsc64, p->d_isc32,
-                    p->d_toff64, p->d_tst64_0, p->d_tst64_2, p->d_rph64, p->d_rph32};
+                    p->d_toff64, p->d_tst64_0, p->d_tst64_2, p->d_rph64, p->d_rph32, p->d_twf64,
+                    p->d_twf32, p->d_jtab};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (int i = 0; i < 7; ++i)

@@ -24,10 +24,11 @@ namespace shtg {
 // Threads per CTA: M / 16 for the launch's longest transform M (every
 // radix-16 pass then has one butterfly per thread), at least 64; resident
 // CTAs per SM for a budget of 128 registers a thread in FP32 (the inlined
-// passes do not spill), 255 in FP64 up to 256 threads (the FP64 passes
-// spill at 128).
-template <typename T, int NT> struct RingBlocks {
-    static constexpr int v = sizeof(T) == 8 ? (NT >= 256 ? 1 : 256 / NT) : 512 / NT;
+// passes do not spill; the fixed-length launches, M = 16 NT: 64 registers,
+// so twice as many threads share an SM), 255 in FP64 up to 256 threads (the
+// FP64 passes spill at 128).
+template <typename T, int NT, int FIX> struct RingBlocks {
+    static constexpr int v = sizeof(T) == 8 ? (NT >= 256 ? 1 : 256 / NT) : (FIX > 0 ? 1024 : 512) / NT;
 };
 
 __device__ __forceinline__ int rpad(int i) { return i + (i >> 4); }
@@ -250,6 +251,170 @@ __device__ __forceinline__ void fft_stockham(C *buf, const int logM, const TwTab
     }
 }
 
+// ---------------------------------------------------------------------------
+// Fixed-length Stockham FFT (M = 2^LOGM known at compile time), used by the
+// launches of the long rings.  Same passes as fft_stockham (one radix-2, -4 or
+// -8 pass when log2 M is not a multiple of four, then radix-16 passes), but
+// every shared-memory address of a pass is a per-thread base plus a
+// compile-time offset, and the twiddles of each radix-16 pass come from a
+// precomputed table (twf_*): entries k and NS + k of pass p hold w^1 and w^4
+// for w = e^{-2 pi i k / (16 NS)}, k < NS = 2^(LOGM mod 4) 16^p (passes with
+// NS = 1 need none), rounded once from FP64; the other powers are products
+// of those.  A warp's 32 consecutive k read 32 consecutive entries.
+//
+// Padded addresses: rpad(i) = i + i / 16.  For a pass with NB = M / R
+// butterflies (NB a multiple of 16), butterfly j reads j + r NB, whose padded
+// address is rpad(j) + r (NB + NB / 16).  Radix-16 outputs go to
+// o = d + r NS with d = 16 (j - k) + k: for NS >= 16, rpad(o) = d + (j - k) +
+// k / 16 + r (NS + NS / 16); for NS = 1, 2, 4, 8 (NS divides 16, k < NS),
+// rpad(o) = d + (j - k) + r NS + (r NS) / 16.  The first pass (NS = 1)
+// writes o = R j + r at rpad(R j) + r.
+__host__ __device__ constexpr int twf_pass_ns(int logm, int p) { return (1 << (logm & 3)) << (4 * p); }
+__host__ __device__ constexpr int twf_pass_off(int logm, int p) {
+    int o = 0;
+    for (int q = 0; q < p; ++q)
+        if (twf_pass_ns(logm, q) > 1) o += 2 * twf_pass_ns(logm, q);
+    return o;
+}
+
+// Radix-16 DFT in place with its outputs left transposed: X[s] ends at
+// v[4 (s mod 4) + s / 4] (the same 4 x 4 decomposition as Dft<16>: DFT-4 down
+// the columns r2, twiddles w16^(r2 s1), DFT-4 along the rows s1), so no second
+// array of 16 values is live; callers read the outputs through the
+// compile-time permutation dft16_at.
+__host__ __device__ constexpr int dft16_at(int s) { return 4 * (s & 3) + (s >> 2); }
+template <typename C>
+__device__ __forceinline__ void dft16_tp(C *v) {
+#pragma unroll
+    for (int r2 = 0; r2 < 4; ++r2) {
+        dft4<false>(v[r2], v[r2 + 4], v[r2 + 8], v[r2 + 12]);
+        v[r2 + 4] = rot16<false>(v[r2 + 4], r2);
+        v[r2 + 8] = rot16<false>(v[r2 + 8], 2 * r2);
+        v[r2 + 12] = rot16<false>(v[r2 + 12], 3 * r2);
+    }
+#pragma unroll
+    for (int s1 = 0; s1 < 4; ++s1) dft4<false>(v[4 * s1], v[4 * s1 + 1], v[4 * s1 + 2], v[4 * s1 + 3]);
+}
+
+template <int R, int LOGM, int NT, typename C>
+__device__ __forceinline__ void fpass_first(C *buf) {
+    constexpr int M = 1 << LOGM, NB = M / R, BPT = (NB + NT - 1) / NT;
+    constexpr int SIN = NB + NB / 16;
+    static_assert(NB % 16 == 0, "first pass needs M / R to be a multiple of 16");
+    C v[BPT][R];
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int j = threadIdx.x + b * NT;
+        if (NB % NT == 0 || j < NB) {
+            const int bi = j + (j >> 4);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[b][r] = buf[bi + r * SIN];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int j = threadIdx.x + b * NT;
+        if (NB % NT == 0 || j < NB) {
+            Dft<R, false, C>::run(v[b]);
+            const int o0 = j * R;
+            const int bo = o0 + (o0 >> 4);
+#pragma unroll
+            for (int r = 0; r < R; ++r) buf[bo + r] = v[b][r];
+        }
+    }
+    __syncthreads();
+}
+
+template <int LOGM, int NS, int NT, typename C>
+__device__ __forceinline__ void fpass16(C *buf, const C *__restrict__ twp) {
+    constexpr int M = 1 << LOGM, NB = M / 16, BPT = (NB + NT - 1) / NT;
+    constexpr int SIN = NB + NB / 16;
+    static_assert(NB % 16 == 0, "radix-16 pass needs M / 16 to be a multiple of 16");
+    C v[BPT][16];
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int j = threadIdx.x + b * NT;
+        if (NB % NT == 0 || j < NB) {
+            const int bi = j + (j >> 4);
+#pragma unroll
+            for (int r = 0; r < 16; ++r) v[b][r] = buf[bi + r * SIN];
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int b = 0; b < BPT; ++b) {
+        const int j = threadIdx.x + b * NT;
+        if (NB % NT == 0 || j < NB) {
+            const int k = j & (NS - 1);
+            if (NS > 1) {
+                // w^r for r = 4a + c from the two table values w and w^4:
+                // w^2, w^3 = w^2 w; w^8 = (w^4)^2, w^12 = w^8 w^4; w^(4a + c) =
+                // w^(4a) w^c: at most five roundings, ten live registers
+                const C w1 = __ldg(twp + k), w4 = __ldg(twp + NS + k);
+                const C w2 = cmul(w1, w1), w3 = cmul(w2, w1);
+                v[b][1] = cmul(v[b][1], w1);
+                v[b][2] = cmul(v[b][2], w2);
+                v[b][3] = cmul(v[b][3], w3);
+                C wa = w4;
+#pragma unroll
+                for (int a = 1; a < 4; ++a) {
+                    if (a > 1) wa = cmul(wa, w4);
+                    v[b][4 * a] = cmul(v[b][4 * a], wa);
+                    v[b][4 * a + 1] = cmul(v[b][4 * a + 1], cmul(wa, w1));
+                    v[b][4 * a + 2] = cmul(v[b][4 * a + 2], cmul(wa, w2));
+                    v[b][4 * a + 3] = cmul(v[b][4 * a + 3], cmul(wa, w3));
+                }
+            }
+            dft16_tp(v[b]);
+            const int d = 16 * (j - k) + k;
+            const int bo = NS >= 16 ? d + (j - k) + (k >> 4) : d + (j - k);
+#pragma unroll
+            for (int r = 0; r < 16; ++r) {
+                const int off = NS >= 16 ? r * (NS + NS / 16) : r * NS + (r * NS) / 16;
+                buf[bo + off] = v[b][dft16_at(r)];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <int LOGM, int NT, int P, typename C>
+__device__ __forceinline__ void fft16_passes(C *buf, const C *__restrict__ tw) {
+    if constexpr (P < (LOGM >> 2)) {
+        fpass16<LOGM, twf_pass_ns(LOGM, P), NT>(buf, tw + twf_pass_off(LOGM, P));
+        fft16_passes<LOGM, NT, P + 1>(buf, tw);
+    }
+}
+
+// Length-2^LOGM forward DFT of buf in place (natural order in and out).
+template <int LOGM, int NT, typename C>
+__device__ __forceinline__ void fft_fixed(C *buf, const C *__restrict__ tw) {
+    static_assert(LOGM >= 8, "fixed-length passes need M >= 256");
+    constexpr int R0L = LOGM & 3;
+    if constexpr (R0L != 0) fpass_first<(1 << R0L), LOGM, NT>(buf);
+    fft16_passes<LOGM, NT, 0>(buf, tw);
+}
+
+// One transform direction with the fixed-length FFT (see transform_dir)
+// (the Bluestein spectrum multiply is a separate sweep over the buffer with
+// coalesced loads of the spectrum, so no pass keeps sixteen of them in flight)
+template <int LOGM, int NT, typename C>
+__device__ __forceinline__ void transform_dir_fixed(C *buf, const C *__restrict__ tw, const C *__restrict__ bh) {
+    constexpr int M = 1 << LOGM;
+    if (bh) {
+        fft_fixed<LOGM, NT>(buf, tw);
+#pragma unroll 4
+        for (int i = threadIdx.x; i < M; i += NT) {
+            C y = cmul(buf[rpad(i)], __ldg(bh + i));
+            y.y = -y.y;
+            buf[rpad(i)] = y;
+        }
+        __syncthreads();
+    }
+    fft_fixed<LOGM, NT>(buf, tw);
+}
+
 template <typename T> struct RingArgs {
     typedef typename VT<T>::C C;
     int lmax, nring, npairs, nmaps;
@@ -261,6 +426,7 @@ template <typename T> struct RingArgs {
     int tw_blo, tw_nlo, tw_nhi, logmax;
     const C *chirp, *bfwd, *binv;
     const C *rph;     // ring phase tables e^{i pi k / n}
+    const C *twf;     // fixed-length launches: pass twiddles for M = 2^FIX
     C *FG;            // [map][ring][m]
     T *map;           // [map][npix]
     const T *ninv;    // fused: [comp][npix]
@@ -286,15 +452,19 @@ __device__ __forceinline__ void transform_dir(C *buf, const int logM, const TwTa
 // Bluestein rings, a convolution = DFT, times the kernel spectrum and
 // conjugated in the last pass, DFT again: buf then holds the conjugate of the
 // convolution.  The directions run in a loop, so the FFT is inlined once.
-template <typename T, int MODE, int NT>
-__global__ void __launch_bounds__(NT, RingBlocks<T, NT>::v) k_ring(const RingArgs<T> a) {
+template <typename T, int MODE, int NT, int FIX>
+__global__ void __launch_bounds__(NT, (RingBlocks<T, NT, FIX>::v)) k_ring(const RingArgs<T> a) {
     typedef typename VT<T>::C C;
     extern __shared__ __align__(16) unsigned char s_raw[];
+    // FIX > 0: every ring of the launch has M = 2^FIX and the fixed-length
+    // passes run (twiddles from twf, no shared twiddle table)
+    constexpr bool fixed = FIX > 0;
+    const int ntw = fixed ? 0 : a.tw_nlo + a.tw_nhi;
     C *s_tw = reinterpret_cast<C *>(s_raw);
-    C *buf = s_tw + a.tw_nlo + a.tw_nhi;
+    C *buf = s_tw + ntw;
     C *s_chirp = buf + a.buf_len;          // this ring's chirp (Bluestein rings)
     C *scr_p = s_chirp + a.chirp_len;      // aliased fold: partial sums [north | south][NT]
-    for (int i = threadIdx.x; i < a.tw_nlo + a.tw_nhi; i += NT) s_tw[i] = a.tw[i];
+    for (int i = threadIdx.x; i < ntw; i += NT) s_tw[i] = a.tw[i];
     TwTab<C> tw;
     tw.lo = s_tw;
     tw.hi = s_tw + a.tw_nlo;
@@ -461,11 +631,17 @@ __global__ void __launch_bounds__(NT, RingBlocks<T, NT>::v) k_ring(const RingArg
         if (f.blue)
             for (int k = n + threadIdx.x; k < M; k += NT) buf[rpad(k)] = zero;
         __syncthreads();
+#pragma unroll 1
         for (int dir = 0; dir < NDIR; ++dir) {
             // inverse (e^{+2 pi i jk/n}) for MODE 0 and the first direction of
             // MODE 2, forward (e^{-2 pi i jk/n}) otherwise
             const bool fwd = MODE == 1 || dir == 1;
-            transform_dir<NT>(buf, logM, tw, f.blue ? (fwd ? a.bfwd : a.binv) + f.bhat_off : nullptr);
+            const C *bh = f.blue ? (fwd ? a.bfwd : a.binv) + f.bhat_off : nullptr;
+            if constexpr (fixed) {
+                transform_dir_fixed<(fixed ? FIX : 8), NT>(buf, a.twf, bh);
+            } else {
+                transform_dir<NT>(buf, logM, tw, bh);
+            }
             if (MODE == 2 && dir == 0) {
                 // ---- N^-1 weighting (each thread rewrites the elements it reads)
                 const int comp = q < a.nT ? 0 : 1;
@@ -575,6 +751,10 @@ __global__ void __launch_bounds__(NT, RingBlocks<T, NT>::v) k_ring(const RingArg
     }
 }
 
+template <typename T> static const typename VT<T>::C *ring_twf(Plan *p);
+template <> const float2 *ring_twf<float>(Plan *p) { return p->d_twf32; }
+template <> const double2 *ring_twf<double>(Plan *p) { return p->d_twf64; }
+
 template <typename T> static RingArgs<T> ring_args(Plan *p);
 template <> RingArgs<float> ring_args<float>(Plan *p) {
     RingArgs<float> a{};
@@ -595,9 +775,9 @@ template <> RingArgs<double> ring_args<double>(Plan *p) {
     return a;
 }
 
-template <typename T, int MODE, int NT>
+template <typename T, int MODE, int NT, int FIX>
 static int launch_ring_nt(const RingArgs<T> &a, int ctas, size_t smem, cudaStream_t st) {
-    auto kern = k_ring<T, MODE, NT>;
+    auto kern = k_ring<T, MODE, NT, FIX>;
     if (smem > 48 * 1024) SHTG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     kern<<<ctas, NT, smem, st>>>(a);
     return SHTG_OK;
@@ -636,18 +816,25 @@ static int launch_ring(Plan *p, RingArgs<T> a, cudaStream_t st) {
             SHTG_CUDA(cudaStreamWaitEvent(ls, p->ring_fork, 0));
         }
         const int M = 1 << g.logm;
-        const int nt = ring_threads(g.logm);
+        // launches of buckets above 1024 hold rings of one transform length
+        // M = 2^g.fix (2^logm, or 2^(logm - 1) for aliased direct rings, whose
+        // buffer still holds 2^logm: checked at plan creation) and run the
+        // fixed-length passes with M / 16 threads
+        const bool fix = g.fix > 0;
+        const int nt = fix ? (1 << g.fix) / 16 : ring_threads(g.logm);
         a.buf_len = M + M / 16;
         a.chirp_len = g.chirp;
-        const size_t smem =
-            sizeof(C) * ((size_t)p->tw_nlo + p->tw_nhi + a.buf_len + a.chirp_len + (g.alias ? 2 * nt : 0));
+        a.twf = fix ? ring_twf<T>(p) + p->twf_off[g.fix] : nullptr;
+        const size_t smem = sizeof(C) * ((fix ? 0 : (size_t)p->tw_nlo + p->tw_nhi) + a.buf_len + a.chirp_len +
+                                         (g.alias ? 2 * nt : 0));
         a.pairs = p->d_ring_groups + g.off;
         int rc = SHTG_OK;
-        switch (nt) {
-            case 64: rc = launch_ring_nt<T, MODE, 64>(a, g.count, smem, ls); break;
-            case 128: rc = launch_ring_nt<T, MODE, 128>(a, g.count, smem, ls); break;
-            case 256: rc = launch_ring_nt<T, MODE, 256>(a, g.count, smem, ls); break;
-            default: rc = launch_ring_nt<T, MODE, 512>(a, g.count, smem, ls); break;
+        switch (g.fix) {
+            case 10: rc = launch_ring_nt<T, MODE, 64, 10>(a, g.count, smem, ls); break;
+            case 11: rc = launch_ring_nt<T, MODE, 128, 11>(a, g.count, smem, ls); break;
+            case 12: rc = launch_ring_nt<T, MODE, 256, 12>(a, g.count, smem, ls); break;
+            case 13: rc = launch_ring_nt<T, MODE, 512, 13>(a, g.count, smem, ls); break;
+            default: rc = launch_ring_nt<T, MODE, 64, 0>(a, g.count, smem, ls); break;
         }
         if (rc != SHTG_OK) return rc;
         if (ls != st) {

@@ -65,14 +65,17 @@ __device__ double block_sum(double v, double *sm) {
 }
 
 // --------------------------------------------------------------- pixel side
-// out rows [T_0 .. T_{nb-1}, Q_0, U_0, Q_1, U_1, ...] (the transform's row order)
-// from inputs in [b][c][npix] order: out (=|+=) N^-1 d (+ sqrt(N^-1) w2).
+// out rows [T_0 .. T_{nt-1}, Q_0, U_0, Q_1, U_1, ...] (the transform's row
+// order for nt realizations) from inputs in [b][c][npix] order: realization
+// b of the inputs goes to realization boff + b of the output;
+// out (=|+=) N^-1 d (+ sqrt(N^-1) w2).
 __global__ void k_rhs_pix(const double *__restrict__ d, const double *__restrict__ w2,
-                          const double *__restrict__ ninv, int nb, int nc, int64_t npix,
+                          const double *__restrict__ ninv, int nt, int boff, int nc, int64_t npix,
                           int accumulate, double *__restrict__ out) {
     const int row = blockIdx.y;
     const int b = row / nc, c = row % nc;
-    const int orow = (c == 0) ? b : nb + 2 * b + (c - 1);
+    const int ob = boff + b;
+    const int orow = (c == 0) ? ob : nt + 2 * ob + (c - 1);
     const double *wv = ninv + (c == 0 ? 0 : npix);
     double *o = out + (int64_t)orow * npix;
     for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix;
@@ -530,6 +533,137 @@ __global__ void k_grad_prior(const float2 *__restrict__ a, float2 *__restrict__ 
     }
 }
 
+// ------------------------------------------------------------- joint move
+// Joint (C_l, a) move of Sect. 2.2.2.
+//
+// Rescaling matrix of the fluctuation term per l: R_l = (C'_l)^{1/2}
+// (C_l)^{-1/2} with the symmetric principal square roots of the T/E block
+// (closed form for 2 x 2: sqrt(M) = (M + sqrt(det) I) / sqrt(tr + 2 sqrt(det)),
+// whose determinant is sqrt(det), so its inverse is adj(M + sqrt(det) I) /
+// (sqrt(tr + 2 sqrt(det)) sqrt(det))) and the scalar B part; R_l = 0 where
+// either block is singular (those multipoles are held at zero).  cl rows:
+// [TT, EE, BB, TE] x L1 for old then new (nc = 1: TT rows only).
+// out rows: R_TT, R_TE, R_ET, R_EE, R_BB.
+__global__ void k_rescale_table(const double *__restrict__ cold, const double *__restrict__ cnew, int nc,
+                                int L1, double *__restrict__ out) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= L1) return;
+    double r[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    if (nc == 1) {
+        const double a = cold[l], b = cnew[l];
+        if (a > 0.0 && b > 0.0) r[0] = sqrt(b / a);
+    } else {
+        const double at = cold[l], ae = cold[L1 + l], ab = cold[2 * L1 + l], ax = cold[3 * L1 + l];
+        const double bt = cnew[l], be = cnew[L1 + l], bb = cnew[2 * L1 + l], bx = cnew[3 * L1 + l];
+        const double dold = at * ae - ax * ax, dnew = bt * be - bx * bx;
+        if (at > 0.0 && dold > 0.0 && ab > 0.0 && bt > 0.0 && dnew > 0.0 && bb > 0.0) {
+            const double so = sqrt(dold), to = sqrt(at + ae + 2.0 * so);
+            const double sn = sqrt(dnew), tn = sqrt(bt + be + 2.0 * sn);
+            // (C')^{1/2} = [[bt + sn, bx], [bx, be + sn]] / tn
+            const double p11 = (bt + sn) / tn, p12 = bx / tn, p22 = (be + sn) / tn;
+            // C^{-1/2} = [[ae + so, -ax], [-ax, at + so]] / (to so)
+            const double q = 1.0 / (to * so);
+            const double q11 = (ae + so) * q, q12 = -ax * q, q22 = (at + so) * q;
+            r[0] = p11 * q11 + p12 * q12;
+            r[1] = p11 * q12 + p12 * q22;
+            r[2] = p12 * q11 + p22 * q12;
+            r[3] = p12 * q12 + p22 * q22;
+            r[4] = sqrt(bb / ab);
+        }
+    }
+    for (int k = 0; k < 5; ++k) out[k * L1 + l] = r[k];
+}
+
+// g = R_l f per alm index (T, E, B of one realization; imaginary part of
+// m = 0 written as 0)
+__global__ void k_rescale(const double2 *__restrict__ f, double2 *__restrict__ g, int nc, int64_t nalm,
+                          const int *__restrict__ lof, const int *__restrict__ mof,
+                          const double *__restrict__ R, int L1) {
+    const int64_t off = (int64_t)blockIdx.y * nc * nalm;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nalm;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int l = lof[i];
+        const bool m0 = mof[i] == 0;
+        if (nc == 1) {
+            double2 v = f[off + i];
+            v.x *= R[l];
+            v.y = m0 ? 0.0 : v.y * R[l];
+            g[off + i] = v;
+        } else {
+            const double2 t = f[off + i], e = f[off + nalm + i], b = f[off + 2 * nalm + i];
+            const double r11 = R[l], r12 = R[L1 + l], r21 = R[2 * L1 + l], r22 = R[3 * L1 + l];
+            const double rb = R[4 * L1 + l];
+            double2 vt = {r11 * t.x + r12 * e.x, r11 * t.y + r12 * e.y};
+            double2 ve = {r21 * t.x + r22 * e.x, r21 * t.y + r22 * e.y};
+            double2 vb = {rb * b.x, rb * b.y};
+            if (m0) vt.y = ve.y = vb.y = 0.0;
+            g[off + i] = vt;
+            g[off + nalm + i] = ve;
+            g[off + 2 * nalm + i] = vb;
+        }
+    }
+}
+
+// Pixel sums of the log target per realization (grid RB x nb): mode 0:
+// sum_c sum_p N^-1_c,p (d - m)^2; mode 1: sum_c sum_p N^-1_c,p m^2.  d is in
+// [b][c][npix] order, m in the transform's row order (T rows, then Q, U
+// pairs), N^-1 [T, P] with Q and U sharing P.
+__global__ void k_joint_pix(const double *__restrict__ d, const double *__restrict__ m,
+                            const double *__restrict__ ninv, int nb, int nc, int64_t npix, int mode,
+                            double *__restrict__ part) {
+    __shared__ double sm[RT / 32];
+    const int b = blockIdx.y;
+    double acc = 0.0;
+    for (int c = 0; c < nc; ++c) {
+        const int row = (c == 0) ? b : nb + 2 * b + (c - 1);
+        const double *mv = m + (int64_t)row * npix;
+        const double *dv = d ? d + ((int64_t)b * nc + c) * npix : nullptr;
+        const double *wv = ninv + (c == 0 ? 0 : npix);
+        for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npix;
+             p += (int64_t)gridDim.x * blockDim.x) {
+            const double v = mode == 0 ? dv[p] - mv[p] : mv[p];
+            acc += wv[p] * v * v;
+        }
+    }
+    acc = block_sum(acc, sm);
+    if (threadIdx.x == 0) part[b * RB + blockIdx.x] = acc;
+}
+
+// Prior term per realization (grid RB x nb): sum over active multipoles of
+// w_m Re(conj(a) S^-1 a) (w_0 = 1, w_m = 2), S^-1 the per-l block scaled by
+// the realization's 1 / (C_l scale); sinv rows TT, TE, EE, BB; a multipole
+// is active where the inverse square root's TT entry sh is positive.
+__global__ void k_prior_quad(const double2 *__restrict__ a, int nc, int64_t nalm, int L1,
+                             const int *__restrict__ lof, const int *__restrict__ mof,
+                             const double *__restrict__ sinv, const double *__restrict__ sh,
+                             const double *__restrict__ isc, double *__restrict__ part) {
+    __shared__ double sm[RT / 32];
+    const int b = blockIdx.y;
+    const double2 *ab = a + (int64_t)b * nc * nalm;
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nalm;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int l = lof[i];
+        if (!(sh[l] > 0.0)) continue;
+        const bool m0 = mof[i] == 0;
+        const double w = m0 ? 1.0 : 2.0;
+        double2 t = ab[i];
+        if (m0) t.y = 0.0;
+        double q;
+        if (nc == 1) {
+            q = sinv[l] * (t.x * t.x + t.y * t.y);
+        } else {
+            double2 e = ab[nalm + i], bb = ab[2 * nalm + i];
+            if (m0) e.y = bb.y = 0.0;
+            q = sinv[l] * (t.x * t.x + t.y * t.y) + 2.0 * sinv[L1 + l] * (t.x * e.x + t.y * e.y) +
+                sinv[2 * L1 + l] * (e.x * e.x + e.y * e.y) + sinv[3 * L1 + l] * (bb.x * bb.x + bb.y * bb.y);
+        }
+        acc += w * q;
+    }
+    acc = block_sum(acc, sm) * isc[b];
+    if (threadIdx.x == 0) part[b * RB + blockIdx.x] = acc;
+}
+
 // ====================================================================== host
 // One PCG iteration (operator application + vector updates) captured as a
 // CUDA graph and replayed between the host's convergence checks: the
@@ -784,9 +918,11 @@ static double now_ms() {
         .count();
 }
 
-// Per-l tables from host C_l and b_l.  Returns SHTG_ERR_NOT_SPD for an
+// Per-l tables from host C_l and b_l, copied on the solve's stream (the
+// kernels that read them run there; a copy on the legacy default stream is
+// not ordered with a non-blocking stream).  Returns SHTG_ERR_NOT_SPD for an
 // indefinite block.
-static int build_ltab(Plan *p, int nc, const double *cl, const double *bl) {
+static int build_ltab(Plan *p, int nc, const double *cl, const double *bl, cudaStream_t st) {
     const int L1 = p->lmax + 1;
     std::vector<double> t64(9 * (size_t)L1, 0.0);
     std::vector<float> t32(5 * (size_t)L1, 0.f);
@@ -841,29 +977,34 @@ static int build_ltab(Plan *p, int nc, const double *cl, const double *bl) {
         }
         t32[l] = (float)beam;
     }
-    SHTG_CUDA(cudaMemcpy(p->d_ltab64, t64.data(), sizeof(double) * t64.size(), cudaMemcpyHostToDevice));
-    SHTG_CUDA(cudaMemcpy(p->d_ltab32, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice));
+    SHTG_CUDA(cudaMemcpyAsync(p->d_ltab64, t64.data(), sizeof(double) * t64.size(), cudaMemcpyHostToDevice, st));
+    SHTG_CUDA(cudaMemcpyAsync(p->d_ltab32, t32.data(), sizeof(float) * t32.size(), cudaMemcpyHostToDevice, st));
+    SHTG_CUDA(cudaStreamSynchronize(st));   // the host tables go out of scope
     return SHTG_OK;
 }
 
 // Copy N^-1 into the plan (FP64 + FP32 copies), build the preconditioner.
+// nsys systems: system k belongs to realization k mod prob->nbatch (the
+// split right-hand sides of a realization share its C_l scale).
 static int setup_operator(Plan *p, const shtg_problem *pr, int host_inputs, int precond,
-                          cudaStream_t st) {
+                          cudaStream_t st, int nsys = 0) {
     const int nc = pr->ncomp;
-    SHTG_TRY(build_ltab(p, nc, pr->cl, pr->bl));
+    if (nsys <= 0) nsys = pr->nbatch;
+    SHTG_TRY(build_ltab(p, nc, pr->cl, pr->bl, st));
     {
         // realization b's C_l is cl_scale[b] x cl: S^-1 scales by 1/s, S^-1/2 by 1/sqrt(s)
-        std::vector<double> i64(pr->nbatch), r64(pr->nbatch);
-        std::vector<float> i32(pr->nbatch);
-        for (int b = 0; b < pr->nbatch; ++b) {
+        std::vector<double> i64(nsys), r64(nsys);
+        std::vector<float> i32(nsys);
+        for (int k = 0; k < nsys; ++k) {
+            const int b = k % pr->nbatch;
             const double sc = pr->cl_scale ? pr->cl_scale[b] : 1.0;
-            i64[b] = 1.0 / sc;
-            r64[b] = 1.0 / sqrt(sc);
-            i32[b] = (float)i64[b];
+            i64[k] = 1.0 / sc;
+            r64[k] = 1.0 / sqrt(sc);
+            i32[k] = (float)i64[k];
         }
-        SHTG_CUDA(cudaMemcpyAsync(p->d_isc64, i64.data(), sizeof(double) * pr->nbatch, cudaMemcpyHostToDevice, st));
-        SHTG_CUDA(cudaMemcpyAsync(p->d_rsc64, r64.data(), sizeof(double) * pr->nbatch, cudaMemcpyHostToDevice, st));
-        SHTG_CUDA(cudaMemcpyAsync(p->d_isc32, i32.data(), sizeof(float) * pr->nbatch, cudaMemcpyHostToDevice, st));
+        SHTG_CUDA(cudaMemcpyAsync(p->d_isc64, i64.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, st));
+        SHTG_CUDA(cudaMemcpyAsync(p->d_rsc64, r64.data(), sizeof(double) * nsys, cudaMemcpyHostToDevice, st));
+        SHTG_CUDA(cudaMemcpyAsync(p->d_isc32, i32.data(), sizeof(float) * nsys, cudaMemcpyHostToDevice, st));
         SHTG_CUDA(cudaStreamSynchronize(st));   // the host vectors go out of scope
     }
     const int ncomp_ninv = nc == 3 ? 2 : 1;
@@ -887,7 +1028,7 @@ static int setup_operator(Plan *p, const shtg_problem *pr, int host_inputs, int 
             SHTG_TRY(leg_diag(p, 2, p->d_wpairP, p->d_diagP, st));
         }
     }
-    k_precond<<<dim3(grid_1d(p->nalm).x, pr->nbatch), RT, 0, st>>>(
+    k_precond<<<dim3(grid_1d(p->nalm).x, nsys), RT, 0, st>>>(
         p->d_diagT, nc == 3 ? p->d_diagP : p->d_diagT, p->d_ltab64, nc, p->nalm, p->lmax + 1, p->d_lofidx,
         precond, p->d_isc64, p->d_minv64, p->d_minv32);
     p->prof.launches += 1;
@@ -1064,8 +1205,13 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
         return SHTG_ERR_ARG;
     }
     const int host = (opt.flags & SHTG_HOST_INPUTS) ? 1 : 0;
+    const int split = (opt.flags & SHTG_SPLIT_RHS) ? 1 : 0;
     if (!pr->d || !pr->w1 || !pr->w2 || !alm_out) {
         set_error("d, w1, w2 and alm_out are required");
+        return SHTG_ERR_ARG;
+    }
+    if (split && 2 * pr->nbatch > p->max_batch) {
+        set_error("SHTG_SPLIT_RHS solves 2 nbatch systems: needs max_batch >= 2 nbatch");
         return SHTG_ERR_ARG;
     }
     shtg_cg_stats stt;
@@ -1075,7 +1221,9 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
     p->prof.open_cls = -1;
     const long long launches0 = p->prof.launches;
     const double t0 = now_ms();
-    const int nb = pr->nbatch, nc = pr->ncomp;
+    // nb systems: the realizations, or (split) their mean-field right-hand
+    // sides followed by their fluctuation right-hand sides
+    const int nr = pr->nbatch, nb = split ? 2 * nr : nr, nc = pr->ncomp;
     Solve s = make_solve(p, nb, nc, st);
     s.tc = opt.mode == SHTG_CG_MIXED_TC;
     s.df = opt.fp64_arith == SHTG_ARITH_DF64 || (opt.fp64_arith == SHTG_ARITH_DEFAULT && opt.mode != SHTG_CG_FP64);
@@ -1083,20 +1231,28 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
         const char *e = getenv("SHTG_GRAPHS");
         s.graphs = !(opt.flags & SHTG_NO_GRAPHS) && !(e && e[0] == '0');
     }
-    SHTG_TRY(setup_operator(p, pr, host, opt.precond, st));
+    SHTG_TRY(setup_operator(p, pr, host, opt.precond, st, nb));
     double2 *B = p->v64[0], *X = p->v64[1], *R = p->v64[2], *Tt = p->v64[6];
-    // ---- RHS: B Y^T (N^-1 d + N^-1/2 w2) + S^-1/2 w1 in FP64
+    // ---- RHS: B Y^T (N^-1 d + N^-1/2 w2) + S^-1/2 w1 in FP64; split: the
+    // mean field's B Y^T N^-1 d (Eq. mean-field-map) for systems [0, nr) and
+    // the fluctuation's S^-1/2 w1 + B Y^T N^-1/2 w2 (Eq. fluc-map) for [nr, 2 nr)
     const int64_t npix = p->npix;
-    const size_t mapbytes = sizeof(double) * (size_t)nb * nc * npix;
-    const dim3 pgrid(grid_1d(npix).x, nb * nc);
+    const size_t mapbytes = sizeof(double) * (size_t)nr * nc * npix;
+    const dim3 pgrid(grid_1d(npix).x, nr * nc);
+    const int wofs = split ? nr : 0;   // first system that receives w2 (and w1)
     if (host) {
         SHTG_CUDA(cudaMemcpyAsync(p->d_stage, pr->d, mapbytes, cudaMemcpyHostToDevice, st));
-        k_rhs_pix<<<pgrid, RT, 0, st>>>(p->d_stage, nullptr, p->d_ninv64, nb, nc, npix, 0, p->d_map64);
+        k_rhs_pix<<<pgrid, RT, 0, st>>>(p->d_stage, nullptr, p->d_ninv64, nb, 0, nc, npix, 0, p->d_map64);
         SHTG_CUDA(cudaMemcpyAsync(p->d_stage, pr->w2, mapbytes, cudaMemcpyHostToDevice, st));
-        k_rhs_pix<<<pgrid, RT, 0, st>>>(nullptr, p->d_stage, p->d_ninv64, nb, nc, npix, 1, p->d_map64);
+        k_rhs_pix<<<pgrid, RT, 0, st>>>(nullptr, p->d_stage, p->d_ninv64, nb, wofs, nc, npix, !split,
+                                        p->d_map64);
+        p->prof.launches += 2;
+    } else if (split) {
+        k_rhs_pix<<<pgrid, RT, 0, st>>>(pr->d, nullptr, p->d_ninv64, nb, 0, nc, npix, 0, p->d_map64);
+        k_rhs_pix<<<pgrid, RT, 0, st>>>(nullptr, pr->w2, p->d_ninv64, nb, nr, nc, npix, 0, p->d_map64);
         p->prof.launches += 2;
     } else {
-        k_rhs_pix<<<pgrid, RT, 0, st>>>(pr->d, pr->w2, p->d_ninv64, nb, nc, npix, 0, p->d_map64);
+        k_rhs_pix<<<pgrid, RT, 0, st>>>(pr->d, pr->w2, p->d_ninv64, nb, 0, nc, npix, 0, p->d_map64);
         p->prof.launches += 1;
     }
     SHTG_CHECK_LAUNCH("k_rhs_pix");
@@ -1106,12 +1262,15 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
         SHTG_TRY(op_analysis(s, 0, p->d_phase64, p->d_ltab64, B, nc));
         if (nc == 3) SHTG_TRY(op_analysis(s, 2, p->d_phase64 + nb * rowsz, p->d_ltab64, B + p->nalm, 3));
         const double2 *w1 = reinterpret_cast<const double2 *>(pr->w1);
+        const size_t w1n = (size_t)nr * nc * p->nalm;
         if (host) {
-            SHTG_CUDA(cudaMemcpyAsync(Tt, pr->w1, sizeof(double2) * (size_t)s.nvec, cudaMemcpyHostToDevice, st));
+            SHTG_CUDA(cudaMemcpyAsync(Tt, pr->w1, sizeof(double2) * w1n, cudaMemcpyHostToDevice, st));
             w1 = Tt;
         }
-        k_rhs_alm<<<s.vgrid, RT, 0, st>>>(w1, B, nc, p->nalm, p->lmax + 1, p->d_lofidx, p->d_mofidx,
-                                         p->d_ltab64 + 5 * (p->lmax + 1), p->d_rsc64);
+        k_rhs_alm<<<dim3(grid_1d(s.per).x, nr), RT, 0, st>>>(w1, B + wofs * s.per, nc, p->nalm, p->lmax + 1,
+                                                             p->d_lofidx, p->d_mofidx,
+                                                             p->d_ltab64 + 5 * (p->lmax + 1),
+                                                             p->d_rsc64 + wofs);
         p->prof.launches += 1;
         SHTG_CHECK_LAUNCH("k_rhs_alm");
     }
@@ -1183,7 +1342,7 @@ int logpost_grad(Plan *p, const double *cl, const double *bl, const float *alm, 
                  const float *ninv, int nbins, const int *blo, const int *bhi, int flags,
                  double *logp, float *grad, double *gcl, cudaStream_t st) {
     const int L1 = p->lmax + 1;
-    SHTG_TRY(build_ltab(p, 1, cl, bl));
+    SHTG_TRY(build_ltab(p, 1, cl, bl, st));
     // row 2 of the FP32 per-l table (unused by temperature problems) holds 1 / C_l, 0 where held
     std::vector<float> icl(L1);
     for (int l = 0; l < L1; ++l) icl[l] = cl[l] > 0 ? (float)(1.0 / cl[l]) : 0.f;
@@ -1220,6 +1379,84 @@ int logpost_grad(Plan *p, const double *cl, const double *bl, const float *alm, 
             for (int l = std::max(0, blo[k]); l <= std::min(p->lmax, bhi[k]); ++l) s += ls[l];
             gcl[k] = 0.5 * s;
         }
+    return SHTG_OK;
+}
+
+}  // namespace shtg
+
+namespace shtg {
+
+int fluctuation_rescale(Plan *p, int nc, const double *cl_old, const double *cl_new, const double *f,
+                        double *g, int nbatch, cudaStream_t st) {
+    if ((nc != 1 && nc != 3) || (nc == 3 && !(p->flags & SHTG_SPIN2)) || !cl_old || !cl_new || !f || !g ||
+        nbatch < 1) {
+        set_error("fluctuation_rescale: ncomp 1 or 3 (3 needs SHTG_SPIN2), non-null C_l and buffers, nbatch >= 1");
+        return SHTG_ERR_ARG;
+    }
+    const int L1 = p->lmax + 1;
+    const int rows = nc == 1 ? 1 : 4;
+    // old and new spectra staged in the plan's joint table, then R_l
+    double *cl = p->d_jtab, *R = p->d_jtab + 8 * (int64_t)L1;
+    SHTG_CUDA(cudaMemcpyAsync(cl, cl_old, sizeof(double) * rows * L1, cudaMemcpyHostToDevice, st));
+    SHTG_CUDA(cudaMemcpyAsync(cl + 4 * (int64_t)L1, cl_new, sizeof(double) * rows * L1, cudaMemcpyHostToDevice, st));
+    k_rescale_table<<<(L1 + 127) / 128, 128, 0, st>>>(cl, cl + 4 * (int64_t)L1, nc, L1, R);
+    SHTG_CHECK_LAUNCH("k_rescale_table");
+    k_rescale<<<dim3(grid_1d(p->nalm).x, nbatch), RT, 0, st>>>(
+        reinterpret_cast<const double2 *>(f), reinterpret_cast<double2 *>(g), nc, p->nalm, p->d_lofidx,
+        p->d_mofidx, R, L1);
+    SHTG_CHECK_LAUNCH("k_rescale");
+    p->prof.launches += 2;
+    // the host spectra must stay valid until the copies ran (pageable memory)
+    SHTG_CUDA(cudaStreamSynchronize(st));
+    return SHTG_OK;
+}
+
+int joint_log_target(Plan *p, const shtg_problem *pr, int precision, const double *a_hat,
+                     const double *f_hat, double *logpi, cudaStream_t st) {
+    SHTG_TRY(check_problem(p, pr));
+    if (!pr->d || !a_hat || !f_hat || !logpi || (precision != SHTG_FP64 && precision != SHTG_DF64)) {
+        set_error("joint_log_target: d, a_hat, f_hat and log_pi are required; precision SHTG_FP64 or SHTG_DF64");
+        return SHTG_ERR_ARG;
+    }
+    SHTG_TRY(setup_operator(p, pr, 0, 0, st));
+    const int nb = pr->nbatch, nc = pr->ncomp, L1 = p->lmax + 1;
+    Solve s = make_solve(p, nb, nc, st);
+    s.df = precision == SHTG_DF64;
+    double2 *F = p->d_phase64;
+    const int64_t rowsz = (int64_t)L1 * p->nring;
+    const double *beam = p->d_ltab64;
+    auto synth = [&](const double *x) -> int {
+        const double2 *a = reinterpret_cast<const double2 *>(x);
+        SHTG_TRY(op_synth(s, 0, a, nc, beam, F));
+        if (nc == 3) SHTG_TRY(op_synth(s, 2, a + p->nalm, 3, beam, F + nb * rowsz));
+        return ring_synth<double>(p, F, nb * nc, p->d_map64, st);
+    };
+    double *part = p->d_part;   // [3][nb][RB]: chi^2, fluctuation, prior
+    SHTG_TRY(synth(a_hat));
+    k_joint_pix<<<dim3(RB, nb), RT, 0, st>>>(pr->d, p->d_map64, p->d_ninv64, nb, nc, p->npix, 0, part);
+    SHTG_CHECK_LAUNCH("k_joint_pix");
+    SHTG_TRY(synth(f_hat));
+    k_joint_pix<<<dim3(RB, nb), RT, 0, st>>>(nullptr, p->d_map64, p->d_ninv64, nb, nc, p->npix, 1,
+                                              part + nb * RB);
+    SHTG_CHECK_LAUNCH("k_joint_pix");
+    k_prior_quad<<<dim3(RB, nb), RT, 0, st>>>(reinterpret_cast<const double2 *>(a_hat), nc, p->nalm, L1,
+                                               p->d_lofidx, p->d_mofidx, p->d_ltab64 + L1,
+                                               p->d_ltab64 + 5 * (int64_t)L1, p->d_isc64, part + 2 * nb * RB);
+    SHTG_CHECK_LAUNCH("k_prior_quad");
+    p->prof.launches += 3;
+    std::vector<double> h(3 * (size_t)nb * RB);
+    SHTG_CUDA(cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
+    SHTG_CUDA(cudaStreamSynchronize(st));
+    for (int b = 0; b < nb; ++b) {
+        double t[3] = {0.0, 0.0, 0.0};
+        for (int q = 0; q < 3; ++q)
+            for (int k = 0; k < RB; ++k) t[q] += h[((size_t)q * nb + b) * RB + k];
+        logpi[b] = -0.5 * t[0] - 0.5 * t[2] - 0.5 * t[1];
+        if (!std::isfinite(logpi[b])) {
+            set_error("joint_log_target: non-finite value in realization " + std::to_string(b));
+            return SHTG_ERR_NONFINITE;
+        }
+    }
     return SHTG_OK;
 }
 

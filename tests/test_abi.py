@@ -66,7 +66,8 @@ def test_binding_constants_match_header():
              "ARITH_DEFAULT": "SHTG_ARITH_DEFAULT", "ARITH_FP64": "SHTG_ARITH_FP64",
              "ARITH_DF64": "SHTG_ARITH_DF64", "CG_FP64": "SHTG_CG_FP64", "CG_MIXED": "SHTG_CG_MIXED",
              "CG_MIXED_TC": "SHTG_CG_MIXED_TC", "HOST_INPUTS": "SHTG_HOST_INPUTS",
-             "PROFILE": "SHTG_PROFILE", "NO_GRAPHS": "SHTG_NO_GRAPHS", "SPIN0": "SHTG_SPIN0",
+             "PROFILE": "SHTG_PROFILE", "NO_GRAPHS": "SHTG_NO_GRAPHS", "SPLIT_RHS": "SHTG_SPLIT_RHS",
+             "SPIN0": "SHTG_SPIN0",
              "SPIN2": "SHTG_SPIN2"}
     for py, c in pairs.items():
         assert getattr(N, py) == defs[c], (py, c)
@@ -132,3 +133,19 @@ def test_noalloc_rejects_invalid_sizes_without_gpu():
                               (512, 1024, buf, buf)]:     # scratch above 16 MiB
         assert f(nside, lmax, a, b, None) == -1, (nside, lmax)
         assert b"noalloc" in lib.shtg_last_error_string()
+
+
+def test_joint_acceptance_without_gpu():
+    """The acceptance rule of the joint move (Eq. acceptance-rate) is host
+    arithmetic in the library: min(1, exp of the log ratio), checked against
+    the oracle's restatement."""
+    from oracle import solver as osol
+    from paper_2306_15511_gb300 import _native as N
+    lib = N.load()
+    out = ctypes.c_double(-1.0)
+    for lpn, lpo, prn, pro in ((-10.0, -12.0, 0.0, 0.0), (-12.0, -10.0, 0.0, 0.0),
+                               (-1e7 - 3.5, -1e7, 0.25, -0.5), (5.0, 5.0, -1.0, 0.0)):
+        assert lib.shtg_joint_acceptance(lpn, lpo, prn, pro, ctypes.byref(out)) == 0
+        assert out.value == osol.joint_acceptance(lpn, lpo, prn, pro)
+    assert lib.shtg_joint_acceptance(float("nan"), 0.0, 0.0, 0.0, ctypes.byref(out)) == -5
+    assert lib.shtg_joint_acceptance(0.0, 0.0, 0.0, 0.0, None) == -1

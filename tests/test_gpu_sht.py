@@ -137,16 +137,17 @@ def polar_tol(prec, spin, L):
     three-term l-recurrence merge (e^{+-i theta}), so a rounding of relative
     size u = 2^-24 made at step k grows like sin((l - k) theta) / sin(theta)
     ~ (l - k) while l theta < 1 (l_max theta_0 ~ 1.6 on the first ring of
-    N_side 1024).  Independent roundings at every step then add up to a
-    relative error of about u sqrt(sum_k (l - k)^2) ~ u l_max^{3/2} / sqrt(3)
-    per rounding per step: c u l_max^{3/2} with c ~ 1 for the spin-0
-    recurrence (three roundings a step) and c ~ 2 for the two coupled spin-2
-    recurrences (measured at l_max 2048: 5e-3 and 1.2e-2 against
-    u l_max^{3/2} = 5.5e-3).  The gate is twice that, so a threefold
-    regression fails."""
+    N_side 1024).  Independent roundings at every step add up to a relative
+    error of about u sqrt(sum_k (l - k)^2) = u l_max^{3/2} / sqrt(3) per
+    rounding per step.  Spin 0 (one rounding a step that the recurrence
+    carries: the rest cancel in the u = 1 - cos(theta) form): the gate is
+    that estimate, u l_max^{3/2} / sqrt(3) = 3.2e-3 at l_max 2048, about twice
+    the measured 1.5e-3.  Spin 2 (two coupled recurrences, several roundings
+    a step): measured 1.24e-2 = 2.2 u l_max^{3/2}, gate 4 u l_max^{3/2}.  A
+    threefold regression fails either gate."""
     if prec == "fp64":
         return 1e-10
-    return (2.0 if spin == 0 else 4.0) * 2.0 ** -24 * L ** 1.5
+    return (1.0 / 3.0 ** 0.5 if spin == 0 else 4.0) * 2.0 ** -24 * L ** 1.5
 
 
 def _ring_err(m, g, rings, ref):
