@@ -540,9 +540,12 @@ template <int SPIN, int NAS, int NBS, int TR> struct TaLayout {
     static constexpr int ASTAGE = TaCfg<SPIN>::NAT * TC_ATILE;
     static constexpr int BSTAGE = TaCfg<SPIN>::NBT * BT;
     static constexpr int BOFF = NAS * ASTAGE;
-    // ring data of one stage: [pair][row][north, south] float2, pair stride GS (odd)
+    // ring data of one stage: [pair][north rows | south rows] float2 with pair
+    // stride GS = 2 NROW + 2: the B-tile builder's warp reads 8 consecutive
+    // floats per K pair and its four K pairs sit 4 GS = 8 (mod 32) floats
+    // apart, so every load hits 32 distinct banks
     static constexpr int NROW = SPIN == 2 ? 2 * TC_NMT : TC_NMT;
-    static constexpr int GS = 2 * NROW + 1;
+    static constexpr int GS = 2 * NROW + 2;
     static constexpr int GBUF = ((TA_K * GS * 8) + 15) & ~15;
     static constexpr int GOFF = BOFF + NBS * BSTAGE;
     static constexpr int COEF = GOFF + GBUF;
@@ -678,7 +681,7 @@ __device__ __forceinline__ void gen_atiles_ana(const PairStart &q, const float4 
 }
 
 // Asynchronous copy (cp.async) of the ring data of stage ps into sg:
-// element (pair p, row q, ring z) at sg[p GS + 2 q + z]; rows are the maps of
+// element (pair p, row q, ring z) at sg[p GS + z NROW + q]; rows are the maps of
 // this CTA (spin 2: Q, U of each); zeros for pairs beyond npairs, missing
 // maps and the south ring of the equator pair.
 template <int SPIN>
@@ -693,7 +696,7 @@ __device__ __forceinline__ void stage_ring_data(const LegArgs<float> &a, const i
         const int q = (it >> 1) % Lay::NROW;
         const int pp = it / (2 * Lay::NROW);
         const int pr = ps * TA_K + pp;
-        float2 *dst = sg + pp * Lay::GS + 2 * q + z;
+        float2 *dst = sg + pp * Lay::GS + z * Lay::NROW + q;
         const int rn = pr, rs = a.nring - 1 - pr;
         if (pr < a.npairs && q < nrow && !(z && rs == rn)) {
             const int64_t grow = (SPIN == 2 ? 2 * map0 : map0) + q;
@@ -728,12 +731,13 @@ __device__ __forceinline__ void gen_btiles_ana(const float2 *sg, unsigned char *
         const int k0 = 8 * kg + 2 * kq;
         unsigned char *tile = bt + kg * (32 * NO) + kq * 4;
         if (SPIN == 0) {
-            // column c: component c & 1 of map c >> 1
+            // column c: component c & 1 of map c >> 1, i.e. float c of the
+            // north rows and float 2 NROW + c (the south rows)
             float vp[2], vm[2];
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
-                const float *g = sgf + 2 * ((k0 + q) * Lay::GS + 2 * (c >> 1)) + (c & 1);
-                const float gn = g[0], gs = g[2];
+                const float *g = sgf + 2 * (k0 + q) * Lay::GS;
+                const float gn = g[c], gs = g[2 * Lay::NROW + c];
                 vp[q] = gn + gs;
                 vm[q] = gn + (-1.f) * gs;
             }
@@ -752,12 +756,14 @@ __device__ __forceinline__ void gen_btiles_ana(const float2 *sg, unsigned char *
             const int wf = comp < 2 ? 0 : 1, wc = comp & 1;            // field (Q 0, U 1), re / im
             const int xf = comp < 2 ? 1 : 0, xc = (comp & 1) ^ 1;
             const float xs = (comp == 1 || comp == 2) ? -1.f : 1.f;
+            // (row 2 k + field of the north rows at float 2 (2 k + field) + re/im,
+            // the south rows 2 NROW floats later)
             float wp[2], wm[2], xp[2], xm[2];
 #pragma unroll
             for (int q = 0; q < 2; ++q) {
-                const float *g = sgf + 2 * ((k0 + q) * Lay::GS + 4 * k);
-                const float wn = g[4 * wf + wc], wsv = g[4 * wf + 2 + wc];
-                const float xn = g[4 * xf + xc], xsv = g[4 * xf + 2 + xc];
+                const float *g = sgf + 2 * (k0 + q) * Lay::GS + 4 * k;
+                const float wn = g[2 * wf + wc], wsv = g[2 * Lay::NROW + 2 * wf + wc];
+                const float xn = g[2 * xf + xc], xsv = g[2 * Lay::NROW + 2 * xf + xc];
                 wp[q] = -(wn + wsv);
                 wm[q] = -(wn + (-1.f) * wsv);
                 xp[q] = xs * (xn + xsv);
