@@ -78,12 +78,21 @@ extern "C" {
 
 #define SHTG_SPIN0 1                 /* plan flag: temperature transforms */
 #define SHTG_SPIN2 2                 /* plan flag: also spin-2 (Q, U) transforms */
+#define SHTG_BLOCK_SOLVER 4          /* plan flag: also the workspace of SHTG_CG_BLOCK (per-m blocks of
+                                        one chunk of m, at most 512 MB, and their recurrence values,
+                                        at most 256 MB) */
 
 #define SHTG_CG_FP64 0               /* plain FP64 PCG */
 #define SHTG_CG_MIXED 1              /* FP32 PCG inside FP64-accurate iterative refinement
                                         (residual replacement; arithmetic: fp64_arith) */
 #define SHTG_CG_MIXED_TC 2           /* as SHTG_CG_MIXED with the FP32 operator's Legendre
                                         sums on the tensor cores (SHTG_TC32) */
+#define SHTG_CG_BLOCK 3              /* exact solve by one dense FP64 Cholesky per m (App. A): for
+                                        temperature with N^-1 constant along every ring on a grid whose
+                                        rings all have nphi >= 2 lmax + 1 (e.g. Gauss-Legendre with
+                                        nphi_gauss >= 2 lmax + 1), where A is block-diagonal in m; the
+                                        realizations share one C_l scale; the plan needs
+                                        SHTG_BLOCK_SOLVER; SHTG_ERR_ARG when a condition fails */
 
 #define SHTG_ARITH_DEFAULT 0         /* shtg_cg_opts.fp64_arith */
 #define SHTG_ARITH_FP64 1            /* native FP64 multiply-adds */
@@ -221,7 +230,7 @@ typedef struct {
 typedef struct {
     double tol;         /* stop when ||b - A x|| / ||b|| <= tol for every realization */
     int maxiter;        /* PCG iterations (FP64 mode) or FP32 iterations (mixed) */
-    int mode;           /* SHTG_CG_FP64, SHTG_CG_MIXED or SHTG_CG_MIXED_TC */
+    int mode;           /* SHTG_CG_FP64, SHTG_CG_MIXED, SHTG_CG_MIXED_TC or SHTG_CG_BLOCK */
     int precond;        /* 1: diagonal preconditioner of Sect. 4 (default); 0: none */
     double reliable_delta; /* mixed mode: an FP64 residual replacement happens when the FP32
                               residual has dropped by this factor since the last one (default 1e-2) */

@@ -17,8 +17,9 @@ and the synthesis Y written out:
 All inner products use the metric of :func:`oracle.sht.dot_q6`.
 
 Also here: the Gaussian log-posterior of Eq. (joint-posterior) with its
-gradients, and the pieces of the joint (C_l, a) move of Sect. 2.2.2 (the
-fluctuation rescaling, log pi(theta) and the acceptance rule).
+gradients, the pieces of the joint (C_l, a) move of Sect. 2.2.2 (the
+fluctuation rescaling, log pi(theta) and the acceptance rule), and the
+per-m dense block solve of App. A for azimuthally symmetric noise.
 """
 from __future__ import annotations
 
@@ -184,6 +185,67 @@ def pcg(prob: Problem, b, tol: float, maxiter: int = 1000, precond=True, x0=None
         it += 1
         hist.append(np.sqrt(prob.dot(r, r)) / bn)
     return x, it, np.array(hist)
+
+
+# ----------------------------------------------------------------------------
+# Per-m dense block solve for azimuthally symmetric noise (App. A)
+# ----------------------------------------------------------------------------
+def ring_weights(prob: Problem):
+    """N^-1 of each ring when it is constant along every ring (App. A: a
+    constant-latitude mask with noise that depends on latitude only), else
+    None.  Temperature only."""
+    g = prob.g
+    w = np.zeros(g.nring)
+    nv = prob.ninv[0]
+    for r in range(g.nring):
+        seg = nv[g.ofs[r]:g.ofs[r] + g.nphi[r]]
+        if np.any(seg != seg[0]):
+            return None
+        w[r] = seg[0]
+    return w
+
+
+def azimuthal_block(prob: Problem, m: int, wring):
+    """The m-block of A for ring-constant N^-1 (App. A, Eq. N_lml'm'_step in
+    its discrete form): with every ring holding nphi >= 2 lmax + 1 pixels the
+    phi sum of e^{-i (m - m') phi} vanishes unless m = m', so
+    A^(m)_{l l'} = delta_{l l'} / C_l + b_l b_l' sum_r nphi_r w_r
+    lambda_lm(theta_r) lambda_l'm(theta_r)
+    for l, l' >= m; held multipoles (singular C_l) are identity rows.
+    Returns (l values, dense block)."""
+    L = prob.lmax
+    g = prob.g
+    lr = np.arange(m, L + 1)
+    lam = np.array([sht.lambda_lm(L, m, g.cth[r], g.sth[r]) for r in range(g.nring)])  # (nring, nl)
+    K = (lam * (g.nphi * wring)[:, None]).T @ lam
+    bm = prob.bmask[lr]
+    A = bm[:, None] * K * bm[None, :]
+    act = prob.active[lr]
+    A[np.ix_(act, act)] += np.diag(prob.sinv[0, 0][lr][act])
+    held = np.where(~act)[0]
+    A[held, :] = 0.0
+    A[:, held] = 0.0
+    A[held, held] = 1.0
+    return lr, A
+
+
+def block_solve(prob: Problem, b):
+    """x = A^-1 b by one dense solve per m (App. A), for temperature with
+    ring-constant N^-1 on a grid whose rings all have nphi >= 2 lmax + 1."""
+    assert prob.ncomp == 1
+    wring = ring_weights(prob)
+    g = prob.g
+    if wring is None or np.any(g.nphi < 2 * prob.lmax + 1):
+        raise ValueError("block_solve needs ring-constant N^-1 and nphi >= 2 lmax + 1 on every ring")
+    b = np.asarray(b, np.complex128).reshape(1, -1)
+    x = np.zeros_like(b)
+    ms = sht.ms_of(prob.lmax)
+    for m in range(prob.lmax + 1):
+        _, A = azimuthal_block(prob, m, wring)
+        sel = ms == m
+        rhs = b[0, sel]
+        x[0, sel] = np.linalg.solve(A, rhs.real) + 1j * np.linalg.solve(A, rhs.imag)
+    return _zero_im_m0(x, prob.lmax)
 
 
 def true_residual(prob: Problem, x, b) -> float:

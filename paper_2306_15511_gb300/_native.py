@@ -16,8 +16,8 @@ ERRORS = {-1: "SHTG_ERR_ARG", -2: "SHTG_ERR_CUDA", -3: "SHTG_ERR_NOT_CONVERGED",
 GEOM_HEALPIX, GEOM_GAUSS = 0, 1
 FP64, FP32, TC32, DF64 = 0, 1, 2, 3
 ARITH_DEFAULT, ARITH_FP64, ARITH_DF64 = 0, 1, 2
-SPIN0, SPIN2 = 1, 2
-CG_FP64, CG_MIXED, CG_MIXED_TC = 0, 1, 2
+SPIN0, SPIN2, BLOCK_SOLVER = 1, 2, 4
+CG_FP64, CG_MIXED, CG_MIXED_TC, CG_BLOCK = 0, 1, 2, 3
 HOST_INPUTS = 1
 PROFILE = 2
 NO_GRAPHS = 4

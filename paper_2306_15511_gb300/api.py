@@ -64,15 +64,16 @@ class Plan:
 
     Plan(nside=N, lmax=L)                      HEALPix RING grid
     Plan(gauss=(nring, nphi), lmax=L)          Gauss-Legendre grid
-    max_batch: realizations per call; spin2: also Q/U transforms (T+E+B).
+    max_batch: realizations per call; spin2: also Q/U transforms (T+E+B);
+    block_solver: workspace of the exact per-m block solve (mode "block").
     """
 
     def __init__(self, nside: int | None = None, lmax: int = 0, max_batch: int = 1,
-                 spin2: bool = False, gauss: tuple | None = None):
+                 spin2: bool = False, gauss: tuple | None = None, block_solver: bool = False):
         lib = N.load()
         self._lib = lib
         h = C.c_void_p()
-        flags = N.SPIN0 | (N.SPIN2 if spin2 else 0)
+        flags = N.SPIN0 | (N.SPIN2 if spin2 else 0) | (N.BLOCK_SOLVER if block_solver else 0)
         if gauss is not None:
             rc = lib.shtg_plan_create(N.GEOM_GAUSS, int(gauss[0]), int(gauss[1]), int(lmax),
                                       int(max_batch), flags, C.byref(h))
@@ -191,6 +192,12 @@ class Plan:
                   cl_scale=None, fp64_arith: str = "default", split: bool = False):
         """Constrained realization(s) of Eq. (mapmakingeq).
 
+        mode: "fp64" (plain FP64 PCG), "mixed" / "mixed_tc" (FP32 PCG with
+        FP64-accurate residual replacement; CUDA-core / tensor-core Legendre
+        sums) or "block" (exact per-m dense solve of App. A for temperature
+        with ring-constant N^-1 on a grid with nphi >= 2 lmax + 1 on every
+        ring; the plan needs block_solver=True).
+
         cl_scale: optional [nbatch] amplitudes; realization b uses cl_scale[b] x cl.
 
         split: solve the mean field (Eq. mean-field-map) and the fluctuation
@@ -228,7 +235,7 @@ class Plan:
         pr = self._problem(cl, bl, ninv, d, w1, w2, nb, nc, cl_scale)
         o = N.CGOpts()
         o.tol, o.maxiter = float(tol), int(maxiter)
-        modes = {"fp64": N.CG_FP64, "mixed": N.CG_MIXED, "mixed_tc": N.CG_MIXED_TC}
+        modes = {"fp64": N.CG_FP64, "mixed": N.CG_MIXED, "mixed_tc": N.CG_MIXED_TC, "block": N.CG_BLOCK}
         if mode not in modes:
             raise ValueError(f"mode must be one of {sorted(modes)}")
         o.mode = modes[mode]

@@ -198,6 +198,12 @@ struct Plan {
     double4_32a *d_tst64_2 = nullptr;
     double *d_lsum = nullptr;      // [lmax+1] per-l sums (log-posterior)
     double *d_jtab = nullptr;      // [13][lmax+1] joint move: old and new spectra [2][4], rescaling rows [5]
+    // per-m dense block solve (plans created with SHTG_BLOCK_SOLVER): blocks
+    // and recurrence values of one chunk of m, ring-pair weights, offsets, flag
+    double *d_blk = nullptr, *d_blklam = nullptr, *d_blkw = nullptr;
+    int64_t *d_blkoff = nullptr;
+    int *d_blkflag = nullptr;
+    int64_t blk_cap = 0, lam_cap = 0;
     double *d_stage = nullptr;     // [nmaps_max][npix] staging for host inputs
     double *h_pinned = nullptr;    // pinned host scalars
 };
@@ -211,6 +217,9 @@ int fluctuation_rescale(Plan *p, int nc, const double *cl_old, const double *cl_
                         double *g, int nbatch, cudaStream_t st);
 int joint_log_target(Plan *p, const shtg_problem *pr, int precision, const double *a_hat,
                      const double *f_hat, double *logpi, cudaStream_t st);
+// block.cu: per-m dense block solve for azimuthally symmetric noise (App. A)
+int block_workspace(Plan *p);
+int block_solve(Plan *p, const double2 *B, double2 *X, int nb, double isc, cudaStream_t st);
 int logpost_grad(Plan *p, const double *cl, const double *bl, const float *alm, const float *d,
                  const float *ninv, int nbins, const int *blo, const int *bhi, int flags,
                  double *logp, float *grad, double *gcl, cudaStream_t st);

@@ -549,11 +549,18 @@ template <int SPIN, int NAS, int NBS, int TR> struct TaLayout {
     static constexpr int GBUF = ((TA_K * GS * 8) + 15) & ~15;
     static constexpr int GOFF = BOFF + NBS * BSTAGE;
     static constexpr int COEF = GOFF + GBUF;
-    static constexpr int BARS = COEF + 256 * TR * (SPIN == 2 ? 16 : 8);
+    // coefficients of 256 TR l, one padding entry after every 32 (ta_cpad)
+    static constexpr int BARS = COEF + 264 * TR * (SPIN == 2 ? 16 : 8);
     static constexpr int TMEM = TR * TaCfg<SPIN>::TMEM / 2;   // 2 NO columns per 256-l tile
     static constexpr int TMEMA = BARS + 16;
     static constexpr int BYTES = TMEMA + 16;
 };
+
+// Shared index of the recurrence coefficients of l = lbase + i in the
+// transpose: one padding entry after every 32, so the two 32-l segments that
+// a warp's threads step through at once (256 or 512 bytes apart unpadded,
+// the same banks) read distinct banks.
+__device__ __forceinline__ int ta_cpad(int i) { return i + (i >> 5); }
 
 // MN-major A (bit 15), K-major B, bf16 in, FP32 accumulator
 __host__ __device__ constexpr uint32_t idesc_bf16_amn(int m, int n) {
@@ -649,9 +656,9 @@ __device__ __forceinline__ void gen_atiles_ana(const PairStart &q, const float4 
                 const int d = 16 * h + 2 * i;
                 e[i] = o[i] = 0.f;
                 if (live) {
-                    stepx<float, 1, 0, INJ>(S, s_rec, s_s2c, l0 + d - lbase, l0 + d);
+                    stepx<float, 1, 0, INJ>(S, s_rec, s_s2c, ta_cpad(l0 + d - lbase), l0 + d);
                     e[i] = S.a1[0];
-                    stepx<float, 1, 0, INJ>(S, s_rec, s_s2c, l0 + d + 1 - lbase, l0 + d + 1);
+                    stepx<float, 1, 0, INJ>(S, s_rec, s_s2c, ta_cpad(l0 + d + 1 - lbase), l0 + d + 1);
                     o[i] = S.a1[0];
                 }
             }
@@ -664,10 +671,10 @@ __device__ __forceinline__ void gen_atiles_ana(const PairStart &q, const float4 
                 const int d = 16 * h + 2 * i;
                 wE[i] = wO[i] = xE[i] = xO[i] = 0.f;
                 if (live) {
-                    stepx<float, 1, 2, INJ>(S, s_rec, s_s2c, l0 + d - lbase, l0 + d);
+                    stepx<float, 1, 2, INJ>(S, s_rec, s_s2c, ta_cpad(l0 + d - lbase), l0 + d);
                     wE[i] = S.a1[0] + S.b1[0];
                     xE[i] = S.a1[0] - S.b1[0];
-                    stepx<float, 1, 2, INJ>(S, s_rec, s_s2c, l0 + d + 1 - lbase, l0 + d + 1);
+                    stepx<float, 1, 2, INJ>(S, s_rec, s_s2c, ta_cpad(l0 + d + 1 - lbase), l0 + d + 1);
                     wO[i] = S.a1[0] + S.b1[0];
                     xO[i] = S.a1[0] - S.b1[0];
                 }
@@ -811,8 +818,8 @@ __global__ void __launch_bounds__(TC_M) k_leg_analysis_tc(const LegArgs<float> a
     for (int i = tid; i < 256 * TR; i += TC_M) {
         const int l = lbase + i;
         const bool in = l <= L;
-        if (SPIN == 2) s_s2c[i] = in ? a.s2c[base + l] : make_float4(0.f, 0.f, 0.f, 0.f);
-        else s_rec[i] = in ? a.rec[base + l] : make_float2(0.f, 0.f);
+        if (SPIN == 2) s_s2c[ta_cpad(i)] = in ? a.s2c[base + l] : make_float4(0.f, 0.f, 0.f, 0.f);
+        else s_rec[ta_cpad(i)] = in ? a.rec[base + l] : make_float2(0.f, 0.f);
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])));

@@ -727,6 +727,14 @@ int plan_build(Plan *p) {
     SHTG_TRY(dalloc(p, &p->d_wpairP, p->npairs));
     SHTG_TRY(dalloc(p, &p->d_ltab64, 9 * (int64_t)(p->lmax + 1)));
     SHTG_TRY(dalloc(p, &p->d_jtab, 13 * (int64_t)(p->lmax + 1)));
+    if (p->flags & SHTG_BLOCK_SOLVER) {
+        SHTG_TRY(block_workspace(p));
+        SHTG_TRY(dalloc(p, &p->d_blk, p->blk_cap));
+        SHTG_TRY(dalloc(p, &p->d_blklam, p->lam_cap));
+        SHTG_TRY(dalloc(p, &p->d_blkw, 2 * (int64_t)p->npairs));
+        SHTG_TRY(dalloc(p, &p->d_blkoff, 2 * (int64_t)(p->lmax + 1)));
+        SHTG_TRY(dalloc(p, &p->d_blkflag, 4));
+    }
     SHTG_TRY(dalloc(p, &p->d_ltab32, 5 * (int64_t)(p->lmax + 1)));
     SHTG_TRY(dalloc(p, &p->d_scal, 16 * (int64_t)p->max_batch));
     SHTG_TRY(dalloc(p, &p->d_part, 4 * (int64_t)p->max_batch * SHTG_RED_BLOCKS + 4 * (int64_t)p->max_batch + 64));
@@ -761,7 +769,8 @@ void plan_free(Plan *p) {
                     p->d_ls2_64, p->d_st2_64, p->d_ls2_32, p->d_st2_32, p->d_ring_groups, p->d_flag,
                     p->d_toff, p->d_tst0, p->d_tst2, p->d_isc64, p->d_rsc64, p->d_isc32,
                     p->d_toff64, p->d_tst64_0, p->d_tst64_2, p->d_rph64, p->d_rph32, p->d_twf64,
-                    p->d_twf32, p->d_jtab};
+                    p->d_twf32, p->d_jtab, p->d_blk, p->d_blklam, p->d_blkw, p->d_blkoff,
+                    p->d_blkflag};
     for (void *q : ptrs)
         if (q) cudaFree(q);
     for (int i = 0; i < 7; ++i)

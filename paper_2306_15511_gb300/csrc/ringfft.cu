@@ -17,6 +17,8 @@
 // with precomputed kernel spectra.  The fused variant applies N^-1 between
 // the inverse and the forward transform, so the pixel map never goes to
 // global memory inside an operator application.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace shtg {
@@ -296,6 +298,8 @@ __device__ __forceinline__ void dft16_tp(C *v) {
     for (int s1 = 0; s1 < 4; ++s1) dft4<false>(v[4 * s1], v[4 * s1 + 1], v[4 * s1 + 2], v[4 * s1 + 3]);
 }
 
+__host__ __device__ constexpr int twf_len(int logm) { return twf_pass_off(logm, logm >> 2); }
+
 template <int R, int LOGM, int NT, typename C>
 __device__ __forceinline__ void fpass_first(C *buf) {
     constexpr int M = 1 << LOGM, NB = M / R, BPT = (NB + NT - 1) / NT;
@@ -351,7 +355,7 @@ __device__ __forceinline__ void fpass16(C *buf, const C *__restrict__ twp) {
                 // w^r for r = 4a + c from the two table values w and w^4:
                 // w^2, w^3 = w^2 w; w^8 = (w^4)^2, w^12 = w^8 w^4; w^(4a + c) =
                 // w^(4a) w^c: at most five roundings, ten live registers
-                const C w1 = __ldg(twp + k), w4 = __ldg(twp + NS + k);
+                const C w1 = twp[k], w4 = twp[NS + k];
                 const C w2 = cmul(w1, w1), w3 = cmul(w2, w1);
                 v[b][1] = cmul(v[b][1], w1);
                 v[b][2] = cmul(v[b][2], w2);
@@ -427,6 +431,7 @@ template <typename T> struct RingArgs {
     const C *chirp, *bfwd, *binv;
     const C *rph;     // ring phase tables e^{i pi k / n}
     const C *twf;     // fixed-length launches: pass twiddles for M = 2^FIX
+    int mpg;          // maps per CTA: CTA (pair, y) handles maps [y mpg, min(nmaps, (y + 1) mpg))
     C *FG;            // [map][ring][m]
     T *map;           // [map][npix]
     const T *ninv;    // fused: [comp][npix]
@@ -459,12 +464,18 @@ __global__ void __launch_bounds__(NT, (RingBlocks<T, NT, FIX>::v)) k_ring(const 
     // FIX > 0: every ring of the launch has M = 2^FIX and the fixed-length
     // passes run (twiddles from twf, no shared twiddle table)
     constexpr bool fixed = FIX > 0;
-    const int ntw = fixed ? 0 : a.tw_nlo + a.tw_nhi;
+    // FP32 fixed-length launches stage their pass twiddles in shared memory
+    // (at most 1092 entries); FP64 ones read them through L1 (the FP64
+    // 8192-point buffer and chirp leave no room)
+    constexpr bool twf_smem = fixed && sizeof(T) == 4;
+    const int ntw = fixed ? (twf_smem ? twf_len(FIX > 0 ? FIX : 8) : 0) : a.tw_nlo + a.tw_nhi;
     C *s_tw = reinterpret_cast<C *>(s_raw);
     C *buf = s_tw + ntw;
     C *s_chirp = buf + a.buf_len;          // this ring's chirp (Bluestein rings)
-    C *scr_p = s_chirp + a.chirp_len;      // aliased fold: partial sums [north | south][NT]
-    for (int i = threadIdx.x; i < ntw; i += NT) s_tw[i] = a.tw[i];
+    C *scr_p = s_chirp + a.chirp_len;      // aliased fold: partial sums [north | south][NT] (generic launches)
+    const C *tw_src = fixed ? a.twf : a.tw;
+    for (int i = threadIdx.x; i < ntw; i += NT) s_tw[i] = tw_src[i];
+    const C *twf = twf_smem ? s_tw : a.twf;
     TwTab<C> tw;
     tw.lo = s_tw;
     tw.hi = s_tw + a.tw_nlo;
@@ -489,7 +500,8 @@ __global__ void __launch_bounds__(NT, (RingBlocks<T, NT, FIX>::v)) k_ring(const 
     const C zero = {T(0), T(0)};
     constexpr int NDIR = MODE == 2 ? 2 : 1;
 
-    for (int q = 0; q < a.nmaps; ++q) {
+    const int q0 = blockIdx.y * a.mpg, q1 = min(a.nmaps, q0 + a.mpg);
+    for (int q = q0; q < q1; ++q) {
         if (MODE != 1 && n >= 2 * L) {
             // ---- fold without aliasing (n >= 2 l_max): F(m) alone fills bin m
             // and conj F(m) bin n - m (phase e^{+-i pi s m / n}); with n = 2 l_max
@@ -531,7 +543,7 @@ __global__ void __launch_bounds__(NT, (RingBlocks<T, NT, FIX>::v)) k_ring(const 
             // Q of the south ring in buf[n, 2n) (the launch's buffer holds 2n
             // for every aliased ring; Bluestein rings: M >= 2n)
             auto qsr = [&](int k) -> C & { return buf[rpad(n + k)]; };
-            const int S = n <= NT / 2 ? NT / n : 1;
+            const int S = (!fixed && n <= NT / 2) ? NT / n : 1;   // fixed launches: n > NT / 2
             if (S > 1) {
                 const int k = threadIdx.x % n, s = threadIdx.x / n;
                 if (s < S) {
@@ -638,7 +650,7 @@ __global__ void __launch_bounds__(NT, (RingBlocks<T, NT, FIX>::v)) k_ring(const 
             const bool fwd = MODE == 1 || dir == 1;
             const C *bh = f.blue ? (fwd ? a.bfwd : a.binv) + f.bhat_off : nullptr;
             if constexpr (fixed) {
-                transform_dir_fixed<(fixed ? FIX : 8), NT>(buf, a.twf, bh);
+                transform_dir_fixed<(fixed ? FIX : 8), NT>(buf, twf, bh);
             } else {
                 transform_dir<NT>(buf, logM, tw, bh);
             }
@@ -776,10 +788,22 @@ template <> RingArgs<double> ring_args<double>(Plan *p) {
 }
 
 template <typename T, int MODE, int NT, int FIX>
-static int launch_ring_nt(const RingArgs<T> &a, int ctas, size_t smem, cudaStream_t st) {
+static int launch_ring_nt(RingArgs<T> a, int ctas, size_t smem, cudaStream_t st) {
     auto kern = k_ring<T, MODE, NT, FIX>;
     if (smem > 48 * 1024) SHTG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<ctas, NT, smem, st>>>(a);
+    // The maps of a ring pair are split over grid.y when the pairs alone give
+    // fewer than four waves of resident CTAs (a CTA still handles at least
+    // two maps, so its chirp and twiddle staging stay amortized)
+    int dev = 0, nsm = 0, per = 0;
+    SHTG_CUDA(cudaGetDevice(&dev));
+    SHTG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    SHTG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, NT, smem));
+    const int want = 4 * nsm * (per > 0 ? per : 1);
+    int groups = (want + ctas - 1) / ctas;
+    groups = std::max(1, std::min(groups, (a.nmaps + 1) / 2));
+    a.mpg = (a.nmaps + groups - 1) / groups;
+    groups = (a.nmaps + a.mpg - 1) / a.mpg;
+    kern<<<dim3(ctas, groups), NT, smem, st>>>(a);
     return SHTG_OK;
 }
 
@@ -825,8 +849,12 @@ static int launch_ring(Plan *p, RingArgs<T> a, cudaStream_t st) {
         a.buf_len = M + M / 16;
         a.chirp_len = g.chirp;
         a.twf = fix ? ring_twf<T>(p) + p->twf_off[g.fix] : nullptr;
-        const size_t smem = sizeof(C) * ((fix ? 0 : (size_t)p->tw_nlo + p->tw_nhi) + a.buf_len + a.chirp_len +
-                                         (g.alias ? 2 * nt : 0));
+        // shared memory: twiddles (generic: two-level table; FP32 fixed: the
+        // pass tables), buffer, chirp, and the aliased fold's partial sums
+        // (generic launches only: a fixed launch's rings have n >= M / 2 >
+        // NT / 2, so they never split a residue's sum)
+        const size_t ntw = fix ? (sizeof(T) == 4 ? (size_t)twf_len(g.fix) : 0) : (size_t)p->tw_nlo + p->tw_nhi;
+        const size_t smem = sizeof(C) * (ntw + a.buf_len + a.chirp_len + ((g.alias && !fix) ? 2 * nt : 0));
         a.pairs = p->d_ring_groups + g.off;
         int rc = SHTG_OK;
         switch (g.fix) {

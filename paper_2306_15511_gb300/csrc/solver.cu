@@ -1195,9 +1195,34 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
     if (opt.maxiter <= 0) opt.maxiter = 1000;
     if (!(opt.reliable_delta > 0 && opt.reliable_delta < 1)) opt.reliable_delta = 1e-2;
     if (opt.check_every <= 0) opt.check_every = 4;
-    if (opt.mode != SHTG_CG_FP64 && opt.mode != SHTG_CG_MIXED && opt.mode != SHTG_CG_MIXED_TC) {
-        set_error("mode must be SHTG_CG_FP64, SHTG_CG_MIXED or SHTG_CG_MIXED_TC");
+    if (opt.mode != SHTG_CG_FP64 && opt.mode != SHTG_CG_MIXED && opt.mode != SHTG_CG_MIXED_TC &&
+        opt.mode != SHTG_CG_BLOCK) {
+        set_error("mode must be SHTG_CG_FP64, SHTG_CG_MIXED, SHTG_CG_MIXED_TC or SHTG_CG_BLOCK");
         return SHTG_ERR_ARG;
+    }
+    if (opt.mode == SHTG_CG_BLOCK) {
+        // the conditions of App. A's block-diagonal form (the ring-constant
+        // N^-1 is checked on the device once it is staged)
+        if (!(p->flags & SHTG_BLOCK_SOLVER)) {
+            set_error("SHTG_CG_BLOCK needs a plan created with SHTG_BLOCK_SOLVER");
+            return SHTG_ERR_ARG;
+        }
+        if (pr->ncomp != 1) {
+            set_error("SHTG_CG_BLOCK solves temperature problems only");
+            return SHTG_ERR_ARG;
+        }
+        for (int r = 0; r < p->nring; ++r)
+            if (p->nphi[r] < 2 * p->lmax + 1) {
+                set_error("SHTG_CG_BLOCK needs nphi >= 2 lmax + 1 on every ring (ring " + std::to_string(r) +
+                          " has " + std::to_string(p->nphi[r]) + ")");
+                return SHTG_ERR_ARG;
+            }
+        if (pr->cl_scale)
+            for (int b = 1; b < pr->nbatch; ++b)
+                if (pr->cl_scale[b] != pr->cl_scale[0]) {
+                    set_error("SHTG_CG_BLOCK: the realizations must share one C_l scale");
+                    return SHTG_ERR_ARG;
+                }
     }
     if (opt.fp64_arith != SHTG_ARITH_DEFAULT && opt.fp64_arith != SHTG_ARITH_FP64 &&
         opt.fp64_arith != SHTG_ARITH_DF64) {
@@ -1226,12 +1251,13 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
     const int nr = pr->nbatch, nb = split ? 2 * nr : nr, nc = pr->ncomp;
     Solve s = make_solve(p, nb, nc, st);
     s.tc = opt.mode == SHTG_CG_MIXED_TC;
-    s.df = opt.fp64_arith == SHTG_ARITH_DF64 || (opt.fp64_arith == SHTG_ARITH_DEFAULT && opt.mode != SHTG_CG_FP64);
+    s.df = opt.fp64_arith == SHTG_ARITH_DF64 ||
+           (opt.fp64_arith == SHTG_ARITH_DEFAULT && opt.mode != SHTG_CG_FP64 && opt.mode != SHTG_CG_BLOCK);
     {
         const char *e = getenv("SHTG_GRAPHS");
         s.graphs = !(opt.flags & SHTG_NO_GRAPHS) && !(e && e[0] == '0');
     }
-    SHTG_TRY(setup_operator(p, pr, host, opt.precond, st, nb));
+    SHTG_TRY(setup_operator(p, pr, host, opt.mode == SHTG_CG_BLOCK ? 0 : opt.precond, st, nb));
     double2 *B = p->v64[0], *X = p->v64[1], *R = p->v64[2], *Tt = p->v64[6];
     // ---- RHS: B Y^T (N^-1 d + N^-1/2 w2) + S^-1/2 w1 in FP64; split: the
     // mean field's B Y^T N^-1 d (Eq. mean-field-map) for systems [0, nr) and
@@ -1287,7 +1313,15 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
     stt.ms_rhs = t1 - t0;
     int rc = SHTG_OK;
     std::vector<double> rr;
-    if (opt.mode == SHTG_CG_FP64) {
+    if (opt.mode == SHTG_CG_BLOCK) {
+        SHTG_TRY(block_solve(p, B, X, nb, pr->cl_scale ? 1.0 / pr->cl_scale[0] : 1.0, st));
+        // the FP64 residual of the exact solve, for the stats
+        SHTG_TRY(matvec<double>(s, X, Tt));
+        stt.fp64_matvecs = 1;
+        k_resid<<<grid_1d(s.nvec), RT, 0, st>>>(B, Tt, R, s.nvec);
+        p->prof.launches += 1;
+        SHTG_TRY(norms2(s, R, rr));
+    } else if (opt.mode == SHTG_CG_FP64) {
         int iters = 0, conv = 0;
         rc = pcg<double>(s, B, X, opt.tol, opt.maxiter, opt.check_every, &iters, &conv);
         stt.iterations = iters;

@@ -65,7 +65,7 @@ def test_binding_constants_match_header():
     pairs = {"FP64": "SHTG_FP64", "FP32": "SHTG_FP32", "TC32": "SHTG_TC32", "DF64": "SHTG_DF64",
              "ARITH_DEFAULT": "SHTG_ARITH_DEFAULT", "ARITH_FP64": "SHTG_ARITH_FP64",
              "ARITH_DF64": "SHTG_ARITH_DF64", "CG_FP64": "SHTG_CG_FP64", "CG_MIXED": "SHTG_CG_MIXED",
-             "CG_MIXED_TC": "SHTG_CG_MIXED_TC", "HOST_INPUTS": "SHTG_HOST_INPUTS",
+             "CG_MIXED_TC": "SHTG_CG_MIXED_TC", "CG_BLOCK": "SHTG_CG_BLOCK", "BLOCK_SOLVER": "SHTG_BLOCK_SOLVER", "HOST_INPUTS": "SHTG_HOST_INPUTS",
              "PROFILE": "SHTG_PROFILE", "NO_GRAPHS": "SHTG_NO_GRAPHS", "SPLIT_RHS": "SHTG_SPLIT_RHS",
              "SPIN0": "SHTG_SPIN0",
              "SPIN2": "SHTG_SPIN2"}

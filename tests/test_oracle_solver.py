@@ -197,6 +197,64 @@ def test_constant_latitude_mask_block_structure():
     assert np.max(np.abs(Av[0, ms != 3])) < 1e-13 * np.max(np.abs(Av))
 
 
+def _azimuthal_problem(L, north_south_asymmetric=False):
+    """GL grid (nphi >= 2 L + 1), ring-constant N^-1: a |b| < 25 deg cut and
+    optionally noise that differs between the hemispheres."""
+    g = sht.gauss_legendre(L + 1, 2 * L + 2)
+    ninv_ring = np.where(np.abs(g.cth) < math.sin(25 * C.DEG), 0.0, 1.0 / 5.0 ** 2)
+    if north_south_asymmetric:
+        ninv_ring = ninv_ring * np.where(g.cth > 0, 1.0, 0.35) * (1.0 + 0.5 * g.cth ** 2)
+    ninv = np.repeat(ninv_ring, g.nphi)
+    prob = solver.Problem(g, L, C.cl_flat(L), C.gauss_beam(L, 10 * C.DEG), ninv)
+    return g, prob, ninv_ring
+
+
+@pytest.mark.parametrize("asym", [False, True])
+def test_block_solve_equals_pcg(asym):
+    """The per-m dense solves of App. A equal a PCG solve converged to 1e-13
+    (an independent method on the same operator); with hemispheres of
+    different noise the l + l' odd entries no longer vanish and still
+    solve correctly."""
+    L = 24
+    g, prob, wr = _azimuthal_problem(L, asym)
+    assert np.array_equal(solver.ring_weights(prob), wr)
+    rng = np.random.default_rng(12)
+    b = _rand_alm(L, rng)
+    b[:, sht.ls_of(L) < 2] = 0
+    xb = solver.block_solve(prob, b)
+    xp, _, _ = solver.pcg(prob, b, 1e-13, 800)
+    assert np.max(np.abs(xb - xp)) < 1e-10 * np.max(np.abs(xp))
+    _, A3 = solver.azimuthal_block(prob, 3, wr)
+    odd = ((np.arange(3, L + 1)[:, None] + np.arange(3, L + 1)[None, :]) % 2) == 1
+    assert (np.max(np.abs(A3[odd])) > 1e-6 * np.max(np.abs(A3))) == asym
+
+
+def test_azimuthal_block_is_the_operator_restricted_to_m():
+    """Brute force: apply A to every unit vector of one m (real parts) and
+    read the m-block off the operator; it equals azimuthal_block."""
+    L, m = 12, 2
+    g, prob, wr = _azimuthal_problem(L, True)
+    ls, ms = sht.ls_of(L), sht.ms_of(L)
+    idx = np.where(ms == m)[0]
+    cols = []
+    for i in idx:
+        e = np.zeros((1, ls.size), complex)
+        e[0, i] = 1.0
+        cols.append(prob.matvec(e)[0, idx].real)
+    Abf = np.array(cols).T
+    lr, A = solver.azimuthal_block(prob, m, wr)
+    assert np.array_equal(lr, ls[idx])
+    assert np.max(np.abs(Abf - A)) < 1e-12 * np.max(np.abs(A))
+
+
+def test_block_solve_refuses_non_azimuthal_noise():
+    p = C.masked_temperature(8, 16)
+    prob = solver.Problem(sht.healpix(8), 16, p.cl, p.bl, p.ninv)
+    assert solver.ring_weights(prob) is None
+    with pytest.raises(ValueError):
+        solver.block_solve(prob, np.zeros((1, (17 * 18) // 2), complex))
+
+
 # ----------------------------------------------------------- linearity
 def test_mean_field_plus_fluctuation():
     p = C.fullsky_temperature(8, 16)
