@@ -345,6 +345,27 @@ def joint_log_target(prob: Problem, d, a_hat, f_hat):
     return -0.5 * chi2 - 0.5 * prior - 0.5 * fl
 
 
+def observed_spectrum(r, lmax):
+    """C^o_l = 1/(2l+1) sum_{m=-l..l} |r_lm|^2 of a real field stored with
+    m >= 0 (the m < 0 terms are the m > 0 ones conjugated)."""
+    r = np.asarray(r, np.complex128).reshape(-1)
+    ls, ms = sht.ls_of(lmax), sht.ms_of(lmax)
+    w = np.where(ms == 0, 1.0, 2.0)
+    p = np.bincount(ls, weights=w * np.abs(r) ** 2, minlength=lmax + 1)
+    return p / (2.0 * np.arange(lmax + 1) + 1.0)
+
+
+def exact_harmonic_loglike(cl_obs, cl_theta, bl, nl, lmin=2):
+    """Eq. (exact_harm): ln P(theta | r) for full-sky temperature data with
+    uniform noise, up to a theta-independent constant:
+    sum_l -(2l+1)/2 [x_l - ln x_l], x_l = C^o_l / (b_l^2 C_l(theta) + N_l),
+    over l >= lmin."""
+    l = np.arange(len(cl_obs))
+    sel = l >= lmin
+    x = np.asarray(cl_obs)[sel] / (np.asarray(bl)[sel] ** 2 * np.asarray(cl_theta)[sel] + np.asarray(nl)[sel])
+    return float(np.sum(-(2.0 * l[sel] + 1.0) / 2.0 * (x - np.log(x))))
+
+
 def joint_acceptance(log_pi_new, log_pi_old, log_prior_new=0.0, log_prior_old=0.0):
     """A = min[1, pi(theta') P(theta') / (pi(theta) P(theta))] (Eq. acceptance-rate)."""
     return float(min(1.0, np.exp((log_pi_new + log_prior_new) - (log_pi_old + log_prior_old))))

@@ -645,6 +645,9 @@ __device__ __forceinline__ void gen_atiles_ana(const PairStart &q, const float4 
     S.b1[0] = ts.z;
     S.b2[0] = ts.w;
     const int kg = pin >> 3, krow = pin & 7;
+    // padded shared index of l0 + d: l0 - lbase is a multiple of 32 and d <= 31,
+    // so ta_cpad(l0 - lbase + d) = ta_cpad(l0 - lbase) + d
+    const int cb = ta_cpad(l0 - lbase);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         // rows 16 seg + 8 h .. + 7: core matrix (M group 2 seg + h, K group kg)
@@ -656,9 +659,9 @@ __device__ __forceinline__ void gen_atiles_ana(const PairStart &q, const float4 
                 const int d = 16 * h + 2 * i;
                 e[i] = o[i] = 0.f;
                 if (live) {
-                    stepx<float, 1, 0, INJ>(S, s_rec, s_s2c, ta_cpad(l0 + d - lbase), l0 + d);
+                    stepx<float, 1, 0, INJ>(S, s_rec, s_s2c, cb + d, l0 + d);
                     e[i] = S.a1[0];
-                    stepx<float, 1, 0, INJ>(S, s_rec, s_s2c, ta_cpad(l0 + d + 1 - lbase), l0 + d + 1);
+                    stepx<float, 1, 0, INJ>(S, s_rec, s_s2c, cb + d + 1, l0 + d + 1);
                     o[i] = S.a1[0];
                 }
             }
@@ -671,10 +674,10 @@ __device__ __forceinline__ void gen_atiles_ana(const PairStart &q, const float4 
                 const int d = 16 * h + 2 * i;
                 wE[i] = wO[i] = xE[i] = xO[i] = 0.f;
                 if (live) {
-                    stepx<float, 1, 2, INJ>(S, s_rec, s_s2c, ta_cpad(l0 + d - lbase), l0 + d);
+                    stepx<float, 1, 2, INJ>(S, s_rec, s_s2c, cb + d, l0 + d);
                     wE[i] = S.a1[0] + S.b1[0];
                     xE[i] = S.a1[0] - S.b1[0];
-                    stepx<float, 1, 2, INJ>(S, s_rec, s_s2c, ta_cpad(l0 + d + 1 - lbase), l0 + d + 1);
+                    stepx<float, 1, 2, INJ>(S, s_rec, s_s2c, cb + d + 1, l0 + d + 1);
                     wO[i] = S.a1[0] + S.b1[0];
                     xO[i] = S.a1[0] - S.b1[0];
                 }
