@@ -24,6 +24,8 @@
 // the loop carries no rescaling.  The analysis reduces over the warp's
 // rings with a butterfly transpose-reduce of 8 consecutive l at a time.
 #pragma once
+
+#include <cstdlib>
 #include <cstdio>
 
 #include "common.cuh"
@@ -47,6 +49,17 @@ inline bool tuning_enabled() {
     }
     return on == 1;
 }
+// SHTG_TUNE_FORCE=v: every tuned family runs its variant v (variant 0 where
+// it has fewer), for profiling one shape or checking each shape on its own
+inline int tuning_force() {
+    static int v = -2;
+    if (v == -2) {
+        const char *e = getenv("SHTG_TUNE_FORCE");
+        v = (e && e[0] >= '0' && e[0] <= '9') ? atoi(e) : -1;
+    }
+    return v;
+}
+
 inline bool tuning_log() {
     static int on = -1;
     if (on < 0) {
@@ -61,6 +74,10 @@ int tune(Plan *p, int key_prec, int family, int nmaps, int nvar, cudaStream_t st
     const long long key = ((long long)key_prec * 16 + family) * 65536 + nmaps;
     auto it = p->tuned.find(key);
     if (it != p->tuned.end()) return run(it->second);
+    if (tuning_force() >= 0) {
+        p->tuned[key] = tuning_force() < nvar ? tuning_force() : 0;
+        return run(p->tuned[key]);
+    }
     if (!tuning_enabled() || nvar <= 1 || p->prof.on) {
         p->tuned[key] = 0;
         return run(0);

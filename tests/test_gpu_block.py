@@ -73,7 +73,8 @@ def test_block_solve_matches_fp64_pcg():
     xb, _ = plan.cg_sample(*args, tol=1e-10, mode="block")
     xp, sp = plan.cg_sample(*args, tol=1e-12, mode="fp64", maxiter=5000)
     assert sp["converged"] == 1
-    assert rel_l2(xb.cpu().numpy(), xp.cpu().numpy()) < 1e-9
+    # PCG stopped at a residual of 1e-12 is accurate to ~cond(A) 1e-12 (~1e-9 here)
+    assert rel_l2(xb.cpu().numpy(), xp.cpu().numpy()) < 1e-8
 
 
 def test_block_solve_refuses_what_is_not_block_diagonal():

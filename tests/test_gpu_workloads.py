@@ -2,11 +2,11 @@
 sizes, through the C ABI, against the FP64 oracle.
 
 - Masked temperature (N_side 256, l_max 512, hits-weighted noise, |b| < 20 deg
-  plus 50 holes): plain FP64 PCG and both mixed forms to 1e-6; the
-  oracle-evaluated residual of each GPU solution is <= 1.05e-6 and its
-  relative L2 distance to the oracle's solution converged to 1e-11 (stored
-  by tests/golden/make_masked_solution.py, which calls only the oracle) is
-  <= 1e-5.
+  plus 50 holes): plain FP64 PCG and both mixed forms to 1e-6 and to 1e-9;
+  the oracle-evaluated residual of each GPU solution is <= 1.05 tol, and at
+  1e-9 its relative L2 distance to the oracle's solution converged to 1e-11
+  (stored by tests/golden/make_masked_solution.py, which calls only the
+  oracle) is <= 1e-5.
 - Log-posterior (N_side 512, l_max 1024, 50 bins of width 20): value and
   gradients (FP32 transforms) against the oracle's.
 - Chains: the N_side 256 geometries of the mixed-geometry recipe (l_max 512
@@ -55,19 +55,27 @@ def masked_plan():
 
 @pytest.mark.parametrize("mode", ["fp64", "mixed", "mixed_tc"])
 def test_masked_full_size(mode, masked, masked_plan):
+    """PCG stopped at 1e-6: the oracle-evaluated residual is <= 1.05e-6; the
+    solution is then ~3e-3 from the exact one (the system's effective
+    condition number is ~3e3, in every form).  Stopped at 1e-9, the mixed
+    forms after refinement reproduce the oracle's solution (converged to
+    1e-11) to <= 1e-5, like the FP64 form: mixed precision does not limit
+    the accuracy the refinement reaches."""
     p, g, d, prob, b, xref = masked
-    x, st = masked_plan.cg_sample(p.cl, p.bl, _cuda(p.ninv, torch.float64), _cuda(d[None, None], torch.float64),
-                                  _cuda(p.w1[None], torch.complex128), _cuda(p.w2[None], torch.float64),
-                                  tol=1e-6, mode=mode, maxiter=8000, check_every=8)
-    assert st["converged"] == 1, st
-    xh = x.cpu().numpy()[0]
-    res = osol.true_residual(prob, xh, b)
-    err = rel_l2(xh[0], xref)
-    print(f"masked N_side 256 / l_max 512 {mode}: {st['iterations']} iterations, "
-          f"{st['fp64_matvecs']} FP64 operator applications, oracle residual {res:.3e}, "
-          f"error vs oracle solution {err:.3e}")
-    assert res <= 1.05e-6, (res, st)
-    assert err <= 1e-5, err
+    args = (p.cl, p.bl, _cuda(p.ninv, torch.float64), _cuda(d[None, None], torch.float64),
+            _cuda(p.w1[None], torch.complex128), _cuda(p.w2[None], torch.float64))
+    for tol in (1e-6, 1e-9):
+        x, st = masked_plan.cg_sample(*args, tol=tol, mode=mode, maxiter=12000, check_every=8)
+        assert st["converged"] == 1, st
+        xh = x.cpu().numpy()[0]
+        res = osol.true_residual(prob, xh, b)
+        err = rel_l2(xh[0], xref)
+        print(f"masked N_side 256 / l_max 512 {mode} tol {tol:.0e}: {st['iterations']} iterations, "
+              f"{st['fp64_matvecs']} FP64 operator applications, oracle residual {res:.3e}, "
+              f"error vs oracle solution {err:.3e}")
+        assert res <= 1.05 * tol, (res, st)
+        if tol < 1e-6:
+            assert err <= 1e-5, err
 
 
 def test_logposterior_full_size():
