@@ -94,6 +94,9 @@ extern "C" {
                                         realizations share one C_l scale; the plan needs
                                         SHTG_BLOCK_SOLVER; SHTG_ERR_ARG when a condition fails */
 
+#define SHTG_PRECOND_NONE 0          /* shtg_cg_opts.precond */
+#define SHTG_PRECOND_DIAG 1
+#define SHTG_PRECOND_LOWL 2
 #define SHTG_ARITH_DEFAULT 0         /* shtg_cg_opts.fp64_arith */
 #define SHTG_ARITH_FP64 1            /* native FP64 multiply-adds */
 #define SHTG_ARITH_DF64 2            /* Legendre sums in double-FP32 (hi + lo float pairs, ~2^-47
@@ -231,7 +234,9 @@ typedef struct {
     double tol;         /* stop when ||b - A x|| / ||b|| <= tol for every realization */
     int maxiter;        /* PCG iterations (FP64 mode) or FP32 iterations (mixed) */
     int mode;           /* SHTG_CG_FP64, SHTG_CG_MIXED, SHTG_CG_MIXED_TC or SHTG_CG_BLOCK */
-    int precond;        /* 1: diagonal preconditioner of Sect. 4 (default); 0: none */
+    int precond;        /* SHTG_PRECOND_DIAG (1): diagonal preconditioner of Sect. 4 (default);
+                           SHTG_PRECOND_NONE (0); SHTG_PRECOND_LOWL (2): two-level, the exact
+                           inverse of the operator on l <= lowl_lmax plus the diagonal above */
     double reliable_delta; /* mixed mode: an FP64 residual replacement happens when the FP32
                               residual has dropped by this factor since the last one (default 1e-2) */
     int fp64_arith;     /* arithmetic of the FP64-accurate steps (RHS, residual replacements,
@@ -240,6 +245,8 @@ typedef struct {
                            SHTG_ARITH_DF64 */
     int check_every;    /* iterations per CUDA graph launch between host convergence checks */
     int flags;          /* SHTG_HOST_INPUTS: ninv, d, w1, w2 and alm_out are host memory */
+    int lowl_lmax;      /* SHTG_PRECOND_LOWL: l_c, the largest multipole of the dense block
+                           (0: min(lmax, 32); at most min(lmax, 48)) */
 } shtg_cg_opts;
 
 typedef struct {
@@ -293,6 +300,25 @@ int shtg_cg_sample_chains(int ngroups, shtg_plan *const *plans, const shtg_probl
  * cl, bl and ninv (d, w1, w2 unused).  Held multipoles pass through (y = x). */
 int shtg_apply_operator(shtg_plan *plan, const shtg_problem *prob, const double *x, double *y,
                         void *stream);
+
+/* The dense low-multipole block of SHTG_PRECOND_LOWL (the paper's Sect. 4
+ * asks for preconditioners beyond the diagonal one; this is the coarse level
+ * of a two-level one).  In the real parametrization a_lm = u + i v (no v at
+ * m = 0) with the metric weight w = 1 for m = 0, 2 otherwise, the operator A
+ * of Eq. (mapmakingeq) restricted to the active multipoles l <= l_c is
+ * W^-1 H with the symmetric
+ *   H_ij = b_l(i) b_l(j) sum_p N^-1_p phi_i(p) phi_j(p)
+ *          + w_i [S^-1 / cl_scale[0]]_{comp(i) comp(j)} (same l, m, part),
+ * phi_i the pixel field of a unit parameter (App. A's ring-pair sums with
+ * each ring's Fourier coefficients of N^-1).  Writes H (HOST, [n][n] row
+ * major; capacity (ncomp (l_c+1)^2)^2 doubles), params (HOST, [n][4] ints
+ * l, m, component 0 T / 1 E / 2 B, part 0 u / 1 v; capacity 4 ncomp
+ * (l_c+1)^2, may be NULL) and n.  Uses cl, bl, ninv (d, w1, w2 unused);
+ * l_c = 0 is the default.  Inactive multipoles (singular C_l block) are left
+ * out.  Synchronizes the stream; the workspace stays with the plan.
+ * SHTG_ERR_NOT_SPD if the block is not positive definite. */
+int shtg_lowl_block(shtg_plan *plan, const shtg_problem *prob, int lowl_lmax, double *H, int *params, int *n,
+                    void *stream);
 
 /* ------------------------------------------- joint (C_l, a) move (Sect. 2.2.2) */
 /* The deterministic rescaling of the fluctuation term,

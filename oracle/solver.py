@@ -158,15 +158,20 @@ def apply_block_inverse(M, r):
 def pcg(prob: Problem, b, tol: float, maxiter: int = 1000, precond=True, x0=None):
     """Plain preconditioned conjugate gradients in FP64.
 
-    Stops when ||b - A x|| / ||b|| <= tol (recursively updated residual,
-    checked once more with a fresh A x at exit).  Returns (x, iterations,
-    relative residual history)."""
+    precond: True (the diagonal preconditioner of Sect. 4), False (none) or a
+    callable r -> z.  Stops when ||b - A x|| / ||b|| <= tol (recursively
+    updated residual).  Returns (x, iterations, relative residual history)."""
     b = np.asarray(b, np.complex128).reshape(prob.ncomp, -1)
-    M = prob.precond_diag() if precond else None
+    if callable(precond):
+        apply_m = precond
+    elif precond:
+        M = prob.precond_diag()
+        apply_m = lambda r: apply_block_inverse(M, r)  # noqa: E731
+    else:
+        apply_m = lambda r: r.copy()  # noqa: E731
     x = np.zeros_like(b) if x0 is None else np.array(x0, np.complex128).reshape(b.shape)
     r = b - prob.matvec(x) if x0 is not None else b.copy()
-    z = apply_block_inverse(M, r) if precond else r.copy()
-    z = _zero_im_m0(z, prob.lmax)
+    z = _zero_im_m0(apply_m(r), prob.lmax)
     p = z.copy()
     bn = np.sqrt(prob.dot(b, b))
     rz = prob.dot(r, z)
@@ -177,14 +182,84 @@ def pcg(prob: Problem, b, tol: float, maxiter: int = 1000, precond=True, x0=None
         alpha = rz / prob.dot(p, q)
         x = x + alpha * p
         r = r - alpha * q
-        z = apply_block_inverse(M, r) if precond else r.copy()
-        z = _zero_im_m0(z, prob.lmax)
+        z = _zero_im_m0(apply_m(r), prob.lmax)
         rz_new = prob.dot(r, z)
         p = z + (rz_new / rz) * p
         rz = rz_new
         it += 1
         hist.append(np.sqrt(prob.dot(r, r)) / bn)
     return x, it, np.array(hist)
+
+
+# ----------------------------------------------------------------------------
+# Two-level preconditioner: exact inverse on the low multipoles (Sect. 4 asks
+# for preconditioners beyond the diagonal one)
+# ----------------------------------------------------------------------------
+def low_parameters(prob: Problem, lc: int):
+    """Real parameters (l, m, comp, part) of the active multipoles l <= lc,
+    a_lm = u + i v (part 0 = u, 1 = v; no v at m = 0), ordered by component,
+    then l, m, part."""
+    out = []
+    for c in range(prob.ncomp):
+        for l in range(lc + 1):
+            if not prob.active[l]:
+                continue
+            for m in range(l + 1):
+                for w in range(1 if m == 0 else 2):
+                    out.append((l, m, c, w))
+    return out
+
+
+def low_block(prob: Problem, lc: int):
+    """H = W A on the low parameters, one column per operator application:
+    column j is A applied to the unit parameter e_j (a_lm = 1 or i), read
+    back as real parts, times the metric weight w_i (1 for m = 0, else 2) of
+    the row.  With the metric <a, c> = sum w (u u' + v v') of the inner
+    products, H is symmetric.  Returns (parameters, H)."""
+    L = prob.lmax
+    params = low_parameters(prob, lc)
+    n = len(params)
+    nalm = (L + 1) * (L + 2) // 2
+    idx = [m * (2 * L + 1 - m) // 2 + l for (l, m, _, _) in params]
+    H = np.zeros((n, n))
+    for j, (l, m, c, w) in enumerate(params):
+        e = np.zeros((prob.ncomp, nalm), np.complex128)
+        e[c, idx[j]] = 1.0 if w == 0 else 1j
+        y = prob.matvec(e)
+        for i, (l2, m2, c2, w2) in enumerate(params):
+            v = y[c2, idx[i]]
+            H[i, j] = (1.0 if m2 == 0 else 2.0) * (v.real if w2 == 0 else v.imag)
+    return params, H
+
+
+def two_level_precond(prob: Problem, lc: int):
+    """z = M^-1 r with M^-1 the diagonal preconditioner's inverse outside
+    the low block and A^-1 = H^-1 W on it (block Jacobi with one dense
+    block).  Returns the callable for :func:`pcg`."""
+    M = prob.precond_diag()
+    params, H = low_block(prob, lc)
+    L = prob.lmax
+    comp = np.array([c for (_, _, c, _) in params], int)
+    idx = np.array([m * (2 * L + 1 - m) // 2 + l for (l, m, _, _) in params], int)
+    part = np.array([w for (_, _, _, w) in params], int)
+    wgt = np.array([1.0 if m == 0 else 2.0 for (_, m, _, _) in params])
+
+    def apply(r):
+        z = apply_block_inverse(M, r)
+        if not params:
+            return z
+        rv = r[comp, idx]
+        g = wgt * np.where(part == 0, rv.real, rv.imag)
+        zl = np.linalg.solve(H, g)
+        z = np.array(z, np.complex128, copy=True)
+        for k in range(len(params)):
+            if part[k] == 0:
+                z[comp[k], idx[k]] = zl[k] + 1j * z[comp[k], idx[k]].imag
+            else:
+                z[comp[k], idx[k]] = z[comp[k], idx[k]].real + 1j * zl[k]
+        return z
+
+    return apply
 
 
 # ----------------------------------------------------------------------------

@@ -42,6 +42,17 @@ def _arith(fp64_arith: str) -> int:
     return _ARITH[fp64_arith]
 
 
+_PRECOND = {"none": N.PRECOND_NONE, "diag": N.PRECOND_DIAG, "lowl": N.PRECOND_LOWL}
+
+
+def _precond(precond) -> int:
+    if precond is True or precond is False:
+        return N.PRECOND_DIAG if precond else N.PRECOND_NONE
+    if precond not in _PRECOND:
+        raise ValueError(f"precond must be True, False or one of {sorted(_PRECOND)}")
+    return _PRECOND[precond]
+
+
 def _stream():
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
@@ -186,10 +197,10 @@ class Plan:
         return pr
 
     def cg_sample(self, cl, bl, ninv, d, w1, w2, tol: float = 1e-6, mode: str = "mixed",
-                  maxiter: int = 4000, precond: bool = True, reliable_delta: float = 1e-2,
+                  maxiter: int = 4000, precond=True, reliable_delta: float = 1e-2,
                   check_every: int = 4, out=None,
                   allow_not_converged: bool = False, profile: bool = False, graphs: bool = True,
-                  cl_scale=None, fp64_arith: str = "default", split: bool = False):
+                  cl_scale=None, fp64_arith: str = "default", split: bool = False, lowl_lmax: int = 0):
         """Constrained realization(s) of Eq. (mapmakingeq).
 
         mode: "fp64" (plain FP64 PCG), "mixed" / "mixed_tc" (FP32 PCG with
@@ -199,6 +210,11 @@ class Plan:
         ring; the plan needs block_solver=True).
 
         cl_scale: optional [nbatch] amplitudes; realization b uses cl_scale[b] x cl.
+
+        precond: True / "diag" (the diagonal preconditioner of Sect. 4),
+        False / "none", or "lowl" (two-level: the exact inverse of the
+        operator on the multipoles l <= lowl_lmax, 0 = min(lmax, 32), plus
+        the diagonal above; built with the first realization's cl_scale).
 
         split: solve the mean field (Eq. mean-field-map) and the fluctuation
         (Eq. fluc-map) as separate systems of one batch; the result is then
@@ -239,7 +255,8 @@ class Plan:
         if mode not in modes:
             raise ValueError(f"mode must be one of {sorted(modes)}")
         o.mode = modes[mode]
-        o.precond = 1 if precond else 0
+        o.precond = _precond(precond)
+        o.lowl_lmax = int(lowl_lmax)
         o.reliable_delta, o.fp64_arith = float(reliable_delta), _arith(fp64_arith)
         o.check_every = int(check_every)
         o.flags = ((N.HOST_INPUTS if host else 0) | (N.PROFILE if profile else 0) |
@@ -281,6 +298,22 @@ class Plan:
         N.check(self._lib.shtg_joint_log_target(self._h, C.byref(pr), prec, _ptr(a_hat), _ptr(f_hat),
                                                 _ptr(lp), _stream()))
         return lp
+
+    def lowl_block(self, cl, bl, ninv, ncomp: int = 1, lowl_lmax: int = 0, cl_scale=None):
+        """The dense low-multipole block H of the two-level preconditioner
+        (shtg_lowl_block): returns (H [n, n] float64, params [n, 4] int32 of
+        (l, m, component, part)) for the active multipoles l <= l_c."""
+        _need_cuda(ninv, "ninv")
+        lc = int(lowl_lmax) if lowl_lmax > 0 else min(self.lmax, 32)
+        cap = ncomp * (lc + 1) ** 2
+        H = np.zeros(cap * cap)
+        par = np.zeros(4 * cap, np.int32)
+        n = C.c_int(0)
+        pr = self._problem(cl, bl, ninv, nbatch=1, ncomp=ncomp, cl_scale=cl_scale)
+        N.check(self._lib.shtg_lowl_block(self._h, C.byref(pr), int(lowl_lmax), _ptr(H), _ptr(par),
+                                          C.byref(n), _stream()))
+        k = n.value
+        return H[:k * k].reshape(k, k).copy(), par[:4 * k].reshape(k, 4).copy()
 
     def apply_operator(self, cl, bl, ninv, x: torch.Tensor, cl_scale=None) -> torch.Tensor:
         """y = (S^-1 + B Y^T N^-1 Y B) x for x [nbatch, ncomp, nalm] complex128 (CUDA)."""
@@ -338,8 +371,9 @@ def fma_peak(precision: str = "fp32"):
 
 
 def chains_sample(groups, tol: float = 1e-6, mode: str = "mixed_tc", maxiter: int = 4000,
-                  precond: bool = True, reliable_delta: float = 1e-2, check_every: int = 4,
-                  allow_not_converged: bool = False, graphs: bool = True, fp64_arith: str = "default"):
+                  precond=True, reliable_delta: float = 1e-2, check_every: int = 4,
+                  allow_not_converged: bool = False, graphs: bool = True, fp64_arith: str = "default",
+                  lowl_lmax: int = 0):
     """Constrained realizations of many chains of uneven geometry in one call.
 
     groups: list of dicts, one per geometry, with keys plan, cl, bl, ninv, d,
@@ -374,7 +408,8 @@ def chains_sample(groups, tol: float = 1e-6, mode: str = "mixed_tc", maxiter: in
     if mode not in modes:
         raise ValueError(f"mode must be one of {sorted(modes)}")
     o.mode = modes[mode]
-    o.precond = 1 if precond else 0
+    o.precond = _precond(precond)
+    o.lowl_lmax = int(lowl_lmax)
     o.reliable_delta, o.fp64_arith = float(reliable_delta), _arith(fp64_arith)
     o.check_every = int(check_every)
     o.flags = 0 if graphs else N.NO_GRAPHS

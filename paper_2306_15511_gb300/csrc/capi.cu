@@ -377,6 +377,15 @@ int shtg_apply_operator(shtg_plan *plan, const shtg_problem *prob, const double 
     return apply_operator(reinterpret_cast<Plan *>(plan), prob, x, y, (cudaStream_t)stream);
 }
 
+int shtg_lowl_block(shtg_plan *plan, const shtg_problem *prob, int lowl_lmax, double *H, int *params, int *n,
+                    void *stream) {
+    if (!plan || !prob || !H || !n) {
+        set_error("null argument");
+        return SHTG_ERR_ARG;
+    }
+    return lowl_block(reinterpret_cast<Plan *>(plan), prob, lowl_lmax, H, params, n, (cudaStream_t)stream);
+}
+
 int shtg_logpost_grad(shtg_plan *plan, const double *cl, const double *bl, const float *alm,
                       const float *d, const float *ninv, int nbins, const int *bin_lo,
                       const int *bin_hi, int flags, double *logp, float *grad_alm,

@@ -35,6 +35,21 @@ int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
     } while (0)
 
 // ----------------------------------------------------------- real types
+// Allow a kernel the device's whole opt-in shared memory per block.  Every
+// call sets the same value, so host threads that launch the kernel for
+// plans of different sizes at once (chains) cannot lower the limit another
+// thread's launch needs; occupancy follows the launch's own request.
+template <typename K> inline cudaError_t allow_max_smem(K kern) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kern);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+    return e;
+}
+
 template <typename T> struct VT;
 template <> struct VT<float> { typedef float2 C; };
 template <> struct VT<double> { typedef double2 C; };
@@ -84,6 +99,32 @@ struct Prof {
     int n = 0;                     // recorded (begin, end) pairs
     int open_cls = -1;
     long long launches = 0;        // kernels launched by the library (always counted)
+};
+
+// two-level preconditioner (lowl.cu): workspace, the kept Gram matrix of the
+// low multipoles and the inverse of the current low block
+#define SHTG_LOWL_LCMAX 48
+#define SHTG_LOWL_LC_DEFAULT 32
+struct LowL {
+    double2 *W = nullptr;          // [ch][ring][2 l_c + 1] Fourier coefficients of N^-1 per ring
+    double *lam = nullptr;         // [lo(l, m)][pair] lambda_lm on the north ring
+    double *lw = nullptr, *lx = nullptr;   // spin-2 profiles, same layout
+    double *G = nullptr;           // [nfull][nfull] sum_p N^-1 phi_i phi_j (no beam, no prior)
+    double *H = nullptr, *S = nullptr;     // ping-pong buffers of the sweep
+    double *h64 = nullptr;         // H^-1 (one of H, S)
+    float *h32 = nullptr;          // H^-1 in FP32
+    int4 *par = nullptr;           // [nfull] (l, m, comp, part)
+    int *sel = nullptr, *emap = nullptr;   // [n] active parameter -> full index / vector element
+    float *wv = nullptr;           // [n] metric weight (1 for m = 0, else 2)
+    double *part = nullptr;        // [max_batch][32] <r, z> corrections
+    int *flag = nullptr, *shift = nullptr;
+    double *ninv = nullptr;        // N^-1 the kept Gram matrix was built from
+    int64_t bytes = 0;
+    int cap_lc = -1, cap_nc = 0;   // workspace size
+    int n = 0, lc = 0, nc = 0;     // current active block
+    int gram_lc = -1, gram_nc = 0;
+    bool gram_ok = false;
+    std::vector<int4> params;      // host copy of the active parameters
 };
 
 struct Plan {
@@ -204,6 +245,7 @@ struct Plan {
     int64_t *d_blkoff = nullptr;
     int *d_blkflag = nullptr;
     int64_t blk_cap = 0, lam_cap = 0;
+    LowL lowl;
     double *d_stage = nullptr;     // [nmaps_max][npix] staging for host inputs
     double *h_pinned = nullptr;    // pinned host scalars
 };
@@ -220,6 +262,16 @@ int joint_log_target(Plan *p, const shtg_problem *pr, int precision, const doubl
 // block.cu: per-m dense block solve for azimuthally symmetric noise (App. A)
 int block_workspace(Plan *p);
 int block_solve(Plan *p, const double2 *B, double2 *X, int nb, double isc, cudaStream_t st);
+// lowl.cu: two-level preconditioner.  lowl_setup builds H^-1 for l_c
+// (<= 0: the default) and nc components with 1 / (C_l scale) = isc (copying
+// H to h_host first when given); lowl_apply replaces z on the low block of nb
+// systems (r, z viewed as reals, per complex entries per system) and adds
+// the change of <r, z> to the rz partials.
+int lowl_setup(Plan *p, int lc, int nc, double isc, cudaStream_t st, double *h_host = nullptr);
+template <typename T>
+int lowl_apply(Plan *p, const T *r, T *z, int nb, int64_t per, double *part, cudaStream_t st);
+void lowl_free(Plan *p);
+int lowl_block(Plan *p, const shtg_problem *pr, int lc, double *H, int *params, int *n, cudaStream_t st);
 int logpost_grad(Plan *p, const double *cl, const double *bl, const float *alm, const float *d,
                  const float *ninv, int nbins, const int *blo, const int *bhi, int flags,
                  double *logp, float *grad, double *gcl, cudaStream_t st);

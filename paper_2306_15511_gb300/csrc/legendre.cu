@@ -91,10 +91,10 @@ int leg_diag(Plan *p, int spin, const float *wpair, float *out, cudaStream_t st)
     dim3 grid(gx, p->lmax + 1, 1);
     prof_begin(p, K_DIAG, st);
     if (spin == 2) {
-        if (smem > 48 * 1024) SHTG_CUDA(cudaFuncSetAttribute(k_leg_diag<NR, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (smem > 48 * 1024) SHTG_CUDA(allow_max_smem(k_leg_diag<NR, 2>));
         k_leg_diag<NR, 2><<<grid, LEG_THREADS, smem, st>>>(a);
     } else {
-        if (smem > 48 * 1024) SHTG_CUDA(cudaFuncSetAttribute(k_leg_diag<NR, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        if (smem > 48 * 1024) SHTG_CUDA(allow_max_smem(k_leg_diag<NR, 0>));
         k_leg_diag<NR, 0><<<grid, LEG_THREADS, smem, st>>>(a);
     }
     prof_end(p, st);

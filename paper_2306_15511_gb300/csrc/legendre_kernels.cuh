@@ -690,8 +690,7 @@ int launch_analysis_v(Plan *p, const typename VT<T>::C *G, int nmaps, const T *b
     }
     const size_t smem = sizeof(T) * (size_t)(p->lmax + 1) * NM * NO;
     auto kern = k_leg_analysis<T, NR, NM, SPIN>;
-    if (smem > 48 * 1024)
-        SHTG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 48 * 1024) SHTG_CUDA(allow_max_smem(kern));
     dim3 grid(gx, p->lmax + 1, (nmaps + NM - 1) / NM);
     prof_begin(p, sizeof(T) == 8 ? K_LEG_ANA64 : K_LEG_ANA32, st);
     kern<<<grid, LEG_THREADS, smem, st>>>(a);

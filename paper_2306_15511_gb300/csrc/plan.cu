@@ -748,6 +748,11 @@ int plan_build(Plan *p) {
     }
     SHTG_TRY(dalloc(p, &p->d_flag, 16));
     SHTG_CUDA(cudaMemset(p->d_flag, 0, 16 * sizeof(int)));
+    // solver scalars and partials start defined (a fresh allocation may hold
+    // what an earlier plan left there)
+    SHTG_CUDA(cudaMemset(p->d_scal, 0, sizeof(double) * 16 * (size_t)p->max_batch));
+    SHTG_CUDA(cudaMemset(p->d_part, 0,
+                         sizeof(double) * (4 * (size_t)p->max_batch * SHTG_RED_BLOCKS + 4 * (size_t)p->max_batch + 64)));
     SHTG_TRY(dalloc(p, &p->d_stage, nmp));
     SHTG_CUDA(cudaMallocHost((void **)&p->h_pinned, 4096 * sizeof(double)));
     p->prof.ev.resize(16384);
@@ -758,6 +763,7 @@ int plan_build(Plan *p) {
 }
 
 void plan_free(Plan *p) {
+    lowl_free(p);
     void *ptrs[] = {p->d_nphi, p->d_ofs, p->d_wring, p->d_u64, p->d_u32, p->d_x64, p->d_is2_64,
                     p->d_x32, p->d_is2_32, p->d_lofidx, p->d_mofidx, p->d_rec64, p->d_rec32,
                     p->d_ls64, p->d_ls32, p->d_st64, p->d_st32, p->d_s2c64, p->d_s2c32,

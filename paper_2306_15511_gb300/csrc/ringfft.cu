@@ -790,7 +790,7 @@ template <> RingArgs<double> ring_args<double>(Plan *p) {
 template <typename T, int MODE, int NT, int FIX>
 static int launch_ring_nt(RingArgs<T> a, int ctas, size_t smem, cudaStream_t st) {
     auto kern = k_ring<T, MODE, NT, FIX>;
-    if (smem > 48 * 1024) SHTG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > 48 * 1024) SHTG_CUDA(allow_max_smem(kern));
     // The maps of a ring pair are split over grid.y when the pairs alone give
     // fewer than four waves of resident CTAs (a CTA still handles at least
     // two maps, so its chirp and twiddle staging stay amortized)

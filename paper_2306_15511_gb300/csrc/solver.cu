@@ -474,7 +474,11 @@ __global__ void k_scal_reliable(const double *__restrict__ part, double *__restr
     s[S_BB] = 1.0;                       // the FP32 residual is normalized to 1
     s[S_TOL2] = tol2[b];
     s[S_ACTIVE] = (tol2[b] >= 0.0 && rr > 0.0) ? 1.0 : 0.0;
-    s[S_BAD] = (isfinite(rr) && isfinite(rz)) ? s[S_BAD] : 1.0;
+    // set, not accumulated: the first replacement of a solve runs on scalar
+    // slots that hold whatever an earlier call (or a fresh allocation) left,
+    // and a bad FP32 stage already ended the solve at its host check
+    s[S_BAD] = (isfinite(rr) && isfinite(rz)) ? 0.0 : 1.0;
+    s[S_ITERS] = 0.0;
     s[S_ALPHA] = s[S_BETA] = 0.0;
 }
 
@@ -689,6 +693,7 @@ struct Solve {
     int tc = 0;      // FP32 operator: Legendre sums on the tensor cores
     int df = 0;      // FP64 operator: Legendre sums in double-FP32 arithmetic
     int graphs = 1;  // replay captured iterations (off while profiling)
+    int lowl = 0;    // two-level preconditioner: exact inverse on the low multipoles
     int64_t nalm, per, nvec;
     dim3 vgrid;   // (blocks, nb)
     dim3 rgrid;   // (RB, nb)
@@ -785,6 +790,9 @@ static int pcg_iteration(Solve &s, typename HT<T>::C *x, typename HT<T>::C *r, t
     k_scal_alpha<<<1, 1024, 0, s.st>>>(p->d_part, p->d_scal, s.nb);
     k_update<T, false><<<s.rgrid, RT, 0, s.st>>>(x, r, z, pv, q, minv, s.nc, s.nalm, p->d_mofidx,
                                                  p->d_scal, p->d_part);
+    if (s.lowl)
+        SHTG_TRY(lowl_apply<T>(p, reinterpret_cast<const T *>(r), reinterpret_cast<T *>(z), s.nb, s.per, p->d_part,
+                               s.st));
     k_scal_beta<<<1, 1024, 0, s.st>>>(p->d_part, p->d_scal, s.nb);
     k_pupdate<C><<<dim3(grid_1d(s.per).x, s.nb), RT, 0, s.st>>>(pv, z, s.nc, s.nalm, p->d_scal);
     prof_end(p, s.st, 4);
@@ -852,6 +860,9 @@ static int pcg(Solve &s, const typename HT<T>::C *b, typename HT<T>::C *x, doubl
     k_update<T, true><<<s.rgrid, RT, 0, s.st>>>(nullptr, r, z, nullptr, nullptr, minv, s.nc, s.nalm,
                                                 p->d_mofidx, p->d_scal, p->d_part);
     SHTG_CHECK_LAUNCH("k_update init");
+    if (s.lowl)
+        SHTG_TRY(lowl_apply<T>(p, reinterpret_cast<const T *>(r), reinterpret_cast<T *>(z), s.nb, s.per, p->d_part,
+                               s.st));
     k_scal_init<<<1, 1024, 0, s.st>>>(p->d_part, p->d_scal, s.nb, tol * tol);
     p->prof.launches += 2;
     SHTG_CHECK_LAUNCH("k_scal_init");
@@ -1126,6 +1137,9 @@ static int mixed_solve(Solve &s, const shtg_cg_opts &opt, const std::vector<doub
         else k_scale_vec<<<s.vgrid, RT, 0, st>>>(p32, s.per, d_sc + 2 * nb);
         k_update<float, true><<<s.rgrid, RT, 0, st>>>(nullptr, r32, z32, nullptr, nullptr, minv, s.nc,
                                                      s.nalm, p->d_mofidx, p->d_scal, p->d_part);
+        if (s.lowl)
+            SHTG_TRY(lowl_apply<float>(p, reinterpret_cast<const float *>(r32), reinterpret_cast<float *>(z32), nb,
+                                       s.per, p->d_part, st));
         k_scal_reliable<<<1, 1024, 0, st>>>(p->d_part, p->d_scal, nb, d_sc + nb);
         p->prof.launches += first ? 3 : 4;
         SHTG_CHECK_LAUNCH("reliable update");
@@ -1189,7 +1203,7 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
         opt.tol = 1e-6;
         opt.maxiter = 1000;
         opt.mode = SHTG_CG_MIXED;
-        opt.precond = 1;
+        opt.precond = SHTG_PRECOND_DIAG;
     }
     if (!(opt.tol > 0)) opt.tol = 1e-6;
     if (opt.maxiter <= 0) opt.maxiter = 1000;
@@ -1223,6 +1237,10 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
                     set_error("SHTG_CG_BLOCK: the realizations must share one C_l scale");
                     return SHTG_ERR_ARG;
                 }
+    }
+    if (opt.precond < SHTG_PRECOND_NONE || opt.precond > SHTG_PRECOND_LOWL) {
+        set_error("precond must be SHTG_PRECOND_NONE, SHTG_PRECOND_DIAG or SHTG_PRECOND_LOWL");
+        return SHTG_ERR_ARG;
     }
     if (opt.fp64_arith != SHTG_ARITH_DEFAULT && opt.fp64_arith != SHTG_ARITH_FP64 &&
         opt.fp64_arith != SHTG_ARITH_DF64) {
@@ -1258,6 +1276,14 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
         s.graphs = !(opt.flags & SHTG_NO_GRAPHS) && !(e && e[0] == '0');
     }
     SHTG_TRY(setup_operator(p, pr, host, opt.mode == SHTG_CG_BLOCK ? 0 : opt.precond, st, nb));
+    if (opt.precond == SHTG_PRECOND_LOWL && opt.mode != SHTG_CG_BLOCK) {
+        // one low block for every system, built with the first realization's
+        // C_l scale (for the others it is still a symmetric positive definite
+        // preconditioner, only not the exact block inverse)
+        SHTG_TRY(lowl_setup(p, opt.lowl_lmax, nc, pr->cl_scale ? 1.0 / pr->cl_scale[0] : 1.0, st));
+        s.lowl = 1;
+    }
+    const double ts = now_ms();
     double2 *B = p->v64[0], *X = p->v64[1], *R = p->v64[2], *Tt = p->v64[6];
     // ---- RHS: B Y^T (N^-1 d + N^-1/2 w2) + S^-1/2 w1 in FP64; split: the
     // mean field's B Y^T N^-1 d (Eq. mean-field-map) for systems [0, nr) and
@@ -1309,8 +1335,8 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
             return SHTG_ERR_NONFINITE;
         }
     const double t1 = now_ms();
-    stt.ms_setup = 0;
-    stt.ms_rhs = t1 - t0;
+    stt.ms_setup = ts - t0;
+    stt.ms_rhs = t1 - ts;
     int rc = SHTG_OK;
     std::vector<double> rr;
     if (opt.mode == SHTG_CG_BLOCK) {
@@ -1370,6 +1396,22 @@ int apply_operator(Plan *p, const shtg_problem *pr, const double *x, double *y, 
     SHTG_TRY(setup_operator(p, pr, 0, 0, st));
     Solve s = make_solve(p, pr->nbatch, pr->ncomp, st);
     return matvec<double>(s, reinterpret_cast<const double2 *>(x), reinterpret_cast<double2 *>(y));
+}
+
+int lowl_block(Plan *p, const shtg_problem *pr, int lc, double *H, int *params, int *n, cudaStream_t st) {
+    SHTG_TRY(check_problem(p, pr));
+    SHTG_TRY(setup_operator(p, pr, 0, 1, st));
+    SHTG_TRY(lowl_setup(p, lc, pr->ncomp, pr->cl_scale ? 1.0 / pr->cl_scale[0] : 1.0, st, H));
+    const LowL &q = p->lowl;
+    *n = q.n;
+    if (params)
+        for (int i = 0; i < q.n; ++i) {
+            params[4 * i + 0] = q.params[i].x;
+            params[4 * i + 1] = q.params[i].y;
+            params[4 * i + 2] = q.params[i].z;
+            params[4 * i + 3] = q.params[i].w;
+        }
+    return SHTG_OK;
 }
 
 int logpost_grad(Plan *p, const double *cl, const double *bl, const float *alm, const float *d,

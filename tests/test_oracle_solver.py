@@ -581,3 +581,109 @@ def test_joint_move_samples_the_exact_marginal_posterior():
     chain = np.array(chain[400:])
     assert abs(chain.mean() - mean) < 0.2 * std
     assert abs(chain.std() / std - 1.0) < 0.2
+
+
+# --------------------------------------------- two-level preconditioner
+def test_low_block_matches_dense_bruteforce():
+    """The low-l block read off the operator column by column equals
+    W S^-1 + B Yd^T N^-1 Yd B restricted to l <= l_c, with Yd the real
+    spherical harmonics from scipy on the pixel centres (independent of the
+    oracle's transforms)."""
+    nside, L, lc = 4, 10, 5
+    rng = np.random.default_rng(21)
+    g = sht.healpix(nside)
+    cl = C.cl_flat(L)
+    bl = C.gauss_beam(L, 20 * C.DEG)
+    ninv = rng.uniform(0.5, 2.0, g.npix) * (rng.uniform(size=g.npix) > 0.3)
+    prob = solver.Problem(g, L, cl, bl, ninv)
+    params, H = solver.low_block(prob, lc)
+    assert [p[0] for p in params] == sorted(p[0] for p in params)
+    assert all(2 <= l <= lc for (l, _, _, _) in params)        # C_0 = C_1 = 0 are held
+    Yd, W, cols = _dense_Y(L, nside)
+    pos = {(l, m, 0 if part == "re" else 1): k for k, (_, l, m, part) in enumerate(cols)}
+    sel = [pos[(l, m, w)] for (l, m, _, w) in params]
+    lcol = np.array([cols[k][1] for k in sel])
+    G = Yd[:, sel].T @ (ninv[:, None] * Yd[:, sel])
+    ref = np.diag(W[sel] / cl[lcol]) + bl[lcol][:, None] * G * bl[lcol][None, :]
+    assert np.max(np.abs(H - ref)) < 1e-11 * np.max(np.abs(ref))
+
+
+def _teb_problem(nside, L, seed):
+    rng = np.random.default_rng(seed)
+    g = sht.healpix(nside)
+    tt = C.cl_flat(L)
+    cl4 = np.stack([tt, 0.05 * tt, 1e-3 * 0.05 * tt, 0.3 * np.sqrt(0.05) * tt])
+    mask = rng.uniform(size=g.npix) > 0.25
+    ninv = np.stack([rng.uniform(0.5, 2, g.npix) * mask, rng.uniform(0.2, 1, g.npix) * mask])
+    return g, solver.Problem(g, L, cl4, C.gauss_beam(L, 0.2), ninv), rng
+
+
+def test_low_block_teb_symmetric_positive_definite():
+    """T, E, B: H is symmetric positive definite (A is self-adjoint in the
+    metric of the inner products), and T couples to E only through the
+    prior's TE term (no noise coupling between T and Q, U)."""
+    g, prob, _ = _teb_problem(4, 8, 31)
+    params, H = solver.low_block(prob, 4)
+    assert np.max(np.abs(H - H.T)) < 1e-12 * np.max(np.abs(H))
+    assert np.linalg.eigvalsh(H).min() > 0
+    comp = np.array([c for (_, _, c, _) in params])
+    key = [(l, m, w) for (l, m, _, w) in params]
+    for i in np.where(comp == 0)[0]:
+        for j in np.where(comp != 0)[0]:
+            if key[i] == key[j] and comp[j] == 1:
+                continue                                   # S^-1_TE at the same (l, m, part)
+            assert abs(H[i, j]) < 1e-13 * np.max(np.abs(H))
+
+
+@pytest.mark.parametrize("ncomp", [1, 3])
+def test_two_level_with_every_multipole_is_the_exact_inverse(ncomp):
+    """l_c = l_max: the preconditioner is A^-1 itself, so PCG ends after one
+    iteration."""
+    if ncomp == 1:
+        g = sht.healpix(4)
+        L = 8
+        rng = np.random.default_rng(5)
+        ninv = rng.uniform(0.5, 2.0, g.npix) * (rng.uniform(size=g.npix) > 0.3)
+        prob = solver.Problem(g, L, C.cl_flat(L), C.gauss_beam(L, 0.2), ninv)
+    else:
+        g, prob, rng = _teb_problem(4, 6, 7)
+        L = 6
+    b = prob.matvec(_rand_alm(L, rng, ncomp))
+    x, it, hist = solver.pcg(prob, b, 1e-10, 20, precond=solver.two_level_precond(prob, L))
+    assert it == 1 and solver.true_residual(prob, x, b) < 1e-11
+
+
+def test_low_block_azimuthal_noise_is_the_per_m_block():
+    """App. A conditions (ring-constant N^-1, nphi >= 2 l_max + 1): H couples
+    only equal m and part, and its (l, l') entries at one m are w times the
+    per-m block of :func:`solver.azimuthal_block`."""
+    L, lc = 12, 6
+    g, prob, wr = _azimuthal_problem(L, True)
+    params, H = solver.low_block(prob, lc)
+    for m in (0, 3):
+        lr, A = solver.azimuthal_block(prob, m, wr)
+        w = 1.0 if m == 0 else 2.0
+        for part in ((0,) if m == 0 else (0, 1)):
+            rows = [k for k, (l, mm, _, pw) in enumerate(params) if mm == m and pw == part]
+            ls_ = np.array([params[k][0] for k in rows])
+            sub = H[np.ix_(rows, rows)]
+            ref = w * A[np.ix_(ls_ - m, ls_ - m)]
+            assert np.max(np.abs(sub - ref)) < 1e-12 * np.max(np.abs(ref))
+    key_m = np.array([p[1] for p in params])
+    key_w = np.array([p[3] for p in params])
+    off = (key_m[:, None] != key_m[None, :]) | (key_w[:, None] != key_w[None, :])
+    assert np.max(np.abs(H[off])) < 1e-12 * np.max(np.abs(H))
+
+
+def test_two_level_cuts_iterations_under_a_mask():
+    """The masked temperature workload at N_side 16: the same solution as
+    the diagonal preconditioner, in fewer iterations."""
+    p = C.masked_temperature(16, 32)
+    g = sht.healpix(16)
+    prob = solver.Problem(g, 32, p.cl, p.bl, p.ninv)
+    d = sht.alm2map(g, 32, p.signal_alm[0] * p.bl[sht.ls_of(32)]) + p.noise_map[0]
+    b = prob.rhs(d, p.w1, p.w2)
+    xd, itd, _ = solver.pcg(prob, b, 1e-10, 2000)
+    xl, itl, _ = solver.pcg(prob, b, 1e-10, 2000, precond=solver.two_level_precond(prob, 12))
+    assert itl < 0.6 * itd
+    assert np.max(np.abs(xl - xd)) < 1e-7 * np.max(np.abs(xd))
