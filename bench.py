@@ -5,7 +5,10 @@
 Workload: 8 T+E+B realizations sharing C_l, beam and N^-1 (hits-weighted
 noise, |b| < 20 deg mask + 200 holes, 10' beam).  One "step" is one
 cg_sample call with a fixed iteration budget: RHS assembly (FP64-accurate
-transforms), preconditioner, then --iters-per-step batched mixed-precision
+transforms), preconditioner (by default the two-level one: the exact
+inverse of the operator on l <= 32, kept between calls while C_l, the beam
+and N^-1 are unchanged, plus the diagonal above), then --iters-per-step
+batched mixed-precision
 PCG iterations (FP32 operator applications) with FP64-accurate residual
 replacements (reliable updates), the last one at the end of the step.
 Inputs are synthetic (seeded Philox), resident in HBM and larger than L2.
@@ -19,7 +22,8 @@ FP64-accurate residual replacements are not counted), summed over ranks.
 Ranks run independent replicas (weak scaling, no data-path collective);
 `--gpus N` spawns N local ranks itself unless it runs under torchrun.
 
-Extras: the full solve to a true FP64-accurate relative residual of 1e-6;
+Extras: the full solve to a true FP64-accurate relative residual of 1e-6
+with the two-level and with the diagonal preconditioner;
 the same steps with native FP64 residual replacements; the plain FP64 PCG
 per-iteration time; both forms solved to 1e-6 on the masked temperature
 workload (N_side 256, l_max 512), whose iteration ratio turns the FP64 form's
@@ -419,7 +423,8 @@ def gpu_rank(args):
     inp = make_inputs(plan, dev, rank=rank)
     kw = dict(tol=1e-6, mode=args.mode, maxiter=args.iters_per_step,
               reliable_delta=args.reliable_delta, check_every=args.check_every,
-              allow_not_converged=True, fp64_arith=args.fp64_arith)
+              allow_not_converged=True, fp64_arith=args.fp64_arith, precond=args.precond,
+              lowl_lmax=args.lowl_lmax)
     out = torch.empty(NB, 3, plan.nalm, dtype=torch.complex128, device=dev)
 
     def step(profile=False, **over):
@@ -586,6 +591,7 @@ def gpu_rank(args):
                                (", Legendre sums on the tensor cores (bf16 hi/lo split)"
                                 if args.mode == "mixed_tc" else ""),
                    "mode": args.mode, "fp64_arith": args.fp64_arith, "iters_per_step": args.iters_per_step,
+                   "precond": args.precond + (f" (l_c {args.lowl_lmax or 32})" if args.precond == "lowl" else ""),
                    "global_batch": NB * world, "fsky": inp["fsky"], "parallelism": f"replicas x{world}",
                    "timed_path": "default (PCG iteration replayed as a CUDA graph)",
                    "value_counts": "FP32 PCG iterations (FP64-accurate residual replacements not counted)",
@@ -639,14 +645,17 @@ def measure_extras(plan, inp, dev, kw, step, full_solve=True):
     import torch
     ex = {}
     if full_solve:
-        kwf = dict(kw)
-        kwf["maxiter"] = 6000
-        t, (_, st) = _event_time(lambda: plan.cg_sample(inp["cl"], inp["bl"], inp["ninv"], inp["d"],
-                                                        inp["w1"], inp["w2"], **kwf))
-        ex["mixed_full_solve"] = {"time_to_1e-6_s": t, "iterations": st["iterations"],
-                                  "fp64_matvecs": st["fp64_matvecs"],
-                                  "converged": bool(st["converged"]),
-                                  "rel_residual": st["rel_residual"], "ms_rhs": st["ms_rhs"]}
+        # to 1e-6 with the bench's preconditioner, then with the other one
+        other = "diag" if kw["precond"] == "lowl" else "lowl"
+        for key, pc in (("mixed_full_solve", kw["precond"]), (f"mixed_full_solve_{other}", other)):
+            kwf = dict(kw)
+            kwf["maxiter"] = 6000
+            kwf["precond"] = pc
+            t, (_, st) = _event_time(lambda: plan.cg_sample(inp["cl"], inp["bl"], inp["ninv"], inp["d"],
+                                                            inp["w1"], inp["w2"], **kwf))
+            ex[key] = {"precond": pc, "time_to_1e-6_s": t, "iterations": st["iterations"],
+                       "fp64_matvecs": st["fp64_matvecs"], "converged": bool(st["converged"]),
+                       "rel_residual": st["rel_residual"], "ms_setup": st["ms_setup"], "ms_rhs": st["ms_rhs"]}
     # the headline steps with native FP64 residual replacements and RHS
     t, sts = _event_time(lambda: [step(fp64_arith="fp64") for _ in range(2)])
     ex["steps_fp64_arith_fp64"] = {"value": sum(s["iterations"] for s in sts) / (2 * t), "unit": UNIT,
@@ -667,7 +676,7 @@ def measure_extras(plan, inp, dev, kw, step, full_solve=True):
         ex[f"fp64_form_{arith}"] = {"s_per_iteration": per_it, "iters_per_s": 1.0 / per_it,
                                     "fixed_s": runs[4][0] - 4 * per_it,
                                     "how": "two calls with 4 and 8 PCG iterations, difference / 4"}
-    ex["masked_nside256"] = measure_masked_pair(dev)
+    ex["masked_nside256"] = measure_masked_pair(dev, kw["precond"])
     if "mixed_full_solve" in ex:
         fs = ex["mixed_full_solve"]
         ratio = ex["masked_nside256"]["iteration_ratio_fp64_over_mixed"]
@@ -678,7 +687,7 @@ def measure_extras(plan, inp, dev, kw, step, full_solve=True):
             "iterations_model": it_model,
             "model": ("measured fixed cost + measured s/iteration x (the mixed solve's FP32 iterations at "
                       "this size x the FP64 / mixed iteration ratio measured to 1e-6 on the masked "
-                      "N_side 256 workload)")}
+                      "N_side 256 workload, both with the bench's preconditioner)")}
         ex["mixed_speedup_time_to_1e-6"] = ex["fp64_form_time_to_1e-6_model"]["s"] / fs["time_to_1e-6_s"]
     sht = {}
     for spin in (0, 2):
@@ -688,15 +697,16 @@ def measure_extras(plan, inp, dev, kw, step, full_solve=True):
     ex["sht_pairs_per_s"] = sht
     ex["sht_pairs_per_s_note"] = ("one alm2map + one alm2map_adjoint per map (spin 2: per (E, B) -> "
                                   "(Q, U) map pair), N_side 1024, l_max 2048, CUDA events")
-    ex["chains"] = measure_chains(dev)
+    ex["chains"] = measure_chains(dev, precond=kw["precond"])
     torch.cuda.synchronize()
     return ex
 
 
-def measure_masked_pair(dev):
+def measure_masked_pair(dev, precond="lowl"):
     """Both forms solved to 1e-6 on the masked temperature workload
     (N_side 256, l_max 512): iterations and time to 1e-6 of the plain FP64
-    PCG (native FP64) and of the mixed solver (tensor cores)."""
+    PCG (native FP64) and of the mixed solver (tensor cores), with the given
+    preconditioner and, for comparison, the other one."""
     import torch
     from inputs import configs as C
     from paper_2306_15511_gb300 import Plan
@@ -707,20 +717,23 @@ def measure_masked_pair(dev):
     d = (plan.alm2map(a[None].contiguous()) + torch.as_tensor(p.noise_map, device=dev))[:, None].contiguous()
     args = (p.cl, p.bl, torch.as_tensor(p.ninv, device=dev), d,
             torch.as_tensor(p.w1[None], device=dev).contiguous(), torch.as_tensor(p.w2[None], device=dev).contiguous())
-    out = {}
-    for mode in ("mixed_tc", "fp64"):
-        plan.cg_sample(*args, tol=1e-6, mode=mode, maxiter=2, allow_not_converged=True)   # autotuning
-        t, (_, st) = _event_time(lambda: plan.cg_sample(*args, tol=1e-6, mode=mode, maxiter=8000,
-                                                        check_every=8))
-        out[mode] = {"time_to_1e-6_s": t, "iterations": st["iterations"], "fp64_matvecs": st["fp64_matvecs"],
-                     "converged": bool(st["converged"]), "rel_residual": st["rel_residual"]}
+    out = {"precond": precond}
+    other = "diag" if precond == "lowl" else "lowl"
+    for pc, sfx in ((precond, ""), (other, f"_{other}")):
+        for mode in ("mixed_tc", "fp64"):
+            plan.cg_sample(*args, tol=1e-6, mode=mode, maxiter=2, allow_not_converged=True, precond=pc)   # tuning
+            t, (_, st) = _event_time(lambda: plan.cg_sample(*args, tol=1e-6, mode=mode, maxiter=8000,
+                                                            check_every=8, precond=pc))
+            out[mode + sfx] = {"time_to_1e-6_s": t, "iterations": st["iterations"],
+                               "fp64_matvecs": st["fp64_matvecs"], "converged": bool(st["converged"]),
+                               "rel_residual": st["rel_residual"], "ms_setup": st["ms_setup"]}
     out["iteration_ratio_fp64_over_mixed"] = out["fp64"]["iterations"] / max(1, out["mixed_tc"]["iterations"])
     out["speedup_time_to_1e-6"] = out["fp64"]["time_to_1e-6_s"] / out["mixed_tc"]["time_to_1e-6_s"]
     plan.close()
     return out
 
 
-def measure_chains(dev, nchains=64):
+def measure_chains(dev, nchains=64, precond="diag"):
     """Mixed-geometry chains: 64 independent chains with N_side in {64, 128, 256},
     l_max in {2 N_side, 3 N_side - 1} and their own signal amplitudes, all
     solved to 1e-6 in one chains call (one plan per geometry)."""
@@ -743,13 +756,14 @@ def measure_chains(dev, nchains=64):
                     "w1": torch.stack([torch.as_tensor(ch.w1, device=dev) for ch in chs]).contiguous(),
                     "w2": torch.stack([torch.as_tensor(ch.w2, device=dev) for ch in chs]).contiguous(),
                     "cl_scale": [ch.extra["amp"] for ch in chs]})
-    chains_sample(req, tol=1e-6, mode="mixed_tc", maxiter=4000)   # autotuning and warm-up
+    chains_sample(req, tol=1e-6, mode="mixed_tc", maxiter=4000, precond=precond)   # tuning, warm-up
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    res = chains_sample(req, tol=1e-6, mode="mixed_tc", maxiter=4000)
+    res = chains_sample(req, tol=1e-6, mode="mixed_tc", maxiter=4000, precond=precond)
     torch.cuda.synchronize()
     el = time.perf_counter() - t0
-    return {"chains": nchains, "groups": len(req), "time_to_1e-6_s": el, "chains_per_s": nchains / el,
+    return {"chains": nchains, "groups": len(req), "precond": precond, "time_to_1e-6_s": el,
+            "chains_per_s": nchains / el,
             "geometries": [f"N_side {ns} l_max {L} x{len(chs)}" for (ns, L), chs in sorted(groups.items())],
             "iterations": [st["iterations"] for _, st in res],
             "converged": all(st["converged"] == 1 for _, st in res)}
@@ -770,6 +784,9 @@ def main():
     ap.add_argument("--lmax", type=int, default=LMAX, help="profiling only: smaller l_max")
     ap.add_argument("--batch", type=int, default=NB, help="profiling only: fewer realizations")
     ap.add_argument("--no-full-solve", action="store_true")
+    ap.add_argument("--precond", default="lowl", choices=["none", "diag", "lowl"],
+                    help="diagonal preconditioner of Sect. 4, or two-level (exact inverse on l <= l_c)")
+    ap.add_argument("--lowl-lmax", type=int, default=0, help="l_c of the two-level preconditioner (0: 32)")
     ap.add_argument("--reliable-delta", type=float, default=1e-2)
     ap.add_argument("--check-every", type=int, default=8)
     ap.add_argument("--e2e-steps", type=int, default=1)

@@ -125,6 +125,10 @@ struct LowL {
     int gram_lc = -1, gram_nc = 0;
     bool gram_ok = false;
     std::vector<int4> params;      // host copy of the active parameters
+    // the per-l table rows (beam, S^-1) and C_l scale H^-1 was built from
+    std::vector<double> inv_ltab;
+    double inv_isc = 0.0;
+    bool inv_ok = false;
 };
 
 struct Plan {

@@ -459,10 +459,11 @@ int lowl_setup(Plan *p, int lc, int nc, double isc, cudaStream_t st, double *h_h
             for (int m = 0; m <= l; ++m)
                 for (int w = 0; w < (m ? 2 : 1); ++w) par.push_back(make_int4(l, m, c, w));
     const int nf = (int)par.size();
-    std::vector<double> sh(L1);
-    SHTG_CUDA(cudaMemcpyAsync(sh.data(), p->d_ltab64 + 5 * (int64_t)L1, sizeof(double) * L1,
-                              cudaMemcpyDeviceToHost, st));
+    // per-l rows 0 (beam), 1-4 (S^-1) and 5 (S^-1/2 TT: zero where held)
+    std::vector<double> tab(6 * (size_t)L1);
+    SHTG_CUDA(cudaMemcpyAsync(tab.data(), p->d_ltab64, sizeof(double) * tab.size(), cudaMemcpyDeviceToHost, st));
     SHTG_CUDA(cudaStreamSynchronize(st));
+    const double *sh = tab.data() + 5 * (size_t)L1;
     std::vector<int> sel, emap;
     std::vector<float> wv;
     q.params.clear();
@@ -475,6 +476,8 @@ int lowl_setup(Plan *p, int lc, int nc, double isc, cudaStream_t st, double *h_h
         q.params.push_back(a);
     }
     const int n = (int)sel.size();
+    const bool same = q.inv_ok && q.n == n && q.lc == lc && q.nc == nc && q.inv_isc == isc && q.inv_ltab == tab;
+    q.inv_ok = false;
     q.n = n;
     q.lc = lc;
     q.nc = nc;
@@ -523,7 +526,12 @@ int lowl_setup(Plan *p, int lc, int nc, double isc, cudaStream_t st, double *h_h
         q.gram_lc = lc;
         q.gram_nc = nc;
     }
-    // ---- H and its inverse
+    // ---- H and its inverse (kept while G, the per-l table and the C_l scale
+    // are unchanged, e.g. across the calls of one chain state)
+    if (same && !rebuild && !h_host) {
+        q.inv_ok = true;
+        return SHTG_OK;
+    }
     const int64_t nn = (int64_t)n * n;
     SHTG_CUDA(cudaMemsetAsync(q.flag, 0, sizeof(int), st));
     k_lowl_assemble<<<blocks_for(nn), 256, 0, st>>>(n, nf, q.sel, q.par, q.G, p->d_ltab64, L1, isc, q.H, q.flag);
@@ -547,6 +555,9 @@ int lowl_setup(Plan *p, int lc, int nc, double isc, cudaStream_t st, double *h_h
         set_error("two-level preconditioner: the low-l block is not positive definite");
         return SHTG_ERR_NOT_SPD;
     }
+    q.inv_ltab = tab;
+    q.inv_isc = isc;
+    q.inv_ok = true;
     // the apply kernel stages n values per system in shared memory (at most
     // 3 x 49^2 doubles = 57.6 KB)
     if (sizeof(double) * (size_t)n > 48 * 1024) {
