@@ -263,6 +263,81 @@ def two_level_precond(prob: Problem, lc: int):
 
 
 # ----------------------------------------------------------------------------
+# Azimuthal block preconditioner: the per-m blocks of App. A built from the
+# ring average of N^-1 (exact when N^-1 is constant along every ring)
+# ----------------------------------------------------------------------------
+def ring_sum_weights(prob: Problem):
+    """sum over the pixels of each ring of N^-1: (ncomp_noise, nring) (T, and
+    P for T+E+B), i.e. nphi_r times the ring average."""
+    g = prob.g
+    return np.stack([sht.ring_sums(g, prob.ninv[c]) for c in range(prob.ninv.shape[0])])
+
+
+def azimuthal_te_block(prob: Problem, m: int, lb: int, wsum):
+    """The m-block of A on the multipoles l = m .. lb of T (and E) with N^-1
+    replaced by the ring weights wsum (per ring: sum of N^-1 over its pixels)
+    and the aliasing of rings with nphi < 2 lmax + 1 left out:
+      T-T: delta S^-1_TT + b_l b_l' sum_r wsum_T,r lambda_l lambda_l',
+      E-E: delta S^-1_EE + b_l b_l' sum_r wsum_P,r (lw_l lw_l' + lx_l lx_l'),
+      T-E: delta S^-1_TE;
+    held multipoles (singular C_l block) give identity rows.  The E-B noise
+    coupling at equal m (imaginary, sum_r wsum_P (lw lx' + lx lw')) and B are
+    not part of the block.  Returns (l values, block) with rows [T l..] or
+    [T l.., E l..]."""
+    g = prob.g
+    lr = np.arange(m, lb + 1)
+    k = lr.size
+    bm = prob.bmask[lr]
+    act = prob.active[lr]
+    lam = np.array([sht.lambda_lm(lb, m, g.cth[r], g.sth[r]) for r in range(g.nring)])   # (nring, k)
+    GT = (lam * wsum[0][:, None]).T @ lam
+    blocks = [[bm[:, None] * GT * bm[None, :] + np.diag(np.where(act, prob.sinv[0, 0][lr], 0.0))]]
+    if prob.ncomp == 3:
+        lw = np.zeros((g.nring, k))
+        lx = np.zeros((g.nring, k))
+        for r in range(g.nring):
+            lw[r], lx[r] = sht.lambda_spin2(lb, m, g.cth[r], g.sth[r])
+        GE = (lw * wsum[1][:, None]).T @ lw + (lx * wsum[1][:, None]).T @ lx
+        te = np.diag(np.where(act, prob.sinv[0, 1][lr], 0.0))
+        ee = bm[:, None] * GE * bm[None, :] + np.diag(np.where(act, prob.sinv[1, 1][lr], 0.0))
+        blocks = [[blocks[0][0], te], [te, ee]]
+    A = np.block(blocks)
+    held = np.where(np.tile(~act, len(blocks)))[0]
+    A[held, :] = 0.0
+    A[:, held] = 0.0
+    A[held, held] = 1.0
+    return lr, A
+
+
+def azimuthal_precond(prob: Problem, lb: int):
+    """z = M^-1 r for the azimuthal block preconditioner: on the T (and E)
+    multipoles l <= lb of every m <= lb the inverse of
+    :func:`azimuthal_te_block` (real and imaginary parts alike), elsewhere
+    (B, l > lb) the diagonal preconditioner.  A block Jacobi preconditioner:
+    symmetric and positive definite.  Returns the callable for :func:`pcg`."""
+    M = prob.precond_diag()
+    L = prob.lmax
+    wsum = ring_sum_weights(prob)
+    ls, ms = sht.ls_of(L), sht.ms_of(L)
+    nb = 1 if prob.ncomp == 1 else 2
+    inv = {}
+    for m in range(min(lb, L) + 1):
+        _, A = azimuthal_te_block(prob, m, lb, wsum)
+        inv[m] = (np.where((ms == m) & (ls <= lb))[0], np.linalg.inv(A))
+
+    def apply(r):
+        z = np.array(apply_block_inverse(M, r), np.complex128, copy=True)
+        for m, (idx, Ai) in inv.items():
+            v = np.concatenate([r[c, idx] for c in range(nb)])
+            w = Ai @ v.real + 1j * (Ai @ v.imag)
+            for c in range(nb):
+                z[c, idx] = w[c * idx.size:(c + 1) * idx.size]
+        return z
+
+    return apply
+
+
+# ----------------------------------------------------------------------------
 # Per-m dense block solve for azimuthally symmetric noise (App. A)
 # ----------------------------------------------------------------------------
 def ring_weights(prob: Problem):
