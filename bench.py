@@ -5,9 +5,10 @@
 Workload: 8 T+E+B realizations sharing C_l, beam and N^-1 (hits-weighted
 noise, |b| < 20 deg mask + 200 holes, 10' beam).  One "step" is one
 cg_sample call with a fixed iteration budget: RHS assembly (FP64-accurate
-transforms), preconditioner (by default the two-level one: the exact
-inverse of the operator on l <= 32, kept between calls while C_l, the beam
-and N^-1 are unchanged, plus the diagonal above), then --iters-per-step
+transforms), preconditioner (by default the azimuthal blocks: the exact
+per-m inverse, for l <= 1024, of the operator with N^-1 averaged along
+every ring, App. A's blocks of T and E, kept between calls while C_l, the
+beam and N^-1 are unchanged; the diagonal elsewhere), then --iters-per-step
 batched mixed-precision
 PCG iterations (FP32 operator applications) with FP64-accurate residual
 replacements (reliable updates), the last one at the end of the step.
@@ -23,7 +24,7 @@ Ranks run independent replicas (weak scaling, no data-path collective);
 `--gpus N` spawns N local ranks itself unless it runs under torchrun.
 
 Extras: the full solve to a true FP64-accurate relative residual of 1e-6
-with the two-level and with the diagonal preconditioner;
+with the bench's and with the diagonal preconditioner;
 the same steps with native FP64 residual replacements; the plain FP64 PCG
 per-iteration time; both forms solved to 1e-6 on the masked temperature
 workload (N_side 256, l_max 512), whose iteration ratio turns the FP64 form's
@@ -424,7 +425,7 @@ def gpu_rank(args):
     kw = dict(tol=1e-6, mode=args.mode, maxiter=args.iters_per_step,
               reliable_delta=args.reliable_delta, check_every=args.check_every,
               allow_not_converged=True, fp64_arith=args.fp64_arith, precond=args.precond,
-              lowl_lmax=args.lowl_lmax)
+              lowl_lmax=args.lowl_lmax, block_lmax=args.block_lmax)
     out = torch.empty(NB, 3, plan.nalm, dtype=torch.complex128, device=dev)
 
     def step(profile=False, **over):
@@ -591,7 +592,9 @@ def gpu_rank(args):
                                (", Legendre sums on the tensor cores (bf16 hi/lo split)"
                                 if args.mode == "mixed_tc" else ""),
                    "mode": args.mode, "fp64_arith": args.fp64_arith, "iters_per_step": args.iters_per_step,
-                   "precond": args.precond + (f" (l_c {args.lowl_lmax or 32})" if args.precond == "lowl" else ""),
+                   "precond": args.precond + (f" (l_c {args.lowl_lmax or 32})" if args.precond == "lowl" else
+                                              f" (l_b {args.block_lmax or min(LMAX, 1024)})"
+                                              if args.precond == "azim" else ""),
                    "global_batch": NB * world, "fsky": inp["fsky"], "parallelism": f"replicas x{world}",
                    "timed_path": "default (PCG iteration replayed as a CUDA graph)",
                    "value_counts": "FP32 PCG iterations (FP64-accurate residual replacements not counted)",
@@ -646,7 +649,7 @@ def measure_extras(plan, inp, dev, kw, step, full_solve=True):
     ex = {}
     if full_solve:
         # to 1e-6 with the bench's preconditioner, then with the other one
-        other = "diag" if kw["precond"] == "lowl" else "lowl"
+        other = "diag" if kw["precond"] != "diag" else "azim"
         for key, pc in (("mixed_full_solve", kw["precond"]), (f"mixed_full_solve_{other}", other)):
             kwf = dict(kw)
             kwf["maxiter"] = 6000
@@ -702,7 +705,7 @@ def measure_extras(plan, inp, dev, kw, step, full_solve=True):
     return ex
 
 
-def measure_masked_pair(dev, precond="lowl"):
+def measure_masked_pair(dev, precond="azim"):
     """Both forms solved to 1e-6 on the masked temperature workload
     (N_side 256, l_max 512): iterations and time to 1e-6 of the plain FP64
     PCG (native FP64) and of the mixed solver (tensor cores), with the given
@@ -718,7 +721,7 @@ def measure_masked_pair(dev, precond="lowl"):
     args = (p.cl, p.bl, torch.as_tensor(p.ninv, device=dev), d,
             torch.as_tensor(p.w1[None], device=dev).contiguous(), torch.as_tensor(p.w2[None], device=dev).contiguous())
     out = {"precond": precond}
-    other = "diag" if precond == "lowl" else "lowl"
+    other = "diag" if precond != "diag" else "azim"
     for pc, sfx in ((precond, ""), (other, f"_{other}")):
         for mode in ("mixed_tc", "fp64"):
             plan.cg_sample(*args, tol=1e-6, mode=mode, maxiter=2, allow_not_converged=True, precond=pc)   # tuning
@@ -784,9 +787,11 @@ def main():
     ap.add_argument("--lmax", type=int, default=LMAX, help="profiling only: smaller l_max")
     ap.add_argument("--batch", type=int, default=NB, help="profiling only: fewer realizations")
     ap.add_argument("--no-full-solve", action="store_true")
-    ap.add_argument("--precond", default="lowl", choices=["none", "diag", "lowl"],
-                    help="diagonal preconditioner of Sect. 4, or two-level (exact inverse on l <= l_c)")
+    ap.add_argument("--precond", default="azim", choices=["none", "diag", "lowl", "azim"],
+                    help="diagonal preconditioner of Sect. 4, two-level (exact inverse on l <= l_c), or "
+                         "azimuthal blocks (App. A's per-m blocks from ring-averaged N^-1, l <= l_b)")
     ap.add_argument("--lowl-lmax", type=int, default=0, help="l_c of the two-level preconditioner (0: 32)")
+    ap.add_argument("--block-lmax", type=int, default=0, help="l_b of the azimuthal blocks (0: 1024)")
     ap.add_argument("--reliable-delta", type=float, default=1e-2)
     ap.add_argument("--check-every", type=int, default=8)
     ap.add_argument("--e2e-steps", type=int, default=1)

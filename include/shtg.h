@@ -97,6 +97,7 @@ extern "C" {
 #define SHTG_PRECOND_NONE 0          /* shtg_cg_opts.precond */
 #define SHTG_PRECOND_DIAG 1
 #define SHTG_PRECOND_LOWL 2
+#define SHTG_PRECOND_AZIM 3
 #define SHTG_ARITH_DEFAULT 0         /* shtg_cg_opts.fp64_arith */
 #define SHTG_ARITH_FP64 1            /* native FP64 multiply-adds */
 #define SHTG_ARITH_DF64 2            /* Legendre sums in double-FP32 (hi + lo float pairs, ~2^-47
@@ -236,7 +237,10 @@ typedef struct {
     int mode;           /* SHTG_CG_FP64, SHTG_CG_MIXED, SHTG_CG_MIXED_TC or SHTG_CG_BLOCK */
     int precond;        /* SHTG_PRECOND_DIAG (1): diagonal preconditioner of Sect. 4 (default);
                            SHTG_PRECOND_NONE (0); SHTG_PRECOND_LOWL (2): two-level, the exact
-                           inverse of the operator on l <= lowl_lmax plus the diagonal above */
+                           inverse of the operator on l <= lowl_lmax plus the diagonal above;
+                           SHTG_PRECOND_AZIM (3): azimuthal blocks, the exact per-m inverse of the
+                           operator with N^-1 averaged along every ring (App. A's blocks of T and
+                           E) for l <= block_lmax plus the diagonal elsewhere */
     double reliable_delta; /* mixed mode: an FP64 residual replacement happens when the FP32
                               residual has dropped by this factor since the last one (default 1e-2) */
     int fp64_arith;     /* arithmetic of the FP64-accurate steps (RHS, residual replacements,
@@ -247,6 +251,8 @@ typedef struct {
     int flags;          /* SHTG_HOST_INPUTS: ninv, d, w1, w2 and alm_out are host memory */
     int lowl_lmax;      /* SHTG_PRECOND_LOWL: l_c, the largest multipole of the dense block
                            (0: min(lmax, 32); at most min(lmax, 48)) */
+    int block_lmax;     /* SHTG_PRECOND_AZIM: the largest multipole of the per-m blocks
+                           (0: min(lmax, 1024); at most lmax) */
 } shtg_cg_opts;
 
 typedef struct {
@@ -319,6 +325,16 @@ int shtg_apply_operator(shtg_plan *plan, const shtg_problem *prob, const double 
  * SHTG_ERR_NOT_SPD if the block is not positive definite. */
 int shtg_lowl_block(shtg_plan *plan, const shtg_problem *prob, int lowl_lmax, double *H, int *params, int *n,
                     void *stream);
+
+/* Apply the solver's preconditioner once (Sect. 4 and the options above):
+ * z = M^-1 r for r, z device [nbatch][ncomp][nalm] complex128 (FP64; the
+ * azimuthal blocks with their FP64 factors), with the problem's cl, bl,
+ * ninv and cl_scale (d, w1, w2 unused) and opts->precond, lowl_lmax and
+ * block_lmax.  Builds what the preconditioner needs like shtg_cg_sample
+ * (the workspace of SHTG_PRECOND_LOWL and SHTG_PRECOND_AZIM stays with the
+ * plan).  Synchronizes the stream. */
+int shtg_precond_apply(shtg_plan *plan, const shtg_problem *prob, const shtg_cg_opts *opts, const double *r,
+                       double *z, void *stream);
 
 /* ------------------------------------------- joint (C_l, a) move (Sect. 2.2.2) */
 /* The deterministic rescaling of the fluctuation term,

@@ -23,7 +23,7 @@ PROFILE = 2
 NO_GRAPHS = 4
 SPLIT_RHS = 8
 GRAD_COMPONENTS = 1
-PRECOND_NONE, PRECOND_DIAG, PRECOND_LOWL = 0, 1, 2
+PRECOND_NONE, PRECOND_DIAG, PRECOND_LOWL, PRECOND_AZIM = 0, 1, 2, 3
 
 # every symbol include/shtg.h declares
 SYMBOLS = ("shtg_plan_create", "shtg_plan_destroy", "shtg_plan_get_info",
@@ -32,7 +32,7 @@ SYMBOLS = ("shtg_plan_create", "shtg_plan_destroy", "shtg_plan_get_info",
            "shtg_map2alm", "shtg_cg_sample", "shtg_cg_sample_chains", "shtg_apply_operator",
            "shtg_logpost_grad", "shtg_probe_fma_peak", "shtg_fluctuation_rescale",
            "shtg_joint_log_target", "shtg_joint_acceptance", "shtg_logpost_grad_binned",
-           "shtg_lowl_block")
+           "shtg_lowl_block", "shtg_precond_apply")
 
 
 class PlanInfo(C.Structure):
@@ -50,7 +50,8 @@ class Problem(C.Structure):
 class CGOpts(C.Structure):
     _fields_ = [("tol", C.c_double), ("maxiter", C.c_int), ("mode", C.c_int),
                 ("precond", C.c_int), ("reliable_delta", C.c_double), ("fp64_arith", C.c_int),
-                ("check_every", C.c_int), ("flags", C.c_int), ("lowl_lmax", C.c_int)]
+                ("check_every", C.c_int), ("flags", C.c_int), ("lowl_lmax", C.c_int),
+                ("block_lmax", C.c_int)]
 
 
 class CGStats(C.Structure):
@@ -111,6 +112,7 @@ def load(build_if_missing: bool = True):
         L.shtg_joint_log_target.argtypes = [vp, C.POINTER(Problem), ci, vp, vp, vp, vp]
         L.shtg_joint_acceptance.argtypes = [cd, cd, cd, cd, C.POINTER(cd)]
         L.shtg_lowl_block.argtypes = [vp, C.POINTER(Problem), ci, vp, vp, C.POINTER(ci), vp]
+        L.shtg_precond_apply.argtypes = [vp, C.POINTER(Problem), C.POINTER(CGOpts), vp, vp, vp]
         L.shtg_logpost_grad_binned.argtypes = [vp, vp, vp, vp, vp, vp, ci, vp, vp, vp, ci, C.POINTER(cd),
                                                vp, vp, vp]
         for s in SYMBOLS:

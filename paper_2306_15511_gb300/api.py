@@ -42,7 +42,7 @@ def _arith(fp64_arith: str) -> int:
     return _ARITH[fp64_arith]
 
 
-_PRECOND = {"none": N.PRECOND_NONE, "diag": N.PRECOND_DIAG, "lowl": N.PRECOND_LOWL}
+_PRECOND = {"none": N.PRECOND_NONE, "diag": N.PRECOND_DIAG, "lowl": N.PRECOND_LOWL, "azim": N.PRECOND_AZIM}
 
 
 def _precond(precond) -> int:
@@ -200,7 +200,8 @@ class Plan:
                   maxiter: int = 4000, precond=True, reliable_delta: float = 1e-2,
                   check_every: int = 4, out=None,
                   allow_not_converged: bool = False, profile: bool = False, graphs: bool = True,
-                  cl_scale=None, fp64_arith: str = "default", split: bool = False, lowl_lmax: int = 0):
+                  cl_scale=None, fp64_arith: str = "default", split: bool = False, lowl_lmax: int = 0,
+                  block_lmax: int = 0):
         """Constrained realization(s) of Eq. (mapmakingeq).
 
         mode: "fp64" (plain FP64 PCG), "mixed" / "mixed_tc" (FP32 PCG with
@@ -212,9 +213,12 @@ class Plan:
         cl_scale: optional [nbatch] amplitudes; realization b uses cl_scale[b] x cl.
 
         precond: True / "diag" (the diagonal preconditioner of Sect. 4),
-        False / "none", or "lowl" (two-level: the exact inverse of the
+        False / "none", "lowl" (two-level: the exact inverse of the
         operator on the multipoles l <= lowl_lmax, 0 = min(lmax, 32), plus
-        the diagonal above; built with the first realization's cl_scale).
+        the diagonal above) or "azim" (the exact per-m inverse of the
+        operator with N^-1 averaged along every ring, App. A's blocks of T
+        and E, for l <= block_lmax, 0 = min(lmax, 1024), plus the diagonal
+        elsewhere); both built with the first realization's cl_scale.
 
         split: solve the mean field (Eq. mean-field-map) and the fluctuation
         (Eq. fluc-map) as separate systems of one batch; the result is then
@@ -256,7 +260,7 @@ class Plan:
             raise ValueError(f"mode must be one of {sorted(modes)}")
         o.mode = modes[mode]
         o.precond = _precond(precond)
-        o.lowl_lmax = int(lowl_lmax)
+        o.lowl_lmax, o.block_lmax = int(lowl_lmax), int(block_lmax)
         o.reliable_delta, o.fp64_arith = float(reliable_delta), _arith(fp64_arith)
         o.check_every = int(check_every)
         o.flags = ((N.HOST_INPUTS if host else 0) | (N.PROFILE if profile else 0) |
@@ -314,6 +318,20 @@ class Plan:
                                           C.byref(n), _stream()))
         k = n.value
         return H[:k * k].reshape(k, k).copy(), par[:4 * k].reshape(k, 4).copy()
+
+    def precond_apply(self, cl, bl, ninv, r: torch.Tensor, precond="diag", lowl_lmax: int = 0,
+                      block_lmax: int = 0, cl_scale=None) -> torch.Tensor:
+        """z = M^-1 r with the solver's preconditioner (shtg_precond_apply)
+        for r [nbatch, ncomp, nalm] complex128 (CUDA)."""
+        _need_cuda(r, "r")
+        z = torch.empty_like(r)
+        pr = self._problem(cl, bl, ninv, nbatch=int(r.shape[0]), ncomp=int(r.shape[1]), cl_scale=cl_scale)
+        o = N.CGOpts()
+        o.precond = _precond(precond)
+        o.lowl_lmax, o.block_lmax = int(lowl_lmax), int(block_lmax)
+        N.check(self._lib.shtg_precond_apply(self._h, C.byref(pr), C.byref(o), _ptr(r.contiguous()), _ptr(z),
+                                             _stream()))
+        return z
 
     def apply_operator(self, cl, bl, ninv, x: torch.Tensor, cl_scale=None) -> torch.Tensor:
         """y = (S^-1 + B Y^T N^-1 Y B) x for x [nbatch, ncomp, nalm] complex128 (CUDA)."""
@@ -373,7 +391,7 @@ def fma_peak(precision: str = "fp32"):
 def chains_sample(groups, tol: float = 1e-6, mode: str = "mixed_tc", maxiter: int = 4000,
                   precond=True, reliable_delta: float = 1e-2, check_every: int = 4,
                   allow_not_converged: bool = False, graphs: bool = True, fp64_arith: str = "default",
-                  lowl_lmax: int = 0):
+                  lowl_lmax: int = 0, block_lmax: int = 0):
     """Constrained realizations of many chains of uneven geometry in one call.
 
     groups: list of dicts, one per geometry, with keys plan, cl, bl, ninv, d,
@@ -409,7 +427,7 @@ def chains_sample(groups, tol: float = 1e-6, mode: str = "mixed_tc", maxiter: in
         raise ValueError(f"mode must be one of {sorted(modes)}")
     o.mode = modes[mode]
     o.precond = _precond(precond)
-    o.lowl_lmax = int(lowl_lmax)
+    o.lowl_lmax, o.block_lmax = int(lowl_lmax), int(block_lmax)
     o.reliable_delta, o.fp64_arith = float(reliable_delta), _arith(fp64_arith)
     o.check_every = int(check_every)
     o.flags = 0 if graphs else N.NO_GRAPHS

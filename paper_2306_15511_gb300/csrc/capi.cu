@@ -377,6 +377,15 @@ int shtg_apply_operator(shtg_plan *plan, const shtg_problem *prob, const double 
     return apply_operator(reinterpret_cast<Plan *>(plan), prob, x, y, (cudaStream_t)stream);
 }
 
+int shtg_precond_apply(shtg_plan *plan, const shtg_problem *prob, const shtg_cg_opts *opts, const double *r,
+                       double *z, void *stream) {
+    if (!plan || !prob || !opts || !r || !z) {
+        set_error("null argument");
+        return SHTG_ERR_ARG;
+    }
+    return precond_apply(reinterpret_cast<Plan *>(plan), prob, opts, r, z, (cudaStream_t)stream);
+}
+
 int shtg_lowl_block(shtg_plan *plan, const shtg_problem *prob, int lowl_lmax, double *H, int *params, int *n,
                     void *stream) {
     if (!plan || !prob || !H || !n) {

@@ -131,6 +131,30 @@ struct LowL {
     bool inv_ok = false;
 };
 
+// azimuthal block preconditioner (azblk.cu): per-m blocks of T (and E) for
+// l <= lb from the ring sums of N^-1, their Cholesky factors
+#define SHTG_AZ_LB_DEFAULT 1024
+struct AzBlk {
+    int lb = -1, ncb = 0;          // block l max; components per block (T, or T and E)
+    int64_t gsize = 0, hsize = 0, pcap = 0;
+    double *G = nullptr;           // packed lower Gram matrices per m (T, then E), no beam, no prior
+    double *H = nullptr;           // packed lower blocks per m; Cholesky factor R, then R^-1, in place
+    double *M64 = nullptr;         // full-square block inverses per m (FP64)
+    float *M32 = nullptr;          // their FP32 copy (the FP32 iteration)
+    int64_t *goff = nullptr, *hoff = nullptr, *moff = nullptr, *poff = nullptr, *xoff = nullptr;
+    double *Xg = nullptr;          // [m][q][row] right-hand sides of the blocks (FP32 or FP64 values)
+    int ntile = 0;                 // 128-row tiles of the largest block
+    double *w = nullptr;           // [ch][sum, diff][pair] ring sums of N^-1 over the pair's rings
+    double *pl = nullptr, *pw = nullptr, *px = nullptr;   // profiles of a chunk of m
+    double *slot = nullptr;        // [max_batch][lb + 1] <r, z> corrections
+    int *flag = nullptr;
+    double *ninv = nullptr;        // N^-1 the Gram matrices were built from
+    int64_t bytes = 0;
+    bool gram_ok = false, inv_ok = false;
+    std::vector<double> inv_ltab;
+    double inv_isc = 0.0;
+};
+
 struct Plan {
     int device = 0;
     Prof prof;
@@ -250,6 +274,7 @@ struct Plan {
     int *d_blkflag = nullptr;
     int64_t blk_cap = 0, lam_cap = 0;
     LowL lowl;
+    AzBlk az;
     double *d_stage = nullptr;     // [nmaps_max][npix] staging for host inputs
     double *h_pinned = nullptr;    // pinned host scalars
 };
@@ -275,6 +300,13 @@ int lowl_setup(Plan *p, int lc, int nc, double isc, cudaStream_t st, double *h_h
 template <typename T>
 int lowl_apply(Plan *p, const T *r, T *z, int nb, int64_t per, double *part, cudaStream_t st);
 void lowl_free(Plan *p);
+// azblk.cu: azimuthal block preconditioner for l <= lb (<= 0: the default)
+int az_setup(Plan *p, int lb, int nc, double isc, cudaStream_t st);
+template <typename T>
+int az_apply(Plan *p, const T *r, T *z, int nb, int64_t per, double *part, cudaStream_t st, bool fp64_factor);
+void az_free(Plan *p);
+int precond_apply(Plan *p, const shtg_problem *pr, const shtg_cg_opts *o, const double *r, double *z,
+                  cudaStream_t st);
 int lowl_block(Plan *p, const shtg_problem *pr, int lc, double *H, int *params, int *n, cudaStream_t st);
 int logpost_grad(Plan *p, const double *cl, const double *bl, const float *alm, const float *d,
                  const float *ninv, int nbins, const int *blo, const int *bhi, int flags,

@@ -764,6 +764,7 @@ int plan_build(Plan *p) {
 
 void plan_free(Plan *p) {
     lowl_free(p);
+    az_free(p);
     void *ptrs[] = {p->d_nphi, p->d_ofs, p->d_wring, p->d_u64, p->d_u32, p->d_x64, p->d_is2_64,
                     p->d_x32, p->d_is2_32, p->d_lofidx, p->d_mofidx, p->d_rec64, p->d_rec32,
                     p->d_ls64, p->d_ls32, p->d_st64, p->d_st32, p->d_s2c64, p->d_s2c32,

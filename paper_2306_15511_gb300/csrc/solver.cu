@@ -693,7 +693,8 @@ struct Solve {
     int tc = 0;      // FP32 operator: Legendre sums on the tensor cores
     int df = 0;      // FP64 operator: Legendre sums in double-FP32 arithmetic
     int graphs = 1;  // replay captured iterations (off while profiling)
-    int lowl = 0;    // two-level preconditioner: exact inverse on the low multipoles
+    int pc = SHTG_PRECOND_DIAG;   // preconditioner: the low block (LOWL) or the azimuthal blocks (AZIM)
+                                  // replace z on their rows after every update of the diagonal one
     int64_t nalm, per, nvec;
     dim3 vgrid;   // (blocks, nb)
     dim3 rgrid;   // (RB, nb)
@@ -779,6 +780,19 @@ static int matvec(Solve &s, const typename HT<T>::C *x, typename HT<T>::C *y, bo
     return SHTG_OK;
 }
 
+// The preconditioner beyond the diagonal: z on the rows of the low block or
+// of the azimuthal blocks, and the change of <r, z> in the rz partials.
+template <typename T>
+static int precond_fix(Solve &s, const typename HT<T>::C *r, typename HT<T>::C *z) {
+    if (s.pc == SHTG_PRECOND_LOWL)
+        return lowl_apply<T>(s.p, reinterpret_cast<const T *>(r), reinterpret_cast<T *>(z), s.nb, s.per,
+                             s.p->d_part, s.st);
+    if (s.pc == SHTG_PRECOND_AZIM)
+        return az_apply<T>(s.p, reinterpret_cast<const T *>(r), reinterpret_cast<T *>(z), s.nb, s.per,
+                           s.p->d_part, s.st, false);
+    return SHTG_OK;
+}
+
 // One PCG iteration on the device: q = A p, alpha, x/r/z update, beta, p.
 template <typename T>
 static int pcg_iteration(Solve &s, typename HT<T>::C *x, typename HT<T>::C *r, typename HT<T>::C *z,
@@ -790,9 +804,7 @@ static int pcg_iteration(Solve &s, typename HT<T>::C *x, typename HT<T>::C *r, t
     k_scal_alpha<<<1, 1024, 0, s.st>>>(p->d_part, p->d_scal, s.nb);
     k_update<T, false><<<s.rgrid, RT, 0, s.st>>>(x, r, z, pv, q, minv, s.nc, s.nalm, p->d_mofidx,
                                                  p->d_scal, p->d_part);
-    if (s.lowl)
-        SHTG_TRY(lowl_apply<T>(p, reinterpret_cast<const T *>(r), reinterpret_cast<T *>(z), s.nb, s.per, p->d_part,
-                               s.st));
+    SHTG_TRY(precond_fix<T>(s, r, z));
     k_scal_beta<<<1, 1024, 0, s.st>>>(p->d_part, p->d_scal, s.nb);
     k_pupdate<C><<<dim3(grid_1d(s.per).x, s.nb), RT, 0, s.st>>>(pv, z, s.nc, s.nalm, p->d_scal);
     prof_end(p, s.st, 4);
@@ -860,9 +872,7 @@ static int pcg(Solve &s, const typename HT<T>::C *b, typename HT<T>::C *x, doubl
     k_update<T, true><<<s.rgrid, RT, 0, s.st>>>(nullptr, r, z, nullptr, nullptr, minv, s.nc, s.nalm,
                                                 p->d_mofidx, p->d_scal, p->d_part);
     SHTG_CHECK_LAUNCH("k_update init");
-    if (s.lowl)
-        SHTG_TRY(lowl_apply<T>(p, reinterpret_cast<const T *>(r), reinterpret_cast<T *>(z), s.nb, s.per, p->d_part,
-                               s.st));
+    SHTG_TRY(precond_fix<T>(s, r, z));
     k_scal_init<<<1, 1024, 0, s.st>>>(p->d_part, p->d_scal, s.nb, tol * tol);
     p->prof.launches += 2;
     SHTG_CHECK_LAUNCH("k_scal_init");
@@ -1137,9 +1147,7 @@ static int mixed_solve(Solve &s, const shtg_cg_opts &opt, const std::vector<doub
         else k_scale_vec<<<s.vgrid, RT, 0, st>>>(p32, s.per, d_sc + 2 * nb);
         k_update<float, true><<<s.rgrid, RT, 0, st>>>(nullptr, r32, z32, nullptr, nullptr, minv, s.nc,
                                                      s.nalm, p->d_mofidx, p->d_scal, p->d_part);
-        if (s.lowl)
-            SHTG_TRY(lowl_apply<float>(p, reinterpret_cast<const float *>(r32), reinterpret_cast<float *>(z32), nb,
-                                       s.per, p->d_part, st));
+        SHTG_TRY(precond_fix<float>(s, r32, z32));
         k_scal_reliable<<<1, 1024, 0, st>>>(p->d_part, p->d_scal, nb, d_sc + nb);
         p->prof.launches += first ? 3 : 4;
         SHTG_CHECK_LAUNCH("reliable update");
@@ -1192,6 +1200,42 @@ static int mixed_solve(Solve &s, const shtg_cg_opts &opt, const std::vector<doub
     return SHTG_OK;
 }
 
+// The low block or the azimuthal blocks, built for every system with the
+// first realization's C_l scale (for the others the preconditioner is still
+// symmetric positive definite, only not the exact block inverse).
+static int precond_setup(Solve &s, const shtg_cg_opts &opt, const shtg_problem *pr) {
+    s.pc = opt.precond;
+    const double isc = pr->cl_scale ? 1.0 / pr->cl_scale[0] : 1.0;
+    if (opt.precond == SHTG_PRECOND_LOWL) return lowl_setup(s.p, opt.lowl_lmax, s.nc, isc, s.st);
+    if (opt.precond == SHTG_PRECOND_AZIM) return az_setup(s.p, opt.block_lmax, s.nc, isc, s.st);
+    return SHTG_OK;
+}
+
+int precond_apply(Plan *p, const shtg_problem *pr, const shtg_cg_opts *o, const double *r, double *z,
+                  cudaStream_t st) {
+    SHTG_TRY(check_problem(p, pr));
+    if (!o || o->precond < SHTG_PRECOND_NONE || o->precond > SHTG_PRECOND_AZIM) {
+        set_error("precond must be SHTG_PRECOND_NONE, SHTG_PRECOND_DIAG, SHTG_PRECOND_LOWL or SHTG_PRECOND_AZIM");
+        return SHTG_ERR_ARG;
+    }
+    SHTG_TRY(setup_operator(p, pr, 0, o->precond, st));
+    Solve s = make_solve(p, pr->nbatch, pr->ncomp, st);
+    SHTG_TRY(precond_setup(s, *o, pr));
+    double2 *R = p->v64[2];
+    SHTG_CUDA(cudaMemcpyAsync(R, r, sizeof(double2) * (size_t)s.nvec, cudaMemcpyDeviceToDevice, st));
+    double2 *Z = reinterpret_cast<double2 *>(z);
+    k_update<double, true><<<s.rgrid, RT, 0, st>>>(nullptr, R, Z, nullptr, nullptr, p->d_minv64, s.nc, s.nalm,
+                                                   p->d_mofidx, p->d_scal, p->d_part);
+    SHTG_CHECK_LAUNCH("k_update");
+    p->prof.launches += 1;
+    if (s.pc == SHTG_PRECOND_LOWL)
+        SHTG_TRY(lowl_apply<double>(p, reinterpret_cast<const double *>(R), z, s.nb, s.per, p->d_part, st));
+    if (s.pc == SHTG_PRECOND_AZIM)
+        SHTG_TRY(az_apply<double>(p, reinterpret_cast<const double *>(R), z, s.nb, s.per, p->d_part, st, true));
+    SHTG_CUDA(cudaStreamSynchronize(st));
+    return SHTG_OK;
+}
+
 int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_opts *o,
               shtg_cg_stats *stats, cudaStream_t st) {
     SHTG_TRY(check_problem(p, pr));
@@ -1238,8 +1282,8 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
                     return SHTG_ERR_ARG;
                 }
     }
-    if (opt.precond < SHTG_PRECOND_NONE || opt.precond > SHTG_PRECOND_LOWL) {
-        set_error("precond must be SHTG_PRECOND_NONE, SHTG_PRECOND_DIAG or SHTG_PRECOND_LOWL");
+    if (opt.precond < SHTG_PRECOND_NONE || opt.precond > SHTG_PRECOND_AZIM) {
+        set_error("precond must be SHTG_PRECOND_NONE, SHTG_PRECOND_DIAG, SHTG_PRECOND_LOWL or SHTG_PRECOND_AZIM");
         return SHTG_ERR_ARG;
     }
     if (opt.fp64_arith != SHTG_ARITH_DEFAULT && opt.fp64_arith != SHTG_ARITH_FP64 &&
@@ -1276,13 +1320,7 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
         s.graphs = !(opt.flags & SHTG_NO_GRAPHS) && !(e && e[0] == '0');
     }
     SHTG_TRY(setup_operator(p, pr, host, opt.mode == SHTG_CG_BLOCK ? 0 : opt.precond, st, nb));
-    if (opt.precond == SHTG_PRECOND_LOWL && opt.mode != SHTG_CG_BLOCK) {
-        // one low block for every system, built with the first realization's
-        // C_l scale (for the others it is still a symmetric positive definite
-        // preconditioner, only not the exact block inverse)
-        SHTG_TRY(lowl_setup(p, opt.lowl_lmax, nc, pr->cl_scale ? 1.0 / pr->cl_scale[0] : 1.0, st));
-        s.lowl = 1;
-    }
+    if (opt.mode != SHTG_CG_BLOCK) SHTG_TRY(precond_setup(s, opt, pr));
     const double ts = now_ms();
     double2 *B = p->v64[0], *X = p->v64[1], *R = p->v64[2], *Tt = p->v64[6];
     // ---- RHS: B Y^T (N^-1 d + N^-1/2 w2) + S^-1/2 w1 in FP64; split: the

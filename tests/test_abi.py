@@ -69,7 +69,8 @@ def test_binding_constants_match_header():
              "PROFILE": "SHTG_PROFILE", "NO_GRAPHS": "SHTG_NO_GRAPHS", "SPLIT_RHS": "SHTG_SPLIT_RHS",
              "SPIN0": "SHTG_SPIN0",
              "SPIN2": "SHTG_SPIN2", "PRECOND_NONE": "SHTG_PRECOND_NONE",
-             "PRECOND_DIAG": "SHTG_PRECOND_DIAG", "PRECOND_LOWL": "SHTG_PRECOND_LOWL"}
+             "PRECOND_DIAG": "SHTG_PRECOND_DIAG", "PRECOND_LOWL": "SHTG_PRECOND_LOWL",
+             "PRECOND_AZIM": "SHTG_PRECOND_AZIM"}
     for py, c in pairs.items():
         assert getattr(N, py) == defs[c], (py, c)
     end = src.index("} shtg_cg_opts;")
@@ -120,6 +121,7 @@ def test_transform_and_solver_calls_reject_null_plans_without_gpu():
     assert lib.shtg_apply_operator(None, ctypes.byref(pr), buf, buf, None) == -1
     nn = ctypes.c_int(0)
     assert lib.shtg_lowl_block(None, ctypes.byref(pr), 0, buf, buf, ctypes.byref(nn), None) == -1
+    assert lib.shtg_precond_apply(None, ctypes.byref(pr), ctypes.byref(o), buf, buf, None) == -1
     info = N.PlanInfo()
     assert lib.shtg_plan_get_info(None, ctypes.byref(info)) == -1
     assert lib.shtg_plan_destroy(None) == N.SHTG_OK
