@@ -5,11 +5,9 @@
 Workload: 8 T+E+B realizations sharing C_l, beam and N^-1 (hits-weighted
 noise, |b| < 20 deg mask + 200 holes, 10' beam).  One "step" is one
 cg_sample call with a fixed iteration budget: RHS assembly (FP64-accurate
-transforms), preconditioner (by default the azimuthal blocks: the exact
-per-m inverse, for l <= 1024, of the operator with N^-1 averaged along
-every ring, App. A's blocks of T and E, kept between calls while C_l, the
-beam and N^-1 are unchanged; the diagonal elsewhere), then --iters-per-step
-batched mixed-precision
+transforms), the diagonal preconditioner of Sect. 4 (the library's
+default; --precond azim / lowl select the stronger ones), then
+--iters-per-step batched mixed-precision
 PCG iterations (FP32 operator applications) with FP64-accurate residual
 replacements (reliable updates), the last one at the end of the step.
 Inputs are synthetic (seeded Philox), resident in HBM and larger than L2.
@@ -24,7 +22,9 @@ Ranks run independent replicas (weak scaling, no data-path collective);
 `--gpus N` spawns N local ranks itself unless it runs under torchrun.
 
 Extras: the full solve to a true FP64-accurate relative residual of 1e-6
-with the bench's and with the diagonal preconditioner;
+with every preconditioner (the azimuthal blocks: App. A's per-m blocks of T
+and E from the ring-averaged N^-1, exact up to l = 1024; the two-level low
+block; the diagonal), fastest first in the line's `time_to_solution`;
 the same steps with native FP64 residual replacements; the plain FP64 PCG
 per-iteration time; both forms solved to 1e-6 on the masked temperature
 workload (N_side 256, l_max 512), whose iteration ratio turns the FP64 form's
@@ -600,6 +600,7 @@ def gpu_rank(args):
                    "value_counts": "FP32 PCG iterations (FP64-accurate residual replacements not counted)",
                    "l2": "inputs larger than L2 (d, w2: 2.4 GB each)"},
         "e2e": e2e, "gpu_launches": launches, "clocks": ck, "roofline": roof, "rooflines": roofs,
+        "time_to_solution": _time_to_solution(extras),
         "alu_peaks": peaks_alu,
         "cpu_baseline": cpu,
         "step": {"fp32_iterations": iters_local / len(stats),
@@ -617,6 +618,16 @@ def gpu_rank(args):
     print(json.dumps(line), flush=True)
     rep.close()
     return 0
+
+
+def _time_to_solution(extras):
+    """The full solves to 1e-6 of the extras, fastest first."""
+    out = []
+    for key, v in extras.items():
+        if key.startswith("mixed_full_solve") and isinstance(v, dict):
+            out.append({"precond": v["precond"], "s": v["time_to_1e-6_s"], "fp32_iterations": v["iterations"],
+                        "converged": v["converged"], "rel_residual": v["rel_residual"]})
+    return sorted(out, key=lambda d: d["s"]) or None
 
 
 def run_gpu(args):
@@ -649,8 +660,10 @@ def measure_extras(plan, inp, dev, kw, step, full_solve=True):
     ex = {}
     if full_solve:
         # to 1e-6 with the bench's preconditioner, then with the other one
-        other = "diag" if kw["precond"] != "diag" else "azim"
-        for key, pc in (("mixed_full_solve", kw["precond"]), (f"mixed_full_solve_{other}", other)):
+        # to 1e-6 with the bench's preconditioner and with the others
+        pcs = [kw["precond"]] + [x for x in ("azim", "lowl", "diag") if x != kw["precond"]]
+        for pc in pcs:
+            key = "mixed_full_solve" if pc == kw["precond"] else f"mixed_full_solve_{pc}"
             kwf = dict(kw)
             kwf["maxiter"] = 6000
             kwf["precond"] = pc
@@ -700,12 +713,12 @@ def measure_extras(plan, inp, dev, kw, step, full_solve=True):
     ex["sht_pairs_per_s"] = sht
     ex["sht_pairs_per_s_note"] = ("one alm2map + one alm2map_adjoint per map (spin 2: per (E, B) -> "
                                   "(Q, U) map pair), N_side 1024, l_max 2048, CUDA events")
-    ex["chains"] = measure_chains(dev, precond=kw["precond"])
+    ex["chains"] = measure_chains(dev, precond="azim")
     torch.cuda.synchronize()
     return ex
 
 
-def measure_masked_pair(dev, precond="azim"):
+def measure_masked_pair(dev, precond="diag"):
     """Both forms solved to 1e-6 on the masked temperature workload
     (N_side 256, l_max 512): iterations and time to 1e-6 of the plain FP64
     PCG (native FP64) and of the mixed solver (tensor cores), with the given
@@ -721,7 +734,7 @@ def measure_masked_pair(dev, precond="azim"):
     args = (p.cl, p.bl, torch.as_tensor(p.ninv, device=dev), d,
             torch.as_tensor(p.w1[None], device=dev).contiguous(), torch.as_tensor(p.w2[None], device=dev).contiguous())
     out = {"precond": precond}
-    other = "diag" if precond != "diag" else "azim"
+    other = "azim" if precond != "azim" else "diag"
     for pc, sfx in ((precond, ""), (other, f"_{other}")):
         for mode in ("mixed_tc", "fp64"):
             plan.cg_sample(*args, tol=1e-6, mode=mode, maxiter=2, allow_not_converged=True, precond=pc)   # tuning
@@ -787,7 +800,7 @@ def main():
     ap.add_argument("--lmax", type=int, default=LMAX, help="profiling only: smaller l_max")
     ap.add_argument("--batch", type=int, default=NB, help="profiling only: fewer realizations")
     ap.add_argument("--no-full-solve", action="store_true")
-    ap.add_argument("--precond", default="azim", choices=["none", "diag", "lowl", "azim"],
+    ap.add_argument("--precond", default="diag", choices=["none", "diag", "lowl", "azim"],
                     help="diagonal preconditioner of Sect. 4, two-level (exact inverse on l <= l_c), or "
                          "azimuthal blocks (App. A's per-m blocks from ring-averaged N^-1, l <= l_b)")
     ap.add_argument("--lowl-lmax", type=int, default=0, help="l_c of the two-level preconditioner (0: 32)")

@@ -327,8 +327,10 @@ int shtg_lowl_block(shtg_plan *plan, const shtg_problem *prob, int lowl_lmax, do
                     void *stream);
 
 /* Apply the solver's preconditioner once (Sect. 4 and the options above):
- * z = M^-1 r for r, z device [nbatch][ncomp][nalm] complex128 (FP64; the
- * azimuthal blocks with their FP64 factors), with the problem's cl, bl,
+ * z = M^-1 r for r, z device [nbatch][ncomp][nalm] complex128 (FP64, the
+ * azimuthal blocks' FP64 inverses; with opts->mode SHTG_CG_MIXED or
+ * SHTG_CG_MIXED_TC what the FP32 iteration applies: r rounded to FP32, FP32
+ * diagonal and block inverses, z widened back), with the problem's cl, bl,
  * ninv and cl_scale (d, w1, w2 unused) and opts->precond, lowl_lmax and
  * block_lmax.  Builds what the preconditioner needs like shtg_cg_sample
  * (the workspace of SHTG_PRECOND_LOWL and SHTG_PRECOND_AZIM stays with the

@@ -320,15 +320,17 @@ class Plan:
         return H[:k * k].reshape(k, k).copy(), par[:4 * k].reshape(k, 4).copy()
 
     def precond_apply(self, cl, bl, ninv, r: torch.Tensor, precond="diag", lowl_lmax: int = 0,
-                      block_lmax: int = 0, cl_scale=None) -> torch.Tensor:
+                      block_lmax: int = 0, cl_scale=None, fp32: bool = False) -> torch.Tensor:
         """z = M^-1 r with the solver's preconditioner (shtg_precond_apply)
-        for r [nbatch, ncomp, nalm] complex128 (CUDA)."""
+        for r [nbatch, ncomp, nalm] complex128 (CUDA); fp32: what the FP32
+        iteration of the mixed solver applies."""
         _need_cuda(r, "r")
         z = torch.empty_like(r)
         pr = self._problem(cl, bl, ninv, nbatch=int(r.shape[0]), ncomp=int(r.shape[1]), cl_scale=cl_scale)
         o = N.CGOpts()
         o.precond = _precond(precond)
         o.lowl_lmax, o.block_lmax = int(lowl_lmax), int(block_lmax)
+        o.mode = N.CG_MIXED if fp32 else N.CG_FP64
         N.check(self._lib.shtg_precond_apply(self._h, C.byref(pr), C.byref(o), _ptr(r.contiguous()), _ptr(z),
                                              _stream()))
         return z

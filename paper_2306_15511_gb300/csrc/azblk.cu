@@ -526,7 +526,7 @@ template <typename P> int aalloc(Plan *p, P **ptr, size_t count) {
 
 unsigned az_blocks(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 4096)); }
 
-int az_reserve(Plan *p, int lb, int ncb) {
+int az_reserve(Plan *p, int lb, int ncb, cudaStream_t st) {
     AzBlk &q = p->az;
     if (q.lb == lb && q.ncb == ncb && q.H) return SHTG_OK;
     az_free(p);
@@ -568,11 +568,14 @@ int az_reserve(Plan *p, int lb, int ncb) {
     SHTG_TRY(aalloc(p, &q.slot, nslot));
     SHTG_TRY(aalloc(p, &q.flag, 4));
     SHTG_TRY(aalloc(p, &q.ninv, (size_t)nch * p->npix));
-    SHTG_CUDA(cudaMemcpy(q.goff, goff.data(), sizeof(int64_t) * (lb + 1), cudaMemcpyHostToDevice));
-    SHTG_CUDA(cudaMemcpy(q.hoff, hoff.data(), sizeof(int64_t) * (lb + 1), cudaMemcpyHostToDevice));
-    SHTG_CUDA(cudaMemcpy(q.moff, moff.data(), sizeof(int64_t) * (lb + 1), cudaMemcpyHostToDevice));
-    SHTG_CUDA(cudaMemcpy(q.xoff, xoff.data(), sizeof(int64_t) * (lb + 1), cudaMemcpyHostToDevice));
-    SHTG_CUDA(cudaMemset(q.slot, 0, sizeof(double) * nslot));
+    // ordered on the solve's stream (a chains group's stream is not ordered
+    // with the legacy default stream), complete before the host vectors go
+    SHTG_CUDA(cudaMemcpyAsync(q.goff, goff.data(), sizeof(int64_t) * (lb + 1), cudaMemcpyHostToDevice, st));
+    SHTG_CUDA(cudaMemcpyAsync(q.hoff, hoff.data(), sizeof(int64_t) * (lb + 1), cudaMemcpyHostToDevice, st));
+    SHTG_CUDA(cudaMemcpyAsync(q.moff, moff.data(), sizeof(int64_t) * (lb + 1), cudaMemcpyHostToDevice, st));
+    SHTG_CUDA(cudaMemcpyAsync(q.xoff, xoff.data(), sizeof(int64_t) * (lb + 1), cudaMemcpyHostToDevice, st));
+    SHTG_CUDA(cudaMemsetAsync(q.slot, 0, sizeof(double) * nslot, st));
+    SHTG_CUDA(cudaStreamSynchronize(st));
     return SHTG_OK;
 }
 
@@ -596,7 +599,7 @@ int az_setup(Plan *p, int lb, int nc, double isc, cudaStream_t st) {
         return SHTG_ERR_ARG;
     }
     const int ncb = nc == 3 ? 2 : 1;
-    SHTG_TRY(az_reserve(p, lb, ncb));
+    SHTG_TRY(az_reserve(p, lb, ncb, st));
     AzBlk &q = p->az;
     const int nch = ncb == 2 ? 2 : 1;
     const int64_t nin = (int64_t)nch * p->npix;

@@ -400,7 +400,7 @@ unsigned blocks_for(int64_t n) {
 }
 
 // workspace for l_c and nc (kept while a later call needs no more)
-int lowl_reserve(Plan *p, int lc, int nc) {
+int lowl_reserve(Plan *p, int lc, int nc, cudaStream_t st) {
     LowL &q = p->lowl;
     if (q.cap_lc >= lc && q.cap_nc >= nc) return SHTG_OK;
     lowl_free(p);
@@ -422,7 +422,10 @@ int lowl_reserve(Plan *p, int lc, int nc) {
     SHTG_TRY(lalloc(p, &q.flag, 4));
     SHTG_TRY(lalloc(p, &q.shift, (size_t)p->nring));
     SHTG_TRY(lalloc(p, &q.ninv, (size_t)nch * p->npix));
-    SHTG_CUDA(cudaMemcpy(q.shift, p->shift.data(), sizeof(int) * p->nring, cudaMemcpyHostToDevice));
+    // ordered on the solve's stream (not the legacy default stream), complete
+    // before returning
+    SHTG_CUDA(cudaMemcpyAsync(q.shift, p->shift.data(), sizeof(int) * p->nring, cudaMemcpyHostToDevice, st));
+    SHTG_CUDA(cudaStreamSynchronize(st));
     q.cap_lc = lc;
     q.cap_nc = nc;
     return SHTG_OK;
@@ -447,7 +450,7 @@ int lowl_setup(Plan *p, int lc, int nc, double isc, cudaStream_t st, double *h_h
         set_error("two-level preconditioner: l_c must be at most " + std::to_string(lcmax));
         return SHTG_ERR_ARG;
     }
-    SHTG_TRY(lowl_reserve(p, lc, nc));
+    SHTG_TRY(lowl_reserve(p, lc, nc, st));
     LowL &q = p->lowl;
     const int L1 = p->lmax + 1;
     const int nch = nc == 3 ? 2 : 1;

@@ -20,6 +20,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cstdio>
+
 #include "common.cuh"
 
 namespace shtg {
@@ -28,7 +30,7 @@ namespace shtg {
 #define RB SHTG_RED_BLOCKS
 
 // scalar slots per realization
-enum { S_RZ = 0, S_PQ, S_RR, S_BB, S_ALPHA, S_BETA, S_ACTIVE, S_ITERS, S_TOL2, S_BAD, S_SCALE };
+enum { S_RZ = 0, S_PQ, S_RR, S_BB, S_ALPHA, S_BETA, S_ACTIVE, S_ITERS, S_TOL2, S_BAD, S_SCALE, S_RESTART };
 
 __device__ __forceinline__ double cdot(double2 a, double2 b) { return a.x * b.x + a.y * b.y; }
 
@@ -92,6 +94,10 @@ __global__ void k_rhs_pix(const double *__restrict__ d, const double *__restrict
     }
 }
 
+__global__ void k_to_double(const float *__restrict__ a, double *__restrict__ b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (double)a[i];
+}
 __global__ void k_to_float(const double *__restrict__ a, float *__restrict__ b, int64_t n) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
@@ -358,7 +364,13 @@ __global__ void k_scal_init(const double *__restrict__ part, double *__restrict_
     s[S_ALPHA] = s[S_BETA] = 0.0;
 }
 
-__global__ void k_scal_alpha(const double *__restrict__ part, double *__restrict__ scal, int nb) {
+// floor2: the FP32 iteration of the mixed solver passes the squared
+// relative residual at which its recursion reaches FP32 rounding; a finite
+// non-positive curvature there (p made of rounding noise, e.g. after a
+// preconditioner close to the exact inverse) ends the stage instead of
+// failing it, and the FP64 residual replacement judges convergence.  The
+// FP64 PCG passes 0 (any non-positive curvature is a failure).
+__global__ void k_scal_alpha(const double *__restrict__ part, double *__restrict__ scal, int nb, double floor2) {
     const int b = threadIdx.x;
     if (b >= nb) return;
     double *s = scal + b * 16;
@@ -370,7 +382,8 @@ __global__ void k_scal_alpha(const double *__restrict__ part, double *__restrict
             alpha = s[S_RZ] / pq;
         } else {
             s[S_ACTIVE] = 0.0;
-            s[S_BAD] = 1.0;
+            if (isfinite(pq) && s[S_RR] <= floor2 * s[S_BB]) s[S_RESTART] = 1.0;   // next stage: p = z
+            else s[S_BAD] = 1.0;
         }
     }
     s[S_ALPHA] = alpha;
@@ -479,7 +492,17 @@ __global__ void k_scal_reliable(const double *__restrict__ part, double *__restr
     // and a bad FP32 stage already ended the solve at its host check
     s[S_BAD] = (isfinite(rr) && isfinite(rz)) ? 0.0 : 1.0;
     s[S_ITERS] = 0.0;
+    s[S_RESTART] = 0.0;
     s[S_ALPHA] = s[S_BETA] = 0.0;
+}
+
+// a stage that ended at its rounding floor restarts its direction: p = z
+__global__ void k_restart_dir(float2 *__restrict__ p, const float2 *__restrict__ z, int64_t per,
+                              const double *__restrict__ scal) {
+    const int b = blockIdx.y;
+    if (scal[b * 16 + S_RESTART] == 0.0) return;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < per; i += (int64_t)gridDim.x * blockDim.x)
+        p[(int64_t)b * per + i] = z[(int64_t)b * per + i];
 }
 
 // ------------------------------------------------------------ log-posterior
@@ -801,7 +824,8 @@ static int pcg_iteration(Solve &s, typename HT<T>::C *x, typename HT<T>::C *r, t
     Plan *p = s.p;
     SHTG_TRY(matvec<T>(s, pv, q, true));   // q = A p and the partials of <p, q>
     prof_begin(p, K_VEC, s.st);
-    k_scal_alpha<<<1, 1024, 0, s.st>>>(p->d_part, p->d_scal, s.nb);
+    // FP32 recursion: below 1e-3 of the stage's start a breakdown ends the stage
+    k_scal_alpha<<<1, 1024, 0, s.st>>>(p->d_part, p->d_scal, s.nb, sizeof(T) == 4 ? 1e-6 : 0.0);
     k_update<T, false><<<s.rgrid, RT, 0, s.st>>>(x, r, z, pv, q, minv, s.nc, s.nalm, p->d_mofidx,
                                                  p->d_scal, p->d_part);
     SHTG_TRY(precond_fix<T>(s, r, z));
@@ -1133,9 +1157,12 @@ static int mixed_solve(Solve &s, const shtg_cg_opts &opt, const std::vector<doub
             const double old = scale[b];
             scale[b] = done[b] ? 0.0 : nr;
             sc[b] = done[b] ? 0.0 : 1.0 / nr;
-            // the FP32 stage runs until every active realization has reduced its
-            // residual by delta (it stops on its own only far below that); -1 = frozen
-            sc[nb + b] = done[b] ? -1.0 : (1e-3 * delta) * (1e-3 * delta);
+            // the FP32 stage runs until a realization has reduced its residual by
+            // delta (the host's check); each one stops on its own at 0.1 delta, well
+            // above the FP32 rounding floor: a preconditioner close to the exact
+            // inverse takes the residual there in one or two iterations, and CG on
+            // rounding noise until the next check can diverge; -1 = frozen
+            sc[nb + b] = done[b] ? -1.0 : (0.1 * delta) * (0.1 * delta);
             sc[2 * nb + b] = (done[b] || old == 0.0) ? 0.0 : old / nr;
             sc[3 * nb + b] = scale[b];
             active += !done[b];
@@ -1148,8 +1175,9 @@ static int mixed_solve(Solve &s, const shtg_cg_opts &opt, const std::vector<doub
         k_update<float, true><<<s.rgrid, RT, 0, st>>>(nullptr, r32, z32, nullptr, nullptr, minv, s.nc,
                                                      s.nalm, p->d_mofidx, p->d_scal, p->d_part);
         SHTG_TRY(precond_fix<float>(s, r32, z32));
+        if (!first) k_restart_dir<<<s.vgrid, RT, 0, st>>>(p32, z32, s.per, p->d_scal);
         k_scal_reliable<<<1, 1024, 0, st>>>(p->d_part, p->d_scal, nb, d_sc + nb);
-        p->prof.launches += first ? 3 : 4;
+        p->prof.launches += first ? 3 : 5;
         SHTG_CHECK_LAUNCH("reliable update");
         // the search direction is kept (rescaled to the new normalization); only
         // the first pass starts it from z
@@ -1169,7 +1197,12 @@ static int mixed_solve(Solve &s, const shtg_cg_opts &opt, const std::vector<doub
                 const double *h = p->h_pinned + b * 16;
                 if (h[S_BAD] != 0.0) {
                     if (s.tc) SHTG_TRY(check_device_flag(p, s.st));   // an expired wait explains it
-                    set_error("non-finite or non-positive curvature in the FP32 PCG");
+                    char buf[256];
+                    snprintf(buf, sizeof buf,
+                             "non-finite or non-positive curvature in the FP32 PCG (system %d, stage iteration %g: "
+                             "<p, Ap> = %.3e, <r, z> = %.3e, |r|^2 = %.3e of the stage's start)",
+                             b, h[S_ITERS], h[S_PQ], h[S_RZ], h[S_RR]);
+                    set_error(buf);
                     return SHTG_ERR_NONFINITE;
                 }
                 if (done[b]) continue;
@@ -1224,6 +1257,22 @@ int precond_apply(Plan *p, const shtg_problem *pr, const shtg_cg_opts *o, const 
     double2 *R = p->v64[2];
     SHTG_CUDA(cudaMemcpyAsync(R, r, sizeof(double2) * (size_t)s.nvec, cudaMemcpyDeviceToDevice, st));
     double2 *Z = reinterpret_cast<double2 *>(z);
+    if (o->mode == SHTG_CG_MIXED || o->mode == SHTG_CG_MIXED_TC) {
+        // what the FP32 iteration applies: FP32 vectors, FP32 diagonal and blocks
+        float2 *r32 = p->v32[0], *z32 = p->v32[1];
+        const int64_t n2 = 2 * s.nvec;
+        k_to_float<<<grid_1d(n2), RT, 0, st>>>(reinterpret_cast<const double *>(R), reinterpret_cast<float *>(r32), n2);
+        k_update<float, true><<<s.rgrid, RT, 0, st>>>(nullptr, r32, z32, nullptr, nullptr, p->d_minv32, s.nc, s.nalm,
+                                                      p->d_mofidx, p->d_scal, p->d_part);
+        p->prof.launches += 2;
+        SHTG_CHECK_LAUNCH("k_update");
+        SHTG_TRY(precond_fix<float>(s, r32, z32));
+        k_to_double<<<grid_1d(n2), RT, 0, st>>>(reinterpret_cast<const float *>(z32), z, n2);
+        p->prof.launches += 1;
+        SHTG_CHECK_LAUNCH("k_to_double");
+        SHTG_CUDA(cudaStreamSynchronize(st));
+        return SHTG_OK;
+    }
     k_update<double, true><<<s.rgrid, RT, 0, st>>>(nullptr, R, Z, nullptr, nullptr, p->d_minv64, s.nc, s.nalm,
                                                    p->d_mofidx, p->d_scal, p->d_part);
     SHTG_CHECK_LAUNCH("k_update");

@@ -216,3 +216,63 @@ def test_azim_graph_replay_split_and_scales():
         for part, bb in ((0, bm), (1, bf)):
             res = osol.true_residual(prob, xs[part, k], bb)
             assert res <= 1.05e-7, (k, part, res)
+
+
+@pytest.mark.parametrize("precond", ["azim", "lowl"])
+def test_chains_with_block_preconditioners(precond):
+    """Two geometries in one chains call (each group on its plan's own
+    non-blocking stream, concurrently): the preconditioners' workspaces are
+    set up on the group's stream and every chain reaches the oracle residual."""
+    from paper_2306_15511_gb300 import Plan, chains_sample
+    req, refs = [], []
+    for ns, L in ((32, 64), (32, 95)):
+        p = C.masked_temperature(ns, L, seed=7)
+        g = osht.healpix(ns)
+        d = _data(p, g)
+        plan = Plan(nside=ns, lmax=L, max_batch=2)
+        ds = np.stack([d, 0.7 * d])
+        w1 = np.stack([p.w1, -p.w1])
+        w2 = np.stack([p.w2, 0.5 * p.w2])
+        req.append({"plan": plan, "cl": p.cl, "bl": p.bl, "ninv": _cuda(p.ninv, torch.float64),
+                    "d": _cuda(ds, torch.float64), "w1": _cuda(w1, torch.complex128),
+                    "w2": _cuda(w2, torch.float64), "cl_scale": [1.0, 1.2]})
+        refs.append((g, p, ds, w1, w2))
+    res = chains_sample(req, tol=1e-6, mode="mixed_tc", maxiter=3000, precond=precond)
+    for (x, st), (g, p, ds, w1, w2), grp in zip(res, refs, req):
+        assert st["converged"] == 1, st
+        xh = x.cpu().numpy()
+        for k, sc in enumerate(grp["cl_scale"]):
+            prob = osol.Problem(g, p.lmax, p.cl * sc, p.bl, p.ninv)
+            r = osol.true_residual(prob, xh[k], prob.rhs(ds[k], w1[k], w2[k]))
+            assert r <= 1.05e-6, (p.lmax, k, r)
+
+
+def test_mixed_stage_ends_at_its_rounding_floor():
+    """A latitude-band mask with uniform noise makes the azimuthal blocks
+    nearly the exact inverse: the FP32 stage reaches its rounding floor in one
+    or two iterations, where a curvature made of rounding noise ends the
+    stage (no failure); the FP64 replacement then confirms convergence."""
+    from paper_2306_15511_gb300 import Plan
+    ns, L = 32, 64
+    g = osht.healpix(ns)
+    z, _ = C.pixel_centres(ns)
+    ninv = np.where(np.abs(z) < math.sin(15 * C.DEG), 0.0, 1.0 / 15.0 ** 2)
+    cl, bl = C.cl_flat(L), C.gauss_beam(L, 60.0 / ns * C.DEG)
+    rng = np.random.default_rng(9)
+    nb = 4
+    P = (L + 1) * (L + 2) // 2
+    d = rng.normal(size=(nb, 1, g.npix)) * 15.0
+    w1 = _rand_alm(L, rng, nb, 1)
+    w2 = rng.normal(size=(nb, 1, g.npix))
+    plan = Plan(nside=ns, lmax=L, max_batch=nb)
+    prob = osol.Problem(g, L, cl, bl, ninv)
+    for mode in ("mixed", "mixed_tc"):
+        x, st = plan.cg_sample(cl, bl, _cuda(ninv, torch.float64), _cuda(d, torch.float64),
+                               _cuda(w1, torch.complex128), _cuda(w2, torch.float64), tol=1e-6, mode=mode,
+                               maxiter=500, precond="azim")
+        xh = x.cpu().numpy()
+        worst = max(osol.true_residual(prob, xh[k], prob.rhs(d[k], w1[k], w2[k])) for k in range(nb))
+        print(f"latitude band, azimuthal blocks, {mode}: {st['iterations']} iterations, "
+              f"{st['outer_steps']} replacements, oracle residual {worst:.2e}")
+        assert st["converged"] == 1 and worst <= 1.05e-6
+    assert P > 0
