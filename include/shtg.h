@@ -117,6 +117,9 @@ extern "C" {
                                         replaying one captured iteration as a CUDA graph (graphs are
                                         also off with SHTG_PROFILE, or with SHTG_GRAPHS=0 in the
                                         environment); results are identical either way */
+#define SHTG_GROUPED 16              /* cg_sample_chains flag: run the FP32 PCG iterations of all
+                                        groups together, each stage one launch over the work of every
+                                        geometry (see shtg_cg_sample_chains) */
 
 typedef struct shtg_plan shtg_plan;
 
@@ -296,7 +299,24 @@ int shtg_cg_sample(shtg_plan *plan, const shtg_problem *prob, double *alm_out,
  * converged stop updating while the others go on.  stats: [ngroups] or
  * NULL.  Returns the first error other than SHTG_ERR_NOT_CONVERGED, else
  * SHTG_ERR_NOT_CONVERGED if a group did not converge, else SHTG_OK; the
- * error string names the group. */
+ * error string names the group.
+ *
+ * With SHTG_GROUPED in opts->flags (batching of chains of uneven N_side and
+ * l_max in one launch per stage): the groups run in lockstep on `stream`
+ * instead of concurrently, and every stage of their FP32 PCG iteration is one
+ * kernel launch over the work of all groups (Legendre synthesis and transpose
+ * on the CUDA cores, the prior, the CG scalar and vector updates, the
+ * azimuthal blocks; the ring stage is one launch per transform-length class,
+ * at most five), replayed as one CUDA graph; a group whose realizations have
+ * all converged is skipped on the device.  The FP64-accurate steps (the
+ * right-hand sides, each group's residual replacements) stay per group.
+ * Needs 1 <= ngroups <= 16, non-null opts with mode SHTG_CG_MIXED or
+ * SHTG_CG_MIXED_TC (both run the CUDA-core FP32 Legendre sums here),
+ * precond SHTG_PRECOND_NONE, SHTG_PRECOND_DIAG or SHTG_PRECOND_AZIM, the
+ * same ncomp in every group and neither SHTG_SPLIT_RHS nor SHTG_PROFILE;
+ * otherwise SHTG_ERR_ARG.  Uses each plan's workspace and d_flag slot as the
+ * plain call does; allocates nothing beyond what the chosen preconditioner
+ * allocates in a plain call. */
 int shtg_cg_sample_chains(int ngroups, shtg_plan *const *plans, const shtg_problem *problems,
                           double *const *alm_out, const shtg_cg_opts *opts, shtg_cg_stats *stats,
                           void *stream);

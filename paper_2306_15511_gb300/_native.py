@@ -22,6 +22,7 @@ HOST_INPUTS = 1
 PROFILE = 2
 NO_GRAPHS = 4
 SPLIT_RHS = 8
+GROUPED = 16
 GRAD_COMPONENTS = 1
 PRECOND_NONE, PRECOND_DIAG, PRECOND_LOWL, PRECOND_AZIM = 0, 1, 2, 3
 

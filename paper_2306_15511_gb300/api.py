@@ -393,13 +393,15 @@ def fma_peak(precision: str = "fp32"):
 def chains_sample(groups, tol: float = 1e-6, mode: str = "mixed_tc", maxiter: int = 4000,
                   precond=True, reliable_delta: float = 1e-2, check_every: int = 4,
                   allow_not_converged: bool = False, graphs: bool = True, fp64_arith: str = "default",
-                  lowl_lmax: int = 0, block_lmax: int = 0):
+                  lowl_lmax: int = 0, block_lmax: int = 0, grouped: bool = False):
     """Constrained realizations of many chains of uneven geometry in one call.
 
     groups: list of dicts, one per geometry, with keys plan, cl, bl, ninv, d,
     w1, w2 (CUDA tensors shaped as for Plan.cg_sample) and optionally
     cl_scale (one amplitude per realization of the group).  Every group needs
-    its own Plan.  Returns a list of (alm, stats) per group."""
+    its own Plan.  grouped=True runs every stage of the FP32 iteration as one
+    launch over all groups (SHTG_GROUPED) instead of the groups concurrently
+    on their plans' streams.  Returns a list of (alm, stats) per group."""
     if not groups:
         raise ValueError("no groups")
     lib = N.load()
@@ -432,7 +434,7 @@ def chains_sample(groups, tol: float = 1e-6, mode: str = "mixed_tc", maxiter: in
     o.lowl_lmax, o.block_lmax = int(lowl_lmax), int(block_lmax)
     o.reliable_delta, o.fp64_arith = float(reliable_delta), _arith(fp64_arith)
     o.check_every = int(check_every)
-    o.flags = 0 if graphs else N.NO_GRAPHS
+    o.flags = (0 if graphs else N.NO_GRAPHS) | (N.GROUPED if grouped else 0)
     rc = lib.shtg_cg_sample_chains(n, plans, probs, outs, C.byref(o), stats, _stream())
     N.check(rc, allow=(-3,) if allow_not_converged else ())
     del keep

@@ -368,9 +368,9 @@ __global__ void __launch_bounds__(256) k_az_minv(int lb, int ncb, const int64_t 
 // = r at row j (component j / k, l = m + j % k) of right-hand side q = 2 b +
 // part (m = 0: q = b, real parts); grid (m, q), threads over the rows.
 template <typename T, typename TF>
-__global__ void k_az_gather(int lb, int ncb, int lmax, int nb, const int64_t *__restrict__ xoff,
-                            const T *__restrict__ r, int64_t nalm, int64_t per, TF *__restrict__ Xg) {
-    const int m = blockIdx.x, q = blockIdx.y;
+__device__ __forceinline__ void az_gather_cta(int lb, int ncb, int lmax, int nb, const int64_t *__restrict__ xoff,
+                                              const T *__restrict__ r, int64_t nalm, int64_t per,
+                                              TF *__restrict__ Xg, const int m, const int q) {
     const int nparts = m ? 2 : 1;
     if (q >= nb * nparts) return;
     const int k = lb + 1 - m, n = ncb * k;
@@ -381,6 +381,11 @@ __global__ void k_az_gather(int lb, int ncb, int lmax, int nb, const int64_t *__
         const T *src = r + 2 * ((int64_t)b * per + (int64_t)c * nalm + base) + part;
         for (int ll = threadIdx.x; ll < k; ll += blockDim.x) dst[c * k + ll] = (TF)src[2 * (int64_t)ll];
     }
+}
+template <typename T, typename TF>
+__global__ void k_az_gather(int lb, int ncb, int lmax, int nb, const int64_t *__restrict__ xoff,
+                            const T *__restrict__ r, int64_t nalm, int64_t per, TF *__restrict__ Xg) {
+    az_gather_cta<T, TF>(lb, ncb, lmax, nb, xoff, r, nalm, per, Xg, blockIdx.x, blockIdx.y);
 }
 
 // z <- M^-1 r on the block rows, as a tall-skinny product Z = M X per m
@@ -397,15 +402,15 @@ __global__ void k_az_gather(int lb, int ncb, int lmax, int nb, const int64_t *__
 // zero).
 constexpr int MR = 128, KT = 32;
 template <typename T, typename TF>
-__global__ void __launch_bounds__(128) k_az_mapply(int lb, int ncb, int lmax, int nb, int ntile,
-                                                   const int64_t *__restrict__ moff, const TF *__restrict__ M,
-                                                   const int64_t *__restrict__ xoff, const TF *__restrict__ Xg,
-                                                   const T *__restrict__ r, T *__restrict__ z, int64_t nalm,
-                                                   int64_t per, double *__restrict__ slot) {
+__device__ __forceinline__ void az_mapply_cta(int lb, int ncb, int lmax, int nb, int ntile,
+                                              const int64_t *__restrict__ moff, const TF *__restrict__ M,
+                                              const int64_t *__restrict__ xoff, const TF *__restrict__ Xg,
+                                              const T *__restrict__ r, T *__restrict__ z, int64_t nalm,
+                                              int64_t per, double *__restrict__ slot, const int m,
+                                              const int tile) {
     __shared__ __align__(16) TF As[KT][MR];
     __shared__ __align__(16) TF Xs[KT][16];
     __shared__ double sred[16][33];
-    const int m = blockIdx.x, tile = blockIdx.y;
     const int k = lb + 1 - m, n = ncb * k;
     const int i0 = tile * MR;
     if (i0 >= n) return;
@@ -485,12 +490,21 @@ __global__ void __launch_bounds__(128) k_az_mapply(int lb, int ncb, int lmax, in
         __syncthreads();
     }
 }
+template <typename T, typename TF>
+__global__ void __launch_bounds__(128) k_az_mapply(int lb, int ncb, int lmax, int nb, int ntile,
+                                                   const int64_t *__restrict__ moff, const TF *__restrict__ M,
+                                                   const int64_t *__restrict__ xoff, const TF *__restrict__ Xg,
+                                                   const T *__restrict__ r, T *__restrict__ z, int64_t nalm,
+                                                   int64_t per, double *__restrict__ slot) {
+    az_mapply_cta<T, TF>(lb, ncb, lmax, nb, ntile, moff, M, xoff, Xg, r, z, nalm, per, slot, blockIdx.x,
+                         blockIdx.y);
+}
 
 // per system b: the sum of its slots in a fixed order (each thread a fixed
 // strided subset, then the threads in order), added to its first rz partial
-__global__ void k_az_addpart(int nslot, const double *__restrict__ slot, double *__restrict__ part, int rb) {
+__device__ __forceinline__ void az_addpart_cta(int nslot, const double *__restrict__ slot,
+                                               double *__restrict__ part, int rb, const int b) {
     __shared__ double sm[256];
-    const int b = blockIdx.x;
     const double *s = slot + (int64_t)b * nslot;
     double t = 0.0;
     for (int e = threadIdx.x; e < nslot; e += 256) t += s[e];
@@ -501,6 +515,58 @@ __global__ void k_az_addpart(int nslot, const double *__restrict__ slot, double 
         for (int w = 0; w < 256; ++w) u += sm[w];
         part[((int64_t)b * 2 + 0) * rb + 0] += u;
     }
+}
+__global__ void k_az_addpart(int nslot, const double *__restrict__ slot, double *__restrict__ part, int rb) {
+    az_addpart_cta(nslot, slot, part, rb, blockIdx.x);
+}
+
+// Grouped application (chains of several geometries, FP32 iteration): the
+// three kernels above over every group's blocks in one launch each; flat
+// block i belongs to the group g with first[g] <= i < first[g + 1] and runs
+// (m, y) = (i' % (lb + 1), i' / (lb + 1)), i' = i - first[g] (addpart: the
+// system b = i').  Groups whose device flag is 0 are skipped.
+struct AzGrp {
+    int lb, ncb, lmax, nb, ntile;
+    const int64_t *xoff, *moff;
+    const float *M;
+    float *Xg;
+    const float *r;
+    float *z;
+    int64_t nalm, per;
+    double *slot, *part;
+    const int *active;
+};
+struct AzGroups {
+    int ng;
+    int first[SHTG_MAX_GROUPS + 1];
+    AzGrp a[SHTG_MAX_GROUPS];
+};
+__device__ __forceinline__ int az_group(const AzGroups &G, const int i) {
+    int g = 0;
+    while (g + 1 < G.ng && i >= G.first[g + 1]) ++g;
+    return g;
+}
+__global__ void k_az_gather_grp(const __grid_constant__ AzGroups G) {
+    const int g = az_group(G, blockIdx.x);
+    const AzGrp &a = G.a[g];
+    if (*a.active == 0) return;
+    const int li = blockIdx.x - G.first[g];
+    az_gather_cta<float, float>(a.lb, a.ncb, a.lmax, a.nb, a.xoff, a.r, a.nalm, a.per, a.Xg, li % (a.lb + 1),
+                                li / (a.lb + 1));
+}
+__global__ void __launch_bounds__(128) k_az_mapply_grp(const __grid_constant__ AzGroups G) {
+    const int g = az_group(G, blockIdx.x);
+    const AzGrp &a = G.a[g];
+    if (*a.active == 0) return;
+    const int li = blockIdx.x - G.first[g];
+    az_mapply_cta<float, float>(a.lb, a.ncb, a.lmax, a.nb, a.ntile, a.moff, a.M, a.xoff, a.Xg, a.r, a.z, a.nalm,
+                                a.per, a.slot, li % (a.lb + 1), li / (a.lb + 1));
+}
+__global__ void k_az_addpart_grp(const __grid_constant__ AzGroups G) {
+    const int g = az_group(G, blockIdx.x);
+    const AzGrp &a = G.a[g];
+    if (*a.active == 0) return;
+    az_addpart_cta((a.lb + 1) * a.ntile * 2, a.slot, a.part, SHTG_RED_BLOCKS, blockIdx.x - G.first[g]);
 }
 __global__ void k_az_cmp(const unsigned long long *__restrict__ a, const unsigned long long *__restrict__ b,
                          int64_t n, int *__restrict__ flag) {
@@ -708,6 +774,60 @@ int az_apply(Plan *p, const T *r, T *z, int nb, int64_t per, double *part, cudaS
         return az_apply_t<double, double>(p, reinterpret_cast<const double *>(r), reinterpret_cast<double *>(z), nb,
                                           per, part, st);
     return az_apply_t<T, float>(p, r, z, nb, per, part, st);
+}
+
+int az_apply_grp(int ng, Plan *const *ps, const float *const *r, float *const *z, const int *nb,
+                 const int64_t *per, double *const *part, const int *const *active, cudaStream_t st) {
+    if (ng < 1 || ng > SHTG_MAX_GROUPS) {
+        set_error("grouped azimuthal blocks: 1 to " + std::to_string(SHTG_MAX_GROUPS) + " groups");
+        return SHTG_ERR_ARG;
+    }
+    AzGroups G[3] = {};
+    int64_t tot[3] = {0, 0, 0};
+    for (int g = 0; g < ng; ++g) {
+        const AzBlk &q = ps[g]->az;
+        if (!q.inv_ok || !q.M32 || !active[g]) {
+            set_error("grouped azimuthal blocks: group " + std::to_string(g) + " has no factored blocks");
+            return SHTG_ERR_ARG;
+        }
+        AzGrp a;
+        a.lb = q.lb;
+        a.ncb = q.ncb;
+        a.lmax = ps[g]->lmax;
+        a.nb = nb[g];
+        a.ntile = q.ntile;
+        a.xoff = q.xoff;
+        a.moff = q.moff;
+        a.M = q.M32;
+        a.Xg = reinterpret_cast<float *>(q.Xg);
+        a.r = r[g];
+        a.z = z[g];
+        a.nalm = ps[g]->nalm;
+        a.per = per[g];
+        a.slot = q.slot;
+        a.part = part[g];
+        a.active = active[g];
+        const int64_t n[3] = {(int64_t)(q.lb + 1) * 2 * nb[g], (int64_t)(q.lb + 1) * q.ntile, (int64_t)nb[g]};
+        for (int k = 0; k < 3; ++k) {
+            G[k].ng = ng;
+            G[k].a[g] = a;
+            G[k].first[g] = (int)tot[k];
+            tot[k] += n[k];
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        if (tot[k] > 0x7fffffff) {
+            set_error("grouped azimuthal blocks: too many blocks");
+            return SHTG_ERR_ARG;
+        }
+        G[k].first[ng] = (int)tot[k];
+    }
+    k_az_gather_grp<<<(unsigned)tot[0], 256, 0, st>>>(G[0]);
+    k_az_mapply_grp<<<(unsigned)tot[1], 128, 0, st>>>(G[1]);
+    k_az_addpart_grp<<<(unsigned)tot[2], 256, 0, st>>>(G[2]);
+    ps[0]->prof.launches += 3;
+    SHTG_CHECK_LAUNCH("k_az_mapply_grp");
+    return SHTG_OK;
 }
 
 template int az_apply<float>(Plan *, const float *, float *, int, int64_t, double *, cudaStream_t, bool);

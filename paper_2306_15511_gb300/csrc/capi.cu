@@ -327,6 +327,11 @@ int shtg_cg_sample_chains(int ngroups, shtg_plan *const *plans, const shtg_probl
             }
     }
     cudaStream_t st = (cudaStream_t)stream;
+    if (opts && (opts->flags & SHTG_GROUPED)) {
+        std::vector<Plan *> ps(ngroups);
+        for (int g = 0; g < ngroups; ++g) ps[g] = reinterpret_cast<Plan *>(plans[g]);
+        return cg_sample_grouped(ngroups, ps.data(), probs, alm_out, opts, stats, st);
+    }
     if (ngroups == 1)
         return cg_sample(reinterpret_cast<Plan *>(plans[0]), &probs[0], alm_out[0], opts,
                          stats ? &stats[0] : nullptr, st);

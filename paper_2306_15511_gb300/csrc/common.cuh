@@ -82,6 +82,9 @@ __host__ __device__ constexpr int ring_first_bpt(int R, int nt) {
     return nt >= 512 ? (R == 2 ? 8 : 1) : nt == 256 ? 1 : nt == 128 ? (R == 2 ? 1 : 2) : (R == 8 ? 1 : 4);
 }
 
+// grouped launches (chains of several geometries): plans per launch
+#define SHTG_MAX_GROUPS 16
+
 #define SHTG_FFT_LOGMAX 13   // longest ring transform (Bluestein length included): 8192
 
 // l stride of the FP64 recurrence tile states
@@ -284,6 +287,9 @@ struct Plan {
 int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_opts *o,
               shtg_cg_stats *stats, cudaStream_t st);
 int apply_operator(Plan *p, const shtg_problem *pr, const double *x, double *y, cudaStream_t st);
+// chains of several geometries with one grouped launch per stage of the FP32 iteration
+int cg_sample_grouped(int ng, Plan *const *ps, const shtg_problem *prs, double *const *outs,
+                      const shtg_cg_opts *o, shtg_cg_stats *stats, cudaStream_t st);
 int fluctuation_rescale(Plan *p, int nc, const double *cl_old, const double *cl_new, const double *f,
                         double *g, int nbatch, cudaStream_t st);
 int joint_log_target(Plan *p, const shtg_problem *pr, int precision, const double *a_hat,
@@ -305,6 +311,11 @@ int az_setup(Plan *p, int lb, int nc, double isc, cudaStream_t st);
 template <typename T>
 int az_apply(Plan *p, const T *r, T *z, int nb, int64_t per, double *part, cudaStream_t st, bool fp64_factor);
 void az_free(Plan *p);
+// az_apply (FP32 factors) over ng plans whose blocks are set up, one launch
+// per kernel for every group; groups whose device flag *active[g] is 0 are
+// skipped
+int az_apply_grp(int ng, Plan *const *ps, const float *const *r, float *const *z, const int *nb,
+                 const int64_t *per, double *const *part, const int *const *active, cudaStream_t st);
 int precond_apply(Plan *p, const shtg_problem *pr, const shtg_cg_opts *o, const double *r, double *z,
                   cudaStream_t st);
 int lowl_block(Plan *p, const shtg_problem *pr, int lc, double *H, int *params, int *n, cudaStream_t st);
@@ -349,6 +360,15 @@ int leg_synth(Plan *p, int spin, const typename VT<T>::C *alm, int rs, int nmaps
 template <typename T>
 int leg_analysis(Plan *p, int spin, const typename VT<T>::C *G, int nmaps, const T *beam,
                  typename VT<T>::C *alm, int rs, cudaStream_t st, int vjp = 0);
+// The FP32 CUDA-core Legendre sums of ng plans in one launch (chains of
+// several geometries): group g works on plans[g] with its own buffers and
+// arguments as leg_synth / leg_analysis would; groups whose device flag
+// *active[g] is 0 are skipped (active, or an entry, may be null: always on).
+int leg_synth_grp(int ng, Plan *const *ps, int spin, const float2 *const *alm, const int *rs, const int *nmaps,
+                  const float *const *beam, float2 *const *F, const int *const *active, cudaStream_t st);
+int leg_analysis_grp(int ng, Plan *const *ps, int spin, const float2 *const *G, const int *nmaps,
+                     const float *const *beam, float2 *const *alm, const int *rs, const int *const *active,
+                     cudaStream_t st);
 // out[l, m] = sum_r w_r g_lm(theta_r) (g = lambda^2 or lw^2 + lx^2)
 int leg_diag(Plan *p, int spin, const float *wring, float *out, cudaStream_t st);
 // FP32 recurrence with the l-sum on the tensor cores (bf16 hi / lo split)
@@ -382,6 +402,12 @@ int ring_analysis(Plan *p, const T *map, int nmaps, int weighted, typename VT<T>
 template <typename T>
 int ring_fused(Plan *p, typename VT<T>::C *FG, int nmaps, int nT, const T *ninv,
                cudaStream_t st);
+// ring_fused over ng plans (FP32), one launch per transform-length class
+// (at most five) covering every plan; groups whose device flag *active[g]
+// is 0 are skipped
+template <typename T>
+int ring_fused_grp(int ng, Plan *const *ps, typename VT<T>::C *const *FG, const int *nmaps, const int *nT,
+                   const T *const *ninv, const int *const *active, cudaStream_t st);
 
 int alm2map_vjp(Plan *p, int spin, int precision, const void *g, void *out, int nbatch,
                 cudaStream_t st);

@@ -1,7 +1,9 @@
 // Dispatch of the Legendre kernels: argument set-up, the diag kernel and an
 // autotuner that picks the (ring pairs per thread, maps per pass) shape of
 // each kernel family on first use.
+#include <algorithm>
 #include <map>
+#include <string>
 
 #include "legendre_kernels.cuh"
 
@@ -78,6 +80,95 @@ int leg_analysis<double>(Plan *p, int spin, const double2 *G, int nmaps, const d
         if (v == 0) return leg_analysis_g64(p, spin, G, nmaps, beam, alm, rs, st, vjp);
         return V.ana[s][v - 1](p, G, nmaps, beam, alm, rs, st, vjp);
     });
+}
+
+// ------------------------------------------------------- grouped launches
+// FP32 Legendre sums on the CUDA cores over several plans in one launch (the
+// chains of several geometries), each group with the shape of variant 0 of
+// its family (the shape the tuner keeps at batches of about ten maps).
+namespace {
+template <int SPIN, bool SYN> struct GrpShape;
+template <> struct GrpShape<0, true> { static constexpr int NR = 4, NM = 2; };
+template <> struct GrpShape<2, true> { static constexpr int NR = 2, NM = 2; };
+template <> struct GrpShape<0, false> { static constexpr int NR = 4, NM = 2; };
+template <> struct GrpShape<2, false> { static constexpr int NR = 2, NM = 2; };
+
+template <int SPIN, bool SYN>
+int launch_grp(int ng, Plan *const *ps, const float2 *const *in, const int *rs, const int *nmaps,
+               const float *const *beam, float2 *const *out, const int *const *active, cudaStream_t st) {
+    constexpr int NR = GrpShape<SPIN, SYN>::NR, NM = GrpShape<SPIN, SYN>::NM, NO = SPIN == 2 ? 4 : 2;
+    if (ng < 1 || ng > SHTG_MAX_GROUPS) {
+        set_error("grouped Legendre launch: 1 to " + std::to_string(SHTG_MAX_GROUPS) + " groups");
+        return SHTG_ERR_ARG;
+    }
+    LegGroups<float> G{};
+    G.ng = ng;
+    size_t smem = 0;
+    int64_t total = 0;
+    // entries in the order of decreasing l_max (the longest recurrences per
+    // CTA first, so the launch does not end on them)
+    int order[SHTG_MAX_GROUPS];
+    for (int g = 0; g < ng; ++g) order[g] = g;
+    std::stable_sort(order, order + ng, [&](int x, int y) { return ps[x]->lmax > ps[y]->lmax; });
+    for (int e = 0; e < ng; ++e) {
+        const int g = order[e];
+        Plan *p = ps[g];
+        LegArgs<float> a = leg_make_args<float>(p);
+        a.rs = rs[g];
+        a.beam = beam[g];
+        a.nmaps = nmaps[g];
+        if (SYN) {
+            a.alm = in[g];
+            a.F = out[g];
+        } else {
+            a.F = const_cast<float2 *>(in[g]);
+            a.alm = out[g];
+        }
+        G.a[e] = a;
+        G.active[e] = active ? active[g] : nullptr;
+        G.gx[e] = (p->npairs + LEG_THREADS * NR - 1) / (LEG_THREADS * NR);
+        G.gy[e] = p->lmax + 1;
+        G.first[e] = (int)total;
+        total += (int64_t)G.gx[e] * G.gy[e] * ((nmaps[g] + NM - 1) / NM);
+        if (!SYN) {
+            smem = std::max(smem, sizeof(float) * (size_t)(p->lmax + 1) * NM * NO);
+            if (G.gx[e] > 1) {   // CTAs of one m add their sums atomically
+                const size_t cs = sizeof(float2) * (size_t)p->nalm;
+                SHTG_CUDA(cudaMemset2DAsync(out[g], cs * rs[g], 0, cs * (SPIN == 2 ? 2 : 1), nmaps[g], st));
+            }
+        }
+    }
+    if (total > 0x7fffffff) {
+        set_error("grouped Legendre launch: too many CTAs");
+        return SHTG_ERR_ARG;
+    }
+    G.first[ng] = (int)total;
+    if (total == 0) return SHTG_OK;
+    Plan *acct = ps[0];
+    prof_begin(acct, SYN ? K_LEG_SYN32 : K_LEG_ANA32, st);
+    if (SYN) {
+        k_leg_synth_grp<float, NR, NM, SPIN><<<(unsigned)total, LEG_THREADS, 0, st>>>(G);
+    } else {
+        auto kern = k_leg_analysis_grp<float, NR, NM, SPIN>;
+        if (smem > 48 * 1024) SHTG_CUDA(allow_max_smem(kern));
+        kern<<<(unsigned)total, LEG_THREADS, smem, st>>>(G);
+    }
+    prof_end(acct, st);
+    SHTG_CHECK_LAUNCH(SYN ? "k_leg_synth_grp" : "k_leg_analysis_grp");
+    return SHTG_OK;
+}
+}  // namespace
+
+int leg_synth_grp(int ng, Plan *const *ps, int spin, const float2 *const *alm, const int *rs, const int *nmaps,
+                  const float *const *beam, float2 *const *F, const int *const *active, cudaStream_t st) {
+    if (spin == 2) return launch_grp<2, true>(ng, ps, alm, rs, nmaps, beam, F, active, st);
+    return launch_grp<0, true>(ng, ps, alm, rs, nmaps, beam, F, active, st);
+}
+int leg_analysis_grp(int ng, Plan *const *ps, int spin, const float2 *const *G, const int *nmaps,
+                     const float *const *beam, float2 *const *alm, const int *rs, const int *const *active,
+                     cudaStream_t st) {
+    if (spin == 2) return launch_grp<2, false>(ng, ps, G, rs, nmaps, beam, alm, active, st);
+    return launch_grp<0, false>(ng, ps, G, rs, nmaps, beam, alm, active, st);
 }
 
 int leg_diag(Plan *p, int spin, const float *wpair, float *out, cudaStream_t st) {

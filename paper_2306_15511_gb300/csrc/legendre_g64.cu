@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(LEG_THREADS) k_tile_states64(const LegArgs<dou
     const int L = a.lmax;
     PairState<double, 1> S;
     int wlo, whi;
-    load_pairs<double, 1, SPIN>(a, m, S, wlo, whi);
+    load_pairs<double, 1, SPIN>(a, blockIdx.x, m, S, wlo, whi);
     const int pr = S.pr[0];
     if (pr >= a.npairs) return;
     const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2;

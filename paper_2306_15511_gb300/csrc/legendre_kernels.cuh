@@ -164,13 +164,13 @@ struct PairState {
 
 // Load the per-pair geometry and start states; returns the warp's l range.
 template <typename T, int NR, int SPIN>
-__device__ __forceinline__ void load_pairs(const LegArgs<T> &a, int m, PairState<T, NR> &S,
+__device__ __forceinline__ void load_pairs(const LegArgs<T> &a, int bx, int m, PairState<T, NR> &S,
                                            int &warp_lo, int &warp_hi) {
     const int L = a.lmax;
     int lo = L + 1, hi = -1;
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
-        const int pr = blockIdx.x * (LEG_THREADS * NR) + j * LEG_THREADS + threadIdx.x;
+        const int pr = bx * (LEG_THREADS * NR) + j * LEG_THREADS + threadIdx.x;
         S.pr[j] = pr;
         S.a1[j] = S.a2[j] = S.b1[j] = S.b2[j] = T(0);
         S.u[j] = T(1);
@@ -265,8 +265,11 @@ __device__ __forceinline__ int cta_min(int v, int *s) {
 }
 
 // =========================================================== synthesis
+// The work of one CTA: ring-pair block bx, order m, map group bz.  Called by
+// the plan's kernel (the three block indices) and by the grouped kernel
+// (one work item of a list that spans several geometries).
 template <typename T, int NR, int NM, int SPIN>
-__global__ void __launch_bounds__(LEG_THREADS) k_leg_synth(const LegArgs<T> a) {
+__device__ __forceinline__ void leg_synth_cta(const LegArgs<T> &a, const int bx, const int m, const int bz) {
     typedef typename VT<T>::C C;
     typedef typename V4<T>::t C4;
     constexpr int NA = (SPIN == 2) ? 2 * NM : NM;   // alm rows staged (E, B per map)
@@ -276,15 +279,14 @@ __global__ void __launch_bounds__(LEG_THREADS) k_leg_synth(const LegArgs<T> a) {
     __shared__ C s_alm[NA][LEG_CHUNK];
     __shared__ int s_red[LEG_THREADS / 32];
 
-    const int m = blockIdx.y;
     const int L = a.lmax;
-    const int map0 = blockIdx.z * NM;
+    const int map0 = bz * NM;
     const int nm = min(NM, a.nmaps - map0);
     const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2;
 
     PairState<T, NR> S;
     int warp_lo, warp_hi;
-    load_pairs<T, NR, SPIN>(a, m, S, warp_lo, warp_hi);
+    load_pairs<T, NR, SPIN>(a, bx, m, S, warp_lo, warp_hi);
     const int lo = cta_min(warp_lo, s_red);
 
     T accE[NR][NM][NACC], accO[NR][NM][NACC];
@@ -406,6 +408,11 @@ __global__ void __launch_bounds__(LEG_THREADS) k_leg_synth(const LegArgs<T> a) {
     }
 }
 
+template <typename T, int NR, int NM, int SPIN>
+__global__ void __launch_bounds__(LEG_THREADS) k_leg_synth(const LegArgs<T> a) {
+    leg_synth_cta<T, NR, NM, SPIN>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+}
+
 // =========================================================== analysis
 // butterfly transpose-reduce of 8 values over the warp: afterwards every lane
 // holds the warp sum of value index 4*b4 + 2*b3 + b2 (b = lane bits).
@@ -434,8 +441,11 @@ __device__ __forceinline__ T treduce8(T (&v)[8], const int lane) {
     return v[0];
 }
 
+// The work of one CTA (as leg_synth_cta); single: the CTA covers every ring
+// pair of its m, so it stores its sums instead of adding them atomically
 template <typename T, int NR, int NM, int SPIN>
-__global__ void __launch_bounds__(LEG_THREADS) k_leg_analysis(const LegArgs<T> a) {
+__device__ __forceinline__ void leg_analysis_cta(const LegArgs<T> &a, const int bx, const int m, const int bz,
+                                                 const bool single) {
     typedef typename VT<T>::C C;
     typedef typename V4<T>::t C4;
     constexpr int NO = (SPIN == 2) ? 4 : 2;     // reals out per map per l (E, B or a)
@@ -445,9 +455,8 @@ __global__ void __launch_bounds__(LEG_THREADS) k_leg_analysis(const LegArgs<T> a
     extern __shared__ unsigned char s_dyn[];
     T *s_acc = reinterpret_cast<T *>(s_dyn);     // [(lmax+1-m)][NM][NO]
 
-    const int m = blockIdx.y;
     const int L = a.lmax;
-    const int map0 = blockIdx.z * NM;
+    const int map0 = bz * NM;
     const int nm = min(NM, a.nmaps - map0);
     const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2;
     const int nl = L + 1 - m;
@@ -457,7 +466,7 @@ __global__ void __launch_bounds__(LEG_THREADS) k_leg_analysis(const LegArgs<T> a
 
     PairState<T, NR> S;
     int warp_lo, warp_hi;
-    load_pairs<T, NR, SPIN>(a, m, S, warp_lo, warp_hi);
+    load_pairs<T, NR, SPIN>(a, bx, m, S, warp_lo, warp_hi);
 
     // per-pair even / odd combinations of the north and south ring data
     T gE[NR][NM][2 * (NO / 2)], gO[NR][NM][2 * (NO / 2)];
@@ -560,7 +569,6 @@ __global__ void __launch_bounds__(LEG_THREADS) k_leg_analysis(const LegArgs<T> a
         }
     }
     __syncthreads();
-    const bool single = gridDim.x == 1;
     for (int i = threadIdx.x; i < nl * nm; i += LEG_THREADS) {
         const int li = i / nm, k = i % nm;
         const int l = m + li;
@@ -581,6 +589,52 @@ __global__ void __launch_bounds__(LEG_THREADS) k_leg_analysis(const LegArgs<T> a
     }
 }
 
+template <typename T, int NR, int NM, int SPIN>
+__global__ void __launch_bounds__(LEG_THREADS) k_leg_analysis(const LegArgs<T> a) {
+    leg_analysis_cta<T, NR, NM, SPIN>(a, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x == 1);
+}
+
+// ======================================================= grouped launches
+// One launch over the CTAs of several plans (chains of different N_side and
+// l_max): entry g holds one plan's arguments (the launcher orders them by
+// decreasing l_max); flat CTA i belongs to the entry with first[g] <= i <
+// first[g+1]; within an entry the CTA index runs over (ring-pair block, m,
+// map group), ring-pair blocks fastest and m ascending, so the long low-m
+// recurrences start first.  An entry whose device flag *active[g] is 0 (a
+// null pointer: always active) is skipped.
+template <typename T> struct LegGroups {
+    int ng;
+    int first[SHTG_MAX_GROUPS + 1];
+    int gx[SHTG_MAX_GROUPS];     // ring-pair blocks of the group
+    int gy[SHTG_MAX_GROUPS];     // orders m of the group (l_max + 1)
+    const int *active[SHTG_MAX_GROUPS];
+    LegArgs<T> a[SHTG_MAX_GROUPS];
+};
+
+__device__ __forceinline__ int group_of(const int *first, const int ng, const int i) {
+    int g = 0;
+    while (g + 1 < ng && i >= first[g + 1]) ++g;
+    return g;
+}
+
+template <typename T, int NR, int NM, int SPIN>
+__global__ void __launch_bounds__(LEG_THREADS) k_leg_synth_grp(const __grid_constant__ LegGroups<T> G) {
+    const int i = blockIdx.x;
+    const int g = group_of(G.first, G.ng, i);
+    if (G.active[g] && *G.active[g] == 0) return;
+    const int li = i - G.first[g], t = li / G.gx[g];
+    leg_synth_cta<T, NR, NM, SPIN>(G.a[g], li % G.gx[g], t % G.gy[g], t / G.gy[g]);
+}
+
+template <typename T, int NR, int NM, int SPIN>
+__global__ void __launch_bounds__(LEG_THREADS) k_leg_analysis_grp(const __grid_constant__ LegGroups<T> G) {
+    const int i = blockIdx.x;
+    const int g = group_of(G.first, G.ng, i);
+    if (G.active[g] && *G.active[g] == 0) return;
+    const int li = i - G.first[g], t = li / G.gx[g];
+    leg_analysis_cta<T, NR, NM, SPIN>(G.a[g], li % G.gx[g], t % G.gy[g], t / G.gy[g], G.gx[g] == 1);
+}
+
 // ====================================================== preconditioner
 // diag_lm = sum_pairs wpair_r g_lm(theta_r), g = lambda^2 (spin 0) or
 // lw^2 + lx^2 (spin 2); g has the same value on both rings of a pair.
@@ -599,7 +653,7 @@ __global__ void __launch_bounds__(LEG_THREADS) k_leg_diag(const LegArgs<float> a
     for (int i = threadIdx.x; i < nl; i += LEG_THREADS) s_acc[i] = 0.f;
     PairState<float, NR> S;
     int warp_lo, warp_hi;
-    load_pairs<float, NR, SPIN>(a, m, S, warp_lo, warp_hi);
+    load_pairs<float, NR, SPIN>(a, blockIdx.x, m, S, warp_lo, warp_hi);
     float w[NR];
 #pragma unroll
     for (int j = 0; j < NR; ++j) w[j] = S.pr[j] < a.npairs ? a.wpair[S.pr[j]] : 0.f;

@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(TC_M) k_leg_synth_tc(const LegArgs<float> a) {
 
     PairState<float, 1> S;
     int warp_lo, warp_hi;
-    load_pairs<float, 1, SPIN>(a, m, S, warp_lo, warp_hi);
+    load_pairs<float, 1, SPIN>(a, blockIdx.x, m, S, warp_lo, warp_hi);
     const int lo = cta_min(warp_lo, s_red);
     const int pr = S.pr[0];
     const int rn = pr, rs = a.nring - 1 - pr;
@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(LEG_THREADS) k_tile_states(const LegArgs<float
     const int L = a.lmax;
     PairState<float, 1> S;
     int wlo, whi;
-    load_pairs<float, 1, SPIN>(a, m, S, wlo, whi);
+    load_pairs<float, 1, SPIN>(a, blockIdx.x, m, S, wlo, whi);
     const int pr = S.pr[0];
     if (pr >= a.npairs) return;
     const int64_t base = (int64_t)m * (2 * L + 1 - m) / 2;

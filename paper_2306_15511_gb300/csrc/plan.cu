@@ -754,7 +754,8 @@ int plan_build(Plan *p) {
     SHTG_CUDA(cudaMemset(p->d_part, 0,
                          sizeof(double) * (4 * (size_t)p->max_batch * SHTG_RED_BLOCKS + 4 * (size_t)p->max_batch + 64)));
     SHTG_TRY(dalloc(p, &p->d_stage, nmp));
-    SHTG_CUDA(cudaMallocHost((void **)&p->h_pinned, 4096 * sizeof(double)));
+    // pinned host scalars: the [max_batch][16] CG slots (host convergence checks)
+    SHTG_CUDA(cudaMallocHost((void **)&p->h_pinned, (16 * (size_t)p->max_batch + 64) * sizeof(double)));
     p->prof.ev.resize(16384);
     for (auto &e : p->prof.ev) SHTG_CUDA(cudaEventCreate(&e));
     p->prof.cls.reserve(8192);

@@ -18,6 +18,7 @@
 // the inverse and the forward transform, so the pixel map never goes to
 // global memory inside an operator application.
 #include <algorithm>
+#include <string>
 
 #include "common.cuh"
 
@@ -457,8 +458,11 @@ __device__ __forceinline__ void transform_dir(C *buf, const int logM, const TwTa
 // Bluestein rings, a convolution = DFT, times the kernel spectrum and
 // conjugated in the last pass, DFT again: buf then holds the conjugate of the
 // convolution.  The directions run in a loop, so the FFT is inlined once.
+// The work of one CTA: ring pair a.pairs[pidx], maps [y mpg, (y + 1) mpg).
+// Called by the plan's kernel (the block indices) and by the grouped kernel
+// (one work item of a list that spans several geometries).
 template <typename T, int MODE, int NT, int FIX>
-__global__ void __launch_bounds__(NT, (RingBlocks<T, NT, FIX>::v)) k_ring(const RingArgs<T> a) {
+__device__ __forceinline__ void ring_cta(const RingArgs<T> &a, const int pidx, const int y) {
     typedef typename VT<T>::C C;
     extern __shared__ __align__(16) unsigned char s_raw[];
     // FIX > 0: every ring of the launch has M = 2^FIX and the fixed-length
@@ -483,7 +487,7 @@ __global__ void __launch_bounds__(NT, (RingBlocks<T, NT, FIX>::v)) k_ring(const 
     tw.logmax = a.logmax;
     // (the first FFT pass starts after a barrier that follows the fill below)
 
-    const int pr = a.pairs[blockIdx.x];
+    const int pr = a.pairs[pidx];
     const int rn = pr, rs = a.nring - 1 - pr;
     const bool single = (rn == rs);
     const RingFFT f = a.rf[rn];
@@ -500,7 +504,7 @@ __global__ void __launch_bounds__(NT, (RingBlocks<T, NT, FIX>::v)) k_ring(const 
     const C zero = {T(0), T(0)};
     constexpr int NDIR = MODE == 2 ? 2 : 1;
 
-    const int q0 = blockIdx.y * a.mpg, q1 = min(a.nmaps, q0 + a.mpg);
+    const int q0 = y * a.mpg, q1 = min(a.nmaps, q0 + a.mpg);
     for (int q = q0; q < q1; ++q) {
         if (MODE != 1 && n >= 2 * L) {
             // ---- fold without aliasing (n >= 2 l_max): F(m) alone fills bin m
@@ -763,6 +767,37 @@ __global__ void __launch_bounds__(NT, (RingBlocks<T, NT, FIX>::v)) k_ring(const 
     }
 }
 
+template <typename T, int MODE, int NT, int FIX>
+__global__ void __launch_bounds__(NT, (RingBlocks<T, NT, FIX>::v)) k_ring(const RingArgs<T> a) {
+    ring_cta<T, MODE, NT, FIX>(a, blockIdx.x, blockIdx.y);
+}
+
+// Grouped launch (chains of several geometries): one launch per
+// transform-length class (the template's NT and FIX) over the launch buckets
+// of that class of every plan; entry e is one (plan, bucket) with its own
+// arguments, flat CTA i belongs to the entry with first[e] <= i <
+// first[e + 1] and runs ring pair i' % count[e], map group i' / count[e]
+// (i' = i - first[e]).  Entries whose plan group's device flag is 0 are
+// skipped.
+#define SHTG_RING_ENTRIES (2 * SHTG_MAX_GROUPS)
+template <typename T> struct RingGroups {
+    int ne;
+    int first[SHTG_RING_ENTRIES + 1];
+    int count[SHTG_RING_ENTRIES];
+    const int *active[SHTG_RING_ENTRIES];   // the entry's plan group flag (null: always active)
+    RingArgs<T> a[SHTG_RING_ENTRIES];
+};
+
+template <typename T, int MODE, int NT, int FIX>
+__global__ void __launch_bounds__(NT, (RingBlocks<T, NT, FIX>::v)) k_ring_grp(const __grid_constant__ RingGroups<T> G) {
+    const int i = blockIdx.x;
+    int e = 0;
+    while (e + 1 < G.ne && i >= G.first[e + 1]) ++e;
+    if (G.active[e] && *G.active[e] == 0) return;
+    const int li = i - G.first[e];
+    ring_cta<T, MODE, NT, FIX>(G.a[e], li % G.count[e], li / G.count[e]);
+}
+
 template <typename T> static const typename VT<T>::C *ring_twf(Plan *p);
 template <> const float2 *ring_twf<float>(Plan *p) { return p->d_twf32; }
 template <> const double2 *ring_twf<double>(Plan *p) { return p->d_twf64; }
@@ -876,6 +911,115 @@ static int launch_ring(Plan *p, RingArgs<T> a, cudaStream_t st) {
     SHTG_CHECK_LAUNCH("k_ring");
     return SHTG_OK;
 }
+
+// launch arguments of one bucket of plan p (the fields launch_ring sets)
+template <typename T>
+static void ring_bucket_args(Plan *p, const Plan::RingLaunch &g, RingArgs<T> &a, size_t &smem) {
+    typedef typename VT<T>::C C;
+    a.lmax = p->lmax;
+    a.nring = p->nring;
+    a.npairs = p->npairs;
+    a.npix = p->npix;
+    a.rf = p->d_rfft;
+    a.ofs = p->d_ofs;
+    a.wring = p->d_wring;
+    a.logmax = p->fft_logmax;
+    a.tw_blo = p->tw_blo;
+    a.tw_nlo = p->tw_nlo;
+    a.tw_nhi = p->tw_nhi;
+    const int M = 1 << g.logm;
+    const bool fix = g.fix > 0;
+    const int nt = fix ? (1 << g.fix) / 16 : ring_threads(g.logm);
+    a.buf_len = M + M / 16;
+    a.chirp_len = g.chirp;
+    a.twf = fix ? ring_twf<T>(p) + p->twf_off[g.fix] : nullptr;
+    const size_t ntw = fix ? (sizeof(T) == 4 ? (size_t)twf_len(g.fix) : 0) : (size_t)p->tw_nlo + p->tw_nhi;
+    smem = sizeof(C) * (ntw + a.buf_len + a.chirp_len + ((g.alias && !fix) ? 2 * nt : 0));
+    a.pairs = p->d_ring_groups + g.off;
+}
+
+template <typename T, int MODE, int NT, int FIX>
+static int launch_ring_grp(RingGroups<T> &G, size_t smem, int64_t total, cudaStream_t st) {
+    auto kern = k_ring_grp<T, MODE, NT, FIX>;
+    if (smem > 48 * 1024) SHTG_CUDA(allow_max_smem(kern));
+    kern<<<(unsigned)total, NT, smem, st>>>(G);
+    return SHTG_OK;
+}
+
+template <typename T>
+int ring_fused_grp(int ng, Plan *const *ps, typename VT<T>::C *const *FG, const int *nmaps, const int *nT,
+                   const T *const *ninv, const int *const *active, cudaStream_t st) {
+    if (ng < 1 || ng > SHTG_MAX_GROUPS) {
+        set_error("grouped ring launch: 1 to " + std::to_string(SHTG_MAX_GROUPS) + " groups");
+        return SHTG_ERR_ARG;
+    }
+    Plan *acct = ps[0];
+    int dev = 0, nsm = 0;
+    SHTG_CUDA(cudaGetDevice(&dev));
+    SHTG_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+    prof_begin(acct, sizeof(T) == 8 ? K_RING64 : K_RING32, st);
+    int nl = 0;
+    // classes by FIX (0: the generic passes of the buckets <= 1024, 64 threads)
+    for (int fix : {13, 12, 11, 10, 0}) {
+        RingGroups<T> G{};
+        size_t smem = 0;
+        int npair = 0;
+        for (int g = 0; g < ng; ++g)
+            for (const Plan::RingLaunch &b : ps[g]->ring_launch)
+                if (b.fix == fix && b.count > 0) {
+                    if (G.ne == SHTG_RING_ENTRIES) {
+                        set_error("grouped ring launch: more than " + std::to_string(SHTG_RING_ENTRIES) +
+                                  " launch buckets of one length");
+                        return SHTG_ERR_ARG;
+                    }
+                    RingArgs<T> a = ring_args<T>(ps[g]);
+                    size_t sm = 0;
+                    ring_bucket_args<T>(ps[g], b, a, sm);
+                    a.FG = FG[g];
+                    a.nmaps = nmaps[g];
+                    a.nT = nT[g];
+                    a.ninv = ninv[g];
+                    smem = std::max(smem, sm);
+                    G.a[G.ne] = a;
+                    G.count[G.ne] = b.count;
+                    G.active[G.ne] = active ? active[g] : nullptr;
+                    G.ne += 1;
+                    npair += b.count;
+                }
+        if (G.ne == 0) continue;
+        // maps per CTA as in the plan's launches: enough CTAs for about four
+        // waves, at least two maps per CTA
+        const int nt = fix ? (1 << fix) / 16 : 64;
+        const int per = std::max(1, (sizeof(T) == 4 ? (fix > 0 ? 1024 : 512) : 256) / nt);
+        const int want = 4 * nsm * per;
+        int64_t total = 0;
+        for (int e = 0; e < G.ne; ++e) {
+            RingArgs<T> &a = G.a[e];
+            int groups = (want + npair - 1) / npair;
+            groups = std::max(1, std::min(groups, (a.nmaps + 1) / 2));
+            a.mpg = (a.nmaps + groups - 1) / groups;
+            groups = (a.nmaps + a.mpg - 1) / a.mpg;
+            G.first[e] = (int)total;
+            total += (int64_t)G.count[e] * groups;
+        }
+        G.first[G.ne] = (int)total;
+        int rc = SHTG_OK;
+        switch (fix) {
+            case 10: rc = launch_ring_grp<T, 2, 64, 10>(G, smem, total, st); break;
+            case 11: rc = launch_ring_grp<T, 2, 128, 11>(G, smem, total, st); break;
+            case 12: rc = launch_ring_grp<T, 2, 256, 12>(G, smem, total, st); break;
+            case 13: rc = launch_ring_grp<T, 2, 512, 13>(G, smem, total, st); break;
+            default: rc = launch_ring_grp<T, 2, 64, 0>(G, smem, total, st); break;
+        }
+        if (rc != SHTG_OK) return rc;
+        ++nl;
+    }
+    prof_end(acct, st, nl);
+    SHTG_CHECK_LAUNCH("k_ring_grp");
+    return SHTG_OK;
+}
+template int ring_fused_grp<float>(int, Plan *const *, float2 *const *, const int *, const int *,
+                                   const float *const *, const int *const *, cudaStream_t);
 
 template <typename T>
 int ring_synth(Plan *p, const typename VT<T>::C *F, int nmaps, T *map, cudaStream_t st) {

@@ -18,6 +18,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <string>
 #include <vector>
 
 #include <cstdio>
@@ -128,19 +129,21 @@ template <> struct HT<double> { typedef double2 C; };
 // <p, A p>, the operator's last kernel doing the dot's reads), launched on
 // the reduction grid (RB blocks per realization) with the per-element sums
 // of k_dot, so alpha is the same bit for bit.
+// (the rows of realization b handled by block bx of nbx: the plan's kernel
+// passes its block indices, the grouped kernel those of its group)
 template <typename T, bool DOT>
-__global__ void k_prior_add(const typename HT<T>::C *__restrict__ x, typename HT<T>::C *__restrict__ y,
-                            int nc, int64_t nalm, int lmax1, const int *__restrict__ lof,
-                            const T *__restrict__ sinv, const T *__restrict__ isc,
-                            const int *__restrict__ mof, double *__restrict__ part) {
+__device__ __forceinline__ void prior_add_rows(const typename HT<T>::C *__restrict__ x,
+                                               typename HT<T>::C *__restrict__ y, int nc, int64_t nalm,
+                                               int lmax1, const int *__restrict__ lof,
+                                               const T *__restrict__ sinv, const T *__restrict__ isc,
+                                               const int *__restrict__ mof, double *__restrict__ part,
+                                               const int b, const int bx, const int nbx) {
     typedef typename HT<T>::C C;
     __shared__ double sm[DOT ? RT / 32 : 1];
-    const int b = blockIdx.y;
     const int64_t off = (int64_t)b * nc * nalm;
     const T sc = isc[b];   // 1 / (C_l scale of realization b)
     double s = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nalm;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = bx * (int64_t)blockDim.x + threadIdx.x; i < nalm; i += (int64_t)nbx * blockDim.x) {
         const int l = lof[i];
         const T tt = sinv[l] * sc;
         typename DotAcc<C>::t t = 0;
@@ -174,8 +177,15 @@ __global__ void k_prior_add(const typename HT<T>::C *__restrict__ x, typename HT
     }
     if (DOT) {
         s = block_sum(s, sm);
-        if (threadIdx.x == 0) part[(int64_t)b * RB + blockIdx.x] = s;
+        if (threadIdx.x == 0) part[(int64_t)b * RB + bx] = s;
     }
+}
+template <typename T, bool DOT>
+__global__ void k_prior_add(const typename HT<T>::C *__restrict__ x, typename HT<T>::C *__restrict__ y,
+                            int nc, int64_t nalm, int lmax1, const int *__restrict__ lof,
+                            const T *__restrict__ sinv, const T *__restrict__ isc,
+                            const int *__restrict__ mof, double *__restrict__ part) {
+    prior_add_rows<T, DOT>(x, y, nc, nalm, lmax1, lof, sinv, isc, mof, part, blockIdx.y, blockIdx.x, gridDim.x);
 }
 
 // Preconditioner M = S^-1 + b_l^2 diag(D_T, D_P, D_P), stored as its inverse:
@@ -300,19 +310,19 @@ __device__ __forceinline__ void apply_minv(const T *minv, int64_t nalm, int64_t 
 // INIT: z = M^-1 r and partial (rz, rr).  Otherwise x += alpha p, r -= alpha q,
 // then the same.
 template <typename T, bool INIT>
-__global__ void k_update(typename HT<T>::C *__restrict__ x, typename HT<T>::C *__restrict__ r,
-                         typename HT<T>::C *__restrict__ z, const typename HT<T>::C *__restrict__ p,
-                         const typename HT<T>::C *__restrict__ q, const T *__restrict__ minv,
-                         int nc, int64_t nalm, const int *__restrict__ mof,
-                         const double *__restrict__ scal, double *__restrict__ part) {
+__device__ __forceinline__ void update_rows(typename HT<T>::C *__restrict__ x, typename HT<T>::C *__restrict__ r,
+                                            typename HT<T>::C *__restrict__ z,
+                                            const typename HT<T>::C *__restrict__ p,
+                                            const typename HT<T>::C *__restrict__ q, const T *__restrict__ minv,
+                                            int nc, int64_t nalm, const int *__restrict__ mof,
+                                            const double *__restrict__ scal, double *__restrict__ part,
+                                            const int b, const int bx, const int nbx) {
     typedef typename HT<T>::C C;
     __shared__ double sm[RT / 32];
-    const int b = blockIdx.y;
     const int64_t off = (int64_t)b * nc * nalm;
     const T alpha = INIT ? T(0) : (T)scal[b * 16 + S_ALPHA];
     double srz = 0.0, srr = 0.0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nalm;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = bx * (int64_t)blockDim.x + threadIdx.x; i < nalm; i += (int64_t)nbx * blockDim.x) {
         C rv[3], zv[3];
         for (int k = 0; k < nc; ++k) {
             const int64_t e = off + k * nalm + i;
@@ -343,25 +353,35 @@ __global__ void k_update(typename HT<T>::C *__restrict__ x, typename HT<T>::C *_
     srz = block_sum(srz, sm);
     srr = block_sum(srr, sm);
     if (threadIdx.x == 0) {
-        part[((int64_t)b * 2 + 0) * RB + blockIdx.x] = srz;
-        part[((int64_t)b * 2 + 1) * RB + blockIdx.x] = srr;
+        part[((int64_t)b * 2 + 0) * RB + bx] = srz;
+        part[((int64_t)b * 2 + 1) * RB + bx] = srr;
     }
 }
+template <typename T, bool INIT>
+__global__ void k_update(typename HT<T>::C *__restrict__ x, typename HT<T>::C *__restrict__ r,
+                         typename HT<T>::C *__restrict__ z, const typename HT<T>::C *__restrict__ p,
+                         const typename HT<T>::C *__restrict__ q, const T *__restrict__ minv,
+                         int nc, int64_t nalm, const int *__restrict__ mof,
+                         const double *__restrict__ scal, double *__restrict__ part) {
+    update_rows<T, INIT>(x, r, z, p, q, minv, nc, nalm, mof, scal, part, blockIdx.y, blockIdx.x, gridDim.x);
+}
 
+// The scalar kernels run one block; thread t serves realizations t, t +
+// blockDim.x, ... (a plan holds up to 4096).
 __global__ void k_scal_init(const double *__restrict__ part, double *__restrict__ scal, int nb,
                             double tol2) {
-    const int b = threadIdx.x;
-    if (b >= nb) return;
-    const double rz = sum_part(part, b, 2, 0), rr = sum_part(part, b, 2, 1);
-    double *s = scal + b * 16;
-    s[S_RZ] = rz;
-    s[S_RR] = rr;
-    s[S_BB] = rr;
-    s[S_TOL2] = tol2;
-    s[S_ACTIVE] = (rr > 0.0) ? 1.0 : 0.0;
-    s[S_ITERS] = 0.0;
-    s[S_BAD] = (isfinite(rr) && isfinite(rz)) ? 0.0 : 1.0;
-    s[S_ALPHA] = s[S_BETA] = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        const double rz = sum_part(part, b, 2, 0), rr = sum_part(part, b, 2, 1);
+        double *s = scal + b * 16;
+        s[S_RZ] = rz;
+        s[S_RR] = rr;
+        s[S_BB] = rr;
+        s[S_TOL2] = tol2;
+        s[S_ACTIVE] = (rr > 0.0) ? 1.0 : 0.0;
+        s[S_ITERS] = 0.0;
+        s[S_BAD] = (isfinite(rr) && isfinite(rz)) ? 0.0 : 1.0;
+        s[S_ALPHA] = s[S_BETA] = 0.0;
+    }
 }
 
 // floor2: the FP32 iteration of the mixed solver passes the squared
@@ -370,9 +390,8 @@ __global__ void k_scal_init(const double *__restrict__ part, double *__restrict_
 // preconditioner close to the exact inverse) ends the stage instead of
 // failing it, and the FP64 residual replacement judges convergence.  The
 // FP64 PCG passes 0 (any non-positive curvature is a failure).
-__global__ void k_scal_alpha(const double *__restrict__ part, double *__restrict__ scal, int nb, double floor2) {
-    const int b = threadIdx.x;
-    if (b >= nb) return;
+__device__ __forceinline__ void scal_alpha_one(const double *__restrict__ part, double *__restrict__ scal,
+                                               const int b, const double floor2) {
     double *s = scal + b * 16;
     const double pq = sum_part(part, b, 1, 0);
     s[S_PQ] = pq;
@@ -388,10 +407,12 @@ __global__ void k_scal_alpha(const double *__restrict__ part, double *__restrict
     }
     s[S_ALPHA] = alpha;
 }
+__global__ void k_scal_alpha(const double *__restrict__ part, double *__restrict__ scal, int nb, double floor2) {
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) scal_alpha_one(part, scal, b, floor2);
+}
 
-__global__ void k_scal_beta(const double *__restrict__ part, double *__restrict__ scal, int nb) {
-    const int b = threadIdx.x;
-    if (b >= nb) return;
+__device__ __forceinline__ void scal_beta_one(const double *__restrict__ part, double *__restrict__ scal,
+                                              const int b) {
     double *s = scal + b * 16;
     const double rz = sum_part(part, b, 2, 0), rr = sum_part(part, b, 2, 1);
     double beta = 0.0;
@@ -409,22 +430,86 @@ __global__ void k_scal_beta(const double *__restrict__ part, double *__restrict_
     }
     s[S_BETA] = beta;
 }
+__global__ void k_scal_beta(const double *__restrict__ part, double *__restrict__ scal, int nb) {
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) scal_beta_one(part, scal, b);
+}
 
 template <typename C>
-__global__ void k_pupdate(C *__restrict__ p, const C *__restrict__ z, int nc, int64_t nalm,
-                          const double *__restrict__ scal) {
-    const int b = blockIdx.y;
+__device__ __forceinline__ void pupdate_rows(C *__restrict__ p, const C *__restrict__ z, int nc, int64_t nalm,
+                                             const double *__restrict__ scal, const int b, const int bx,
+                                             const int nbx) {
     const int64_t off = (int64_t)b * nc * nalm;
     const double beta = scal[b * 16 + S_BETA];
     const int64_t n = (int64_t)nc * nalm;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t i = bx * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)nbx * blockDim.x) {
         C pv = p[off + i];
         const C zv = z[off + i];
         pv.x = zv.x + (decltype(pv.x))beta * pv.x;
         pv.y = zv.y + (decltype(pv.y))beta * pv.y;
         p[off + i] = pv;
     }
+}
+template <typename C>
+__global__ void k_pupdate(C *__restrict__ p, const C *__restrict__ z, int nc, int64_t nalm,
+                          const double *__restrict__ scal) {
+    pupdate_rows<C>(p, z, nc, nalm, scal, blockIdx.y, blockIdx.x, gridDim.x);
+}
+
+// ----------------------------------------------- grouped FP32 PCG kernels
+// The vector kernels of the FP32 iteration over several plans in one
+// launch (chains of several geometries): flat realization row = blockIdx.y
+// (row kernels) or group = blockIdx.x (scalar kernels); each group's
+// vectors, tables and scalars are its own plan's.
+struct VecGrp {
+    float2 *x, *r, *z, *p, *q;
+    const float *minv, *sinv, *isc;
+    const int *lof, *mof;
+    double *scal, *part;
+    const int *active;   // device flag: 0 = the group is skipped
+    int64_t nalm;
+    int nc, nb, lmax1;
+};
+struct VecGroups {
+    int ng;
+    int firstb[SHTG_MAX_GROUPS + 1];   // first flat realization row of each group
+    VecGrp v[SHTG_MAX_GROUPS];
+};
+
+__device__ __forceinline__ int vgroup(const VecGroups &G, const int row) {
+    int g = 0;
+    while (g + 1 < G.ng && row >= G.firstb[g + 1]) ++g;
+    return g;
+}
+
+__global__ void k_prior_add_grp(const __grid_constant__ VecGroups G) {
+    const int g = vgroup(G, blockIdx.y);
+    const VecGrp &v = G.v[g];
+    if (*v.active == 0) return;
+    prior_add_rows<float, true>(v.p, v.q, v.nc, v.nalm, v.lmax1, v.lof, v.sinv, v.isc, v.mof, v.part,
+                                blockIdx.y - G.firstb[g], blockIdx.x, gridDim.x);
+}
+__global__ void k_scal_alpha_grp(const __grid_constant__ VecGroups G, double floor2) {
+    const VecGrp &v = G.v[blockIdx.x];
+    if (*v.active == 0) return;
+    for (int b = threadIdx.x; b < v.nb; b += blockDim.x) scal_alpha_one(v.part, v.scal, b, floor2);
+}
+__global__ void k_update_grp(const __grid_constant__ VecGroups G) {
+    const int g = vgroup(G, blockIdx.y);
+    const VecGrp &v = G.v[g];
+    if (*v.active == 0) return;
+    update_rows<float, false>(v.x, v.r, v.z, v.p, v.q, v.minv, v.nc, v.nalm, v.mof, v.scal, v.part,
+                              blockIdx.y - G.firstb[g], blockIdx.x, gridDim.x);
+}
+__global__ void k_scal_beta_grp(const __grid_constant__ VecGroups G) {
+    const VecGrp &v = G.v[blockIdx.x];
+    if (*v.active == 0) return;
+    for (int b = threadIdx.x; b < v.nb; b += blockDim.x) scal_beta_one(v.part, v.scal, b);
+}
+__global__ void k_pupdate_grp(const __grid_constant__ VecGroups G) {
+    const int g = vgroup(G, blockIdx.y);
+    const VecGrp &v = G.v[g];
+    if (*v.active == 0) return;
+    pupdate_rows<float2>(v.p, v.z, v.nc, v.nalm, v.scal, blockIdx.y - G.firstb[g], blockIdx.x, gridDim.x);
 }
 
 // mixed precision helpers
@@ -478,22 +563,22 @@ __global__ void k_scale_vec(float2 *__restrict__ v, int64_t per, const double *_
 // after a residual replacement: new rz, rr from the partials; tol2 per realization
 __global__ void k_scal_reliable(const double *__restrict__ part, double *__restrict__ scal, int nb,
                                 const double *__restrict__ tol2) {
-    const int b = threadIdx.x;
-    if (b >= nb) return;
-    double *s = scal + b * 16;
-    const double rz = sum_part(part, b, 2, 0), rr = sum_part(part, b, 2, 1);
-    s[S_RZ] = rz;
-    s[S_RR] = rr;
-    s[S_BB] = 1.0;                       // the FP32 residual is normalized to 1
-    s[S_TOL2] = tol2[b];
-    s[S_ACTIVE] = (tol2[b] >= 0.0 && rr > 0.0) ? 1.0 : 0.0;
-    // set, not accumulated: the first replacement of a solve runs on scalar
-    // slots that hold whatever an earlier call (or a fresh allocation) left,
-    // and a bad FP32 stage already ended the solve at its host check
-    s[S_BAD] = (isfinite(rr) && isfinite(rz)) ? 0.0 : 1.0;
-    s[S_ITERS] = 0.0;
-    s[S_RESTART] = 0.0;
-    s[S_ALPHA] = s[S_BETA] = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        double *s = scal + b * 16;
+        const double rz = sum_part(part, b, 2, 0), rr = sum_part(part, b, 2, 1);
+        s[S_RZ] = rz;
+        s[S_RR] = rr;
+        s[S_BB] = 1.0;                       // the FP32 residual is normalized to 1
+        s[S_TOL2] = tol2[b];
+        s[S_ACTIVE] = (tol2[b] >= 0.0 && rr > 0.0) ? 1.0 : 0.0;
+        // set, not accumulated: the first replacement of a solve runs on scalar
+        // slots that hold whatever an earlier call (or a fresh allocation) left,
+        // and a bad FP32 stage already ended the solve at its host check
+        s[S_BAD] = (isfinite(rr) && isfinite(rz)) ? 0.0 : 1.0;
+        s[S_ITERS] = 0.0;
+        s[S_RESTART] = 0.0;
+        s[S_ALPHA] = s[S_BETA] = 0.0;
+    }
 }
 
 // a stage that ended at its rounding floor restarts its direction: p = z
@@ -1285,10 +1370,25 @@ int precond_apply(Plan *p, const shtg_problem *pr, const shtg_cg_opts *o, const 
     return SHTG_OK;
 }
 
-int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_opts *o,
-              shtg_cg_stats *stats, cudaStream_t st) {
-    SHTG_TRY(check_problem(p, pr));
+// One cg_sample call between its phases: cg_begin checks the arguments,
+// sets up the operator and the preconditioner and forms the right-hand
+// sides; the solve runs; cg_end reports the FP64 residuals, copies the
+// solution out and fills the stats.  The grouped chains solve runs the
+// phases of several plans around one grouped iteration.
+struct CgCall {
     shtg_cg_opts opt;
+    shtg_cg_stats stt;
+    Solve s;
+    std::vector<double> bb, rr;
+    int host = 0;
+    double t0 = 0.0, t1 = 0.0;
+    long long launches0 = 0;
+};
+
+static int cg_begin(Plan *p, const shtg_problem *pr, const double *alm_out, const shtg_cg_opts *o,
+                    cudaStream_t st, CgCall &c) {
+    SHTG_TRY(check_problem(p, pr));
+    shtg_cg_opts &opt = c.opt;
     if (o) {
         opt = *o;
     } else {
@@ -1341,6 +1441,7 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
         return SHTG_ERR_ARG;
     }
     const int host = (opt.flags & SHTG_HOST_INPUTS) ? 1 : 0;
+    c.host = host;
     const int split = (opt.flags & SHTG_SPLIT_RHS) ? 1 : 0;
     if (!pr->d || !pr->w1 || !pr->w2 || !alm_out) {
         set_error("d, w1, w2 and alm_out are required");
@@ -1350,17 +1451,19 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
         set_error("SHTG_SPLIT_RHS solves 2 nbatch systems: needs max_batch >= 2 nbatch");
         return SHTG_ERR_ARG;
     }
-    shtg_cg_stats stt;
+    shtg_cg_stats &stt = c.stt;
     memset(&stt, 0, sizeof(stt));
     p->prof.on = (opt.flags & SHTG_PROFILE) != 0;
     p->prof.n = 0;
     p->prof.open_cls = -1;
-    const long long launches0 = p->prof.launches;
+    c.launches0 = p->prof.launches;
     const double t0 = now_ms();
+    c.t0 = t0;
     // nb systems: the realizations, or (split) their mean-field right-hand
     // sides followed by their fluctuation right-hand sides
     const int nr = pr->nbatch, nb = split ? 2 * nr : nr, nc = pr->ncomp;
-    Solve s = make_solve(p, nb, nc, st);
+    c.s = make_solve(p, nb, nc, st);
+    Solve &s = c.s;
     s.tc = opt.mode == SHTG_CG_MIXED_TC;
     s.df = opt.fp64_arith == SHTG_ARITH_DF64 ||
            (opt.fp64_arith == SHTG_ARITH_DEFAULT && opt.mode != SHTG_CG_FP64 && opt.mode != SHTG_CG_BLOCK);
@@ -1371,7 +1474,7 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
     SHTG_TRY(setup_operator(p, pr, host, opt.mode == SHTG_CG_BLOCK ? 0 : opt.precond, st, nb));
     if (opt.mode != SHTG_CG_BLOCK) SHTG_TRY(precond_setup(s, opt, pr));
     const double ts = now_ms();
-    double2 *B = p->v64[0], *X = p->v64[1], *R = p->v64[2], *Tt = p->v64[6];
+    double2 *B = p->v64[0], *Tt = p->v64[6];
     // ---- RHS: B Y^T (N^-1 d + N^-1/2 w2) + S^-1/2 w1 in FP64; split: the
     // mean field's B Y^T N^-1 d (Eq. mean-field-map) for systems [0, nr) and
     // the fluctuation's S^-1/2 w1 + B Y^T N^-1/2 w2 (Eq. fluc-map) for [nr, 2 nr)
@@ -1413,7 +1516,7 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
         p->prof.launches += 1;
         SHTG_CHECK_LAUNCH("k_rhs_alm");
     }
-    std::vector<double> bb;
+    std::vector<double> &bb = c.bb;
     SHTG_TRY(norms2(s, B, bb));
     for (int b = 0; b < nb; ++b)
         if (!std::isfinite(bb[b])) {
@@ -1422,10 +1525,55 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
             return SHTG_ERR_NONFINITE;
         }
     const double t1 = now_ms();
+    c.t1 = t1;
     stt.ms_setup = ts - t0;
     stt.ms_rhs = t1 - ts;
+    return SHTG_OK;
+}
+
+static int cg_end(Plan *p, CgCall &c, double *alm_out, shtg_cg_stats *stats, cudaStream_t st) {
+    const shtg_cg_opts &opt = c.opt;
+    shtg_cg_stats &stt = c.stt;
+    Solve &s = c.s;
+    const int nb = s.nb;
+    double2 *X = p->v64[1];
+    double worst = 0.0;
+    int conv_all = 1;
+    for (int b = 0; b < nb; ++b) {
+        const double rel = c.bb[b] > 0 ? sqrt(c.rr[b] / c.bb[b]) : 0.0;
+        worst = std::max(worst, rel);
+        if (rel > opt.tol) conv_all = 0;
+    }
+    stt.rel_residual = worst;
+    stt.converged = conv_all;
+    SHTG_CUDA(cudaMemcpyAsync(alm_out, X, sizeof(double2) * (size_t)s.nvec,
+                              c.host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
+    SHTG_CUDA(cudaStreamSynchronize(st));
+    const double t2 = now_ms();
+    stt.ms_solve = t2 - c.t1;
+    stt.ms_total = t2 - c.t0;
+    prof_collect(p, stt.kernel_ms, stt.kernel_launches);
+    p->prof.on = false;
+    stt.launches = p->prof.launches - c.launches0;
+    if (stats) *stats = stt;
+    if (!conv_all) {
+        set_error("maximum iterations reached before the tolerance");
+        return SHTG_ERR_NOT_CONVERGED;
+    }
+    return SHTG_OK;
+}
+
+int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_opts *o,
+              shtg_cg_stats *stats, cudaStream_t st) {
+    CgCall c;
+    SHTG_TRY(cg_begin(p, pr, alm_out, o, st, c));
+    const shtg_cg_opts &opt = c.opt;
+    shtg_cg_stats &stt = c.stt;
+    Solve &s = c.s;
+    const int nb = s.nb;
+    double2 *B = p->v64[0], *X = p->v64[1], *R = p->v64[2], *Tt = p->v64[6];
     int rc = SHTG_OK;
-    std::vector<double> rr;
+    std::vector<double> &rr = c.rr;
     if (opt.mode == SHTG_CG_BLOCK) {
         SHTG_TRY(block_solve(p, B, X, nb, pr->cl_scale ? 1.0 / pr->cl_scale[0] : 1.0, st));
         // the FP64 residual of the exact solve, for the stats
@@ -1445,33 +1593,344 @@ int cg_sample(Plan *p, const shtg_problem *pr, double *alm_out, const shtg_cg_op
         p->prof.launches += 1;
         SHTG_TRY(norms2(s, R, rr));
     } else {
-        SHTG_TRY(mixed_solve(s, opt, bb, rr, &stt));
+        SHTG_TRY(mixed_solve(s, opt, c.bb, rr, &stt));
         if (s.tc) SHTG_TRY(check_device_flag(p, st));
     }
-    double worst = 0.0;
-    int conv_all = 1;
-    for (int b = 0; b < nb; ++b) {
-        const double rel = bb[b] > 0 ? sqrt(rr[b] / bb[b]) : 0.0;
-        worst = std::max(worst, rel);
-        if (rel > opt.tol) conv_all = 0;
+    (void)nb;
+    return cg_end(p, c, alm_out, stats, st);
+}
+
+// ================================================== chains: grouped solve
+// Chains of several geometries solved together (flag SHTG_GROUPED of
+// shtg_cg_sample_chains): every stage of the FP32 PCG iteration (Legendre
+// synthesis, ring stage with N^-1, Legendre transpose, prior and <p, Ap>,
+// the scalar and vector updates, the azimuthal blocks) is one launch over
+// the work of every group (the ring stage: one per transform-length class),
+// and the iteration is replayed as one CUDA graph.  Each group keeps its own
+// plan, vectors and per-realization scalars; a group whose realizations have
+// all converged is skipped through a device flag (its plan's d_flag[1]).
+// The FP64-accurate steps (right-hand side, residual replacements) stay per
+// group: a group's replacement runs at the host check after one of its
+// realizations has dropped by reliable_delta, while the others go on.
+struct GroupIter {
+    int ng = 0, nc = 1, nbtot = 0, pc = SHTG_PRECOND_DIAG;
+    std::vector<Plan *> ps;
+    std::vector<const float2 *> xin, xin2;
+    std::vector<float2 *> F, F2, q, q2, r32, z32;
+    std::vector<const float *> beam, ninv;
+    std::vector<int> rs0, rs2, nmaps, nring_maps, nT, nb;
+    std::vector<int64_t> per;
+    std::vector<double *> part;
+    std::vector<const int *> act;
+    VecGroups V{};
+};
+
+static int pcg_iteration_grp(GroupIter &G, cudaStream_t st) {
+    Plan *const *ps = G.ps.data();
+    const int *const *act = G.act.data();
+    SHTG_TRY(leg_synth_grp(G.ng, ps, 0, G.xin.data(), G.rs0.data(), G.nmaps.data(), G.beam.data(), G.F.data(), act,
+                           st));
+    if (G.nc == 3)
+        SHTG_TRY(leg_synth_grp(G.ng, ps, 2, G.xin2.data(), G.rs2.data(), G.nmaps.data(), G.beam.data(), G.F2.data(),
+                               act, st));
+    SHTG_TRY(ring_fused_grp<float>(G.ng, ps, G.F.data(), G.nring_maps.data(), G.nT.data(), G.ninv.data(), act, st));
+    SHTG_TRY(leg_analysis_grp(G.ng, ps, 0, G.F.data(), G.nmaps.data(), G.beam.data(), G.q.data(), G.rs0.data(), act,
+                              st));
+    if (G.nc == 3)
+        SHTG_TRY(leg_analysis_grp(G.ng, ps, 2, G.F2.data(), G.nmaps.data(), G.beam.data(), G.q2.data(),
+                                  G.rs2.data(), act, st));
+    Plan *acct = ps[0];
+    prof_begin(acct, K_VEC, st);
+    const dim3 rows(RB, G.nbtot);
+    k_prior_add_grp<<<rows, RT, 0, st>>>(G.V);
+    k_scal_alpha_grp<<<G.ng, 1024, 0, st>>>(G.V, 1e-6);
+    k_update_grp<<<rows, RT, 0, st>>>(G.V);
+    if (G.pc == SHTG_PRECOND_AZIM)
+        SHTG_TRY(az_apply_grp(G.ng, ps, reinterpret_cast<const float *const *>(G.r32.data()),
+                              reinterpret_cast<float *const *>(G.z32.data()), G.nb.data(), G.per.data(),
+                              G.part.data(), act, st));
+    k_scal_beta_grp<<<G.ng, 1024, 0, st>>>(G.V);
+    k_pupdate_grp<<<rows, RT, 0, st>>>(G.V);
+    prof_end(acct, st, 5);
+    SHTG_CHECK_LAUNCH("grouped pcg iteration");
+    return SHTG_OK;
+}
+
+// nrun grouped iterations; the first call runs one eagerly, captures the
+// next one on the first plan's capture stream and replays it
+static int run_iterations_grp(GroupIter &G, IterGraph &graph, int nrun, bool graphs, cudaStream_t st) {
+    Plan *p = G.ps[0];
+    if (!graphs || p->prof.on) {
+        for (int k = 0; k < nrun; ++k) SHTG_TRY(pcg_iteration_grp(G, st));
+        return SHTG_OK;
     }
-    stt.rel_residual = worst;
-    stt.converged = conv_all;
-    SHTG_CUDA(cudaMemcpyAsync(alm_out, X, sizeof(double2) * (size_t)s.nvec,
-                              host ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice, st));
-    SHTG_CUDA(cudaStreamSynchronize(st));
-    const double t2 = now_ms();
-    stt.ms_solve = t2 - t1;
-    stt.ms_total = t2 - t0;
-    prof_collect(p, stt.kernel_ms, stt.kernel_launches);
-    p->prof.on = false;
-    stt.launches = p->prof.launches - launches0;
-    if (stats) *stats = stt;
-    if (!conv_all) {
-        set_error("maximum iterations reached before the tolerance");
-        return SHTG_ERR_NOT_CONVERGED;
+    if (!graph.exec && nrun > 0) {
+        SHTG_TRY(pcg_iteration_grp(G, st));
+        if (--nrun == 0) return SHTG_OK;
+        const long long l0 = p->prof.launches;
+        cudaStream_t cs = p->cap_stream;
+        SHTG_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed));
+        const int rc = pcg_iteration_grp(G, cs);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(cs, &g);
+        graph.launches = p->prof.launches - l0;
+        p->prof.launches = l0;
+        if (rc != SHTG_OK) {
+            if (g) cudaGraphDestroy(g);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+        graph.graph = g;
+        SHTG_CUDA(cudaGraphInstantiate(&graph.exec, g, 0));
+    }
+    for (int k = 0; k < nrun; ++k) {
+        SHTG_CUDA(cudaGraphLaunch(graph.exec, st));
+        p->prof.launches += graph.launches;
     }
     return SHTG_OK;
+}
+
+// The grouped mixed solve: mixed_solve's stages, with the FP32 iterations of
+// every group in one grouped iteration.
+static int mixed_solve_grp(int ng, Plan *const *ps, std::vector<CgCall> &c, cudaStream_t st) {
+    const shtg_cg_opts &opt = c[0].opt;
+    const double delta = opt.reliable_delta;
+    struct GState {
+        std::vector<double> scale, sc;
+        std::vector<char> done;
+        double *d_sc = nullptr;
+        bool first = true, finished = false, replace = true;
+        int since = 0;
+    };
+    std::vector<GState> gs(ng);
+    GroupIter G;
+    G.ng = ng;
+    G.nc = c[0].s.nc;
+    G.pc = opt.precond;
+    G.ps.assign(ps, ps + ng);
+    G.V.ng = ng;
+    for (int g = 0; g < ng; ++g) {
+        Plan *p = ps[g];
+        Solve &s = c[g].s;
+        s.st = st;
+        const int nb = s.nb;
+        const int64_t rowsz = (int64_t)(p->lmax + 1) * p->nring;
+        float2 *r32 = p->v32[0], *z32 = p->v32[1], *p32 = p->v32[2], *q32 = p->v32[3], *x32 = p->v32[4];
+        G.xin.push_back(p32);
+        G.xin2.push_back(p32 + s.nalm);
+        G.F.push_back(p->d_phase32);
+        G.F2.push_back(p->d_phase32 + nb * rowsz);
+        G.q.push_back(q32);
+        G.q2.push_back(q32 + s.nalm);
+        G.r32.push_back(r32);
+        G.z32.push_back(z32);
+        G.beam.push_back(p->d_ltab32);
+        G.ninv.push_back(p->d_ninv32);
+        G.rs0.push_back(s.nc);
+        G.rs2.push_back(3);
+        G.nmaps.push_back(nb);
+        G.nring_maps.push_back(nb * s.nc);
+        G.nT.push_back(nb);
+        G.nb.push_back(nb);
+        G.per.push_back(s.per);
+        G.part.push_back(p->d_part);
+        G.act.push_back(p->d_flag + 1);
+        VecGrp &v = G.V.v[g];
+        v.x = x32;
+        v.r = r32;
+        v.z = z32;
+        v.p = p32;
+        v.q = q32;
+        v.minv = p->d_minv32;
+        v.sinv = p->d_ltab32 + (p->lmax + 1);
+        v.isc = p->d_isc32;
+        v.lof = p->d_lofidx;
+        v.mof = p->d_mofidx;
+        v.scal = p->d_scal;
+        v.part = p->d_part;
+        v.active = p->d_flag + 1;
+        v.nalm = s.nalm;
+        v.nc = s.nc;
+        v.nb = nb;
+        v.lmax1 = p->lmax + 1;
+        G.V.firstb[g] = G.nbtot;
+        G.nbtot += nb;
+        GState &q = gs[g];
+        q.scale.assign(nb, 0.0);
+        q.sc.assign(4 * nb, 0.0);
+        q.done.assign(nb, 0);
+        q.d_sc = p->d_part + 4 * (int64_t)p->max_batch * SHTG_RED_BLOCKS;
+        double2 *B = p->v64[0], *X = p->v64[1], *R = p->v64[2];
+        SHTG_CUDA(cudaMemsetAsync(X, 0, sizeof(double2) * (size_t)s.nvec, st));
+        SHTG_CUDA(cudaMemcpyAsync(R, B, sizeof(double2) * (size_t)s.nvec, cudaMemcpyDeviceToDevice, st));
+        c[g].rr = c[g].bb;
+    }
+    G.V.firstb[ng] = G.nbtot;
+    bool graphs = true;
+    {
+        const char *e = getenv("SHTG_GRAPHS");
+        graphs = !(opt.flags & SHTG_NO_GRAPHS) && !(e && e[0] == '0');
+    }
+    IterGraph graph;
+    int it = 0;
+    for (;;) {
+        // ---- stage starts (after a residual replacement, or the first one)
+        int live = 0;
+        for (int g = 0; g < ng; ++g) {
+            GState &q = gs[g];
+            if (q.finished) continue;
+            if (!q.replace) {
+                ++live;
+                continue;
+            }
+            q.replace = false;
+            Plan *p = ps[g];
+            Solve &s = c[g].s;
+            const int nb = s.nb;
+            const std::vector<double> &bb = c[g].bb, &rr = c[g].rr;
+            int active = 0;
+            for (int b = 0; b < nb; ++b) {
+                q.done[b] = bb[b] == 0.0 || rr[b] <= opt.tol * opt.tol * bb[b];
+                const double nr = sqrt(rr[b]);
+                const double old = q.scale[b];
+                q.scale[b] = q.done[b] ? 0.0 : nr;
+                q.sc[b] = q.done[b] ? 0.0 : 1.0 / nr;
+                q.sc[nb + b] = q.done[b] ? -1.0 : (0.1 * delta) * (0.1 * delta);
+                q.sc[2 * nb + b] = (q.done[b] || old == 0.0) ? 0.0 : old / nr;
+                q.sc[3 * nb + b] = q.scale[b];
+                active += !q.done[b];
+            }
+            if (!active || it >= opt.maxiter) {
+                q.finished = true;
+                SHTG_CUDA(cudaMemsetAsync(p->d_flag + 1, 0, sizeof(int), st));
+                continue;
+            }
+            ++live;
+            float2 *r32 = p->v32[0], *z32 = p->v32[1], *p32 = p->v32[2], *x32 = p->v32[4];
+            const size_t vb32 = sizeof(float2) * (size_t)s.nvec;
+            SHTG_CUDA(cudaMemcpyAsync(q.d_sc, q.sc.data(), sizeof(double) * 4 * nb, cudaMemcpyHostToDevice, st));
+            k_scale_down<<<s.vgrid, RT, 0, st>>>(p->v64[2], r32, s.per, q.d_sc);
+            if (q.first) SHTG_CUDA(cudaMemsetAsync(x32, 0, vb32, st));
+            else k_scale_vec<<<s.vgrid, RT, 0, st>>>(p32, s.per, q.d_sc + 2 * nb);
+            k_update<float, true><<<s.rgrid, RT, 0, st>>>(nullptr, r32, z32, nullptr, nullptr, p->d_minv32, s.nc,
+                                                         s.nalm, p->d_mofidx, p->d_scal, p->d_part);
+            if (G.pc == SHTG_PRECOND_AZIM)
+                SHTG_TRY(az_apply<float>(p, reinterpret_cast<const float *>(r32), reinterpret_cast<float *>(z32), nb,
+                                         s.per, p->d_part, st, false));
+            if (!q.first) k_restart_dir<<<s.vgrid, RT, 0, st>>>(p32, z32, s.per, p->d_scal);
+            k_scal_reliable<<<1, 1024, 0, st>>>(p->d_part, p->d_scal, nb, q.d_sc + nb);
+            p->prof.launches += q.first ? 3 : 5;
+            SHTG_CHECK_LAUNCH("reliable update");
+            if (q.first) SHTG_CUDA(cudaMemcpyAsync(p32, z32, vb32, cudaMemcpyDeviceToDevice, st));
+            q.first = false;
+            SHTG_CUDA(cudaMemsetAsync(p->d_flag + 1, 1, sizeof(int), st));
+        }
+        if (!live) break;
+        // ---- grouped FP32 iterations
+        const int nrun = std::min(std::max(1, opt.check_every), opt.maxiter - it);
+        SHTG_TRY(run_iterations_grp(G, graph, nrun, graphs, st));
+        it += nrun;
+        for (int g = 0; g < ng; ++g)
+            if (!gs[g].finished) {
+                Plan *p = ps[g];
+                SHTG_CUDA(cudaMemcpyAsync(p->h_pinned, p->d_scal, sizeof(double) * 16 * c[g].s.nb,
+                                          cudaMemcpyDeviceToHost, st));
+            }
+        SHTG_CUDA(cudaStreamSynchronize(st));
+        // ---- host check per group; replacements where due
+        for (int g = 0; g < ng; ++g) {
+            GState &q = gs[g];
+            if (q.finished) continue;
+            Plan *p = ps[g];
+            Solve &s = c[g].s;
+            const int nb = s.nb;
+            c[g].stt.iterations += nrun;
+            int ready = 0, still = 0;
+            for (int b = 0; b < nb; ++b) {
+                const double *h = p->h_pinned + b * 16;
+                if (h[S_BAD] != 0.0) {
+                    char buf[256];
+                    snprintf(buf, sizeof buf,
+                             "non-finite or non-positive curvature in the FP32 PCG (group %d, system %d, stage "
+                             "iteration %g: <p, Ap> = %.3e, <r, z> = %.3e, |r|^2 = %.3e of the stage's start)",
+                             g, b, h[S_ITERS], h[S_PQ], h[S_RZ], h[S_RR]);
+                    set_error(buf);
+                    return SHTG_ERR_NONFINITE;
+                }
+                if (q.done[b]) continue;
+                const bool act = h[S_ACTIVE] != 0.0;
+                still += act;
+                if (act && h[S_RR] <= delta * delta) ready += 1;
+            }
+            q.since += nrun;
+            if (!(ready || !still || it >= opt.maxiter || q.since >= 400)) continue;
+            // x += scale x32 ; R = B - A X with the group's FP64-accurate operator
+            double2 *B = p->v64[0], *X = p->v64[1], *R = p->v64[2], *Tt = p->v64[6];
+            float2 *x32 = p->v32[4];
+            k_correct<<<s.vgrid, RT, 0, st>>>(X, x32, s.per, q.d_sc + 3 * nb);
+            p->prof.launches += 1;
+            SHTG_CHECK_LAUNCH("k_correct");
+            SHTG_CUDA(cudaMemsetAsync(x32, 0, sizeof(float2) * (size_t)s.nvec, st));
+            SHTG_TRY(matvec<double>(s, X, Tt));
+            c[g].stt.fp64_matvecs++;
+            c[g].stt.outer_steps++;
+            k_resid<<<grid_1d(s.nvec), RT, 0, st>>>(B, Tt, R, s.nvec);
+            p->prof.launches += 1;
+            SHTG_TRY(norms2(s, R, c[g].rr));
+            q.since = 0;
+            q.replace = true;
+        }
+    }
+    return SHTG_OK;
+}
+
+int cg_sample_grouped(int ng, Plan *const *ps, const shtg_problem *prs, double *const *outs,
+                      const shtg_cg_opts *o, shtg_cg_stats *stats, cudaStream_t st) {
+    if (ng < 1 || ng > SHTG_MAX_GROUPS) {
+        set_error("SHTG_GROUPED: 1 to " + std::to_string(SHTG_MAX_GROUPS) + " geometry groups per call");
+        return SHTG_ERR_ARG;
+    }
+    if (!o || (o->mode != SHTG_CG_MIXED && o->mode != SHTG_CG_MIXED_TC)) {
+        set_error("SHTG_GROUPED needs options with mode SHTG_CG_MIXED or SHTG_CG_MIXED_TC");
+        return SHTG_ERR_ARG;
+    }
+    if (o->precond != SHTG_PRECOND_NONE && o->precond != SHTG_PRECOND_DIAG && o->precond != SHTG_PRECOND_AZIM) {
+        set_error("SHTG_GROUPED supports SHTG_PRECOND_NONE, SHTG_PRECOND_DIAG and SHTG_PRECOND_AZIM");
+        return SHTG_ERR_ARG;
+    }
+    if (o->flags & (SHTG_SPLIT_RHS | SHTG_PROFILE)) {
+        set_error("SHTG_GROUPED does not combine with SHTG_SPLIT_RHS or SHTG_PROFILE");
+        return SHTG_ERR_ARG;
+    }
+    for (int g = 0; g < ng; ++g)
+        if (prs[g].ncomp != prs[0].ncomp) {
+            set_error("SHTG_GROUPED: every group needs the same ncomp");
+            return SHTG_ERR_ARG;
+        }
+    int64_t nbtot = 0;
+    for (int g = 0; g < ng; ++g) nbtot += (prs[g].nbatch > 0 ? prs[g].nbatch : 0);
+    if (nbtot > 65535) {
+        set_error("SHTG_GROUPED: at most 65535 realizations over all groups");
+        return SHTG_ERR_ARG;
+    }
+    std::vector<CgCall> c(ng);
+    for (int g = 0; g < ng; ++g) {
+        const int rc = cg_begin(ps[g], &prs[g], outs[g], o, st, c[g]);
+        if (rc != SHTG_OK) {
+            set_error("chain group " + std::to_string(g) + ": " + shtg_last_error_string());
+            return rc;
+        }
+    }
+    SHTG_TRY(mixed_solve_grp(ng, ps, c, st));
+    int worst = SHTG_OK;
+    for (int g = 0; g < ng; ++g) {
+        const int rc = cg_end(ps[g], c[g], outs[g], stats ? &stats[g] : nullptr, st);
+        if (rc != SHTG_OK && (worst == SHTG_OK || worst == SHTG_ERR_NOT_CONVERGED)) {
+            worst = rc;
+            set_error("chain group " + std::to_string(g) + ": " + shtg_last_error_string());
+        }
+    }
+    return worst;
 }
 
 }  // namespace shtg

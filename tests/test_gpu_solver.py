@@ -189,3 +189,30 @@ def test_graph_replay_matches_eager(mode):
     assert sg["converged"] == 1 and sg["iterations"] == se["iterations"]
     assert torch.equal(xg, xe)
     assert sg["launches"] == se["launches"]
+
+
+@pytest.mark.parametrize("mode", ["fp64", "mixed"])
+def test_more_realizations_than_scalar_threads(mode):
+    """1100 realizations in one batch (more than the 1024 threads of the CG
+    scalar kernels, more than 256 sets of pinned host scalars): a masked
+    N_side 4 / l_max 8 problem with per-realization data and white noise;
+    the oracle residual of sampled realizations, from the first and the
+    last thread strides."""
+    from paper_2306_15511_gb300 import Plan
+    ns, L, nb = 4, 8, 1100
+    p = C.masked_temperature(ns, L)
+    g = osht.healpix(ns)
+    rng = np.random.default_rng(21)
+    d = rng.normal(size=(nb, 1, g.npix)) * 20.0
+    w1 = rand_alm(L, rng, (nb, 1))
+    w2 = rng.normal(size=(nb, 1, g.npix))
+    plan = Plan(nside=ns, lmax=L, max_batch=nb)
+    x, st = plan.cg_sample(p.cl, p.bl, _cuda(p.ninv, torch.float64), _cuda(d, torch.float64),
+                           _cuda(w1, torch.complex128), _cuda(w2, torch.float64), tol=1e-8, mode=mode,
+                           maxiter=2000)
+    assert st["converged"] == 1, st
+    xh = x.cpu().numpy()
+    prob = osol.Problem(g, L, p.cl, p.bl, p.ninv)
+    for k in (0, 1, 1023, 1024, 1099):
+        r = osol.true_residual(prob, xh[k], prob.rhs(d[k], w1[k], w2[k]))
+        assert r <= 1.05e-8, (k, r, st)
