@@ -737,7 +737,9 @@ int plan_build(Plan *p) {
     }
     SHTG_TRY(dalloc(p, &p->d_ltab32, 5 * (int64_t)(p->lmax + 1)));
     SHTG_TRY(dalloc(p, &p->d_scal, 16 * (int64_t)p->max_batch));
-    SHTG_TRY(dalloc(p, &p->d_part, 4 * (int64_t)p->max_batch * SHTG_RED_BLOCKS + 4 * (int64_t)p->max_batch + 64));
+    // reduction partials [4 max_batch][RED_BLOCKS], then per-realization scalars
+    // of the mixed solver [4 max_batch] and per-realization sums [max_batch]
+    SHTG_TRY(dalloc(p, &p->d_part, 4 * (int64_t)p->max_batch * SHTG_RED_BLOCKS + 5 * (int64_t)p->max_batch + 64));
     SHTG_TRY(dalloc(p, &p->d_lsum, (int64_t)p->lmax + 1));
     SHTG_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
     SHTG_CUDA(cudaStreamCreateWithFlags(&p->work_stream, cudaStreamNonBlocking));
@@ -752,10 +754,11 @@ int plan_build(Plan *p) {
     // what an earlier plan left there)
     SHTG_CUDA(cudaMemset(p->d_scal, 0, sizeof(double) * 16 * (size_t)p->max_batch));
     SHTG_CUDA(cudaMemset(p->d_part, 0,
-                         sizeof(double) * (4 * (size_t)p->max_batch * SHTG_RED_BLOCKS + 4 * (size_t)p->max_batch + 64)));
+                         sizeof(double) * (4 * (size_t)p->max_batch * SHTG_RED_BLOCKS + 5 * (size_t)p->max_batch + 64)));
     SHTG_TRY(dalloc(p, &p->d_stage, nmp));
-    // pinned host scalars: the [max_batch][16] CG slots (host convergence checks)
-    SHTG_CUDA(cudaMallocHost((void **)&p->h_pinned, (16 * (size_t)p->max_batch + 64) * sizeof(double)));
+    // pinned host scalars: the [max_batch][16] CG slots (host convergence
+    // checks), then [max_batch] per-realization sums
+    SHTG_CUDA(cudaMallocHost((void **)&p->h_pinned, (17 * (size_t)p->max_batch + 64) * sizeof(double)));
     p->prof.ev.resize(16384);
     for (auto &e : p->prof.ev) SHTG_CUDA(cudaEventCreate(&e));
     p->prof.cls.reserve(8192);

@@ -282,6 +282,16 @@ __global__ void k_dot(const C *__restrict__ a, const C *__restrict__ c, int nc, 
     if (threadIdx.x == 0) part[((int64_t)b * nslot + slot) * RB + blockIdx.x] = s;
 }
 
+// out[b] = sum over the RB partials of realization b (slot 0 of 1), in the
+// order in which the host sums them
+__global__ void k_row_sums(const double *__restrict__ part, int nb, double *__restrict__ out) {
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < RB; ++k) s += part[(int64_t)b * RB + k];
+        out[b] = s;
+    }
+}
+
 __device__ __forceinline__ double sum_part(const double *part, int b, int nslot, int slot) {
     double s = 0.0;
     for (int k = 0; k < RB; ++k) s += part[((int64_t)b * nslot + slot) * RB + k];
@@ -1772,6 +1782,19 @@ static int mixed_solve_grp(int ng, Plan *const *ps, std::vector<CgCall> &c, cuda
         graphs = !(opt.flags & SHTG_NO_GRAPHS) && !(e && e[0] == '0');
     }
     IterGraph graph;
+    // fork / join events of the concurrent replacements
+    struct Events {
+        cudaEvent_t fork = nullptr;
+        std::vector<cudaEvent_t> join;
+        ~Events() {
+            if (fork) cudaEventDestroy(fork);
+            for (cudaEvent_t e : join)
+                if (e) cudaEventDestroy(e);
+        }
+    } ev;
+    SHTG_CUDA(cudaEventCreateWithFlags(&ev.fork, cudaEventDisableTiming));
+    ev.join.assign(ng, nullptr);
+    for (int g = 0; g < ng; ++g) SHTG_CUDA(cudaEventCreateWithFlags(&ev.join[g], cudaEventDisableTiming));
     int it = 0;
     for (;;) {
         // ---- stage starts (after a residual replacement, or the first one)
@@ -1837,7 +1860,8 @@ static int mixed_solve_grp(int ng, Plan *const *ps, std::vector<CgCall> &c, cuda
                                           cudaMemcpyDeviceToHost, st));
             }
         SHTG_CUDA(cudaStreamSynchronize(st));
-        // ---- host check per group; replacements where due
+        // ---- host check per group: which groups are due for a replacement
+        std::vector<int> due;
         for (int g = 0; g < ng; ++g) {
             GState &q = gs[g];
             if (q.finished) continue;
@@ -1863,22 +1887,48 @@ static int mixed_solve_grp(int ng, Plan *const *ps, std::vector<CgCall> &c, cuda
                 if (act && h[S_RR] <= delta * delta) ready += 1;
             }
             q.since += nrun;
-            if (!(ready || !still || it >= opt.maxiter || q.since >= 400)) continue;
-            // x += scale x32 ; R = B - A X with the group's FP64-accurate operator
+            if (ready || !still || it >= opt.maxiter || q.since >= 400) due.push_back(g);
+        }
+        if (due.empty()) continue;
+        // ---- the due groups' replacements, concurrently on their plans' own
+        // streams (forked from and joined back into st): x += scale x32,
+        // R = B - A X with the group's FP64-accurate operator, ||R||^2 per
+        // realization summed on the device in the order of norms2
+        SHTG_CUDA(cudaEventRecord(ev.fork, st));
+        for (int g : due) {
+            Plan *p = ps[g];
+            Solve &s = c[g].s;
+            const int nb = s.nb;
+            cudaStream_t ws = p->work_stream;
+            SHTG_CUDA(cudaStreamWaitEvent(ws, ev.fork, 0));
+            s.st = ws;
             double2 *B = p->v64[0], *X = p->v64[1], *R = p->v64[2], *Tt = p->v64[6];
             float2 *x32 = p->v32[4];
-            k_correct<<<s.vgrid, RT, 0, st>>>(X, x32, s.per, q.d_sc + 3 * nb);
-            p->prof.launches += 1;
+            k_correct<<<s.vgrid, RT, 0, ws>>>(X, x32, s.per, gs[g].d_sc + 3 * nb);
             SHTG_CHECK_LAUNCH("k_correct");
-            SHTG_CUDA(cudaMemsetAsync(x32, 0, sizeof(float2) * (size_t)s.nvec, st));
+            SHTG_CUDA(cudaMemsetAsync(x32, 0, sizeof(float2) * (size_t)s.nvec, ws));
             SHTG_TRY(matvec<double>(s, X, Tt));
+            k_resid<<<grid_1d(s.nvec), RT, 0, ws>>>(B, Tt, R, s.nvec);
+            k_dot<double2><<<s.rgrid, RT, 0, ws>>>(R, R, s.nc, s.nalm, p->d_mofidx, p->d_part, 0, 1);
+            double *rsum = p->d_part + 4 * (int64_t)p->max_batch * SHTG_RED_BLOCKS + 4 * (int64_t)p->max_batch;
+            k_row_sums<<<1, 256, 0, ws>>>(p->d_part, nb, rsum);
+            p->prof.launches += 4;
+            SHTG_CHECK_LAUNCH("grouped replacement");
+            SHTG_CUDA(cudaMemcpyAsync(p->h_pinned + 16 * (size_t)p->max_batch, rsum, sizeof(double) * nb,
+                                      cudaMemcpyDeviceToHost, ws));
+            SHTG_CUDA(cudaEventRecord(ev.join[g], ws));
+            SHTG_CUDA(cudaStreamWaitEvent(st, ev.join[g], 0));
+            s.st = st;
             c[g].stt.fp64_matvecs++;
             c[g].stt.outer_steps++;
-            k_resid<<<grid_1d(s.nvec), RT, 0, st>>>(B, Tt, R, s.nvec);
-            p->prof.launches += 1;
-            SHTG_TRY(norms2(s, R, c[g].rr));
-            q.since = 0;
-            q.replace = true;
+        }
+        SHTG_CUDA(cudaStreamSynchronize(st));
+        for (int g : due) {
+            Plan *p = ps[g];
+            const int nb = c[g].s.nb;
+            c[g].rr.assign(p->h_pinned + 16 * (size_t)p->max_batch, p->h_pinned + 16 * (size_t)p->max_batch + nb);
+            gs[g].since = 0;
+            gs[g].replace = true;
         }
     }
     return SHTG_OK;
