@@ -56,6 +56,37 @@ def test_chains_rejects_bad_arguments_without_gpu():
     assert b"own plan" in lib.shtg_last_error_string()
 
 
+def test_grouped_chains_rejects_options_without_gpu():
+    """SHTG_GROUPED checks its options before it touches a plan or the GPU:
+    the group count, the mode, the preconditioner, the flags it does not
+    combine with, equal ncomp and the total number of realizations."""
+    from paper_2306_15511_gb300 import _native as N
+    lib = N.load()
+
+    def call(ng, mode=N.CG_MIXED, precond=N.PRECOND_DIAG, flags=0, ncomp=(1,), nbatch=2):
+        plans = (ctypes.c_void_p * ng)(*[ctypes.c_void_p(4096 * (g + 1)) for g in range(ng)])
+        probs = (N.Problem * ng)()
+        for g in range(ng):
+            probs[g].ncomp = ncomp[g % len(ncomp)]
+            probs[g].nbatch = nbatch
+        outs = (ctypes.c_void_p * ng)()
+        o = N.CGOpts()
+        o.tol, o.maxiter, o.mode, o.precond, o.flags = 1e-6, 10, mode, precond, N.GROUPED | flags
+        rc = lib.shtg_cg_sample_chains(ng, plans, probs, outs, ctypes.byref(o), None, None)
+        return rc, lib.shtg_last_error_string()
+
+    for kw, msg in (({"ng": 17}, b"1 to 16"), ({"ng": 2, "mode": N.CG_FP64}, b"mode"),
+                    ({"ng": 2, "mode": N.CG_BLOCK}, b"mode"),
+                    ({"ng": 2, "precond": N.PRECOND_LOWL}, b"SHTG_PRECOND"),
+                    ({"ng": 2, "flags": N.SPLIT_RHS}, b"SPLIT_RHS"),
+                    ({"ng": 2, "flags": N.PROFILE}, b"SPLIT_RHS or SHTG_PROFILE"),
+                    ({"ng": 2, "ncomp": (1, 3)}, b"ncomp"),
+                    ({"ng": 16, "nbatch": 4096}, b"65535")):
+        rc, err = call(**kw)
+        assert rc == -1, (kw, rc)
+        assert msg in err, (kw, err)
+
+
 def test_binding_constants_match_header():
     """Every #define the binding mirrors has the header's value, and the
     option struct keeps the header's field order."""
@@ -67,6 +98,7 @@ def test_binding_constants_match_header():
              "ARITH_DF64": "SHTG_ARITH_DF64", "CG_FP64": "SHTG_CG_FP64", "CG_MIXED": "SHTG_CG_MIXED",
              "CG_MIXED_TC": "SHTG_CG_MIXED_TC", "CG_BLOCK": "SHTG_CG_BLOCK", "BLOCK_SOLVER": "SHTG_BLOCK_SOLVER", "HOST_INPUTS": "SHTG_HOST_INPUTS",
              "PROFILE": "SHTG_PROFILE", "NO_GRAPHS": "SHTG_NO_GRAPHS", "SPLIT_RHS": "SHTG_SPLIT_RHS",
+             "GROUPED": "SHTG_GROUPED",
              "SPIN0": "SHTG_SPIN0",
              "SPIN2": "SHTG_SPIN2", "PRECOND_NONE": "SHTG_PRECOND_NONE",
              "PRECOND_DIAG": "SHTG_PRECOND_DIAG", "PRECOND_LOWL": "SHTG_PRECOND_LOWL",
