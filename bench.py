@@ -669,7 +669,9 @@ def measure_extras(plan, inp, dev, kw, step, full_solve=True):
             kwf["precond"] = pc
             t, (_, st) = _event_time(lambda: plan.cg_sample(inp["cl"], inp["bl"], inp["ninv"], inp["d"],
                                                             inp["w1"], inp["w2"], **kwf))
-            ex[key] = {"precond": pc, "time_to_1e-6_s": t, "iterations": st["iterations"],
+            lbl = f" (l_b {kw['block_lmax'] or min(LMAX, 1024)})" if pc == "azim" else ""
+            ex[key] = {"precond": pc + lbl, "time_to_1e-6_s": t,
+                       "iterations": st["iterations"],
                        "fp64_matvecs": st["fp64_matvecs"], "converged": bool(st["converged"]),
                        "rel_residual": st["rel_residual"], "ms_setup": st["ms_setup"], "ms_rhs": st["ms_rhs"]}
     # the headline steps with native FP64 residual replacements and RHS
@@ -717,6 +719,17 @@ def measure_extras(plan, inp, dev, kw, step, full_solve=True):
             "speedup_vs_fp64_df64": tf / tm, "speedup_vs_fp64_native": native / tm,
             "note": ("blocks kept from the first solve; native FP64 = its measured fixed cost + the FP64 "
                      "form's measured iteration count x its measured s/iteration")}
+        # the azimuthal blocks over fewer multipoles: a cheaper set-up (the
+        # factorizations grow as l_b^4), more iterations
+        for lb in (512, 256):
+            kwf = dict(kw)
+            kwf.update(maxiter=6000, precond="azim", block_lmax=lb)
+            t, (_, st) = _event_time(lambda: plan.cg_sample(inp["cl"], inp["bl"], inp["ninv"], inp["d"],
+                                                            inp["w1"], inp["w2"], **kwf))
+            ex[f"mixed_full_solve_azim_lb{lb}"] = {
+                "precond": f"azim (l_b {lb})", "time_to_1e-6_s": t, "iterations": st["iterations"],
+                "fp64_matvecs": st["fp64_matvecs"], "converged": bool(st["converged"]),
+                "rel_residual": st["rel_residual"], "ms_setup": st["ms_setup"], "ms_rhs": st["ms_rhs"]}
     ex["masked_nside256"] = measure_masked_pair(dev, kw["precond"])
     if "mixed_full_solve" in ex:
         fs = ex["mixed_full_solve"]
