@@ -43,7 +43,9 @@ namespace shtg {
 namespace {
 
 constexpr int GT = 32;      // Gram tile and pair chunk
-constexpr int AZT = 256;    // threads of the factor kernels
+constexpr int AZT = 256;    // threads of the ring-sum kernel
+constexpr int AZF = 1024;   // threads of the factor kernels (one CTA per m: the largest block alone
+                            // bounds the launch, so its rank-1 updates need every warp of the SM)
 
 __host__ __device__ __forceinline__ int64_t tri(int64_t i) { return i * (i + 1) / 2; }
 
@@ -143,12 +145,19 @@ __global__ void k_az_prof(int lmax, int lb, int npairs, int m0, int spin2, const
 // Gram matrices of a chunk, packed lower triangles: grid.x the 32 x 32
 // tiles (I >= J) of the largest block, grid.y the m of the chunk, grid.z the
 // component (0: T from lambda with the T weights; 1: E from lw, lx with the
-// P weights); 16 x 16 threads with 2 x 2 entries each.
+// P weights); 16 x 16 threads with 2 x 2 entries each.  The I rows of a pair
+// chunk are staged already multiplied by the pair weights of both parities
+// (W_N + W_S for l + l' even, W_N - W_S for odd; the tile offsets are even,
+// so a thread's entry (a, b) has parity (a + b) & 1), which leaves one FP64
+// multiply-add per profile product on GB300's narrow FP64 pipe.
 __global__ void __launch_bounds__(256) k_az_gram(int lb, int npairs, int m0, const int64_t *__restrict__ poff,
                                                  const int64_t *__restrict__ goff, const double *__restrict__ pl,
                                                  const double *__restrict__ pw, const double *__restrict__ px,
                                                  const double *__restrict__ w, double *__restrict__ G) {
-    __shared__ double sI[2][GT][GT + 1], sJ[2][GT][GT + 1], sw[2][GT];
+    // dynamic: sIw[par][prof][GT][GT] then sJ[prof][GT][GT + 1]
+    extern __shared__ __align__(16) unsigned char az_raw[];
+    double(*sIw)[2][GT][GT] = reinterpret_cast<double(*)[2][GT][GT]>(az_raw);
+    double(*sJ)[GT][GT + 1] = reinterpret_cast<double(*)[GT][GT + 1]>(az_raw + sizeof(double) * 4 * GT * GT);
     const int m = m0 + blockIdx.y, c = blockIdx.z;
     const int k = lb + 1 - m;
     const int nt = (k + GT - 1) / GT;
@@ -171,33 +180,39 @@ __global__ void __launch_bounds__(256) k_az_gram(int lb, int npairs, int m0, con
             const int p = p0 + q;
             const int li = I * GT + r, lj = J * GT + r;
             const bool pi = p < npairs && li < k, pj = p < npairs && lj < k;
-            sI[0][r][q] = pi ? A0[(int64_t)li * npairs + p] : 0.0;
+            const double w0 = p < npairs ? wc[p] : 0.0, w1 = p < npairs ? wc[npairs + p] : 0.0;
+            const double a0 = pi ? A0[(int64_t)li * npairs + p] : 0.0;
+            sIw[0][0][r][q] = a0 * w0;
+            sIw[1][0][r][q] = a0 * w1;
             sJ[0][r][q] = pj ? A0[(int64_t)lj * npairs + p] : 0.0;
             if (nprof == 2) {
-                sI[1][r][q] = pi ? A1[(int64_t)li * npairs + p] : 0.0;
+                const double a1 = pi ? A1[(int64_t)li * npairs + p] : 0.0;
+                sIw[0][1][r][q] = a1 * w0;
+                sIw[1][1][r][q] = a1 * w1;
                 sJ[1][r][q] = pj ? A1[(int64_t)lj * npairs + p] : 0.0;
             }
         }
-        for (int e = threadIdx.x; e < GT; e += 256) {
-            const int p = p0 + e;
-            sw[0][e] = p < npairs ? wc[p] : 0.0;
-            sw[1][e] = p < npairs ? wc[npairs + p] : 0.0;
-        }
         __syncthreads();
-#pragma unroll
-        for (int a = 0; a < 2; ++a)
-#pragma unroll
-            for (int b = 0; b < 2; ++b) {
-                const int par = (2 * ty + a + 2 * tx + b) & 1;   // parity of l + l' (tile offsets are even)
-                double s = 0.0;
-#pragma unroll 4
-                for (int q = 0; q < GT; ++q) {
-                    double v = sI[0][2 * ty + a][q] * sJ[0][2 * tx + b][q];
-                    if (nprof == 2) v = fma(sI[1][2 * ty + a][q], sJ[1][2 * tx + b][q], v);
-                    s = fma(v, sw[par][q], s);
-                }
-                acc[a][b] += s;
+        const int r0 = 2 * ty, r1 = 2 * ty + 1, c0 = 2 * tx, c1 = 2 * tx + 1;
+        if (nprof == 1) {
+#pragma unroll 8
+            for (int q = 0; q < GT; ++q) {
+                const double j0 = sJ[0][c0][q], j1 = sJ[0][c1][q];
+                acc[0][0] = fma(sIw[0][0][r0][q], j0, acc[0][0]);
+                acc[0][1] = fma(sIw[1][0][r0][q], j1, acc[0][1]);
+                acc[1][0] = fma(sIw[1][0][r1][q], j0, acc[1][0]);
+                acc[1][1] = fma(sIw[0][0][r1][q], j1, acc[1][1]);
             }
+        } else {
+#pragma unroll 4
+            for (int q = 0; q < GT; ++q) {
+                const double j0 = sJ[0][c0][q], j1 = sJ[0][c1][q], k0 = sJ[1][c0][q], k1 = sJ[1][c1][q];
+                acc[0][0] = fma(sIw[0][1][r0][q], k0, fma(sIw[0][0][r0][q], j0, acc[0][0]));
+                acc[0][1] = fma(sIw[1][1][r0][q], k1, fma(sIw[1][0][r0][q], j1, acc[0][1]));
+                acc[1][0] = fma(sIw[1][1][r1][q], k0, fma(sIw[1][0][r1][q], j0, acc[1][0]));
+                acc[1][1] = fma(sIw[0][1][r1][q], k1, fma(sIw[0][0][r1][q], j1, acc[1][1]));
+            }
+        }
         __syncthreads();
     }
     double *Gm = G + goff[m] + (int64_t)c * tri(k);
@@ -209,6 +224,7 @@ __global__ void __launch_bounds__(256) k_az_gram(int lb, int npairs, int m0, con
             if (i < k && j <= i) Gm[tri(i) + j] = acc[a][b];
         }
 }
+constexpr size_t AZ_GRAM_SMEM = sizeof(double) * (4 * GT * GT + 2 * GT * (GT + 1));
 
 // H_m = b b G + S^-1 (isc) over the rows [T l = m .. lb, E l = m .. lb];
 // held multipoles give identity rows
@@ -247,7 +263,7 @@ __global__ void k_az_assemble(int lb, int ncb, const int64_t *__restrict__ goff,
 // One CTA per m: Cholesky H = R R^T in place (packed lower, right-looking;
 // column j of the trailing update staged in shared memory).  flag bit 1: a
 // pivot was not positive.
-__global__ void __launch_bounds__(AZT) k_az_chol(int lb, int ncb, const int64_t *__restrict__ hoff, double *H,
+__global__ void __launch_bounds__(AZF) k_az_chol(int lb, int ncb, const int64_t *__restrict__ hoff, double *H,
                                                  int *__restrict__ flag) {
     extern __shared__ __align__(16) unsigned char az_raw[];
     double *col = reinterpret_cast<double *>(az_raw);
@@ -271,10 +287,12 @@ __global__ void __launch_bounds__(AZT) k_az_chol(int lb, int ncb, const int64_t 
         }
         __syncthreads();
         // A_ik -= R_ij R_kj for j < k <= i: one warp per row, lanes over k
+        // (unrolled, so that each lane has several independent loads in flight)
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         for (int i = j + 1 + warp; i < n; i += blockDim.x >> 5) {
             const double rij = col[i];
             double *row = A + tri(i);
+#pragma unroll 4
             for (int kk = j + 1 + lane; kk <= i; kk += 32) row[kk] = fma(-rij, col[kk], row[kk]);
         }
         __syncthreads();
@@ -285,7 +303,7 @@ __global__ void __launch_bounds__(AZT) k_az_chol(int lb, int ncb, const int64_t 
 // the last: X_jj = 1 / R_jj, X_kj = -X_jj sum_{j < t <= k} X_kt R_tj for
 // k > j (the trailing block already inverted; column j of R staged in
 // shared memory, one warp per row k).
-__global__ void __launch_bounds__(AZT) k_az_trinv(int lb, int ncb, const int64_t *__restrict__ hoff, double *H) {
+__global__ void __launch_bounds__(AZF) k_az_trinv(int lb, int ncb, const int64_t *__restrict__ hoff, double *H) {
     extern __shared__ __align__(16) unsigned char az_raw[];
     double *col = reinterpret_cast<double *>(az_raw);
     __shared__ double s_d;
@@ -304,6 +322,7 @@ __global__ void __launch_bounds__(AZT) k_az_trinv(int lb, int ncb, const int64_t
         for (int k = j + 1 + warp; k < n; k += blockDim.x >> 5) {
             const double *row = A + tri(k);
             double s = 0.0;
+#pragma unroll 4
             for (int t = j + 1 + lane; t <= k; t += 32) s = fma(row[t], col[t], s);
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -685,6 +704,7 @@ int az_setup(Plan *p, int lb, int nc, double isc, cudaStream_t st) {
     if (rebuild) {
         q.gram_ok = false;
         q.inv_ok = false;
+        if (AZ_GRAM_SMEM > 48 * 1024) SHTG_CUDA(allow_max_smem(k_az_gram));
         k_az_weights<<<dim3(np, nch), AZT, 0, st>>>(p->d_ninv64, p->npix, p->d_ofs, p->d_nphi, p->nring, np, q.w);
         SHTG_CHECK_LAUNCH("k_az_weights");
         p->prof.launches += 1;
@@ -708,8 +728,8 @@ int az_setup(Plan *p, int lb, int nc, double isc, cudaStream_t st) {
                                                                  p->d_ls2_64, p->d_st2_64, q.pl, q.pw, q.px);
             SHTG_CHECK_LAUNCH("k_az_prof");
             const int nt = (lb + 1 - m0 + GT - 1) / GT;
-            k_az_gram<<<dim3(nt * (nt + 1) / 2, nm, ncb), 256, 0, st>>>(lb, np, m0, q.poff, q.goff, q.pl, q.pw,
-                                                                        q.px, q.w, q.G);
+            k_az_gram<<<dim3(nt * (nt + 1) / 2, nm, ncb), 256, AZ_GRAM_SMEM, st>>>(lb, np, m0, q.poff, q.goff, q.pl,
+                                                                                   q.pw, q.px, q.w, q.G);
             SHTG_CHECK_LAUNCH("k_az_gram");
             p->prof.launches += 2;
             // the offsets are read by this chunk's kernels before the next copy
@@ -733,9 +753,9 @@ int az_setup(Plan *p, int lb, int nc, double isc, cudaStream_t st) {
         SHTG_CUDA(allow_max_smem(k_az_chol));
         SHTG_CUDA(allow_max_smem(k_az_trinv));
     }
-    k_az_chol<<<lb + 1, AZT, csm, st>>>(lb, ncb, q.hoff, q.H, q.flag);
+    k_az_chol<<<lb + 1, AZF, csm, st>>>(lb, ncb, q.hoff, q.H, q.flag);
     SHTG_CHECK_LAUNCH("k_az_chol");
-    k_az_trinv<<<lb + 1, AZT, csm, st>>>(lb, ncb, q.hoff, q.H);
+    k_az_trinv<<<lb + 1, AZF, csm, st>>>(lb, ncb, q.hoff, q.H);
     SHTG_CHECK_LAUNCH("k_az_trinv");
     const int nt = (ncb * (lb + 1) + GT - 1) / GT;
     k_az_minv<<<dim3(nt * (nt + 1) / 2, lb + 1), 256, 0, st>>>(lb, ncb, q.hoff, q.moff, q.H, q.M64, q.M32);
