@@ -1,5 +1,6 @@
 """Host-side parts of bench.py (no GPU): the CPU-baseline extrapolation, the
-reference arm's JSON line, the flop counts behind the rooflines, the clock
+reference arm's JSON line, the flop counts behind the rooflines, the DRAM
+traffic record and its source hashes, the time-to-solution list, the clock
 sampler's parsing and the peak-file fallback."""
 import argparse
 import json
@@ -183,3 +184,29 @@ def test_measured_peaks_fallback(monkeypatch, tmp_path):
     (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6682.5, "bf16_tflops": 1900.3}')
     peaks, src = bench.measured_peaks()
     assert src == "measured" and peaks["hbm_gbs"] == 6682.5
+
+
+def test_committed_traffic_record_matches_the_current_sources():
+    """profiles/traffic.json holds the tensor-core classes' DRAM bytes per
+    Fourier coefficient with the sources' hash at the capture; the bench
+    reports them only while the sources are unchanged, so a record that no
+    longer matches would silently drop roofline.traffic."""
+    path = bench.os.path.join(bench.ROOT, "profiles", "traffic.json")
+    rec = json.load(open(path))
+    for cls in ("leg_synth_fp32", "leg_analysis_fp32"):
+        assert rec[cls]["sources_sha"] == bench.sources_hash(bench.CLASS_SOURCES[cls]), cls
+        assert bench.traffic_record(cls, 1.0) == rec[cls]["dram_bytes_per_unit"]
+
+
+def test_time_to_solution_lists_every_full_solve_fastest_first():
+    ex = {"mixed_full_solve": {"precond": "diag", "time_to_1e-6_s": 35.0, "iterations": 1736, "converged": True,
+                               "rel_residual": 9e-7},
+          "mixed_full_solve_azim": {"precond": "azim (l_b 1024)", "time_to_1e-6_s": 12.7, "iterations": 200,
+                                    "converged": True, "rel_residual": 2e-7},
+          "mixed_full_solve_azim_lb512": {"precond": "azim (l_b 512)", "time_to_1e-6_s": 11.3, "iterations": 440,
+                                          "converged": True, "rel_residual": 9e-7},
+          "sht_pairs_per_s": {}}
+    out = bench._time_to_solution(ex)
+    assert [o["precond"] for o in out] == ["azim (l_b 512)", "azim (l_b 1024)", "diag"]
+    assert out[0]["fp32_iterations"] == 440
+    assert bench._time_to_solution({}) is None
