@@ -218,7 +218,11 @@ class Plan:
         the diagonal above) or "azim" (the exact per-m inverse of the
         operator with N^-1 averaged along every ring, App. A's blocks of T
         and E, for l <= block_lmax, 0 = min(lmax, 1024), plus the diagonal
-        elsewhere); both built with the first realization's cl_scale.
+        elsewhere); both built with the first realization's cl_scale and kept
+        by the plan while N^-1, C_l, the beam and the scale are unchanged.
+        The azimuthal blocks' set-up grows as block_lmax^3 (Gram sums) to
+        block_lmax^4 (factorizations): a smaller block_lmax makes the first
+        call cheaper and later ones take more iterations.
 
         split: solve the mean field (Eq. mean-field-map) and the fluctuation
         (Eq. fluc-map) as separate systems of one batch; the result is then
