@@ -1001,6 +1001,10 @@ int ring_fused_grp(int ng, Plan *const *ps, typename VT<T>::C *const *FG, const 
             groups = (a.nmaps + a.mpg - 1) / a.mpg;
             G.first[e] = (int)total;
             total += (int64_t)G.count[e] * groups;
+            if (total > 0x7fffffff) {
+                set_error("grouped ring launch: too many CTAs");
+                return SHTG_ERR_ARG;
+            }
         }
         G.first[G.ne] = (int)total;
         int rc = SHTG_OK;
