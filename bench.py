@@ -21,7 +21,8 @@ FP64-accurate residual replacements are not counted), summed over ranks.
 Ranks run independent replicas (weak scaling, no data-path collective);
 `--gpus N` spawns N local ranks itself unless it runs under torchrun.
 
-Extras: the full solve to a true FP64-accurate relative residual of 1e-6
+Extras (at N = 1 only, like the CPU baseline): the full solve to a true
+FP64-accurate relative residual of 1e-6
 with every preconditioner (the azimuthal blocks: App. A's per-m blocks of T
 and E from the ring-averaged N^-1, exact up to l = 1024; the two-level low
 block; the diagonal), fastest first in the line's `time_to_solution`;
@@ -486,8 +487,9 @@ def gpu_rank(args):
     inner, outer = sp["iterations"], sp["fp64_matvecs"]
     peaks_alu = fma_peaks()
 
+    # the extras and the CPU baseline describe one GPU: measured at N = 1 only
     extras = {}
-    if not args.no_extras:
+    if not args.no_extras and world == 1:
         extras = measure_extras(plan, inp, dev, kw, step, full_solve=not args.no_full_solve)
 
     # ------------------------------------------------------------ roofline
@@ -568,7 +570,7 @@ def gpu_rank(args):
                               "frac": None, "traffic": None, "kernel": dom}
 
     cpu = None
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:
         try:
             cpu = oracle_sample(strides=(16, 4))
             cpu.pop("per_realization_s", None)
