@@ -148,8 +148,9 @@ int shtg_plan_create(int geom, int nside_or_nring, int nphi_gauss, int lmax, int
 int shtg_plan_destroy(shtg_plan *plan);
 int shtg_plan_get_info(const shtg_plan *plan, shtg_plan_info *info);
 const char *shtg_last_error_string(void);
-/* Interface version: 2 (1 + SHTG_DF64 and shtg_cg_opts.fp64_arith, which was a
- * reserved field set to 0 with the same layout). */
+/* Interface version: 3 (2 + the flag SHTG_GROUPED of shtg_cg_sample_chains;
+ * 2 = 1 + SHTG_DF64 and shtg_cg_opts.fp64_arith, which was a reserved field
+ * set to 0 with the same layout). */
 int shtg_version(void);
 
 /* Y (Sect. 2.1, a(n) = sum a_lm Y_lm(n); App. A pixel sums):

@@ -164,7 +164,7 @@ using namespace shtg;
 
 extern "C" {
 
-int shtg_version(void) { return 2; }
+int shtg_version(void) { return 3; }
 
 const char *shtg_last_error_string(void) { return g_err.c_str(); }
 

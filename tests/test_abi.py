@@ -27,7 +27,7 @@ def test_library_exports_declared_symbols():
 def test_version_and_error_string_without_gpu():
     from paper_2306_15511_gb300 import _native
     lib = _native.load()
-    assert lib.shtg_version() >= 1
+    assert lib.shtg_version() == 3
     # argument validation happens before any CUDA call
     h = ctypes.c_void_p()
     rc = lib.shtg_plan_create(7, 8, 0, 16, 1, 1, ctypes.byref(h))
